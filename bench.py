@@ -1,0 +1,433 @@
+#!/usr/bin/env python
+"""Throughput of the isosurface 3D-GS training step and render on one GB300.
+
+One step = one optimiser step on one 1920x1080 view: projection, binning +
+radix sort, forward blend, masked L1 + SSIM loss, backward (blend replay +
+projection), Adam.  Metric: train iters/s at 10M Gaussians, 1080p (plus render
+Mpix/s).  Inputs are synthetic (see paper_2509_12138_gb300/workload.py) and
+resident in HBM; params + Adam state (9.6 GB) and per-view GT are far larger
+than L2, so no explicit flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+Multi-GPU: one process per GPU under torchrun; each rank trains an independent
+problem (weak scaling), no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # the metric's workload: 10M Gaussians (16-mode interface), SH degree 3, 1080p, 128 orbital views
+    "iso10M-1080p": dict(n=10_000_000, modes=16, views=128, W=1920, H=1080),
+    # smaller workloads for quick checks
+    "iso1M-1080p": dict(n=1_000_000, modes=8, views=64, W=1920, H=1080),
+    "iso200k-540p": dict(n=200_000, modes=8, views=16, W=960, H=540),
+}
+METRIC = "train iters/s & render Mpix/s at 10M Gaussians 1080p; PSNR vs plain form"
+LAMBDA_SSIM = 0.2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="iso10M-1080p", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-window", type=int, default=8, help="CPU sample: 1/(w*w) of the view's pixels")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        rows = []
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 10:
+                continue
+            if self.uuid and self.uuid not in f[1]:
+                continue
+            rows.append(f)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def device_uuid(dev):
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- CPU baseline (oracle)
+def cpu_window_camera(cams, v, frac: int):
+    """Camera block of a centred (W/frac x H/frac) window of view v (same intrinsics, shifted principal point)."""
+    import oracle
+    cam = oracle.camera_block(cams, v).copy()
+    W, H = int(cam[22]), int(cam[23])
+    w, h = W // frac, H // frac
+    x0, y0 = (W - w) // 2, (H - h) // 2
+    cam[14] -= x0
+    cam[15] -= y0
+    cam[22], cam[23] = w, h
+    return cam, (x0, y0, w, h)
+
+
+class CpuSample:
+    """A bounded sample of one training iteration for the FP64 oracle.
+
+    Per-Gaussian stages (projection, projection Jacobian, Adam) run on a 1/gfrac
+    subset of the Gaussians and are scaled by gfrac; per-pixel stages (blend,
+    loss, reverse replay) run on a centred window holding 1/frac^2 of the view's
+    pixels, with every Gaussian that reaches the window, and are scaled by frac^2."""
+
+    def __init__(self, scene, frac: int = 8, gfrac: int = 100, view: int = 1):
+        import oracle
+        oracle.build()
+        self.frac, self.gfrac = frac, gfrac
+        g64 = {k: np.asarray(v, np.float64) for k, v in scene.init.items()}
+        self.cam, (x0, y0, w, h) = cpu_window_camera(scene.cams, view, frac)
+        self.gt = scene.gt[view, :, y0:y0 + h, x0:x0 + w].double().cpu().numpy()
+        self.mask = scene.mask[view, y0:y0 + h, x0:x0 + w].cpu().numpy()
+        # Gaussians that reach the window (selection is set-up, not timed)
+        p = oracle.project(g64, self.cam)
+        sel = np.nonzero(p["tiles"] > 0)[0]
+        self.win = {k: v[sel] for k, v in g64.items()}
+        sub = np.arange(0, scene.n, gfrac)
+        self.sub = {k: v[sub] for k, v in g64.items()}
+        self.sub_cam = oracle.camera_block(scene.cams, view)
+        self.desc = (f"FP64 oracle, 1 training iteration of the {scene.n}-Gaussian scene estimated from: projection, "
+                     f"projection Jacobian and Adam on every {gfrac}th Gaussian (x{gfrac}); blend, loss and reverse "
+                     f"replay on a centred {w}x{h} window (1/{frac * frac} of the {scene.width}x{scene.height} view, "
+                     f"{len(sel)} Gaussians reach it) (x{frac * frac})")
+        self.cores = oracle.num_threads()
+
+    def step(self) -> float:
+        """Seconds of one full iteration, estimated from the timed sample."""
+        import oracle
+        bg = np.ones(3)
+        t0 = time.perf_counter()
+        oracle.project(self.sub, self.sub_cam)
+        n = self.sub["means"].shape[0]
+        rng = np.random.default_rng(0)
+        g2d = dict(dxy=rng.standard_normal((n, 2)), dconic=rng.standard_normal((n, 3)),
+                   dopacity=rng.standard_normal(n), drgb=rng.standard_normal((n, 3)))
+        grads = oracle.project_backward(self.sub, self.sub_cam, g2d)
+        flat = oracle.flatten_params(self.sub)
+        oracle.adam(flat, grads, np.zeros_like(flat), np.zeros_like(flat), 1e-3, 0.9, 0.999, 1e-15, 1)
+        t_gauss = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        r = oracle.render(self.win, self.cam, bg)
+        _, dimg = oracle.loss(r["img"], self.gt, self.mask, LAMBDA_SSIM)
+        oracle.render_backward(self.win, self.cam, bg, dimg)
+        t_pix = time.perf_counter() - t0
+        return t_gauss * self.gfrac + t_pix * self.frac * self.frac
+
+
+def cpu_baseline(scene, frac: int):
+    cs = CpuSample(scene, frac)
+    t = cs.step()
+    return {"value": 1.0 / t, "unit": "iters/s", "cores": cs.cores, "kind": "oracle", "sample": cs.desc,
+            "seconds_per_iter_est": t}
+
+
+# ---------------------------------------------------------------- our arm
+def kernel_launch_count(frame, lam):
+    tile_bits = max(1, math.ceil(math.log2(frame.n_tiles)))
+    unit_bits = math.ceil(math.log2(frame.units.n)) if frame.units.n > 1 else 0
+    passes = (32 + tile_bits + unit_bits + 7) // 8
+    pre = 1
+    sort = 4 + 3 * passes + 1
+    fwd = 1
+    loss = 1 + (2 if lam > 0 else 1) + 1
+    bwd = 2
+    adam = 2
+    return pre + sort + fwd + loss + bwd + adam
+
+
+def run_ours(args, wl, rank, world):
+    import torch
+    import paper_2509_12138_gb300 as gs
+    from paper_2509_12138_gb300 import workload
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    scene = workload.isosurface_scene(wl["n"], wl["modes"], wl["views"], wl["W"], wl["H"], sh_degree=3,
+                                      seed=rank, device=dev)
+    N, W, H = scene.n, scene.width, scene.height
+    params = gs.pack_params(scene.init, 3, dev)
+    frame = gs.Frame(N, gs.Units.single(N), W, H, 3, device=dev, max_instances=6 * N)
+    opt = gs.Adam(params, 3, extent=1.0, lr_steps=7000)
+    bg = scene.bg
+    V = len(scene.cams)
+
+    # stage boundaries for per-kernel timing (events on the launching stream)
+    def step(v, ev=None):
+        cam = scene.cam(v)
+        if ev: ev[0].record()
+        frame.preprocess(params, cam)
+        if ev: ev[1].record()
+        frame.sort()
+        if ev: ev[2].record()
+        frame.render(bg)
+        if ev: ev[3].record()
+        frame.loss(scene.gt[v:v + 1], scene.mask[v:v + 1], LAMBDA_SSIM)
+        if ev: ev[4].record()
+        frame.blend_backward(bg)
+        if ev: ev[5].record()
+        frame.project_backward(params, cam)
+        if ev: ev[6].record()
+        opt.step(frame.grads)
+        if ev: ev[7].record()
+
+    stages = ["preprocess", "bin_sort", "render_fwd", "loss", "blend_bwd", "project_bwd", "adam"]
+    for w in range(args.warmup):
+        step(w % V)
+    torch.cuda.synchronize()
+    st = frame.read_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} after warm-up")
+    instances = frame.instances()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = ClockSampler(device_uuid(dev))
+    clocks.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for k in range(args.steps):
+        step((args.warmup + k) % V, evs[k])
+    t1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms_total = t0.elapsed_time(t1)
+    stage_ms = np.zeros(len(stages))
+    for e in evs:
+        for s in range(len(stages)):
+            stage_ms[s] += e[s].elapsed_time(e[s + 1])
+    stage_ms /= args.steps
+
+    # render-only (a1-a3) for Mpix/s
+    torch.cuda.synchronize()
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    r0.record()
+    for k in range(args.steps):
+        frame.forward(params, scene.cam(k % V), bg)
+    r1.record()
+    torch.cuda.synchronize()
+    ms_render = r0.elapsed_time(r1) / args.steps
+    clk = clocks.stop()
+
+    # end to end through the public API with host buffers: each step copies its GT view and mask from
+    # pinned host memory, runs the step and reads the loss back
+    gt_host = torch.empty((4, 3, H, W), dtype=torch.float32).pin_memory()
+    mask_host = torch.empty((4, H, W), dtype=torch.uint8).pin_memory()
+    for v in range(4):
+        gt_host[v].copy_(scene.gt[v])
+        mask_host[v].copy_(scene.mask[v])
+    gt_dev = torch.empty((1, 3, H, W), dtype=torch.float32, device=dev)
+    mask_dev = torch.empty((1, H, W), dtype=torch.uint8, device=dev)
+    loss_host = torch.empty(args.steps, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    barrier()
+    e0 = time.perf_counter()
+    for k in range(args.steps):
+        v = k % 4
+        gt_dev[0].copy_(gt_host[v], non_blocking=True)
+        mask_dev[0].copy_(mask_host[v], non_blocking=True)
+        cam = scene.cam(v)
+        frame.preprocess(params, cam)
+        frame.sort()
+        frame.render(bg)
+        frame.loss(gt_dev, mask_dev, LAMBDA_SSIM)
+        frame.backward(params, cam, bg)
+        opt.step(frame.grads)
+        loss_host[k:k + 1].copy_(frame.loss_val, non_blocking=True)
+    torch.cuda.synchronize()
+    e_sec = time.perf_counter() - e0
+    barrier()
+    return dict(scene=scene, frame=frame, ms_total=ms_total, stage_ms=stage_ms, stages=stages, ms_render=ms_render,
+                clocks=clk, e2e_sec=e_sec, instances=instances, h2d=(3 * H * W * 4 + H * W), d2h=4,
+                launches=kernel_launch_count(frame, LAMBDA_SSIM) * args.steps, N=N, W=W, H=H)
+
+
+def roofline(res):
+    """Achieved vs peak for the dominant stage (largest share of the step)."""
+    peaks = {}
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        peaks = json.load(open(p))
+    hbm = peaks.get("hbm_gbs")
+    src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    N, I = res["N"], res["instances"]
+    passes = 6
+    bytes_per = {
+        # algorithmic bytes per launch
+        "preprocess": N * (59 * 4 + 52),
+        "bin_sort": N * 8 + I * (12 + passes * 32 + 16),
+        "project_bwd": N * (59 * 4 + 40 + 4 + 59 * 4),
+        "adam": N * 59 * 28,
+        "loss": res["W"] * res["H"] * (3 * 4 * 3 + 1 + 3 * 4 * 6),
+    }
+    order = np.argsort(-res["stage_ms"])
+    out = None
+    for k in order:
+        name = res["stages"][k]
+        if name in bytes_per:
+            ms = res["stage_ms"][k]
+            ach = bytes_per[name] / (ms * 1e-3) / 1e9
+            out = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                   "frac": round(ach / hbm, 4), "traffic": None, "peak_source": src,
+                   "share": round(float(ms / res["stage_ms"].sum()), 4)}
+            break
+    return out
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    config = {"workload": args.workload, "gaussians": wl["n"], "width": wl["W"], "height": wl["H"],
+              "views": wl["views"], "sh_degree": 3, "loss": f"masked L1 + {LAMBDA_SSIM} D-SSIM",
+              "l2": "inputs larger than L2 (params+Adam state 9.6 GB at 10M)"}
+    if args.impl == "reference":
+        return run_reference(args, wl, rank, world, config)
+    import torch
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    res = run_ours(args, wl, rank, world)
+    ms_step = res["ms_total"] / args.steps
+    t_max = res["ms_total"]
+    e2e_sec = res["e2e_sec"]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_max, e2e_sec], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max, e2e_sec = float(t[0]), float(t[1])
+    value = world * args.steps / (t_max * 1e-3)
+    mpix = world * res["W"] * res["H"] / (res["ms_render"] * 1e-3) / 1e6
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+        "render_mpix_s": round(mpix, 1), "render_ms": round(res["ms_render"], 4),
+        "stage_ms": {k: round(float(v), 4) for k, v in zip(res["stages"], res["stage_ms"])},
+        "instances_per_view": res["instances"],
+        "e2e": {"value": round(world * args.steps / e2e_sec, 3), "unit": "iters/s",
+                "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
+        "gpu_launches": res["launches"], "clocks": res["clocks"], "roofline": roofline(res),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(res["scene"], args.cpu_window)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_reference(args, wl, rank, world, config):
+    """The oracle, as it stands, timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return 0
+    import torch
+    import oracle
+    from paper_2509_12138_gb300 import workload
+    oracle.build()
+    have_gpu = torch.cuda.is_available()
+    if not have_gpu:
+        print(json.dumps({"impl": "reference", "unavailable": "the scene's GT is rendered on the GPU; no CUDA device"}))
+        return 0
+    scene = workload.isosurface_scene(wl["n"], wl["modes"], wl["views"], wl["W"], wl["H"], sh_degree=3, seed=0)
+    cs = CpuSample(scene, args.cpu_window)
+    for _ in range(args.warmup):
+        cs.step()
+    times = [cs.step() for _ in range(args.steps)]
+    cb = {"cores": cs.cores, "sample": cs.desc}
+    t = float(np.mean(times))
+    line = {"metric": METRIC, "impl": "reference", "value": round(1.0 / t, 6), "unit": "iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "cpu_baseline": {"value": round(1.0 / t, 6), "unit": "iters/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": round(1.0 / t, 6), "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

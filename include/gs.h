@@ -1,0 +1,237 @@
+/*
+ * gs.h -- C ABI of libgs, a GB300 (sm_103a) differentiable tile-based
+ * Gaussian-splat rasterizer for isosurface 3D Gaussian Splatting.
+ *
+ * The paper (Sec. II) trains 3D Gaussian Splatting per spatial partition
+ * ("Data Partitioning", "Parallel Training") and merges the splats of all
+ * partitions for the final render ("Global Reconstruction"); the masks of
+ * "Image Rendering and Masking" restrict the loss to a partition's pixels.
+ * It does not restate the rasterizer itself, which is the standard 3D-GS
+ * one; the steps below follow that definition with the constants fixed here.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every pointer argument is a DEVICE pointer owned by the caller unless
+ *    its comment says "host".  The library never allocates or frees memory;
+ *    calls that need scratch take a caller-provided workspace whose size is
+ *    given by the matching *_workspace_size() query.
+ *  - Every call enqueues work on `stream` and returns without synchronising.
+ *    Host-side argument checks happen before anything is enqueued: on a bad
+ *    argument the call returns GS_ERR_INVALID and enqueues nothing.
+ *  - Errors found on the device (instance capacity overflow, non-finite
+ *    values) are OR-ed into the caller's device word `d_status` (bits of
+ *    gs_status).  gs_status_read() synchronises the stream and returns it.
+ *  - A launch failure reported by the CUDA runtime returns GS_ERR_CUDA.
+ *  - All floating point is IEEE fp32 except the MLP GEMM operands (bf16).
+ *
+ * Data layout
+ * -----------
+ *  Gaussian parameters: `params` is n_planes x N float4 ("planes"), plane p
+ *  of Gaussian i at params + 4 * (p * N + i):
+ *     plane 0  mean        (x, y, z, unused)
+ *     plane 1  scale/op    (log sx, log sy, log sz, logit opacity)
+ *     plane 2  rotation    (w, x, y, z), any non-zero norm
+ *     plane 3+ SH          the 3 (d+1)^2 colour coefficients, coefficient-major
+ *                          (k0.r k0.g k0.b k1.r ...), packed 4 per plane
+ *  n_planes = gs_param_planes(sh_degree) = 3 + ceil(3 (d+1)^2 / 4).
+ *  Gradients, Adam moments use the same layout.
+ *
+ *  Units: one "unit" is one (partition, view) pair.  Unit u renders the
+ *  Gaussians [gauss_begin[u], gauss_begin[u] + gauss_count[u]) with camera
+ *  cams[u]; its projected records occupy the contiguous range
+ *  [proj_base[u], proj_base[u] + gauss_count[u]) with proj_base the exclusive
+ *  prefix sum of gauss_count.  A single view of one scene is one unit
+ *  covering all N Gaussians.  All units share one image size.
+ *
+ *  Images: img [U][3][H][W] fp32, final_T and n_contrib [U][H][W].
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* gs_stream_t; /* a cudaStream_t */
+
+enum gs_status {
+  GS_OK = 0,
+  GS_ERR_INVALID = 1,   /* bad argument (host check; nothing enqueued) */
+  GS_ERR_CAPACITY = 2,  /* more tile instances than the buffers hold; lists truncated */
+  GS_ERR_TIMEOUT = 4,   /* a bounded wait expired */
+  GS_ERR_NONFINITE = 8, /* a non-finite value was produced */
+  GS_ERR_CUDA = 16      /* CUDA runtime error at launch */
+};
+
+/* Rasterizer constants (the 3D-GS definition; none is stated in the paper). */
+#define GS_TILE 16             /* tile edge in pixels */
+#define GS_MAX_UNITS 256       /* units per call */
+#define GS_MAX_PARTS 64        /* partitions for the ghost filter */
+
+/* Pinhole camera, world -> camera: X_cam = R X + t with viewmat = [R | t]
+ * row-major 3x4.  Camera space: +x right, +y down, +z forward.  Pixel of a
+ * camera-space point: (fx x/z + cx, fy y/z + cy); pixel (px, py) is centred at
+ * integer coordinates.  tan_fov* = tan(fov/2); Gaussians with z <= znear are
+ * culled.  96 bytes. */
+typedef struct gs_camera {
+  float viewmat[12];
+  float fx, fy, cx, cy;
+  float tan_fovx, tan_fovy;
+  float campos[3];
+  float znear;
+  int32_t width, height;
+} gs_camera;
+
+/* Per (unit, Gaussian) projected records, indexed by projected index. */
+typedef struct gs_proj {
+  float* xy;        /* [P][2]  pixel-space mean                            */
+  float* conic_op;  /* [P][4]  (A, B, C, opacity), conic = inverse 2D cov  */
+  float* rgb;       /* [P][4]  (r, g, b, 0) after SH, +0.5 and clamp at 0  */
+  float* depth;     /* [P]     camera-space z                              */
+  int32_t* radius;  /* [P]     3-sigma radius in pixels, 0 = culled        */
+  uint32_t* tiles;  /* [P]     number of 16x16 tiles the splat touches     */
+} gs_proj;
+
+/* Screen-space gradients (accumulated by gs_render_bwd). */
+typedef struct gs_grad2d {
+  float* dxy;       /* [P][2] */
+  float* dconic_op; /* [P][4] (dA, dB, dC, d opacity) */
+  float* drgb;      /* [P][4] */
+} gs_grad2d;
+
+/* Unit table (host arrays, copied by value into the launch). */
+typedef struct gs_units {
+  int32_t n_units;               /* 1 .. GS_MAX_UNITS */
+  const int64_t* gauss_begin;    /* host [n_units] */
+  const int64_t* gauss_count;    /* host [n_units] */
+} gs_units;
+
+/* Optional ghost-cell filter of the merge (Sec. II, "Global Reconstruction"):
+ * Gaussian i of partition k (part_offsets[k] <= i < part_offsets[k+1]) is
+ * kept iff its mean lies in box k = (xmin, ymin, zmin, xmax, ymax, zmax),
+ * lower bounds closed, upper bounds half-open unless closed_hi has bit a set
+ * for axis a.  All host arrays. */
+typedef struct gs_owned {
+  int32_t n_parts;               /* 0 disables the filter, else 1 .. GS_MAX_PARTS */
+  const int64_t* part_offsets;   /* host [n_parts + 1] */
+  const float* boxes;            /* host [n_parts][6] */
+  const int32_t* closed_hi;      /* host [n_parts], bits 0..2 */
+} gs_owned;
+
+/* Number of float4 planes per Gaussian for SH degree 0..3; -1 if invalid. */
+int gs_param_planes(int sh_degree);
+
+/* Synchronise `stream`, read the device status word, return it (and clear it
+ * when `clear` is non-zero). */
+int gs_status_read(int* d_status, int clear, gs_stream_t stream);
+
+/* ---- a1: projection (EWA splatting; 3D-GS preprocess) --------------------
+ * For every unit u and Gaussian i of that unit: camera-space mean t = R mu + t,
+ * cull if t.z <= znear; Sigma3D = R(q) diag(e^{2 ls}) R(q)^T;
+ * Sigma2D = J W Sigma3D W^T J^T + 0.3 I with J the perspective Jacobian at t
+ * (x/z and y/z clamped to +-1.3 tan(fov/2) inside J); conic = Sigma2D^-1
+ * (culled if det <= 0); radius = ceil(3 sqrt(lambda_max)) with
+ * lambda_max = mid + sqrt(max(0.1, mid^2 - det)); tile rectangle
+ * [floor((u - r)/16), floor((u + r + 15)/16)) clamped to the grid (likewise
+ * y), culled if empty; rgb = sum_k Y_k(dir) c_k + 0.5 clamped at 0 with
+ * dir = normalise(mu - campos) and real SH Y_k of degree <= 3 (Condon-Shortley
+ * phase, m = -l..l); opacity = sigmoid(logit).
+ * params: planes layout above (N Gaussians).  cams: device [n_units].
+ * owned: may be NULL (no filter).  Writes every field of `proj` for visible
+ * records and radius = tiles = 0 for culled ones. */
+int gs_preprocess(const float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
+                  const gs_camera* cams, int width, int height, const gs_owned* owned,
+                  const gs_proj* proj, int* d_status, gs_stream_t stream);
+
+/* ---- a2: duplication + radix sort + tile ranges ---------------------------
+ * Each visible record p of unit u is duplicated once per covered tile, in
+ * record order and row-major tile order, with the 64-bit key
+ * (u << (tile_bits + 32)) | (tile << 32) | float_bits(depth) and value p.
+ * A stable LSD radix sort (8-bit digits) orders the keys, so equal keys keep
+ * record order: each tile's list is ordered by (depth, record index).
+ * ranges[u * n_tiles + tile] = [start, end) into sorted_vals.
+ * max_instances: capacity of the instance buffers; on overflow GS_ERR_CAPACITY
+ * is set in d_status and the lists are truncated.  d_num_instances: device
+ * uint32 receiving the instance count.  Workspace: gs_bin_sort_workspace_size. */
+size_t gs_bin_sort_workspace_size(int64_t n_proj, int64_t max_instances);
+int gs_bin_sort(const gs_proj* proj, const gs_units* units, int width, int height,
+                int64_t max_instances, void* workspace, size_t workspace_bytes,
+                uint32_t* sorted_vals, uint32_t* ranges, uint32_t* d_num_instances,
+                int* d_status, gs_stream_t stream);
+
+/* ---- a3: front-to-back blend per 16x16 tile -------------------------------
+ * For pixel (px, py) over its tile's list in order: d = xy - (px, py),
+ * power = -(A dx^2 + C dy^2)/2 - B dx dy, skipped if > 0;
+ * alpha = min(0.99, opacity e^power), skipped if < 1/255; if T (1 - alpha) <
+ * 1e-4 the entry is not blended and the pixel stops; else C += alpha T rgb,
+ * T *= 1 - alpha.  Finally C += T bg.  n_contrib = 1-based list position of
+ * the last blended entry, final_T = T.  bg: host float[3]. */
+int gs_render_fwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges,
+                  int n_units, int width, int height, const float* bg, float* img,
+                  float* final_T, uint32_t* n_contrib, gs_stream_t stream);
+
+/* ---- a4: masked photometric loss (mask: Sec. II, "Image Rendering and
+ * Masking") ---------------------------------------------------------------
+ * Per unit: L = (1 - lambda) L1 + lambda (1 - SSIM), with
+ * L1 = sum_{p in M} sum_c |img - gt| / (3 |M|) and SSIM the mean over mask
+ * pixels and channels of the SSIM map (11x11 Gaussian window, sigma 1.5,
+ * zero-padded same convolution, C1 = 0.01^2, C2 = 0.03^2).  A unit with an
+ * empty mask contributes 0.  The reported loss and its gradient are the mean
+ * over units.  mask: uint8 [U][H][W] (non-zero = in).  d_loss: device float[1].
+ * dL_dimg: [U][3][H][W], overwritten.  Workspace: gs_loss_workspace_size. */
+size_t gs_loss_workspace_size(int n_units, int width, int height);
+int gs_loss(const float* img, const float* gt, const uint8_t* mask, int n_units, int width,
+            int height, float lambda_ssim, void* workspace, size_t workspace_bytes, float* d_loss,
+            float* dL_dimg, gs_stream_t stream);
+
+/* ---- a5: backward ---------------------------------------------------------
+ * Blend backward: per pixel, the tile list is replayed back to front from
+ * n_contrib, recovering T_i = T_{i+1} / (1 - alpha_i) from final_T (no
+ * per-pixel lists are stored); with S the colour behind entry i,
+ * dL/drgb_i = alpha_i T_i g, dL/dalpha_i = T_i (rgb_i - S) . g, and, when
+ * alpha was not clamped, dL/dopacity = e^power dL/dalpha, and dL/dpower =
+ * alpha dL/dalpha onto the conic and the mean.  Per-Gaussian values are
+ * reduced across each warp with shuffles, then across the tile in shared
+ * memory, then added to `g2d` with one set of global atomics per (tile,
+ * Gaussian).  g2d is zeroed by this call.
+ * Projection backward: chain rule of a1 onto all parameters, summed over the
+ * units containing each Gaussian; grads (planes layout) are overwritten. */
+int gs_render_bwd(const float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
+                  const gs_camera* cams, const gs_proj* proj, const uint32_t* sorted_vals,
+                  const uint32_t* ranges, int width, int height, const float* bg,
+                  const float* final_T, const uint32_t* n_contrib, const float* dL_dimg,
+                  const gs_grad2d* g2d, float* grads, gs_stream_t stream);
+
+/* Blend backward only: g2d ([n_proj] records) is zeroed, then accumulated. */
+int gs_blend_bwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges,
+                 int n_units, int width, int height, const float* bg, const float* final_T,
+                 const uint32_t* n_contrib, const float* dL_dimg, const gs_grad2d* g2d,
+                 int64_t n_proj, gs_stream_t stream);
+
+/* Projection backward only (grads overwritten). */
+int gs_project_bwd(const float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
+                   const gs_camera* cams, const gs_proj* proj, const gs_grad2d* g2d,
+                   float* grads, gs_stream_t stream);
+
+/* ---- a6: Adam --------------------------------------------------------------
+ * Textbook Adam with bias correction on the planes layout: t = *d_step + 1,
+ * m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+ * Learning rates per plane component: lr = lr_init * (lr_final / lr_init)^
+ * (min(t, lr_steps) / lr_steps) (log-linear; constant when init == final);
+ * lr_init, lr_final: host float[n_planes][4].  If zero_grad, g is set to 0.
+ * d_step: device int32, read only (advance it with gs_step_advance). */
+int gs_adam_step(float* params, float* grads, float* m, float* v, int64_t n_gauss, int n_planes,
+                 const float* lr_init, const float* lr_final, int32_t lr_steps, float beta1,
+                 float beta2, float eps, const int32_t* d_step, int zero_grad, gs_stream_t stream);
+
+/* *d_step += 1 on the device (keeps CUDA-graph replays advancing). */
+int gs_step_advance(int32_t* d_step, gs_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

@@ -187,13 +187,22 @@ void quat_to_rot(const S q[4], S R[9]) {
 }
 
 // ---------------------------------------------------------------- projection
+// float32 sort key of a mean: camera-space z by a fixed chain of fused
+// multiply-adds on the (float32) inputs.
+static inline double depth_key(const double* R, const double* t, double x, double y, double z) {
+  float k = std::fma((float)R[8], (float)z, (float)t[2]);
+  k = std::fma((float)R[7], (float)y, k);
+  k = std::fma((float)R[6], (float)x, k);
+  return (double)k;
+}
+
 template <class S>
 struct Proj {
   S x, y;        // pixel-space mean
   S A, B, C;     // conic = inverse of the dilated 2D covariance [[a, b], [b, c]]
   S op;          // opacity
   S col[3];      // RGB after the +0.5 offset and the clamp at 0
-  S depth;       // camera-space z
+  S depth;       // float32 sort key (camera-space z), see depth_key
   int radius;    // 0 = culled
   int rect[4];
   int tiles;
@@ -214,7 +223,10 @@ Proj<S> project_one(const S mu[3], const S ls[3], const S q[4], S logit, const S
   const double* R = cam.R;
   S t[3];
   for (int i = 0; i < 3; ++i) t[i] = R[3 * i] * mu[0] + R[3 * i + 1] * mu[1] + R[3 * i + 2] * mu[2] + cam.t[i];
-  P.depth = t[2];
+  // The list order is a discrete decision taken on the float32 camera-space z,
+  // evaluated as fma(r20, x, fma(r21, y, fma(r22, z, t2))) on the float32 inputs;
+  // the blend itself uses the FP64 quantities.
+  P.depth = S(depth_key(R, cam.t, val(mu[0]), val(mu[1]), val(mu[2])));
   if (val(t[2]) <= cam.znear) return P;
 
   // Sigma3D = (Rq S)(Rq S)^T
@@ -323,12 +335,10 @@ static void bin_and_sort(int n, const double* x, const double* y, const int* rad
     L.tile[k] = es[k].tile;
     if (k == 0 || es[k - 1].tile != es[k].tile) L.start[es[k].tile] = (int)k;
     if (k + 1 == es.size() || es[k + 1].tile != es[k].tile) L.end[es[k].tile] = (int)k + 1;
-    // flag tiles whose order could flip between float32 and float64 depths
-    if (tie_tiles && k > 0 && es[k - 1].tile == es[k].tile) {
-      double d0 = es[k - 1].depth, d1 = es[k].depth;
-      if (std::fabs(d1 - d0) <= std::ldexp(std::max(std::fabs(d0), std::fabs(d1)), -22))
-        tie_tiles[es[k].tile] = 1;
-    }
+    // equal keys: the order comes from the index (deterministic on both sides);
+    // recorded for diagnostics only
+    if (tie_tiles && k > 0 && es[k - 1].tile == es[k].tile && es[k - 1].depth == es[k].depth)
+      tie_tiles[es[k].tile] = 1;
   }
 }
 
@@ -360,7 +370,11 @@ PixelOut<S> blend_pixel(int px, int py, const int* list, int len, const Proj<S>*
     const Proj<S>& g = P[list[k]];
     S dx = g.x - (double)px, dy = g.y - (double)py;
     S power = -0.5 * (g.A * dx * dx + g.C * dy * dy) - g.B * dx * dy;
-    margin = std::min(margin, std::fabs(val(power)));
+    // power <= 0 for a positive-definite conic; its sign can only be decided
+    // differently under cancellation, so the margin is relative to the terms
+    double terms = 0.5 * (std::fabs(val(g.A)) * val(dx) * val(dx) + std::fabs(val(g.C)) * val(dy) * val(dy)) +
+                   std::fabs(val(g.B) * val(dx) * val(dy));
+    if (terms > 0.0) margin = std::min(margin, std::fabs(val(power)) / terms);
     if (val(power) > 0.0) continue;
     S G = exp(power);
     S araw = g.op * G;

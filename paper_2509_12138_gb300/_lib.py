@@ -1,0 +1,110 @@
+"""ctypes binding of libgs (include/gs.h).  Argument marshalling only.
+
+Loading fails loudly when the library is missing: there is no fallback
+implementation anywhere in this package.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+c_i64p = C.POINTER(C.c_int64)
+c_i32p = C.POINTER(C.c_int32)
+c_f32p = C.POINTER(C.c_float)
+
+
+class GsCamera(C.Structure):
+    _fields_ = [("viewmat", C.c_float * 12), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float),
+                ("cy", C.c_float), ("tan_fovx", C.c_float), ("tan_fovy", C.c_float), ("campos", C.c_float * 3),
+                ("znear", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class GsProj(C.Structure):
+    _fields_ = [("xy", C.c_void_p), ("conic_op", C.c_void_p), ("rgb", C.c_void_p), ("depth", C.c_void_p),
+                ("radius", C.c_void_p), ("tiles", C.c_void_p)]
+
+
+class GsGrad2d(C.Structure):
+    _fields_ = [("dxy", C.c_void_p), ("dconic_op", C.c_void_p), ("drgb", C.c_void_p)]
+
+
+class GsUnits(C.Structure):
+    _fields_ = [("n_units", C.c_int32), ("gauss_begin", c_i64p), ("gauss_count", c_i64p)]
+
+
+class GsOwned(C.Structure):
+    _fields_ = [("n_parts", C.c_int32), ("part_offsets", c_i64p), ("boxes", c_f32p), ("closed_hi", c_i32p)]
+
+
+assert C.sizeof(GsCamera) == 96
+
+VP = C.c_void_p
+I64 = C.c_int64
+I32 = C.c_int
+F32 = C.c_float
+SZ = C.c_size_t
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "gs_param_planes": (I32, [I32]),
+    "gs_status_read": (I32, [VP, I32, VP]),
+    "gs_preprocess": (I32, [VP, I64, I32, C.POINTER(GsUnits), VP, I32, I32, C.POINTER(GsOwned), C.POINTER(GsProj),
+                            VP, VP]),
+    "gs_bin_sort_workspace_size": (SZ, [I64, I64]),
+    "gs_bin_sort": (I32, [C.POINTER(GsProj), C.POINTER(GsUnits), I32, I32, I64, VP, SZ, VP, VP, VP, VP, VP]),
+    "gs_render_fwd": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, c_f32p, VP, VP, VP, VP]),
+    "gs_loss_workspace_size": (SZ, [I32, I32, I32]),
+    "gs_loss": (I32, [VP, VP, VP, I32, I32, I32, F32, VP, SZ, VP, VP, VP]),
+    "gs_render_bwd": (I32, [VP, I64, I32, C.POINTER(GsUnits), VP, C.POINTER(GsProj), VP, VP, I32, I32, c_f32p, VP,
+                            VP, VP, C.POINTER(GsGrad2d), VP, VP]),
+    "gs_blend_bwd": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, c_f32p, VP, VP, VP, C.POINTER(GsGrad2d), I64,
+                           VP]),
+    "gs_project_bwd": (I32, [VP, I64, I32, C.POINTER(GsUnits), VP, C.POINTER(GsProj), C.POINTER(GsGrad2d), VP, VP]),
+    "gs_adam_step": (I32, [VP, VP, VP, VP, I64, I32, c_f32p, c_f32p, I32, F32, F32, F32, VP, I32, VP]),
+    "gs_step_advance": (I32, [VP, VP]),
+}
+
+OPTIONAL = set()
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libgs.so, building it first if needed.  Raises if it cannot be loaded."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgs is not built ({path}); run paper_2509_12138_gb300/build.py")
+        L = C.CDLL(path, mode=C.RTLD_GLOBAL)
+        for name, (res, args) in SIGNATURES.items():
+            if not hasattr(L, name):
+                if name in OPTIONAL:
+                    continue
+                raise RuntimeError(f"libgs is missing symbol {name}")
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+class GsError(RuntimeError):
+    pass
+
+
+def check(code: int, what: str):
+    if code != 0:
+        raise GsError(f"{what} failed with status {code}")

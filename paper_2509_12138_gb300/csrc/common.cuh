@@ -1,0 +1,91 @@
+// Device helpers shared by the libgs kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs.h"
+
+#define GS_API extern "C" __attribute__((visibility("default")))
+
+namespace gs {
+
+constexpr int TILE = GS_TILE;
+constexpr int TILE_PIX = TILE * TILE;
+constexpr float DILATION = 0.3f;
+constexpr float ALPHA_MAX = 0.99f;
+constexpr float ALPHA_MIN = 1.0f / 255.0f;
+constexpr float T_MIN = 1e-4f;
+constexpr float JCLAMP = 1.3f;
+constexpr float LAMBDA_FLOOR = 0.1f;
+
+// Unit table passed by value: proj_base has n_units + 1 entries.
+struct UnitTable {
+  int32_t n;
+  int64_t proj_base[GS_MAX_UNITS + 1];
+  int64_t gauss_begin[GS_MAX_UNITS];
+};
+
+struct OwnedTable {
+  int32_t n;  // 0 = no filter
+  int64_t part_off[GS_MAX_PARTS + 1];
+  float box[GS_MAX_PARTS][6];
+  int32_t closed_hi[GS_MAX_PARTS];
+};
+
+// unit containing projected index p (proj_base sorted ascending)
+__device__ __forceinline__ int unit_of(const UnitTable& U, int64_t p) {
+  int lo = 0, hi = U.n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (U.proj_base[mid] <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int part_of(const OwnedTable& O, int64_t i) {
+  int lo = 0, hi = O.n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (O.part_off[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int floordiv16(int a) { return a >> 4; }  // arithmetic shift = floor
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+
+// Tile rectangle [x0, x1) x [y0, y1) of a splat at (u, v) with radius r.
+// floor((u - r)/16) = floor((floor(u) - r)/16) for integer r, so the integer
+// form is exact and matches any exact evaluation of the float formula.
+__device__ __forceinline__ void tile_rect(float u, float v, int r, int TX, int TY, int& x0, int& y0,
+                                          int& x1, int& y1) {
+  int fu = (int)floorf(u), fv = (int)floorf(v);
+  x0 = clampi(floordiv16(fu - r), 0, TX);
+  y0 = clampi(floordiv16(fv - r), 0, TY);
+  x1 = clampi(floordiv16(fu + r + TILE - 1), 0, TX);
+  y1 = clampi(floordiv16(fv + r + TILE - 1), 0, TY);
+}
+
+// power = -(A dx^2 + C dy^2)/2 - B dx dy, written with explicit fmas so that
+// the forward and backward kernels evaluate bit-identical values.
+__device__ __forceinline__ float splat_power(float A, float B, float C, float dx, float dy) {
+  float q = __fmul_rn(A, __fmul_rn(dx, dx));
+  q = __fmaf_rn(C, __fmul_rn(dy, dy), q);
+  float r = __fmul_rn(B, __fmul_rn(dx, dy));
+  return __fmaf_rn(-0.5f, q, -r);
+}
+
+__device__ __forceinline__ void set_status(int* st, int bits) {
+  if (st) atomicOr(st, bits);
+}
+
+__host__ __device__ __forceinline__ int param_planes(int deg) {
+  return (deg < 0 || deg > 3) ? -1 : 3 + (3 * (deg + 1) * (deg + 1) + 3) / 4;
+}
+
+}  // namespace gs
+
+// host-side helpers
+int gs_fill_units(const gs_units* u, gs::UnitTable& t, int64_t* total);
+int gs_fill_owned(const gs_owned* o, gs::OwnedTable& t);
+int gs_check_launch();

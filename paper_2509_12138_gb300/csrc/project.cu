@@ -1,0 +1,648 @@
+// a1 projection (EWA splatting), the projection backward and Adam: the
+// per-Gaussian, HBM-bound kernels of libgs.
+//
+// Parameters are float4 planes (mean, scale/opacity, rotation, SH...), so one
+// thread issues coalesced 16-byte loads per plane.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "common.cuh"
+
+using namespace gs;
+
+namespace {
+
+// ---------------------------------------------------------------- real SH
+// Real spherical harmonics of degree <= 3 (Condon-Shortley phase, m = -l..l)
+// as polynomials of the unit direction.  Normalisation constants:
+//   Y_00 = 1/(2 sqrt(pi)),          l=1: sqrt(3/(4 pi)),
+//   l=2: 1/2 sqrt(15/pi), 1/4 sqrt(5/pi), 1/4 sqrt(15/pi),
+//   l=3: 1/4 sqrt(35/(2 pi)), 1/2 sqrt(105/pi), 1/4 sqrt(21/(2 pi)),
+//        1/4 sqrt(7/pi), 1/4 sqrt(105/pi).
+constexpr float SH_C0 = 0.28209479177387814f;
+constexpr float SH_C1 = 0.4886025119029199f;
+constexpr float SH_C2a = 1.0925484305920792f;
+constexpr float SH_C2b = 0.31539156525252005f;
+constexpr float SH_C2c = 0.5462742152960396f;
+constexpr float SH_C3a = 0.5900435899266435f;
+constexpr float SH_C3b = 2.890611442640554f;
+constexpr float SH_C3c = 0.4570457994644658f;
+constexpr float SH_C3d = 0.3731763325901154f;
+constexpr float SH_C3e = 1.445305721320277f;
+
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
+  Y[0] = SH_C0;
+  if (DEG >= 1) {
+    Y[1] = -SH_C1 * y;
+    Y[2] = SH_C1 * z;
+    Y[3] = -SH_C1 * x;
+  }
+  if (DEG >= 2) {
+    float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = SH_C2a * x * y;
+    Y[5] = -SH_C2a * y * z;
+    Y[6] = SH_C2b * (2.f * zz - xx - yy);
+    Y[7] = -SH_C2a * x * z;
+    Y[8] = SH_C2c * (xx - yy);
+    if (DEG >= 3) {
+      Y[9] = -SH_C3a * y * (3.f * xx - yy);
+      Y[10] = SH_C3b * x * y * z;
+      Y[11] = -SH_C3c * y * (4.f * zz - xx - yy);
+      Y[12] = SH_C3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+      Y[13] = -SH_C3c * x * (4.f * zz - xx - yy);
+      Y[14] = SH_C3e * z * (xx - yy);
+      Y[15] = -SH_C3a * x * (xx - 3.f * yy);
+    }
+  }
+}
+
+// sum_k w_k grad Y_k(x, y, z) (Cartesian gradient of the polynomials above)
+template <int DEG>
+__device__ __forceinline__ void sh_grad(float x, float y, float z, const float* w, float& gx, float& gy,
+                                        float& gz) {
+  gx = gy = gz = 0.f;
+  if (DEG >= 1) {
+    gy += -SH_C1 * w[1];
+    gz += SH_C1 * w[2];
+    gx += -SH_C1 * w[3];
+  }
+  if (DEG >= 2) {
+    gx += SH_C2a * y * w[4];
+    gy += SH_C2a * x * w[4];
+    gy += -SH_C2a * z * w[5];
+    gz += -SH_C2a * y * w[5];
+    gx += -2.f * SH_C2b * x * w[6];
+    gy += -2.f * SH_C2b * y * w[6];
+    gz += 4.f * SH_C2b * z * w[6];
+    gx += -SH_C2a * z * w[7];
+    gz += -SH_C2a * x * w[7];
+    gx += 2.f * SH_C2c * x * w[8];
+    gy += -2.f * SH_C2c * y * w[8];
+    if (DEG >= 3) {
+      float xx = x * x, yy = y * y, zz = z * z;
+      gx += -6.f * SH_C3a * x * y * w[9];
+      gy += -3.f * SH_C3a * (xx - yy) * w[9];
+      gx += SH_C3b * y * z * w[10];
+      gy += SH_C3b * x * z * w[10];
+      gz += SH_C3b * x * y * w[10];
+      gx += 2.f * SH_C3c * x * y * w[11];
+      gy += -SH_C3c * (4.f * zz - xx - 3.f * yy) * w[11];
+      gz += -8.f * SH_C3c * y * z * w[11];
+      gx += -6.f * SH_C3d * x * z * w[12];
+      gy += -6.f * SH_C3d * y * z * w[12];
+      gz += SH_C3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+      gx += -SH_C3c * (4.f * zz - 3.f * xx - yy) * w[13];
+      gy += 2.f * SH_C3c * x * y * w[13];
+      gz += -8.f * SH_C3c * x * z * w[13];
+      gx += 2.f * SH_C3e * x * z * w[14];
+      gy += -2.f * SH_C3e * y * z * w[14];
+      gz += SH_C3e * (xx - yy) * w[14];
+      gx += -3.f * SH_C3a * (xx - yy) * w[15];
+      gy += 6.f * SH_C3a * x * y * w[15];
+    }
+  }
+}
+
+template <int DEG>
+struct ShCount { static constexpr int NC = (DEG + 1) * (DEG + 1); static constexpr int NP = (3 * NC + 3) / 4; };
+
+template <int DEG>
+__device__ __forceinline__ void load_sh(const float4* __restrict__ params, int64_t N, int64_t i, float* c) {
+  constexpr int NP = ShCount<DEG>::NP;
+  #pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    float4 q = __ldg(params + (3 + k) * N + i);
+    c[4 * k] = q.x; c[4 * k + 1] = q.y; c[4 * k + 2] = q.z; c[4 * k + 3] = q.w;
+  }
+}
+
+// Quantities of the forward projection that the backward recomputes.
+struct Geo {
+  float t[3];
+  float Rq[9];
+  float s[3];
+  float Sig[6];  // xx xy xz yy yz zz
+  float T2[6];   // rows of J W
+  float a, b, c, det;
+  bool clx, cly;
+  float xzc, yzc;
+};
+
+// Camera-space z by a fixed fma chain: it is the depth sort key, so its
+// rounding is part of the definition of the list order.
+__device__ __forceinline__ float cam_z(const float* V, float4 m) {
+  return __fmaf_rn(V[8], m.x, __fmaf_rn(V[9], m.y, __fmaf_rn(V[10], m.z, V[11])));
+}
+
+__device__ __forceinline__ void quat_rot(float4 q, float* R, float* qn_out) {
+  float inv = 1.0f / sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+  float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
+  R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+  if (qn_out) { qn_out[0] = w; qn_out[1] = x; qn_out[2] = y; qn_out[3] = z; qn_out[4] = inv; }
+}
+
+__device__ __forceinline__ void geometry(const gs_camera& cam, float4 mean, float4 sop, float4 quat, Geo& g,
+                                         float* qn) {
+  const float* V = cam.viewmat;
+  g.t[0] = V[0] * mean.x + V[1] * mean.y + V[2] * mean.z + V[3];
+  g.t[1] = V[4] * mean.x + V[5] * mean.y + V[6] * mean.z + V[7];
+  g.t[2] = cam_z(V, mean);
+  quat_rot(quat, g.Rq, qn);
+  g.s[0] = expf(sop.x); g.s[1] = expf(sop.y); g.s[2] = expf(sop.z);
+  float M[9];
+  #pragma unroll
+  for (int i = 0; i < 3; ++i)
+    #pragma unroll
+    for (int j = 0; j < 3; ++j) M[3 * i + j] = g.Rq[3 * i + j] * g.s[j];
+  g.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+  g.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+  g.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+  g.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+  g.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+  g.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+  float tz = g.t[2];
+  float limx = JCLAMP * cam.tan_fovx, limy = JCLAMP * cam.tan_fovy;
+  float xz = g.t[0] / tz, yz = g.t[1] / tz;
+  g.clx = (xz < -limx) || (xz > limx);
+  g.cly = (yz < -limy) || (yz > limy);
+  g.xzc = fminf(fmaxf(xz, -limx), limx);
+  g.yzc = fminf(fmaxf(yz, -limy), limy);
+  float J00 = cam.fx / tz, J02 = -cam.fx * g.xzc / tz;
+  float J11 = cam.fy / tz, J12 = -cam.fy * g.yzc / tz;
+  #pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    g.T2[j] = J00 * V[4 * 0 + j] + J02 * V[4 * 2 + j];
+    g.T2[3 + j] = J11 * V[4 * 1 + j] + J12 * V[4 * 2 + j];
+  }
+  // cov = T2 Sig T2^T
+  const float* S = g.Sig;
+  float v0[3], v1[3];
+  #pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const float* T = g.T2 + 3 * r;
+    float* v = r == 0 ? v0 : v1;
+    v[0] = S[0] * T[0] + S[1] * T[1] + S[2] * T[2];
+    v[1] = S[1] * T[0] + S[3] * T[1] + S[4] * T[2];
+    v[2] = S[2] * T[0] + S[4] * T[1] + S[5] * T[2];
+  }
+  g.a = g.T2[0] * v0[0] + g.T2[1] * v0[1] + g.T2[2] * v0[2] + DILATION;
+  g.b = g.T2[0] * v1[0] + g.T2[1] * v1[1] + g.T2[2] * v1[2];
+  g.c = g.T2[3] * v1[0] + g.T2[4] * v1[1] + g.T2[5] * v1[2] + DILATION;
+  g.det = g.a * g.c - g.b * g.b;
+}
+
+__device__ __forceinline__ bool owned_keep(const OwnedTable& O, int64_t i, float4 mean) {
+  if (O.n == 0) return true;
+  int k = part_of(O, i);
+  const float* b = O.box[k];
+  float x[3] = {mean.x, mean.y, mean.z};
+  bool in = true;
+  #pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    bool hi = (O.closed_hi[k] >> a) & 1 ? (x[a] <= b[3 + a]) : (x[a] < b[3 + a]);
+    in = in && (x[a] >= b[a]) && hi;
+  }
+  return in;
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) k_preprocess(const float4* __restrict__ params, int64_t N,
+                                                    UnitTable U, OwnedTable O,
+                                                    const gs_camera* __restrict__ cams, int W, int H,
+                                                    float2* __restrict__ xy, float4* __restrict__ conic_op,
+                                                    float4* __restrict__ rgb, float* __restrict__ depth,
+                                                    int* __restrict__ radius, uint32_t* __restrict__ tiles,
+                                                    int* status) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= U.proj_base[U.n]) return;
+  int u = unit_of(U, p);
+  int64_t i = U.gauss_begin[u] + (p - U.proj_base[u]);
+  const gs_camera& cam = cams[u];
+  int TX = (W + TILE - 1) / TILE, TY = (H + TILE - 1) / TILE;
+  float4 mean = __ldg(params + i);
+  float4 sop = __ldg(params + N + i);
+  float4 quat = __ldg(params + 2 * N + i);
+  int r_out = 0;
+  uint32_t tiles_out = 0;
+  const float* V = cam.viewmat;
+  float tz = cam_z(V, mean);
+  depth[p] = tz;
+  if (tz > cam.znear && owned_keep(O, i, mean)) {
+    Geo g;
+    geometry(cam, mean, sop, quat, g, nullptr);
+    if (g.det > 0.f) {
+      float idet = 1.0f / g.det;
+      float mid = 0.5f * (g.a + g.c);
+      float lam = mid + sqrtf(fmaxf(LAMBDA_FLOOR, mid * mid - g.det));
+      int r = (int)ceilf(3.0f * sqrtf(lam));
+      float px = cam.fx * g.t[0] / tz + cam.cx;
+      float py = cam.fy * g.t[1] / tz + cam.cy;
+      int x0, y0, x1, y1;
+      tile_rect(px, py, r, TX, TY, x0, y0, x1, y1);
+      uint32_t nt = (uint32_t)((x1 - x0) * (y1 - y0));
+      if (r > 0 && nt > 0) {
+        // colour
+        float dx = mean.x - cam.campos[0], dy = mean.y - cam.campos[1], dz = mean.z - cam.campos[2];
+        float il = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= il; dy *= il; dz *= il;
+        float Y[16];
+        sh_basis<DEG>(dx, dy, dz, Y);
+        float c[4 * ShCount<DEG>::NP];
+        load_sh<DEG>(params, N, i, c);
+        float col[3];
+        #pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          float acc = 0.5f;
+          #pragma unroll
+          for (int k = 0; k < ShCount<DEG>::NC; ++k) acc += Y[k] * c[3 * k + ch];
+          col[ch] = fmaxf(acc, 0.f);
+        }
+        float op = 1.0f / (1.0f + expf(-sop.w));
+        xy[p] = make_float2(px, py);
+        conic_op[p] = make_float4(g.c * idet, -g.b * idet, g.a * idet, op);
+        rgb[p] = make_float4(col[0], col[1], col[2], 0.f);
+        r_out = r;
+        tiles_out = nt;
+        if (!(isfinite(px) && isfinite(py) && isfinite(col[0] + col[1] + col[2]))) {
+          set_status(status, GS_ERR_NONFINITE);
+          r_out = 0;
+          tiles_out = 0;
+        }
+      }
+    }
+  }
+  radius[p] = r_out;
+  tiles[p] = tiles_out;
+}
+
+// Projection backward: chain rule of k_preprocess for every parameter,
+// summed over the units that contain Gaussian i.
+template <int DEG>
+__global__ void __launch_bounds__(128) k_project_bwd(const float4* __restrict__ params, int64_t N,
+                                                     UnitTable U, const gs_camera* __restrict__ cams,
+                                                     const int* __restrict__ radius,
+                                                     const float2* __restrict__ gxy,
+                                                     const float4* __restrict__ gco,
+                                                     const float4* __restrict__ grgb,
+                                                     float4* __restrict__ grads) {
+  constexpr int NC = ShCount<DEG>::NC;
+  constexpr int NP = ShCount<DEG>::NP;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  float4 mean = __ldg(params + i);
+  float4 sop = __ldg(params + N + i);
+  float4 quat = __ldg(params + 2 * N + i);
+  float c[4 * NP];
+  load_sh<DEG>(params, N, i, c);
+  float dmean[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
+  float dlogit = 0.f;
+  float dsh[4 * NP];
+  #pragma unroll
+  for (int k = 0; k < 4 * NP; ++k) dsh[k] = 0.f;
+
+  for (int u = 0; u < U.n; ++u) {
+    int64_t cnt = U.proj_base[u + 1] - U.proj_base[u];
+    int64_t l = i - U.gauss_begin[u];
+    if (l < 0 || l >= cnt) continue;
+    int64_t p = U.proj_base[u] + l;
+    if (__ldg(radius + p) <= 0) continue;
+    const gs_camera& cam = cams[u];
+    float2 g_xy = gxy[p];
+    float4 g_co = gco[p];
+    float4 g_rgb = grgb[p];
+    float qn[5];
+    Geo g;
+    geometry(cam, mean, sop, quat, g, qn);
+    float tz = g.t[2], itz = 1.0f / tz;
+    float dt[3] = {0.f, 0.f, 0.f};
+
+    // colour: rgb = max(sum Y c + 0.5, 0)
+    {
+      float vx = mean.x - cam.campos[0], vy = mean.y - cam.campos[1], vz = mean.z - cam.campos[2];
+      float il = 1.0f / sqrtf(vx * vx + vy * vy + vz * vz);
+      float dx = vx * il, dy = vy * il, dz = vz * il;
+      float Y[16];
+      sh_basis<DEG>(dx, dy, dz, Y);
+      float gc[3] = {g_rgb.x, g_rgb.y, g_rgb.z};
+      #pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.5f;
+        #pragma unroll
+        for (int k = 0; k < NC; ++k) acc += Y[k] * c[3 * k + ch];
+        if (acc < 0.f) gc[ch] = 0.f;
+      }
+      float wsum[16];
+      #pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        dsh[3 * k] += Y[k] * gc[0];
+        dsh[3 * k + 1] += Y[k] * gc[1];
+        dsh[3 * k + 2] += Y[k] * gc[2];
+        wsum[k] = c[3 * k] * gc[0] + c[3 * k + 1] * gc[1] + c[3 * k + 2] * gc[2];
+      }
+      if (DEG > 0) {
+        float gx, gy, gz;
+        sh_grad<DEG>(dx, dy, dz, wsum, gx, gy, gz);
+        float dot = gx * dx + gy * dy + gz * dz;
+        dmean[0] += (gx - dot * dx) * il;
+        dmean[1] += (gy - dot * dy) * il;
+        dmean[2] += (gz - dot * dz) * il;
+      }
+    }
+    // opacity
+    {
+      float op = 1.0f / (1.0f + expf(-sop.w));
+      dlogit += g_co.w * op * (1.f - op);
+    }
+    // mean2D
+    dt[0] += g_xy.x * cam.fx * itz;
+    dt[1] += g_xy.y * cam.fy * itz;
+    dt[2] += -(g_xy.x * cam.fx * g.t[0] + g_xy.y * cam.fy * g.t[1]) * itz * itz;
+    // conic -> dilated 2D covariance (a, b, c)
+    float a = g.a, b = g.b, cc = g.c, det = g.det;
+    float id2 = 1.0f / (det * det);
+    float gA = g_co.x, gB = g_co.y, gC = g_co.z;
+    float da = (-cc * cc * gA + b * cc * gB - b * b * gC) * id2;
+    float db = (2.f * b * cc * gA - (det + 2.f * b * b) * gB + 2.f * a * b * gC) * id2;
+    float dc = (-b * b * gA + a * b * gB - a * a * gC) * id2;
+    // Gs = [[da, db/2], [db/2, dc]]; dSig = T2^T Gs T2; dT2 = 2 Gs T2 Sig
+    const float* T = g.T2;
+    float hb = 0.5f * db;
+    float GT0[3], GT1[3];  // rows of Gs T2
+    #pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      GT0[j] = da * T[j] + hb * T[3 + j];
+      GT1[j] = hb * T[j] + dc * T[3 + j];
+    }
+    float dSig[9];
+    #pragma unroll
+    for (int i2 = 0; i2 < 3; ++i2)
+      #pragma unroll
+      for (int j = 0; j < 3; ++j) dSig[3 * i2 + j] = T[i2] * GT0[j] + T[3 + i2] * GT1[j];
+    const float* S6 = g.Sig;
+    float Sg[9] = {S6[0], S6[1], S6[2], S6[1], S6[3], S6[4], S6[2], S6[4], S6[5]};
+    float dT2[6];
+    #pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      dT2[j] = 2.f * (GT0[0] * Sg[j] + GT0[1] * Sg[3 + j] + GT0[2] * Sg[6 + j]);
+      dT2[3 + j] = 2.f * (GT1[0] * Sg[j] + GT1[1] * Sg[3 + j] + GT1[2] * Sg[6 + j]);
+    }
+    // T2 = J W: dJ = dT2 W^T (J00, J02 from row 0; J11, J12 from row 1)
+    const float* V = cam.viewmat;
+    float dJ00 = dT2[0] * V[0] + dT2[1] * V[1] + dT2[2] * V[2];
+    float dJ02 = dT2[0] * V[8] + dT2[1] * V[9] + dT2[2] * V[10];
+    float dJ11 = dT2[3] * V[4] + dT2[4] * V[5] + dT2[5] * V[6];
+    float dJ12 = dT2[3] * V[8] + dT2[4] * V[9] + dT2[5] * V[10];
+    dt[2] += -(dJ00 * cam.fx + dJ11 * cam.fy) * itz * itz;
+    if (g.clx) {
+      dt[2] += dJ02 * cam.fx * g.xzc * itz * itz;
+    } else {
+      dt[0] += -dJ02 * cam.fx * itz * itz;
+      dt[2] += 2.f * dJ02 * cam.fx * g.t[0] * itz * itz * itz;
+    }
+    if (g.cly) {
+      dt[2] += dJ12 * cam.fy * g.yzc * itz * itz;
+    } else {
+      dt[1] += -dJ12 * cam.fy * itz * itz;
+      dt[2] += 2.f * dJ12 * cam.fy * g.t[1] * itz * itz * itz;
+    }
+    // t = W mu + t0
+    #pragma unroll
+    for (int k = 0; k < 3; ++k) dmean[k] += V[k] * dt[0] + V[4 + k] * dt[1] + V[8 + k] * dt[2];
+    // Sigma = M M^T, M = Rq diag(s): dM = 2 dSig M
+    float M[9];
+    #pragma unroll
+    for (int i2 = 0; i2 < 3; ++i2)
+      #pragma unroll
+      for (int j = 0; j < 3; ++j) M[3 * i2 + j] = g.Rq[3 * i2 + j] * g.s[j];
+    float dR[9];
+    #pragma unroll
+    for (int i2 = 0; i2 < 3; ++i2)
+      #pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        float dM = 2.f * (dSig[3 * i2] * M[j] + dSig[3 * i2 + 1] * M[3 + j] + dSig[3 * i2 + 2] * M[6 + j]);
+        dls[j] += dM * g.Rq[3 * i2 + j] * g.s[j];
+        dR[3 * i2 + j] = dM * g.s[j];
+      }
+    // rotation of the normalised quaternion
+    float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+    float gw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+    float gx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] +
+                      w * dR[7] - 2.f * x * dR[8]);
+    float gy = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] +
+                      z * dR[7] - 2.f * y * dR[8]);
+    float gz = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
+                      x * dR[6] + y * dR[7]);
+    float dot = gw * w + gx * x + gy * y + gz * z;
+    float inv = qn[4];
+    dq[0] += (gw - dot * w) * inv;
+    dq[1] += (gx - dot * x) * inv;
+    dq[2] += (gy - dot * y) * inv;
+    dq[3] += (gz - dot * z) * inv;
+  }
+  grads[i] = make_float4(dmean[0], dmean[1], dmean[2], 0.f);
+  grads[N + i] = make_float4(dls[0], dls[1], dls[2], dlogit);
+  grads[2 * N + i] = make_float4(dq[0], dq[1], dq[2], dq[3]);
+  #pragma unroll
+  for (int k = 0; k < NP; ++k)
+    grads[(3 + k) * N + i] = make_float4(dsh[4 * k], dsh[4 * k + 1], dsh[4 * k + 2], dsh[4 * k + 3]);
+}
+
+struct AdamLR {
+  float4 init[16];
+  float4 fin[16];
+};
+
+__global__ void __launch_bounds__(256) k_adam(float4* __restrict__ p, float4* __restrict__ g,
+                                              float4* __restrict__ m, float4* __restrict__ v, int64_t N,
+                                              int n_planes, AdamLR lr, int lr_steps, float b1, float b2,
+                                              float eps, const int32_t* __restrict__ d_step, int zero) {
+  __shared__ float4 s_lr[16];
+  int t = *d_step + 1;
+  if (threadIdx.x < n_planes) {
+    float frac = lr_steps > 0 ? (float)min(t, lr_steps) / (float)lr_steps : 0.f;
+    float4 a = lr.init[threadIdx.x], b = lr.fin[threadIdx.x];
+    auto sched = [&](float x0, float x1) { return (x0 == x1 || x0 <= 0.f) ? x0 : x0 * powf(x1 / x0, frac); };
+    s_lr[threadIdx.x] = make_float4(sched(a.x, b.x), sched(a.y, b.y), sched(a.z, b.z), sched(a.w, b.w));
+  }
+  __syncthreads();
+  float bc1 = 1.f - powf(b1, (float)t), bc2 = 1.f - powf(b2, (float)t);
+  float ibc1 = 1.f / bc1, ibc2 = 1.f / bc2;
+  int64_t total = (int64_t)n_planes * N;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int plane = (int)(k / N);
+    float4 L = s_lr[plane];
+    float4 P = p[k], G = g[k], Mv = m[k], Vv = v[k];
+    float* pp = &P.x; float* gg = &G.x; float* mm = &Mv.x; float* vv = &Vv.x; const float* ll = &L.x;
+    #pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      mm[c] = b1 * mm[c] + (1.f - b1) * gg[c];
+      vv[c] = b2 * vv[c] + (1.f - b2) * gg[c] * gg[c];
+      pp[c] -= ll[c] * (mm[c] * ibc1) / (sqrtf(vv[c] * ibc2) + eps);
+    }
+    p[k] = P; m[k] = Mv; v[k] = Vv;
+    if (zero) g[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+__global__ void k_step_advance(int32_t* s) { *s += 1; }
+
+template <template <int> class K>
+struct DegDispatch;
+
+}  // namespace
+
+// ---------------------------------------------------------------- host helpers
+int gs_check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "libgs: CUDA error %s\n", cudaGetErrorString(e));
+    return GS_ERR_CUDA;
+  }
+  return GS_OK;
+}
+
+int gs_fill_units(const gs_units* u, UnitTable& t, int64_t* total) {
+  if (!u || u->n_units < 1 || u->n_units > GS_MAX_UNITS || !u->gauss_begin || !u->gauss_count)
+    return GS_ERR_INVALID;
+  t.n = u->n_units;
+  int64_t acc = 0;
+  for (int k = 0; k < t.n; ++k) {
+    if (u->gauss_begin[k] < 0 || u->gauss_count[k] < 0) return GS_ERR_INVALID;
+    t.proj_base[k] = acc;
+    t.gauss_begin[k] = u->gauss_begin[k];
+    acc += u->gauss_count[k];
+  }
+  t.proj_base[t.n] = acc;
+  if (acc >= (int64_t)UINT32_MAX) return GS_ERR_INVALID;  // record ids are 32-bit
+  if (total) *total = acc;
+  return GS_OK;
+}
+
+int gs_fill_owned(const gs_owned* o, OwnedTable& t) {
+  memset(&t, 0, sizeof(t));
+  if (!o || o->n_parts == 0) return GS_OK;
+  if (o->n_parts < 0 || o->n_parts > GS_MAX_PARTS || !o->part_offsets || !o->boxes || !o->closed_hi)
+    return GS_ERR_INVALID;
+  t.n = o->n_parts;
+  for (int k = 0; k <= t.n; ++k) t.part_off[k] = o->part_offsets[k];
+  for (int k = 0; k < t.n; ++k) {
+    for (int a = 0; a < 6; ++a) t.box[k][a] = o->boxes[6 * k + a];
+    t.closed_hi[k] = o->closed_hi[k];
+  }
+  return GS_OK;
+}
+
+static bool units_in_range(const UnitTable& t, int64_t n_gauss) {
+  for (int k = 0; k < t.n; ++k)
+    if (t.gauss_begin[k] + (t.proj_base[k + 1] - t.proj_base[k]) > n_gauss) return false;
+  return true;
+}
+
+GS_API int gs_param_planes(int sh_degree) { return param_planes(sh_degree); }
+
+GS_API int gs_status_read(int* d_status, int clear, gs_stream_t stream) {
+  if (!d_status) return GS_ERR_INVALID;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess)
+    return GS_ERR_CUDA;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GS_ERR_CUDA;
+  if (clear && cudaMemsetAsync(d_status, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess) return GS_ERR_CUDA;
+  return h;
+}
+
+GS_API int gs_preprocess(const float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
+                         const gs_camera* cams, int width, int height, const gs_owned* owned,
+                         const gs_proj* proj, int* d_status, gs_stream_t stream) {
+  UnitTable U;
+  OwnedTable O;
+  int64_t P = 0;
+  if ((!params && n_gauss > 0) || !cams || !proj || n_gauss < 0 || width <= 0 || height <= 0 ||
+      param_planes(sh_degree) < 0)
+    return GS_ERR_INVALID;
+  if (!proj->xy || !proj->conic_op || !proj->rgb || !proj->depth || !proj->radius || !proj->tiles)
+    return GS_ERR_INVALID;
+  if (gs_fill_units(units, U, &P) != GS_OK || !units_in_range(U, n_gauss)) return GS_ERR_INVALID;
+  if (gs_fill_owned(owned, O) != GS_OK) return GS_ERR_INVALID;
+  if (O.n > 0 && O.part_off[O.n] != n_gauss) return GS_ERR_INVALID;
+  if (P == 0) return GS_OK;
+  dim3 block(256), grid((unsigned)((P + 255) / 256));
+  cudaStream_t s = (cudaStream_t)stream;
+  const float4* p4 = (const float4*)params;
+#define GS_PRE(D)                                                                                   \
+  k_preprocess<D><<<grid, block, 0, s>>>(p4, n_gauss, U, O, cams, width, height, (float2*)proj->xy, \
+                                         (float4*)proj->conic_op, (float4*)proj->rgb, proj->depth,   \
+                                         proj->radius, proj->tiles, d_status)
+  switch (sh_degree) {
+    case 0: GS_PRE(0); break;
+    case 1: GS_PRE(1); break;
+    case 2: GS_PRE(2); break;
+    default: GS_PRE(3); break;
+  }
+#undef GS_PRE
+  return gs_check_launch();
+}
+
+GS_API int gs_project_bwd(const float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
+                          const gs_camera* cams, const gs_proj* proj, const gs_grad2d* g2d, float* grads,
+                          gs_stream_t stream) {
+  UnitTable U;
+  int64_t P = 0;
+  if (((!params || !grads) && n_gauss > 0) || !cams || !proj || !g2d || n_gauss < 0 ||
+      param_planes(sh_degree) < 0)
+    return GS_ERR_INVALID;
+  if (!proj->radius || !g2d->dxy || !g2d->dconic_op || !g2d->drgb) return GS_ERR_INVALID;
+  if (gs_fill_units(units, U, &P) != GS_OK || !units_in_range(U, n_gauss)) return GS_ERR_INVALID;
+  if (n_gauss == 0) return GS_OK;
+  dim3 block(128), grid((unsigned)((n_gauss + 127) / 128));
+  cudaStream_t s = (cudaStream_t)stream;
+#define GS_PB(D)                                                                                           \
+  k_project_bwd<D><<<grid, block, 0, s>>>((const float4*)params, n_gauss, U, cams, proj->radius,          \
+                                          (const float2*)g2d->dxy, (const float4*)g2d->dconic_op,         \
+                                          (const float4*)g2d->drgb, (float4*)grads)
+  switch (sh_degree) {
+    case 0: GS_PB(0); break;
+    case 1: GS_PB(1); break;
+    case 2: GS_PB(2); break;
+    default: GS_PB(3); break;
+  }
+#undef GS_PB
+  return gs_check_launch();
+}
+
+GS_API int gs_adam_step(float* params, float* grads, float* m, float* v, int64_t n_gauss, int n_planes,
+                        const float* lr_init, const float* lr_final, int32_t lr_steps, float beta1, float beta2,
+                        float eps, const int32_t* d_step, int zero_grad, gs_stream_t stream) {
+  if (!params || !grads || !m || !v || !lr_init || !d_step || n_gauss < 0 || n_planes < 1 || n_planes > 16)
+    return GS_ERR_INVALID;
+  if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps >= 0.f)) return GS_ERR_INVALID;
+  AdamLR lr;
+  memset(&lr, 0, sizeof(lr));
+  for (int k = 0; k < n_planes; ++k) {
+    lr.init[k] = make_float4(lr_init[4 * k], lr_init[4 * k + 1], lr_init[4 * k + 2], lr_init[4 * k + 3]);
+    const float* f = lr_final ? lr_final : lr_init;
+    lr.fin[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+  }
+  if (n_gauss == 0) return GS_OK;
+  int64_t total = (int64_t)n_planes * n_gauss;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t want = (total + 255) / 256;
+  int64_t cap = (int64_t)sms * 8;
+  unsigned grid = (unsigned)(want < cap ? want : cap);
+  k_adam<<<grid, 256, 0, (cudaStream_t)stream>>>((float4*)params, (float4*)grads, (float4*)m, (float4*)v, n_gauss,
+                                                 n_planes, lr, lr_steps, beta1, beta2, eps, d_step, zero_grad);
+  return gs_check_launch();
+}
+
+GS_API int gs_step_advance(int32_t* d_step, gs_stream_t stream) {
+  if (!d_step) return GS_ERR_INVALID;
+  k_step_advance<<<1, 1, 0, (cudaStream_t)stream>>>(d_step);
+  return gs_check_launch();
+}

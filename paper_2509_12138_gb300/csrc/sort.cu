@@ -1,0 +1,420 @@
+// a2: tile-instance duplication, stable LSD radix sort of 64-bit
+// (unit | tile | depth) keys, and per-tile list ranges.
+//
+// Sort design (one pass per 8-bit digit, three kernels per pass, all sized
+// from the instance capacity so the chain is CUDA-graph capturable):
+//   hist    : each 4096-key block builds a 256-bin digit histogram (per-warp
+//             shared-memory bins) and adds it to the pass totals;
+//   scan    : one CTA per digit scans that digit's per-block counts in block
+//             order and adds the digit's global base; a pass whose keys all
+//             share one digit is detected here and skipped (no data moves);
+//   scatter : each block ranks its keys stably (warp match + per-warp digit
+//             counts, in key order) and writes them to the other buffer.
+// Which buffer holds the current keys is tracked on the device (cur[pass]),
+// so skipped passes need no host decision.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "common.cuh"
+
+using namespace gs;
+
+namespace {
+
+constexpr int SCAN_T = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_BLOCK = SCAN_T * SCAN_ITEMS;  // 2048 records per scan block
+constexpr int RS_T = 256;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_T * RS_ITEMS;  // 4096 keys per sort block
+constexpr int RS_BINS = 256;
+constexpr int MAX_PASSES = 8;
+
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct WsLayout {
+  size_t offsets, bsums, keys0, keys1, vals0, vals1, hist, totals, cur, total;
+};
+
+WsLayout ws_layout(int64_t P, int64_t C) {
+  WsLayout L;
+  size_t o = 0;
+  int64_t nsb = (P + SCAN_BLOCK - 1) / SCAN_BLOCK;
+  int64_t nrb = (C + RS_TILE - 1) / RS_TILE;
+  L.offsets = o; o += align256(sizeof(uint32_t) * (size_t)(P > 0 ? P : 1));
+  L.bsums = o; o += align256(sizeof(uint32_t) * (size_t)(nsb + 1));
+  L.keys0 = o; o += align256(sizeof(uint64_t) * (size_t)(C > 0 ? C : 1));
+  L.keys1 = o; o += align256(sizeof(uint64_t) * (size_t)(C > 0 ? C : 1));
+  L.vals0 = o; o += align256(sizeof(uint32_t) * (size_t)(C > 0 ? C : 1));
+  L.vals1 = o; o += align256(sizeof(uint32_t) * (size_t)(C > 0 ? C : 1));
+  L.hist = o; o += align256(sizeof(uint32_t) * RS_BINS * (size_t)(nrb > 0 ? nrb : 1));
+  L.totals = o; o += align256(sizeof(uint32_t) * RS_BINS * MAX_PASSES);
+  L.cur = o; o += align256(sizeof(int32_t) * (MAX_PASSES + 1));
+  L.total = o;
+  return L;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  int lane = threadIdx.x & 31;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+// exclusive scan of one value per thread over a 256-thread block; returns
+// the block total through *total
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t inc = warp_incl_scan(v);
+  if (lane == 31) s_warp[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t x = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0u;
+    uint32_t xi = warp_incl_scan(x);
+    if (lane < (int)(blockDim.x >> 5)) s_warp[lane] = xi - x;
+    if (lane == (int)(blockDim.x >> 5) - 1) s_warp[32] = xi;
+  }
+  __syncthreads();
+  uint32_t r = inc - v + s_warp[w];
+  if (total) *total = s_warp[32];
+  __syncthreads();
+  return r;
+}
+
+// ---- exclusive scan of tiles_touched -> instance offsets
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const uint32_t* __restrict__ in, int64_t P,
+                                                        uint32_t* __restrict__ bsums) {
+  __shared__ uint32_t s_warp[33];
+  int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK;
+  uint32_t s = 0;
+  #pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j) {
+    int64_t k = base + (int64_t)j * SCAN_T + threadIdx.x;
+    if (k < P) s += in[k];
+  }
+  uint32_t tot;
+  block_excl_scan(s, s_warp, &tot);
+  if (threadIdx.x == 0) bsums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_bsums(uint32_t* bsums, int64_t nb) {
+  __shared__ uint32_t s_warp[33];
+  __shared__ uint32_t s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nb; base += blockDim.x) {
+    int64_t k = base + threadIdx.x;
+    uint32_t v = k < nb ? bsums[k] : 0u;
+    uint32_t tot;
+    uint32_t ex = block_excl_scan(v, s_warp, &tot);
+    uint32_t carry = s_carry;
+    if (k < nb) bsums[k] = ex + carry;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry = carry + tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsums[nb] = s_carry;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_down(const uint32_t* __restrict__ in, int64_t P,
+                                                      const uint32_t* __restrict__ bsums, int64_t nb,
+                                                      uint32_t* __restrict__ out, int64_t cap,
+                                                      uint32_t* d_count, int* status) {
+  __shared__ uint32_t s_warp[33];
+  __shared__ uint32_t s_items[SCAN_BLOCK];
+  int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK;
+  // blocked arrangement: thread t owns items [t*ITEMS, (t+1)*ITEMS) of the block
+  #pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j) {
+    int64_t k = base + (int64_t)j * SCAN_T + threadIdx.x;
+    s_items[j * SCAN_T + threadIdx.x] = k < P ? in[k] : 0u;
+  }
+  __syncthreads();
+  uint32_t loc[SCAN_ITEMS];
+  uint32_t s = 0;
+  #pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j) {
+    loc[j] = s;
+    s += s_items[threadIdx.x * SCAN_ITEMS + j];
+  }
+  uint32_t ex = block_excl_scan(s, s_warp, nullptr) + bsums[blockIdx.x];
+  #pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j) s_items[threadIdx.x * SCAN_ITEMS + j] = loc[j] + ex;
+  __syncthreads();
+  #pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j) {
+    int64_t k = base + (int64_t)j * SCAN_T + threadIdx.x;
+    if (k < P) out[k] = s_items[j * SCAN_T + threadIdx.x];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    uint32_t total = bsums[nb];
+    if ((int64_t)total > cap) {
+      set_status(status, GS_ERR_CAPACITY);
+      total = (uint32_t)cap;
+    }
+    *d_count = total;
+  }
+}
+
+// ---- duplication: one key per (record, covered tile)
+__global__ void __launch_bounds__(256) k_duplicate(UnitTable U, const float2* __restrict__ xy,
+                                                   const float* __restrict__ depth,
+                                                   const int* __restrict__ radius,
+                                                   const uint32_t* __restrict__ tiles,
+                                                   const uint32_t* __restrict__ offsets, int W, int H,
+                                                   int tile_bits, int64_t cap, uint64_t* __restrict__ keys,
+                                                   uint32_t* __restrict__ vals) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t P = U.proj_base[U.n];
+  if (p >= P) return;
+  uint32_t nt = tiles[p];
+  if (nt == 0) return;
+  int u = unit_of(U, p);
+  int TX = (W + TILE - 1) / TILE, TY = (H + TILE - 1) / TILE;
+  float2 m = xy[p];
+  int x0, y0, x1, y1;
+  tile_rect(m.x, m.y, radius[p], TX, TY, x0, y0, x1, y1);
+  uint64_t dbits = (uint64_t)__float_as_uint(depth[p]);
+  uint64_t hi = (uint64_t)u << (tile_bits + 32);
+  int64_t o = offsets[p];
+  for (int ty = y0; ty < y1; ++ty)
+    for (int tx = x0; tx < x1; ++tx) {
+      if (o < cap) {
+        keys[o] = hi | ((uint64_t)(ty * TX + tx) << 32) | dbits;
+        vals[o] = (uint32_t)p;
+      }
+      ++o;
+    }
+}
+
+// ---- radix pass kernels
+__global__ void __launch_bounds__(RS_T) k_radix_hist(const uint64_t* __restrict__ k0,
+                                                     const uint64_t* __restrict__ k1,
+                                                     const int32_t* __restrict__ cur, int pass,
+                                                     const uint32_t* __restrict__ d_count, int shift,
+                                                     uint32_t* __restrict__ hist, int64_t stride,
+                                                     uint32_t* __restrict__ totals) {
+  __shared__ uint32_t s_h[RS_T / 32][RS_BINS];
+  int64_t I = *d_count;
+  int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  if (base >= I) return;
+  const uint64_t* keys = cur[pass] ? k1 : k0;
+  int w = threadIdx.x >> 5;
+  for (int k = threadIdx.x; k < (RS_T / 32) * RS_BINS; k += RS_T) (&s_h[0][0])[k] = 0u;
+  __syncthreads();
+  #pragma unroll 4
+  for (int j = 0; j < RS_ITEMS; ++j) {
+    int64_t k = base + (int64_t)j * RS_T + threadIdx.x;
+    if (k < I) {
+      uint32_t d = (uint32_t)(keys[k] >> shift) & 255u;
+      atomicAdd(&s_h[w][d], 1u);
+    }
+  }
+  __syncthreads();
+  int d = threadIdx.x;
+  uint32_t s = 0;
+  #pragma unroll
+  for (int q = 0; q < RS_T / 32; ++q) s += s_h[q][d];
+  hist[(int64_t)d * stride + blockIdx.x] = s;
+  if (s) atomicAdd(&totals[pass * RS_BINS + d], s);
+}
+
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ hist, int64_t stride,
+                                                     const uint32_t* __restrict__ totals, int pass,
+                                                     const uint32_t* __restrict__ d_count,
+                                                     int32_t* __restrict__ cur) {
+  __shared__ uint32_t s_warp[33];
+  __shared__ uint32_t s_carry;
+  __shared__ int s_skip;
+  __shared__ uint32_t s_base;
+  int64_t I = *d_count;
+  int d = blockIdx.x;
+  const uint32_t* tot = totals + pass * RS_BINS;
+  if (threadIdx.x == 0) { s_skip = 0; s_base = 0; s_carry = 0; }
+  __syncthreads();
+  if (threadIdx.x < RS_BINS) {
+    uint32_t t = tot[threadIdx.x];
+    if ((int64_t)t == I) s_skip = 1;  // every key has this digit (or I == 0)
+    if ((int)threadIdx.x < d) atomicAdd(&s_base, t);
+  }
+  if (I == 0 && threadIdx.x == 0) s_skip = 1;
+  __syncthreads();
+  if (d == 0 && threadIdx.x == 0) cur[pass + 1] = s_skip ? cur[pass] : 1 - cur[pass];
+  if (s_skip) return;
+  int64_t nb = (I + RS_TILE - 1) / RS_TILE;
+  uint32_t* row = hist + (int64_t)d * stride;
+  for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+    int64_t b = b0 + threadIdx.x;
+    uint32_t v = b < nb ? row[b] : 0u;
+    uint32_t t;
+    uint32_t ex = block_excl_scan(v, s_warp, &t);
+    uint32_t carry = s_carry;
+    if (b < nb) row[b] = ex + carry + s_base;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry = carry + t;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(RS_T) k_radix_scatter(uint64_t* __restrict__ k0, uint64_t* __restrict__ k1,
+                                                        uint32_t* __restrict__ v0, uint32_t* __restrict__ v1,
+                                                        const int32_t* __restrict__ cur, int pass,
+                                                        const uint32_t* __restrict__ d_count, int shift,
+                                                        const uint32_t* __restrict__ hist, int64_t stride) {
+  __shared__ uint32_t s_off[RS_BINS];
+  __shared__ uint32_t s_run[RS_BINS];
+  __shared__ uint32_t s_wc[RS_T / 32][RS_BINS];
+  __shared__ uint32_t s_rt[RS_BINS];
+  int64_t I = *d_count;
+  int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  if (base >= I) return;
+  int c = cur[pass];
+  if (cur[pass + 1] == c) return;  // skipped pass
+  const uint64_t* kin = c ? k1 : k0;
+  const uint32_t* vin = c ? v1 : v0;
+  uint64_t* kout = c ? k0 : k1;
+  uint32_t* vout = c ? v0 : v1;
+  int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  s_off[tid] = hist[(int64_t)tid * stride + blockIdx.x];
+  s_run[tid] = 0u;
+  #pragma unroll
+  for (int q = 0; q < RS_T / 32; ++q) s_wc[q][tid] = 0u;
+  __syncthreads();
+  uint32_t lt = (1u << lane) - 1u;
+  for (int j = 0; j < RS_ITEMS; ++j) {
+    int64_t k = base + (int64_t)j * RS_T + tid;
+    bool valid = k < I;
+    uint64_t key = valid ? kin[k] : 0ull;
+    uint32_t val = valid ? vin[k] : 0u;
+    uint32_t d = valid ? ((uint32_t)(key >> shift) & 255u) : 256u;
+    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t rank = __popc(peers & lt);
+    if (valid && rank == 0) s_wc[w][d] = __popc(peers);
+    __syncthreads();
+    {  // per digit: exclusive prefix over warps
+      uint32_t s = 0;
+      #pragma unroll
+      for (int q = 0; q < RS_T / 32; ++q) {
+        uint32_t cq = s_wc[q][tid];
+        s_wc[q][tid] = s;
+        s += cq;
+      }
+      s_rt[tid] = s;
+    }
+    __syncthreads();
+    if (valid) {
+      uint32_t pos = s_off[d] + s_run[d] + s_wc[w][d] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+    s_run[tid] += s_rt[tid];
+    #pragma unroll
+    for (int q = 0; q < RS_T / 32; ++q) s_wc[q][tid] = 0u;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ k0, const uint64_t* __restrict__ k1,
+                                                const uint32_t* __restrict__ v0, const uint32_t* __restrict__ v1,
+                                                const int32_t* __restrict__ cur, int final_pass,
+                                                const uint32_t* __restrict__ d_count, int tile_bits,
+                                                int n_tiles, uint32_t* __restrict__ ranges,
+                                                uint32_t* __restrict__ out_vals) {
+  int64_t I = *d_count;
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= I) return;
+  int c = cur[final_pass];
+  const uint64_t* keys = c ? k1 : k0;
+  const uint32_t* vals = c ? v1 : v0;
+  uint32_t ut = (uint32_t)(keys[k] >> 32);
+  out_vals[k] = vals[k];
+  uint32_t mask = (1u << tile_bits) - 1u;
+  int64_t flat = (int64_t)(ut >> tile_bits) * n_tiles + (ut & mask);
+  if (k == 0 || (uint32_t)(keys[k - 1] >> 32) != ut) ranges[2 * flat] = (uint32_t)k;
+  if (k == I - 1 || (uint32_t)(keys[k + 1] >> 32) != ut) ranges[2 * flat + 1] = (uint32_t)(k + 1);
+}
+
+int bits_for(int64_t n) {
+  int b = 0;
+  while (((int64_t)1 << b) < n) ++b;
+  return b;
+}
+
+}  // namespace
+
+GS_API size_t gs_bin_sort_workspace_size(int64_t n_proj, int64_t max_instances) {
+  if (n_proj < 0 || max_instances < 0) return 0;
+  return ws_layout(n_proj, max_instances).total;
+}
+
+// The sort chain, shared by gs_bin_sort and the fixed-scratch variant.
+int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int height, int64_t max_instances,
+                     void* workspace, size_t workspace_bytes, uint32_t* sorted_vals, uint32_t* ranges,
+                     uint32_t* d_num_instances, int* d_status, cudaStream_t s) {
+  UnitTable U;
+  int64_t P = 0;
+  if (!proj || !proj->xy || !proj->depth || !proj->radius || !proj->tiles || width <= 0 || height <= 0 ||
+      !workspace || !sorted_vals || !ranges || !d_num_instances || max_instances < 0 ||
+      max_instances >= (int64_t)UINT32_MAX)
+    return GS_ERR_INVALID;
+  if (gs_fill_units(units, U, &P) != GS_OK) return GS_ERR_INVALID;
+  WsLayout L = ws_layout(P, max_instances);
+  if (workspace_bytes < L.total || ((uintptr_t)workspace & 255u)) return GS_ERR_INVALID;
+  int TX = (width + TILE - 1) / TILE, TY = (height + TILE - 1) / TILE;
+  int n_tiles = TX * TY;
+  int tile_bits = bits_for(n_tiles);
+  int unit_bits = bits_for(U.n);
+  if (tile_bits + unit_bits > 32) return GS_ERR_INVALID;
+  int passes = (32 + tile_bits + unit_bits + 7) / 8;
+  char* ws = (char*)workspace;
+  uint32_t* offsets = (uint32_t*)(ws + L.offsets);
+  uint32_t* bsums = (uint32_t*)(ws + L.bsums);
+  uint64_t* k0 = (uint64_t*)(ws + L.keys0);
+  uint64_t* k1 = (uint64_t*)(ws + L.keys1);
+  uint32_t* v0 = (uint32_t*)(ws + L.vals0);
+  uint32_t* v1 = (uint32_t*)(ws + L.vals1);
+  uint32_t* hist = (uint32_t*)(ws + L.hist);
+  uint32_t* totals = (uint32_t*)(ws + L.totals);
+  int32_t* cur = (int32_t*)(ws + L.cur);
+  int64_t stride = (max_instances + RS_TILE - 1) / RS_TILE;
+  if (stride < 1) stride = 1;
+
+  if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)n_tiles * U.n, s) != cudaSuccess ||
+      cudaMemsetAsync(totals, 0, sizeof(uint32_t) * RS_BINS * MAX_PASSES, s) != cudaSuccess ||
+      cudaMemsetAsync(cur, 0, sizeof(int32_t) * (MAX_PASSES + 1), s) != cudaSuccess ||
+      cudaMemsetAsync(d_num_instances, 0, sizeof(uint32_t), s) != cudaSuccess)
+    return GS_ERR_CUDA;
+  if (P == 0) return gs_check_launch();
+  int64_t nsb = (P + SCAN_BLOCK - 1) / SCAN_BLOCK;
+  k_scan_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, P, bsums);
+  k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);
+  k_scan_down<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, P, bsums, nsb, offsets, max_instances,
+                                               d_num_instances, d_status);
+  k_duplicate<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(U, (const float2*)proj->xy, proj->depth, proj->radius,
+                                                          proj->tiles, offsets, width, height, tile_bits,
+                                                          max_instances, k0, v0);
+  if (max_instances > 0) {
+    unsigned nrb = (unsigned)stride;
+    for (int pass = 0; pass < passes; ++pass) {
+      int shift = 8 * pass;
+      k_radix_hist<<<nrb, RS_T, 0, s>>>(k0, k1, cur, pass, d_num_instances, shift, hist, stride, totals);
+      k_radix_scan<<<RS_BINS, 1024, 0, s>>>(hist, stride, totals, pass, d_num_instances, cur);
+      k_radix_scatter<<<nrb, RS_T, 0, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift, hist, stride);
+    }
+    k_ranges<<<(unsigned)((max_instances + 255) / 256), 256, 0, s>>>(k0, k1, v0, v1, cur, passes, d_num_instances,
+                                                                     tile_bits, n_tiles, ranges, sorted_vals);
+  }
+  return gs_check_launch();
+}
+
+GS_API int gs_bin_sort(const gs_proj* proj, const gs_units* units, int width, int height, int64_t max_instances,
+                       void* workspace, size_t workspace_bytes, uint32_t* sorted_vals, uint32_t* ranges,
+                       uint32_t* d_num_instances, int* d_status, gs_stream_t stream) {
+  return gs_bin_sort_impl(proj, units, width, height, max_instances, workspace, workspace_bytes, sorted_vals,
+                          ranges, d_num_instances, d_status, (cudaStream_t)stream);
+}

@@ -1,0 +1,114 @@
+"""Synthetic isosurface training workloads on the device.
+
+The paper's datasets (isosurfaces of 4M-107M points, Sec. III) are not
+available; a Richtmyer-Meshkov-like perturbed interface (synth.interface_points)
+stands in.  Ground-truth images are renders of a surfel set on the same points
+(flat, opaque, normal-aligned Gaussians with the points' Lambert colours),
+made with this library's own forward pass; the background mask of a view is
+the GT coverage, 1 - T_final >= 1/255 (Sec. II, "Image Rendering and Masking").
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+import synth
+
+from .raster import Frame, Units, pack_cameras, pack_params
+
+Y00 = 0.28209479177387814
+
+
+def spacing_estimate(normals: np.ndarray, n: int) -> float:
+    """Mean 3-NN distance of n uniform samples on the unit-square height field:
+    area = mean(1/n_z); for a planar Poisson process of density lam the mean of the
+    first three NN distances is (0.5 + 0.75 + 0.9375) / 3 / sqrt(lam)."""
+    area = float(np.mean(1.0 / np.abs(np.asarray(normals, np.float64)[:, 2])))
+    lam = n / area
+    return (0.5 + 0.75 + 0.9375) / 3.0 / math.sqrt(lam)
+
+
+def gaussians_from_points(pts, colors, log_scales, quats, logit, sh_degree: int):
+    n = pts.shape[0]
+    sh = np.zeros((n, (sh_degree + 1) ** 2, 3), np.float32)
+    sh[:, 0, :] = (colors - 0.5) / Y00
+    return dict(means=pts.astype(np.float32), log_scales=np.asarray(log_scales, np.float32),
+                quats=np.asarray(quats, np.float32), logit_opacity=np.asarray(logit, np.float32), sh=sh)
+
+
+def gt_surfels(pts, nrm, colors, spacing: float, sh_degree: int = 0):
+    n = pts.shape[0]
+    ls = np.tile(np.log([spacing, spacing, 0.1 * spacing]).astype(np.float32), (n, 1))
+    q = synth.surfel_quats(nrm)
+    logit = np.full(n, math.log(0.99 / 0.01), np.float32)
+    return gaussians_from_points(pts, colors, ls, q, logit, sh_degree)
+
+
+def plain_init(pts, colors, log_scale, sh_degree: int = 3, opacity: float = 0.1):
+    """Plain isosurface initialisation: isotropic scale, identity rotation, opacity 0.1, DC colour."""
+    n = pts.shape[0]
+    ls = np.broadcast_to(np.asarray(log_scale, np.float32).reshape(-1, 1), (n, 3)).copy() \
+        if np.ndim(log_scale) else np.full((n, 3), float(log_scale), np.float32)
+    q = np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1))
+    logit = np.full(n, math.log(opacity / (1 - opacity)), np.float32)
+    return gaussians_from_points(pts, colors, ls, q, logit, sh_degree)
+
+
+@dataclass
+class Scene:
+    n: int
+    sh_degree: int
+    width: int
+    height: int
+    cams: synth.Cameras
+    cams_dev: torch.Tensor      # [V * 96] bytes of gs_camera
+    gt: torch.Tensor            # [V, 3, H, W]
+    mask: torch.Tensor          # [V, H, W] uint8
+    init: dict                  # numpy Gaussian dict (plain init)
+    pts: np.ndarray
+    nrm: np.ndarray
+    colors: np.ndarray
+    spacing: float
+    bg: tuple = (1.0, 1.0, 1.0)
+
+    def cam(self, v: int) -> torch.Tensor:
+        return self.cams_dev[v * 96:(v + 1) * 96]
+
+
+def render_gt(gauss: dict, cams: synth.Cameras, sh_degree: int, bg, device="cuda", max_instances=None):
+    """GT images and masks of every camera, rendered one view at a time."""
+    n = gauss["means"].shape[0]
+    W, H = cams.width, cams.height
+    fr = Frame(n, Units.single(n), W, H, sh_degree, device=device, with_backward=False, with_loss=False,
+               max_instances=max_instances)
+    params = pack_params(gauss, sh_degree, device)
+    camd = pack_cameras(cams, device)
+    V = len(cams)
+    gt = torch.empty((V, 3, H, W), dtype=torch.float32, device=device)
+    mask = torch.empty((V, H, W), dtype=torch.uint8, device=device)
+    for v in range(V):
+        fr.forward(params, camd[v * 96:(v + 1) * 96], bg)
+        gt[v] = fr.img[0]
+        mask[v] = (1.0 - fr.final_T[0]) >= (1.0 / 255.0)
+    st = fr.read_status()
+    if st != 0:
+        raise RuntimeError(f"GT render status {st}")
+    del fr, params
+    return gt, mask
+
+
+def isosurface_scene(n: int, n_modes: int, n_views: int, width: int, height: int, sh_degree: int = 3,
+                     seed: int = 0, radius: float = 1.5, device="cuda", init_log_scale=None) -> Scene:
+    pts, nrm, _ = synth.interface_points(n, n_modes, seed)
+    colors = synth.lambert_colors(pts, nrm)
+    spacing = spacing_estimate(nrm, n)
+    cams = synth.orbital_cameras(n_views, radius, center=(0.5, 0.5, 0.5), width=width, height=height)
+    gt, mask = render_gt(gt_surfels(pts, nrm, colors, spacing), cams, 0, (1.0, 1.0, 1.0), device,
+                         max_instances=max(8 * n, 1 << 20))
+    ls = math.log(spacing) if init_log_scale is None else init_log_scale
+    init = plain_init(pts, colors, ls, sh_degree)
+    return Scene(n=n, sh_degree=sh_degree, width=width, height=height, cams=cams, cams_dev=pack_cameras(cams, device),
+                 gt=gt, mask=mask, init=init, pts=pts, nrm=nrm, colors=colors, spacing=spacing)

@@ -40,6 +40,7 @@ __all__ = [
     "random_gaussians",
     "target_perturbation",
     "slab_density_points",
+    "surfel_quats",
     "Cameras",
 ]
 
@@ -177,11 +178,16 @@ def interface_points(n: int, n_modes: int, seed: int = 0, x_density=None):
         bins = np.repeat(np.arange(nb), counts)
         x = (bins + s["x"].uniform(0.0, 1.0, n)) / nb
     y = s["y"].uniform(0.0, 1.0, n)
-    arg = 2.0 * math.pi * (np.outer(x, kx) + np.outer(y, ky)) + phase
-    h = 0.1 * (np.sin(arg) * amp).sum(axis=1)
-    dh = 0.1 * np.cos(arg) * amp * 2.0 * math.pi
-    hx = (dh * kx).sum(axis=1)
-    hy = (dh * ky).sum(axis=1)
+    h = np.empty(n)
+    hx = np.empty(n)
+    hy = np.empty(n)
+    for a in range(0, n, 1 << 20):  # chunks keep the n x modes temporaries small
+        b = min(n, a + (1 << 20))
+        arg = 2.0 * math.pi * (np.outer(x[a:b], kx) + np.outer(y[a:b], ky)) + phase
+        h[a:b] = 0.1 * (np.sin(arg) * amp).sum(axis=1)
+        dh = 0.1 * np.cos(arg) * amp * 2.0 * math.pi
+        hx[a:b] = (dh * kx).sum(axis=1)
+        hy[a:b] = (dh * ky).sum(axis=1)
     z = 0.5 + h
     pts = np.stack([x, y, z], axis=1)
     nrm = np.stack([-hx, -hy, np.ones_like(hx)], axis=1)
@@ -219,6 +225,16 @@ def lambert_colors(points, normals):
     ndl = np.abs(nrm @ L)
     col = albedo * (0.2 + 0.8 * ndl)[:, None]
     return col.astype(np.float32)
+
+
+def surfel_quats(normals):
+    """Unit quaternions (w, x, y, z) rotating +z onto each normal (GT surfel orientation)."""
+    n = np.asarray(normals, np.float64)
+    q = np.stack([1.0 + n[:, 2], -n[:, 1], n[:, 0], np.zeros(len(n))], axis=1)
+    bad = q[:, 0] < 1e-9  # normal = -z: rotate by pi about x
+    q[bad] = [0.0, 1.0, 0.0, 0.0]
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    return q.astype(np.float32)
 
 
 def random_gaussians(n: int, sh_degree: int = 3, seed: int = 0, center=(0.0, 0.0, 0.0),

@@ -1,0 +1,245 @@
+"""CUDA path vs the FP64 oracle, element by element (needs a GPU).
+
+Bars (from the method's statement of parity):
+* tile counts and sorted per-tile lists: bit-exact (the oracle's binning and
+  sort fed the CUDA path's own float32 means, radii and depths);
+* images: max abs error <= 1e-4 per colour channel, excluding pixels whose
+  FP64 decisions sit within 1e-5 (relative) of a threshold and tiles touched by
+  a splat whose float32 rectangle differs from the FP64 one (both counted,
+  must stay below 1% of the image);
+* gradients: per parameter group, max |g_gpu - g_orc| <= 1e-3 * max |g_orc|.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests import scenes
+from tests.gpu_util import exclusion_mask, gauss64, rects, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4
+GRAD_TOL = 1e-3
+BG = np.array([1.0, 1.0, 1.0])
+
+
+def _case(n, deg, seed, W, H, extent=0.9, ls=(-3.5, -2.0)):
+    g, cams = scenes.random_scene(n, deg, seed, W, H, extent=extent, log_scale_range=ls)
+    return g, cams
+
+
+@pytest.mark.parametrize("n,deg,W,H,seed", [(3000, 3, 200, 150, 0), (2000, 0, 128, 128, 1), (1500, 1, 97, 61, 2),
+                                            (2500, 2, 256, 144, 3)])
+def test_preprocess_parity(n, deg, W, H, seed):
+    g, cams = _case(n, deg, seed, W, H)
+    out = run_gpu(g, cams, deg, BG)
+    cam = oracle.camera_block(cams, 0)
+    o = oracle.project(gauss64(g), cam)
+    vis_o = o["radius"] > 0
+    vis_g = out["radius"] > 0
+    # visibility differs only through a radius/rect near-tie at the image border
+    assert (vis_o != vis_g).sum() <= max(1, n // 1000)
+    both = vis_o & vis_g
+    assert np.allclose(out["xy"][both], o["xy"][both], rtol=1e-5, atol=2e-4)
+    assert np.allclose(out["depth"][both], o["depth"][both], rtol=1e-6)
+    A = o["conic"][both]
+    sc = np.abs(A).max(axis=1, keepdims=True)
+    assert np.all(np.abs(out["conic_op"][both, :3] - A) <= 2e-4 * sc)
+    assert np.allclose(out["conic_op"][both, 3], o["opacity"][both], rtol=1e-5, atol=1e-6)
+    assert np.allclose(out["rgb"][both, :3], o["rgb"][both], atol=2e-5)
+    same_r = out["radius"] == o["radius"]
+    assert same_r[both].mean() > 0.995
+    ok = both & same_r
+    r_gpu = rects(out["xy"].astype(np.float64), out["radius"], W, H)
+    same_rect = np.all(r_gpu == o["rect"], axis=1)
+    assert same_rect[ok].mean() > 0.995
+    assert np.array_equal(out["tiles"][ok & same_rect], o["tiles"][ok & same_rect])
+
+
+@pytest.mark.parametrize("n,deg,W,H,seed", [(3000, 3, 200, 150, 4), (5000, 0, 333, 97, 5)])
+def test_sort_lists_bit_exact(n, deg, W, H, seed):
+    """Oracle binning+sort fed the GPU's own float32 xy / radius / depth equals the GPU lists exactly."""
+    g, cams = _case(n, deg, seed, W, H)
+    out = run_gpu(g, cams, deg, BG)
+    L = oracle.bin_sort(out["xy"].astype(np.float64), out["radius"], out["depth"].astype(np.float64), W, H)
+    assert out["status"] == 0
+    assert len(out["vals"]) == int(out["tiles"].sum()) == len(L["idx"])
+    assert np.array_equal(out["vals"], L["idx"])
+    assert np.array_equal(out["ranges"], L["ranges"])
+
+
+@pytest.mark.parametrize("n,deg,W,H,seed", [(3000, 3, 200, 150, 6), (800, 0, 64, 64, 7), (4000, 1, 161, 93, 8)])
+def test_render_parity(n, deg, W, H, seed):
+    g, cams = _case(n, deg, seed, W, H)
+    bg = np.array([0.2, 0.5, 0.9])
+    out = run_gpu(g, cams, deg, bg)
+    cam = oracle.camera_block(cams, 0)
+    o = oracle.render(gauss64(g), cam, bg)
+    op = oracle.project(gauss64(g), cam)
+    excl, ndiff = exclusion_mask(op, out["xy"], out["radius"], o["tie_tiles"], o["margin"], W, H)
+    assert excl.mean() < 0.01, (excl.mean(), ndiff)
+    err = np.abs(out["img"][0] - o["img"]).max(axis=0)
+    assert err[~excl].max() <= IMG_TOL, err[~excl].max()
+    assert np.abs(out["final_T"][0] - o["final_T"])[~excl].max() <= IMG_TOL
+    assert np.array_equal(out["n_contrib"][0][~excl], o["n_contrib"][~excl])
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.2])
+def test_loss_parity(lam):
+    W, H = 150, 110
+    rng = np.random.default_rng(3)
+    img = rng.uniform(0, 1, (1, 3, H, W)).astype(np.float32)
+    gt, mask = scenes.random_gt(W, H, 9)
+    import paper_2509_12138_gb300 as gsp
+    fr = gsp.Frame(1, gsp.Units.single(1), W, H, 0, with_backward=False)
+    fr.img.copy_(torch.from_numpy(img))
+    fr.loss(torch.from_numpy(gt).cuda(), torch.from_numpy(mask).cuda(), lam)
+    val, d = oracle.loss(img[0].astype(np.float64), gt.astype(np.float64), mask, lam)
+    assert float(fr.loss_val.item()) == pytest.approx(val, rel=1e-5)
+    dg = fr.dimg.cpu().numpy()[0]
+    assert np.abs(dg - d).max() <= 1e-3 * np.abs(d).max()
+
+
+def _group_check(gg, go, deg, tol=GRAD_TOL):
+    groups = dict(mean=slice(0, 3), log_scale=slice(3, 6), quat=slice(6, 10), opacity=slice(10, 11),
+                  sh_dc=slice(11, 14), sh_rest=slice(14, gg.shape[1]))
+    if deg == 0:
+        groups.pop("sh_rest")
+    for name, sl in groups.items():
+        ref = go[:, sl]
+        scale = np.abs(ref).max()
+        if scale == 0:
+            continue
+        err = np.abs(gg[:, sl] - ref).max()
+        assert err <= tol * scale, (name, err, scale)
+
+
+@pytest.mark.parametrize("n,deg,W,H,seed,lam", [(500, 3, 64, 64, 10, 0.2), (2000, 3, 150, 100, 11, 0.2),
+                                                (1500, 0, 128, 128, 12, 0.0), (1200, 1, 90, 70, 13, 0.2)])
+def test_backward_parity(n, deg, W, H, seed, lam):
+    """All parameter gradients of the full pipeline (loss -> blend bwd -> projection bwd)."""
+    g, cams = _case(n, deg, seed, W, H, ls=(-3.0, -1.8))
+    gt, mask = scenes.random_gt(W, H, seed + 50)
+    out = run_gpu(g, cams, deg, BG, gt[None], mask[None], lam)
+    cam = oracle.camera_block(cams, 0)
+    r = oracle.loss_and_grads(gauss64(g), cam, BG, gt.astype(np.float64), mask, lam)
+    assert out["loss"] == pytest.approx(r["loss"], rel=1e-4)
+    # screen-space gradients
+    g2 = r["g2d"]
+    vis = out["radius"] > 0
+    for a, b in [(out["dxy"][:, :2], g2["dxy"]), (out["dco"][:, :3], g2["dconic"]), (out["dco"][:, 3], g2["dopacity"]),
+                 (out["drgb"][:, :3], g2["drgb"])]:
+        sc = np.abs(b).max()
+        assert np.abs(a[vis] - b[vis]).max() <= GRAD_TOL * sc
+    _group_check(out["grads"], r["grads"], deg)
+
+
+def test_multi_unit_batch_parity():
+    """Three views of one scene in one launch chain: each unit equals its own single-view oracle run."""
+    n, deg = 1500, 3
+    g = synth.random_gaussians(n, deg, 20, extent=0.7, log_scale_range=(-3.2, -2.0))
+    cams = synth.orbital_cameras(3, 3.0, width=120, height=88)
+    gts = np.stack([scenes.random_gt(120, 88, 30 + k)[0] for k in range(3)])
+    masks = np.stack([scenes.random_gt(120, 88, 30 + k)[1] for k in range(3)])
+    out = run_gpu(g, cams, deg, BG, gts, masks, 0.2)
+    loss_sum = 0.0
+    grad_sum = None
+    for k in range(3):
+        cam = oracle.camera_block(cams, k)
+        o = oracle.render(gauss64(g), cam, BG)
+        op = oracle.project(gauss64(g), cam)
+        P = slice(k * n, (k + 1) * n)
+        excl, _ = exclusion_mask(op, out["xy"][P], out["radius"][P], o["tie_tiles"], o["margin"], 120, 88)
+        assert excl.mean() < 0.01
+        assert np.abs(out["img"][k] - o["img"]).max(axis=0)[~excl].max() <= IMG_TOL
+        r = oracle.loss_and_grads(gauss64(g), cam, BG, gts[k].astype(np.float64), masks[k], 0.2)
+        loss_sum += r["loss"]
+        grad_sum = r["grads"] if grad_sum is None else grad_sum + r["grads"]
+    # loss and gradients are the mean over units
+    assert out["loss"] == pytest.approx(loss_sum / 3, rel=1e-4)
+    _group_check(out["grads"], grad_sum / 3, deg)
+
+
+def test_adam_parity():
+    import paper_2509_12138_gb300 as gsp
+    n, deg = 1000, 3
+    g = synth.random_gaussians(n, deg, 40)
+    params = gsp.pack_params(g, deg)
+    opt = gsp.Adam(params, deg, extent=2.0, lr_steps=10)
+    rng = np.random.default_rng(0)
+    p_ref = params.cpu().numpy().astype(np.float64).reshape(-1)
+    m_ref = np.zeros_like(p_ref)
+    v_ref = np.zeros_like(p_ref)
+    npl = params.shape[0]
+    for t in range(1, 6):
+        grads = torch.from_numpy(rng.standard_normal(params.shape).astype(np.float32)).cuda()
+        gnp = grads.cpu().numpy().astype(np.float64).reshape(-1)
+        frac = min(t, 10) / 10
+        lr = opt.lr_init.astype(np.float64) * (opt.lr_final.astype(np.float64) /
+                                               np.where(opt.lr_init > 0, opt.lr_init, 1)) ** frac
+        lr = np.where(opt.lr_init == opt.lr_final, opt.lr_init, lr)
+        lr_el = np.repeat(lr.reshape(npl, 1, 4), n, axis=1).reshape(-1)
+        p_ref, m_ref, v_ref = oracle.adam(p_ref, gnp, m_ref, v_ref, lr_el, 0.9, 0.999, 1e-15, t)
+        opt.step(grads, zero_grad=True)
+        assert torch.count_nonzero(grads).item() == 0
+    got = params.cpu().numpy().astype(np.float64).reshape(-1)
+    assert np.allclose(got, p_ref, rtol=1e-5, atol=1e-6)
+    assert np.allclose(opt.m.cpu().numpy().reshape(-1), m_ref, rtol=1e-4, atol=1e-7)
+    assert int(opt.step_dev.item()) == 5
+
+
+def test_autograd_function_matches_frame_backward():
+    import paper_2509_12138_gb300 as gsp
+    n, deg, W, H = 800, 1, 80, 64
+    g, cams = _case(n, deg, 50, W, H)
+    params = gsp.pack_params(g, deg).requires_grad_(True)
+    fr = gsp.Frame(n, gsp.Units.single(n), W, H, deg)
+    camd = gsp.pack_cameras(cams)
+    img = gsp.rasterize(params, fr, camd, BG)
+    w = torch.randn_like(img)
+    (img * w).sum().backward()
+    fr2 = gsp.Frame(n, gsp.Units.single(n), W, H, deg)
+    fr2.forward(params.detach(), camd, BG)
+    g2 = fr2.backward(params.detach(), camd, BG, w.contiguous())
+    assert torch.allclose(params.grad, g2, rtol=1e-5, atol=1e-7)
+    # and against the oracle: d<w, img>/dparams
+    cam = oracle.camera_block(cams, 0)
+    d2 = oracle.render_backward(gauss64(g), cam, BG, w[0].cpu().numpy().astype(np.float64))
+    go = oracle.project_backward(gauss64(g), cam, d2)
+    _group_check(gsp.unpack_grads(params.grad, deg), go, deg)
+
+
+# ---------------------------------------------------------------- edge cases
+def test_empty_and_all_culled():
+    import paper_2509_12138_gb300 as gsp
+    W, H = 40, 30
+    cams = scenes.identity_camera(W, H)
+    g = synth.random_gaussians(50, 0, 60, center=(0, 0, -5.0), extent=0.5)  # all behind the camera
+    out = run_gpu(g, cams, 0, BG)
+    assert np.all(out["radius"] == 0) and len(out["vals"]) == 0
+    assert np.allclose(out["img"], 1.0) and np.all(out["final_T"] == 1.0) and np.all(out["n_contrib"] == 0)
+    # zero Gaussians
+    fr = gsp.Frame(0, gsp.Units.single(0), W, H, 0)
+    fr.forward(torch.zeros((4, 0, 4), device="cuda"), gsp.pack_cameras(cams), BG)
+    torch.cuda.synchronize()
+    assert np.allclose(fr.img.cpu().numpy(), 1.0)
+
+
+def test_capacity_overflow_sets_status_without_fault():
+    g, cams = _case(2000, 0, 70, 128, 96)
+    out = run_gpu(g, cams, 0, BG, max_instances=100)
+    assert out["status"] & 2  # GS_ERR_CAPACITY
+    assert len(out["vals"]) == 100
+
+
+def test_invalid_arguments_rejected_on_host():
+    import ctypes as C
+    from paper_2509_12138_gb300 import _lib
+    L = _lib.load()
+    assert L.gs_param_planes(4) == -1 and L.gs_param_planes(3) == 15 and L.gs_param_planes(0) == 4
+    rc = L.gs_preprocess(None, 10, 0, None, None, 10, 10, None, None, None, None)
+    assert rc == 1
