@@ -34,6 +34,8 @@ WORKLOADS = {
     # smaller workloads for quick checks
     "iso1M-1080p": dict(n=1_000_000, modes=8, views=64, W=1920, H=1080),
     "iso200k-540p": dict(n=200_000, modes=8, views=16, W=960, H=540),
+    # small device footprint (about 2.5 GB) for Nsight Compute captures of single kernels
+    "iso2M-1080p-prof": dict(n=2_000_000, modes=16, views=4, W=1920, H=1080),
 }
 METRIC = "train iters/s & render Mpix/s at 10M Gaussians 1080p; PSNR vs plain form"
 LAMBDA_SSIM = 0.2
@@ -242,6 +244,10 @@ def run_ours(args, wl, rank, world):
     if st != 0:
         raise RuntimeError(f"device status {st} after warm-up")
     instances = frame.instances()
+    lens = (frame.ranges[:, 1] - frame.ranges[:, 0]).float()
+    nz = lens[lens > 0]
+    tile_len = {"nonempty_tiles": int(nz.numel()), "mean": round(float(nz.mean()), 1) if nz.numel() else 0,
+                "p99": float(torch.quantile(nz, 0.99)) if nz.numel() else 0, "max": int(lens.max())}
 
     def barrier():
         if world > 1:
@@ -282,11 +288,10 @@ def run_ours(args, wl, rank, world):
 
     # end to end through the public API with host buffers: each step copies its GT view and mask from
     # pinned host memory, runs the step and reads the loss back
-    gt_host = torch.empty((4, 3, H, W), dtype=torch.float32).pin_memory()
-    mask_host = torch.empty((4, H, W), dtype=torch.uint8).pin_memory()
-    for v in range(4):
-        gt_host[v].copy_(scene.gt[v])
-        mask_host[v].copy_(scene.mask[v])
+    gt_host = torch.empty((V, 3, H, W), dtype=torch.float32).pin_memory()
+    mask_host = torch.empty((V, H, W), dtype=torch.uint8).pin_memory()
+    gt_host.copy_(scene.gt)
+    mask_host.copy_(scene.mask)
     gt_dev = torch.empty((1, 3, H, W), dtype=torch.float32, device=dev)
     mask_dev = torch.empty((1, H, W), dtype=torch.uint8, device=dev)
     loss_host = torch.empty(args.steps, dtype=torch.float32).pin_memory()
@@ -294,7 +299,7 @@ def run_ours(args, wl, rank, world):
     barrier()
     e0 = time.perf_counter()
     for k in range(args.steps):
-        v = k % 4
+        v = (args.warmup + k) % V  # the same views as the device-timed loop
         gt_dev[0].copy_(gt_host[v], non_blocking=True)
         mask_dev[0].copy_(mask_host[v], non_blocking=True)
         cam = scene.cam(v)
@@ -309,7 +314,7 @@ def run_ours(args, wl, rank, world):
     e_sec = time.perf_counter() - e0
     barrier()
     return dict(scene=scene, frame=frame, ms_total=ms_total, stage_ms=stage_ms, stages=stages, ms_render=ms_render,
-                clocks=clk, e2e_sec=e_sec, instances=instances, h2d=(3 * H * W * 4 + H * W), d2h=4,
+                clocks=clk, e2e_sec=e_sec, instances=instances, tile_len=tile_len, h2d=(3 * H * W * 4 + H * W), d2h=4,
                 launches=kernel_launch_count(frame, LAMBDA_SSIM) * args.steps, N=N, W=W, H=H)
 
 
@@ -384,7 +389,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
         "render_mpix_s": round(mpix, 1), "render_ms": round(res["ms_render"], 4),
         "stage_ms": {k: round(float(v), 4) for k, v in zip(res["stages"], res["stage_ms"])},
-        "instances_per_view": res["instances"],
+        "instances_per_view": res["instances"], "tile_list_len": res["tile_len"],
         "e2e": {"value": round(world * args.steps / e2e_sec, 3), "unit": "iters/s",
                 "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
         "gpu_launches": res["launches"], "clocks": res["clocks"], "roofline": roofline(res),

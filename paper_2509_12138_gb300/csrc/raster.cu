@@ -1,13 +1,12 @@
 // a3 / a5: front-to-back alpha blending per 16x16 tile and its reverse replay.
 //
-// One CTA per (unit, tile), one thread per pixel.  The tile's sorted list is
-// consumed in batches of BATCH records staged in shared memory (each thread
-// gathers one record: its projected index, mean, conic/opacity and colour).
-// The backward replays the same list back to front, recovering each
-// transmittance by division, reduces the per-record gradients of a warp with
-// shuffles (only when some lane contributed), accumulates the 8 warps in
-// shared memory and issues one set of global vector atomics per
-// (tile, record).
+// One CTA per (unit, tile), one thread per pixel; warp w owns the 8x4 pixel
+// block (8 (w & 1), 4 (w >> 1)) of the 16x16 tile and walks the tile's list
+// independently of the other warps (no block barriers: warps whose block few
+// splats reach do not wait for the busy ones).  A record is blended by a warp
+// only if the bounding box of the ellipse where its alpha can reach 1/255
+// meets the warp's block; this skips only (pixel, record) pairs that the
+// per-pixel alpha test would reject anyway, so results are unchanged.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -16,8 +15,6 @@
 using namespace gs;
 
 namespace {
-
-constexpr int BATCH = 256;
 
 __device__ __forceinline__ void atomic_add2(float* p, float a, float b) {
 #if __CUDA_ARCH__ >= 900
@@ -34,6 +31,34 @@ __device__ __forceinline__ void atomic_add4(float* p, float a, float b, float c,
 #endif
 }
 
+// Bounding box (xmin, xmax, ymin, ymax) of {d : o exp(-d^T Q d / 2) >= 1/255},
+// i.e. d^T Q d <= 2 ln(255 o), half-widths sqrt(2 ln(255 o) Sigma_xx) with
+// Sigma = Q^-1; inflated so float rounding can never cull a passing pixel.
+// An empty box (xmin > xmax) when o < 1/255.  Also returns the power below
+// which alpha < 1/255 for certain (used to skip the exponential).
+__device__ __forceinline__ float4 alpha_box(float2 m, float4 co, float& pmin) {
+  float tau = logf(255.f * co.w) + 1e-3f;  // >= ln(255 o) with margin
+  float det = co.x * co.z - co.y * co.y;
+  if (!(tau > 0.f) || !(det > 0.f)) {
+    pmin = 0.f;
+    return make_float4(1.f, -1.f, 1.f, -1.f);
+  }
+  float sxx = co.z / det, syy = co.x / det;
+  float ex = sqrtf(2.f * tau * sxx) * 1.001f + 0.01f;
+  float ey = sqrtf(2.f * tau * syy) * 1.001f + 0.01f;
+  pmin = -tau * 1.001f - 1e-3f;
+  return make_float4(m.x - ex, m.x + ex, m.y - ey, m.y + ey);
+}
+
+__device__ __forceinline__ bool box_misses(float4 b, float x0, float x1, float y0, float y1) {
+  return b.y < x0 || b.x > x1 || b.w < y0 || b.z > y1;
+}
+
+// Forward.  Each warp walks its tile's list on its own, 32 records per round
+// (one per lane): a lane loads a record and tests its alpha box against the
+// warp's 8x4 pixel block; the records that hit are taken in list order and
+// broadcast with shuffles.  The next round's loads are issued before the
+// current round is blended.
 __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict__ ranges,
                                                          const uint32_t* __restrict__ vals,
                                                          const float2* __restrict__ xy,
@@ -42,13 +67,13 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict
                                                          int n_tiles, float bg0, float bg1, float bg2,
                                                          float* __restrict__ img, float* __restrict__ final_T,
                                                          uint32_t* __restrict__ n_contrib) {
-  __shared__ float2 s_xy[BATCH];
-  __shared__ float4 s_co[BATCH];
-  __shared__ float4 s_rgb[BATCH];
+  const unsigned FULL = 0xffffffffu;
   int tile = blockIdx.x, u = blockIdx.y;
   int tx = tile % TX, ty = tile / TX;
-  int px = tx * TILE + (threadIdx.x & (TILE - 1));
-  int py = ty * TILE + (threadIdx.x / TILE);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float wx0 = (float)(tx * TILE + ((w & 1) << 3)), wy0 = (float)(ty * TILE + ((w >> 1) << 2));
+  float wx1 = wx0 + 7.f, wy1 = wy0 + 3.f;
+  int px = (int)wx0 + (lane & 7), py = (int)wy0 + (lane >> 3);
   bool inside = px < W && py < H;
   uint2 rg = ranges[(int64_t)u * n_tiles + tile];
   int n = (int)(rg.y - rg.x);
@@ -56,31 +81,47 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict
   int last = 0;
   bool done = !inside;
   float fx = (float)px, fy = (float)py;
-  for (int b0 = 0; b0 < n; b0 += BATCH) {
-    if (__syncthreads_count(!done) == 0) break;
-    int k = b0 + threadIdx.x;
-    if (k < n) {
-      uint32_t p = vals[rg.x + k];
-      s_xy[threadIdx.x] = xy[p];
-      s_co[threadIdx.x] = conic_op[p];
-      s_rgb[threadIdx.x] = rgb[p];
+  // prefetch of the first round
+  uint32_t p_n = 0;
+  float2 m_n = make_float2(0.f, 0.f);
+  float4 co_n = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (lane < n) { p_n = vals[rg.x + lane]; m_n = xy[p_n]; co_n = conic_op[p_n]; }
+  for (int base = 0; base < n; base += 32) {
+    if (__all_sync(FULL, done)) break;
+    uint32_t p = p_n;
+    float2 m = m_n;
+    float4 co = co_n;
+    bool valid = base + lane < n;
+    int kn = base + 32 + lane;
+    if (kn < n) { p_n = vals[rg.x + kn]; m_n = xy[p_n]; co_n = conic_op[p_n]; }
+    float pmin = 0.f;
+    bool hit = false;
+    if (valid) {
+      float4 b = alpha_box(m, co, pmin);
+      hit = !box_misses(b, wx0, wx1, wy0, wy1);
     }
-    __syncthreads();
-    int m = min(BATCH, n - b0);
-    for (int j = 0; !done && j < m; ++j) {
-      float2 mxy = s_xy[j];
-      float4 co = s_co[j];
-      float power = splat_power(co.x, co.y, co.z, mxy.x - fx, mxy.y - fy);
-      if (power > 0.f) continue;
-      float alpha = fminf(ALPHA_MAX, co.w * __expf(power));
+    unsigned mask = __ballot_sync(FULL, hit);
+    float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (hit) c = rgb[p];
+    while (mask) {
+      int j = __ffs(mask) - 1;
+      mask &= mask - 1;
+      float ex = __shfl_sync(FULL, m.x, j), ey = __shfl_sync(FULL, m.y, j);
+      float A = __shfl_sync(FULL, co.x, j), B = __shfl_sync(FULL, co.y, j);
+      float Cc = __shfl_sync(FULL, co.z, j), op = __shfl_sync(FULL, co.w, j);
+      float pm = __shfl_sync(FULL, pmin, j);
+      float r = __shfl_sync(FULL, c.x, j), gg = __shfl_sync(FULL, c.y, j), bb = __shfl_sync(FULL, c.z, j);
+      if (done) continue;
+      float power = splat_power(A, B, Cc, ex - fx, ey - fy);
+      if (power > 0.f || power < pm) continue;
+      float alpha = fminf(ALPHA_MAX, op * __expf(power));
       if (alpha < ALPHA_MIN) continue;
       float tT = T * (1.f - alpha);
-      if (tT < T_MIN) { done = true; break; }
-      float4 c = s_rgb[j];
+      if (tT < T_MIN) { done = true; continue; }
       float wgt = alpha * T;
-      c0 += c.x * wgt; c1 += c.y * wgt; c2 += c.z * wgt;
+      c0 += r * wgt; c1 += gg * wgt; c2 += bb * wgt;
       T = tT;
-      last = b0 + j + 1;
+      last = base + j + 1;
     }
   }
   if (inside) {
@@ -95,6 +136,12 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict
   }
 }
 
+// Backward.  Each warp replays its tile's list back to front from the largest
+// n_contrib among its pixels, in rounds of 32 records; hits are taken in
+// reverse list order.  The 9 gradient values of a record are summed over the
+// warp with xor shuffles (only if some lane contributed); the lane that loaded
+// the record keeps the sum and issues the global vector atomics at the end of
+// the round.
 __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict__ ranges,
                                                          const uint32_t* __restrict__ vals,
                                                          const float2* __restrict__ xy,
@@ -105,17 +152,13 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict
                                                          const uint32_t* __restrict__ n_contrib,
                                                          const float* __restrict__ dimg, float* __restrict__ dxy,
                                                          float* __restrict__ dco, float* __restrict__ drgb) {
-  __shared__ float2 s_xy[BATCH];
-  __shared__ float4 s_co[BATCH];
-  __shared__ float4 s_rgb[BATCH];
-  __shared__ uint32_t s_p[BATCH];
-  __shared__ float s_acc[BATCH][9];
-  __shared__ int s_max[TILE_PIX / 32];
+  const unsigned FULL = 0xffffffffu;
   int tile = blockIdx.x, u = blockIdx.y;
   int tx = tile % TX, ty = tile / TX;
-  int px = tx * TILE + (threadIdx.x & (TILE - 1));
-  int py = ty * TILE + (threadIdx.x / TILE);
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float wx0 = (float)(tx * TILE + ((w & 1) << 3)), wy0 = (float)(ty * TILE + ((w >> 1) << 2));
+  float wx1 = wx0 + 7.f, wy1 = wy0 + 3.f;
+  int px = (int)wx0 + (lane & 7), py = (int)wy0 + (lane >> 3);
   bool inside = px < W && py < H;
   uint2 rg = ranges[(int64_t)u * n_tiles + tile];
   int64_t plane = (int64_t)W * H;
@@ -128,96 +171,91 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict
     const float* d = dimg + (int64_t)u * 3 * plane;
     g0 = d[pix]; g1 = d[plane + pix]; g2 = d[2 * plane + pix];
   }
-  int wm = __reduce_max_sync(0xffffffffu, last);
-  if (lane == 0) s_max[w] = wm;
-  __syncthreads();
-  int n = 0;
-  #pragma unroll
-  for (int q = 0; q < TILE_PIX / 32; ++q) n = max(n, s_max[q]);
-  n = min(n, (int)(rg.y - rg.x));
+  int n = min(__reduce_max_sync(FULL, last), (int)(rg.y - rg.x));
   float S0 = bg0, S1 = bg1, S2 = bg2;  // colour behind the current entry
   float fx = (float)px, fy = (float)py;
-  for (int bend = n; bend > 0; bend -= BATCH) {
-    int bstart = max(0, bend - BATCH);
-    int m = bend - bstart;
-    __syncthreads();
-    if ((int)threadIdx.x < m) {
-      uint32_t p = vals[rg.x + bstart + threadIdx.x];
-      s_p[threadIdx.x] = p;
-      s_xy[threadIdx.x] = xy[p];
-      s_co[threadIdx.x] = conic_op[p];
-      s_rgb[threadIdx.x] = rgb[p];
-      #pragma unroll
-      for (int q = 0; q < 9; ++q) s_acc[threadIdx.x][q] = 0.f;
+  for (int top = n; top > 0; top -= 32) {
+    int base = top - 32;
+    int k = base + lane;
+    bool valid = k >= 0;
+    uint32_t p = 0;
+    float2 m = make_float2(0.f, 0.f);
+    float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool hit = false;
+    if (valid) {
+      p = vals[rg.x + k];
+      m = xy[p];
+      co = conic_op[p];
+      float pm;
+      float4 b = alpha_box(m, co, pm);
+      hit = !box_misses(b, wx0, wx1, wy0, wy1);
     }
-    __syncthreads();
-    for (int j = m - 1; j >= 0; --j) {
-      int pos = bstart + j;
+    unsigned mask = __ballot_sync(FULL, hit);
+    float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (hit) c = rgb[p];
+    float acc[9];
+    #pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] = 0.f;
+    bool mine = false;  // this lane's record received a contribution
+    while (mask) {
+      int j = 31 - __clz(mask);
+      mask &= ~(1u << j);
+      float ex = __shfl_sync(FULL, m.x, j), ey = __shfl_sync(FULL, m.y, j);
+      float A = __shfl_sync(FULL, co.x, j), B = __shfl_sync(FULL, co.y, j);
+      float Cc = __shfl_sync(FULL, co.z, j), op = __shfl_sync(FULL, co.w, j);
+      float cr = __shfl_sync(FULL, c.x, j), cg = __shfl_sync(FULL, c.y, j), cb = __shfl_sync(FULL, c.z, j);
+      int pos = base + j;
       float v[9];
       #pragma unroll
       for (int q = 0; q < 9; ++q) v[q] = 0.f;
       bool contrib = false;
       if (pos < last) {
-        float2 mxy = s_xy[j];
-        float4 co = s_co[j];
-        float dx = mxy.x - fx, dy = mxy.y - fy;
-        float power = splat_power(co.x, co.y, co.z, dx, dy);
+        float dx = ex - fx, dy = ey - fy;
+        float power = splat_power(A, B, Cc, dx, dy);
         if (power <= 0.f) {
           float G = __expf(power);
-          float araw = co.w * G;
+          float araw = op * G;
           bool clamped = araw > ALPHA_MAX;
           float alpha = clamped ? ALPHA_MAX : araw;
           if (alpha >= ALPHA_MIN) {
             contrib = true;
-            T = T / (1.f - alpha);  // transmittance in front of this entry
-            float4 c = s_rgb[j];
+            T = __fdividef(T, 1.f - alpha);  // transmittance in front of this entry
             float wgt = alpha * T;
             v[6] = wgt * g0; v[7] = wgt * g1; v[8] = wgt * g2;
-            float dalpha = T * ((c.x - S0) * g0 + (c.y - S1) * g1 + (c.z - S2) * g2);
-            S0 = alpha * c.x + (1.f - alpha) * S0;
-            S1 = alpha * c.y + (1.f - alpha) * S1;
-            S2 = alpha * c.z + (1.f - alpha) * S2;
+            float dalpha = T * ((cr - S0) * g0 + (cg - S1) * g1 + (cb - S2) * g2);
+            S0 = alpha * cr + (1.f - alpha) * S0;
+            S1 = alpha * cg + (1.f - alpha) * S1;
+            S2 = alpha * cb + (1.f - alpha) * S2;
             if (!clamped) {
               v[5] = G * dalpha;
               float dp = araw * dalpha;
               v[2] = -0.5f * dx * dx * dp;
               v[3] = -dx * dy * dp;
               v[4] = -0.5f * dy * dy * dp;
-              v[0] = -(co.x * dx + co.y * dy) * dp;
-              v[1] = -(co.z * dy + co.y * dx) * dp;
+              v[0] = -(A * dx + B * dy) * dp;
+              v[1] = -(Cc * dy + B * dx) * dp;
             }
           }
         }
       }
-      if (__ballot_sync(0xffffffffu, contrib)) {
+      if (__ballot_sync(FULL, contrib)) {
         #pragma unroll
         for (int q = 0; q < 9; ++q) {
           float x = v[q];
-          x += __shfl_xor_sync(0xffffffffu, x, 16);
-          x += __shfl_xor_sync(0xffffffffu, x, 8);
-          x += __shfl_xor_sync(0xffffffffu, x, 4);
-          x += __shfl_xor_sync(0xffffffffu, x, 2);
-          x += __shfl_xor_sync(0xffffffffu, x, 1);
-          v[q] = x;
+          x += __shfl_xor_sync(FULL, x, 16);
+          x += __shfl_xor_sync(FULL, x, 8);
+          x += __shfl_xor_sync(FULL, x, 4);
+          x += __shfl_xor_sync(FULL, x, 2);
+          x += __shfl_xor_sync(FULL, x, 1);
+          if (lane == j) acc[q] = x;
         }
-        if (lane == 0) {
-          #pragma unroll
-          for (int q = 0; q < 9; ++q) atomicAdd(&s_acc[j][q], v[q]);
-        }
+        if (lane == j) mine = true;
       }
     }
-    __syncthreads();
-    if ((int)threadIdx.x < m) {
-      const float* a = s_acc[threadIdx.x];
-      bool nz = false;
-      #pragma unroll
-      for (int q = 0; q < 9; ++q) nz |= a[q] != 0.f;
-      if (nz) {
-        uint32_t p = s_p[threadIdx.x];
-        atomic_add2(dxy + 2 * (int64_t)p, a[0], a[1]);
-        atomic_add4(dco + 4 * (int64_t)p, a[2], a[3], a[4], a[5]);
-        atomic_add4(drgb + 4 * (int64_t)p, a[6], a[7], a[8], 0.f);
-      }
+    if (mine) {
+      atomic_add2(dxy + 2 * (int64_t)p, acc[0], acc[1]);
+      atomic_add4(dco + 4 * (int64_t)p, acc[2], acc[3], acc[4], acc[5]);
+      atomic_add4(drgb + 4 * (int64_t)p, acc[6], acc[7], acc[8], 0.f);
     }
   }
 }
