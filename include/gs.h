@@ -168,10 +168,12 @@ int gs_bin_sort(const gs_proj* proj, const gs_units* units, int width, int heigh
  * alpha = min(0.99, opacity e^power), skipped if < 1/255; if T (1 - alpha) <
  * 1e-4 the entry is not blended and the pixel stops; else C += alpha T rgb,
  * T *= 1 - alpha.  Finally C += T bg.  n_contrib = 1-based list position of
- * the last blended entry, final_T = T.  bg: host float[3]. */
+ * the last blended entry, final_T = T.  bg: host float[3].
+ * variant: execution shape only (results are identical): each warp owns a
+ * BW x 32/BW pixel block of the tile, BW = 8 (0), 16 (1) or 4 (2). */
 int gs_render_fwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges,
                   int n_units, int width, int height, const float* bg, float* img,
-                  float* final_T, uint32_t* n_contrib, gs_stream_t stream);
+                  float* final_T, uint32_t* n_contrib, int variant, gs_stream_t stream);
 
 /* ---- a4: masked photometric loss (mask: Sec. II, "Image Rendering and
  * Masking") ---------------------------------------------------------------
@@ -198,18 +200,19 @@ int gs_loss(const float* img, const float* gt, const uint8_t* mask, int n_units,
  * memory, then added to `g2d` with one set of global atomics per (tile,
  * Gaussian).  g2d is zeroed by this call.
  * Projection backward: chain rule of a1 onto all parameters, summed over the
- * units containing each Gaussian; grads (planes layout) are overwritten. */
+ * units containing each Gaussian; grads (planes layout) are overwritten.
+ * variant: as for gs_render_fwd (execution shape of the blend replay). */
 int gs_render_bwd(const float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
                   const gs_camera* cams, const gs_proj* proj, const uint32_t* sorted_vals,
                   const uint32_t* ranges, int width, int height, const float* bg,
                   const float* final_T, const uint32_t* n_contrib, const float* dL_dimg,
-                  const gs_grad2d* g2d, float* grads, gs_stream_t stream);
+                  const gs_grad2d* g2d, float* grads, int variant, gs_stream_t stream);
 
 /* Blend backward only: g2d ([n_proj] records) is zeroed, then accumulated. */
 int gs_blend_bwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges,
                  int n_units, int width, int height, const float* bg, const float* final_T,
                  const uint32_t* n_contrib, const float* dL_dimg, const gs_grad2d* g2d,
-                 int64_t n_proj, gs_stream_t stream);
+                 int64_t n_proj, int variant, gs_stream_t stream);
 
 /* Projection backward only (grads overwritten). */
 int gs_project_bwd(const float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
@@ -230,6 +233,21 @@ int gs_adam_step(float* params, float* grads, float* m, float* v, int64_t n_gaus
 
 /* *d_step += 1 on the device (keeps CUDA-graph replays advancing). */
 int gs_step_advance(int32_t* d_step, gs_stream_t stream);
+
+/* ---- a8: merged render of all partitions (Sec. II, "Global Reconstruction")
+ * The splats of all partitions, concatenated in partition order, are rendered
+ * as one scene after the ghost filter: a Gaussian of partition k is kept iff
+ * its (trained) mean lies in partition k's owned box (see gs_owned).  One
+ * camera (device, 1 entry), one image [3][H][W].  Equivalent to
+ * gs_preprocess (one unit over all N, with `owned`) + gs_bin_sort +
+ * gs_render_fwd; proj must hold N records and the workspace
+ * gs_bin_sort_workspace_size(N, max_instances) bytes. */
+int gs_merge_render(const float* params, int64_t n_gauss, int sh_degree, const gs_owned* owned,
+                    const gs_camera* cam, int width, int height, const float* bg,
+                    const gs_proj* proj, int64_t max_instances, void* workspace,
+                    size_t workspace_bytes, uint32_t* sorted_vals, uint32_t* ranges,
+                    uint32_t* d_num_instances, float* img, float* final_T, uint32_t* n_contrib,
+                    int* d_status, gs_stream_t stream);
 
 #ifdef __cplusplus
 }

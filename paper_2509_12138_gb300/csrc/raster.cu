@@ -1,7 +1,7 @@
 // a3 / a5: front-to-back alpha blending per 16x16 tile and its reverse replay.
 //
-// One CTA per (unit, tile), one thread per pixel; warp w owns the 8x4 pixel
-// block (8 (w & 1), 4 (w >> 1)) of the 16x16 tile and walks the tile's list
+// One CTA per (unit, tile), one thread per pixel; each warp owns a BW x (32/BW)
+// pixel block of the 16x16 tile (BW = 8, 16 or 4: the tunable variant) and walks the tile's list
 // independently of the other warps (no block barriers: warps whose block few
 // splats reach do not wait for the busy ones).  A record is blended by a warp
 // only if the bounding box of the ellipse where its alpha can reach 1/255
@@ -59,6 +59,7 @@ __device__ __forceinline__ bool box_misses(float4 b, float x0, float x1, float y
 // warp's 8x4 pixel block; the records that hit are taken in list order and
 // broadcast with shuffles.  The next round's loads are issued before the
 // current round is blended.
+template <int BW>
 __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict__ ranges,
                                                          const uint32_t* __restrict__ vals,
                                                          const float2* __restrict__ xy,
@@ -70,10 +71,11 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict
   const unsigned FULL = 0xffffffffu;
   int tile = blockIdx.x, u = blockIdx.y;
   int tx = tile % TX, ty = tile / TX;
+  constexpr int BH = 32 / BW, NWX = TILE / BW;
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float wx0 = (float)(tx * TILE + ((w & 1) << 3)), wy0 = (float)(ty * TILE + ((w >> 1) << 2));
-  float wx1 = wx0 + 7.f, wy1 = wy0 + 3.f;
-  int px = (int)wx0 + (lane & 7), py = (int)wy0 + (lane >> 3);
+  float wx0 = (float)(tx * TILE + (w % NWX) * BW), wy0 = (float)(ty * TILE + (w / NWX) * BH);
+  float wx1 = wx0 + (float)(BW - 1), wy1 = wy0 + (float)(BH - 1);
+  int px = (int)wx0 + (lane % BW), py = (int)wy0 + (lane / BW);
   bool inside = px < W && py < H;
   uint2 rg = ranges[(int64_t)u * n_tiles + tile];
   int n = (int)(rg.y - rg.x);
@@ -142,6 +144,7 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict
 // warp with xor shuffles (only if some lane contributed); the lane that loaded
 // the record keeps the sum and issues the global vector atomics at the end of
 // the round.
+template <int BW>
 __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict__ ranges,
                                                          const uint32_t* __restrict__ vals,
                                                          const float2* __restrict__ xy,
@@ -155,10 +158,11 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict
   const unsigned FULL = 0xffffffffu;
   int tile = blockIdx.x, u = blockIdx.y;
   int tx = tile % TX, ty = tile / TX;
+  constexpr int BH = 32 / BW, NWX = TILE / BW;
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float wx0 = (float)(tx * TILE + ((w & 1) << 3)), wy0 = (float)(ty * TILE + ((w >> 1) << 2));
-  float wx1 = wx0 + 7.f, wy1 = wy0 + 3.f;
-  int px = (int)wx0 + (lane & 7), py = (int)wy0 + (lane >> 3);
+  float wx0 = (float)(tx * TILE + (w % NWX) * BW), wy0 = (float)(ty * TILE + (w / NWX) * BH);
+  float wx1 = wx0 + (float)(BW - 1), wy1 = wy0 + (float)(BH - 1);
+  int px = (int)wx0 + (lane % BW), py = (int)wy0 + (lane / BW);
   bool inside = px < W && py < H;
   uint2 rg = ranges[(int64_t)u * n_tiles + tile];
   int64_t plane = (int64_t)W * H;
@@ -262,26 +266,37 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict
 
 }  // namespace
 
-GS_API int gs_render_fwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
-                         int width, int height, const float* bg, float* img, float* final_T, uint32_t* n_contrib,
-                         gs_stream_t stream) {
+int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
+                       int width, int height, const float* bg, float* img, float* final_T, uint32_t* n_contrib,
+                       int variant, cudaStream_t s) {
   if (!proj || !proj->xy || !proj->conic_op || !proj->rgb || !sorted_vals || !ranges || !bg || !img ||
-      !final_T || !n_contrib || n_units < 1 || n_units > GS_MAX_UNITS || width <= 0 || height <= 0)
+      !final_T || !n_contrib || n_units < 1 || n_units > GS_MAX_UNITS || width <= 0 || height <= 0 ||
+      variant < 0 || variant > 2)
     return GS_ERR_INVALID;
   int TX = (width + TILE - 1) / TILE, TY = (height + TILE - 1) / TILE;
   dim3 grid(TX * TY, n_units);
-  k_render_fwd<<<grid, TILE_PIX, 0, (cudaStream_t)stream>>>(
-      (const uint2*)ranges, sorted_vals, (const float2*)proj->xy, (const float4*)proj->conic_op,
-      (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib);
+#define GS_FWD(BW)                                                                                                \
+  k_render_fwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, sorted_vals, (const float2*)proj->xy,          \
+                                             (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, \
+                                             TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib)
+  if (variant == 0) GS_FWD(8); else if (variant == 1) GS_FWD(16); else GS_FWD(4);
+#undef GS_FWD
   return gs_check_launch();
+}
+
+GS_API int gs_render_fwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
+                         int width, int height, const float* bg, float* img, float* final_T, uint32_t* n_contrib,
+                         int variant, gs_stream_t stream) {
+  return gs_render_fwd_impl(proj, sorted_vals, ranges, n_units, width, height, bg, img, final_T, n_contrib, variant,
+                            (cudaStream_t)stream);
 }
 
 int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
                       int width, int height, const float* bg, const float* final_T, const uint32_t* n_contrib,
-                      const float* dL_dimg, const gs_grad2d* g2d, int64_t n_proj, cudaStream_t s) {
+                      const float* dL_dimg, const gs_grad2d* g2d, int64_t n_proj, int variant, cudaStream_t s) {
   if (!proj || !proj->xy || !proj->conic_op || !proj->rgb || !sorted_vals || !ranges || !bg || !final_T ||
       !n_contrib || !dL_dimg || !g2d || !g2d->dxy || !g2d->dconic_op || !g2d->drgb || n_units < 1 ||
-      n_units > GS_MAX_UNITS || width <= 0 || height <= 0 || n_proj < 0)
+      n_units > GS_MAX_UNITS || width <= 0 || height <= 0 || n_proj < 0 || variant < 0 || variant > 2)
     return GS_ERR_INVALID;
   if (cudaMemsetAsync(g2d->dxy, 0, sizeof(float) * 2 * (size_t)n_proj, s) != cudaSuccess ||
       cudaMemsetAsync(g2d->dconic_op, 0, sizeof(float) * 4 * (size_t)n_proj, s) != cudaSuccess ||
@@ -289,9 +304,12 @@ int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const ui
     return GS_ERR_CUDA;
   int TX = (width + TILE - 1) / TILE, TY = (height + TILE - 1) / TILE;
   dim3 grid(TX * TY, n_units);
-  k_render_bwd<<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, sorted_vals, (const float2*)proj->xy,
-                                         (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX,
-                                         TX * TY, bg[0], bg[1], bg[2], final_T, n_contrib, dL_dimg, g2d->dxy,
-                                         g2d->dconic_op, g2d->drgb);
+#define GS_BWD(BW)                                                                                                   \
+  k_render_bwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, sorted_vals, (const float2*)proj->xy,             \
+                                             (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height,    \
+                                             TX, TX * TY, bg[0], bg[1], bg[2], final_T, n_contrib, dL_dimg, g2d->dxy, \
+                                             g2d->dconic_op, g2d->drgb)
+  if (variant == 0) GS_BWD(8); else if (variant == 1) GS_BWD(16); else GS_BWD(4);
+#undef GS_BWD
   return gs_check_launch();
 }

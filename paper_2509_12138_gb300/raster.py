@@ -137,8 +137,10 @@ class Frame:
     """All device buffers of one rasterizer configuration (N Gaussians, a unit table, W x H)."""
 
     def __init__(self, n_gauss: int, units: Units, width: int, height: int, sh_degree: int, device="cuda",
-                 max_instances: int | None = None, with_backward: bool = True, with_loss: bool = True):
+                 max_instances: int | None = None, with_backward: bool = True, with_loss: bool = True,
+                 variant: int = 0):
         self.L = _lib.load()
+        self.variant = int(variant)
         self.device = torch.device(device)
         self.N = int(n_gauss)
         self.units = units
@@ -199,7 +201,7 @@ class Frame:
         bgc = (C.c_float * 3)(*[float(x) for x in bg])
         check(self.L.gs_render_fwd(C.byref(self.proj), _ptr(self.sorted_vals), _ptr(self.ranges), self.units.n,
                                    self.W, self.H, bgc, _ptr(self.img), _ptr(self.final_T), _ptr(self.n_contrib),
-                                   _stream()), "gs_render_fwd")
+                                   self.variant, _stream()), "gs_render_fwd")
         return self.img
 
     def forward(self, params, cams_dev, bg, owned=None):
@@ -230,7 +232,7 @@ class Frame:
         d = self.dimg if dimg is None else dimg
         check(self.L.gs_blend_bwd(C.byref(self.proj), _ptr(self.sorted_vals), _ptr(self.ranges), self.units.n,
                                   self.W, self.H, bgc, _ptr(self.final_T), _ptr(self.n_contrib), _ptr(d),
-                                  C.byref(self.g2d), self.P, _stream()), "gs_blend_bwd")
+                                  C.byref(self.g2d), self.P, self.variant, _stream()), "gs_blend_bwd")
 
     def project_backward(self, params, cams_dev):
         check(self.L.gs_project_bwd(_ptr(params), self.N, self.deg, C.byref(self.units.struct), _ptr(cams_dev),
@@ -244,8 +246,19 @@ class Frame:
         check(self.L.gs_render_bwd(_ptr(params), self.N, self.deg, C.byref(self.units.struct), _ptr(cams_dev),
                                    C.byref(self.proj), _ptr(self.sorted_vals), _ptr(self.ranges), self.W, self.H,
                                    bgc, _ptr(self.final_T), _ptr(self.n_contrib), _ptr(d), C.byref(self.g2d),
-                                   _ptr(self.grads), _stream()), "gs_render_bwd")
+                                   _ptr(self.grads), self.variant, _stream()), "gs_render_bwd")
         return self.grads
+
+    def merge_render(self, params, cam_dev, bg, owned: Owned):
+        """Ghost-filtered render of all partitions' splats (one unit over all N Gaussians)."""
+        assert self.units.n == 1 and self.P == self.N
+        bgc = (C.c_float * 3)(*[float(x) for x in bg])
+        check(self.L.gs_merge_render(_ptr(params), self.N, self.deg, C.byref(owned.struct), _ptr(cam_dev), self.W,
+                                     self.H, bgc, C.byref(self.proj), self.cap, _ptr(self.sort_ws),
+                                     self.sort_ws.numel(), _ptr(self.sorted_vals), _ptr(self.ranges),
+                                     _ptr(self.num_instances), _ptr(self.img), _ptr(self.final_T),
+                                     _ptr(self.n_contrib), _ptr(self.status), _stream()), "gs_merge_render")
+        return self.img
 
     def read_status(self, clear=True) -> int:
         return int(self.L.gs_status_read(_ptr(self.status), 1 if clear else 0, _stream()))

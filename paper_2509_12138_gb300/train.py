@@ -1,0 +1,208 @@
+"""Training drivers over libgs.
+
+* ``PlainTrainer``  -- the plain form: one scene, one view per optimiser step
+  (projection, sort, blend, loss, backward, Adam launched one by one).
+* ``BatchedTrainer`` -- the batched form (paper Sec. II trains partitions
+  independently; here all partitions and a batch of views per partition are
+  one set of units): every kernel of a step covers all (partition, view)
+  units, and the whole step is captured once in a CUDA graph and replayed.
+
+Each step draws its views from the training set; the per-step GT images,
+masks and cameras are copied into static buffers that the graph reads.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+import torch
+
+from .raster import Adam, Frame, LearningRates, Owned, Units, pack_cameras
+
+CAM_BYTES = 96
+
+
+def psnr(img: torch.Tensor, gt: torch.Tensor, mask: torch.Tensor | None = None) -> float:
+    """10 log10(1 / MSE) over the mask pixels (all pixels if no mask) of [3, H, W] images in [0, 1]."""
+    d = (img.float().clamp(0, 1) - gt.float()) ** 2
+    if mask is not None:
+        m = mask.bool()
+        if not bool(m.any()):
+            return float("nan")
+        mse = d[:, m].mean()
+    else:
+        mse = d.mean()
+    return float(10.0 * torch.log10(1.0 / mse.clamp_min(1e-12)))
+
+
+def split_views(n_views: int, hold_every: int = 8):
+    """Every 8th view is held out for evaluation; the rest train."""
+    test = list(range(0, n_views, hold_every))
+    train = [v for v in range(n_views) if v % hold_every != 0]
+    return train, test
+
+
+class PlainTrainer:
+    def __init__(self, params: torch.Tensor, sh_degree: int, cams_dev: torch.Tensor, gt: torch.Tensor,
+                 mask: torch.Tensor, train_views, lrs: LearningRates | None = None, extent: float = 1.0,
+                 lr_steps: int = 7000, lam: float = 0.2, bg=(1.0, 1.0, 1.0), variant: int = 0, seed: int = 0,
+                 capacity_slack: float = 1.5):
+        self.params = params
+        self.deg = sh_degree
+        self.cams = cams_dev
+        self.gt, self.mask = gt, mask
+        self.views = list(train_views)
+        self.lam, self.bg = lam, tuple(bg)
+        N = params.shape[1]
+        H, W = gt.shape[-2], gt.shape[-1]
+        self.frame = Frame(N, Units.single(N), W, H, sh_degree, device=params.device, variant=variant)
+        self.opt = Adam(params, sh_degree, lrs, extent, lr_steps)
+        self.rng = np.random.default_rng(seed)
+        self.t = 0
+        need = max(self.frame.fit_capacity(params, self.cam(v)) for v in self.views[:: max(1, len(self.views) // 8)])
+        self.frame.set_capacity(int(need * capacity_slack) + 4096)
+
+    def cam(self, v):
+        return self.cams[v * CAM_BYTES:(v + 1) * CAM_BYTES]
+
+    def next_view(self):
+        if self.t % len(self.views) == 0:
+            self.order = self.rng.permutation(self.views)
+        v = int(self.order[self.t % len(self.views)])
+        self.t += 1
+        return v
+
+    def step(self, v: int | None = None):
+        v = self.next_view() if v is None else v
+        fr, cam = self.frame, self.cam(v)
+        fr.preprocess(self.params, cam)
+        fr.sort()
+        fr.render(self.bg)
+        fr.loss(self.gt[v:v + 1], self.mask[v:v + 1], self.lam)
+        fr.backward(self.params, cam, self.bg)
+        self.opt.step(fr.grads)
+
+    def check(self):
+        st = self.frame.read_status()
+        if st & 2:  # capacity: grow and continue (lists of the last steps were truncated)
+            self.frame.set_capacity(int(self.frame.cap * 1.5))
+        return st
+
+    def render(self, v: int):
+        self.frame.forward(self.params, self.cam(v), self.bg)
+        return self.frame.img[0]
+
+    def evaluate(self, views, gt=None, mask=None) -> float:
+        gt = self.gt if gt is None else gt
+        mask = self.mask if mask is None else mask
+        vals = [psnr(self.render(v), gt[v], mask[v]) for v in views]
+        return float(np.nanmean(vals))
+
+
+class BatchedTrainer:
+    """All partitions x ``views_per_step`` views in one graph-captured step.
+
+    params: partition-major planes tensor; part_offsets [n_parts + 1];
+    gt [n_parts, V, 3, H, W], mask [n_parts, V, H, W]: each partition's own GT
+    and background mask; cams_dev: the V cameras (shared by all partitions)."""
+
+    def __init__(self, params: torch.Tensor, sh_degree: int, part_offsets, cams_dev: torch.Tensor, gt: torch.Tensor,
+                 mask: torch.Tensor, train_views, views_per_step: int = 1, lrs: LearningRates | None = None,
+                 extent: float = 1.0, lr_steps: int = 7000, lam: float = 0.2, bg=(1.0, 1.0, 1.0), variant: int = 0,
+                 use_graph: bool = True, capacity_slack: float = 1.5):
+        self.params = params
+        self.deg = sh_degree
+        self.off = np.asarray(part_offsets, np.int64)
+        self.n_parts = len(self.off) - 1
+        self.vps = int(views_per_step)
+        self.cams = cams_dev
+        self.gt, self.mask = gt, mask
+        self.views = list(train_views)
+        self.lam, self.bg = lam, tuple(bg)
+        self.use_graph = use_graph
+        N = params.shape[1]
+        H, W = gt.shape[-2], gt.shape[-1]
+        dev = params.device
+        self.units = Units.partitions(self.off, self.vps)
+        U = self.units.n
+        self.frame = Frame(N, self.units, W, H, sh_degree, device=dev, variant=variant)
+        self.opt = Adam(params, sh_degree, lrs, extent, lr_steps)
+        self.cams_step = torch.zeros(U * CAM_BYTES, dtype=torch.uint8, device=dev)
+        self.gt_step = torch.zeros((U, 3, H, W), dtype=torch.float32, device=dev)
+        self.mask_step = torch.zeros((U, H, W), dtype=torch.uint8, device=dev)
+        self.t = 0
+        self.graph = None
+        # instance capacity: the largest need over a sweep of the training views
+        need = 0
+        for t0 in range(0, len(self.views), max(1, len(self.views) // 4)):
+            self._load(t0)
+            need = max(need, self.frame.fit_capacity(params, self.cams_step))
+        self.frame.set_capacity(int(need * capacity_slack) + 4096)
+
+    def view_of(self, t: int, k: int, j: int) -> int:
+        """View of unit (partition k, slot j) at step t (staggered across partitions)."""
+        return self.views[(t * self.vps + j + k) % len(self.views)]
+
+    def _load(self, t: int):
+        u = 0
+        for k in range(self.n_parts):
+            for j in range(self.vps):
+                v = self.view_of(t, k, j)
+                self.cams_step[u * CAM_BYTES:(u + 1) * CAM_BYTES].copy_(self.cams[v * CAM_BYTES:(v + 1) * CAM_BYTES])
+                self.gt_step[u].copy_(self.gt[k, v])
+                self.mask_step[u].copy_(self.mask[k, v])
+                u += 1
+
+    def _chain(self):
+        fr = self.frame
+        fr.preprocess(self.params, self.cams_step)
+        fr.sort()
+        fr.render(self.bg)
+        fr.loss(self.gt_step, self.mask_step, self.lam)
+        fr.backward(self.params, self.cams_step, self.bg)
+        self.opt.step(fr.grads)
+
+    def capture(self):
+        """Run step t eagerly (on a side stream, so lazy initialisation happens outside the capture), then
+        record the whole training step (all units) as a CUDA graph for the following steps."""
+        self._load(self.t)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self._chain()
+        torch.cuda.current_stream().wait_stream(s)
+        self.t += 1
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._chain()
+        self.graph = g
+
+    def step(self):
+        if self.use_graph and self.graph is None:
+            self.capture()
+            return
+        self._load(self.t)
+        if self.use_graph:
+            self.graph.replay()
+        else:
+            self._chain()
+        self.t += 1
+
+    def check(self):
+        st = self.frame.read_status()
+        if st & 2:
+            self.frame.set_capacity(int(self.frame.cap * 1.5))
+            self.graph = None  # buffers changed: capture again
+        return st
+
+    def merged(self, part) -> Owned:
+        return Owned(self.off, part.boxes, part.closed_hi)
+
+    def merge_render(self, owned: Owned, cam_dev: torch.Tensor, width: int, height: int, frame: Frame | None = None):
+        N = self.params.shape[1]
+        fr = frame or Frame(N, Units.single(N), width, height, self.deg, device=self.params.device,
+                            with_backward=False, with_loss=False)
+        fr.fit_capacity(self.params, cam_dev, owned)
+        fr.merge_render(self.params, cam_dev, self.bg, owned)
+        return fr.img[0], fr

@@ -112,3 +112,54 @@ def isosurface_scene(n: int, n_modes: int, n_views: int, width: int, height: int
     init = plain_init(pts, colors, ls, sh_degree)
     return Scene(n=n, sh_degree=sh_degree, width=width, height=height, cams=cams, cams_dev=pack_cameras(cams, device),
                  gt=gt, mask=mask, init=init, pts=pts, nrm=nrm, colors=colors, spacing=spacing)
+
+
+@dataclass
+class PartitionedScene:
+    part: object                 # partition.Partition
+    sh_degree: int
+    width: int
+    height: int
+    cams: synth.Cameras
+    cams_dev: torch.Tensor
+    gt: torch.Tensor             # [n_parts, V, 3, H, W]: each partition's own GT (owned + ghost points)
+    mask: torch.Tensor           # [n_parts, V, H, W]
+    gt_full: torch.Tensor        # [V, 3, H, W]: GT of the whole scene (for the merged render)
+    mask_full: torch.Tensor
+    init: dict                   # plain init, partition-major
+    pts: np.ndarray
+    spacing: float
+    bg: tuple = (1.0, 1.0, 1.0)
+
+    @property
+    def offsets(self):
+        return self.part.offsets
+
+
+def partitioned_scene(slab_counts, n_modes: int, n_views: int, width: int, height: int, n_parts: int = 8,
+                      ghost: float = 0.05, sh_degree: int = 3, seed: int = 0, radius: float = 1.5,
+                      device="cuda") -> PartitionedScene:
+    """The interface split into x-slabs with ghost layers; uneven slab populations from a piecewise
+    constant x-density (slab_counts points per slab)."""
+    from .partition import slab_partition
+    pts, nrm, _ = synth.slab_density_points(n_modes=n_modes, slab_counts=slab_counts, seed=seed)
+    n = pts.shape[0]
+    colors = synth.lambert_colors(pts, nrm)
+    spacing = spacing_estimate(nrm, n)
+    cams = synth.orbital_cameras(n_views, radius, center=(0.5, 0.5, 0.5), width=width, height=height)
+    part = slab_partition(pts, n_parts, ghost)
+    H, W = height, width
+    gt = torch.empty((n_parts, n_views, 3, H, W), dtype=torch.float32, device=device)
+    mask = torch.empty((n_parts, n_views, H, W), dtype=torch.uint8, device=device)
+    for k in range(n_parts):
+        idx = part.members[k]
+        g, m = render_gt(gt_surfels(pts[idx], nrm[idx], colors[idx], spacing), cams, 0, (1.0, 1.0, 1.0), device,
+                         max_instances=max(8 * len(idx), 1 << 20))
+        gt[k], mask[k] = g, m
+    gt_full, mask_full = render_gt(gt_surfels(pts, nrm, colors, spacing), cams, 0, (1.0, 1.0, 1.0), device,
+                                   max_instances=max(8 * n, 1 << 20))
+    order = part.order
+    init = plain_init(pts[order], colors[order], math.log(spacing), sh_degree)
+    return PartitionedScene(part=part, sh_degree=sh_degree, width=W, height=H, cams=cams,
+                            cams_dev=pack_cameras(cams, device), gt=gt, mask=mask, gt_full=gt_full,
+                            mask_full=mask_full, init=init, pts=pts, spacing=spacing)

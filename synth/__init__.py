@@ -196,7 +196,7 @@ def interface_points(n: int, n_modes: int, seed: int = 0, x_density=None):
     return pts.astype(np.float32), nrm.astype(np.float32), field
 
 
-def slab_density_points(n: int, n_modes: int, slab_counts, seed: int = 0):
+def slab_density_points(n_modes: int, slab_counts, seed: int = 0):
     """Interface samples whose x-distribution gives the requested per-slab counts.
 
     ``slab_counts`` are the wanted counts for equal-width x-slabs of [0, 1]

@@ -1,0 +1,166 @@
+"""Partitions, batching, graph capture, autotuning and the merged render on the GPU."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2509_12138_gb300 as gs
+import synth
+from paper_2509_12138_gb300 import train as T
+from paper_2509_12138_gb300.partition import owned_mask, slab_partition
+from tests import scenes
+from tests.gpu_util import exclusion_mask, gauss64
+
+pytestmark = pytest.mark.gpu
+
+BG = np.ones(3)
+
+
+def _subset(g, idx):
+    return {k: np.asarray(v)[idx] for k, v in g.items()}
+
+
+def test_merge_render_parity():
+    """Ghost-filtered merged render equals the oracle's render of the Gaussians the oracle's filter keeps."""
+    n, deg, W, H = 3000, 1, 160, 120
+    g = synth.random_gaussians(n, deg, 5, center=(0.5, 0.5, 0.5), extent=0.5, log_scale_range=(-4.0, -2.5))
+    part = slab_partition(g["means"], 4, 0.1)
+    order = part.order
+    gp = _subset(g, order)
+    # move the means a little, as training does, so that some ghosts leave / enter their slab
+    gp["means"] = gp["means"] + np.random.default_rng(0).normal(0, 0.01, gp["means"].shape).astype(np.float32)
+    N = len(order)
+    cams = scenes.front_camera(W, H, eye=(0.5, -2.0, 1.5), target=(0.5, 0.5, 0.5))
+    owned = gs.Owned(part.offsets, part.boxes, part.closed_hi)
+    fr = gs.Frame(N, gs.Units.single(N), W, H, deg, with_backward=False, with_loss=False)
+    params = gs.pack_params(gp, deg)
+    camd = gs.pack_cameras(cams)
+    fr.fit_capacity(params, camd, owned)
+    fr.merge_render(params, camd, BG, owned)
+    torch.cuda.synchronize()
+    assert fr.read_status() == 0
+    part_of = np.repeat(np.arange(part.n), part.sizes())
+    keep = oracle.owned(gp["means"], part_of, part.boxes, part.closed_hi)
+    assert np.array_equal(keep, owned_mask(gp["means"], part))
+    assert (~keep).sum() > 0
+    # culled exactly where the filter drops
+    rad = fr.radius.cpu().numpy()
+    assert np.all(rad[~keep] == 0)
+    sub = _subset(gp, np.nonzero(keep)[0])
+    cam = oracle.camera_block(cams, 0)
+    o = oracle.render(gauss64(sub), cam, BG)
+    op = oracle.project(gauss64(sub), cam)
+    xy = fr.xy.cpu().numpy()[keep]
+    excl, _ = exclusion_mask(op, xy, rad[keep], o["tie_tiles"], o["margin"], W, H)
+    assert excl.mean() < 0.01
+    err = np.abs(fr.img.cpu().numpy()[0] - o["img"]).max(axis=0)
+    assert err[~excl].max() <= 1e-4
+
+
+def _partitioned(seed=0, n=6000, W=96, H=72, n_parts=3, views=6):
+    pts, nrm, _ = synth.interface_points(n, 4, seed)
+    col = synth.lambert_colors(pts, nrm)
+    part = slab_partition(pts, n_parts, 0.1)
+    from paper_2509_12138_gb300 import workload
+    sp = workload.spacing_estimate(nrm, n)
+    init = workload.plain_init(pts[part.order], col[part.order], np.log(2 * sp), 1)
+    init["logit_opacity"][:] = 0.5
+    cams = synth.orbital_cameras(views, 1.6, center=(0.5, 0.5, 0.5), width=W, height=H)
+    s = synth.streams(seed + 7, ["gt", "mask"])
+    gt = s["gt"].uniform(0, 1, (n_parts, views, 3, H, W)).astype(np.float32)
+    mask = (s["mask"].uniform(0, 1, (n_parts, views, H, W)) > 0.3).astype(np.uint8)
+    return init, part, cams, gt, mask
+
+
+def test_batched_partition_units_parity():
+    """One batched step over 3 partitions x 2 views: loss and gradients equal the oracle summed per unit."""
+    init, part, cams, gt, mask = _partitioned()
+    deg = 1
+    params = gs.pack_params(init, deg)
+    tr = T.BatchedTrainer(params, deg, part.offsets, gs.pack_cameras(cams), torch.from_numpy(gt).cuda(),
+                          torch.from_numpy(mask).cuda(), list(range(6)), views_per_step=2, use_graph=False)
+    tr._load(0)
+    fr = tr.frame
+    fr.preprocess(params, tr.cams_step)
+    fr.sort()
+    fr.render(tr.bg)
+    fr.loss(tr.gt_step, tr.mask_step, 0.2)
+    fr.backward(params, tr.cams_step, tr.bg)
+    torch.cuda.synchronize()
+    assert fr.read_status() == 0
+    grads = gs.unpack_grads(fr.grads, deg)
+    U = tr.units.n
+    ref_loss = 0.0
+    ref_grad = np.zeros_like(grads)
+    u = 0
+    for k in range(part.n):
+        s, e = part.offsets[k], part.offsets[k + 1]
+        sub = gauss64(_subset(init, np.arange(s, e)))
+        for j in range(2):
+            v = tr.view_of(0, k, j)
+            r = oracle.loss_and_grads(sub, oracle.camera_block(cams, v), BG, gt[k, v].astype(np.float64),
+                                      mask[k, v], 0.2)
+            ref_loss += r["loss"] / U
+            ref_grad[s:e] += r["grads"] / U
+            u += 1
+    assert float(fr.loss_val.item()) == pytest.approx(ref_loss, rel=1e-4)
+    scale = np.abs(ref_grad).max()
+    assert np.abs(grads - ref_grad).max() <= 1e-3 * scale
+
+
+def test_graph_replay_matches_eager():
+    init, part, cams, gt, mask = _partitioned(seed=1)
+    deg = 1
+    out = []
+    for use_graph in (False, True):
+        params = gs.pack_params(init, deg)
+        tr = T.BatchedTrainer(params, deg, part.offsets, gs.pack_cameras(cams), torch.from_numpy(gt).cuda(),
+                              torch.from_numpy(mask).cuda(), list(range(6)), views_per_step=1, use_graph=use_graph)
+        for _ in range(4):
+            tr.step()
+        torch.cuda.synchronize()
+        assert tr.check() == 0
+        out.append(params.clone())
+        assert int(tr.opt.step_dev.item()) == 4
+    a, b = out
+    # same arithmetic; only the order of the float atomics may differ
+    assert torch.allclose(a, b, rtol=1e-4, atol=1e-6)
+
+
+def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
+    from paper_2509_12138_gb300 import tune
+    monkeypatch.setattr(tune, "CACHE", str(tmp_path / "cache.json"))
+    init, part, cams, gt, mask = _partitioned(seed=2)
+    deg = 1
+    gtd, mkd, camd = torch.from_numpy(gt).cuda(), torch.from_numpy(mask).cuda(), gs.pack_cameras(cams)
+
+    def make(variant, vps):
+        return T.BatchedTrainer(gs.pack_params(init, deg), deg, part.offsets, camd, gtd, mkd, list(range(6)),
+                                views_per_step=vps, variant=variant)
+
+    best, table = tune.autotune(make, "test", candidates=[(0, 1), (1, 1), (2, 2)], steps=2, warmup=1)
+    assert best in [(0, 1), (1, 1), (2, 2)] and len(table) == 3 and all(v > 0 for v in table.values())
+    best2, _ = tune.autotune(make, "test", candidates=[(0, 1)])  # from the cache
+    assert best2 == best
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_blend_variants_identical(variant):
+    """The execution-shape variants give bit-identical images and identical screen-space gradients up to
+    atomic summation order."""
+    n, deg, W, H = 2000, 0, 100, 70
+    g, cams = scenes.random_scene(n, deg, 3, W, H)
+    params = gs.pack_params(g, deg)
+    camd = gs.pack_cameras(cams)
+    gt, mask = scenes.random_gt(W, H, 4)
+    res = []
+    for var in (0, variant):
+        fr = gs.Frame(n, gs.Units.single(n), W, H, deg, variant=var)
+        fr.fit_capacity(params, camd)
+        fr.forward(params, camd, BG)
+        fr.loss(torch.from_numpy(gt).cuda()[None], torch.from_numpy(mask).cuda()[None], 0.2)
+        fr.backward(params, camd, BG)
+        torch.cuda.synchronize()
+        res.append((fr.img.clone(), fr.n_contrib.clone(), fr.grads.clone()))
+    assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
+    assert torch.allclose(res[0][2], res[1][2], rtol=1e-4, atol=1e-7)
