@@ -249,6 +249,58 @@ int gs_merge_render(const float* params, int64_t n_gauss, int sh_degree, const g
                     uint32_t* d_num_instances, float* img, float* final_T, uint32_t* n_contrib,
                     int* d_status, gs_stream_t stream);
 
+/* ---- a9: learned initialiser --------------------------------------------
+ * Not in the paper: its Sec. II initialises the Gaussians from the extracted
+ * isosurface points.  The plain form used there sets each Gaussian's scale
+ * from its neighbours' distances; the learned form predicts scale, rotation
+ * and opacity from the kNN geometry with a small MLP trained on converged
+ * splats, and keeps the plain form as fallback.
+ *
+ * gs_knn: exact k nearest neighbours (self excluded) of n points [n][3] on a
+ * uniform grid of grid_dims[0..2] cells of edge cell_size starting at
+ * grid_lo (host float[3]; the grid must cover the points' bounding box),
+ * k in {3, 8, 16}.  idx [n][k] int32, dist [n][k] fp32 (Euclidean),
+ * ordered by (distance, index); -1 / inf when fewer than k other points
+ * exist.  Workspace: gs_knn_workspace_size(n, grid_dims (host int32[3])). */
+size_t gs_knn_workspace_size(int64_t n, const int32_t* grid_dims);
+int gs_knn(const float* points, int64_t n, int k, const float* grid_lo, float cell_size,
+           const int32_t* grid_dims, void* workspace, size_t workspace_bytes, int32_t* idx,
+           float* dist, gs_stream_t stream);
+
+/* MLP 112 -> 64 -> 64 -> 8 with ReLU.  Parameters: one fp32 buffer of
+ * gs_mlp_param_count() = 11912 values: W1 [112][64] (input-major), b1[64],
+ * W2 [64][64], b2[64], W3 [64][8], b3[8].  Features of point i from its 16
+ * nearest neighbours (idx/dist from gs_knn with k = 16): offsets / mean
+ * neighbour distance [0,48), neighbour normals [48,96), own normal [96,99),
+ * zeros [99,112).  GEMM operands bf16 (round to nearest even), fp32
+ * accumulation; activations and back-propagated signals rounded to bf16
+ * where they become GEMM operands.  Outputs [n][8]:
+ * (log-scale offsets (3), rotation (w, x, y, z), logit opacity). */
+int gs_mlp_param_count(void);
+/* features [n][112] as bf16 bit patterns (for inspection and tests) */
+int gs_mlp_features(const float* points, const float* normals, const int32_t* knn_idx,
+                    const float* knn_dist, int64_t n, uint16_t* features, gs_stream_t stream);
+int gs_mlp_forward(const float* points, const float* normals, const int32_t* knn_idx,
+                   const float* knn_dist, int64_t n, const float* weights, float* out,
+                   gs_stream_t stream);
+/* One Adam step (lr, betas 0.9 / 0.999, eps 1e-8, t = *d_step + 1) on the
+ * loss sum (out - targets)^2 / (8 n) over all n points.  grad: fp32 scratch
+ * [11912] (overwritten); m, v: Adam moments [11912]; d_loss: device float. */
+int gs_mlp_train_step(const float* points, const float* normals, const int32_t* knn_idx,
+                      const float* knn_dist, const float* targets, int64_t n, float* weights,
+                      float* grad, float* m, float* v, float lr, const int32_t* d_step,
+                      float* d_loss, gs_stream_t stream);
+/* Initial Gaussians 0..n-1 of a planes buffer of n_gauss Gaussians: mean =
+ * point; plain form (weights NULL): isotropic log-scale log(d3), d3 the mean
+ * of the 3 nearest distances (floored at 1e-7), identity rotation, logit
+ * opacity logit_default; learned form: log-scale log(d3) + out[0:3],
+ * rotation out[3:7], logit out[7], falling back to the plain values for a
+ * Gaussian whose outputs are non-finite or whose rotation has norm < 1e-6.
+ * SH planes are not touched.  knn_k >= 3 (16 with weights). */
+int gs_init_gaussians(const float* points, const float* normals, const int32_t* knn_idx,
+                      const float* knn_dist, int knn_k, int64_t n, const float* weights,
+                      float logit_default, float* params, int64_t n_gauss, gs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

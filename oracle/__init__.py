@@ -17,6 +17,7 @@ paper; the optimiser itself is pinned).
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -90,6 +91,7 @@ def _declare(L):
     L.orc_mlp_forward.argtypes = [C.c_int] + [_D] * 10
     L.orc_mlp_backward.argtypes = [C.c_int] + [_D] * 14
     L.orc_mlp_backward.restype = C.c_double
+    L.orc_init_gaussians.argtypes = [C.c_int, _D, C.c_int, _D, C.c_double, _D, _D, _D]
 
 
 def _d(a):
@@ -338,3 +340,13 @@ def mlp_backward(X, w, T):
     L = lib().orc_mlp_backward(n, _p(X), *[_p(a) for a in ws], _p(T),
                                *[_p(g[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
     return L, g
+
+
+def init_gaussians(knn_dist, Y=None, logit_default=math.log(0.1 / 0.9)):
+    """(log_scales [n,3], quats [n,4], logit [n]) of the plain (Y None) or learned initialiser."""
+    knn_dist = _d(knn_dist)
+    n, k = knn_dist.shape
+    ls, q, lo = np.zeros((n, 3)), np.zeros((n, 4)), np.zeros(n)
+    Yd = _d(Y) if Y is not None else None
+    lib().orc_init_gaussians(n, _p(knn_dist), k, _p(Yd), float(logit_default), _p(ls), _p(q), _p(lo))
+    return ls, q, lo

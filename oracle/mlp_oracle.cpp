@@ -156,4 +156,34 @@ double orc_mlp_backward(int n, const double* X, const double* W1, const double* 
   return L * scale;
 }
 
+// Initial Gaussian parameters from the kNN distances (and optionally the MLP
+// outputs Y [n][8]): log-scale log(max(d3, 1e-7)) (+ Y[0:3]), rotation
+// identity (or Y[3:7]), logit opacity logit_default (or Y[7]); a Gaussian whose
+// outputs are non-finite or whose rotation has norm <= 1e-6 keeps the plain
+// values.  d3 = mean of the first three neighbour distances.
+void orc_init_gaussians(int n, const double* knn_dist, int k, const double* Y, double logit_default,
+                        double* log_scales, double* quats, double* logit) {
+  for (int i = 0; i < n; ++i) {
+    double d3 = (knn_dist[(size_t)k * i] + knn_dist[(size_t)k * i + 1] + knn_dist[(size_t)k * i + 2]) / 3.0;
+    double ls = std::log(d3 > 1e-7 ? d3 : 1e-7);
+    double q[4] = {1, 0, 0, 0};
+    double s[3] = {ls, ls, ls};
+    double lo = logit_default;
+    if (Y) {
+      const double* y = Y + (size_t)KOUT * i;
+      bool ok = true;
+      for (int c = 0; c < KOUT; ++c) ok = ok && std::isfinite(y[c]);
+      double qn = std::sqrt(y[3] * y[3] + y[4] * y[4] + y[5] * y[5] + y[6] * y[6]);
+      if (ok && qn > 1e-6) {
+        for (int c = 0; c < 3; ++c) s[c] = ls + y[c];
+        for (int c = 0; c < 4; ++c) q[c] = y[3 + c];
+        lo = y[7];
+      }
+    }
+    for (int c = 0; c < 3; ++c) log_scales[3 * i + c] = s[c];
+    for (int c = 0; c < 4; ++c) quats[4 * i + c] = q[c];
+    logit[i] = lo;
+  }
+}
+
 }  // extern "C"

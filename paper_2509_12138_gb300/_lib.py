@@ -68,6 +68,13 @@ SIGNATURES = {
     "gs_project_bwd": (I32, [VP, I64, I32, C.POINTER(GsUnits), VP, C.POINTER(GsProj), C.POINTER(GsGrad2d), VP, VP]),
     "gs_adam_step": (I32, [VP, VP, VP, VP, I64, I32, c_f32p, c_f32p, I32, F32, F32, F32, VP, I32, VP]),
     "gs_step_advance": (I32, [VP, VP]),
+    "gs_knn_workspace_size": (SZ, [I64, c_i32p]),
+    "gs_knn": (I32, [VP, I64, I32, c_f32p, F32, c_i32p, VP, SZ, VP, VP, VP]),
+    "gs_mlp_param_count": (I32, []),
+    "gs_mlp_features": (I32, [VP, VP, VP, VP, I64, VP, VP]),
+    "gs_mlp_forward": (I32, [VP, VP, VP, VP, I64, VP, VP, VP]),
+    "gs_mlp_train_step": (I32, [VP, VP, VP, VP, VP, I64, VP, VP, VP, VP, F32, VP, VP, VP]),
+    "gs_init_gaussians": (I32, [VP, VP, VP, VP, I32, I64, VP, F32, VP, I64, VP]),
     "gs_merge_render": (I32, [VP, I64, I32, C.POINTER(GsOwned), VP, I32, I32, c_f32p, C.POINTER(GsProj), I64, VP, SZ,
                               VP, VP, VP, VP, VP, VP, VP, VP]),
 }

@@ -89,3 +89,5 @@ __host__ __device__ __forceinline__ int param_planes(int deg) {
 int gs_fill_units(const gs_units* u, gs::UnitTable& t, int64_t* total);
 int gs_fill_owned(const gs_owned* o, gs::OwnedTable& t);
 int gs_check_launch();
+size_t gs_scan_ws_bytes(int64_t n);
+int gs_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, void* ws, uint32_t* d_total, cudaStream_t s);

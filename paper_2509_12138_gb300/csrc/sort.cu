@@ -347,6 +347,20 @@ int bits_for(int64_t n) {
 
 }  // namespace
 
+// Exclusive scan of n uint32 values (helper for other stages): out[i] = sum in[0..i);
+// *d_total receives the sum.  ws must hold gs_scan_ws_bytes(n) bytes.
+size_t gs_scan_ws_bytes(int64_t n) { return sizeof(uint32_t) * (size_t)((n + SCAN_BLOCK - 1) / SCAN_BLOCK + 1); }
+
+int gs_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, void* ws, uint32_t* d_total, cudaStream_t s) {
+  if (n <= 0) return cudaMemsetAsync(d_total, 0, sizeof(uint32_t), s) == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+  int64_t nsb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+  uint32_t* bsums = (uint32_t*)ws;
+  k_scan_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(in, n, bsums);
+  k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);
+  k_scan_down<<<(unsigned)nsb, SCAN_T, 0, s>>>(in, n, bsums, nsb, out, INT64_MAX, d_total, nullptr);
+  return gs_check_launch();
+}
+
 GS_API size_t gs_bin_sort_workspace_size(int64_t n_proj, int64_t max_instances) {
   if (n_proj < 0 || max_instances < 0) return 0;
   return ws_layout(n_proj, max_instances).total;

@@ -109,22 +109,33 @@ def test_batched_partition_units_parity():
 
 
 def test_graph_replay_matches_eager():
+    """From identical state, one graph replay computes the same step as the eager launch chain: same
+    gradients (up to the order of float atomics), same views, same device step counter.  (Parameters are
+    not compared across several steps: Adam with eps = 1e-15 turns near-zero gradients into +-lr steps,
+    so atomic-order noise in those is amplified; that is the optimiser's definition, not a graph effect.)"""
     init, part, cams, gt, mask = _partitioned(seed=1)
     deg = 1
-    out = []
-    for use_graph in (False, True):
-        params = gs.pack_params(init, deg)
-        tr = T.BatchedTrainer(params, deg, part.offsets, gs.pack_cameras(cams), torch.from_numpy(gt).cuda(),
-                              torch.from_numpy(mask).cuda(), list(range(6)), views_per_step=1, use_graph=use_graph)
-        for _ in range(4):
-            tr.step()
+    mk = lambda g: T.BatchedTrainer(gs.pack_params(init, deg), deg, part.offsets, gs.pack_cameras(cams),
+                                    torch.from_numpy(gt).cuda(), torch.from_numpy(mask).cuda(), list(range(6)),
+                                    views_per_step=1, use_graph=g)
+    tg, te = mk(True), mk(False)
+    tg.step()  # eager first step + capture
+    te.step()
+    for a, b in ((te.params, tg.params), (te.opt.m, tg.opt.m), (te.opt.v, tg.opt.v), (te.opt.step_dev, tg.opt.step_dev)):
+        a.copy_(b)
+    for _ in range(2):
+        tg.step()  # graph replay
+        te.step()
         torch.cuda.synchronize()
-        assert tr.check() == 0
-        out.append(params.clone())
-        assert int(tr.opt.step_dev.item()) == 4
-    a, b = out
-    # same arithmetic; only the order of the float atomics may differ
-    assert torch.allclose(a, b, rtol=1e-4, atol=1e-6)
+        ga, gb = te.frame.grads, tg.frame.grads
+        scale = float(ga.abs().max())
+        assert torch.allclose(ga, gb, rtol=1e-4, atol=1e-6 * scale)
+        assert abs(float(te.frame.loss_val) - float(tg.frame.loss_val)) <= 1e-5 * abs(float(te.frame.loss_val))
+        te.params.copy_(tg.params)
+        te.opt.m.copy_(tg.opt.m)
+        te.opt.v.copy_(tg.opt.v)
+    assert tg.check() == 0 and te.check() == 0
+    assert int(tg.opt.step_dev.item()) == int(te.opt.step_dev.item()) == 3
 
 
 def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
