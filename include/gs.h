@@ -162,6 +162,29 @@ int gs_bin_sort(const gs_proj* proj, const gs_units* units, int width, int heigh
                 uint32_t* sorted_vals, uint32_t* ranges, uint32_t* d_num_instances,
                 int* d_status, gs_stream_t stream);
 
+/* ---- gs_bin_sort without a caller workspace ----------------------------
+ * The paper has no counterpart: this is a deployment variant of gs_bin_sort
+ * for callers that cannot allocate device memory (a host framework or plugin
+ * that owns every allocation, or a program that must not allocate after
+ * start-up).  It takes only the inputs and outputs of gs_bin_sort; its
+ * scratch is a fixed array of GS_STATIC_SORT_SCRATCH_BYTES in the library's
+ * own device memory, held on every GPU that loads the library until exit.
+ * Limits: at most GS_STATIC_SORT_MAX_RECORDS records (sum of gauss_count)
+ * and GS_STATIC_SORT_MAX_INSTANCES instances (the capacity: more set
+ * GS_ERR_CAPACITY in d_status and truncate, as in gs_bin_sort); more records
+ * return GS_ERR_INVALID with a message on stderr and enqueue nothing.
+ * sorted_vals must hold GS_STATIC_SORT_MAX_INSTANCES entries.  All calls share
+ * the array and it keeps the last call's contents (each call clears what must
+ * start at zero): calls whose work overlaps on the GPU race.  The first call
+ * on a device looks up the array's address with that device current; make it
+ * before any stream capture. */
+#define GS_STATIC_SORT_MAX_RECORDS 131072
+#define GS_STATIC_SORT_MAX_INSTANCES 524288
+#define GS_STATIC_SORT_SCRATCH_BYTES 13631488
+int gs_bin_sort_static(const gs_proj* proj, const gs_units* units, int width, int height,
+                       uint32_t* sorted_vals, uint32_t* ranges, uint32_t* d_num_instances,
+                       int* d_status, gs_stream_t stream);
+
 /* ---- a3: front-to-back blend per 16x16 tile -------------------------------
  * For pixel (px, py) over its tile's list in order: d = xy - (px, py),
  * power = -(A dx^2 + C dy^2)/2 - B dx dy, skipped if > 0;

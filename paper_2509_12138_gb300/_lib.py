@@ -58,6 +58,7 @@ SIGNATURES = {
                             VP, VP]),
     "gs_bin_sort_workspace_size": (SZ, [I64, I64]),
     "gs_bin_sort": (I32, [C.POINTER(GsProj), C.POINTER(GsUnits), I32, I32, I64, VP, SZ, VP, VP, VP, VP, VP]),
+    "gs_bin_sort_static": (I32, [C.POINTER(GsProj), C.POINTER(GsUnits), I32, I32, VP, VP, VP, VP, VP]),
     "gs_render_fwd": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, c_f32p, VP, VP, VP, I32, VP]),
     "gs_loss_workspace_size": (SZ, [I32, I32, I32]),
     "gs_loss": (I32, [VP, VP, VP, I32, I32, I32, F32, VP, SZ, VP, VP, VP]),

@@ -1,0 +1,88 @@
+// gs_bin_sort_static: the duplication + radix sort + tile ranges of
+// gs_bin_sort for callers that cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc at all: code running inside another
+// framework's memory pool or a plugin host that owns every allocation, and
+// programs that must not allocate after start-up.  This entry point takes
+// only the caller's inputs and outputs; its scratch is a fixed array in the
+// library's own device memory, which every GPU that loads the library holds
+// (GS_STATIC_SORT_SCRATCH_BYTES) until the process exits.
+//
+// Limits: at most GS_STATIC_SORT_MAX_RECORDS projected records and
+// GS_STATIC_SORT_MAX_INSTANCES tile instances per call; larger inputs are
+// rejected with GS_ERR_INVALID before anything is enqueued (and more
+// instances than the capacity set GS_ERR_CAPACITY, as in gs_bin_sort).
+//
+// All calls share the one array: two calls whose work overlaps on the GPU
+// (different streams, or different host threads) race on it.  Every call
+// clears the parts of the array that must start at zero.
+//
+// The first call on a device looks up the array's device address
+// (cudaGetSymbolAddress, with that device current) and caches it; make that
+// first call outside any stream capture.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int height, int64_t max_instances,
+                     void* workspace, size_t workspace_bytes, uint32_t* sorted_vals, uint32_t* ranges,
+                     uint32_t* d_num_instances, int* d_status, cudaStream_t s);
+
+namespace {
+
+constexpr size_t SCRATCH_BYTES = (size_t)GS_STATIC_SORT_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_sort_scratch[SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_mu;
+void* g_ptr[MAX_DEVICES] = {nullptr};
+
+// Device address of the scratch array on the current device (set up once per device).
+int scratch_ptr(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return GS_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
+    if (e != cudaSuccess || !p) {
+      fprintf(stderr, "libgs: gs_bin_sort_static: cudaGetSymbolAddress failed on device %d: %s\n", dev,
+              cudaGetErrorString(e));
+      return GS_ERR_CUDA;
+    }
+    g_ptr[dev] = p;
+  }
+  *out = g_ptr[dev];
+  return GS_OK;
+}
+
+}  // namespace
+
+GS_API int gs_bin_sort_static(const gs_proj* proj, const gs_units* units, int width, int height,
+                              uint32_t* sorted_vals, uint32_t* ranges, uint32_t* d_num_instances, int* d_status,
+                              gs_stream_t stream) {
+  if (!units || units->n_units < 1 || !units->gauss_count) return GS_ERR_INVALID;
+  int64_t P = 0;
+  for (int u = 0; u < units->n_units; ++u) P += units->gauss_count[u];
+  if (P > GS_STATIC_SORT_MAX_RECORDS) {
+    fprintf(stderr, "libgs: gs_bin_sort_static: %lld records exceed the limit of %d\n", (long long)P,
+            GS_STATIC_SORT_MAX_RECORDS);
+    return GS_ERR_INVALID;
+  }
+  const int64_t cap = GS_STATIC_SORT_MAX_INSTANCES;
+  size_t need = gs_bin_sort_workspace_size(P, cap);
+  if (need == 0 || need > SCRATCH_BYTES) {
+    fprintf(stderr, "libgs: gs_bin_sort_static: scratch of %zu bytes needed, %zu available\n", need,
+            SCRATCH_BYTES);
+    return GS_ERR_INVALID;
+  }
+  void* ws = nullptr;
+  int r = scratch_ptr(&ws);
+  if (r != GS_OK) return r;
+  return gs_bin_sort_impl(proj, units, width, height, cap, ws, SCRATCH_BYTES, sorted_vals, ranges, d_num_instances,
+                          d_status, (cudaStream_t)stream);
+}
