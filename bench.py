@@ -197,7 +197,7 @@ def kernel_launch_count(frame, lam):
     sort = 4 + 3 * passes + 1
     fwd = 1
     loss = 1 + (2 if lam > 0 else 1) + 1
-    bwd = 2
+    bwd = 1
     adam = 2
     return pre + sort + fwd + loss + bwd + adam
 
@@ -231,12 +231,10 @@ def run_ours(args, wl, rank, world):
         if ev: ev[4].record()
         frame.blend_backward(bg)
         if ev: ev[5].record()
-        frame.project_backward(params, cam)
+        opt.fused_step(frame, cam)
         if ev: ev[6].record()
-        opt.step(frame.grads)
-        if ev: ev[7].record()
 
-    stages = ["preprocess", "bin_sort", "render_fwd", "loss", "blend_bwd", "project_bwd", "adam"]
+    stages = ["preprocess", "bin_sort", "render_fwd", "loss", "blend_bwd", "project_bwd_adam"]
     for w in range(args.warmup):
         step(w % V)
     torch.cuda.synchronize()
@@ -256,7 +254,7 @@ def run_ours(args, wl, rank, world):
 
     clocks = ClockSampler(device_uuid(dev))
     clocks.start()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
@@ -273,6 +271,13 @@ def run_ours(args, wl, rank, world):
         for s in range(len(stages)):
             stage_ms[s] += e[s].elapsed_time(e[s + 1])
     stage_ms /= args.steps
+
+    # blended (pixel, record) pairs of the timed views: the blend kernels' algorithmic work
+    pairs = []
+    for k in range(min(args.steps, 16)):
+        frame.forward(params, scene.cam((args.warmup + k) % V), bg)
+        pairs.append(frame.blend_pairs())
+    pairs_per_step = float(np.mean(pairs))
 
     # render-only (a1-a3) for Mpix/s
     torch.cuda.synchronize()
@@ -307,19 +312,23 @@ def run_ours(args, wl, rank, world):
         frame.sort()
         frame.render(bg)
         frame.loss(gt_dev, mask_dev, LAMBDA_SSIM)
-        frame.backward(params, cam, bg)
-        opt.step(frame.grads)
+        frame.blend_backward(bg)
+        opt.fused_step(frame, cam)
         loss_host[k:k + 1].copy_(frame.loss_val, non_blocking=True)
     torch.cuda.synchronize()
     e_sec = time.perf_counter() - e0
     barrier()
     return dict(scene=scene, frame=frame, ms_total=ms_total, stage_ms=stage_ms, stages=stages, ms_render=ms_render,
-                clocks=clk, e2e_sec=e_sec, instances=instances, tile_len=tile_len, h2d=(3 * H * W * 4 + H * W), d2h=4,
+                clocks=clk, e2e_sec=e_sec, instances=instances, tile_len=tile_len, pairs=pairs_per_step, h2d=(3 * H * W * 4 + H * W), d2h=4,
                 launches=kernel_launch_count(frame, LAMBDA_SSIM) * args.steps, N=N, W=W, H=H)
 
 
-def roofline(res):
-    """Achieved vs peak for the dominant stage (largest share of the step)."""
+FWD_FLOP_PER_PAIR = 21   # FP32 operations per blended pair in k_render_fwd (an FMA counts 2)
+BWD_FLOP_PER_PAIR = 60   # likewise for k_render_bwd
+
+
+def rooflines(res):
+    """Achieved vs peak for every stage; returns (dominant stage's roofline, all)."""
     peaks = {}
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -327,28 +336,41 @@ def roofline(res):
     hbm = peaks.get("hbm_gbs")
     src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    N, I = res["N"], res["instances"]
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    sms = 152
+    fp32_tflops = 2 * 128 * sms * mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 x clock
+    N, I, pairs = res["N"], res["instances"], res["pairs"]
     passes = 6
-    bytes_per = {
-        # algorithmic bytes per launch
-        "preprocess": N * (59 * 4 + 52),
-        "bin_sort": N * 8 + I * (12 + passes * 32 + 16),
-        "project_bwd": N * (59 * 4 + 40 + 4 + 59 * 4),
-        "adam": N * 59 * 28,
-        "loss": res["W"] * res["H"] * (3 * 4 * 3 + 1 + 3 * 4 * 6),
+    work = {
+        "preprocess": ("hbm", N * (59 * 4 + 52)),
+        "bin_sort": ("hbm", N * 8 + I * (12 + passes * 32 + 16)),
+        "project_bwd_adam": ("hbm", N * (59 * 4 * 6 + 40 + 4)),
+        "loss": ("hbm", res["W"] * res["H"] * (3 * 4 * 3 + 1 + 3 * 4 * 6)),
+        "render_fwd": ("alu", pairs * FWD_FLOP_PER_PAIR),
+        "blend_bwd": ("alu", pairs * BWD_FLOP_PER_PAIR),
     }
-    order = np.argsort(-res["stage_ms"])
-    out = None
-    for k in order:
-        name = res["stages"][k]
-        if name in bytes_per:
-            ms = res["stage_ms"][k]
-            ach = bytes_per[name] / (ms * 1e-3) / 1e9
-            out = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                   "frac": round(ach / hbm, 4), "traffic": None, "peak_source": src,
-                   "share": round(float(ms / res["stage_ms"].sum()), 4)}
-            break
-    return out
+    kernel = {"preprocess": "k_preprocess", "bin_sort": "sort chain", "project_bwd_adam": "k_project_bwd_adam",
+              "loss": "loss kernels", "render_fwd": "k_render_fwd", "blend_bwd": "k_render_bwd"}
+    out = {}
+    for name, ms in zip(res["stages"], res["stage_ms"]):
+        if name not in work:
+            continue
+        bound, amount = work[name]
+        if bound == "hbm":
+            ach = amount / (ms * 1e-3) / 1e9
+            out[name] = {"kernel": kernel[name], "bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
+                         "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
+                         "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+        else:
+            ach = amount / (ms * 1e-3) / 1e12
+            out[name] = {"kernel": kernel[name], "bound": "alu", "achieved": round(ach, 3),
+                         "peak": round(fp32_tflops, 2), "unit": "TFLOP/s",
+                         "frac": round(ach / fp32_tflops, 4), "traffic": None,
+                         "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz",
+                         "work": f"{pairs:.3e} blended pairs x {FWD_FLOP_PER_PAIR if name == 'render_fwd' else BWD_FLOP_PER_PAIR} FLOP"}
+        out[name]["share"] = round(float(ms / res["stage_ms"].sum()), 4)
+    dom = max(out, key=lambda k: out[k]["share"])
+    return out[dom], out
 
 
 def main():
@@ -392,8 +414,10 @@ def main():
         "instances_per_view": res["instances"], "tile_list_len": res["tile_len"],
         "e2e": {"value": round(world * args.steps / e2e_sec, 3), "unit": "iters/s",
                 "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
-        "gpu_launches": res["launches"], "clocks": res["clocks"], "roofline": roofline(res),
+        "gpu_launches": res["launches"], "clocks": res["clocks"],
     }
+    line["roofline"], line["stage_rooflines"] = rooflines(res)
+    line["blended_pairs_per_view"] = res["pairs"]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(res["scene"], args.cpu_window)
     if rank == 0:

@@ -198,6 +198,13 @@ int gs_render_fwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32
                   int n_units, int width, int height, const float* bg, float* img,
                   float* final_T, uint32_t* n_contrib, int variant, gs_stream_t stream);
 
+/* Diagnostic: *d_count = number of blended (pixel, record) pairs of the last
+ * gs_render_fwd (records before n_contrib whose alpha reaches 1/255); the
+ * algorithmic work unit of the blend kernels. */
+int gs_blend_pairs(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges,
+                   int n_units, int width, int height, const uint32_t* n_contrib,
+                   unsigned long long* d_count, gs_stream_t stream);
+
 /* ---- a4: masked photometric loss (mask: Sec. II, "Image Rendering and
  * Masking") ---------------------------------------------------------------
  * Per unit: L = (1 - lambda) L1 + lambda (1 - SSIM), with
@@ -253,6 +260,16 @@ int gs_project_bwd(const float* params, int64_t n_gauss, int sh_degree, const gs
 int gs_adam_step(float* params, float* grads, float* m, float* v, int64_t n_gauss, int n_planes,
                  const float* lr_init, const float* lr_final, int32_t lr_steps, float beta1,
                  float beta2, float eps, const int32_t* d_step, int zero_grad, gs_stream_t stream);
+
+/* Projection backward fused with the Adam step (same arithmetic as
+ * gs_project_bwd followed by gs_adam_step with zero_grad = 0): each
+ * Gaussian's parameter gradient is formed in registers and applied at once.
+ * grads may be NULL; otherwise it also receives the gradient. */
+int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
+                        const gs_camera* cams, const gs_proj* proj, const gs_grad2d* g2d, float* m,
+                        float* v, const float* lr_init, const float* lr_final, int32_t lr_steps,
+                        float beta1, float beta2, float eps, const int32_t* d_step, float* grads,
+                        gs_stream_t stream);
 
 /* *d_step += 1 on the device (keeps CUDA-graph replays advancing). */
 int gs_step_advance(int32_t* d_step, gs_stream_t stream);

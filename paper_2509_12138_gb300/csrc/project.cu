@@ -280,31 +280,24 @@ __global__ void __launch_bounds__(256) k_preprocess(const float4* __restrict__ p
   tiles[p] = tiles_out;
 }
 
-// Projection backward: chain rule of k_preprocess for every parameter,
-// summed over the units that contain Gaussian i.
+// Projection backward: chain rule of k_preprocess for every parameter of
+// Gaussian i, summed over the units that contain it.  c holds the SH
+// coefficients (loaded by the caller); the results go to dmean, dls, dq,
+// dlogit and dsh (SH gradients, same packing as c).
 template <int DEG>
-__global__ void __launch_bounds__(128) k_project_bwd(const float4* __restrict__ params, int64_t N,
-                                                     UnitTable U, const gs_camera* __restrict__ cams,
-                                                     const int* __restrict__ radius,
-                                                     const float2* __restrict__ gxy,
-                                                     const float4* __restrict__ gco,
-                                                     const float4* __restrict__ grgb,
-                                                     float4* __restrict__ grads) {
+__device__ __forceinline__ void project_grads(int64_t i, float4 mean, float4 sop, float4 quat, const float* c,
+                                              const UnitTable& U, const gs_camera* __restrict__ cams,
+                                              const int* __restrict__ radius, const float2* __restrict__ gxy,
+                                              const float4* __restrict__ gco, const float4* __restrict__ grgb,
+                                              float* dmean, float* dls, float* dq, float& dlogit, float* dsh) {
   constexpr int NC = ShCount<DEG>::NC;
   constexpr int NP = ShCount<DEG>::NP;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  float4 mean = __ldg(params + i);
-  float4 sop = __ldg(params + N + i);
-  float4 quat = __ldg(params + 2 * N + i);
-  float c[4 * NP];
-  load_sh<DEG>(params, N, i, c);
-  float dmean[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
-  float dlogit = 0.f;
-  float dsh[4 * NP];
+  dmean[0] = dmean[1] = dmean[2] = 0.f;
+  dls[0] = dls[1] = dls[2] = 0.f;
+  dq[0] = dq[1] = dq[2] = dq[3] = 0.f;
+  dlogit = 0.f;
   #pragma unroll
   for (int k = 0; k < 4 * NP; ++k) dsh[k] = 0.f;
-
   for (int u = 0; u < U.n; ++u) {
     int64_t cnt = U.proj_base[u + 1] - U.proj_base[u];
     int64_t l = i - U.gauss_begin[u];
@@ -444,6 +437,26 @@ __global__ void __launch_bounds__(128) k_project_bwd(const float4* __restrict__ 
     dq[2] += (gy - dot * y) * inv;
     dq[3] += (gz - dot * z) * inv;
   }
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(128) k_project_bwd(const float4* __restrict__ params, int64_t N,
+                                                     UnitTable U, const gs_camera* __restrict__ cams,
+                                                     const int* __restrict__ radius,
+                                                     const float2* __restrict__ gxy,
+                                                     const float4* __restrict__ gco,
+                                                     const float4* __restrict__ grgb,
+                                                     float4* __restrict__ grads) {
+  constexpr int NP = ShCount<DEG>::NP;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  float4 mean = __ldg(params + i);
+  float4 sop = __ldg(params + N + i);
+  float4 quat = __ldg(params + 2 * N + i);
+  float c[4 * NP];
+  load_sh<DEG>(params, N, i, c);
+  float dmean[3], dls[3], dq[4], dlogit, dsh[4 * NP];
+  project_grads<DEG>(i, mean, sop, quat, c, U, cams, radius, gxy, gco, grgb, dmean, dls, dq, dlogit, dsh);
   grads[i] = make_float4(dmean[0], dmean[1], dmean[2], 0.f);
   grads[N + i] = make_float4(dls[0], dls[1], dls[2], dlogit);
   grads[2 * N + i] = make_float4(dq[0], dq[1], dq[2], dq[3]);
@@ -490,10 +503,80 @@ __global__ void __launch_bounds__(256) k_adam(float4* __restrict__ p, float4* __
   }
 }
 
-__global__ void k_step_advance(int32_t* s) { *s += 1; }
+// Adam update of one float4 of parameters (textbook form, bias-corrected).
+__device__ __forceinline__ void adam4(float4& P, float4 G, float4& M, float4& V, float4 L, float b1, float b2,
+                                      float ibc1, float ibc2, float eps) {
+  float* pp = &P.x; const float* gg = &G.x; float* mm = &M.x; float* vv = &V.x; const float* ll = &L.x;
+  #pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    mm[c] = b1 * mm[c] + (1.f - b1) * gg[c];
+    vv[c] = b2 * vv[c] + (1.f - b2) * gg[c] * gg[c];
+    pp[c] -= ll[c] * (mm[c] * ibc1) / (sqrtf(vv[c] * ibc2) + eps);
+  }
+}
 
-template <template <int> class K>
-struct DegDispatch;
+// Projection backward fused with Adam: the parameter gradient of Gaussian i
+// is formed in registers and applied at once, so it never goes to memory
+// (optionally it is also written to `grads`).
+template <int DEG>
+__global__ void __launch_bounds__(128) k_project_bwd_adam(float4* __restrict__ params, int64_t N, UnitTable U,
+                                                          const gs_camera* __restrict__ cams,
+                                                          const int* __restrict__ radius,
+                                                          const float2* __restrict__ gxy,
+                                                          const float4* __restrict__ gco,
+                                                          const float4* __restrict__ grgb, float4* __restrict__ m,
+                                                          float4* __restrict__ v, AdamLR lr, int lr_steps, float b1,
+                                                          float b2, float eps, const int32_t* __restrict__ d_step,
+                                                          float4* __restrict__ grads) {
+  constexpr int NP = ShCount<DEG>::NP;
+  constexpr int NPL = 3 + NP;
+  __shared__ float4 s_lr[16];
+  int t = *d_step + 1;
+  if (threadIdx.x < NPL) {
+    float frac = lr_steps > 0 ? (float)min(t, lr_steps) / (float)lr_steps : 0.f;
+    float4 a = lr.init[threadIdx.x], b = lr.fin[threadIdx.x];
+    auto sched = [&](float x0, float x1) { return (x0 == x1 || x0 <= 0.f) ? x0 : x0 * powf(x1 / x0, frac); };
+    s_lr[threadIdx.x] = make_float4(sched(a.x, b.x), sched(a.y, b.y), sched(a.z, b.z), sched(a.w, b.w));
+  }
+  __syncthreads();
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  float ibc1 = 1.f / (1.f - powf(b1, (float)t)), ibc2 = 1.f / (1.f - powf(b2, (float)t));
+  float4 mean = params[i];
+  float4 sop = params[N + i];
+  float4 quat = params[2 * N + i];
+  float c[4 * NP];
+  #pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    float4 q = params[(3 + k) * N + i];
+    c[4 * k] = q.x; c[4 * k + 1] = q.y; c[4 * k + 2] = q.z; c[4 * k + 3] = q.w;
+  }
+  float dmean[3], dls[3], dq[4], dlogit, dsh[4 * NP];
+  project_grads<DEG>(i, mean, sop, quat, c, U, cams, radius, gxy, gco, grgb, dmean, dls, dq, dlogit, dsh);
+  float4 G[3] = {make_float4(dmean[0], dmean[1], dmean[2], 0.f), make_float4(dls[0], dls[1], dls[2], dlogit),
+                 make_float4(dq[0], dq[1], dq[2], dq[3])};
+  float4 Pv[3] = {mean, sop, quat};
+  #pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    int64_t o = k * N + i;
+    float4 M = m[o], V = v[o];
+    adam4(Pv[k], G[k], M, V, s_lr[k], b1, b2, ibc1, ibc2, eps);
+    params[o] = Pv[k]; m[o] = M; v[o] = V;
+    if (grads) grads[o] = G[k];
+  }
+  #pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    int64_t o = (3 + k) * N + i;
+    float4 P = make_float4(c[4 * k], c[4 * k + 1], c[4 * k + 2], c[4 * k + 3]);
+    float4 Gk = make_float4(dsh[4 * k], dsh[4 * k + 1], dsh[4 * k + 2], dsh[4 * k + 3]);
+    float4 M = m[o], V = v[o];
+    adam4(P, Gk, M, V, s_lr[3 + k], b1, b2, ibc1, ibc2, eps);
+    params[o] = P; m[o] = M; v[o] = V;
+    if (grads) grads[o] = Gk;
+  }
+}
+
+__global__ void k_step_advance(int32_t* s) { *s += 1; }
 
 }  // namespace
 
@@ -644,5 +727,43 @@ GS_API int gs_adam_step(float* params, float* grads, float* m, float* v, int64_t
 GS_API int gs_step_advance(int32_t* d_step, gs_stream_t stream) {
   if (!d_step) return GS_ERR_INVALID;
   k_step_advance<<<1, 1, 0, (cudaStream_t)stream>>>(d_step);
+  return gs_check_launch();
+}
+
+GS_API int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
+                               const gs_camera* cams, const gs_proj* proj, const gs_grad2d* g2d, float* m, float* v,
+                               const float* lr_init, const float* lr_final, int32_t lr_steps, float beta1,
+                               float beta2, float eps, const int32_t* d_step, float* grads, gs_stream_t stream) {
+  UnitTable U;
+  int64_t P = 0;
+  int npl = param_planes(sh_degree);
+  if (((!params || !m || !v) && n_gauss > 0) || !cams || !proj || !g2d || n_gauss < 0 || npl < 0 || !lr_init ||
+      !d_step)
+    return GS_ERR_INVALID;
+  if (!proj->radius || !g2d->dxy || !g2d->dconic_op || !g2d->drgb) return GS_ERR_INVALID;
+  if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps >= 0.f)) return GS_ERR_INVALID;
+  if (gs_fill_units(units, U, &P) != GS_OK || !units_in_range(U, n_gauss)) return GS_ERR_INVALID;
+  AdamLR lr;
+  memset(&lr, 0, sizeof(lr));
+  for (int k = 0; k < npl; ++k) {
+    const float* f = lr_final ? lr_final : lr_init;
+    lr.init[k] = make_float4(lr_init[4 * k], lr_init[4 * k + 1], lr_init[4 * k + 2], lr_init[4 * k + 3]);
+    lr.fin[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+  }
+  if (n_gauss == 0) return GS_OK;
+  dim3 block(128), grid((unsigned)((n_gauss + 127) / 128));
+  cudaStream_t s = (cudaStream_t)stream;
+#define GS_PBA(D)                                                                                                \
+  k_project_bwd_adam<D><<<grid, block, 0, s>>>((float4*)params, n_gauss, U, cams, proj->radius,                 \
+                                               (const float2*)g2d->dxy, (const float4*)g2d->dconic_op,          \
+                                               (const float4*)g2d->drgb, (float4*)m, (float4*)v, lr, lr_steps,   \
+                                               beta1, beta2, eps, d_step, (float4*)grads)
+  switch (sh_degree) {
+    case 0: GS_PBA(0); break;
+    case 1: GS_PBA(1); break;
+    case 2: GS_PBA(2); break;
+    default: GS_PBA(3); break;
+  }
+#undef GS_PBA
   return gs_check_launch();
 }

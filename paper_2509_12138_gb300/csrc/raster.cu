@@ -264,6 +264,36 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict
   }
 }
 
+// Number of blended (pixel, record) pairs: records before n_contrib whose
+// alpha reaches 1/255 (the work any implementation of the blend must do).
+__global__ void __launch_bounds__(TILE_PIX) k_blend_pairs(const uint2* __restrict__ ranges,
+                                                          const uint32_t* __restrict__ vals,
+                                                          const float2* __restrict__ xy,
+                                                          const float4* __restrict__ conic_op, int W, int H, int TX,
+                                                          int n_tiles, const uint32_t* __restrict__ n_contrib,
+                                                          unsigned long long* __restrict__ count) {
+  int tile = blockIdx.x, u = blockIdx.y;
+  int tx = tile % TX, ty = tile / TX;
+  int px = tx * TILE + (threadIdx.x & 15), py = ty * TILE + (threadIdx.x >> 4);
+  unsigned long long c = 0;
+  if (px < W && py < H) {
+    uint2 rg = ranges[(int64_t)u * n_tiles + tile];
+    int last = (int)n_contrib[(int64_t)u * W * H + (int64_t)py * W + px];
+    for (int j = 0; j < last; ++j) {
+      uint32_t p = vals[rg.x + j];
+      float2 m = xy[p];
+      float4 co = conic_op[p];
+      float power = splat_power(co.x, co.y, co.z, m.x - (float)px, m.y - (float)py);
+      if (power > 0.f) continue;
+      float alpha = fminf(ALPHA_MAX, co.w * __expf(power));
+      if (alpha >= ALPHA_MIN) ++c;
+    }
+  }
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
 }  // namespace
 
 int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
@@ -311,5 +341,20 @@ int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const ui
                                              g2d->dconic_op, g2d->drgb)
   if (variant == 0) GS_BWD(8); else if (variant == 1) GS_BWD(16); else GS_BWD(4);
 #undef GS_BWD
+  return gs_check_launch();
+}
+
+GS_API int gs_blend_pairs(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
+                          int width, int height, const uint32_t* n_contrib, unsigned long long* d_count,
+                          gs_stream_t stream) {
+  if (!proj || !proj->xy || !proj->conic_op || !sorted_vals || !ranges || !n_contrib || !d_count || n_units < 1 ||
+      n_units > GS_MAX_UNITS || width <= 0 || height <= 0)
+    return GS_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), s) != cudaSuccess) return GS_ERR_CUDA;
+  int TX = (width + TILE - 1) / TILE, TY = (height + TILE - 1) / TILE;
+  k_blend_pairs<<<dim3(TX * TY, n_units), TILE_PIX, 0, s>>>((const uint2*)ranges, sorted_vals, (const float2*)proj->xy,
+                                                            (const float4*)proj->conic_op, width, height, TX, TX * TY,
+                                                            n_contrib, d_count);
   return gs_check_launch();
 }

@@ -263,6 +263,13 @@ class Frame:
     def read_status(self, clear=True) -> int:
         return int(self.L.gs_status_read(_ptr(self.status), 1 if clear else 0, _stream()))
 
+    def blend_pairs(self) -> int:
+        """Blended (pixel, record) pairs of the last forward (diagnostic; synchronises)."""
+        cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
+        check(self.L.gs_blend_pairs(C.byref(self.proj), _ptr(self.sorted_vals), _ptr(self.ranges), self.units.n,
+                                    self.W, self.H, _ptr(self.n_contrib), _ptr(cnt), _stream()), "gs_blend_pairs")
+        return int(cnt.item())
+
     def instances(self) -> int:
         return int(self.num_instances.item())
 
@@ -343,6 +350,18 @@ class Adam:
         self.lr_steps = int(lr_steps)
         self.b1, self.b2 = betas
         self.eps = eps
+
+    def fused_step(self, frame: "Frame", cams_dev, keep_grads: bool = False):
+        """Projection backward of ``frame``'s screen-space gradients fused with this Adam step
+        (gs_project_bwd_adam); ``frame.grads`` receives the gradient only if keep_grads."""
+        npl, n = self.params.shape[0], self.params.shape[1]
+        check(self.L.gs_project_bwd_adam(_ptr(self.params), n, frame.deg, C.byref(frame.units.struct),
+                                         _ptr(cams_dev), C.byref(frame.proj), C.byref(frame.g2d), _ptr(self.m),
+                                         _ptr(self.v), self.lr_init.ctypes.data_as(_lib.c_f32p),
+                                         self.lr_final.ctypes.data_as(_lib.c_f32p), self.lr_steps, self.b1, self.b2,
+                                         self.eps, _ptr(self.step_dev), _ptr(frame.grads) if keep_grads else None,
+                                         _stream()), "gs_project_bwd_adam")
+        check(self.L.gs_step_advance(_ptr(self.step_dev), _stream()), "gs_step_advance")
 
     def step(self, grads: torch.Tensor, zero_grad: bool = False):
         npl, n = self.params.shape[0], self.params.shape[1]

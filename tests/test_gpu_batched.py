@@ -119,6 +119,7 @@ def test_graph_replay_matches_eager():
                                     torch.from_numpy(gt).cuda(), torch.from_numpy(mask).cuda(), list(range(6)),
                                     views_per_step=1, use_graph=g)
     tg, te = mk(True), mk(False)
+    tg.keep_grads = te.keep_grads = True
     tg.step()  # eager first step + capture
     te.step()
     for a, b in ((te.params, tg.params), (te.opt.m, tg.opt.m), (te.opt.v, tg.opt.v), (te.opt.step_dev, tg.opt.step_dev)):
@@ -175,3 +176,55 @@ def test_blend_variants_identical(variant):
         res.append((fr.img.clone(), fr.n_contrib.clone(), fr.grads.clone()))
     assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
     assert torch.allclose(res[0][2], res[1][2], rtol=1e-4, atol=1e-7)
+
+
+def test_fused_projection_backward_adam_matches_separate():
+    """gs_project_bwd_adam == gs_project_bwd followed by gs_adam_step (same gradient, same update)."""
+    n, deg, W, H = 3000, 3, 120, 90
+    g, cams = scenes.random_scene(n, deg, 21, W, H)
+    camd = gs.pack_cameras(cams)
+    gt, mask = scenes.random_gt(W, H, 22)
+    out = []
+    for fused in (False, True):
+        params = gs.pack_params(g, deg)
+        fr = gs.Frame(n, gs.Units.single(n), W, H, deg)
+        fr.fit_capacity(params, camd)
+        opt = gs.Adam(params, deg, extent=1.5, lr_steps=5)
+        for _ in range(3):
+            fr.forward(params, camd, BG)
+            fr.loss(torch.from_numpy(gt).cuda()[None], torch.from_numpy(mask).cuda()[None], 0.2)
+            fr.blend_backward(BG)
+            if fused:
+                opt.fused_step(fr, camd, keep_grads=True)
+            else:
+                fr.project_backward(params, camd)
+                opt.step(fr.grads)
+                torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        out.append((params.clone(), opt.m.clone(), fr.grads.clone()))
+        if not fused:
+            state = (params.clone(), opt.m.clone(), opt.v.clone(), opt.step_dev.clone())
+    # one more step from identical state: same gradient and same update
+    (p0, m0, v0, s0) = state
+    res = []
+    for fused in (False, True):
+        params = p0.clone()
+        fr = gs.Frame(n, gs.Units.single(n), W, H, deg)
+        fr.fit_capacity(params, camd)
+        opt = gs.Adam(params, deg, extent=1.5, lr_steps=5)
+        opt.m.copy_(m0); opt.v.copy_(v0); opt.step_dev.copy_(s0)
+        fr.forward(params, camd, BG)
+        fr.loss(torch.from_numpy(gt).cuda()[None], torch.from_numpy(mask).cuda()[None], 0.2)
+        fr.blend_backward(BG)
+        if fused:
+            opt.fused_step(fr, camd, keep_grads=True)
+        else:
+            fr.project_backward(params, camd)
+            opt.step(fr.grads)
+        torch.cuda.synchronize()
+        res.append((params.clone(), opt.m.clone(), opt.v.clone(), fr.grads.clone()))
+    (pa, ma, va, ga), (pb, mb, vb, gb) = res
+    sc = float(ga.abs().max())
+    assert torch.allclose(ga, gb, rtol=1e-4, atol=1e-6 * sc)
+    assert torch.allclose(ma, mb, rtol=1e-4, atol=1e-7 * sc)
+    assert torch.allclose(pa, pb, rtol=1e-5, atol=1e-5)
