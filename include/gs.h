@@ -89,7 +89,8 @@ typedef struct gs_camera {
 typedef struct gs_proj {
   float* xy;        /* [P][2]  pixel-space mean                            */
   float* conic_op;  /* [P][4]  (A, B, C, opacity), conic = inverse 2D cov  */
-  float* rgb;       /* [P][4]  (r, g, b, 0) after SH, +0.5 and clamp at 0  */
+  float* rgb;       /* [P][4]  (r, g, b, f) after SH, +0.5 and clamp at 0;
+                     f: power below which alpha < 1/255 for certain      */
   float* depth;     /* [P]     camera-space z                              */
   int32_t* radius;  /* [P]     3-sigma radius in pixels, 0 = culled        */
   uint32_t* tiles;  /* [P]     number of 16x16 tiles the splat touches     */
@@ -153,6 +154,14 @@ int gs_preprocess(const float* params, int64_t n_gauss, int sh_degree, const gs_
  * A stable LSD radix sort (8-bit digits) orders the keys, so equal keys keep
  * record order: each tile's list is ordered by (depth, record index).
  * ranges[u * n_tiles + tile] = [start, end) into sorted_vals.
+ * tile_order (may be NULL): receives the U * n_tiles block indices u * n_tiles +
+ * tile ordered by decreasing list length class (heaviest first), which the
+ * blend calls use to schedule long lists early.
+ * block_masks (may be NULL; [max_instances] uint16): for each sorted instance,
+ * bit 4 by + bx is set iff the record's alpha >= 1/255 ellipse (a conservative
+ * box of it) reaches pixel block (bx, by) (4x4 pixels) of the instance's
+ * tile; the blend calls use it to skip records that cannot touch a warp's
+ * pixels.
  * max_instances: capacity of the instance buffers; on overflow GS_ERR_CAPACITY
  * is set in d_status and the lists are truncated.  d_num_instances: device
  * uint32 receiving the instance count.  Workspace: gs_bin_sort_workspace_size. */
@@ -160,7 +169,7 @@ size_t gs_bin_sort_workspace_size(int64_t n_proj, int64_t max_instances);
 int gs_bin_sort(const gs_proj* proj, const gs_units* units, int width, int height,
                 int64_t max_instances, void* workspace, size_t workspace_bytes,
                 uint32_t* sorted_vals, uint32_t* ranges, uint32_t* d_num_instances,
-                int* d_status, gs_stream_t stream);
+                uint32_t* tile_order, uint16_t* block_masks, int* d_status, gs_stream_t stream);
 
 /* ---- gs_bin_sort without a caller workspace ----------------------------
  * The paper has no counterpart: this is a deployment variant of gs_bin_sort
@@ -193,10 +202,14 @@ int gs_bin_sort_static(const gs_proj* proj, const gs_units* units, int width, in
  * T *= 1 - alpha.  Finally C += T bg.  n_contrib = 1-based list position of
  * the last blended entry, final_T = T.  bg: host float[3].
  * variant: execution shape only (results are identical): each warp owns a
- * BW x 32/BW pixel block of the tile, BW = 8 (0), 16 (1) or 4 (2). */
+ * BW x 32/BW pixel block of the tile, BW = 8 (0), 16 (1) or 4 (2).
+ * tile_order: NULL (natural order) or gs_bin_sort's heaviest-first order.
+ * block_masks: NULL, or gs_bin_sort's per-instance block masks (warps then
+ * skip records whose mask misses their pixels; results are unchanged). */
 int gs_render_fwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges,
                   int n_units, int width, int height, const float* bg, float* img,
-                  float* final_T, uint32_t* n_contrib, int variant, gs_stream_t stream);
+                  float* final_T, uint32_t* n_contrib, int variant, const uint32_t* tile_order,
+                  const uint16_t* block_masks, gs_stream_t stream);
 
 /* Diagnostic: *d_count = number of blended (pixel, record) pairs of the last
  * gs_render_fwd (records before n_contrib whose alpha reaches 1/255); the
@@ -236,13 +249,15 @@ int gs_render_bwd(const float* params, int64_t n_gauss, int sh_degree, const gs_
                   const gs_camera* cams, const gs_proj* proj, const uint32_t* sorted_vals,
                   const uint32_t* ranges, int width, int height, const float* bg,
                   const float* final_T, const uint32_t* n_contrib, const float* dL_dimg,
-                  const gs_grad2d* g2d, float* grads, int variant, gs_stream_t stream);
+                  const gs_grad2d* g2d, float* grads, int variant, const uint32_t* tile_order,
+                  const uint16_t* block_masks, gs_stream_t stream);
 
 /* Blend backward only: g2d ([n_proj] records) is zeroed, then accumulated. */
 int gs_blend_bwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges,
                  int n_units, int width, int height, const float* bg, const float* final_T,
                  const uint32_t* n_contrib, const float* dL_dimg, const gs_grad2d* g2d,
-                 int64_t n_proj, int variant, gs_stream_t stream);
+                 int64_t n_proj, int variant, const uint32_t* tile_order,
+                 const uint16_t* block_masks, gs_stream_t stream);
 
 /* Projection backward only (grads overwritten). */
 int gs_project_bwd(const float* params, int64_t n_gauss, int sh_degree, const gs_units* units,

@@ -75,6 +75,49 @@ __device__ __forceinline__ float splat_power(float A, float B, float C, float dx
   return __fmaf_rn(-0.5f, q, -r);
 }
 
+// Power below which alpha = o e^power < 1/255 for certain (with margin):
+// -(ln(255 o) + 1e-3) * 1.001 - 1e-3.  Lets the blend skip the exponential.
+__device__ __forceinline__ float power_floor(float o) {
+  float tau = logf(255.f * o) + 1e-3f;
+  return -tau * 1.001f - 1e-3f;
+}
+
+// Bounding box (xmin, xmax, ymin, ymax) of {d : o exp(-d^T Q d / 2) >= 1/255},
+// i.e. d^T Q d <= 2 ln(255 o), half-widths sqrt(2 ln(255 o) Sigma_xx) with
+// Sigma = Q^-1; inflated so float rounding can never cull a passing pixel.
+// An empty box (xmin > xmax) when o < 1/255.  Also returns power_floor(o).
+__device__ __forceinline__ float4 alpha_box(float2 m, float4 co, float& pmin) {
+  float tau = logf(255.f * co.w) + 1e-3f;  // >= ln(255 o) with margin
+  float det = co.x * co.z - co.y * co.y;
+  if (!(tau > 0.f) || !(det > 0.f)) {
+    pmin = 0.f;
+    return make_float4(1.f, -1.f, 1.f, -1.f);
+  }
+  float sxx = co.z / det, syy = co.x / det;
+  float ex = sqrtf(2.f * tau * sxx) * 1.001f + 0.01f;
+  float ey = sqrtf(2.f * tau * syy) * 1.001f + 0.01f;
+  pmin = -tau * 1.001f - 1e-3f;
+  return make_float4(m.x - ex, m.x + ex, m.y - ey, m.y + ey);
+}
+
+// 16-bit mask of the 4x4-pixel blocks (bit 4 by + bx) of tile (tx, ty) whose
+// pixel centres the box reaches.
+__device__ __forceinline__ uint32_t block_mask(float4 b, int tx, int ty) {
+  uint32_t m = 0;
+  if (!(b.x <= b.y)) return 0u;
+  #pragma unroll
+  for (int by = 0; by < 4; ++by) {
+    float y0 = (float)(ty * TILE + 4 * by), y1 = y0 + 3.f;
+    bool yo = !(b.w < y0 || b.z > y1);
+    #pragma unroll
+    for (int bx = 0; bx < 4; ++bx) {
+      float x0 = (float)(tx * TILE + 4 * bx), x1 = x0 + 3.f;
+      if (yo && !(b.y < x0 || b.x > x1)) m |= 1u << (4 * by + bx);
+    }
+  }
+  return m;
+}
+
 __device__ __forceinline__ void set_status(int* st, int bits) {
   if (st) atomicOr(st, bits);
 }

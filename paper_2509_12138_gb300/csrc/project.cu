@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const float4* __restrict__ p
         float op = 1.0f / (1.0f + expf(-sop.w));
         xy[p] = make_float2(px, py);
         conic_op[p] = make_float4(g.c * idet, -g.b * idet, g.a * idet, op);
-        rgb[p] = make_float4(col[0], col[1], col[2], 0.f);
+        rgb[p] = make_float4(col[0], col[1], col[2], power_floor(op));
         r_out = r;
         tiles_out = nt;
         if (!(isfinite(px) && isfinite(py) && isfinite(col[0] + col[1] + col[2]))) {

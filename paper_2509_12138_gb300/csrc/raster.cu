@@ -31,36 +31,33 @@ __device__ __forceinline__ void atomic_add4(float* p, float a, float b, float c,
 #endif
 }
 
-// Bounding box (xmin, xmax, ymin, ymax) of {d : o exp(-d^T Q d / 2) >= 1/255},
-// i.e. d^T Q d <= 2 ln(255 o), half-widths sqrt(2 ln(255 o) Sigma_xx) with
-// Sigma = Q^-1; inflated so float rounding can never cull a passing pixel.
-// An empty box (xmin > xmax) when o < 1/255.  Also returns the power below
-// which alpha < 1/255 for certain (used to skip the exponential).
-__device__ __forceinline__ float4 alpha_box(float2 m, float4 co, float& pmin) {
-  float tau = logf(255.f * co.w) + 1e-3f;  // >= ln(255 o) with margin
-  float det = co.x * co.z - co.y * co.y;
-  if (!(tau > 0.f) || !(det > 0.f)) {
-    pmin = 0.f;
-    return make_float4(1.f, -1.f, 1.f, -1.f);
-  }
-  float sxx = co.z / det, syy = co.x / det;
-  float ex = sqrtf(2.f * tau * sxx) * 1.001f + 0.01f;
-  float ey = sqrtf(2.f * tau * syy) * 1.001f + 0.01f;
-  pmin = -tau * 1.001f - 1e-3f;
-  return make_float4(m.x - ex, m.x + ex, m.y - ey, m.y + ey);
-}
-
 __device__ __forceinline__ bool box_misses(float4 b, float x0, float x1, float y0, float y1) {
   return b.y < x0 || b.x > x1 || b.w < y0 || b.z > y1;
 }
 
+// Per-warp staging of one round of 32 records in shared memory: lane k writes
+// record k, then every hit is read back as a broadcast.
+struct __align__(16) Rec {
+  float4 a;  // x, y, A, B
+  float4 b;  // C, opacity, power floor, record id (bits)
+  float4 c;  // r, g, b, unused
+};
+
+// Block index -> (unit, tile): heaviest tiles first when an order is given.
+__device__ __forceinline__ void block_tile(const uint32_t* __restrict__ order, int n_tiles, int& u, int& tile) {
+  uint32_t f = order ? order[blockIdx.x] : blockIdx.x;
+  u = (int)(f / (uint32_t)n_tiles);
+  tile = (int)(f % (uint32_t)n_tiles);
+}
+
 // Forward.  Each warp walks its tile's list on its own, 32 records per round
 // (one per lane): a lane loads a record and tests its alpha box against the
-// warp's 8x4 pixel block; the records that hit are taken in list order and
-// broadcast with shuffles.  The next round's loads are issued before the
+// warp's pixel block; the records that hit are taken in list order, read back
+// from the warp's staging area.  The next round's loads are issued before the
 // current round is blended.
 template <int BW>
 __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict__ ranges,
+                                                         const uint32_t* __restrict__ order,
                                                          const uint32_t* __restrict__ vals,
                                                          const float2* __restrict__ xy,
                                                          const float4* __restrict__ conic_op,
@@ -69,7 +66,9 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict
                                                          float* __restrict__ img, float* __restrict__ final_T,
                                                          uint32_t* __restrict__ n_contrib) {
   const unsigned FULL = 0xffffffffu;
-  int tile = blockIdx.x, u = blockIdx.y;
+  __shared__ Rec s_rec[TILE_PIX / 32][32];
+  int u, tile;
+  block_tile(order, n_tiles, u, tile);
   int tx = tile % TX, ty = tile / TX;
   constexpr int BH = 32 / BW, NWX = TILE / BW;
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -83,19 +82,18 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict
   int last = 0;
   bool done = !inside;
   float fx = (float)px, fy = (float)py;
-  // prefetch of the first round
+  Rec* my = &s_rec[w][0];
   uint32_t p_n = 0;
   float2 m_n = make_float2(0.f, 0.f);
-  float4 co_n = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (lane < n) { p_n = vals[rg.x + lane]; m_n = xy[p_n]; co_n = conic_op[p_n]; }
+  float4 co_n = make_float4(0.f, 0.f, 0.f, 0.f), c_n = co_n;
+  if (lane < n) { p_n = vals[rg.x + lane]; m_n = xy[p_n]; co_n = conic_op[p_n]; c_n = rgb[p_n]; }
   for (int base = 0; base < n; base += 32) {
     if (__all_sync(FULL, done)) break;
-    uint32_t p = p_n;
     float2 m = m_n;
-    float4 co = co_n;
+    float4 co = co_n, c = c_n;
     bool valid = base + lane < n;
     int kn = base + 32 + lane;
-    if (kn < n) { p_n = vals[rg.x + kn]; m_n = xy[p_n]; co_n = conic_op[p_n]; }
+    if (kn < n) { p_n = vals[rg.x + kn]; m_n = xy[p_n]; co_n = conic_op[p_n]; c_n = rgb[p_n]; }
     float pmin = 0.f;
     bool hit = false;
     if (valid) {
@@ -103,28 +101,30 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict
       hit = !box_misses(b, wx0, wx1, wy0, wy1);
     }
     unsigned mask = __ballot_sync(FULL, hit);
-    float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (hit) c = rgb[p];
+    if (hit) {
+      my[lane].a = make_float4(m.x, m.y, co.x, co.y);
+      my[lane].b = make_float4(co.z, co.w, pmin, 0.f);
+      my[lane].c = c;
+    }
+    __syncwarp();
     while (mask) {
       int j = __ffs(mask) - 1;
       mask &= mask - 1;
-      float ex = __shfl_sync(FULL, m.x, j), ey = __shfl_sync(FULL, m.y, j);
-      float A = __shfl_sync(FULL, co.x, j), B = __shfl_sync(FULL, co.y, j);
-      float Cc = __shfl_sync(FULL, co.z, j), op = __shfl_sync(FULL, co.w, j);
-      float pm = __shfl_sync(FULL, pmin, j);
-      float r = __shfl_sync(FULL, c.x, j), gg = __shfl_sync(FULL, c.y, j), bb = __shfl_sync(FULL, c.z, j);
       if (done) continue;
-      float power = splat_power(A, B, Cc, ex - fx, ey - fy);
-      if (power > 0.f || power < pm) continue;
-      float alpha = fminf(ALPHA_MAX, op * __expf(power));
+      float4 ra = my[j].a, rb = my[j].b;
+      float power = splat_power(ra.z, ra.w, rb.x, ra.x - fx, ra.y - fy);
+      if (power > 0.f || power < rb.z) continue;
+      float alpha = fminf(ALPHA_MAX, rb.y * __expf(power));
       if (alpha < ALPHA_MIN) continue;
       float tT = T * (1.f - alpha);
       if (tT < T_MIN) { done = true; continue; }
+      float4 rc = my[j].c;
       float wgt = alpha * T;
-      c0 += r * wgt; c1 += gg * wgt; c2 += bb * wgt;
+      c0 += rc.x * wgt; c1 += rc.y * wgt; c2 += rc.z * wgt;
       T = tT;
       last = base + j + 1;
     }
+    __syncwarp();
   }
   if (inside) {
     int64_t plane = (int64_t)W * H;
@@ -138,14 +138,41 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict
   }
 }
 
+// Sum of 8 values over the warp in 9 shuffles: each butterfly level halves the
+// set of values a lane carries; afterwards lane l holds the total of value
+// 4 bit4(l) + 2 bit3(l) + bit2(l).
+__device__ __forceinline__ float reduce8(const float* v, int lane) {
+  const unsigned FULL = 0xffffffffu;
+  float a[4], b[2];
+  bool h = lane & 16;
+  #pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float send = h ? v[i] : v[i + 4], keep = h ? v[i + 4] : v[i];
+    a[i] = keep + __shfl_xor_sync(FULL, send, 16);
+  }
+  h = lane & 8;
+  #pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    float send = h ? a[i] : a[i + 2], keep = h ? a[i + 2] : a[i];
+    b[i] = keep + __shfl_xor_sync(FULL, send, 8);
+  }
+  h = lane & 4;
+  float send = h ? b[0] : b[1], keep = h ? b[1] : b[0];
+  float c = keep + __shfl_xor_sync(FULL, send, 4);
+  c += __shfl_xor_sync(FULL, c, 2);
+  c += __shfl_xor_sync(FULL, c, 1);
+  return c;
+}
+
 // Backward.  Each warp replays its tile's list back to front from the largest
 // n_contrib among its pixels, in rounds of 32 records; hits are taken in
-// reverse list order.  The 9 gradient values of a record are summed over the
-// warp with xor shuffles (only if some lane contributed); the lane that loaded
-// the record keeps the sum and issues the global vector atomics at the end of
-// the round.
+// reverse list order.  The 9 gradient values of a record (d xy, d conic,
+// d opacity, d rgb) are summed over the warp (butterfly for 8, a plain xor
+// tree for the ninth) only if some lane contributed, and the lanes holding
+// the totals add them to the record's gradients with one atomic instruction.
 template <int BW>
 __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict__ ranges,
+                                                         const uint32_t* __restrict__ order,
                                                          const uint32_t* __restrict__ vals,
                                                          const float2* __restrict__ xy,
                                                          const float4* __restrict__ conic_op,
@@ -156,7 +183,9 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict
                                                          const float* __restrict__ dimg, float* __restrict__ dxy,
                                                          float* __restrict__ dco, float* __restrict__ drgb) {
   const unsigned FULL = 0xffffffffu;
-  int tile = blockIdx.x, u = blockIdx.y;
+  __shared__ Rec s_rec[TILE_PIX / 32][32];
+  int u, tile;
+  block_tile(order, n_tiles, u, tile);
   int tx = tile % TX, ty = tile / TX;
   constexpr int BH = 32 / BW, NWX = TILE / BW;
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -178,58 +207,56 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict
   int n = min(__reduce_max_sync(FULL, last), (int)(rg.y - rg.x));
   float S0 = bg0, S1 = bg1, S2 = bg2;  // colour behind the current entry
   float fx = (float)px, fy = (float)py;
+  Rec* my = &s_rec[w][0];
+  // lanes (l & 3) == 0 hold butterfly value q(l); value 8 (d blue) is held by all lanes
+  int q = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
   for (int top = n; top > 0; top -= 32) {
     int base = top - 32;
     int k = base + lane;
-    bool valid = k >= 0;
-    uint32_t p = 0;
-    float2 m = make_float2(0.f, 0.f);
-    float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
     bool hit = false;
-    if (valid) {
-      p = vals[rg.x + k];
-      m = xy[p];
-      co = conic_op[p];
+    if (k >= 0) {
+      uint32_t p = vals[rg.x + k];
+      float2 m = xy[p];
+      float4 co = conic_op[p];
       float pm;
       float4 b = alpha_box(m, co, pm);
       hit = !box_misses(b, wx0, wx1, wy0, wy1);
+      if (hit) {
+        my[lane].a = make_float4(m.x, m.y, co.x, co.y);
+        my[lane].b = make_float4(co.z, co.w, pm, __uint_as_float(p));
+        my[lane].c = rgb[p];
+      }
     }
     unsigned mask = __ballot_sync(FULL, hit);
-    float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (hit) c = rgb[p];
-    float acc[9];
-    #pragma unroll
-    for (int q = 0; q < 9; ++q) acc[q] = 0.f;
-    bool mine = false;  // this lane's record received a contribution
+    __syncwarp();
     while (mask) {
       int j = 31 - __clz(mask);
       mask &= ~(1u << j);
-      float ex = __shfl_sync(FULL, m.x, j), ey = __shfl_sync(FULL, m.y, j);
-      float A = __shfl_sync(FULL, co.x, j), B = __shfl_sync(FULL, co.y, j);
-      float Cc = __shfl_sync(FULL, co.z, j), op = __shfl_sync(FULL, co.w, j);
-      float cr = __shfl_sync(FULL, c.x, j), cg = __shfl_sync(FULL, c.y, j), cb = __shfl_sync(FULL, c.z, j);
       int pos = base + j;
       float v[9];
       #pragma unroll
-      for (int q = 0; q < 9; ++q) v[q] = 0.f;
+      for (int e = 0; e < 9; ++e) v[e] = 0.f;
       bool contrib = false;
+      float4 ra = my[j].a, rb = my[j].b;
       if (pos < last) {
-        float dx = ex - fx, dy = ey - fy;
+        float dx = ra.x - fx, dy = ra.y - fy;
+        float A = ra.z, B = ra.w, Cc = rb.x, op = rb.y;
         float power = splat_power(A, B, Cc, dx, dy);
-        if (power <= 0.f) {
+        if (power <= 0.f && power >= rb.z) {
           float G = __expf(power);
           float araw = op * G;
           bool clamped = araw > ALPHA_MAX;
           float alpha = clamped ? ALPHA_MAX : araw;
           if (alpha >= ALPHA_MIN) {
             contrib = true;
+            float4 rc = my[j].c;
             T = __fdividef(T, 1.f - alpha);  // transmittance in front of this entry
             float wgt = alpha * T;
             v[6] = wgt * g0; v[7] = wgt * g1; v[8] = wgt * g2;
-            float dalpha = T * ((cr - S0) * g0 + (cg - S1) * g1 + (cb - S2) * g2);
-            S0 = alpha * cr + (1.f - alpha) * S0;
-            S1 = alpha * cg + (1.f - alpha) * S1;
-            S2 = alpha * cb + (1.f - alpha) * S2;
+            float dalpha = T * ((rc.x - S0) * g0 + (rc.y - S1) * g1 + (rc.z - S2) * g2);
+            S0 = alpha * rc.x + (1.f - alpha) * S0;
+            S1 = alpha * rc.y + (1.f - alpha) * S1;
+            S2 = alpha * rc.z + (1.f - alpha) * S2;
             if (!clamped) {
               v[5] = G * dalpha;
               float dp = araw * dalpha;
@@ -243,25 +270,295 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict
         }
       }
       if (__ballot_sync(FULL, contrib)) {
+        float tot = reduce8(v, lane);
+        float e8 = v[8];
         #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-          float x = v[q];
-          x += __shfl_xor_sync(FULL, x, 16);
-          x += __shfl_xor_sync(FULL, x, 8);
-          x += __shfl_xor_sync(FULL, x, 4);
-          x += __shfl_xor_sync(FULL, x, 2);
-          x += __shfl_xor_sync(FULL, x, 1);
-          if (lane == j) acc[q] = x;
+        for (int o = 16; o > 0; o >>= 1) e8 += __shfl_xor_sync(FULL, e8, o);
+        int64_t pr = (int64_t)__float_as_uint(rb.w);
+        if ((lane & 3) == 0) {
+          float* dst = q < 2 ? dxy + 2 * pr + q : (q < 6 ? dco + 4 * pr + (q - 2) : drgb + 4 * pr + (q - 6));
+          atomicAdd(dst, tot);
+        } else if (lane == 1) {
+          atomicAdd(drgb + 4 * pr + 2, e8);
         }
-        if (lane == j) mine = true;
       }
     }
-    if (mine) {
-      atomic_add2(dxy + 2 * (int64_t)p, acc[0], acc[1]);
-      atomic_add4(dco + 4 * (int64_t)p, acc[2], acc[3], acc[4], acc[5]);
-      atomic_add4(drgb + 4 * (int64_t)p, acc[6], acc[7], acc[8], 0.f);
+    __syncwarp();
+  }
+}
+
+// Bits of the 4x4 pixel blocks that a warp's BW x (32/BW) pixel block overlaps.
+template <int BW>
+__device__ __forceinline__ uint32_t warp_block_bits(int w) {
+  constexpr int BH = 32 / BW, NWX = TILE / BW;
+  int ox = (w % NWX) * BW, oy = (w / NWX) * BH;
+  uint32_t bits = 0;
+  #pragma unroll
+  for (int by = 0; by < 4; ++by)
+    #pragma unroll
+    for (int bx = 0; bx < 4; ++bx)
+      if (4 * bx <= ox + BW - 1 && 4 * bx + 3 >= ox && 4 * by <= oy + BH - 1 && 4 * by + 3 >= oy)
+        bits |= 1u << (4 * by + bx);
+  return bits;
+}
+
+// Forward with per-instance block masks: a warp reads 2 bytes (mask) and 4
+// bytes (record id) per list entry, two rounds ahead, and gathers the records
+// of its hits one round ahead; the blend itself is that of k_render_fwd.
+template <int BW>
+__global__ void __launch_bounds__(TILE_PIX) k_render_fwd_m(const uint2* __restrict__ ranges,
+                                                           const uint32_t* __restrict__ order,
+                                                           const uint32_t* __restrict__ vals,
+                                                           const uint16_t* __restrict__ masks,
+                                                           const float2* __restrict__ xy,
+                                                           const float4* __restrict__ conic_op,
+                                                           const float4* __restrict__ rgb, int W, int H, int TX,
+                                                           int n_tiles, float bg0, float bg1, float bg2,
+                                                           float* __restrict__ img, float* __restrict__ final_T,
+                                                           uint32_t* __restrict__ n_contrib) {
+  const unsigned FULL = 0xffffffffu;
+  __shared__ Rec s_rec[TILE_PIX / 32][32];
+  int u, tile;
+  block_tile(order, n_tiles, u, tile);
+  int tx = tile % TX, ty = tile / TX;
+  constexpr int BH = 32 / BW, NWX = TILE / BW;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int px = tx * TILE + (w % NWX) * BW + (lane % BW), py = ty * TILE + (w / NWX) * BH + (lane / BW);
+  uint32_t wbits = warp_block_bits<BW>(w);
+  bool inside = px < W && py < H;
+  uint2 rg = ranges[(int64_t)u * n_tiles + tile];
+  int n = (int)(rg.y - rg.x);
+  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+  int last = 0;
+  bool done = !inside;
+  float fx = (float)px, fy = (float)py;
+  Rec* my = &s_rec[w][0];
+  // round r's record (hit lanes), round r+1's header
+  bool h1 = false;
+  float2 m1 = make_float2(0.f, 0.f);
+  float4 co1 = make_float4(0.f, 0.f, 0.f, 0.f), cc1 = co1;
+  uint32_t mk2 = 0, pk2 = 0;
+  if (lane < n) {
+    uint32_t mk = masks[rg.x + lane];
+    if (mk & wbits) {
+      uint32_t pk = vals[rg.x + lane];
+      h1 = true; m1 = xy[pk]; co1 = conic_op[pk]; cc1 = rgb[pk];
     }
   }
+  if (32 + lane < n) { mk2 = masks[rg.x + 32 + lane]; pk2 = vals[rg.x + 32 + lane]; }
+  for (int base = 0; base < n; base += 32) {
+    if (__all_sync(FULL, done)) break;
+    bool hit = h1;
+    float2 m = m1;
+    float4 co = co1, c = cc1;
+    h1 = (mk2 & wbits) != 0;
+    if (h1) { m1 = xy[pk2]; co1 = conic_op[pk2]; cc1 = rgb[pk2]; }
+    int k2 = base + 64 + lane;
+    mk2 = 0;
+    if (k2 < n) { mk2 = masks[rg.x + k2]; pk2 = vals[rg.x + k2]; }
+    unsigned mask = __ballot_sync(FULL, hit);
+    if (hit) {
+      my[lane].a = make_float4(m.x, m.y, co.x, co.y);
+      my[lane].b = make_float4(co.z, co.w, c.w, 0.f);
+      my[lane].c = c;
+    }
+    __syncwarp();
+    while (mask) {
+      int j = __ffs(mask) - 1;
+      mask &= mask - 1;
+      if (done) continue;
+      float4 ra = my[j].a, rb = my[j].b;
+      float power = splat_power(ra.z, ra.w, rb.x, ra.x - fx, ra.y - fy);
+      if (power > 0.f || power < rb.z) continue;
+      float alpha = fminf(ALPHA_MAX, rb.y * __expf(power));
+      if (alpha < ALPHA_MIN) continue;
+      float tT = T * (1.f - alpha);
+      if (tT < T_MIN) { done = true; continue; }
+      float4 rc = my[j].c;
+      float wgt = alpha * T;
+      c0 += rc.x * wgt; c1 += rc.y * wgt; c2 += rc.z * wgt;
+      T = tT;
+      last = base + j + 1;
+    }
+    __syncwarp();
+  }
+  if (inside) {
+    int64_t plane = (int64_t)W * H;
+    int64_t pix = (int64_t)py * W + px;
+    float* im = img + (int64_t)u * 3 * plane;
+    im[pix] = c0 + T * bg0;
+    im[plane + pix] = c1 + T * bg1;
+    im[2 * plane + pix] = c2 + T * bg2;
+    final_T[(int64_t)u * plane + pix] = T;
+    n_contrib[(int64_t)u * plane + pix] = (uint32_t)last;
+  }
+}
+
+// Backward with per-instance block masks (the replay of k_render_bwd; headers
+// two rounds ahead, hit records one round ahead, rounds in reverse order).
+template <int BW>
+__global__ void __launch_bounds__(TILE_PIX) k_render_bwd_m(const uint2* __restrict__ ranges,
+                                                           const uint32_t* __restrict__ order,
+                                                           const uint32_t* __restrict__ vals,
+                                                           const uint16_t* __restrict__ masks,
+                                                           const float2* __restrict__ xy,
+                                                           const float4* __restrict__ conic_op,
+                                                           const float4* __restrict__ rgb, int W, int H, int TX,
+                                                           int n_tiles, float bg0, float bg1, float bg2,
+                                                           const float* __restrict__ final_T,
+                                                           const uint32_t* __restrict__ n_contrib,
+                                                           const float* __restrict__ dimg, float* __restrict__ dxy,
+                                                           float* __restrict__ dco, float* __restrict__ drgb) {
+  const unsigned FULL = 0xffffffffu;
+  __shared__ Rec s_rec[TILE_PIX / 32][32];
+  int u, tile;
+  block_tile(order, n_tiles, u, tile);
+  int tx = tile % TX, ty = tile / TX;
+  constexpr int BH = 32 / BW, NWX = TILE / BW;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int px = tx * TILE + (w % NWX) * BW + (lane % BW), py = ty * TILE + (w / NWX) * BH + (lane / BW);
+  uint32_t wbits = warp_block_bits<BW>(w);
+  bool inside = px < W && py < H;
+  uint2 rg = ranges[(int64_t)u * n_tiles + tile];
+  int64_t plane = (int64_t)W * H;
+  int64_t pix = (int64_t)py * W + px;
+  float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+  int last = 0;
+  if (inside) {
+    T = final_T[(int64_t)u * plane + pix];
+    last = (int)n_contrib[(int64_t)u * plane + pix];
+    const float* d = dimg + (int64_t)u * 3 * plane;
+    g0 = d[pix]; g1 = d[plane + pix]; g2 = d[2 * plane + pix];
+  }
+  int n = min(__reduce_max_sync(FULL, last), (int)(rg.y - rg.x));
+  float S0 = bg0, S1 = bg1, S2 = bg2;
+  float fx = (float)px, fy = (float)py;
+  Rec* my = &s_rec[w][0];
+  int q = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+  // rounds cover [top - 32, top); round r's record (hit lanes) and round r+1's header
+  bool h1 = false;
+  uint32_t p1 = 0;
+  float2 m1 = make_float2(0.f, 0.f);
+  float4 co1 = make_float4(0.f, 0.f, 0.f, 0.f), cc1 = co1;
+  uint32_t mk2 = 0, pk2 = 0;
+  {
+    int k = n - 32 + lane;
+    if (n > 0 && k >= 0) {
+      uint32_t mk = masks[rg.x + k];
+      if (mk & wbits) {
+        p1 = vals[rg.x + k];
+        h1 = true; m1 = xy[p1]; co1 = conic_op[p1]; cc1 = rgb[p1];
+      }
+    }
+    int k2 = n - 64 + lane;
+    if (n > 32 && k2 >= 0) { mk2 = masks[rg.x + k2]; pk2 = vals[rg.x + k2]; }
+  }
+  for (int top = n; top > 0; top -= 32) {
+    int base = top - 32;
+    bool hit = h1;
+    uint32_t p = p1;
+    float2 m = m1;
+    float4 co = co1, c = cc1;
+    h1 = (mk2 & wbits) != 0;
+    if (h1) { p1 = pk2; m1 = xy[pk2]; co1 = conic_op[pk2]; cc1 = rgb[pk2]; }
+    int k2 = top - 96 + lane;
+    mk2 = 0;
+    if (top > 64 && k2 >= 0) { mk2 = masks[rg.x + k2]; pk2 = vals[rg.x + k2]; }
+    unsigned mask = __ballot_sync(FULL, hit);
+    if (hit) {
+      my[lane].a = make_float4(m.x, m.y, co.x, co.y);
+      my[lane].b = make_float4(co.z, co.w, c.w, __uint_as_float(p));
+      my[lane].c = c;
+    }
+    __syncwarp();
+    while (mask) {
+      int j = 31 - __clz(mask);
+      mask &= ~(1u << j);
+      int pos = base + j;
+      float v[9];
+      #pragma unroll
+      for (int e = 0; e < 9; ++e) v[e] = 0.f;
+      bool contrib = false;
+      float4 ra = my[j].a, rb = my[j].b;
+      if (pos < last) {
+        float dx = ra.x - fx, dy = ra.y - fy;
+        float A = ra.z, B = ra.w, Cc = rb.x, op = rb.y;
+        float power = splat_power(A, B, Cc, dx, dy);
+        if (power <= 0.f && power >= rb.z) {
+          float G = __expf(power);
+          float araw = op * G;
+          bool clamped = araw > ALPHA_MAX;
+          float alpha = clamped ? ALPHA_MAX : araw;
+          if (alpha >= ALPHA_MIN) {
+            contrib = true;
+            float4 rc = my[j].c;
+            T = __fdividef(T, 1.f - alpha);
+            float wgt = alpha * T;
+            v[6] = wgt * g0; v[7] = wgt * g1; v[8] = wgt * g2;
+            float dalpha = T * ((rc.x - S0) * g0 + (rc.y - S1) * g1 + (rc.z - S2) * g2);
+            S0 = alpha * rc.x + (1.f - alpha) * S0;
+            S1 = alpha * rc.y + (1.f - alpha) * S1;
+            S2 = alpha * rc.z + (1.f - alpha) * S2;
+            if (!clamped) {
+              v[5] = G * dalpha;
+              float dp = araw * dalpha;
+              v[2] = -0.5f * dx * dx * dp;
+              v[3] = -dx * dy * dp;
+              v[4] = -0.5f * dy * dy * dp;
+              v[0] = -(A * dx + B * dy) * dp;
+              v[1] = -(Cc * dy + B * dx) * dp;
+            }
+          }
+        }
+      }
+      if (__ballot_sync(FULL, contrib)) {
+        float tot = reduce8(v, lane);
+        float e8 = v[8];
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e8 += __shfl_xor_sync(FULL, e8, o);
+        int64_t pr = (int64_t)__float_as_uint(rb.w);
+        if ((lane & 3) == 0) {
+          float* dst = q < 2 ? dxy + 2 * pr + q : (q < 6 ? dco + 4 * pr + (q - 2) : drgb + 4 * pr + (q - 6));
+          atomicAdd(dst, tot);
+        } else if (lane == 1) {
+          atomicAdd(drgb + 4 * pr + 2, e8);
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Tile order: heaviest lists first (counting sort of (unit, tile) by the
+// bit length of the list length; order within a class is arbitrary and the
+// blend results do not depend on it).
+__global__ void k_order_hist(const uint2* __restrict__ ranges, int n, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t s[33];
+  if (threadIdx.x < 33) s[threadIdx.x] = 0;
+  __syncthreads();
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    uint2 r = ranges[i];
+    uint32_t len = r.y - r.x;
+    atomicAdd(&s[32 - __clz(len)], 1u);  // class 0: empty; class c: 2^(c-1) <= len < 2^c
+  }
+  __syncthreads();
+  if (threadIdx.x < 33 && s[threadIdx.x]) atomicAdd(&hist[threadIdx.x], s[threadIdx.x]);
+}
+
+__global__ void k_order_scatter(const uint2* __restrict__ ranges, int n, const uint32_t* __restrict__ hist,
+                                uint32_t* __restrict__ cursor, uint32_t* __restrict__ order) {
+  __shared__ uint32_t s_base[33];
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int c = 32; c >= 0; --c) { s_base[c] = acc; acc += hist[c]; }  // heavy classes first
+  }
+  __syncthreads();
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint2 r = ranges[i];
+  int c = 32 - __clz(r.y - r.x);
+  order[s_base[c] + atomicAdd(&cursor[c], 1u)] = (uint32_t)i;
 }
 
 // Number of blended (pixel, record) pairs: records before n_contrib whose
@@ -298,32 +595,39 @@ __global__ void __launch_bounds__(TILE_PIX) k_blend_pairs(const uint2* __restric
 
 int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
                        int width, int height, const float* bg, float* img, float* final_T, uint32_t* n_contrib,
-                       int variant, cudaStream_t s) {
+                       int variant, const uint32_t* tile_order, const uint16_t* block_masks, cudaStream_t s) {
   if (!proj || !proj->xy || !proj->conic_op || !proj->rgb || !sorted_vals || !ranges || !bg || !img ||
       !final_T || !n_contrib || n_units < 1 || n_units > GS_MAX_UNITS || width <= 0 || height <= 0 ||
       variant < 0 || variant > 2)
     return GS_ERR_INVALID;
   int TX = (width + TILE - 1) / TILE, TY = (height + TILE - 1) / TILE;
-  dim3 grid(TX * TY, n_units);
-#define GS_FWD(BW)                                                                                                \
-  k_render_fwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, sorted_vals, (const float2*)proj->xy,          \
-                                             (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, \
-                                             TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib)
-  if (variant == 0) GS_FWD(8); else if (variant == 1) GS_FWD(16); else GS_FWD(4);
+  dim3 grid(TX * TY * n_units);
+#define GS_FWD(BW)                                                                                                  \
+  if (block_masks)                                                                                                  \
+    k_render_fwd_m<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, tile_order, sorted_vals, block_masks,       \
+                                                 (const float2*)proj->xy, (const float4*)proj->conic_op,           \
+                                                 (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0],      \
+                                                 bg[1], bg[2], img, final_T, n_contrib);                           \
+  else                                                                                                              \
+    k_render_fwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, tile_order, sorted_vals, (const float2*)proj->xy, \
+                                               (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, \
+                                               TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib)
+  if (variant == 0) { GS_FWD(8); } else if (variant == 1) { GS_FWD(16); } else { GS_FWD(4); }
 #undef GS_FWD
   return gs_check_launch();
 }
 
 GS_API int gs_render_fwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
                          int width, int height, const float* bg, float* img, float* final_T, uint32_t* n_contrib,
-                         int variant, gs_stream_t stream) {
+                         int variant, const uint32_t* tile_order, const uint16_t* block_masks, gs_stream_t stream) {
   return gs_render_fwd_impl(proj, sorted_vals, ranges, n_units, width, height, bg, img, final_T, n_contrib, variant,
-                            (cudaStream_t)stream);
+                            tile_order, block_masks, (cudaStream_t)stream);
 }
 
 int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
                       int width, int height, const float* bg, const float* final_T, const uint32_t* n_contrib,
-                      const float* dL_dimg, const gs_grad2d* g2d, int64_t n_proj, int variant, cudaStream_t s) {
+                      const float* dL_dimg, const gs_grad2d* g2d, int64_t n_proj, int variant,
+                      const uint32_t* tile_order, const uint16_t* block_masks, cudaStream_t s) {
   if (!proj || !proj->xy || !proj->conic_op || !proj->rgb || !sorted_vals || !ranges || !bg || !final_T ||
       !n_contrib || !dL_dimg || !g2d || !g2d->dxy || !g2d->dconic_op || !g2d->drgb || n_units < 1 ||
       n_units > GS_MAX_UNITS || width <= 0 || height <= 0 || n_proj < 0 || variant < 0 || variant > 2)
@@ -333,13 +637,20 @@ int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const ui
       cudaMemsetAsync(g2d->drgb, 0, sizeof(float) * 4 * (size_t)n_proj, s) != cudaSuccess)
     return GS_ERR_CUDA;
   int TX = (width + TILE - 1) / TILE, TY = (height + TILE - 1) / TILE;
-  dim3 grid(TX * TY, n_units);
+  dim3 grid(TX * TY * n_units);
 #define GS_BWD(BW)                                                                                                   \
-  k_render_bwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, sorted_vals, (const float2*)proj->xy,             \
-                                             (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height,    \
-                                             TX, TX * TY, bg[0], bg[1], bg[2], final_T, n_contrib, dL_dimg, g2d->dxy, \
-                                             g2d->dconic_op, g2d->drgb)
-  if (variant == 0) GS_BWD(8); else if (variant == 1) GS_BWD(16); else GS_BWD(4);
+  if (block_masks)                                                                                                   \
+    k_render_bwd_m<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, tile_order, sorted_vals, block_masks,        \
+                                                 (const float2*)proj->xy, (const float4*)proj->conic_op,            \
+                                                 (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], \
+                                                 bg[2], final_T, n_contrib, dL_dimg, g2d->dxy, g2d->dconic_op,      \
+                                                 g2d->drgb);                                                         \
+  else                                                                                                               \
+    k_render_bwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, tile_order, sorted_vals, (const float2*)proj->xy, \
+                                               (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height,  \
+                                               TX, TX * TY, bg[0], bg[1], bg[2], final_T, n_contrib, dL_dimg, g2d->dxy, \
+                                               g2d->dconic_op, g2d->drgb)
+  if (variant == 0) { GS_BWD(8); } else if (variant == 1) { GS_BWD(16); } else { GS_BWD(4); }
 #undef GS_BWD
   return gs_check_launch();
 }
@@ -356,5 +667,15 @@ GS_API int gs_blend_pairs(const gs_proj* proj, const uint32_t* sorted_vals, cons
   k_blend_pairs<<<dim3(TX * TY, n_units), TILE_PIX, 0, s>>>((const uint2*)ranges, sorted_vals, (const float2*)proj->xy,
                                                             (const float4*)proj->conic_op, width, height, TX, TX * TY,
                                                             n_contrib, d_count);
+  return gs_check_launch();
+}
+
+// Heaviest-first order of the (unit, tile) blocks from the tile ranges.
+// ws: 2 x 33 uint32 of scratch.
+int gs_tile_order_impl(const uint32_t* ranges, int n, uint32_t* ws, uint32_t* order, cudaStream_t s) {
+  if (cudaMemsetAsync(ws, 0, sizeof(uint32_t) * 66, s) != cudaSuccess) return GS_ERR_CUDA;
+  unsigned nb = (unsigned)((n + 255) / 256);
+  k_order_hist<<<nb, 256, 0, s>>>((const uint2*)ranges, n, ws);
+  k_order_scatter<<<nb, 256, 0, s>>>((const uint2*)ranges, n, ws, ws + 33, order);
   return gs_check_launch();
 }

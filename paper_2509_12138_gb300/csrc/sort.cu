@@ -34,7 +34,7 @@ constexpr int MAX_PASSES = 8;
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsLayout {
-  size_t offsets, bsums, keys0, keys1, vals0, vals1, hist, totals, cur, total;
+  size_t offsets, bsums, keys0, keys1, vals0, vals1, hist, totals, cur, order, total;
 };
 
 WsLayout ws_layout(int64_t P, int64_t C) {
@@ -51,6 +51,7 @@ WsLayout ws_layout(int64_t P, int64_t C) {
   L.hist = o; o += align256(sizeof(uint32_t) * RS_BINS * (size_t)(nrb > 0 ? nrb : 1));
   L.totals = o; o += align256(sizeof(uint32_t) * RS_BINS * MAX_PASSES);
   L.cur = o; o += align256(sizeof(int32_t) * (MAX_PASSES + 1));
+  L.order = o; o += align256(sizeof(uint32_t) * 66);
   L.total = o;
   return L;
 }
@@ -323,8 +324,9 @@ __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ k0,
                                                 const uint32_t* __restrict__ v0, const uint32_t* __restrict__ v1,
                                                 const int32_t* __restrict__ cur, int final_pass,
                                                 const uint32_t* __restrict__ d_count, int tile_bits,
-                                                int n_tiles, uint32_t* __restrict__ ranges,
-                                                uint32_t* __restrict__ out_vals) {
+                                                int n_tiles, int TX, uint32_t* __restrict__ ranges,
+                                                uint32_t* __restrict__ out_vals, const float2* __restrict__ xy,
+                                                const float4* __restrict__ conic_op, uint16_t* __restrict__ masks) {
   int64_t I = *d_count;
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= I) return;
@@ -332,11 +334,19 @@ __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ k0,
   const uint64_t* keys = c ? k1 : k0;
   const uint32_t* vals = c ? v1 : v0;
   uint32_t ut = (uint32_t)(keys[k] >> 32);
-  out_vals[k] = vals[k];
+  uint32_t p = vals[k];
+  out_vals[k] = p;
   uint32_t mask = (1u << tile_bits) - 1u;
-  int64_t flat = (int64_t)(ut >> tile_bits) * n_tiles + (ut & mask);
+  uint32_t tile = ut & mask;
+  int64_t flat = (int64_t)(ut >> tile_bits) * n_tiles + tile;
   if (k == 0 || (uint32_t)(keys[k - 1] >> 32) != ut) ranges[2 * flat] = (uint32_t)k;
   if (k == I - 1 || (uint32_t)(keys[k + 1] >> 32) != ut) ranges[2 * flat + 1] = (uint32_t)(k + 1);
+  if (masks) {
+    // which 4x4 pixel blocks of its tile the record's alpha >= 1/255 box reaches
+    float pm;
+    float4 b = alpha_box(xy[p], conic_op[p], pm);
+    masks[k] = (uint16_t)block_mask(b, (int)(tile % (uint32_t)TX), (int)(tile / (uint32_t)TX));
+  }
 }
 
 int bits_for(int64_t n) {
@@ -367,12 +377,16 @@ GS_API size_t gs_bin_sort_workspace_size(int64_t n_proj, int64_t max_instances) 
 }
 
 // The sort chain, shared by gs_bin_sort and the fixed-scratch variant.
+int gs_tile_order_impl(const uint32_t* ranges, int n, uint32_t* ws, uint32_t* order, cudaStream_t s);
+
 int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int height, int64_t max_instances,
                      void* workspace, size_t workspace_bytes, uint32_t* sorted_vals, uint32_t* ranges,
-                     uint32_t* d_num_instances, int* d_status, cudaStream_t s) {
+                     uint32_t* d_num_instances, uint32_t* tile_order, uint16_t* block_masks, int* d_status,
+                     cudaStream_t s) {
   UnitTable U;
   int64_t P = 0;
   if (!proj || !proj->xy || !proj->depth || !proj->radius || !proj->tiles || width <= 0 || height <= 0 ||
+      (block_masks && !proj->conic_op) ||
       !workspace || !sorted_vals || !ranges || !d_num_instances || max_instances < 0 ||
       max_instances >= (int64_t)UINT32_MAX)
     return GS_ERR_INVALID;
@@ -403,7 +417,10 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
       cudaMemsetAsync(cur, 0, sizeof(int32_t) * (MAX_PASSES + 1), s) != cudaSuccess ||
       cudaMemsetAsync(d_num_instances, 0, sizeof(uint32_t), s) != cudaSuccess)
     return GS_ERR_CUDA;
-  if (P == 0) return gs_check_launch();
+  if (P == 0) {
+    if (tile_order) return gs_tile_order_impl(ranges, n_tiles * U.n, (uint32_t*)(ws + L.order), tile_order, s);
+    return gs_check_launch();
+  }
   int64_t nsb = (P + SCAN_BLOCK - 1) / SCAN_BLOCK;
   k_scan_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, P, bsums);
   k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);
@@ -420,22 +437,25 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
       k_radix_scan<<<RS_BINS, 1024, 0, s>>>(hist, stride, totals, pass, d_num_instances, cur);
       k_radix_scatter<<<nrb, RS_T, 0, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift, hist, stride);
     }
-    k_ranges<<<(unsigned)((max_instances + 255) / 256), 256, 0, s>>>(k0, k1, v0, v1, cur, passes, d_num_instances,
-                                                                     tile_bits, n_tiles, ranges, sorted_vals);
+    k_ranges<<<(unsigned)((max_instances + 255) / 256), 256, 0, s>>>(
+        k0, k1, v0, v1, cur, passes, d_num_instances, tile_bits, n_tiles, TX, ranges, sorted_vals,
+        (const float2*)proj->xy, (const float4*)proj->conic_op, block_masks);
   }
+  if (tile_order) return gs_tile_order_impl(ranges, n_tiles * U.n, (uint32_t*)(ws + L.order), tile_order, s);
   return gs_check_launch();
 }
 
 GS_API int gs_bin_sort(const gs_proj* proj, const gs_units* units, int width, int height, int64_t max_instances,
                        void* workspace, size_t workspace_bytes, uint32_t* sorted_vals, uint32_t* ranges,
-                       uint32_t* d_num_instances, int* d_status, gs_stream_t stream) {
+                       uint32_t* d_num_instances, uint32_t* tile_order, uint16_t* block_masks, int* d_status,
+                       gs_stream_t stream) {
   return gs_bin_sort_impl(proj, units, width, height, max_instances, workspace, workspace_bytes, sorted_vals,
-                          ranges, d_num_instances, d_status, (cudaStream_t)stream);
+                          ranges, d_num_instances, tile_order, block_masks, d_status, (cudaStream_t)stream);
 }
 
 int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
                        int width, int height, const float* bg, float* img, float* final_T, uint32_t* n_contrib,
-                       int variant, cudaStream_t s);
+                       int variant, const uint32_t* tile_order, const uint16_t* block_masks, cudaStream_t s);
 
 GS_API int gs_merge_render(const float* params, int64_t n_gauss, int sh_degree, const gs_owned* owned,
                            const gs_camera* cam, int width, int height, const float* bg, const gs_proj* proj,
@@ -448,8 +468,8 @@ GS_API int gs_merge_render(const float* params, int64_t n_gauss, int sh_degree, 
   int r = gs_preprocess(params, n_gauss, sh_degree, &one, cam, width, height, owned, proj, d_status, stream);
   if (r != GS_OK) return r;
   r = gs_bin_sort_impl(proj, &one, width, height, max_instances, workspace, workspace_bytes, sorted_vals, ranges,
-                       d_num_instances, d_status, (cudaStream_t)stream);
+                       d_num_instances, nullptr, nullptr, d_status, (cudaStream_t)stream);
   if (r != GS_OK) return r;
-  return gs_render_fwd_impl(proj, sorted_vals, ranges, 1, width, height, bg, img, final_T, n_contrib, 0,
-                            (cudaStream_t)stream);
+  return gs_render_fwd_impl(proj, sorted_vals, ranges, 1, width, height, bg, img, final_T, n_contrib, 0, nullptr,
+                            nullptr, (cudaStream_t)stream);
 }

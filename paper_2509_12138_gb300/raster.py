@@ -141,6 +141,7 @@ class Frame:
                  variant: int = 0):
         self.L = _lib.load()
         self.variant = int(variant)
+        self.use_masks = True  # per-instance block masks from the sort drive the blend kernels' culling
         self.device = torch.device(device)
         self.N = int(n_gauss)
         self.units = units
@@ -164,6 +165,7 @@ class Frame:
         self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
         self.set_capacity(max_instances if max_instances is not None else max(4 * P, 1024))
         self.ranges = torch.zeros((U * self.n_tiles, 2), dtype=torch.int32, device=self.device)
+        self.tile_order = torch.zeros(U * self.n_tiles, dtype=torch.int32, device=self.device)
         self.img = torch.zeros((U, 3, self.H, self.W), **f32)
         self.final_T = torch.zeros((U, self.H, self.W), **f32)
         self.n_contrib = torch.zeros((U, self.H, self.W), dtype=torch.int32, device=self.device)
@@ -178,11 +180,15 @@ class Frame:
             self.g2d = GsGrad2d(self.dxy.data_ptr(), self.dco.data_ptr(), self.drgb.data_ptr())
             self.grads = torch.zeros((self.planes, max(self.N, 1), 4), **f32)
 
+    def _masks(self):
+        return _ptr(self.block_masks) if self.use_masks else None
+
     def set_capacity(self, max_instances: int):
         self.cap = int(max_instances)
         ws = self.L.gs_bin_sort_workspace_size(self.P, self.cap)
         self.sort_ws = _alloc_ws(ws, self.device)
         self.sorted_vals = torch.zeros(max(self.cap, 1), dtype=torch.int32, device=self.device)
+        self.block_masks = torch.zeros(max(self.cap, 1), dtype=torch.int16, device=self.device)
         self.num_instances = torch.zeros(1, dtype=torch.int32, device=self.device)
 
     # -- steps
@@ -195,13 +201,14 @@ class Frame:
     def sort(self):
         check(self.L.gs_bin_sort(C.byref(self.proj), C.byref(self.units.struct), self.W, self.H, self.cap,
                                  _ptr(self.sort_ws), self.sort_ws.numel(), _ptr(self.sorted_vals), _ptr(self.ranges),
-                                 _ptr(self.num_instances), _ptr(self.status), _stream()), "gs_bin_sort")
+                                 _ptr(self.num_instances), _ptr(self.tile_order), self._masks(), _ptr(self.status),
+                                 _stream()), "gs_bin_sort")
 
     def render(self, bg):
         bgc = (C.c_float * 3)(*[float(x) for x in bg])
         check(self.L.gs_render_fwd(C.byref(self.proj), _ptr(self.sorted_vals), _ptr(self.ranges), self.units.n,
                                    self.W, self.H, bgc, _ptr(self.img), _ptr(self.final_T), _ptr(self.n_contrib),
-                                   self.variant, _stream()), "gs_render_fwd")
+                                   self.variant, _ptr(self.tile_order), self._masks(), _stream()), "gs_render_fwd")
         return self.img
 
     def forward(self, params, cams_dev, bg, owned=None):
@@ -232,7 +239,8 @@ class Frame:
         d = self.dimg if dimg is None else dimg
         check(self.L.gs_blend_bwd(C.byref(self.proj), _ptr(self.sorted_vals), _ptr(self.ranges), self.units.n,
                                   self.W, self.H, bgc, _ptr(self.final_T), _ptr(self.n_contrib), _ptr(d),
-                                  C.byref(self.g2d), self.P, self.variant, _stream()), "gs_blend_bwd")
+                                  C.byref(self.g2d), self.P, self.variant, _ptr(self.tile_order), self._masks(),
+                                  _stream()), "gs_blend_bwd")
 
     def project_backward(self, params, cams_dev):
         check(self.L.gs_project_bwd(_ptr(params), self.N, self.deg, C.byref(self.units.struct), _ptr(cams_dev),
@@ -246,7 +254,8 @@ class Frame:
         check(self.L.gs_render_bwd(_ptr(params), self.N, self.deg, C.byref(self.units.struct), _ptr(cams_dev),
                                    C.byref(self.proj), _ptr(self.sorted_vals), _ptr(self.ranges), self.W, self.H,
                                    bgc, _ptr(self.final_T), _ptr(self.n_contrib), _ptr(d), C.byref(self.g2d),
-                                   _ptr(self.grads), self.variant, _stream()), "gs_render_bwd")
+                                   _ptr(self.grads), self.variant, _ptr(self.tile_order), self._masks(), _stream()),
+              "gs_render_bwd")
         return self.grads
 
     def merge_render(self, params, cam_dev, bg, owned: Owned):

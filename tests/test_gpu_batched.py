@@ -119,7 +119,6 @@ def test_graph_replay_matches_eager():
                                     torch.from_numpy(gt).cuda(), torch.from_numpy(mask).cuda(), list(range(6)),
                                     views_per_step=1, use_graph=g)
     tg, te = mk(True), mk(False)
-    tg.keep_grads = te.keep_grads = True
     tg.step()  # eager first step + capture
     te.step()
     for a, b in ((te.params, tg.params), (te.opt.m, tg.opt.m), (te.opt.v, tg.opt.v), (te.opt.step_dev, tg.opt.step_dev)):
@@ -228,3 +227,30 @@ def test_fused_projection_backward_adam_matches_separate():
     assert torch.allclose(ga, gb, rtol=1e-4, atol=1e-6 * sc)
     assert torch.allclose(ma, mb, rtol=1e-4, atol=1e-7 * sc)
     assert torch.allclose(pa, pb, rtol=1e-5, atol=1e-5)
+
+
+def test_block_masks_and_tile_order_do_not_change_results():
+    """Per-instance block masks and the heaviest-first tile order only skip work / reorder blocks: images,
+    n_contrib are bit-identical and gradients equal up to atomic order, with and without them."""
+    n, deg, W, H = 3000, 1, 150, 110
+    g, cams = scenes.random_scene(n, deg, 31, W, H)
+    params = gs.pack_params(g, deg)
+    camd = gs.pack_cameras(cams)
+    gt, mask = scenes.random_gt(W, H, 32)
+    res = []
+    for use_masks, order in ((False, False), (True, True), (True, False)):
+        fr = gs.Frame(n, gs.Units.single(n), W, H, deg)
+        fr.use_masks = use_masks
+        fr.fit_capacity(params, camd)
+        fr.preprocess(params, camd)
+        fr.sort()
+        if not order:
+            fr.tile_order.copy_(torch.arange(fr.tile_order.numel(), dtype=torch.int32, device="cuda"))
+        fr.render(BG)
+        fr.loss(torch.from_numpy(gt).cuda()[None], torch.from_numpy(mask).cuda()[None], 0.2)
+        fr.backward(params, camd, BG)
+        torch.cuda.synchronize()
+        res.append((fr.img.clone(), fr.n_contrib.clone(), fr.grads.clone()))
+    for r in res[1:]:
+        assert torch.equal(res[0][0], r[0]) and torch.equal(res[0][1], r[1])
+        assert torch.allclose(res[0][2], r[2], rtol=1e-4, atol=1e-7)
