@@ -197,7 +197,7 @@ def kernel_launch_count(frame, lam):
     sort = 4 + 3 * passes + 1
     fwd = 1
     loss = 1 + (2 if lam > 0 else 1) + 1
-    bwd = 2
+    bwd = 1
     adam = 2
     return pre + sort + fwd + loss + bwd + adam
 
@@ -231,12 +231,10 @@ def run_ours(args, wl, rank, world):
         if ev: ev[4].record()
         frame.blend_backward(bg)
         if ev: ev[5].record()
-        frame.project_backward(params, cam)
+        opt.fused_step(frame, cam)
         if ev: ev[6].record()
-        opt.step(frame.grads)
-        if ev: ev[7].record()
 
-    stages = ["preprocess", "bin_sort", "render_fwd", "loss", "blend_bwd", "project_bwd", "adam"]
+    stages = ["preprocess", "bin_sort", "render_fwd", "loss", "blend_bwd", "project_bwd_adam"]
     for w in range(args.warmup):
         step(w % V)
     torch.cuda.synchronize()
@@ -314,8 +312,8 @@ def run_ours(args, wl, rank, world):
         frame.sort()
         frame.render(bg)
         frame.loss(gt_dev, mask_dev, LAMBDA_SSIM)
-        frame.backward(params, cam, bg)
-        opt.step(frame.grads)
+        frame.blend_backward(bg)
+        opt.fused_step(frame, cam)
         loss_host[k:k + 1].copy_(frame.loss_val, non_blocking=True)
     torch.cuda.synchronize()
     e_sec = time.perf_counter() - e0
@@ -346,13 +344,13 @@ def rooflines(res):
     work = {
         "preprocess": ("hbm", N * (59 * 4 + 52)),
         "bin_sort": ("hbm", N * 8 + I * (12 + passes * 32 + 16)),
-        "project_bwd": ("hbm", N * (59 * 4 * 2 + 40 + 4)),
-        "adam": ("hbm", N * 59 * 28),
+        # params, m, v read and written; the gradient stays in registers; screen gradients read
+        "project_bwd_adam": ("hbm", N * (59 * 4 * 6 + 40 + 4)),
         "loss": ("hbm", res["W"] * res["H"] * (3 * 4 * 3 + 1 + 3 * 4 * 6)),
         "render_fwd": ("alu", pairs * FWD_FLOP_PER_PAIR),
         "blend_bwd": ("alu", pairs * BWD_FLOP_PER_PAIR),
     }
-    kernel = {"preprocess": "k_preprocess", "bin_sort": "sort chain", "project_bwd": "k_project_bwd", "adam": "k_adam",
+    kernel = {"preprocess": "k_preprocess", "bin_sort": "sort chain", "project_bwd_adam": "k_project_bwd_adam1",
               "loss": "loss kernels", "render_fwd": "k_render_fwd", "blend_bwd": "k_render_bwd"}
     out = {}
     for name, ms in zip(res["stages"], res["stage_ms"]):

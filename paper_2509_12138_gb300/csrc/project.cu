@@ -576,6 +576,208 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam(float4* __restrict__ p
   }
 }
 
+// Projection backward fused with Adam for Gaussians that belong to exactly
+// one unit (one view of one partition): the SH planes are streamed twice
+// (colour and clamp first, then each plane's gradient and Adam update), so
+// neither the 48 coefficients nor their gradients are held in registers.
+template <int DEG>
+__global__ void __launch_bounds__(128) k_project_bwd_adam1(float4* __restrict__ params, int64_t N, UnitTable U,
+                                                           const gs_camera* __restrict__ cams,
+                                                           const int* __restrict__ radius,
+                                                           const float2* __restrict__ gxy,
+                                                           const float4* __restrict__ gco,
+                                                           const float4* __restrict__ grgb, float4* __restrict__ m,
+                                                           float4* __restrict__ v, AdamLR lr, int lr_steps, float b1,
+                                                           float b2, float eps, const int32_t* __restrict__ d_step,
+                                                           float4* __restrict__ grads) {
+  constexpr int NC = ShCount<DEG>::NC;
+  constexpr int NP = ShCount<DEG>::NP;
+  constexpr int NPL = 3 + NP;
+  __shared__ float4 s_lr[16];
+  int t = *d_step + 1;
+  if (threadIdx.x < NPL) {
+    float frac = lr_steps > 0 ? (float)min(t, lr_steps) / (float)lr_steps : 0.f;
+    float4 a = lr.init[threadIdx.x], b = lr.fin[threadIdx.x];
+    auto sched = [&](float x0, float x1) { return (x0 == x1 || x0 <= 0.f) ? x0 : x0 * powf(x1 / x0, frac); };
+    s_lr[threadIdx.x] = make_float4(sched(a.x, b.x), sched(a.y, b.y), sched(a.z, b.z), sched(a.w, b.w));
+  }
+  __syncthreads();
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  float ibc1 = 1.f / (1.f - powf(b1, (float)t)), ibc2 = 1.f / (1.f - powf(b2, (float)t));
+  // the unit containing i (units are disjoint here)
+  int uu = -1;
+  int64_t pidx = 0;
+  for (int u = 0; u < U.n; ++u) {
+    int64_t l = i - U.gauss_begin[u];
+    if (l >= 0 && l < U.proj_base[u + 1] - U.proj_base[u]) { uu = u; pidx = U.proj_base[u] + l; break; }
+  }
+  bool vis = uu >= 0 && __ldg(radius + pidx) > 0;
+  float4 mean = params[i], sop = params[N + i], quat = params[2 * N + i];
+  float dmean[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, dlogit = 0.f;
+  float Y[16], gc[3] = {0.f, 0.f, 0.f}, il = 0.f, dir[3] = {0.f, 0.f, 0.f};
+  if (vis) {
+    const gs_camera& cam = cams[uu];
+    float2 g_xy = gxy[pidx];
+    float4 g_co = gco[pidx];
+    float4 g_rgb = grgb[pidx];
+    // pass A: colour before the clamp
+    float vx = mean.x - cam.campos[0], vy = mean.y - cam.campos[1], vz = mean.z - cam.campos[2];
+    il = 1.0f / sqrtf(vx * vx + vy * vy + vz * vz);
+    dir[0] = vx * il; dir[1] = vy * il; dir[2] = vz * il;
+    sh_basis<DEG>(dir[0], dir[1], dir[2], Y);
+    float col[3] = {0.5f, 0.5f, 0.5f};
+    #pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      float4 q = params[(3 + k) * N + i];
+      const float* qq = &q.x;
+      #pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        int f = 4 * k + e;
+        if (f < 3 * NC) col[f % 3] += Y[f / 3] * qq[e];
+      }
+    }
+    gc[0] = col[0] < 0.f ? 0.f : g_rgb.x;
+    gc[1] = col[1] < 0.f ? 0.f : g_rgb.y;
+    gc[2] = col[2] < 0.f ? 0.f : g_rgb.z;
+    // everything but the SH direction term (as in project_grads)
+    float qn[5];
+    Geo g;
+    geometry(cam, mean, sop, quat, g, qn);
+    float itz = 1.0f / g.t[2];
+    float dt[3] = {0.f, 0.f, 0.f};
+    {
+      float op = 1.0f / (1.0f + expf(-sop.w));
+      dlogit = g_co.w * op * (1.f - op);
+    }
+    dt[0] += g_xy.x * cam.fx * itz;
+    dt[1] += g_xy.y * cam.fy * itz;
+    dt[2] += -(g_xy.x * cam.fx * g.t[0] + g_xy.y * cam.fy * g.t[1]) * itz * itz;
+    float a = g.a, b = g.b, cc = g.c, det = g.det;
+    float id2 = 1.0f / (det * det);
+    float gA = g_co.x, gB = g_co.y, gC = g_co.z;
+    float da = (-cc * cc * gA + b * cc * gB - b * b * gC) * id2;
+    float db = (2.f * b * cc * gA - (det + 2.f * b * b) * gB + 2.f * a * b * gC) * id2;
+    float dc = (-b * b * gA + a * b * gB - a * a * gC) * id2;
+    const float* T = g.T2;
+    float hb = 0.5f * db;
+    float GT0[3], GT1[3];
+    #pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      GT0[j] = da * T[j] + hb * T[3 + j];
+      GT1[j] = hb * T[j] + dc * T[3 + j];
+    }
+    float dSig[9];
+    #pragma unroll
+    for (int i2 = 0; i2 < 3; ++i2)
+      #pragma unroll
+      for (int j = 0; j < 3; ++j) dSig[3 * i2 + j] = T[i2] * GT0[j] + T[3 + i2] * GT1[j];
+    const float* S6 = g.Sig;
+    float Sg[9] = {S6[0], S6[1], S6[2], S6[1], S6[3], S6[4], S6[2], S6[4], S6[5]};
+    float dT2[6];
+    #pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      dT2[j] = 2.f * (GT0[0] * Sg[j] + GT0[1] * Sg[3 + j] + GT0[2] * Sg[6 + j]);
+      dT2[3 + j] = 2.f * (GT1[0] * Sg[j] + GT1[1] * Sg[3 + j] + GT1[2] * Sg[6 + j]);
+    }
+    const float* V = cam.viewmat;
+    float dJ00 = dT2[0] * V[0] + dT2[1] * V[1] + dT2[2] * V[2];
+    float dJ02 = dT2[0] * V[8] + dT2[1] * V[9] + dT2[2] * V[10];
+    float dJ11 = dT2[3] * V[4] + dT2[4] * V[5] + dT2[5] * V[6];
+    float dJ12 = dT2[3] * V[8] + dT2[4] * V[9] + dT2[5] * V[10];
+    dt[2] += -(dJ00 * cam.fx + dJ11 * cam.fy) * itz * itz;
+    if (g.clx) {
+      dt[2] += dJ02 * cam.fx * g.xzc * itz * itz;
+    } else {
+      dt[0] += -dJ02 * cam.fx * itz * itz;
+      dt[2] += 2.f * dJ02 * cam.fx * g.t[0] * itz * itz * itz;
+    }
+    if (g.cly) {
+      dt[2] += dJ12 * cam.fy * g.yzc * itz * itz;
+    } else {
+      dt[1] += -dJ12 * cam.fy * itz * itz;
+      dt[2] += 2.f * dJ12 * cam.fy * g.t[1] * itz * itz * itz;
+    }
+    #pragma unroll
+    for (int k = 0; k < 3; ++k) dmean[k] += V[k] * dt[0] + V[4 + k] * dt[1] + V[8 + k] * dt[2];
+    float M[9];
+    #pragma unroll
+    for (int i2 = 0; i2 < 3; ++i2)
+      #pragma unroll
+      for (int j = 0; j < 3; ++j) M[3 * i2 + j] = g.Rq[3 * i2 + j] * g.s[j];
+    float dR[9];
+    #pragma unroll
+    for (int i2 = 0; i2 < 3; ++i2)
+      #pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        float dM = 2.f * (dSig[3 * i2] * M[j] + dSig[3 * i2 + 1] * M[3 + j] + dSig[3 * i2 + 2] * M[6 + j]);
+        dls[j] += dM * g.Rq[3 * i2 + j] * g.s[j];
+        dR[3 * i2 + j] = dM * g.s[j];
+      }
+    float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+    float gw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+    float gx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] +
+                      w * dR[7] - 2.f * x * dR[8]);
+    float gy = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] +
+                      z * dR[7] - 2.f * y * dR[8]);
+    float gz = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
+                      x * dR[6] + y * dR[7]);
+    float dot = gw * w + gx * x + gy * y + gz * z;
+    float inv = qn[4];
+    dq[0] = (gw - dot * w) * inv;
+    dq[1] = (gx - dot * x) * inv;
+    dq[2] = (gy - dot * y) * inv;
+    dq[3] = (gz - dot * z) * inv;
+  } else {
+    #pragma unroll
+    for (int k = 0; k < 16; ++k) Y[k] = 0.f;
+  }
+  // pass B: per SH plane, its gradient, the direction term and the Adam update
+  float wsum[16];
+  #pragma unroll
+  for (int k = 0; k < 16; ++k) wsum[k] = 0.f;
+  #pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    int64_t o = (3 + k) * N + i;
+    float4 P = params[o];
+    float* pp = &P.x;
+    float G[4];
+    #pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int f = 4 * k + e;
+      G[e] = 0.f;
+      if (f < 3 * NC) {
+        G[e] = Y[f / 3] * gc[f % 3];
+        wsum[f / 3] += pp[e] * gc[f % 3];
+      }
+    }
+    float4 Gk = make_float4(G[0], G[1], G[2], G[3]);
+    float4 Mv = m[o], Vv = v[o];
+    adam4(P, Gk, Mv, Vv, s_lr[3 + k], b1, b2, ibc1, ibc2, eps);
+    params[o] = P; m[o] = Mv; v[o] = Vv;
+    if (grads) grads[o] = Gk;
+  }
+  if (vis && DEG > 0) {
+    float sx, sy, sz;
+    sh_grad<DEG>(dir[0], dir[1], dir[2], wsum, sx, sy, sz);
+    float d = sx * dir[0] + sy * dir[1] + sz * dir[2];
+    dmean[0] += (sx - d * dir[0]) * il;
+    dmean[1] += (sy - d * dir[1]) * il;
+    dmean[2] += (sz - d * dir[2]) * il;
+  }
+  float4 Gp[3] = {make_float4(dmean[0], dmean[1], dmean[2], 0.f), make_float4(dls[0], dls[1], dls[2], dlogit),
+                  make_float4(dq[0], dq[1], dq[2], dq[3])};
+  float4 Pv[3] = {mean, sop, quat};
+  #pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    int64_t o = k * N + i;
+    float4 Mv = m[o], Vv = v[o];
+    adam4(Pv[k], Gp[k], Mv, Vv, s_lr[k], b1, b2, ibc1, ibc2, eps);
+    params[o] = Pv[k]; m[o] = Mv; v[o] = Vv;
+    if (grads) grads[o] = Gp[k];
+  }
+}
+
 __global__ void k_step_advance(int32_t* s) { *s += 1; }
 
 }  // namespace
@@ -753,6 +955,29 @@ GS_API int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, co
   if (n_gauss == 0) return GS_OK;
   dim3 block(128), grid((unsigned)((n_gauss + 127) / 128));
   cudaStream_t s = (cudaStream_t)stream;
+  // every Gaussian in at most one unit: the streaming kernel applies
+  bool disjoint = true;
+  for (int a = 0; a < U.n && disjoint; ++a)
+    for (int b = a + 1; b < U.n && disjoint; ++b) {
+      int64_t a0 = U.gauss_begin[a], a1 = a0 + (U.proj_base[a + 1] - U.proj_base[a]);
+      int64_t b0 = U.gauss_begin[b], b1 = b0 + (U.proj_base[b + 1] - U.proj_base[b]);
+      if (a0 < b1 && b0 < a1) disjoint = false;
+    }
+  if (disjoint) {
+#define GS_PBA1(D)                                                                                                \
+  k_project_bwd_adam1<D><<<grid, block, 0, s>>>((float4*)params, n_gauss, U, cams, proj->radius,                 \
+                                                (const float2*)g2d->dxy, (const float4*)g2d->dconic_op,          \
+                                                (const float4*)g2d->drgb, (float4*)m, (float4*)v, lr, lr_steps,   \
+                                                beta1, beta2, eps, d_step, (float4*)grads)
+    switch (sh_degree) {
+      case 0: GS_PBA1(0); break;
+      case 1: GS_PBA1(1); break;
+      case 2: GS_PBA1(2); break;
+      default: GS_PBA1(3); break;
+    }
+#undef GS_PBA1
+    return gs_check_launch();
+  }
 #define GS_PBA(D)                                                                                                \
   k_project_bwd_adam<D><<<grid, block, 0, s>>>((float4*)params, n_gauss, U, cams, proj->radius,                 \
                                                (const float2*)g2d->dxy, (const float4*)g2d->dconic_op,          \

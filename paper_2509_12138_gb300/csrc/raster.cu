@@ -269,17 +269,27 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict
           }
         }
       }
-      if (__ballot_sync(FULL, contrib)) {
-        float tot = reduce8(v, lane);
-        float e8 = v[8];
-        #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) e8 += __shfl_xor_sync(FULL, e8, o);
+      unsigned cm = __ballot_sync(FULL, contrib);
+      if (cm) {
         int64_t pr = (int64_t)__float_as_uint(rb.w);
-        if ((lane & 3) == 0) {
-          float* dst = q < 2 ? dxy + 2 * pr + q : (q < 6 ? dco + 4 * pr + (q - 2) : drgb + 4 * pr + (q - 6));
-          atomicAdd(dst, tot);
-        } else if (lane == 1) {
-          atomicAdd(drgb + 4 * pr + 2, e8);
+        if ((cm & (cm - 1)) == 0) {
+          // a single contributing lane: no reduction, three vector atomics
+          if (contrib) {
+            atomic_add2(dxy + 2 * pr, v[0], v[1]);
+            atomic_add4(dco + 4 * pr, v[2], v[3], v[4], v[5]);
+            atomic_add4(drgb + 4 * pr, v[6], v[7], v[8], 0.f);
+          }
+        } else {
+          float tot = reduce8(v, lane);
+          float e8 = v[8];
+          #pragma unroll
+          for (int o = 16; o > 0; o >>= 1) e8 += __shfl_xor_sync(FULL, e8, o);
+          if ((lane & 3) == 0) {
+            float* dst = q < 2 ? dxy + 2 * pr + q : (q < 6 ? dco + 4 * pr + (q - 2) : drgb + 4 * pr + (q - 6));
+            atomicAdd(dst, tot);
+          } else if (lane == 1) {
+            atomicAdd(drgb + 4 * pr + 2, e8);
+          }
         }
       }
     }
@@ -511,17 +521,27 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd_m(const uint2* __restri
           }
         }
       }
-      if (__ballot_sync(FULL, contrib)) {
-        float tot = reduce8(v, lane);
-        float e8 = v[8];
-        #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) e8 += __shfl_xor_sync(FULL, e8, o);
+      unsigned cm = __ballot_sync(FULL, contrib);
+      if (cm) {
         int64_t pr = (int64_t)__float_as_uint(rb.w);
-        if ((lane & 3) == 0) {
-          float* dst = q < 2 ? dxy + 2 * pr + q : (q < 6 ? dco + 4 * pr + (q - 2) : drgb + 4 * pr + (q - 6));
-          atomicAdd(dst, tot);
-        } else if (lane == 1) {
-          atomicAdd(drgb + 4 * pr + 2, e8);
+        if ((cm & (cm - 1)) == 0) {
+          // a single contributing lane: no reduction, three vector atomics
+          if (contrib) {
+            atomic_add2(dxy + 2 * pr, v[0], v[1]);
+            atomic_add4(dco + 4 * pr, v[2], v[3], v[4], v[5]);
+            atomic_add4(drgb + 4 * pr, v[6], v[7], v[8], 0.f);
+          }
+        } else {
+          float tot = reduce8(v, lane);
+          float e8 = v[8];
+          #pragma unroll
+          for (int o = 16; o > 0; o >>= 1) e8 += __shfl_xor_sync(FULL, e8, o);
+          if ((lane & 3) == 0) {
+            float* dst = q < 2 ? dxy + 2 * pr + q : (q < 6 ? dco + 4 * pr + (q - 2) : drgb + 4 * pr + (q - 6));
+            atomicAdd(dst, tot);
+          } else if (lane == 1) {
+            atomicAdd(drgb + 4 * pr + 2, e8);
+          }
         }
       }
     }

@@ -60,6 +60,7 @@ class PlainTrainer:
         self.opt = Adam(params, sh_degree, lrs, extent, lr_steps)
         self.rng = np.random.default_rng(seed)
         self.t = 0
+        self.keep_grads = False  # also write the parameter gradient (for inspection)
         need = max(self.frame.fit_capacity(params, self.cam(v)) for v in self.views[:: max(1, len(self.views) // 8)])
         self.frame.set_capacity(int(need * capacity_slack) + 4096)
 
@@ -80,8 +81,8 @@ class PlainTrainer:
         fr.sort()
         fr.render(self.bg)
         fr.loss(self.gt[v:v + 1], self.mask[v:v + 1], self.lam)
-        fr.backward(self.params, cam, self.bg)
-        self.opt.step(fr.grads)
+        fr.blend_backward(self.bg)
+        self.opt.fused_step(fr, cam, self.keep_grads)
 
     def check(self):
         st = self.frame.read_status()
@@ -133,6 +134,7 @@ class BatchedTrainer:
         self.mask_step = torch.zeros((U, H, W), dtype=torch.uint8, device=dev)
         self.t = 0
         self.graph = None
+        self.keep_grads = False  # also write the parameter gradient (for inspection)
         # instance capacity: the largest need over a sweep of the training views
         need = 0
         for t0 in range(0, len(self.views), max(1, len(self.views) // 4)):
@@ -160,8 +162,8 @@ class BatchedTrainer:
         fr.sort()
         fr.render(self.bg)
         fr.loss(self.gt_step, self.mask_step, self.lam)
-        fr.backward(self.params, self.cams_step, self.bg)
-        self.opt.step(fr.grads)
+        fr.blend_backward(self.bg)
+        self.opt.fused_step(fr, self.cams_step, self.keep_grads)
 
     def capture(self):
         """Run step t eagerly (on a side stream, so lazy initialisation happens outside the capture), then

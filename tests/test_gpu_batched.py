@@ -119,6 +119,7 @@ def test_graph_replay_matches_eager():
                                     torch.from_numpy(gt).cuda(), torch.from_numpy(mask).cuda(), list(range(6)),
                                     views_per_step=1, use_graph=g)
     tg, te = mk(True), mk(False)
+    tg.keep_grads = te.keep_grads = True
     tg.step()  # eager first step + capture
     te.step()
     for a, b in ((te.params, tg.params), (te.opt.m, tg.opt.m), (te.opt.v, tg.opt.v), (te.opt.step_dev, tg.opt.step_dev)):
@@ -177,21 +178,25 @@ def test_blend_variants_identical(variant):
     assert torch.allclose(res[0][2], res[1][2], rtol=1e-4, atol=1e-7)
 
 
-def test_fused_projection_backward_adam_matches_separate():
-    """gs_project_bwd_adam == gs_project_bwd followed by gs_adam_step (same gradient, same update)."""
+@pytest.mark.parametrize("n_views", [1, 2])
+def test_fused_projection_backward_adam_matches_separate(n_views):
+    """gs_project_bwd_adam == gs_project_bwd followed by gs_adam_step (same gradient, same update), for
+    Gaussians in one unit (streaming kernel) and in several views at once (general kernel)."""
     n, deg, W, H = 3000, 3, 120, 90
-    g, cams = scenes.random_scene(n, deg, 21, W, H)
+    g = synth.random_gaussians(n, deg, 21, extent=0.7, log_scale_range=(-3.5, -2.0))
+    cams = synth.orbital_cameras(n_views, 3.0, width=W, height=H)
     camd = gs.pack_cameras(cams)
-    gt, mask = scenes.random_gt(W, H, 22)
+    gts = np.stack([scenes.random_gt(W, H, 22 + k)[0] for k in range(n_views)])
+    masks = np.stack([scenes.random_gt(W, H, 22 + k)[1] for k in range(n_views)])
     out = []
     for fused in (False, True):
         params = gs.pack_params(g, deg)
-        fr = gs.Frame(n, gs.Units.single(n), W, H, deg)
+        fr = gs.Frame(n, gs.Units.single(n, n_views), W, H, deg)
         fr.fit_capacity(params, camd)
         opt = gs.Adam(params, deg, extent=1.5, lr_steps=5)
         for _ in range(3):
             fr.forward(params, camd, BG)
-            fr.loss(torch.from_numpy(gt).cuda()[None], torch.from_numpy(mask).cuda()[None], 0.2)
+            fr.loss(torch.from_numpy(gts).cuda(), torch.from_numpy(masks).cuda(), 0.2)
             fr.blend_backward(BG)
             if fused:
                 opt.fused_step(fr, camd, keep_grads=True)
@@ -208,12 +213,12 @@ def test_fused_projection_backward_adam_matches_separate():
     res = []
     for fused in (False, True):
         params = p0.clone()
-        fr = gs.Frame(n, gs.Units.single(n), W, H, deg)
+        fr = gs.Frame(n, gs.Units.single(n, n_views), W, H, deg)
         fr.fit_capacity(params, camd)
         opt = gs.Adam(params, deg, extent=1.5, lr_steps=5)
         opt.m.copy_(m0); opt.v.copy_(v0); opt.step_dev.copy_(s0)
         fr.forward(params, camd, BG)
-        fr.loss(torch.from_numpy(gt).cuda()[None], torch.from_numpy(mask).cuda()[None], 0.2)
+        fr.loss(torch.from_numpy(gts).cuda(), torch.from_numpy(masks).cuda(), 0.2)
         fr.blend_backward(BG)
         if fused:
             opt.fused_step(fr, camd, keep_grads=True)
