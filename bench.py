@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--workload", default="iso10M-1080p", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-window", type=int, default=8, help="CPU sample: 1/(w*w) of the view's pixels")
+    ap.add_argument("--experiment", default=None, choices=["learned-init"],
+                    help="instead of the throughput line: the plain vs batched + learned-init comparison")
+    ap.add_argument("--exp-gaussians", type=int, default=1_000_000)
+    ap.add_argument("--exp-steps", type=int, default=3000)
     return ap.parse_args()
 
 
@@ -385,6 +389,8 @@ def main():
               "l2": "inputs larger than L2 (params+Adam state 9.6 GB at 10M)"}
     if args.impl == "reference":
         return run_reference(args, wl, rank, world, config)
+    if args.experiment == "learned-init":
+        return run_learned_init_experiment(args)
     import torch
     if not torch.cuda.is_available():
         print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
@@ -427,6 +433,47 @@ def main():
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+    return 0
+
+
+def run_learned_init_experiment(args):
+    """Plain form vs batched + learned-init form on a scene the MLP has not seen: held-out PSNR against
+    wall-clock time (one JSON line)."""
+    import torch
+    from paper_2509_12138_gb300 import experiment as X
+    from paper_2509_12138_gb300 import workload
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    n, W, H, V, steps = args.exp_gaussians, 1920, 1080, 64, args.exp_steps
+    every = max(steps // 15, 1)
+    src = workload.isosurface_scene(n, 8, V, W, H, sh_degree=3, seed=101)
+    h_src, trained = X.run_plain(src, steps, every)
+    t0 = time.perf_counter()
+    w, losses = X.fit_mlp(src, trained, steps=600)
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t0
+    del src, trained
+    torch.cuda.empty_cache()
+    dst = workload.isosurface_scene(n, 8, V, W, H, sh_degree=3, seed=202)
+    h_plain, _ = X.run_plain(dst, steps, every)
+    target = h_plain.psnr[-1] - 0.1
+    h_learn, _ = X.run_learned_batched(dst, w, steps, every, views_per_step=2, stop_at=target)
+    s_hit, t_hit = h_learn.time_to(target)
+    line = {"experiment": "learned-init vs plain", "gaussians": n, "width": W, "height": H, "views": V,
+            "plain": {"steps": steps, "seconds": round(h_plain.seconds[-1], 3), "psnr": round(h_plain.psnr[-1], 3),
+                      "psnr_at_init": round(h_plain.psnr[0], 3)},
+            "batched_learned": {"views_per_step": 2, "psnr_at_init": round(h_learn.psnr[0], 3),
+                                "steps_to_plain_psnr_minus_0.1dB": s_hit,
+                                "seconds_to_plain_psnr_minus_0.1dB": None if t_hit is None else round(t_hit, 3),
+                                "final_psnr": round(h_learn.psnr[-1], 3)},
+            "mlp": {"fit_seconds": round(t_fit, 3), "loss_first": losses[0], "loss_last": losses[-1],
+                    "trained_on": "converged splats of another seed of the interface"},
+            "history": {"plain": [h_plain.steps, [round(x, 3) for x in h_plain.seconds],
+                                  [round(x, 3) for x in h_plain.psnr]],
+                        "learned": [h_learn.steps, [round(x, 3) for x in h_learn.seconds],
+                                    [round(x, 3) for x in h_learn.psnr]]}}
+    print(json.dumps(line))
     return 0
 
 

@@ -1,7 +1,9 @@
 // a3 / a5: front-to-back alpha blending per 16x16 tile and its reverse replay.
 //
-// One CTA per (unit, tile), one thread per pixel; each warp owns a BW x (32/BW)
-// pixel block of the 16x16 tile (BW = 8, 16 or 4: the tunable variant) and walks the tile's list
+// One thread per pixel; each warp owns a BW x (32/BW) pixel block of a 16x16
+// tile (BW = 8, 16 or 4: the tunable variant).  With the sort's block masks
+// every (tile, pixel block) is a one-warp CTA; without them one CTA covers a
+// tile.  Each warp walks the tile's list
 // independently of the other warps (no block barriers: warps whose block few
 // splats reach do not wait for the busy ones).  A record is blended by a warp
 // only if the bounding box of the ellipse where its alpha can reach 1/255
@@ -46,6 +48,16 @@ struct __align__(16) Rec {
 // Block index -> (unit, tile): heaviest tiles first when an order is given.
 __device__ __forceinline__ void block_tile(const uint32_t* __restrict__ order, int n_tiles, int& u, int& tile) {
   uint32_t f = order ? order[blockIdx.x] : blockIdx.x;
+  u = (int)(f / (uint32_t)n_tiles);
+  tile = (int)(f % (uint32_t)n_tiles);
+}
+
+// One-warp blocks: block index -> (unit, tile, warp block w of the tile).
+// Each (tile, pixel block) job retires as soon as its own walk ends.
+__device__ __forceinline__ void warp_job(const uint32_t* __restrict__ order, int n_tiles, int& u, int& tile, int& w) {
+  uint32_t j = blockIdx.x >> 3;
+  w = (int)(blockIdx.x & 7u);
+  uint32_t f = order ? order[j] : j;
   u = (int)(f / (uint32_t)n_tiles);
   tile = (int)(f % (uint32_t)n_tiles);
 }
@@ -316,7 +328,7 @@ __device__ __forceinline__ uint32_t warp_block_bits(int w) {
 // bytes (record id) per list entry, two rounds ahead, and gathers the records
 // of its hits one round ahead; the blend itself is that of k_render_fwd.
 template <int BW>
-__global__ void __launch_bounds__(TILE_PIX) k_render_fwd_m(const uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ ranges,
                                                            const uint32_t* __restrict__ order,
                                                            const uint32_t* __restrict__ vals,
                                                            const uint16_t* __restrict__ masks,
@@ -327,12 +339,12 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_fwd_m(const uint2* __restri
                                                            float* __restrict__ img, float* __restrict__ final_T,
                                                            uint32_t* __restrict__ n_contrib) {
   const unsigned FULL = 0xffffffffu;
-  __shared__ Rec s_rec[TILE_PIX / 32][32];
-  int u, tile;
-  block_tile(order, n_tiles, u, tile);
+  __shared__ Rec s_rec[1][32];
+  int u, tile, w;
+  warp_job(order, n_tiles, u, tile, w);
   int tx = tile % TX, ty = tile / TX;
   constexpr int BH = 32 / BW, NWX = TILE / BW;
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int lane = threadIdx.x & 31;
   int px = tx * TILE + (w % NWX) * BW + (lane % BW), py = ty * TILE + (w / NWX) * BH + (lane / BW);
   uint32_t wbits = warp_block_bits<BW>(w);
   bool inside = px < W && py < H;
@@ -342,7 +354,7 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_fwd_m(const uint2* __restri
   int last = 0;
   bool done = !inside;
   float fx = (float)px, fy = (float)py;
-  Rec* my = &s_rec[w][0];
+  Rec* my = &s_rec[0][0];
   // round r's record (hit lanes), round r+1's header
   bool h1 = false;
   float2 m1 = make_float2(0.f, 0.f);
@@ -407,7 +419,7 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_fwd_m(const uint2* __restri
 // Backward with per-instance block masks (the replay of k_render_bwd; headers
 // two rounds ahead, hit records one round ahead, rounds in reverse order).
 template <int BW>
-__global__ void __launch_bounds__(TILE_PIX) k_render_bwd_m(const uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ ranges,
                                                            const uint32_t* __restrict__ order,
                                                            const uint32_t* __restrict__ vals,
                                                            const uint16_t* __restrict__ masks,
@@ -420,12 +432,12 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd_m(const uint2* __restri
                                                            const float* __restrict__ dimg, float* __restrict__ dxy,
                                                            float* __restrict__ dco, float* __restrict__ drgb) {
   const unsigned FULL = 0xffffffffu;
-  __shared__ Rec s_rec[TILE_PIX / 32][32];
-  int u, tile;
-  block_tile(order, n_tiles, u, tile);
+  __shared__ Rec s_rec[1][32];
+  int u, tile, w;
+  warp_job(order, n_tiles, u, tile, w);
   int tx = tile % TX, ty = tile / TX;
   constexpr int BH = 32 / BW, NWX = TILE / BW;
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int lane = threadIdx.x & 31;
   int px = tx * TILE + (w % NWX) * BW + (lane % BW), py = ty * TILE + (w / NWX) * BH + (lane / BW);
   uint32_t wbits = warp_block_bits<BW>(w);
   bool inside = px < W && py < H;
@@ -443,7 +455,7 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd_m(const uint2* __restri
   int n = min(__reduce_max_sync(FULL, last), (int)(rg.y - rg.x));
   float S0 = bg0, S1 = bg1, S2 = bg2;
   float fx = (float)px, fy = (float)py;
-  Rec* my = &s_rec[w][0];
+  Rec* my = &s_rec[0][0];
   int q = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
   // rounds cover [top - 32, top); round r's record (hit lanes) and round r+1's header
   bool h1 = false;
@@ -624,7 +636,7 @@ int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const u
   dim3 grid(TX * TY * n_units);
 #define GS_FWD(BW)                                                                                                  \
   if (block_masks)                                                                                                  \
-    k_render_fwd_m<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, tile_order, sorted_vals, block_masks,       \
+    k_render_fwd_m<BW><<<dim3(grid.x * 8), 32, 0, s>>>((const uint2*)ranges, tile_order, sorted_vals, block_masks, \
                                                  (const float2*)proj->xy, (const float4*)proj->conic_op,           \
                                                  (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0],      \
                                                  bg[1], bg[2], img, final_T, n_contrib);                           \
@@ -660,7 +672,7 @@ int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const ui
   dim3 grid(TX * TY * n_units);
 #define GS_BWD(BW)                                                                                                   \
   if (block_masks)                                                                                                   \
-    k_render_bwd_m<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, tile_order, sorted_vals, block_masks,        \
+    k_render_bwd_m<BW><<<dim3(grid.x * 8), 32, 0, s>>>((const uint2*)ranges, tile_order, sorted_vals, block_masks,  \
                                                  (const float2*)proj->xy, (const float4*)proj->conic_op,            \
                                                  (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], \
                                                  bg[2], final_T, n_contrib, dL_dimg, g2d->dxy, g2d->dconic_op,      \

@@ -30,6 +30,7 @@ constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_T * RS_ITEMS;  // 4096 keys per sort block
 constexpr int RS_BINS = 256;
 constexpr int MAX_PASSES = 8;
+constexpr int SCATTER_DYN_SMEM = RS_TILE * (int)(sizeof(uint64_t) + sizeof(uint32_t));  // 48 KB
 
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -261,15 +262,24 @@ __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ hist
   }
 }
 
+// Stable scatter of one 4096-key block: keys are ranked within their digit in
+// key order (warp match + per-warp digit counts, round by round), placed in a
+// block-local digit-sorted buffer in shared memory, then written out so that
+// each digit's run goes to consecutive global positions (coalesced stores).
 __global__ void __launch_bounds__(RS_T) k_radix_scatter(uint64_t* __restrict__ k0, uint64_t* __restrict__ k1,
                                                         uint32_t* __restrict__ v0, uint32_t* __restrict__ v1,
                                                         const int32_t* __restrict__ cur, int pass,
                                                         const uint32_t* __restrict__ d_count, int shift,
                                                         const uint32_t* __restrict__ hist, int64_t stride) {
-  __shared__ uint32_t s_off[RS_BINS];
-  __shared__ uint32_t s_run[RS_BINS];
+  __shared__ uint32_t s_off[RS_BINS];    // global start of this block's run of each digit
+  __shared__ uint32_t s_run[RS_BINS];    // keys of each digit ranked so far
+  __shared__ uint32_t s_lstart[RS_BINS]; // block-local start of each digit
   __shared__ uint32_t s_wc[RS_T / 32][RS_BINS];
   __shared__ uint32_t s_rt[RS_BINS];
+  __shared__ uint32_t s_warp[33];
+  extern __shared__ __align__(16) unsigned char s_dyn[];  // RS_TILE keys, then RS_TILE values
+  uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);
+  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(uint64_t) * RS_TILE);
   int64_t I = *d_count;
   int64_t base = (int64_t)blockIdx.x * RS_TILE;
   if (base >= I) return;
@@ -286,37 +296,84 @@ __global__ void __launch_bounds__(RS_T) k_radix_scatter(uint64_t* __restrict__ k
   for (int q = 0; q < RS_T / 32; ++q) s_wc[q][tid] = 0u;
   __syncthreads();
   uint32_t lt = (1u << lane) - 1u;
+  uint64_t key[RS_ITEMS];
+  uint32_t val[RS_ITEMS];
+  uint32_t rnk[RS_ITEMS];  // rank within the digit (block-local); 0xffffffff = no key
+  #pragma unroll
   for (int j = 0; j < RS_ITEMS; ++j) {
     int64_t k = base + (int64_t)j * RS_T + tid;
     bool valid = k < I;
-    uint64_t key = valid ? kin[k] : 0ull;
-    uint32_t val = valid ? vin[k] : 0u;
-    uint32_t d = valid ? ((uint32_t)(key >> shift) & 255u) : 256u;
+    key[j] = valid ? kin[k] : 0ull;
+    val[j] = valid ? vin[k] : 0u;
+  }
+  #pragma unroll
+  for (int j = 0; j < RS_ITEMS; ++j) {
+    int64_t k = base + (int64_t)j * RS_T + tid;
+    bool valid = k < I;
+    uint32_t d = valid ? ((uint32_t)(key[j] >> shift) & 255u) : 256u;
     uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t rank = __popc(peers & lt);
     if (valid && rank == 0) s_wc[w][d] = __popc(peers);
     __syncthreads();
-    {  // per digit: exclusive prefix over warps
-      uint32_t s = 0;
+    {
+      uint32_t acc = 0;
       #pragma unroll
       for (int q = 0; q < RS_T / 32; ++q) {
         uint32_t cq = s_wc[q][tid];
-        s_wc[q][tid] = s;
-        s += cq;
+        s_wc[q][tid] = acc;
+        acc += cq;
       }
-      s_rt[tid] = s;
+      s_rt[tid] = acc;
     }
     __syncthreads();
-    if (valid) {
-      uint32_t pos = s_off[d] + s_run[d] + s_wc[w][d] + rank;
-      kout[pos] = key;
-      vout[pos] = val;
-    }
+    rnk[j] = valid ? s_run[d] + s_wc[w][d] + rank : 0xffffffffu;
     __syncthreads();
     s_run[tid] += s_rt[tid];
     #pragma unroll
     for (int q = 0; q < RS_T / 32; ++q) s_wc[q][tid] = 0u;
     __syncthreads();
+  }
+  // block-local digit starts (exclusive prefix of the block's digit counts)
+  {
+    uint32_t cnt = s_run[tid];
+    int l = lane;
+    uint32_t inc = cnt;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t nb = __shfl_up_sync(0xffffffffu, inc, o);
+      if (l >= o) inc += nb;
+    }
+    if (lane == 31) s_warp[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+      uint32_t x = lane < RS_T / 32 ? s_warp[lane] : 0u, xi = x;
+      #pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t nb = __shfl_up_sync(0xffffffffu, xi, o);
+        if (lane >= o) xi += nb;
+      }
+      if (lane < RS_T / 32) s_warp[lane] = xi - x;
+    }
+    __syncthreads();
+    s_lstart[tid] = inc - cnt + s_warp[w];
+  }
+  __syncthreads();
+  #pragma unroll
+  for (int j = 0; j < RS_ITEMS; ++j) {
+    if (rnk[j] == 0xffffffffu) continue;
+    uint32_t d = (uint32_t)(key[j] >> shift) & 255u;
+    uint32_t pos = s_lstart[d] + rnk[j];
+    s_keys[pos] = key[j];
+    s_vals[pos] = val[j];
+  }
+  __syncthreads();
+  int n_here = (int)min((int64_t)RS_TILE, I - base);
+  for (int i = tid; i < n_here; i += RS_T) {
+    uint64_t kk = s_keys[i];
+    uint32_t d = (uint32_t)(kk >> shift) & 255u;
+    uint32_t gp = s_off[d] + (uint32_t)i - s_lstart[d];
+    kout[gp] = kk;
+    vout[gp] = s_vals[i];
   }
 }
 
@@ -430,12 +487,16 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
                                                           proj->tiles, offsets, width, height, tile_bits,
                                                           max_instances, k0, v0);
   if (max_instances > 0) {
+    if (cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, SCATTER_DYN_SMEM) !=
+        cudaSuccess)
+      return GS_ERR_CUDA;
     unsigned nrb = (unsigned)stride;
     for (int pass = 0; pass < passes; ++pass) {
       int shift = 8 * pass;
       k_radix_hist<<<nrb, RS_T, 0, s>>>(k0, k1, cur, pass, d_num_instances, shift, hist, stride, totals);
       k_radix_scan<<<RS_BINS, 1024, 0, s>>>(hist, stride, totals, pass, d_num_instances, cur);
-      k_radix_scatter<<<nrb, RS_T, 0, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift, hist, stride);
+      k_radix_scatter<<<nrb, RS_T, SCATTER_DYN_SMEM, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift, hist,
+                                                          stride);
     }
     k_ranges<<<(unsigned)((max_instances + 255) / 256), 256, 0, s>>>(
         k0, k1, v0, v1, cur, passes, d_num_instances, tile_bits, n_tiles, TX, ranges, sorted_vals,
