@@ -103,6 +103,30 @@ typedef struct gs_grad2d {
   float* drgb;      /* [P][4] */
 } gs_grad2d;
 
+/* Blend schedule (all device buffers; see gs_bin_sort and the blend calls):
+ * tile_order   [U * n_tiles]      blocks ordered by decreasing list length class
+ * block_masks  [max_instances]    per sorted instance: bit 4 by + bx set iff the
+ *                                 record's alpha >= 1/255 ellipse (a conservative
+ *                                 box of it) reaches 4x4 pixel block (bx, by)
+ * job_base     [U * n_tiles + 1]  exclusive prefix (in tile_order) of the number
+ *                                 of chunks of each list; job_base[U n_tiles] = jobs
+ * jobs         [2 * max_jobs]     (order position, chunk) of every chunk job
+ * checkpoints  [max_checkpoints][256][4]  per pixel (T, r, g, b) of the forward
+ *                                 at every interior chunk boundary
+ * chunk        entries per chunk (a multiple of 32); max_jobs >= U n_tiles +
+ *              max_instances / chunk + 1, max_checkpoints >= max_instances /
+ *              chunk + 1 (gs_schedule_sizes). */
+typedef struct gs_schedule {
+  uint32_t* tile_order;
+  uint16_t* block_masks;
+  uint32_t* job_base;
+  uint32_t* jobs;
+  float* checkpoints;
+  int64_t max_jobs;
+  int64_t max_checkpoints;
+  int32_t chunk;
+} gs_schedule;
+
 /* Unit table (host arrays, copied by value into the launch). */
 typedef struct gs_units {
   int32_t n_units;               /* 1 .. GS_MAX_UNITS */
@@ -154,14 +178,10 @@ int gs_preprocess(const float* params, int64_t n_gauss, int sh_degree, const gs_
  * A stable LSD radix sort (8-bit digits) orders the keys, so equal keys keep
  * record order: each tile's list is ordered by (depth, record index).
  * ranges[u * n_tiles + tile] = [start, end) into sorted_vals.
- * tile_order (may be NULL): receives the U * n_tiles block indices u * n_tiles +
- * tile ordered by decreasing list length class (heaviest first), which the
- * blend calls use to schedule long lists early.
- * block_masks (may be NULL; [max_instances] uint16): for each sorted instance,
- * bit 4 by + bx is set iff the record's alpha >= 1/255 ellipse (a conservative
- * box of it) reaches pixel block (bx, by) (4x4 pixels) of the instance's
- * tile; the blend calls use it to skip records that cannot touch a warp's
- * pixels.
+ * sched (may be NULL): also fills the blend schedule: tile order (heaviest
+ * lists first), per-instance block masks and the chunk jobs of every list
+ * (see gs_schedule); the blend calls use it to skip records that cannot touch
+ * a warp's pixels and to replay long lists in parallel chunks.
  * max_instances: capacity of the instance buffers; on overflow GS_ERR_CAPACITY
  * is set in d_status and the lists are truncated.  d_num_instances: device
  * uint32 receiving the instance count.  Workspace: gs_bin_sort_workspace_size. */
@@ -169,7 +189,12 @@ size_t gs_bin_sort_workspace_size(int64_t n_proj, int64_t max_instances);
 int gs_bin_sort(const gs_proj* proj, const gs_units* units, int width, int height,
                 int64_t max_instances, void* workspace, size_t workspace_bytes,
                 uint32_t* sorted_vals, uint32_t* ranges, uint32_t* d_num_instances,
-                uint32_t* tile_order, uint16_t* block_masks, int* d_status, gs_stream_t stream);
+                const gs_schedule* sched, int* d_status, gs_stream_t stream);
+
+/* Buffer sizes of a gs_schedule for n_units units of width x height and the
+ * given instance capacity and chunk length: *max_jobs, *max_checkpoints. */
+int gs_schedule_sizes(int n_units, int width, int height, int64_t max_instances, int chunk,
+                      int64_t* max_jobs, int64_t* max_checkpoints);
 
 /* ---- gs_bin_sort without a caller workspace ----------------------------
  * The paper has no counterpart: this is a deployment variant of gs_bin_sort
@@ -203,13 +228,14 @@ int gs_bin_sort_static(const gs_proj* proj, const gs_units* units, int width, in
  * the last blended entry, final_T = T.  bg: host float[3].
  * variant: execution shape only (results are identical): each warp owns a
  * BW x 32/BW pixel block of the tile, BW = 8 (0), 16 (1) or 4 (2).
- * tile_order: NULL (natural order) or gs_bin_sort's heaviest-first order.
- * block_masks: NULL, or gs_bin_sort's per-instance block masks (warps then
- * skip records whose mask misses their pixels; results are unchanged). */
+ * sched: NULL (one CTA per tile, natural order) or gs_bin_sort's schedule:
+ * one-warp jobs per (tile, 8x4 block) in heaviest-first order that skip
+ * records whose block mask misses their pixels, and write the per-pixel
+ * checkpoints the chunked backward starts from.  Results are identical. */
 int gs_render_fwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges,
                   int n_units, int width, int height, const float* bg, float* img,
-                  float* final_T, uint32_t* n_contrib, int variant, const uint32_t* tile_order,
-                  const uint16_t* block_masks, gs_stream_t stream);
+                  float* final_T, uint32_t* n_contrib, int variant, const gs_schedule* sched,
+                  gs_stream_t stream);
 
 /* Diagnostic: *d_count = number of blended (pixel, record) pairs of the last
  * gs_render_fwd (records before n_contrib whose alpha reaches 1/255); the
@@ -244,20 +270,24 @@ int gs_loss(const float* img, const float* gt, const uint8_t* mask, int n_units,
  * Gaussian).  g2d is zeroed by this call.
  * Projection backward: chain rule of a1 onto all parameters, summed over the
  * units containing each Gaussian; grads (planes layout) are overwritten.
- * variant: as for gs_render_fwd (execution shape of the blend replay). */
+ * variant, sched: as for gs_render_fwd.  With a schedule, each list is
+ * replayed in chunks of sched->chunk entries by independent warps: a chunk
+ * starts from the forward's checkpoint at its end (transmittance T and the
+ * colour C accumulated in front of it; the colour behind is (img - C) / T).
+ * img: the forward's image (read only with a schedule). */
 int gs_render_bwd(const float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
                   const gs_camera* cams, const gs_proj* proj, const uint32_t* sorted_vals,
-                  const uint32_t* ranges, int width, int height, const float* bg,
+                  const uint32_t* ranges, int width, int height, const float* bg, const float* img,
                   const float* final_T, const uint32_t* n_contrib, const float* dL_dimg,
-                  const gs_grad2d* g2d, float* grads, int variant, const uint32_t* tile_order,
-                  const uint16_t* block_masks, gs_stream_t stream);
+                  const gs_grad2d* g2d, float* grads, int variant, const gs_schedule* sched,
+                  gs_stream_t stream);
 
 /* Blend backward only: g2d ([n_proj] records) is zeroed, then accumulated. */
 int gs_blend_bwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges,
-                 int n_units, int width, int height, const float* bg, const float* final_T,
-                 const uint32_t* n_contrib, const float* dL_dimg, const gs_grad2d* g2d,
-                 int64_t n_proj, int variant, const uint32_t* tile_order,
-                 const uint16_t* block_masks, gs_stream_t stream);
+                 int n_units, int width, int height, const float* bg, const float* img,
+                 const float* final_T, const uint32_t* n_contrib, const float* dL_dimg,
+                 const gs_grad2d* g2d,
+                 int64_t n_proj, int variant, const gs_schedule* sched, gs_stream_t stream);
 
 /* Projection backward only (grads overwritten). */
 int gs_project_bwd(const float* params, int64_t n_gauss, int sh_degree, const gs_units* units,

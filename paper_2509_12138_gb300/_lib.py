@@ -34,6 +34,12 @@ class GsGrad2d(C.Structure):
     _fields_ = [("dxy", C.c_void_p), ("dconic_op", C.c_void_p), ("drgb", C.c_void_p)]
 
 
+class GsSchedule(C.Structure):
+    _fields_ = [("tile_order", C.c_void_p), ("block_masks", C.c_void_p), ("job_base", C.c_void_p),
+                ("jobs", C.c_void_p), ("checkpoints", C.c_void_p), ("max_jobs", C.c_int64),
+                ("max_checkpoints", C.c_int64), ("chunk", C.c_int32)]
+
+
 class GsUnits(C.Structure):
     _fields_ = [("n_units", C.c_int32), ("gauss_begin", c_i64p), ("gauss_count", c_i64p)]
 
@@ -57,16 +63,19 @@ SIGNATURES = {
     "gs_preprocess": (I32, [VP, I64, I32, C.POINTER(GsUnits), VP, I32, I32, C.POINTER(GsOwned), C.POINTER(GsProj),
                             VP, VP]),
     "gs_bin_sort_workspace_size": (SZ, [I64, I64]),
-    "gs_bin_sort": (I32, [C.POINTER(GsProj), C.POINTER(GsUnits), I32, I32, I64, VP, SZ, VP, VP, VP, VP, VP, VP, VP]),
+    "gs_bin_sort": (I32, [C.POINTER(GsProj), C.POINTER(GsUnits), I32, I32, I64, VP, SZ, VP, VP, VP,
+                          C.POINTER(GsSchedule), VP, VP]),
+    "gs_schedule_sizes": (I32, [I32, I32, I32, I64, I32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "gs_bin_sort_static": (I32, [C.POINTER(GsProj), C.POINTER(GsUnits), I32, I32, VP, VP, VP, VP, VP]),
-    "gs_render_fwd": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, c_f32p, VP, VP, VP, I32, VP, VP, VP]),
+    "gs_render_fwd": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, c_f32p, VP, VP, VP, I32,
+                            C.POINTER(GsSchedule), VP]),
     "gs_blend_pairs": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, VP, VP, VP]),
     "gs_loss_workspace_size": (SZ, [I32, I32, I32]),
     "gs_loss": (I32, [VP, VP, VP, I32, I32, I32, F32, VP, SZ, VP, VP, VP]),
     "gs_render_bwd": (I32, [VP, I64, I32, C.POINTER(GsUnits), VP, C.POINTER(GsProj), VP, VP, I32, I32, c_f32p, VP,
-                            VP, VP, C.POINTER(GsGrad2d), VP, I32, VP, VP, VP]),
-    "gs_blend_bwd": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, c_f32p, VP, VP, VP, C.POINTER(GsGrad2d), I64,
-                           I32, VP, VP, VP]),
+                            VP, VP, VP, C.POINTER(GsGrad2d), VP, I32, C.POINTER(GsSchedule), VP]),
+    "gs_blend_bwd": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, c_f32p, VP, VP, VP, VP, C.POINTER(GsGrad2d),
+                           I64, I32, C.POINTER(GsSchedule), VP]),
     "gs_project_bwd": (I32, [VP, I64, I32, C.POINTER(GsUnits), VP, C.POINTER(GsProj), C.POINTER(GsGrad2d), VP, VP]),
     "gs_adam_step": (I32, [VP, VP, VP, VP, I64, I32, c_f32p, c_f32p, I32, F32, F32, F32, VP, I32, VP]),
     "gs_step_advance": (I32, [VP, VP]),

@@ -282,27 +282,27 @@ GS_API int gs_loss(const float* img, const float* gt, const uint8_t* mask, int n
 int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
                       int width, int height, const float* bg, const float* final_T, const uint32_t* n_contrib,
                       const float* dL_dimg, const gs_grad2d* g2d, int64_t n_proj, int variant,
-                      const uint32_t* tile_order, const uint16_t* block_masks, cudaStream_t s);
+                      const gs_schedule* sched, const float* img, cudaStream_t s);
 
 GS_API int gs_blend_bwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
-                        int width, int height, const float* bg, const float* final_T, const uint32_t* n_contrib,
-                        const float* dL_dimg, const gs_grad2d* g2d, int64_t n_proj, int variant,
-                        const uint32_t* tile_order, const uint16_t* block_masks, gs_stream_t stream) {
+                        int width, int height, const float* bg, const float* img, const float* final_T,
+                        const uint32_t* n_contrib, const float* dL_dimg, const gs_grad2d* g2d, int64_t n_proj,
+                        int variant, const gs_schedule* sched, gs_stream_t stream) {
   return gs_blend_bwd_impl(proj, sorted_vals, ranges, n_units, width, height, bg, final_T, n_contrib, dL_dimg,
-                           g2d, n_proj, variant, tile_order, block_masks, (cudaStream_t)stream);
+                           g2d, n_proj, variant, sched, img, (cudaStream_t)stream);
 }
 
 GS_API int gs_render_bwd(const float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
                          const gs_camera* cams, const gs_proj* proj, const uint32_t* sorted_vals,
-                         const uint32_t* ranges, int width, int height, const float* bg, const float* final_T,
-                         const uint32_t* n_contrib, const float* dL_dimg, const gs_grad2d* g2d, float* grads,
-                         int variant, const uint32_t* tile_order, const uint16_t* block_masks,
+                         const uint32_t* ranges, int width, int height, const float* bg, const float* img,
+                         const float* final_T, const uint32_t* n_contrib, const float* dL_dimg,
+                         const gs_grad2d* g2d, float* grads, int variant, const gs_schedule* sched,
                          gs_stream_t stream) {
   UnitTable U;
   int64_t P = 0;
   if (gs_fill_units(units, U, &P) != GS_OK) return GS_ERR_INVALID;
   int r = gs_blend_bwd_impl(proj, sorted_vals, ranges, U.n, width, height, bg, final_T, n_contrib, dL_dimg, g2d, P,
-                            variant, tile_order, block_masks, (cudaStream_t)stream);
+                            variant, sched, img, (cudaStream_t)stream);
   if (r != GS_OK) return r;
   return gs_project_bwd(params, n_gauss, sh_degree, units, cams, proj, g2d, grads, stream);
 }

@@ -150,6 +150,9 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict
   }
 }
 
+__device__ __forceinline__ float fx_of(int px) { return (float)px; }
+__device__ __forceinline__ float fy_of(int py) { return (float)py; }
+
 // Sum of 8 values over the warp in 9 shuffles: each butterfly level halves the
 // set of values a lane carries; afterwards lane l holds the total of value
 // 4 bit4(l) + 2 bit3(l) + bit2(l).
@@ -330,6 +333,8 @@ __device__ __forceinline__ uint32_t warp_block_bits(int w) {
 template <int BW>
 __global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ ranges,
                                                            const uint32_t* __restrict__ order,
+                                                           const uint32_t* __restrict__ job_base, int K,
+                                                           float4* __restrict__ ckpt,
                                                            const uint32_t* __restrict__ vals,
                                                            const uint16_t* __restrict__ masks,
                                                            const float2* __restrict__ xy,
@@ -368,7 +373,17 @@ __global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ r
     }
   }
   if (32 + lane < n) { mk2 = masks[rg.x + 32 + lane]; pk2 = vals[rg.x + 32 + lane]; }
+  // checkpoints at the interior chunk boundaries b K (b = 1 .. nch - 1) of this list
+  int o = (int)(blockIdx.x >> 3);
+  int nch = (int)(job_base[o + 1] - job_base[o]);
+  int64_t cp0 = (int64_t)job_base[o] - o;  // this list's first checkpoint
+  int pix_local = (py - ty * TILE) * TILE + (px - tx * TILE);
+  int next_b = 1;
   for (int base = 0; base < n; base += 32) {
+    if (base == next_b * K && next_b < nch) {
+      if (inside) ckpt[(cp0 + next_b - 1) * TILE_PIX + pix_local] = make_float4(T, c0, c1, c2);
+      ++next_b;
+    }
     if (__all_sync(FULL, done)) break;
     bool hit = h1;
     float2 m = m1;
@@ -404,6 +419,8 @@ __global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ r
     }
     __syncwarp();
   }
+  for (; next_b < nch; ++next_b)  // boundaries after an early exit: the state is final
+    if (inside) ckpt[(cp0 + next_b - 1) * TILE_PIX + pix_local] = make_float4(T, c0, c1, c2);
   if (inside) {
     int64_t plane = (int64_t)W * H;
     int64_t pix = (int64_t)py * W + px;
@@ -416,25 +433,38 @@ __global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ r
   }
 }
 
-// Backward with per-instance block masks (the replay of k_render_bwd; headers
-// two rounds ahead, hit records one round ahead, rounds in reverse order).
+// Backward over chunk jobs: job (list, chunk c, pixel block) replays entries
+// [c K, min((c + 1) K, L)) of the list back to front.  It starts from the
+// forward's checkpoint at the chunk's end (T and the colour C accumulated in
+// front of it; the colour behind is (img - C) / T), or from final_T and the
+// background for the last chunk.  Headers two rounds ahead, hit records one
+// round ahead, as in the forward.
 template <int BW>
 __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ ranges,
                                                            const uint32_t* __restrict__ order,
+                                                           const uint32_t* __restrict__ job_base,
+                                                           const uint32_t* __restrict__ jobs, int K,
+                                                           const float4* __restrict__ ckpt,
                                                            const uint32_t* __restrict__ vals,
                                                            const uint16_t* __restrict__ masks,
                                                            const float2* __restrict__ xy,
                                                            const float4* __restrict__ conic_op,
                                                            const float4* __restrict__ rgb, int W, int H, int TX,
-                                                           int n_tiles, float bg0, float bg1, float bg2,
+                                                           int n_tiles, int NT, float bg0, float bg1, float bg2,
+                                                           const float* __restrict__ img,
                                                            const float* __restrict__ final_T,
                                                            const uint32_t* __restrict__ n_contrib,
                                                            const float* __restrict__ dimg, float* __restrict__ dxy,
                                                            float* __restrict__ dco, float* __restrict__ drgb) {
   const unsigned FULL = 0xffffffffu;
-  __shared__ Rec s_rec[1][32];
-  int u, tile, w;
-  warp_job(order, n_tiles, u, tile, w);
+  __shared__ Rec s_rec[32];
+  uint32_t jid = blockIdx.x >> 3;
+  if (jid >= job_base[NT]) return;
+  int w = (int)(blockIdx.x & 7u);
+  int o = (int)jobs[2 * (int64_t)jid], ch = (int)jobs[2 * (int64_t)jid + 1];
+  uint32_t f = order[o];
+  int u = (int)(f / (uint32_t)n_tiles), tile = (int)(f % (uint32_t)n_tiles);
+  int nch = (int)(job_base[o + 1] - job_base[o]);
   int tx = tile % TX, ty = tile / TX;
   constexpr int BH = 32 / BW, NWX = TILE / BW;
   int lane = threadIdx.x & 31;
@@ -442,22 +472,33 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
   uint32_t wbits = warp_block_bits<BW>(w);
   bool inside = px < W && py < H;
   uint2 rg = ranges[(int64_t)u * n_tiles + tile];
+  int L = (int)(rg.y - rg.x);
+  int cbeg = ch * K, cend = min(cbeg + K, L);
   int64_t plane = (int64_t)W * H;
   int64_t pix = (int64_t)py * W + px;
-  float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+  float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, S0 = bg0, S1 = bg1, S2 = bg2;
   int last = 0;
   if (inside) {
-    T = final_T[(int64_t)u * plane + pix];
     last = (int)n_contrib[(int64_t)u * plane + pix];
     const float* d = dimg + (int64_t)u * 3 * plane;
     g0 = d[pix]; g1 = d[plane + pix]; g2 = d[2 * plane + pix];
+    if (ch + 1 < nch && last > cbeg) {
+      int pix_local = (py - ty * TILE) * TILE + (px - tx * TILE);
+      float4 cp = ckpt[((int64_t)job_base[o] - o + ch) * TILE_PIX + pix_local];
+      const float* im = img + (int64_t)u * 3 * plane;
+      T = cp.x;
+      float iT = 1.f / T;
+      S0 = (im[pix] - cp.y) * iT;
+      S1 = (im[plane + pix] - cp.z) * iT;
+      S2 = (im[2 * plane + pix] - cp.w) * iT;
+    } else {
+      T = final_T[(int64_t)u * plane + pix];
+    }
   }
-  int n = min(__reduce_max_sync(FULL, last), (int)(rg.y - rg.x));
-  float S0 = bg0, S1 = bg1, S2 = bg2;
-  float fx = (float)px, fy = (float)py;
-  Rec* my = &s_rec[0][0];
+  // entries this warp replays: [cbeg, min(cend, max over its pixels of last))
+  int n = min(__reduce_max_sync(FULL, last), cend);
+  Rec* my = &s_rec[0];
   int q = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-  // rounds cover [top - 32, top); round r's record (hit lanes) and round r+1's header
   bool h1 = false;
   uint32_t p1 = 0;
   float2 m1 = make_float2(0.f, 0.f);
@@ -465,7 +506,7 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
   uint32_t mk2 = 0, pk2 = 0;
   {
     int k = n - 32 + lane;
-    if (n > 0 && k >= 0) {
+    if (n > cbeg && k >= cbeg) {
       uint32_t mk = masks[rg.x + k];
       if (mk & wbits) {
         p1 = vals[rg.x + k];
@@ -473,9 +514,9 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
       }
     }
     int k2 = n - 64 + lane;
-    if (n > 32 && k2 >= 0) { mk2 = masks[rg.x + k2]; pk2 = vals[rg.x + k2]; }
+    if (n - 32 > cbeg && k2 >= cbeg) { mk2 = masks[rg.x + k2]; pk2 = vals[rg.x + k2]; }
   }
-  for (int top = n; top > 0; top -= 32) {
+  for (int top = n; top > cbeg; top -= 32) {
     int base = top - 32;
     bool hit = h1;
     uint32_t p = p1;
@@ -485,7 +526,7 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
     if (h1) { p1 = pk2; m1 = xy[pk2]; co1 = conic_op[pk2]; cc1 = rgb[pk2]; }
     int k2 = top - 96 + lane;
     mk2 = 0;
-    if (top > 64 && k2 >= 0) { mk2 = masks[rg.x + k2]; pk2 = vals[rg.x + k2]; }
+    if (top - 64 > cbeg && k2 >= cbeg) { mk2 = masks[rg.x + k2]; pk2 = vals[rg.x + k2]; }
     unsigned mask = __ballot_sync(FULL, hit);
     if (hit) {
       my[lane].a = make_float4(m.x, m.y, co.x, co.y);
@@ -503,7 +544,7 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
       bool contrib = false;
       float4 ra = my[j].a, rb = my[j].b;
       if (pos < last) {
-        float dx = ra.x - fx, dy = ra.y - fy;
+        float dx = ra.x - fx_of(px), dy = ra.y - fy_of(py);
         float A = ra.z, B = ra.w, Cc = rb.x, op = rb.y;
         float power = splat_power(A, B, Cc, dx, dy);
         if (power <= 0.f && power >= rb.z) {
@@ -537,7 +578,6 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
       if (cm) {
         int64_t pr = (int64_t)__float_as_uint(rb.w);
         if ((cm & (cm - 1)) == 0) {
-          // a single contributing lane: no reduction, three vector atomics
           if (contrib) {
             atomic_add2(dxy + 2 * pr, v[0], v[1]);
             atomic_add4(dco + 4 * pr, v[2], v[3], v[4], v[5]);
@@ -547,7 +587,7 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
           float tot = reduce8(v, lane);
           float e8 = v[8];
           #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) e8 += __shfl_xor_sync(FULL, e8, o);
+          for (int oo = 16; oo > 0; oo >>= 1) e8 += __shfl_xor_sync(FULL, e8, oo);
           if ((lane & 3) == 0) {
             float* dst = q < 2 ? dxy + 2 * pr + q : (q < 6 ? dco + 4 * pr + (q - 2) : drgb + 4 * pr + (q - 6));
             atomicAdd(dst, tot);
@@ -627,7 +667,7 @@ __global__ void __launch_bounds__(TILE_PIX) k_blend_pairs(const uint2* __restric
 
 int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
                        int width, int height, const float* bg, float* img, float* final_T, uint32_t* n_contrib,
-                       int variant, const uint32_t* tile_order, const uint16_t* block_masks, cudaStream_t s) {
+                       int variant, const gs_schedule* sched, cudaStream_t s) {
   if (!proj || !proj->xy || !proj->conic_op || !proj->rgb || !sorted_vals || !ranges || !bg || !img ||
       !final_T || !n_contrib || n_units < 1 || n_units > GS_MAX_UNITS || width <= 0 || height <= 0 ||
       variant < 0 || variant > 2)
@@ -635,13 +675,15 @@ int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const u
   int TX = (width + TILE - 1) / TILE, TY = (height + TILE - 1) / TILE;
   dim3 grid(TX * TY * n_units);
 #define GS_FWD(BW)                                                                                                  \
-  if (block_masks)                                                                                                  \
-    k_render_fwd_m<BW><<<dim3(grid.x * 8), 32, 0, s>>>((const uint2*)ranges, tile_order, sorted_vals, block_masks, \
+  if (sched)                                                                                                        \
+    k_render_fwd_m<BW><<<dim3(grid.x * 8), 32, 0, s>>>((const uint2*)ranges, sched->tile_order, sched->job_base,  \
+                                                       sched->chunk, (float4*)sched->checkpoints, sorted_vals,   \
+                                                       sched->block_masks,                                        \
                                                  (const float2*)proj->xy, (const float4*)proj->conic_op,           \
                                                  (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0],      \
                                                  bg[1], bg[2], img, final_T, n_contrib);                           \
   else                                                                                                              \
-    k_render_fwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, tile_order, sorted_vals, (const float2*)proj->xy, \
+    k_render_fwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, nullptr, sorted_vals, (const float2*)proj->xy, \
                                                (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, \
                                                TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib)
   if (variant == 0) { GS_FWD(8); } else if (variant == 1) { GS_FWD(16); } else { GS_FWD(4); }
@@ -651,17 +693,17 @@ int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const u
 
 GS_API int gs_render_fwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
                          int width, int height, const float* bg, float* img, float* final_T, uint32_t* n_contrib,
-                         int variant, const uint32_t* tile_order, const uint16_t* block_masks, gs_stream_t stream) {
+                         int variant, const gs_schedule* sched, gs_stream_t stream) {
   return gs_render_fwd_impl(proj, sorted_vals, ranges, n_units, width, height, bg, img, final_T, n_contrib, variant,
-                            tile_order, block_masks, (cudaStream_t)stream);
+                            sched, (cudaStream_t)stream);
 }
 
 int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
                       int width, int height, const float* bg, const float* final_T, const uint32_t* n_contrib,
                       const float* dL_dimg, const gs_grad2d* g2d, int64_t n_proj, int variant,
-                      const uint32_t* tile_order, const uint16_t* block_masks, cudaStream_t s) {
+                      const gs_schedule* sched, const float* img, cudaStream_t s) {
   if (!proj || !proj->xy || !proj->conic_op || !proj->rgb || !sorted_vals || !ranges || !bg || !final_T ||
-      !n_contrib || !dL_dimg || !g2d || !g2d->dxy || !g2d->dconic_op || !g2d->drgb || n_units < 1 ||
+      !n_contrib || !dL_dimg || !g2d || !g2d->dxy || !g2d->dconic_op || !g2d->drgb || n_units < 1 || (sched && !img) ||
       n_units > GS_MAX_UNITS || width <= 0 || height <= 0 || n_proj < 0 || variant < 0 || variant > 2)
     return GS_ERR_INVALID;
   if (cudaMemsetAsync(g2d->dxy, 0, sizeof(float) * 2 * (size_t)n_proj, s) != cudaSuccess ||
@@ -671,14 +713,15 @@ int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const ui
   int TX = (width + TILE - 1) / TILE, TY = (height + TILE - 1) / TILE;
   dim3 grid(TX * TY * n_units);
 #define GS_BWD(BW)                                                                                                   \
-  if (block_masks)                                                                                                   \
-    k_render_bwd_m<BW><<<dim3(grid.x * 8), 32, 0, s>>>((const uint2*)ranges, tile_order, sorted_vals, block_masks,  \
-                                                 (const float2*)proj->xy, (const float4*)proj->conic_op,            \
-                                                 (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], \
-                                                 bg[2], final_T, n_contrib, dL_dimg, g2d->dxy, g2d->dconic_op,      \
-                                                 g2d->drgb);                                                         \
+  if (sched)                                                                                                         \
+    k_render_bwd_m<BW><<<dim3((unsigned)(sched->max_jobs * 8)), 32, 0, s>>>(                                        \
+        (const uint2*)ranges, sched->tile_order, sched->job_base, sched->jobs, sched->chunk,                         \
+        (const float4*)sched->checkpoints, sorted_vals, sched->block_masks, (const float2*)proj->xy,                 \
+        (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX, TX * TY, TX * TY * n_units,     \
+        bg[0], bg[1], bg[2],                                                                                         \
+        img, final_T, n_contrib, dL_dimg, g2d->dxy, g2d->dconic_op, g2d->drgb);                                      \
   else                                                                                                               \
-    k_render_bwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, tile_order, sorted_vals, (const float2*)proj->xy, \
+    k_render_bwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, nullptr, sorted_vals, (const float2*)proj->xy, \
                                                (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height,  \
                                                TX, TX * TY, bg[0], bg[1], bg[2], final_T, n_contrib, dL_dimg, g2d->dxy, \
                                                g2d->dconic_op, g2d->drgb)

@@ -35,8 +35,11 @@ constexpr int SCATTER_DYN_SMEM = RS_TILE * (int)(sizeof(uint64_t) + sizeof(uint3
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsLayout {
-  size_t offsets, bsums, keys0, keys1, vals0, vals1, hist, totals, cur, order, total;
+  size_t offsets, bsums, keys0, keys1, vals0, vals1, hist, totals, cur, order, jscan, total;
 };
+
+// per-(unit, tile) scan scratch is sized for the largest tile grid (4K, 256 units)
+constexpr int64_t MAX_SCHED_TILES = (int64_t)GS_MAX_UNITS * 240 * 135;
 
 WsLayout ws_layout(int64_t P, int64_t C) {
   WsLayout L;
@@ -53,6 +56,7 @@ WsLayout ws_layout(int64_t P, int64_t C) {
   L.totals = o; o += align256(sizeof(uint32_t) * RS_BINS * MAX_PASSES);
   L.cur = o; o += align256(sizeof(int32_t) * (MAX_PASSES + 1));
   L.order = o; o += align256(sizeof(uint32_t) * 66);
+  L.jscan = o; o += align256(sizeof(uint32_t) * (size_t)((MAX_SCHED_TILES + SCAN_BLOCK - 1) / SCAN_BLOCK + 1));
   L.total = o;
   return L;
 }
@@ -406,6 +410,27 @@ __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ k0,
   }
 }
 
+// number of chunks of each list, in tile order
+__global__ void k_chunk_count(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order, int NT, int K,
+                              uint32_t* __restrict__ counts) {
+  int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= NT) return;
+  uint2 r = ranges[order[o]];
+  counts[o] = (r.y - r.x + (uint32_t)K - 1u) / (uint32_t)K;
+}
+
+// (order position, chunk) of every chunk job
+__global__ void k_chunk_jobs(const uint32_t* __restrict__ job_base, int NT, int64_t max_jobs,
+                             uint32_t* __restrict__ jobs) {
+  int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= NT) return;
+  uint32_t b = job_base[o], e = job_base[o + 1];
+  for (uint32_t j = b; j < e && (int64_t)j < max_jobs; ++j) {
+    jobs[2 * (int64_t)j] = (uint32_t)o;
+    jobs[2 * (int64_t)j + 1] = j - b;
+  }
+}
+
 int bits_for(int64_t n) {
   int b = 0;
   while (((int64_t)1 << b) < n) ++b;
@@ -436,10 +461,36 @@ GS_API size_t gs_bin_sort_workspace_size(int64_t n_proj, int64_t max_instances) 
 // The sort chain, shared by gs_bin_sort and the fixed-scratch variant.
 int gs_tile_order_impl(const uint32_t* ranges, int n, uint32_t* ws, uint32_t* order, cudaStream_t s);
 
+// Tile order, then the chunk jobs in that order.
+int gs_schedule_jobs(const uint32_t* ranges, int NT, char* order_ws, char* scan_ws, const gs_schedule* sched,
+                     cudaStream_t s) {
+  int r = gs_tile_order_impl(ranges, NT, (uint32_t*)order_ws, sched->tile_order, s);
+  if (r != GS_OK) return r;
+  unsigned nb = (unsigned)((NT + 255) / 256);
+  k_chunk_count<<<nb, 256, 0, s>>>((const uint2*)ranges, sched->tile_order, NT, sched->chunk, sched->job_base);
+  r = gs_scan_u32(sched->job_base, sched->job_base, NT, scan_ws, sched->job_base + NT, s);
+  if (r != GS_OK) return r;
+  k_chunk_jobs<<<nb, 256, 0, s>>>(sched->job_base, NT, sched->max_jobs, sched->jobs);
+  return gs_check_launch();
+}
+
+int gs_schedule_check(const gs_schedule* sched, int n_units, int n_tiles, int64_t max_instances) {
+  if (!sched) return GS_OK;
+  if (!sched->tile_order || !sched->block_masks || !sched->job_base || !sched->jobs || !sched->checkpoints ||
+      sched->chunk < 32 || (sched->chunk & 31))
+    return GS_ERR_INVALID;
+  int64_t NT = (int64_t)n_units * n_tiles;
+  if (NT > MAX_SCHED_TILES) return GS_ERR_INVALID;
+  if (sched->max_jobs < NT + max_instances / sched->chunk + 1) return GS_ERR_INVALID;
+  if (sched->max_checkpoints < max_instances / sched->chunk + 1) return GS_ERR_INVALID;
+  return GS_OK;
+}
+
 int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int height, int64_t max_instances,
                      void* workspace, size_t workspace_bytes, uint32_t* sorted_vals, uint32_t* ranges,
-                     uint32_t* d_num_instances, uint32_t* tile_order, uint16_t* block_masks, int* d_status,
-                     cudaStream_t s) {
+                     uint32_t* d_num_instances, const gs_schedule* sched, int* d_status, cudaStream_t s) {
+  uint32_t* tile_order = sched ? sched->tile_order : nullptr;
+  uint16_t* block_masks = sched ? sched->block_masks : nullptr;
   UnitTable U;
   int64_t P = 0;
   if (!proj || !proj->xy || !proj->depth || !proj->radius || !proj->tiles || width <= 0 || height <= 0 ||
@@ -452,6 +503,7 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
   if (workspace_bytes < L.total || ((uintptr_t)workspace & 255u)) return GS_ERR_INVALID;
   int TX = (width + TILE - 1) / TILE, TY = (height + TILE - 1) / TILE;
   int n_tiles = TX * TY;
+  if (gs_schedule_check(sched, U.n, n_tiles, max_instances) != GS_OK) return GS_ERR_INVALID;
   int tile_bits = bits_for(n_tiles);
   int unit_bits = bits_for(U.n);
   if (tile_bits + unit_bits > 32) return GS_ERR_INVALID;
@@ -475,7 +527,7 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
       cudaMemsetAsync(d_num_instances, 0, sizeof(uint32_t), s) != cudaSuccess)
     return GS_ERR_CUDA;
   if (P == 0) {
-    if (tile_order) return gs_tile_order_impl(ranges, n_tiles * U.n, (uint32_t*)(ws + L.order), tile_order, s);
+    if (sched) return gs_schedule_jobs(ranges, n_tiles * U.n, ws + L.order, ws + L.jscan, sched, s);
     return gs_check_launch();
   }
   int64_t nsb = (P + SCAN_BLOCK - 1) / SCAN_BLOCK;
@@ -502,21 +554,31 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
         k0, k1, v0, v1, cur, passes, d_num_instances, tile_bits, n_tiles, TX, ranges, sorted_vals,
         (const float2*)proj->xy, (const float4*)proj->conic_op, block_masks);
   }
-  if (tile_order) return gs_tile_order_impl(ranges, n_tiles * U.n, (uint32_t*)(ws + L.order), tile_order, s);
+  if (sched) return gs_schedule_jobs(ranges, n_tiles * U.n, ws + L.order, ws + L.jscan, sched, s);
   return gs_check_launch();
 }
 
 GS_API int gs_bin_sort(const gs_proj* proj, const gs_units* units, int width, int height, int64_t max_instances,
                        void* workspace, size_t workspace_bytes, uint32_t* sorted_vals, uint32_t* ranges,
-                       uint32_t* d_num_instances, uint32_t* tile_order, uint16_t* block_masks, int* d_status,
-                       gs_stream_t stream) {
+                       uint32_t* d_num_instances, const gs_schedule* sched, int* d_status, gs_stream_t stream) {
   return gs_bin_sort_impl(proj, units, width, height, max_instances, workspace, workspace_bytes, sorted_vals,
-                          ranges, d_num_instances, tile_order, block_masks, d_status, (cudaStream_t)stream);
+                          ranges, d_num_instances, sched, d_status, (cudaStream_t)stream);
+}
+
+GS_API int gs_schedule_sizes(int n_units, int width, int height, int64_t max_instances, int chunk, int64_t* max_jobs,
+                             int64_t* max_checkpoints) {
+  if (n_units < 1 || width <= 0 || height <= 0 || max_instances < 0 || chunk < 32 || (chunk & 31) || !max_jobs ||
+      !max_checkpoints)
+    return GS_ERR_INVALID;
+  int64_t nt = (int64_t)n_units * ((width + TILE - 1) / TILE) * ((height + TILE - 1) / TILE);
+  *max_jobs = nt + max_instances / chunk + 1;
+  *max_checkpoints = max_instances / chunk + 1;
+  return GS_OK;
 }
 
 int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
                        int width, int height, const float* bg, float* img, float* final_T, uint32_t* n_contrib,
-                       int variant, const uint32_t* tile_order, const uint16_t* block_masks, cudaStream_t s);
+                       int variant, const gs_schedule* sched, cudaStream_t s);
 
 GS_API int gs_merge_render(const float* params, int64_t n_gauss, int sh_degree, const gs_owned* owned,
                            const gs_camera* cam, int width, int height, const float* bg, const gs_proj* proj,
@@ -529,8 +591,8 @@ GS_API int gs_merge_render(const float* params, int64_t n_gauss, int sh_degree, 
   int r = gs_preprocess(params, n_gauss, sh_degree, &one, cam, width, height, owned, proj, d_status, stream);
   if (r != GS_OK) return r;
   r = gs_bin_sort_impl(proj, &one, width, height, max_instances, workspace, workspace_bytes, sorted_vals, ranges,
-                       d_num_instances, nullptr, nullptr, d_status, (cudaStream_t)stream);
+                       d_num_instances, nullptr, d_status, (cudaStream_t)stream);
   if (r != GS_OK) return r;
   return gs_render_fwd_impl(proj, sorted_vals, ranges, 1, width, height, bg, img, final_T, n_contrib, 0, nullptr,
-                            nullptr, (cudaStream_t)stream);
+                            (cudaStream_t)stream);
 }

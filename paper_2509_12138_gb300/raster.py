@@ -13,7 +13,9 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import GsCamera, GsGrad2d, GsOwned, GsProj, GsUnits, check
+from ._lib import GsCamera, GsGrad2d, GsOwned, GsProj, GsSchedule, GsUnits, check
+
+CHUNK = 1024  # list entries per backward chunk job
 
 TILE = 16
 
@@ -138,9 +140,10 @@ class Frame:
 
     def __init__(self, n_gauss: int, units: Units, width: int, height: int, sh_degree: int, device="cuda",
                  max_instances: int | None = None, with_backward: bool = True, with_loss: bool = True,
-                 variant: int = 0):
+                 variant: int = 0, chunk: int = CHUNK):
         self.L = _lib.load()
         self.variant = int(variant)
+        self.chunk = int(chunk)
         self.use_masks = True  # per-instance block masks from the sort drive the blend kernels' culling
         self.device = torch.device(device)
         self.N = int(n_gauss)
@@ -165,7 +168,6 @@ class Frame:
         self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
         self.set_capacity(max_instances if max_instances is not None else max(4 * P, 1024))
         self.ranges = torch.zeros((U * self.n_tiles, 2), dtype=torch.int32, device=self.device)
-        self.tile_order = torch.zeros(U * self.n_tiles, dtype=torch.int32, device=self.device)
         self.img = torch.zeros((U, 3, self.H, self.W), **f32)
         self.final_T = torch.zeros((U, self.H, self.W), **f32)
         self.n_contrib = torch.zeros((U, self.H, self.W), dtype=torch.int32, device=self.device)
@@ -180,8 +182,8 @@ class Frame:
             self.g2d = GsGrad2d(self.dxy.data_ptr(), self.dco.data_ptr(), self.drgb.data_ptr())
             self.grads = torch.zeros((self.planes, max(self.N, 1), 4), **f32)
 
-    def _masks(self):
-        return _ptr(self.block_masks) if self.use_masks else None
+    def _sched(self):
+        return C.byref(self.sched) if self.use_masks else None
 
     def set_capacity(self, max_instances: int):
         self.cap = int(max_instances)
@@ -189,6 +191,16 @@ class Frame:
         self.sort_ws = _alloc_ws(ws, self.device)
         self.sorted_vals = torch.zeros(max(self.cap, 1), dtype=torch.int32, device=self.device)
         self.block_masks = torch.zeros(max(self.cap, 1), dtype=torch.int16, device=self.device)
+        mj, mc = C.c_int64(), C.c_int64()
+        check(self.L.gs_schedule_sizes(self.units.n, self.W, self.H, self.cap, self.chunk, C.byref(mj), C.byref(mc)),
+              "gs_schedule_sizes")
+        nt = self.units.n * self.n_tiles
+        self.tile_order = torch.zeros(nt, dtype=torch.int32, device=self.device)
+        self.job_base = torch.zeros(nt + 1, dtype=torch.int32, device=self.device)
+        self.jobs = torch.zeros(2 * mj.value, dtype=torch.int32, device=self.device)
+        self.checkpoints = torch.zeros((mc.value, 256, 4), dtype=torch.float32, device=self.device)
+        self.sched = GsSchedule(self.tile_order.data_ptr(), self.block_masks.data_ptr(), self.job_base.data_ptr(),
+                                self.jobs.data_ptr(), self.checkpoints.data_ptr(), mj.value, mc.value, self.chunk)
         self.num_instances = torch.zeros(1, dtype=torch.int32, device=self.device)
 
     # -- steps
@@ -201,14 +213,14 @@ class Frame:
     def sort(self):
         check(self.L.gs_bin_sort(C.byref(self.proj), C.byref(self.units.struct), self.W, self.H, self.cap,
                                  _ptr(self.sort_ws), self.sort_ws.numel(), _ptr(self.sorted_vals), _ptr(self.ranges),
-                                 _ptr(self.num_instances), _ptr(self.tile_order), self._masks(), _ptr(self.status),
-                                 _stream()), "gs_bin_sort")
+                                 _ptr(self.num_instances), self._sched(), _ptr(self.status), _stream()),
+              "gs_bin_sort")
 
     def render(self, bg):
         bgc = (C.c_float * 3)(*[float(x) for x in bg])
         check(self.L.gs_render_fwd(C.byref(self.proj), _ptr(self.sorted_vals), _ptr(self.ranges), self.units.n,
                                    self.W, self.H, bgc, _ptr(self.img), _ptr(self.final_T), _ptr(self.n_contrib),
-                                   self.variant, _ptr(self.tile_order), self._masks(), _stream()), "gs_render_fwd")
+                                   self.variant, self._sched(), _stream()), "gs_render_fwd")
         return self.img
 
     def forward(self, params, cams_dev, bg, owned=None):
@@ -238,9 +250,9 @@ class Frame:
         bgc = (C.c_float * 3)(*[float(x) for x in bg])
         d = self.dimg if dimg is None else dimg
         check(self.L.gs_blend_bwd(C.byref(self.proj), _ptr(self.sorted_vals), _ptr(self.ranges), self.units.n,
-                                  self.W, self.H, bgc, _ptr(self.final_T), _ptr(self.n_contrib), _ptr(d),
-                                  C.byref(self.g2d), self.P, self.variant, _ptr(self.tile_order), self._masks(),
-                                  _stream()), "gs_blend_bwd")
+                                  self.W, self.H, bgc, _ptr(self.img), _ptr(self.final_T), _ptr(self.n_contrib),
+                                  _ptr(d), C.byref(self.g2d), self.P, self.variant, self._sched(), _stream()),
+              "gs_blend_bwd")
 
     def project_backward(self, params, cams_dev):
         check(self.L.gs_project_bwd(_ptr(params), self.N, self.deg, C.byref(self.units.struct), _ptr(cams_dev),
@@ -253,8 +265,8 @@ class Frame:
         d = self.dimg if dimg is None else dimg
         check(self.L.gs_render_bwd(_ptr(params), self.N, self.deg, C.byref(self.units.struct), _ptr(cams_dev),
                                    C.byref(self.proj), _ptr(self.sorted_vals), _ptr(self.ranges), self.W, self.H,
-                                   bgc, _ptr(self.final_T), _ptr(self.n_contrib), _ptr(d), C.byref(self.g2d),
-                                   _ptr(self.grads), self.variant, _ptr(self.tile_order), self._masks(), _stream()),
+                                   bgc, _ptr(self.img), _ptr(self.final_T), _ptr(self.n_contrib), _ptr(d),
+                                   C.byref(self.g2d), _ptr(self.grads), self.variant, self._sched(), _stream()),
               "gs_render_bwd")
         return self.grads
 

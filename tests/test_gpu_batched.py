@@ -234,28 +234,32 @@ def test_fused_projection_backward_adam_matches_separate(n_views):
     assert torch.allclose(pa, pb, rtol=1e-5, atol=1e-5)
 
 
-def test_block_masks_and_tile_order_do_not_change_results():
-    """Per-instance block masks and the heaviest-first tile order only skip work / reorder blocks: images,
-    n_contrib are bit-identical and gradients equal up to atomic order, with and without them."""
+@pytest.mark.parametrize("chunk", [32, 96, 1024])
+def test_schedule_does_not_change_results(chunk):
+    """The blend schedule (heaviest-first order, per-instance block masks, backward replayed in chunks from
+    forward checkpoints) only skips and reorders work: images and n_contrib are bit-identical and gradients
+    equal up to atomic order, with and without it; small chunks put many checkpoints on every list."""
     n, deg, W, H = 3000, 1, 150, 110
     g, cams = scenes.random_scene(n, deg, 31, W, H)
     params = gs.pack_params(g, deg)
     camd = gs.pack_cameras(cams)
     gt, mask = scenes.random_gt(W, H, 32)
     res = []
-    for use_masks, order in ((False, False), (True, True), (True, False)):
-        fr = gs.Frame(n, gs.Units.single(n), W, H, deg)
-        fr.use_masks = use_masks
+    for use_sched in (False, True):
+        fr = gs.Frame(n, gs.Units.single(n), W, H, deg, chunk=chunk)
+        fr.use_masks = use_sched
         fr.fit_capacity(params, camd)
-        fr.preprocess(params, camd)
-        fr.sort()
-        if not order:
-            fr.tile_order.copy_(torch.arange(fr.tile_order.numel(), dtype=torch.int32, device="cuda"))
-        fr.render(BG)
+        fr.forward(params, camd, BG)
         fr.loss(torch.from_numpy(gt).cuda()[None], torch.from_numpy(mask).cuda()[None], 0.2)
         fr.backward(params, camd, BG)
         torch.cuda.synchronize()
-        res.append((fr.img.clone(), fr.n_contrib.clone(), fr.grads.clone()))
-    for r in res[1:]:
-        assert torch.equal(res[0][0], r[0]) and torch.equal(res[0][1], r[1])
-        assert torch.allclose(res[0][2], r[2], rtol=1e-4, atol=1e-7)
+        assert fr.read_status() == 0
+        res.append((fr.img.clone(), fr.n_contrib.clone(), fr.grads.clone(), fr.dco.clone()))
+        if use_sched:
+            lens = (fr.ranges[:, 1] - fr.ranges[:, 0]).cpu().numpy()
+            assert int(fr.job_base[-1].item()) == int(np.sum((lens + chunk - 1) // chunk))
+    a, b = res
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    sc = float(a[2].abs().max())
+    assert torch.allclose(a[2], b[2], rtol=1e-3, atol=1e-5 * sc)
+    assert torch.allclose(a[3], b[3], rtol=1e-3, atol=1e-5 * float(a[3].abs().max()))
