@@ -36,6 +36,13 @@ WORKLOADS = {
     "iso200k-540p": dict(n=200_000, modes=8, views=16, W=960, H=540),
     # small device footprint (about 2.5 GB) for Nsight Compute captures of single kernels
     "iso2M-1080p-prof": dict(n=2_000_000, modes=16, views=4, W=1920, H=1080),
+    # batched form: 8 x-slabs with 5% ghosts, uneven populations (28M), 16 masked views each, one
+    # graph-captured launch chain per step (metric: (partition, view) units per second)
+    "batched28M-1080p": dict(n=28_000_000, modes=8, views=16, W=1920, H=1080,
+                             slabs=[500_000, 1_500_000, 2_500_000, 3_500_000, 4_000_000, 4_500_000, 5_500_000,
+                                    6_000_000]),
+    # merged render of 8 ghost-celled partitions, 100M Gaussians (SH3), 3840x2160, render only
+    "merge100M-4k": dict(n=100_000_000, modes=32, views=8, W=3840, H=2160),
 }
 METRIC = "train iters/s & render Mpix/s at 10M Gaussians 1080p; PSNR vs plain form"
 LAMBDA_SSIM = 0.2
@@ -391,6 +398,10 @@ def main():
         return run_reference(args, wl, rank, world, config)
     if args.experiment == "learned-init":
         return run_learned_init_experiment(args)
+    if args.workload.startswith("batched"):
+        return run_batched(args, wl)
+    if args.workload.startswith("merge"):
+        return run_merge(args, wl)
     import torch
     if not torch.cuda.is_available():
         print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
@@ -473,6 +484,85 @@ def run_learned_init_experiment(args):
                                   [round(x, 3) for x in h_plain.psnr]],
                         "learned": [h_learn.steps, [round(x, 3) for x in h_learn.seconds],
                                     [round(x, 3) for x in h_learn.psnr]]}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_batched(args, wl):
+    """Batched form: all 8 partitions x views-per-step units as one graph-captured step, autotuned."""
+    import torch
+    import paper_2509_12138_gb300 as gs
+    from paper_2509_12138_gb300 import train as T, tune, workload
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    ps = workload.partitioned_scene(wl["slabs"], wl["modes"], wl["views"], wl["W"], wl["H"], n_parts=8, ghost=0.05)
+    train_v, test_v = T.split_views(wl["views"], 8)
+    init = gs.pack_params(ps.init, 3)
+
+    def make(variant, vps):
+        return T.BatchedTrainer(init.clone(), 3, ps.offsets, ps.cams_dev, ps.gt, ps.mask, train_v,
+                                views_per_step=vps, variant=variant, lr_steps=7000)
+
+    best, table = tune.autotune(make, f"batched28M-{wl['W']}x{wl['H']}", candidates=[(0, 1), (1, 1), (0, 2)],
+                                steps=3, warmup=2)
+    tr = make(*best)
+    sec = tune.time_trainer(tr, steps=args.steps, warmup=args.warmup)
+    st = tr.check()
+    line = {"metric": "batched train step, 8 ghost-celled partitions (28M Gaussians) x views per step, 1080p",
+            "value": round(tr.units.n / sec, 3), "unit": "(partition, view) units/s",
+            "steps_per_s": round(1.0 / sec, 3), "ms_per_step": round(sec * 1e3, 3), "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": args.workload, "gaussians_with_ghosts": int(ps.offsets[-1]),
+                                            "slab_sizes": wl["slabs"], "views_per_partition": wl["views"],
+                                            "graph": True, "autotune": {"best": best, "units_per_s": table}},
+            "status": st}
+    print(json.dumps(line))
+    return 0
+
+
+def run_merge(args, wl):
+    """Render-only merged scene: ghost-filtered render of all partitions at 4K."""
+    import torch
+    import paper_2509_12138_gb300 as gs
+    from paper_2509_12138_gb300 import workload
+    import synth
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    params, xs = workload.interface_gaussians_device(wl["n"], wl["modes"], seed=0)
+    params, off, boxes, closed = workload.partition_device(params, xs, 8, 0.05)
+    del xs
+    torch.cuda.empty_cache()
+    N = params.shape[1]
+    owned = gs.Owned(off, boxes, closed)
+    cams = synth.orbital_cameras(wl["views"], 1.5, center=(0.5, 0.5, 0.5), width=wl["W"], height=wl["H"])
+    camd = gs.pack_cameras(cams)
+    fr = gs.Frame(N, gs.Units.single(N), wl["W"], wl["H"], 3, with_backward=False, with_loss=False,
+                  max_instances=1 << 20)
+    need = max(fr.fit_capacity(params, camd[v * 96:(v + 1) * 96], owned) for v in range(wl["views"]))
+    fr.set_capacity(int(need * 1.1) + 4096)
+    V = wl["views"]
+    for k in range(args.warmup):
+        fr.forward(params, camd[(k % V) * 96:(k % V + 1) * 96], (1.0, 1.0, 1.0), owned)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for k in range(args.steps):
+        v = (args.warmup + k) % V
+        fr.forward(params, camd[v * 96:(v + 1) * 96], (1.0, 1.0, 1.0), owned)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    st = fr.read_status()
+    kept = int((fr.radius > 0).sum())
+    line = {"metric": "merged render (ghost filter + projection + sort + blend), 100M Gaussians SH3, 3840x2160",
+            "value": round(wl["W"] * wl["H"] / (ms * 1e-3) / 1e6, 2), "unit": "Mpix/s", "ms_per_frame": round(ms, 3),
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": args.workload, "gaussians_with_ghosts": N,
+                                            "partitions": 8, "ghost": 0.05, "visible_after_filter_last_view": kept,
+                                            "instances_last_view": fr.instances()},
+            "status": st}
     print(json.dumps(line))
     return 0
 

@@ -163,3 +163,73 @@ def partitioned_scene(slab_counts, n_modes: int, n_views: int, width: int, heigh
     return PartitionedScene(part=part, sh_degree=sh_degree, width=W, height=H, cams=cams,
                             cams_dev=pack_cameras(cams, device), gt=gt, mask=mask, gt_full=gt_full,
                             mask_full=mask_full, init=init, pts=pts, spacing=spacing)
+
+
+def interface_gaussians_device(n: int, n_modes: int, seed: int, sh_degree: int = 3, device="cuda",
+                               chunk: int = 1 << 24):
+    """Plain-initialised Gaussians on the perturbed interface generated directly on the device (for
+    render-only scenes too large to stage through host memory).  Same field as synth.interface_points
+    (the amplitudes, directions and phases come from synth's seeded streams); positions from a seeded
+    torch generator.  Returns (planes [n_planes, n, 4], x coordinates [n])."""
+    from .raster import param_planes
+    s = synth.streams(seed, ["amp", "dir", "phase"])
+    k = torch.arange(1, n_modes + 1, dtype=torch.float64)
+    amp = torch.from_numpy(s["amp"].uniform(0.0, 1.0, n_modes)) / k
+    theta = torch.from_numpy(s["dir"].uniform(0.0, 2.0 * math.pi, n_modes))
+    phase = torch.from_numpy(s["phase"].uniform(0.0, 2.0 * math.pi, n_modes))
+    kx, ky = (k * torch.cos(theta)).float().to(device), (k * torch.sin(theta)).float().to(device)
+    amp, phase = amp.float().to(device), phase.float().to(device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    npl = param_planes(sh_degree)
+    params = torch.zeros((npl, n, 4), dtype=torch.float32, device=device)
+    xs = torch.empty(n, dtype=torch.float32, device=device)
+    area = 0.0
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        x = torch.rand(b - a, generator=gen, device=device)
+        y = torch.rand(b - a, generator=gen, device=device)
+        arg = 2.0 * math.pi * (x[:, None] * kx + y[:, None] * ky) + phase
+        h = 0.1 * (torch.sin(arg) * amp).sum(1)
+        dh = 0.1 * torch.cos(arg) * amp * 2.0 * math.pi
+        hx, hy = (dh * kx).sum(1), (dh * ky).sum(1)
+        nz = 1.0 / torch.sqrt(hx * hx + hy * hy + 1.0)
+        area += float((1.0 / nz).sum())
+        z = 0.5 + h
+        params[0, a:b, 0], params[0, a:b, 1], params[0, a:b, 2] = x, y, z
+        zn = (z - 0.2) / 0.6
+        ndl = torch.abs((-hx * 0.3 - hy * 0.5 + 0.8) * nz / math.sqrt(0.98))
+        shade = 0.2 + 0.8 * ndl
+        col = torch.stack([0.2 + 0.75 * zn, 0.4 + 0.2 * zn, 0.9 - 0.7 * zn], 1) * shade[:, None]
+        dc = (col.clamp(0, 1) - 0.5) / Y00
+        params[3, a:b, 0:3] = dc
+        xs[a:b] = x
+    spacing = (0.5 + 0.75 + 0.9375) / 3.0 / math.sqrt(n / (area / n))
+    params[1, :, 0:3] = math.log(spacing)
+    params[1, :, 3] = math.log(0.5 / 0.5)  # opacity 0.5 for a visible render-only scene
+    params[2, :, 0] = 1.0
+    return params, xs
+
+
+def partition_device(params: torch.Tensor, xs: torch.Tensor, n_parts: int = 8, ghost: float = 0.05):
+    """Partition-major copy of a planes tensor by x-slabs with ghost layers (as partition.slab_partition),
+    built on the device.  Returns (planes, part_offsets, owned boxes, closed_hi)."""
+    from .partition import BIG
+    edges = np.linspace(0.0, 1.0, n_parts + 1)
+    w = 1.0 / n_parts
+    idx = []
+    for k in range(n_parts):
+        a = edges[k] - (ghost * w if k > 0 else 0.0)
+        b = edges[k + 1] + (ghost * w if k < n_parts - 1 else 0.0)
+        sel = (xs >= a) & ((xs <= b) if k == n_parts - 1 else (xs < b))
+        idx.append(torch.nonzero(sel).squeeze(1))
+    offsets = np.concatenate([[0], np.cumsum([len(i) for i in idx])]).astype(np.int64)
+    order = torch.cat(idx)
+    out = params[:, order].contiguous()
+    boxes = np.zeros((n_parts, 6), np.float32)
+    boxes[:, 0], boxes[:, 3] = edges[:-1], edges[1:]
+    boxes[:, 1] = boxes[:, 2] = -BIG
+    boxes[:, 4] = boxes[:, 5] = BIG
+    closed = np.full(n_parts, 0b110, np.int32)
+    closed[-1] |= 1
+    return out, offsets, boxes, closed
