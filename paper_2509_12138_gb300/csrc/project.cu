@@ -576,12 +576,32 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam(float4* __restrict__ p
   }
 }
 
+// Async 16-byte global -> shared copies (cp.async, L2 only); each thread
+// copies and later reads only its own slots, so a thread-local wait suffices.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NG>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NG) : "memory"); }
+
+constexpr int PBA_T = 64;  // Gaussians per block of the staged kernel
+constexpr int PBA_R = 4;   // moment planes (m and v) in flight per thread
+
 // Projection backward fused with Adam for Gaussians that belong to exactly
-// one unit (one view of one partition): the SH planes are streamed twice
-// (colour and clamp first, then each plane's gradient and Adam update), so
-// neither the 48 coefficients nor their gradients are held in registers.
+// one unit (one view of one partition).  On entry every thread starts async
+// copies of its Gaussian's parameter planes (one commit group) and of the
+// first PBA_R planes of its Adam moments, in the order the updates use them
+// (SH planes, then mean, scale/opacity, rotation), into its own
+// shared-memory slots; each update then starts the copy of the moments
+// PBA_R planes ahead into the slot it has just consumed.  The geometry
+// gradient runs once the parameters have landed.  The SH planes are read
+// twice from shared memory (colour and clamp first, then each plane's
+// gradient and update), so neither the 48 coefficients nor their gradients
+// are held in registers.
 template <int DEG>
-__global__ void __launch_bounds__(128) k_project_bwd_adam1(float4* __restrict__ params, int64_t N, UnitTable U,
+__global__ void __launch_bounds__(PBA_T) k_project_bwd_adam1(float4* __restrict__ params, int64_t N, UnitTable U,
                                                            const gs_camera* __restrict__ cams,
                                                            const int* __restrict__ radius,
                                                            const float2* __restrict__ gxy,
@@ -604,6 +624,25 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam1(float4* __restrict__ 
   __syncthreads();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
+  extern __shared__ float4 s_stage[];  // [NPL][PBA_T] parameters, then [PBA_R][2][PBA_T] m, v ring
+  const int tl = threadIdx.x;
+  float4* sP = s_stage;
+  float4* sR = s_stage + NPL * PBA_T;
+  // update sequence q = 0 .. NPL - 1 takes plane (q + 3) % NPL: the SH planes, then 0, 1, 2
+  auto mv_copy = [&](int q) {
+    if (q < NPL) {
+      int k = (q + 3) % NPL;
+      float4* slot = sR + (q % PBA_R) * 2 * PBA_T;
+      cp_async16(slot + tl, m + k * N + i);
+      cp_async16(slot + PBA_T + tl, v + k * N + i);
+    }
+    cp_async_commit();  // one group per sequence step (empty past the end) keeps the counting uniform
+  };
+  #pragma unroll
+  for (int k = 0; k < NPL; ++k) cp_async16(sP + k * PBA_T + tl, params + k * N + i);
+  cp_async_commit();
+  #pragma unroll
+  for (int q = 0; q < PBA_R; ++q) mv_copy(q);
   float ibc1 = 1.f / (1.f - powf(b1, (float)t)), ibc2 = 1.f / (1.f - powf(b2, (float)t));
   // the unit containing i (units are disjoint here)
   int uu = -1;
@@ -613,7 +652,8 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam1(float4* __restrict__ 
     if (l >= 0 && l < U.proj_base[u + 1] - U.proj_base[u]) { uu = u; pidx = U.proj_base[u] + l; break; }
   }
   bool vis = uu >= 0 && __ldg(radius + pidx) > 0;
-  float4 mean = params[i], sop = params[N + i], quat = params[2 * N + i];
+  cp_async_wait<PBA_R>();  // this thread's parameter planes have landed
+  float4 mean = sP[tl], sop = sP[PBA_T + tl], quat = sP[2 * PBA_T + tl];
   float dmean[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, dlogit = 0.f;
   float Y[16], gc[3] = {0.f, 0.f, 0.f}, il = 0.f, dir[3] = {0.f, 0.f, 0.f};
   if (vis) {
@@ -629,7 +669,7 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam1(float4* __restrict__ 
     float col[3] = {0.5f, 0.5f, 0.5f};
     #pragma unroll
     for (int k = 0; k < NP; ++k) {
-      float4 q = params[(3 + k) * N + i];
+      float4 q = sP[(3 + k) * PBA_T + tl];
       const float* qq = &q.x;
       #pragma unroll
       for (int e = 0; e < 4; ++e) {
@@ -739,7 +779,9 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam1(float4* __restrict__ 
   #pragma unroll
   for (int k = 0; k < NP; ++k) {
     int64_t o = (3 + k) * N + i;
-    float4 P = params[o];
+    float4 P = sP[(3 + k) * PBA_T + tl];
+    cp_async_wait<PBA_R - 1>();  // the moments of sequence step k
+    const float4* slot = sR + (k % PBA_R) * 2 * PBA_T;
     float* pp = &P.x;
     float G[4];
     #pragma unroll
@@ -752,10 +794,11 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam1(float4* __restrict__ 
       }
     }
     float4 Gk = make_float4(G[0], G[1], G[2], G[3]);
-    float4 Mv = m[o], Vv = v[o];
+    float4 Mv = slot[tl], Vv = slot[PBA_T + tl];
     adam4(P, Gk, Mv, Vv, s_lr[3 + k], b1, b2, ibc1, ibc2, eps);
     params[o] = P; m[o] = Mv; v[o] = Vv;
     if (grads) grads[o] = Gk;
+    mv_copy(k + PBA_R);  // the slot's values are consumed: refill it PBA_R steps ahead
   }
   if (vis && DEG > 0) {
     float sx, sy, sz;
@@ -771,10 +814,13 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam1(float4* __restrict__ 
   #pragma unroll
   for (int k = 0; k < 3; ++k) {
     int64_t o = k * N + i;
-    float4 Mv = m[o], Vv = v[o];
+    cp_async_wait<PBA_R - 1>();  // the moments of sequence step NP + k
+    const float4* slot = sR + ((NP + k) % PBA_R) * 2 * PBA_T;
+    float4 Mv = slot[tl], Vv = slot[PBA_T + tl];
     adam4(Pv[k], Gp[k], Mv, Vv, s_lr[k], b1, b2, ibc1, ibc2, eps);
     params[o] = Pv[k]; m[o] = Mv; v[o] = Vv;
     if (grads) grads[o] = Gp[k];
+    mv_copy(NP + k + PBA_R);
   }
 }
 
@@ -964,8 +1010,10 @@ GS_API int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, co
       if (a0 < b1 && b0 < a1) disjoint = false;
     }
   if (disjoint) {
+    dim3 grid1((unsigned)((n_gauss + PBA_T - 1) / PBA_T));
+    size_t smem1 = sizeof(float4) * ((size_t)npl + 2 * PBA_R) * PBA_T;  // 23,552 B at degree 3
 #define GS_PBA1(D)                                                                                                \
-  k_project_bwd_adam1<D><<<grid, block, 0, s>>>((float4*)params, n_gauss, U, cams, proj->radius,                 \
+  k_project_bwd_adam1<D><<<grid1, PBA_T, smem1, s>>>((float4*)params, n_gauss, U, cams, proj->radius,            \
                                                 (const float2*)g2d->dxy, (const float4*)g2d->dconic_op,          \
                                                 (const float4*)g2d->drgb, (float4*)m, (float4*)v, lr, lr_steps,   \
                                                 beta1, beta2, eps, d_step, (float4*)grads)

@@ -52,16 +52,6 @@ __device__ __forceinline__ void block_tile(const uint32_t* __restrict__ order, i
   tile = (int)(f % (uint32_t)n_tiles);
 }
 
-// One-warp blocks: block index -> (unit, tile, warp block w of the tile).
-// Each (tile, pixel block) job retires as soon as its own walk ends.
-__device__ __forceinline__ void warp_job(const uint32_t* __restrict__ order, int n_tiles, int& u, int& tile, int& w) {
-  uint32_t j = blockIdx.x >> 3;
-  w = (int)(blockIdx.x & 7u);
-  uint32_t f = order ? order[j] : j;
-  u = (int)(f / (uint32_t)n_tiles);
-  tile = (int)(f % (uint32_t)n_tiles);
-}
-
 // Forward.  Each warp walks its tile's list on its own, 32 records per round
 // (one per lane): a lane loads a record and tests its alpha box against the
 // warp's pixel block; the records that hit are taken in list order, read back
@@ -327,63 +317,32 @@ __device__ __forceinline__ uint32_t warp_block_bits(int w) {
   return bits;
 }
 
-// Forward with per-instance block masks: a warp reads 2 bytes (mask) and 4
-// bytes (record id) per list entry, two rounds ahead, and gathers the records
-// of its hits one round ahead; the blend itself is that of k_render_fwd.
-template <int BW>
-__global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ ranges,
-                                                           const uint32_t* __restrict__ order,
-                                                           const uint32_t* __restrict__ job_base, int K,
-                                                           float4* __restrict__ ckpt,
-                                                           const uint32_t* __restrict__ vals,
-                                                           const uint16_t* __restrict__ masks,
-                                                           const float2* __restrict__ xy,
-                                                           const float4* __restrict__ conic_op,
-                                                           const float4* __restrict__ rgb, int W, int H, int TX,
-                                                           int n_tiles, float bg0, float bg1, float bg2,
-                                                           float* __restrict__ img, float* __restrict__ final_T,
-                                                           uint32_t* __restrict__ n_contrib) {
+// Front-to-back walk of list entries [beg, end) (indices from the list's
+// start `off`) for one warp's pixel block, compositing into (T, c, last) of
+// the lanes that are not done; a lane whose transmittance would fall below
+// T_MIN stops (done).  A warp reads 2 bytes (mask) and 4 bytes (record id)
+// per entry, two rounds ahead, and gathers the records of its hits one round
+// ahead; the blend itself is that of k_render_fwd.
+__device__ __forceinline__ void walk_fwd(const uint32_t* __restrict__ vals, const uint16_t* __restrict__ masks,
+                                         const float2* __restrict__ xy, const float4* __restrict__ conic_op,
+                                         const float4* __restrict__ rgb, uint32_t off, int beg, int end,
+                                         uint32_t wbits, float fx, float fy, Rec* my, float& T, float& c0,
+                                         float& c1, float& c2, int& last, bool& done) {
   const unsigned FULL = 0xffffffffu;
-  __shared__ Rec s_rec[1][32];
-  int u, tile, w;
-  warp_job(order, n_tiles, u, tile, w);
-  int tx = tile % TX, ty = tile / TX;
-  constexpr int BH = 32 / BW, NWX = TILE / BW;
   int lane = threadIdx.x & 31;
-  int px = tx * TILE + (w % NWX) * BW + (lane % BW), py = ty * TILE + (w / NWX) * BH + (lane / BW);
-  uint32_t wbits = warp_block_bits<BW>(w);
-  bool inside = px < W && py < H;
-  uint2 rg = ranges[(int64_t)u * n_tiles + tile];
-  int n = (int)(rg.y - rg.x);
-  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-  int last = 0;
-  bool done = !inside;
-  float fx = (float)px, fy = (float)py;
-  Rec* my = &s_rec[0][0];
-  // round r's record (hit lanes), round r+1's header
   bool h1 = false;
   float2 m1 = make_float2(0.f, 0.f);
   float4 co1 = make_float4(0.f, 0.f, 0.f, 0.f), cc1 = co1;
   uint32_t mk2 = 0, pk2 = 0;
-  if (lane < n) {
-    uint32_t mk = masks[rg.x + lane];
+  if (beg + lane < end) {
+    uint32_t mk = masks[off + beg + lane];
     if (mk & wbits) {
-      uint32_t pk = vals[rg.x + lane];
+      uint32_t pk = vals[off + beg + lane];
       h1 = true; m1 = xy[pk]; co1 = conic_op[pk]; cc1 = rgb[pk];
     }
   }
-  if (32 + lane < n) { mk2 = masks[rg.x + 32 + lane]; pk2 = vals[rg.x + 32 + lane]; }
-  // checkpoints at the interior chunk boundaries b K (b = 1 .. nch - 1) of this list
-  int o = (int)(blockIdx.x >> 3);
-  int nch = (int)(job_base[o + 1] - job_base[o]);
-  int64_t cp0 = (int64_t)job_base[o] - o;  // this list's first checkpoint
-  int pix_local = (py - ty * TILE) * TILE + (px - tx * TILE);
-  int next_b = 1;
-  for (int base = 0; base < n; base += 32) {
-    if (base == next_b * K && next_b < nch) {
-      if (inside) ckpt[(cp0 + next_b - 1) * TILE_PIX + pix_local] = make_float4(T, c0, c1, c2);
-      ++next_b;
-    }
+  if (beg + 32 + lane < end) { mk2 = masks[off + beg + 32 + lane]; pk2 = vals[off + beg + 32 + lane]; }
+  for (int base = beg; base < end; base += 32) {
     if (__all_sync(FULL, done)) break;
     bool hit = h1;
     float2 m = m1;
@@ -392,7 +351,7 @@ __global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ r
     if (h1) { m1 = xy[pk2]; co1 = conic_op[pk2]; cc1 = rgb[pk2]; }
     int k2 = base + 64 + lane;
     mk2 = 0;
-    if (k2 < n) { mk2 = masks[rg.x + k2]; pk2 = vals[rg.x + k2]; }
+    if (k2 < end) { mk2 = masks[off + k2]; pk2 = vals[off + k2]; }
     unsigned mask = __ballot_sync(FULL, hit);
     if (hit) {
       my[lane].a = make_float4(m.x, m.y, co.x, co.y);
@@ -419,8 +378,49 @@ __global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ r
     }
     __syncwarp();
   }
-  for (; next_b < nch; ++next_b)  // boundaries after an early exit: the state is final
-    if (inside) ckpt[(cp0 + next_b - 1) * TILE_PIX + pix_local] = make_float4(T, c0, c1, c2);
+}
+
+// Forward with the blend schedule: one warp per (list, pixel block), lists
+// in tile order (heaviest first).  The warp walks its list in chunks of K
+// entries and stores (T, C) of each pixel in front of every interior chunk
+// boundary: the checkpoints the chunked backward starts from.  After an
+// early exit the remaining checkpoints hold the final state.
+template <int BW>
+__global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ ranges,
+                                                           const uint32_t* __restrict__ order,
+                                                           const uint32_t* __restrict__ job_base, int K,
+                                                           float4* __restrict__ ckpt,
+                                                           const uint32_t* __restrict__ vals,
+                                                           const uint16_t* __restrict__ masks,
+                                                           const float2* __restrict__ xy,
+                                                           const float4* __restrict__ conic_op,
+                                                           const float4* __restrict__ rgb, int W, int H, int TX,
+                                                           int n_tiles, float bg0, float bg1, float bg2,
+                                                           float* __restrict__ img, float* __restrict__ final_T,
+                                                           uint32_t* __restrict__ n_contrib) {
+  __shared__ Rec s_rec[32];
+  int o = (int)(blockIdx.x >> 3), w = (int)(blockIdx.x & 7u);
+  uint32_t f = order[o];
+  int u = (int)(f / (uint32_t)n_tiles), tile = (int)(f % (uint32_t)n_tiles);
+  int tx = tile % TX, ty = tile / TX;
+  constexpr int BH = 32 / BW, NWX = TILE / BW;
+  int lane = threadIdx.x & 31;
+  int px = tx * TILE + (w % NWX) * BW + (lane % BW), py = ty * TILE + (w / NWX) * BH + (lane / BW);
+  uint32_t wbits = warp_block_bits<BW>(w);
+  bool inside = px < W && py < H;
+  uint2 rg = ranges[(int64_t)u * n_tiles + tile];
+  int L = (int)(rg.y - rg.x);
+  int nch = (int)(job_base[o + 1] - job_base[o]);
+  int64_t cp0 = (int64_t)job_base[o] - o;  // this list's first checkpoint
+  int pix_local = (py - ty * TILE) * TILE + (px - tx * TILE);
+  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+  int last = 0;
+  bool done = !inside;
+  for (int c = 0; c < max(nch, 1); ++c) {
+    if (c > 0 && inside) ckpt[(cp0 + c - 1) * TILE_PIX + pix_local] = make_float4(T, c0, c1, c2);
+    walk_fwd(vals, masks, xy, conic_op, rgb, rg.x, c * K, min(c * K + K, L), wbits, (float)px, (float)py, s_rec, T,
+             c0, c1, c2, last, done);
+  }
   if (inside) {
     int64_t plane = (int64_t)W * H;
     int64_t pix = (int64_t)py * W + px;
@@ -675,14 +675,12 @@ int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const u
   int TX = (width + TILE - 1) / TILE, TY = (height + TILE - 1) / TILE;
   dim3 grid(TX * TY * n_units);
 #define GS_FWD(BW)                                                                                                  \
-  if (sched)                                                                                                        \
-    k_render_fwd_m<BW><<<dim3(grid.x * 8), 32, 0, s>>>((const uint2*)ranges, sched->tile_order, sched->job_base,  \
-                                                       sched->chunk, (float4*)sched->checkpoints, sorted_vals,   \
-                                                       sched->block_masks,                                        \
-                                                 (const float2*)proj->xy, (const float4*)proj->conic_op,           \
-                                                 (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0],      \
-                                                 bg[1], bg[2], img, final_T, n_contrib);                           \
-  else                                                                                                              \
+  if (sched) {                                                                                                      \
+    k_render_fwd_m<BW><<<dim3(grid.x * 8), 32, 0, s>>>(                                                             \
+        (const uint2*)ranges, sched->tile_order, sched->job_base, sched->chunk, (float4*)sched->checkpoints,        \
+        sorted_vals, sched->block_masks, (const float2*)proj->xy, (const float4*)proj->conic_op,                    \
+        (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib);        \
+  } else                                                                                                            \
     k_render_fwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, nullptr, sorted_vals, (const float2*)proj->xy, \
                                                (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, \
                                                TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib)

@@ -28,7 +28,7 @@ constexpr int SCAN_BLOCK = SCAN_T * SCAN_ITEMS;  // 2048 records per scan block
 constexpr int RS_T = 256;
 constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_T * RS_ITEMS;  // 4096 keys per sort block
-constexpr int RS_BINS = 256;
+constexpr int RS_BINS_MAX = 512;  // digits of up to 9 bits
 constexpr int MAX_PASSES = 8;
 constexpr int SCATTER_DYN_SMEM = RS_TILE * (int)(sizeof(uint64_t) + sizeof(uint32_t));  // 48 KB
 
@@ -52,8 +52,8 @@ WsLayout ws_layout(int64_t P, int64_t C) {
   L.keys1 = o; o += align256(sizeof(uint64_t) * (size_t)(C > 0 ? C : 1));
   L.vals0 = o; o += align256(sizeof(uint32_t) * (size_t)(C > 0 ? C : 1));
   L.vals1 = o; o += align256(sizeof(uint32_t) * (size_t)(C > 0 ? C : 1));
-  L.hist = o; o += align256(sizeof(uint32_t) * RS_BINS * (size_t)(nrb > 0 ? nrb : 1));
-  L.totals = o; o += align256(sizeof(uint32_t) * RS_BINS * MAX_PASSES);
+  L.hist = o; o += align256(sizeof(uint32_t) * RS_BINS_MAX * (size_t)(nrb > 0 ? nrb : 1));
+  L.totals = o; o += align256(sizeof(uint32_t) * RS_BINS_MAX * MAX_PASSES);
   L.cur = o; o += align256(sizeof(int32_t) * (MAX_PASSES + 1));
   L.order = o; o += align256(sizeof(uint32_t) * 66);
   L.jscan = o; o += align256(sizeof(uint32_t) * (size_t)((MAX_SCHED_TILES + SCAN_BLOCK - 1) / SCAN_BLOCK + 1));
@@ -167,13 +167,17 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_down(const uint32_t* __restrict
 }
 
 // ---- duplication: one key per (record, covered tile)
+// With key_masks set, the 16-bit block mask of each (record, tile) instance
+// rides in key bits 48..63, above every bit the radix passes sort on, so the
+// sort carries it to the instance's sorted position at no extra traffic.
 __global__ void __launch_bounds__(256) k_duplicate(UnitTable U, const float2* __restrict__ xy,
+                                                   const float4* __restrict__ conic_op,
                                                    const float* __restrict__ depth,
                                                    const int* __restrict__ radius,
                                                    const uint32_t* __restrict__ tiles,
                                                    const uint32_t* __restrict__ offsets, int W, int H,
-                                                   int tile_bits, int64_t cap, uint64_t* __restrict__ keys,
-                                                   uint32_t* __restrict__ vals) {
+                                                   int tile_bits, int64_t cap, int key_masks,
+                                                   uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t P = U.proj_base[U.n];
   if (p >= P) return;
@@ -186,11 +190,17 @@ __global__ void __launch_bounds__(256) k_duplicate(UnitTable U, const float2* __
   tile_rect(m.x, m.y, radius[p], TX, TY, x0, y0, x1, y1);
   uint64_t dbits = (uint64_t)__float_as_uint(depth[p]);
   uint64_t hi = (uint64_t)u << (tile_bits + 32);
+  float4 box = make_float4(1.f, -1.f, 1.f, -1.f);
+  if (key_masks) {
+    float pm;
+    box = alpha_box(m, conic_op[p], pm);
+  }
   int64_t o = offsets[p];
   for (int ty = y0; ty < y1; ++ty)
     for (int tx = x0; tx < x1; ++tx) {
       if (o < cap) {
-        keys[o] = hi | ((uint64_t)(ty * TX + tx) << 32) | dbits;
+        uint64_t mk = key_masks ? (uint64_t)block_mask(box, tx, ty) << 48 : 0ull;
+        keys[o] = mk | hi | ((uint64_t)(ty * TX + tx) << 32) | dbits;
         vals[o] = (uint32_t)p;
       }
       ++o;
@@ -198,39 +208,42 @@ __global__ void __launch_bounds__(256) k_duplicate(UnitTable U, const float2* __
 }
 
 // ---- radix pass kernels
+template <int BITS>
 __global__ void __launch_bounds__(RS_T) k_radix_hist(const uint64_t* __restrict__ k0,
                                                      const uint64_t* __restrict__ k1,
                                                      const int32_t* __restrict__ cur, int pass,
                                                      const uint32_t* __restrict__ d_count, int shift,
                                                      uint32_t* __restrict__ hist, int64_t stride,
                                                      uint32_t* __restrict__ totals) {
-  __shared__ uint32_t s_h[RS_T / 32][RS_BINS];
+  constexpr int BINS = 1 << BITS;
+  __shared__ uint32_t s_h[RS_T / 32][BINS];
   int64_t I = *d_count;
   int64_t base = (int64_t)blockIdx.x * RS_TILE;
   if (base >= I) return;
   const uint64_t* keys = cur[pass] ? k1 : k0;
   int w = threadIdx.x >> 5;
-  for (int k = threadIdx.x; k < (RS_T / 32) * RS_BINS; k += RS_T) (&s_h[0][0])[k] = 0u;
+  for (int k = threadIdx.x; k < (RS_T / 32) * BINS; k += RS_T) (&s_h[0][0])[k] = 0u;
   __syncthreads();
   #pragma unroll 4
   for (int j = 0; j < RS_ITEMS; ++j) {
     int64_t k = base + (int64_t)j * RS_T + threadIdx.x;
     if (k < I) {
-      uint32_t d = (uint32_t)(keys[k] >> shift) & 255u;
+      uint32_t d = (uint32_t)(keys[k] >> shift) & (BINS - 1u);
       atomicAdd(&s_h[w][d], 1u);
     }
   }
   __syncthreads();
-  int d = threadIdx.x;
-  uint32_t s = 0;
-  #pragma unroll
-  for (int q = 0; q < RS_T / 32; ++q) s += s_h[q][d];
-  hist[(int64_t)d * stride + blockIdx.x] = s;
-  if (s) atomicAdd(&totals[pass * RS_BINS + d], s);
+  for (int d = threadIdx.x; d < BINS; d += RS_T) {
+    uint32_t s = 0;
+    #pragma unroll
+    for (int q = 0; q < RS_T / 32; ++q) s += s_h[q][d];
+    hist[(int64_t)d * stride + blockIdx.x] = s;
+    if (s) atomicAdd(&totals[pass * RS_BINS_MAX + d], s);
+  }
 }
 
 __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ hist, int64_t stride,
-                                                     const uint32_t* __restrict__ totals, int pass,
+                                                     const uint32_t* __restrict__ totals, int pass, int bins,
                                                      const uint32_t* __restrict__ d_count,
                                                      int32_t* __restrict__ cur) {
   __shared__ uint32_t s_warp[33];
@@ -239,10 +252,10 @@ __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ hist
   __shared__ uint32_t s_base;
   int64_t I = *d_count;
   int d = blockIdx.x;
-  const uint32_t* tot = totals + pass * RS_BINS;
+  const uint32_t* tot = totals + pass * RS_BINS_MAX;
   if (threadIdx.x == 0) { s_skip = 0; s_base = 0; s_carry = 0; }
   __syncthreads();
-  if (threadIdx.x < RS_BINS) {
+  if ((int)threadIdx.x < bins) {
     uint32_t t = tot[threadIdx.x];
     if ((int64_t)t == I) s_skip = 1;  // every key has this digit (or I == 0)
     if ((int)threadIdx.x < d) atomicAdd(&s_base, t);
@@ -266,20 +279,26 @@ __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ hist
   }
 }
 
-// Stable scatter of one 4096-key block: keys are ranked within their digit in
-// key order (warp match + per-warp digit counts, round by round), placed in a
-// block-local digit-sorted buffer in shared memory, then written out so that
-// each digit's run goes to consecutive global positions (coalesced stores).
-__global__ void __launch_bounds__(RS_T) k_radix_scatter(uint64_t* __restrict__ k0, uint64_t* __restrict__ k1,
+// Stable scatter of one 4096-key block.  Warp w owns the block's keys
+// [512 w, 512 (w + 1)) (16 rounds of 32 consecutive keys), so ranking each
+// warp's keys in round order with warp-private digit counters (warp match,
+// no block barrier) ranks the block's keys in key order once the per-warp
+// counts are scanned across warps.  Keys are then placed in a block-local
+// digit-sorted buffer in shared memory and written out so that each digit's
+// run goes to consecutive global positions (coalesced stores).
+template <int BITS>
+__global__ void __launch_bounds__(RS_T, 2) k_radix_scatter(uint64_t* __restrict__ k0, uint64_t* __restrict__ k1,
                                                         uint32_t* __restrict__ v0, uint32_t* __restrict__ v1,
                                                         const int32_t* __restrict__ cur, int pass,
                                                         const uint32_t* __restrict__ d_count, int shift,
                                                         const uint32_t* __restrict__ hist, int64_t stride) {
-  __shared__ uint32_t s_off[RS_BINS];    // global start of this block's run of each digit
-  __shared__ uint32_t s_run[RS_BINS];    // keys of each digit ranked so far
-  __shared__ uint32_t s_lstart[RS_BINS]; // block-local start of each digit
-  __shared__ uint32_t s_wc[RS_T / 32][RS_BINS];
-  __shared__ uint32_t s_rt[RS_BINS];
+  constexpr int BINS = 1 << BITS;
+  constexpr int NW = RS_T / 32;
+  constexpr int DPT = BINS / RS_T;      // digits per thread in the per-digit steps
+  constexpr int WKEYS = RS_TILE / NW;   // keys per warp
+  __shared__ uint32_t s_off[BINS];      // global start of this block's run of each digit
+  __shared__ uint32_t s_lstart[BINS];   // block-local start of each digit
+  __shared__ uint32_t s_wc[NW][BINS];   // per-warp digit counts, then each warp's offset within the digit
   __shared__ uint32_t s_warp[33];
   extern __shared__ __align__(16) unsigned char s_dyn[];  // RS_TILE keys, then RS_TILE values
   uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);
@@ -294,79 +313,89 @@ __global__ void __launch_bounds__(RS_T) k_radix_scatter(uint64_t* __restrict__ k
   uint64_t* kout = c ? k0 : k1;
   uint32_t* vout = c ? v0 : v1;
   int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  s_off[tid] = hist[(int64_t)tid * stride + blockIdx.x];
-  s_run[tid] = 0u;
   #pragma unroll
-  for (int q = 0; q < RS_T / 32; ++q) s_wc[q][tid] = 0u;
-  __syncthreads();
+  for (int e = 0; e < DPT; ++e) {
+    int dd = tid + e * RS_T;
+    s_off[dd] = hist[(int64_t)dd * stride + blockIdx.x];
+    #pragma unroll
+    for (int q = 0; q < NW; ++q) s_wc[q][dd] = 0u;
+  }
   uint32_t lt = (1u << lane) - 1u;
   uint64_t key[RS_ITEMS];
   uint32_t val[RS_ITEMS];
-  uint32_t rnk[RS_ITEMS];  // rank within the digit (block-local); 0xffffffff = no key
+  uint32_t rnk[RS_ITEMS / 2];  // ranks within the digit among this warp's keys, two 16-bit ranks a word
+  int64_t wk = base + (int64_t)w * WKEYS + lane;  // this lane's key of round 0
+  int64_t rem64 = I - wk;
+  int rem = rem64 > RS_TILE ? RS_TILE : (int)rem64;  // round j holds a key iff 32 j < rem
+  const uint64_t* kp = kin + wk;
+  const uint32_t* vp = vin + wk;
   #pragma unroll
   for (int j = 0; j < RS_ITEMS; ++j) {
-    int64_t k = base + (int64_t)j * RS_T + tid;
-    bool valid = k < I;
-    key[j] = valid ? kin[k] : 0ull;
-    val[j] = valid ? vin[k] : 0u;
+    bool valid = j * 32 < rem;
+    key[j] = valid ? kp[j * 32] : 0ull;
+    val[j] = valid ? vp[j * 32] : 0u;
   }
+  __syncthreads();
   #pragma unroll
   for (int j = 0; j < RS_ITEMS; ++j) {
-    int64_t k = base + (int64_t)j * RS_T + tid;
-    bool valid = k < I;
-    uint32_t d = valid ? ((uint32_t)(key[j] >> shift) & 255u) : 256u;
+    bool valid = j * 32 < rem;
+    uint32_t d = valid ? ((uint32_t)(key[j] >> shift) & (BINS - 1u)) : (uint32_t)BINS;
     uint32_t peers = __match_any_sync(0xffffffffu, d);
-    uint32_t rank = __popc(peers & lt);
-    if (valid && rank == 0) s_wc[w][d] = __popc(peers);
-    __syncthreads();
-    {
+    uint32_t before = valid ? s_wc[w][d] : 0u;
+    uint32_t r = before + __popc(peers & lt);  // < WKEYS: fits 16 bits
+    if (j & 1) rnk[j >> 1] |= r << 16; else rnk[j >> 1] = r;
+    __syncwarp();
+    if (valid && (peers & lt) == 0u) s_wc[w][d] = before + __popc(peers);  // lowest lane of the group
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: exclusive scan of the warp counts (warp order = key order); thread tid
+  // owns digits tid * DPT .. tid * DPT + DPT - 1, then a block scan gives digit starts
+  {
+    uint32_t cnts[DPT];
+    uint32_t cnt = 0;
+    #pragma unroll
+    for (int e = 0; e < DPT; ++e) {
+      int dd = tid * DPT + e;
       uint32_t acc = 0;
       #pragma unroll
-      for (int q = 0; q < RS_T / 32; ++q) {
-        uint32_t cq = s_wc[q][tid];
-        s_wc[q][tid] = acc;
+      for (int q = 0; q < NW; ++q) {
+        uint32_t cq = s_wc[q][dd];
+        s_wc[q][dd] = acc;
         acc += cq;
       }
-      s_rt[tid] = acc;
+      cnts[e] = acc;
+      cnt += acc;
     }
-    __syncthreads();
-    rnk[j] = valid ? s_run[d] + s_wc[w][d] + rank : 0xffffffffu;
-    __syncthreads();
-    s_run[tid] += s_rt[tid];
-    #pragma unroll
-    for (int q = 0; q < RS_T / 32; ++q) s_wc[q][tid] = 0u;
-    __syncthreads();
-  }
-  // block-local digit starts (exclusive prefix of the block's digit counts)
-  {
-    uint32_t cnt = s_run[tid];
-    int l = lane;
     uint32_t inc = cnt;
     #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       uint32_t nb = __shfl_up_sync(0xffffffffu, inc, o);
-      if (l >= o) inc += nb;
+      if (lane >= o) inc += nb;
     }
     if (lane == 31) s_warp[w] = inc;
     __syncthreads();
     if (w == 0) {
-      uint32_t x = lane < RS_T / 32 ? s_warp[lane] : 0u, xi = x;
+      uint32_t x = lane < NW ? s_warp[lane] : 0u, xi = x;
       #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         uint32_t nb = __shfl_up_sync(0xffffffffu, xi, o);
         if (lane >= o) xi += nb;
       }
-      if (lane < RS_T / 32) s_warp[lane] = xi - x;
+      if (lane < NW) s_warp[lane] = xi - x;
     }
     __syncthreads();
-    s_lstart[tid] = inc - cnt + s_warp[w];
+    uint32_t st = inc - cnt + s_warp[w];
+    #pragma unroll
+    for (int e = 0; e < DPT; ++e) { s_lstart[tid * DPT + e] = st; st += cnts[e]; }
   }
   __syncthreads();
   #pragma unroll
   for (int j = 0; j < RS_ITEMS; ++j) {
-    if (rnk[j] == 0xffffffffu) continue;
-    uint32_t d = (uint32_t)(key[j] >> shift) & 255u;
-    uint32_t pos = s_lstart[d] + rnk[j];
+    if (j * 32 >= rem) continue;
+    uint32_t d = (uint32_t)(key[j] >> shift) & (BINS - 1u);
+    uint32_t r = (j & 1) ? (rnk[j >> 1] >> 16) : (rnk[j >> 1] & 0xffffu);
+    uint32_t pos = s_lstart[d] + s_wc[w][d] + r;
     s_keys[pos] = key[j];
     s_vals[pos] = val[j];
   }
@@ -374,7 +403,7 @@ __global__ void __launch_bounds__(RS_T) k_radix_scatter(uint64_t* __restrict__ k
   int n_here = (int)min((int64_t)RS_TILE, I - base);
   for (int i = tid; i < n_here; i += RS_T) {
     uint64_t kk = s_keys[i];
-    uint32_t d = (uint32_t)(kk >> shift) & 255u;
+    uint32_t d = (uint32_t)(kk >> shift) & (BINS - 1u);
     uint32_t gp = s_off[d] + (uint32_t)i - s_lstart[d];
     kout[gp] = kk;
     vout[gp] = s_vals[i];
@@ -387,22 +416,28 @@ __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ k0,
                                                 const uint32_t* __restrict__ d_count, int tile_bits,
                                                 int n_tiles, int TX, uint32_t* __restrict__ ranges,
                                                 uint32_t* __restrict__ out_vals, const float2* __restrict__ xy,
-                                                const float4* __restrict__ conic_op, uint16_t* __restrict__ masks) {
+                                                const float4* __restrict__ conic_op, uint16_t* __restrict__ masks,
+                                                int key_masks) {
   int64_t I = *d_count;
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= I) return;
   int c = cur[final_pass];
   const uint64_t* keys = c ? k1 : k0;
   const uint32_t* vals = c ? v1 : v0;
-  uint32_t ut = (uint32_t)(keys[k] >> 32);
+  // unit | tile bits (key bits 32..47 when the block masks ride in bits 48..63)
+  uint32_t utm = key_masks ? 0xffffu : 0xffffffffu;
+  uint64_t kk = keys[k];
+  uint32_t ut = (uint32_t)(kk >> 32) & utm;
   uint32_t p = vals[k];
   out_vals[k] = p;
   uint32_t mask = (1u << tile_bits) - 1u;
   uint32_t tile = ut & mask;
   int64_t flat = (int64_t)(ut >> tile_bits) * n_tiles + tile;
-  if (k == 0 || (uint32_t)(keys[k - 1] >> 32) != ut) ranges[2 * flat] = (uint32_t)k;
-  if (k == I - 1 || (uint32_t)(keys[k + 1] >> 32) != ut) ranges[2 * flat + 1] = (uint32_t)(k + 1);
-  if (masks) {
+  if (k == 0 || ((uint32_t)(keys[k - 1] >> 32) & utm) != ut) ranges[2 * flat] = (uint32_t)k;
+  if (k == I - 1 || ((uint32_t)(keys[k + 1] >> 32) & utm) != ut) ranges[2 * flat + 1] = (uint32_t)(k + 1);
+  if (masks && key_masks) {
+    masks[k] = (uint16_t)(kk >> 48);
+  } else if (masks) {
     // which 4x4 pixel blocks of its tile the record's alpha >= 1/255 box reaches
     float pm;
     float4 b = alpha_box(xy[p], conic_op[p], pm);
@@ -507,7 +542,10 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
   int tile_bits = bits_for(n_tiles);
   int unit_bits = bits_for(U.n);
   if (tile_bits + unit_bits > 32) return GS_ERR_INVALID;
-  int passes = (32 + tile_bits + unit_bits + 7) / 8;
+  int key_bits = 32 + tile_bits + unit_bits;
+  // 9-bit digits when they save a pass (45-bit keys at 1080p: 5 passes instead of 6)
+  int digit = ((key_bits + 8) / 9 < (key_bits + 7) / 8) ? 9 : 8;
+  int passes = (key_bits + digit - 1) / digit;
   char* ws = (char*)workspace;
   uint32_t* offsets = (uint32_t*)(ws + L.offsets);
   uint32_t* bsums = (uint32_t*)(ws + L.bsums);
@@ -522,7 +560,7 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
   if (stride < 1) stride = 1;
 
   if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)n_tiles * U.n, s) != cudaSuccess ||
-      cudaMemsetAsync(totals, 0, sizeof(uint32_t) * RS_BINS * MAX_PASSES, s) != cudaSuccess ||
+      cudaMemsetAsync(totals, 0, sizeof(uint32_t) * RS_BINS_MAX * MAX_PASSES, s) != cudaSuccess ||
       cudaMemsetAsync(cur, 0, sizeof(int32_t) * (MAX_PASSES + 1), s) != cudaSuccess ||
       cudaMemsetAsync(d_num_instances, 0, sizeof(uint32_t), s) != cudaSuccess)
     return GS_ERR_CUDA;
@@ -535,24 +573,35 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
   k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);
   k_scan_down<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, P, bsums, nsb, offsets, max_instances,
                                                d_num_instances, d_status);
-  k_duplicate<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(U, (const float2*)proj->xy, proj->depth, proj->radius,
-                                                          proj->tiles, offsets, width, height, tile_bits,
-                                                          max_instances, k0, v0);
+  // block masks ride in the keys when unit | tile | depth leave bits 48..63 free
+  int key_masks = (block_masks && key_bits <= 48) ? 1 : 0;
+  k_duplicate<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(U, (const float2*)proj->xy, (const float4*)proj->conic_op,
+                                                          proj->depth, proj->radius, proj->tiles, offsets, width,
+                                                          height, tile_bits, max_instances, key_masks, k0, v0);
   if (max_instances > 0) {
-    if (cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, SCATTER_DYN_SMEM) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(k_radix_scatter<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SCATTER_DYN_SMEM) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_radix_scatter<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, SCATTER_DYN_SMEM) !=
+            cudaSuccess)
       return GS_ERR_CUDA;
     unsigned nrb = (unsigned)stride;
     for (int pass = 0; pass < passes; ++pass) {
-      int shift = 8 * pass;
-      k_radix_hist<<<nrb, RS_T, 0, s>>>(k0, k1, cur, pass, d_num_instances, shift, hist, stride, totals);
-      k_radix_scan<<<RS_BINS, 1024, 0, s>>>(hist, stride, totals, pass, d_num_instances, cur);
-      k_radix_scatter<<<nrb, RS_T, SCATTER_DYN_SMEM, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift, hist,
-                                                          stride);
+      int shift = digit * pass;
+      if (digit == 9) {
+        k_radix_hist<9><<<nrb, RS_T, 0, s>>>(k0, k1, cur, pass, d_num_instances, shift, hist, stride, totals);
+        k_radix_scan<<<512, 1024, 0, s>>>(hist, stride, totals, pass, 512, d_num_instances, cur);
+        k_radix_scatter<9><<<nrb, RS_T, SCATTER_DYN_SMEM, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift,
+                                                                hist, stride);
+      } else {
+        k_radix_hist<8><<<nrb, RS_T, 0, s>>>(k0, k1, cur, pass, d_num_instances, shift, hist, stride, totals);
+        k_radix_scan<<<256, 1024, 0, s>>>(hist, stride, totals, pass, 256, d_num_instances, cur);
+        k_radix_scatter<8><<<nrb, RS_T, SCATTER_DYN_SMEM, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift,
+                                                                hist, stride);
+      }
     }
     k_ranges<<<(unsigned)((max_instances + 255) / 256), 256, 0, s>>>(
         k0, k1, v0, v1, cur, passes, d_num_instances, tile_bits, n_tiles, TX, ranges, sorted_vals,
-        (const float2*)proj->xy, (const float4*)proj->conic_op, block_masks);
+        (const float2*)proj->xy, (const float4*)proj->conic_op, block_masks, key_masks);
   }
   if (sched) return gs_schedule_jobs(ranges, n_tiles * U.n, ws + L.order, ws + L.jscan, sched, s);
   return gs_check_launch();

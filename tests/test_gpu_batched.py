@@ -234,13 +234,18 @@ def test_fused_projection_backward_adam_matches_separate(n_views):
     assert torch.allclose(pa, pb, rtol=1e-5, atol=1e-5)
 
 
-@pytest.mark.parametrize("chunk", [32, 96, 1024])
-def test_schedule_does_not_change_results(chunk):
+@pytest.mark.parametrize("chunk,opaque", [(32, False), (96, False), (1024, False), (32, True), (96, True)])
+def test_schedule_does_not_change_results(chunk, opaque):
     """The blend schedule (heaviest-first order, per-instance block masks, backward replayed in chunks from
     forward checkpoints) only skips and reorders work: images and n_contrib are bit-identical and gradients
-    equal up to atomic order, with and without it; small chunks put many checkpoints on every list."""
+    equal up to atomic order, with and without it.  Small chunks put many checkpoints on every list; the
+    opaque scenes make most pixels stop after the first chunk, so checkpoints after an early stop are
+    exercised."""
     n, deg, W, H = 3000, 1, 150, 110
     g, cams = scenes.random_scene(n, deg, 31, W, H)
+    if opaque:
+        g["logit_opacity"][:] = np.log(0.9 / 0.1)
+        g["log_scales"][:] += 0.7
     params = gs.pack_params(g, deg)
     camd = gs.pack_cameras(cams)
     gt, mask = scenes.random_gt(W, H, 32)
@@ -254,12 +259,18 @@ def test_schedule_does_not_change_results(chunk):
         fr.backward(params, camd, BG)
         torch.cuda.synchronize()
         assert fr.read_status() == 0
-        res.append((fr.img.clone(), fr.n_contrib.clone(), fr.grads.clone(), fr.dco.clone()))
+        res.append((fr.img.clone(), fr.n_contrib.clone(), fr.grads.clone(), fr.dco.clone(), fr.final_T.clone()))
         if use_sched:
             lens = (fr.ranges[:, 1] - fr.ranges[:, 0]).cpu().numpy()
             assert int(fr.job_base[-1].item()) == int(np.sum((lens + chunk - 1) // chunk))
+            if chunk == 32:
+                assert lens.max() > 4 * chunk  # several chunks per list
     a, b = res
-    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    if opaque:
+        stopped = a[4] < 1e-3
+        assert float(stopped.float().mean()) > 0.2  # the early stop is exercised
+        assert float((a[1][stopped] > chunk).float().mean()) > 0.3  # ... often after the first chunk
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[4], b[4])
     sc = float(a[2].abs().max())
     assert torch.allclose(a[2], b[2], rtol=1e-3, atol=1e-5 * sc)
     assert torch.allclose(a[3], b[3], rtol=1e-3, atol=1e-5 * float(a[3].abs().max()))
