@@ -131,11 +131,17 @@ __global__ void __launch_bounds__(256) k_ssim_stats(const float* __restrict__ im
   __shared__ float s_tmp[5][HT][LT];
   __shared__ float s_red[32];
   __shared__ float s_win[11];
-  load_window(s_win);
   int tiles_x = (W + LT - 1) / LT;
   int bx = blockIdx.x % tiles_x, by = blockIdx.x / tiles_x;
   int c = blockIdx.y, u = blockIdx.z;
   int64_t plane = (int64_t)W * H;
+  {
+    // a tile without mask pixels adds nothing to the loss and has no factor map entries
+    int qx = bx * LT + (int)(threadIdx.x % LT), qy = by * LT + (int)(threadIdx.x / LT);
+    bool m = qx < W && qy < H && mask[(int64_t)u * plane + (int64_t)qy * W + qx] != 0;
+    if (!__syncthreads_or(m)) return;
+  }
+  load_window(s_win);
   const float* X = img + ((int64_t)u * 3 + c) * plane;
   const float* Y = gt + ((int64_t)u * 3 + c) * plane;
   int x0 = bx * LT - R, y0 = by * LT - R;
@@ -170,11 +176,13 @@ __global__ void __launch_bounds__(256) k_ssim_stats(const float* __restrict__ im
       fxx = wp * S * (-1.f / B2);
       fxy = wp * S * (2.f / A2);
     }
-    int64_t base = ((int64_t)u * 3 + c) * plane + pix;
-    int64_t fs = (int64_t)3 * plane * gridDim.z;  // stride between the three factor maps
-    fac[base] = fmu;
-    fac[fs + base] = fxx;
-    fac[2 * fs + base] = fxy;
+    if (in) {  // the factor maps are zero off the mask; only mask pixels are stored and read
+      int64_t base = ((int64_t)u * 3 + c) * plane + pix;
+      int64_t fs = (int64_t)3 * plane * gridDim.z;  // stride between the three factor maps
+      fac[base] = fmu;
+      fac[fs + base] = fxx;
+      fac[2 * fs + base] = fxy;
+    }
   }
   float ts = block_sum(sacc, s_red);
   if (threadIdx.x == 0 && ts != 0.f) atomicAdd(&ssum[u], (double)ts);
@@ -190,7 +198,6 @@ __global__ void __launch_bounds__(256) k_ssim_grad(const float* __restrict__ img
   __shared__ float s_in[3][HT][HT];
   __shared__ float s_tmp[3][HT][LT];
   __shared__ float s_win[11];
-  load_window(s_win);
   int tiles_x = (W + LT - 1) / LT;
   int bx = blockIdx.x % tiles_x, by = blockIdx.x / tiles_x;
   int c = blockIdx.y, u = blockIdx.z;
@@ -198,16 +205,26 @@ __global__ void __launch_bounds__(256) k_ssim_grad(const float* __restrict__ img
   int64_t off = ((int64_t)u * 3 + c) * plane;
   int64_t fs = (int64_t)3 * plane * gridDim.z;
   int x0 = bx * LT - R, y0 = by * LT - R;
+  // factor maps are nonzero only at mask pixels: read them there, zero elsewhere
+  bool any = false;
   for (int k = threadIdx.x; k < HT * HT; k += blockDim.x) {
     int r = k / HT, q = k % HT;
     int gx = x0 + q, gy = y0 + r;
     float a = 0.f, b = 0.f, d = 0.f;
-    if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+    if (gx >= 0 && gx < W && gy >= 0 && gy < H && mask[(int64_t)u * plane + (int64_t)gy * W + gx] != 0) {
       int64_t pix = off + (int64_t)gy * W + gx;
       a = fac[pix]; b = fac[fs + pix]; d = fac[2 * fs + pix];
+      any = true;
     }
     s_in[0][r][q] = a; s_in[1][r][q] = b; s_in[2][r][q] = d;
   }
+  if (!__syncthreads_or(any)) {
+    // no mask pixel within the window's reach: both gradient terms vanish
+    int px = bx * LT + (int)(threadIdx.x % LT), py = by * LT + (int)(threadIdx.x / LT);
+    if (px < W && py < H) dimg[off + (int64_t)py * W + px] = 0.f;
+    return;
+  }
+  load_window(s_win);
   __syncthreads();
   int lx = threadIdx.x % LT, ly = threadIdx.x / LT;
   float cv[3];

@@ -433,6 +433,10 @@ __global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ r
   }
 }
 
+// Contributing lanes up to which the scheduled backward skips the warp
+// reduction of a record's nine gradient values.
+constexpr int DIRECT_LANES = 3;
+
 // Backward over chunk jobs: job (list, chunk c, pixel block) replays entries
 // [c K, min((c + 1) K, L)) of the list back to front.  It starts from the
 // forward's checkpoint at the chunk's end (T and the colour C accumulated in
@@ -577,7 +581,9 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
       unsigned cm = __ballot_sync(FULL, contrib);
       if (cm) {
         int64_t pr = (int64_t)__float_as_uint(rb.w);
-        if ((cm & (cm - 1)) == 0) {
+        if (__popc(cm) <= DIRECT_LANES) {
+          // few contributing lanes (small splats): each issues its own three vector
+          // atomics, which costs fewer instructions and atomic operations than a reduction
           if (contrib) {
             atomic_add2(dxy + 2 * pr, v[0], v[1]);
             atomic_add4(dco + 4 * pr, v[2], v[3], v[4], v[5]);

@@ -104,6 +104,31 @@ def test_loss_parity(lam):
     assert np.abs(dg - d).max() <= 1e-3 * np.abs(d).max()
 
 
+@pytest.mark.parametrize("lam", [0.0, 0.2])
+def test_loss_parity_sparse_mask(lam):
+    """A mask covering a disc and a thin stripe only: most 16x16 tiles hold no mask pixel and many gradient
+    windows reach none, so the SSIM kernels' tile skipping is exercised; loss and gradient still match the
+    oracle, and the gradient is exactly zero wherever no mask pixel lies within the window's reach."""
+    W, H = 200, 150
+    rng = np.random.default_rng(4)
+    img = rng.uniform(0, 1, (1, 3, H, W)).astype(np.float32)
+    gt, _ = scenes.random_gt(W, H, 10)
+    yy, xx = np.mgrid[0:H, 0:W]
+    mask = (((xx - 60) ** 2 + (yy - 50) ** 2 < 25 ** 2) | ((yy >= 120) & (yy < 122) & (xx > 100))).astype(np.uint8)
+    import paper_2509_12138_gb300 as gsp
+    fr = gsp.Frame(1, gsp.Units.single(1), W, H, 0, with_backward=False)
+    fr.img.copy_(torch.from_numpy(img))
+    fr.loss(torch.from_numpy(gt).cuda(), torch.from_numpy(mask).cuda(), lam)
+    val, d = oracle.loss(img[0].astype(np.float64), gt.astype(np.float64), mask, lam)
+    assert float(fr.loss_val.item()) == pytest.approx(val, rel=1e-5)
+    dg = fr.dimg.cpu().numpy()[0]
+    assert np.abs(dg - d).max() <= 1e-3 * np.abs(d).max()
+    far = np.ones((H, W), bool)
+    for y, x in zip(*np.nonzero(mask)):
+        far[max(0, y - 5):y + 6, max(0, x - 5):x + 6] = False
+    assert far.mean() > 0.5 and np.all(dg[:, far] == 0.0)
+
+
 def _group_check(gg, go, deg, tol=GRAD_TOL):
     groups = dict(mean=slice(0, 3), log_scale=slice(3, 6), quat=slice(6, 10), opacity=slice(10, 11),
                   sh_dc=slice(11, 14), sh_rest=slice(14, gg.shape[1]))
