@@ -113,6 +113,8 @@ typedef struct gs_grad2d {
  * jobs         [2 * max_jobs]     (order position, chunk) of every chunk job
  * checkpoints  [max_checkpoints][256][4]  per pixel (T, r, g, b) of the forward
  *                                 at every interior chunk boundary
+ * chunk_last   [max_checkpoints][256]     forward scratch: per pixel the last
+ *                                 blended entry of each chunk and a stop flag
  * chunk        entries per chunk (a multiple of 32); max_jobs >= U n_tiles +
  *              max_instances / chunk + 1, max_checkpoints >= max_instances /
  *              chunk + 1 (gs_schedule_sizes). */
@@ -122,6 +124,7 @@ typedef struct gs_schedule {
   uint32_t* job_base;
   uint32_t* jobs;
   float* checkpoints;
+  uint32_t* chunk_last;
   int64_t max_jobs;
   int64_t max_checkpoints;
   int32_t chunk;

@@ -36,7 +36,7 @@ class GsGrad2d(C.Structure):
 
 class GsSchedule(C.Structure):
     _fields_ = [("tile_order", C.c_void_p), ("block_masks", C.c_void_p), ("job_base", C.c_void_p),
-                ("jobs", C.c_void_p), ("checkpoints", C.c_void_p), ("max_jobs", C.c_int64),
+                ("jobs", C.c_void_p), ("checkpoints", C.c_void_p), ("chunk_last", C.c_void_p), ("max_jobs", C.c_int64),
                 ("max_checkpoints", C.c_int64), ("chunk", C.c_int32)]
 
 

@@ -380,16 +380,63 @@ __device__ __forceinline__ void walk_fwd(const uint32_t* __restrict__ vals, cons
   }
 }
 
-// Forward with the blend schedule: one warp per (list, pixel block), lists
-// in tile order (heaviest first).  The warp walks its list in chunks of K
-// entries and stores (T, C) of each pixel in front of every interior chunk
-// boundary: the checkpoints the chunked backward starts from.  After an
-// early exit the remaining checkpoints hold the final state.
+// ---- scheduled forward: chunk-parallel compositing in three passes
+//
+// Per pixel, front-to-back compositing over a list is a product of (1 - alpha)
+// factors and a sum of colours weighted by the running product, so chunks of
+// K entries can be composited independently from T = 1 and combined:
+// C += T C_c, T *= T_c.  The early stop is the only order-dependent decision:
+// a pixel whose (T T_c) would fall below T_MIN, or whose chunk stopped on its
+// own, stops inside that chunk, which is then walked again from the true
+// incoming state.
+//   pass 1 (chunk jobs):   partial (T_c, C_c, last_c | stop) of every chunk;
+//   pass 2 (list warps):   combine in order, find each pixel's stop chunk c*,
+//                          write the checkpoints in front of chunks <= c*,
+//                          finish the pixels that never stop;
+//   pass 3 (chunk jobs):   walk chunk c* again for the pixels that stop there,
+//                          write their final state and remaining checkpoints.
+// Per pixel the blended entries and the stop decision are those of the
+// sequential walk; the combine changes only the rounding order of T and C.
+constexpr uint32_t STOP_BIT = 0x80000000u;  // chunk partial: the pixel stopped inside the chunk
+constexpr uint32_t REWALK_BIT = 0x80000000u;  // n_contrib between passes 2 and 3: stop chunk pending
+constexpr int CSTAR_SHIFT = 24;              // ... with the stop chunk in bits 24..30
+constexpr int MAX_CSTAR = 127;               // lists of more chunks are finished serially in pass 2
+
+// The warp's pixel of (list o, block w) and its geometry.
+template <int BW>
+struct PixelOf {
+  int u, tile, tx, ty, px, py, pix_local;
+  bool inside;
+  uint32_t wbits;
+  __device__ __forceinline__ PixelOf(const uint32_t* __restrict__ order, int o, int w, int n_tiles, int TX, int W,
+                                     int H) {
+    uint32_t f = order[o];
+    u = (int)(f / (uint32_t)n_tiles);
+    tile = (int)(f % (uint32_t)n_tiles);
+    tx = tile % TX;
+    ty = tile / TX;
+    constexpr int BH = 32 / BW, NWX = TILE / BW;
+    int lane = threadIdx.x & 31;
+    px = tx * TILE + (w % NWX) * BW + (lane % BW);
+    py = ty * TILE + (w / NWX) * BH + (lane / BW);
+    pix_local = (py - ty * TILE) * TILE + (px - tx * TILE);
+    inside = px < W && py < H;
+    wbits = warp_block_bits<BW>(w);
+  }
+};
+
+// Pass 1: job (list o, chunk c, block w) composites entries [c K, min((c+1) K, L))
+// from T = 1.  A list of one chunk is final here.  Otherwise chunk 0's state
+// (exact: nothing lies in front of it) goes to img (colour without
+// background), final_T and n_contrib (| STOP_BIT), chunk c >= 1's partial to
+// checkpoint slot c - 1 and chunk_last.
 template <int BW>
 __global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ ranges,
                                                            const uint32_t* __restrict__ order,
-                                                           const uint32_t* __restrict__ job_base, int K,
+                                                           const uint32_t* __restrict__ job_base,
+                                                           const uint32_t* __restrict__ jobs, int K, int NT,
                                                            float4* __restrict__ ckpt,
+                                                           uint32_t* __restrict__ chunk_last,
                                                            const uint32_t* __restrict__ vals,
                                                            const uint16_t* __restrict__ masks,
                                                            const float2* __restrict__ xy,
@@ -399,38 +446,193 @@ __global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ r
                                                            float* __restrict__ img, float* __restrict__ final_T,
                                                            uint32_t* __restrict__ n_contrib) {
   __shared__ Rec s_rec[32];
-  int o = (int)(blockIdx.x >> 3), w = (int)(blockIdx.x & 7u);
-  uint32_t f = order[o];
-  int u = (int)(f / (uint32_t)n_tiles), tile = (int)(f % (uint32_t)n_tiles);
-  int tx = tile % TX, ty = tile / TX;
-  constexpr int BH = 32 / BW, NWX = TILE / BW;
-  int lane = threadIdx.x & 31;
-  int px = tx * TILE + (w % NWX) * BW + (lane % BW), py = ty * TILE + (w / NWX) * BH + (lane / BW);
-  uint32_t wbits = warp_block_bits<BW>(w);
-  bool inside = px < W && py < H;
-  uint2 rg = ranges[(int64_t)u * n_tiles + tile];
-  int L = (int)(rg.y - rg.x);
+  uint32_t jid = blockIdx.x >> 3;
+  if (jid >= job_base[NT]) return;
+  int w = (int)(blockIdx.x & 7u);
+  int o = (int)jobs[2 * (int64_t)jid], ch = (int)jobs[2 * (int64_t)jid + 1];
+  PixelOf<BW> P(order, o, w, n_tiles, TX, W, H);
   int nch = (int)(job_base[o + 1] - job_base[o]);
-  int64_t cp0 = (int64_t)job_base[o] - o;  // this list's first checkpoint
-  int pix_local = (py - ty * TILE) * TILE + (px - tx * TILE);
+  uint2 rg = ranges[(int64_t)P.u * n_tiles + P.tile];
+  int L = (int)(rg.y - rg.x);
   float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
   int last = 0;
-  bool done = !inside;
-  for (int c = 0; c < max(nch, 1); ++c) {
-    if (c > 0 && inside) ckpt[(cp0 + c - 1) * TILE_PIX + pix_local] = make_float4(T, c0, c1, c2);
-    walk_fwd(vals, masks, xy, conic_op, rgb, rg.x, c * K, min(c * K + K, L), wbits, (float)px, (float)py, s_rec, T,
-             c0, c1, c2, last, done);
+  bool done = !P.inside;
+  walk_fwd(vals, masks, xy, conic_op, rgb, rg.x, ch * K, min(ch * K + K, L), P.wbits, (float)P.px, (float)P.py,
+           s_rec, T, c0, c1, c2, last, done);
+  if (!P.inside) return;
+  int64_t plane = (int64_t)W * H;
+  int64_t pix = (int64_t)P.py * W + P.px;
+  float* im = img + (int64_t)P.u * 3 * plane;
+  if (nch == 1 || ch == 0) {
+    bool fin = nch == 1;
+    im[pix] = fin ? c0 + T * bg0 : c0;
+    im[plane + pix] = fin ? c1 + T * bg1 : c1;
+    im[2 * plane + pix] = fin ? c2 + T * bg2 : c2;
+    final_T[(int64_t)P.u * plane + pix] = T;
+    n_contrib[(int64_t)P.u * plane + pix] = (uint32_t)last | (!fin && done ? STOP_BIT : 0u);
+  } else {
+    int64_t slot = ((int64_t)job_base[o] - o + ch - 1) * TILE_PIX + P.pix_local;
+    ckpt[slot] = make_float4(T, c0, c1, c2);
+    chunk_last[slot] = (uint32_t)last | (done ? STOP_BIT : 0u);
   }
-  if (inside) {
-    int64_t plane = (int64_t)W * H;
-    int64_t pix = (int64_t)py * W + px;
-    float* im = img + (int64_t)u * 3 * plane;
+}
+
+// Pass 2: one warp per (list, block) in tile order.  Empty lists give the
+// background.  For lists of several chunks, the state in front of chunk c is
+// (T, C); the chunk's partial is applied when it shows no stop and
+// T T_c >= T_MIN (then no entry of the chunk can stop the pixel), and
+// otherwise chunk c is the pixel's stop chunk c*.  The state in front of each
+// boundary up to c* is written over its partial (the backward's checkpoint).
+// Pixels that never stop are final here; pixels with c* >= 1 leave their
+// state in front of c* in img / final_T and (last | c* | REWALK_BIT) in
+// n_contrib for pass 3.  Lists of more than MAX_CSTAR + 1 chunks (or of
+// 2^24 entries or more) walk their stop chunks here, one after another.
+template <int BW>
+__global__ void __launch_bounds__(32) k_render_fwd_combine(const uint2* __restrict__ ranges,
+                                                                 const uint32_t* __restrict__ order,
+                                                                 const uint32_t* __restrict__ job_base, int K,
+                                                                 float4* __restrict__ ckpt,
+                                                                 const uint32_t* __restrict__ chunk_last,
+                                                                 const uint32_t* __restrict__ vals,
+                                                                 const uint16_t* __restrict__ masks,
+                                                                 const float2* __restrict__ xy,
+                                                                 const float4* __restrict__ conic_op,
+                                                                 const float4* __restrict__ rgb, int W, int H,
+                                                                 int TX, int n_tiles, float bg0, float bg1, float bg2,
+                                                                 float* __restrict__ img, float* __restrict__ final_T,
+                                                                 uint32_t* __restrict__ n_contrib) {
+  const unsigned FULL = 0xffffffffu;
+  __shared__ Rec s_rec[32];
+  int o = (int)(blockIdx.x >> 3), w = (int)(blockIdx.x & 7u);
+  int nch = (int)(job_base[o + 1] - job_base[o]);
+  if (nch == 1) return;
+  PixelOf<BW> P(order, o, w, n_tiles, TX, W, H);
+  int64_t plane = (int64_t)W * H;
+  int64_t pix = (int64_t)P.py * W + P.px;
+  float* im = img + (int64_t)P.u * 3 * plane;
+  float* fT = final_T + (int64_t)P.u * plane;
+  uint32_t* nc = n_contrib + (int64_t)P.u * plane;
+  if (nch == 0) {
+    if (P.inside) {
+      im[pix] = bg0; im[plane + pix] = bg1; im[2 * plane + pix] = bg2;
+      fT[pix] = 1.f;
+      nc[pix] = 0u;
+    }
+    return;
+  }
+  uint2 rg = ranges[(int64_t)P.u * n_tiles + P.tile];
+  int L = (int)(rg.y - rg.x);
+  bool serial = nch > MAX_CSTAR + 1 || L >= (1 << CSTAR_SHIFT);
+  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+  int last = 0, cstar = -1;
+  bool done = !P.inside;
+  if (P.inside) {
+    c0 = im[pix]; c1 = im[plane + pix]; c2 = im[2 * plane + pix];
+    T = fT[pix];
+    uint32_t lw = nc[pix];
+    last = (int)(lw & ~STOP_BIT);
+    done = (lw & STOP_BIT) != 0u;  // a stop in chunk 0 is exact
+  }
+  int64_t cp0 = (int64_t)job_base[o] - o;
+  for (int c = 1; c < nch; ++c) {
+    int64_t slot = (cp0 + c - 1) * TILE_PIX + P.pix_local;
+    bool need = false;
+    if (P.inside && cstar < 0) {
+      float4 pt = ckpt[slot];
+      uint32_t lw = chunk_last[slot];
+      ckpt[slot] = make_float4(T, c0, c1, c2);  // the state in front of chunk c (final once done)
+      if (!done) {
+        float Tn = T * pt.x;
+        if ((lw & STOP_BIT) == 0u && !(Tn < T_MIN)) {
+          c0 += T * pt.y; c1 += T * pt.z; c2 += T * pt.w;
+          T = Tn;
+          uint32_t lc = lw & ~STOP_BIT;
+          if (lc) last = (int)lc;
+        } else if (serial) {
+          need = true;
+        } else {
+          cstar = c;  // pass 3 walks chunk c for this pixel and writes the rest
+        }
+      }
+    }
+    if (serial && __any_sync(FULL, need)) {
+      bool dd = !need;  // lanes that do not walk take no part
+      walk_fwd(vals, masks, xy, conic_op, rgb, rg.x, c * K, min(c * K + K, L), P.wbits, (float)P.px, (float)P.py,
+               s_rec, T, c0, c1, c2, last, dd);
+      if (need) done = dd;
+    }
+  }
+  if (!P.inside) return;
+  if (cstar >= 1) {
+    im[pix] = c0; im[plane + pix] = c1; im[2 * plane + pix] = c2;
+    fT[pix] = T;
+    nc[pix] = (uint32_t)last | ((uint32_t)cstar << CSTAR_SHIFT) | REWALK_BIT;
+  } else {
     im[pix] = c0 + T * bg0;
     im[plane + pix] = c1 + T * bg1;
     im[2 * plane + pix] = c2 + T * bg2;
-    final_T[(int64_t)u * plane + pix] = T;
-    n_contrib[(int64_t)u * plane + pix] = (uint32_t)last;
+    fT[pix] = T;
+    nc[pix] = (uint32_t)last;
   }
+}
+
+// Pass 3: job (list o, chunk c, block w) walks chunk c again for the pixels
+// whose stop chunk is c, from the state pass 2 left, and writes their final
+// image, final_T, n_contrib and the checkpoints after c (final state).
+template <int BW>
+__global__ void __launch_bounds__(32) k_render_fwd_stop(const uint2* __restrict__ ranges,
+                                                              const uint32_t* __restrict__ order,
+                                                              const uint32_t* __restrict__ job_base,
+                                                              const uint32_t* __restrict__ jobs, int K, int NT,
+                                                              float4* __restrict__ ckpt,
+                                                              const uint32_t* __restrict__ vals,
+                                                              const uint16_t* __restrict__ masks,
+                                                              const float2* __restrict__ xy,
+                                                              const float4* __restrict__ conic_op,
+                                                              const float4* __restrict__ rgb, int W, int H, int TX,
+                                                              int n_tiles, float bg0, float bg1, float bg2,
+                                                              float* __restrict__ img, float* __restrict__ final_T,
+                                                              uint32_t* __restrict__ n_contrib) {
+  __shared__ Rec s_rec[32];
+  uint32_t jid = blockIdx.x >> 3;
+  if (jid >= job_base[NT]) return;
+  int o = (int)jobs[2 * (int64_t)jid], ch = (int)jobs[2 * (int64_t)jid + 1];
+  if (ch == 0) return;
+  int nch = (int)(job_base[o + 1] - job_base[o]);
+  int w = (int)(blockIdx.x & 7u);
+  PixelOf<BW> P(order, o, w, n_tiles, TX, W, H);
+  uint2 rg = ranges[(int64_t)P.u * n_tiles + P.tile];
+  int L = (int)(rg.y - rg.x);
+  if (nch > MAX_CSTAR + 1 || L >= (1 << CSTAR_SHIFT)) return;  // finished in pass 2
+  int64_t plane = (int64_t)W * H;
+  int64_t pix = (int64_t)P.py * W + P.px;
+  float* im = img + (int64_t)P.u * 3 * plane;
+  float* fT = final_T + (int64_t)P.u * plane;
+  uint32_t* nc = n_contrib + (int64_t)P.u * plane;
+  bool mine = false;
+  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+  int last = 0;
+  if (P.inside) {
+    uint32_t lw = nc[pix];
+    mine = (lw & REWALK_BIT) != 0u && (int)((lw >> CSTAR_SHIFT) & 127u) == ch;
+    if (mine) {
+      last = (int)(lw & ((1u << CSTAR_SHIFT) - 1u));
+      c0 = im[pix]; c1 = im[plane + pix]; c2 = im[2 * plane + pix];
+      T = fT[pix];
+    }
+  }
+  if (!__any_sync(0xffffffffu, mine)) return;
+  bool done = !mine;
+  walk_fwd(vals, masks, xy, conic_op, rgb, rg.x, ch * K, min(ch * K + K, L), P.wbits, (float)P.px, (float)P.py,
+           s_rec, T, c0, c1, c2, last, done);
+  if (!mine) return;
+  int64_t cp0 = (int64_t)job_base[o] - o;
+  for (int b = ch + 1; b < nch; ++b) ckpt[(cp0 + b - 1) * TILE_PIX + P.pix_local] = make_float4(T, c0, c1, c2);
+  im[pix] = c0 + T * bg0;
+  im[plane + pix] = c1 + T * bg1;
+  im[2 * plane + pix] = c2 + T * bg2;
+  fT[pix] = T;
+  nc[pix] = (uint32_t)last;
 }
 
 // Contributing lanes up to which the scheduled backward skips the warp
@@ -685,10 +887,21 @@ int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const u
   dim3 grid(TX * TY * n_units);
 #define GS_FWD(BW)                                                                                                  \
   if (sched) {                                                                                                      \
-    k_render_fwd_m<BW><<<dim3(grid.x * 8), 32, 0, s>>>(                                                             \
+    dim3 gj((unsigned)(sched->max_jobs * 8));                                                                       \
+    k_render_fwd_m<BW><<<gj, 32, 0, s>>>(                                                                           \
+        (const uint2*)ranges, sched->tile_order, sched->job_base, sched->jobs, sched->chunk, (int)grid.x,            \
+        (float4*)sched->checkpoints, sched->chunk_last, sorted_vals, sched->block_masks, (const float2*)proj->xy,   \
+        (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2],  \
+        img, final_T, n_contrib);                                                                                   \
+    k_render_fwd_combine<BW><<<dim3(grid.x * 8), 32, 0, s>>>(                                                       \
         (const uint2*)ranges, sched->tile_order, sched->job_base, sched->chunk, (float4*)sched->checkpoints,        \
-        sorted_vals, sched->block_masks, (const float2*)proj->xy, (const float4*)proj->conic_op,                    \
+        sched->chunk_last, sorted_vals, sched->block_masks, (const float2*)proj->xy, (const float4*)proj->conic_op, \
         (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib);        \
+    k_render_fwd_stop<BW><<<gj, 32, 0, s>>>(                                                                        \
+        (const uint2*)ranges, sched->tile_order, sched->job_base, sched->jobs, sched->chunk, (int)grid.x,            \
+        (float4*)sched->checkpoints, sorted_vals, sched->block_masks, (const float2*)proj->xy,                       \
+        (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2],  \
+        img, final_T, n_contrib);                                                                                   \
   } else                                                                                                            \
     k_render_fwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, nullptr, sorted_vals, (const float2*)proj->xy, \
                                                (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, \

@@ -512,6 +512,7 @@ int gs_schedule_jobs(const uint32_t* ranges, int NT, char* order_ws, char* scan_
 int gs_schedule_check(const gs_schedule* sched, int n_units, int n_tiles, int64_t max_instances) {
   if (!sched) return GS_OK;
   if (!sched->tile_order || !sched->block_masks || !sched->job_base || !sched->jobs || !sched->checkpoints ||
+      !sched->chunk_last ||
       sched->chunk < 32 || (sched->chunk & 31))
     return GS_ERR_INVALID;
   int64_t NT = (int64_t)n_units * n_tiles;

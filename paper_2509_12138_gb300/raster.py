@@ -199,8 +199,10 @@ class Frame:
         self.job_base = torch.zeros(nt + 1, dtype=torch.int32, device=self.device)
         self.jobs = torch.zeros(2 * mj.value, dtype=torch.int32, device=self.device)
         self.checkpoints = torch.zeros((mc.value, 256, 4), dtype=torch.float32, device=self.device)
+        self.chunk_last = torch.zeros((mc.value, 256), dtype=torch.int32, device=self.device)
         self.sched = GsSchedule(self.tile_order.data_ptr(), self.block_masks.data_ptr(), self.job_base.data_ptr(),
-                                self.jobs.data_ptr(), self.checkpoints.data_ptr(), mj.value, mc.value, self.chunk)
+                                self.jobs.data_ptr(), self.checkpoints.data_ptr(), self.chunk_last.data_ptr(),
+                                mj.value, mc.value, self.chunk)
         self.num_instances = torch.zeros(1, dtype=torch.int32, device=self.device)
 
     # -- steps

@@ -234,14 +234,17 @@ def test_fused_projection_backward_adam_matches_separate(n_views):
     assert torch.allclose(pa, pb, rtol=1e-5, atol=1e-5)
 
 
-@pytest.mark.parametrize("chunk,opaque", [(32, False), (96, False), (1024, False), (32, True), (96, True)])
-def test_schedule_does_not_change_results(chunk, opaque):
-    """The blend schedule (heaviest-first order, per-instance block masks, backward replayed in chunks from
-    forward checkpoints) only skips and reorders work: images and n_contrib are bit-identical and gradients
-    equal up to atomic order, with and without it.  Small chunks put many checkpoints on every list; the
-    opaque scenes make most pixels stop after the first chunk, so checkpoints after an early stop are
-    exercised."""
-    n, deg, W, H = 3000, 1, 150, 110
+@pytest.mark.parametrize("chunk,opaque,n", [(32, False, 3000), (96, False, 3000), (1024, False, 3000),
+                                            (32, True, 3000), (96, True, 3000), (32, True, 60000)])
+def test_schedule_does_not_change_results(chunk, opaque, n):
+    """The blend schedule (heaviest-first order, per-instance block masks, lists composited in parallel
+    chunks and combined, stop chunks walked again, backward replayed in chunks from the combined
+    checkpoints) only skips and reorders work.  Combining per-chunk (T, C) products changes the rounding
+    order only: images agree to float rounding, n_contrib exactly, gradients up to atomic order.  Small
+    chunks put many chunks on every list; the opaque scenes make most pixels stop after the first chunk,
+    so the stop-chunk walk and the checkpoints after a stop are exercised; the dense scene has lists of
+    more than 128 chunks, whose stop chunks the combine pass walks itself."""
+    deg, W, H = 1, 150, 110
     g, cams = scenes.random_scene(n, deg, 31, W, H)
     if opaque:
         g["logit_opacity"][:] = np.log(0.9 / 0.1)
@@ -265,12 +268,16 @@ def test_schedule_does_not_change_results(chunk, opaque):
             assert int(fr.job_base[-1].item()) == int(np.sum((lens + chunk - 1) // chunk))
             if chunk == 32:
                 assert lens.max() > 4 * chunk  # several chunks per list
+            if n > 10000:
+                assert lens.max() > 128 * chunk  # the combine pass's serial path
     a, b = res
     if opaque:
         stopped = a[4] < 1e-3
         assert float(stopped.float().mean()) > 0.2  # the early stop is exercised
         assert float((a[1][stopped] > chunk).float().mean()) > 0.3  # ... often after the first chunk
-    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[4], b[4])
+    assert torch.equal(a[1], b[1])
+    assert torch.allclose(a[0], b[0], rtol=0, atol=1e-5)
+    assert torch.allclose(a[4], b[4], rtol=1e-4, atol=1e-7)
     sc = float(a[2].abs().max())
     assert torch.allclose(a[2], b[2], rtol=1e-3, atol=1e-5 * sc)
     assert torch.allclose(a[3], b[3], rtol=1e-3, atol=1e-5 * float(a[3].abs().max()))
