@@ -101,21 +101,24 @@ __device__ __forceinline__ float4 alpha_box(float2 m, float4 co, float& pmin) {
 }
 
 // 16-bit mask of the 4x4-pixel blocks (bit 4 by + bx) of tile (tx, ty) whose
-// pixel centres the box reaches.
-__device__ __forceinline__ uint32_t block_mask(float4 b, int tx, int ty) {
+// pixel centres the box reaches.  Block bx covers pixel centres
+// [16 tx + 4 bx, 16 tx + 4 bx + 3]; it is reached iff b.x <= its right end and
+// b.y >= its left end, which holds for a contiguous run of bx (and of by).
+__device__ __forceinline__ uint32_t axis_bits(float lo, float hi, int origin) {
   uint32_t m = 0;
-  if (!(b.x <= b.y)) return 0u;
   #pragma unroll
-  for (int by = 0; by < 4; ++by) {
-    float y0 = (float)(ty * TILE + 4 * by), y1 = y0 + 3.f;
-    bool yo = !(b.w < y0 || b.z > y1);
-    #pragma unroll
-    for (int bx = 0; bx < 4; ++bx) {
-      float x0 = (float)(tx * TILE + 4 * bx), x1 = x0 + 3.f;
-      if (yo && !(b.y < x0 || b.x > x1)) m |= 1u << (4 * by + bx);
-    }
+  for (int k = 0; k < 4; ++k) {
+    float a = (float)(origin + 4 * k);
+    if (!(hi < a || lo > a + 3.f)) m |= 1u << k;
   }
   return m;
+}
+__device__ __forceinline__ uint32_t block_mask(float4 b, int tx, int ty) {
+  if (!(b.x <= b.y)) return 0u;
+  uint32_t cx = axis_bits(b.x, b.y, tx * TILE), ry = axis_bits(b.z, b.w, ty * TILE);
+  // row by of the mask gets the column bits when ry has bit by
+  uint32_t spread = (ry & 1u) | ((ry & 2u) << 3) | ((ry & 4u) << 6) | ((ry & 8u) << 9);
+  return cx * spread;
 }
 
 __device__ __forceinline__ void set_status(int* st, int bits) {

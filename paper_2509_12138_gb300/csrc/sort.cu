@@ -223,15 +223,17 @@ __global__ void __launch_bounds__(RS_T) k_radix_hist(const uint64_t* __restrict_
   const uint64_t* keys = cur[pass] ? k1 : k0;
   int w = threadIdx.x >> 5;
   for (int k = threadIdx.x; k < (RS_T / 32) * BINS; k += RS_T) (&s_h[0][0])[k] = 0u;
-  __syncthreads();
-  #pragma unroll 4
+  // every load of the block's keys in flight at once, then the counting
+  uint32_t dg[RS_ITEMS];
+  #pragma unroll
   for (int j = 0; j < RS_ITEMS; ++j) {
     int64_t k = base + (int64_t)j * RS_T + threadIdx.x;
-    if (k < I) {
-      uint32_t d = (uint32_t)(keys[k] >> shift) & (BINS - 1u);
-      atomicAdd(&s_h[w][d], 1u);
-    }
+    dg[j] = k < I ? ((uint32_t)(keys[k] >> shift) & (BINS - 1u)) : 0xffffffffu;
   }
+  __syncthreads();
+  #pragma unroll
+  for (int j = 0; j < RS_ITEMS; ++j)
+    if (dg[j] != 0xffffffffu) atomicAdd(&s_h[w][dg[j]], 1u);
   __syncthreads();
   for (int d = threadIdx.x; d < BINS; d += RS_T) {
     uint32_t s = 0;

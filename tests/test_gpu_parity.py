@@ -230,7 +230,8 @@ def test_autograd_function_matches_frame_backward():
     fr2 = gsp.Frame(n, gsp.Units.single(n), W, H, deg)
     fr2.forward(params.detach(), camd, BG)
     g2 = fr2.backward(params.detach(), camd, BG, w.contiguous())
-    assert torch.allclose(params.grad, g2, rtol=1e-5, atol=1e-7)
+    # the same kernels on both paths: equal up to the order of the float atomics that accumulate gradients
+    assert torch.allclose(params.grad, g2, rtol=1e-4, atol=1e-5 * float(g2.abs().max()))
     # and against the oracle: d<w, img>/dparams
     cam = oracle.camera_block(cams, 0)
     d2 = oracle.render_backward(gauss64(g), cam, BG, w[0].cpu().numpy().astype(np.float64))
