@@ -285,12 +285,12 @@ def run_ours(args, wl, rank, world):
             stage_ms[s] += e[s].elapsed_time(e[s + 1])
     stage_ms /= args.steps
 
-    # blended (pixel, record) pairs of the timed views: the blend kernels' algorithmic work
+    # work counters of the timed views (the blend kernels' algorithmic units), outside the timed region
     pairs = []
     for k in range(min(args.steps, 16)):
         frame.forward(params, scene.cam((args.warmup + k) % V), bg)
         pairs.append(frame.blend_pairs())
-    pairs_per_step = float(np.mean(pairs))
+    pairs_per_step = {key: float(np.mean([p[key] for p in pairs])) for key in pairs[0]}
 
     # render-only (a1-a3) for Mpix/s
     torch.cuda.synchronize()
@@ -336,8 +336,12 @@ def run_ours(args, wl, rank, world):
                 launches=kernel_launch_count(frame, LAMBDA_SSIM) * args.steps, N=N, W=W, H=H)
 
 
-FWD_FLOP_PER_PAIR = 21   # FP32 operations per blended pair in k_render_fwd (an FMA counts 2)
-BWD_FLOP_PER_PAIR = 60   # likewise for k_render_bwd
+# Blend kernels' algorithmic work: FP32 issue slots (one per lane-operation, FMA and MUFU included) per
+# (pixel, list entry) pair of the standard per-pixel walk: the forward evaluates every entry until the pixel
+# stops (~15 slots: offset, quadratic form, exp, alpha, tests, T and colour updates), the reverse replay every
+# entry up to n_contrib (~50 slots: alpha, T recovery, colour-behind update, 9 gradient terms).
+FWD_SLOTS_PER_PAIR = 15
+BWD_SLOTS_PER_PAIR = 50
 
 
 def rooflines(res):
@@ -351,20 +355,23 @@ def rooflines(res):
     hbm = hbm or 6800.0
     mhz = peaks.get("sm_max_mhz", 2070.0)
     sms = 152
-    fp32_tflops = 2 * 128 * sms * mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 x clock
+    slots = 128 * sms * mhz * 1e6 / 1e12  # FP32 lane issue slots per second (T/s)
     N, I, pairs = res["N"], res["instances"], res["pairs"]
-    passes = 6
+    tiles = ((res["W"] + 15) // 16) * ((res["H"] + 15) // 16)
+    key_bits = 32 + max(1, (tiles - 1).bit_length())
+    passes = min(-(-key_bits // 9), -(-key_bits // 8))  # 9-bit digits when they save a pass
     work = {
         "preprocess": ("hbm", N * (59 * 4 + 52)),
         "bin_sort": ("hbm", N * 8 + I * (12 + passes * 32 + 16)),
         # params, m, v read and written; the gradient stays in registers; screen gradients read
         "project_bwd_adam": ("hbm", N * (59 * 4 * 6 + 40 + 4)),
         "loss": ("hbm", res["W"] * res["H"] * (3 * 4 * 3 + 1 + 3 * 4 * 6)),
-        "render_fwd": ("alu", pairs * FWD_FLOP_PER_PAIR),
-        "blend_bwd": ("alu", pairs * BWD_FLOP_PER_PAIR),
+        "render_fwd": ("alu", pairs["fwd_pairs"] * FWD_SLOTS_PER_PAIR),
+        "blend_bwd": ("alu", pairs["bwd_pairs"] * BWD_SLOTS_PER_PAIR),
     }
     kernel = {"preprocess": "k_preprocess", "bin_sort": "sort chain", "project_bwd_adam": "k_project_bwd_adam1",
-              "loss": "loss kernels", "render_fwd": "k_render_fwd", "blend_bwd": "k_render_bwd"}
+              "loss": "loss kernels", "render_fwd": "k_render_fwd_m + k_render_fwd_combine + k_render_fwd_stop",
+              "blend_bwd": "k_render_bwd_m"}
     out = {}
     for name, ms in zip(res["stages"], res["stage_ms"]):
         if name not in work:
@@ -377,11 +384,15 @@ def rooflines(res):
                          "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
         else:
             ach = amount / (ms * 1e-3) / 1e12
+            fwd = name == "render_fwd"
+            units = pairs["fwd_pairs"] if fwd else pairs["bwd_pairs"]
             out[name] = {"kernel": kernel[name], "bound": "alu", "achieved": round(ach, 3),
-                         "peak": round(fp32_tflops, 2), "unit": "TFLOP/s",
-                         "frac": round(ach / fp32_tflops, 4), "traffic": None,
-                         "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz",
-                         "work": f"{pairs:.3e} blended pairs x {FWD_FLOP_PER_PAIR if name == 'render_fwd' else BWD_FLOP_PER_PAIR} FLOP"}
+                         "peak": round(slots, 2), "unit": "TFLOP/s",
+                         "frac": round(ach / slots, 4), "traffic": None,
+                         "peak_source": f"derived: 152 SMs x 128 FP32 lanes x {mhz:.0f} MHz (one issue slot "
+                                        f"per lane per clock; FLOP-equivalent = one FP32 issue slot)",
+                         "work": f"{units:.3e} (pixel, list entry) pairs x "
+                                 f"{FWD_SLOTS_PER_PAIR if fwd else BWD_SLOTS_PER_PAIR} FP32 issue slots"}
         out[name]["share"] = round(float(ms / res["stage_ms"].sum()), 4)
     dom = max(out, key=lambda k: out[k]["share"])
     return out[dom], out
@@ -437,7 +448,7 @@ def main():
         "gpu_launches": res["launches"], "clocks": res["clocks"],
     }
     line["roofline"], line["stage_rooflines"] = rooflines(res)
-    line["blended_pairs_per_view"] = res["pairs"]
+    line["blend_pairs_per_view"] = {k: round(v) for k, v in res["pairs"].items()}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(res["scene"], args.cpu_window)
     if rank == 0:

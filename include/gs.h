@@ -234,15 +234,21 @@ int gs_bin_sort_static(const gs_proj* proj, const gs_units* units, int width, in
  * sched: NULL (one CTA per tile, natural order) or gs_bin_sort's schedule:
  * one-warp jobs per (tile, 8x4 block) in heaviest-first order that skip
  * records whose block mask misses their pixels, and write the per-pixel
- * checkpoints the chunked backward starts from.  Results are identical. */
+ * checkpoints the chunked backward starts from; lists are composited in
+ * parallel chunks of sched->chunk entries and combined in order.  Blended
+ * entries, n_contrib and the stop decisions are those of the sequential walk;
+ * image and final_T agree with it to float rounding. */
 int gs_render_fwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges,
                   int n_units, int width, int height, const float* bg, float* img,
                   float* final_T, uint32_t* n_contrib, int variant, const gs_schedule* sched,
                   gs_stream_t stream);
 
-/* Diagnostic: *d_count = number of blended (pixel, record) pairs of the last
- * gs_render_fwd (records before n_contrib whose alpha reaches 1/255); the
- * algorithmic work unit of the blend kernels. */
+/* Diagnostic work counters of the last gs_render_fwd (device uint64 [3]):
+ * d_count[0] = blended (pixel, record) pairs (records before n_contrib whose
+ * alpha reaches 1/255); d_count[1] = (pixel, list entry) pairs a sequential
+ * front-to-back walk evaluates up to and including the entry that stops the
+ * pixel (the forward's algorithmic work unit); d_count[2] = sum of n_contrib
+ * over pixels (the entries the reverse replay walks: the backward's unit). */
 int gs_blend_pairs(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges,
                    int n_units, int width, int height, const uint32_t* n_contrib,
                    unsigned long long* d_count, gs_stream_t stream);

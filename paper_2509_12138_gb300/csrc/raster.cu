@@ -844,34 +844,55 @@ __global__ void k_order_scatter(const uint2* __restrict__ ranges, int n, const u
   order[s_base[c] + atomicAdd(&cursor[c], 1u)] = (uint32_t)i;
 }
 
-// Number of blended (pixel, record) pairs: records before n_contrib whose
-// alpha reaches 1/255 (the work any implementation of the blend must do).
+// Work counters of one rendered view (diagnostic, outside any timed region):
+// counts[0] = blended (pixel, record) pairs (records before n_contrib whose
+// alpha reaches 1/255); counts[1] = (pixel, list entry) pairs the sequential
+// front-to-back walk evaluates, up to and including the entry that stops the
+// pixel (the forward's algorithmic unit); counts[2] = sum of n_contrib, the
+// entries the reverse replay walks per pixel (the backward's unit).
 __global__ void __launch_bounds__(TILE_PIX) k_blend_pairs(const uint2* __restrict__ ranges,
                                                           const uint32_t* __restrict__ vals,
                                                           const float2* __restrict__ xy,
                                                           const float4* __restrict__ conic_op, int W, int H, int TX,
                                                           int n_tiles, const uint32_t* __restrict__ n_contrib,
-                                                          unsigned long long* __restrict__ count) {
+                                                          unsigned long long* __restrict__ counts) {
   int tile = blockIdx.x, u = blockIdx.y;
   int tx = tile % TX, ty = tile / TX;
   int px = tx * TILE + (threadIdx.x & 15), py = ty * TILE + (threadIdx.x >> 4);
-  unsigned long long c = 0;
+  unsigned long long c = 0, visited = 0, replay = 0;
   if (px < W && py < H) {
     uint2 rg = ranges[(int64_t)u * n_tiles + tile];
+    int L = (int)(rg.y - rg.x);
     int last = (int)n_contrib[(int64_t)u * W * H + (int64_t)py * W + px];
-    for (int j = 0; j < last; ++j) {
+    replay = (unsigned long long)last;
+    float T = 1.f;
+    int j = 0;
+    for (; j < L; ++j) {
       uint32_t p = vals[rg.x + j];
       float2 m = xy[p];
       float4 co = conic_op[p];
       float power = splat_power(co.x, co.y, co.z, m.x - (float)px, m.y - (float)py);
       if (power > 0.f) continue;
       float alpha = fminf(ALPHA_MAX, co.w * __expf(power));
-      if (alpha >= ALPHA_MIN) ++c;
+      if (alpha < ALPHA_MIN) continue;
+      if (j < last) ++c;
+      float tT = T * (1.f - alpha);
+      if (tT < T_MIN) break;
+      T = tT;
     }
+    visited = (unsigned long long)min(j + 1, L);
   }
   #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    visited += __shfl_xor_sync(0xffffffffu, visited, o);
+    replay += __shfl_xor_sync(0xffffffffu, replay, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (c) atomicAdd(&counts[0], c);
+    if (visited) atomicAdd(&counts[1], visited);
+    if (replay) atomicAdd(&counts[2], replay);
+  }
 }
 
 }  // namespace
@@ -957,7 +978,7 @@ GS_API int gs_blend_pairs(const gs_proj* proj, const uint32_t* sorted_vals, cons
       n_units > GS_MAX_UNITS || width <= 0 || height <= 0)
     return GS_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), s) != cudaSuccess) return GS_ERR_CUDA;
+  if (cudaMemsetAsync(d_count, 0, 3 * sizeof(unsigned long long), s) != cudaSuccess) return GS_ERR_CUDA;
   int TX = (width + TILE - 1) / TILE, TY = (height + TILE - 1) / TILE;
   k_blend_pairs<<<dim3(TX * TY, n_units), TILE_PIX, 0, s>>>((const uint2*)ranges, sorted_vals, (const float2*)proj->xy,
                                                             (const float4*)proj->conic_op, width, height, TX, TX * TY,

@@ -286,12 +286,14 @@ class Frame:
     def read_status(self, clear=True) -> int:
         return int(self.L.gs_status_read(_ptr(self.status), 1 if clear else 0, _stream()))
 
-    def blend_pairs(self) -> int:
-        """Blended (pixel, record) pairs of the last forward (diagnostic; synchronises)."""
-        cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
+    def blend_pairs(self) -> dict:
+        """Work counters of the last forward (diagnostic; synchronises): blended (pixel, record) pairs,
+        (pixel, entry) pairs a sequential walk evaluates until each pixel stops, and the sum of n_contrib."""
+        cnt = torch.zeros(3, dtype=torch.int64, device=self.device)
         check(self.L.gs_blend_pairs(C.byref(self.proj), _ptr(self.sorted_vals), _ptr(self.ranges), self.units.n,
                                     self.W, self.H, _ptr(self.n_contrib), _ptr(cnt), _stream()), "gs_blend_pairs")
-        return int(cnt.item())
+        c = cnt.tolist()
+        return {"blended": int(c[0]), "fwd_pairs": int(c[1]), "bwd_pairs": int(c[2])}
 
     def instances(self) -> int:
         return int(self.num_instances.item())

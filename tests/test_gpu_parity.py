@@ -269,3 +269,22 @@ def test_invalid_arguments_rejected_on_host():
     assert L.gs_param_planes(4) == -1 and L.gs_param_planes(3) == 15 and L.gs_param_planes(0) == 4
     rc = L.gs_preprocess(None, 10, 0, None, None, 10, 10, None, None, None, None)
     assert rc == 1
+
+
+def test_blend_work_counters():
+    """The diagnostic counters: the reverse replay's unit is sum(n_contrib); every blended pair lies before
+    n_contrib, and the forward walk evaluates at least the entries up to n_contrib."""
+    import paper_2509_12138_gb300 as gsp
+    n, deg, W, H = 1500, 1, 120, 90
+    g, cams = _case(n, deg, 71, W, H)
+    params = gsp.pack_params(g, deg)
+    camd = gsp.pack_cameras(cams)
+    fr = gsp.Frame(n, gsp.Units.single(n), W, H, deg, with_backward=False, with_loss=False)
+    fr.fit_capacity(params, camd)
+    fr.forward(params, camd, BG)
+    c = fr.blend_pairs()
+    nc = int(fr.n_contrib.sum().item())
+    assert c["bwd_pairs"] == nc > 0
+    assert 0 < c["blended"] <= c["bwd_pairs"] <= c["fwd_pairs"]
+    lens = (fr.ranges[:, 1] - fr.ranges[:, 0]).cpu().numpy()
+    assert c["fwd_pairs"] <= int(lens.sum()) * 256
