@@ -219,8 +219,10 @@ def run_ours(args, wl, rank, world):
     from paper_2509_12138_gb300 import workload
 
     dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2509_12138_gb300 import shard
+    # weak scaling: every rank trains its own independent scene (no collective on the data path)
     scene = workload.isosurface_scene(wl["n"], wl["modes"], wl["views"], wl["W"], wl["H"], sh_degree=3,
-                                      seed=rank, device=dev)
+                                      seed=shard.rank_seed(0, rank), device=dev)
     N, W, H = scene.n, scene.width, scene.height
     params = gs.pack_params(scene.init, 3, dev)
     frame = gs.Frame(N, gs.Units.single(N), W, H, 3, device=dev, max_instances=6 * N)
@@ -429,13 +431,10 @@ def main():
     ms_step = res["ms_total"] / args.steps
     t_max = res["ms_total"]
     e2e_sec = res["e2e_sec"]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_max, e2e_sec], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max, e2e_sec = float(t[0]), float(t[1])
-    value = world * args.steps / (t_max * 1e-3)
-    mpix = world * res["W"] * res["H"] / (res["ms_render"] * 1e-3) / 1e6
+    from paper_2509_12138_gb300 import shard
+    t_max, e2e_sec, r_max = shard.reduce_max([t_max, e2e_sec, res["ms_render"]], device="cuda")
+    value = shard.job_throughput([args.steps] * world, t_max)
+    mpix = shard.job_throughput([res["W"] * res["H"]] * world, r_max) / 1e6
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
@@ -443,7 +442,7 @@ def main():
         "render_mpix_s": round(mpix, 1), "render_ms": round(res["ms_render"], 4),
         "stage_ms": {k: round(float(v), 4) for k, v in zip(res["stages"], res["stage_ms"])},
         "instances_per_view": res["instances"], "tile_list_len": res["tile_len"],
-        "e2e": {"value": round(world * args.steps / e2e_sec, 3), "unit": "iters/s",
+        "e2e": {"value": round(shard.job_throughput([args.steps] * world, e2e_sec * 1e3), 3), "unit": "iters/s",
                 "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
         "gpu_launches": res["launches"], "clocks": res["clocks"],
     }

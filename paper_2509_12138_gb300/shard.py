@@ -1,0 +1,81 @@
+"""Host logic of the multi-GPU form: one process per GPU, partitions as independent units.
+
+The partitions of the method (Sec. II, "Data Partitioning" / "Parallel Training") are independent
+problems: each trains on its own Gaussians, views and masks with no communication.  Across GPUs they
+are sharded with no collective on the data path; the only collectives are the timing reduction of a
+measurement (max over ranks) and the merge (Sec. II, "Global Reconstruction"), which gathers every
+rank's owned splats to the rank that renders them.
+
+Nothing here launches GPU work; the collectives run on whatever backend the caller's process group
+uses (NCCL on GPUs, gloo on the CPU in the tests).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+
+def rank_seed(base_seed: int, rank: int) -> int:
+    """Seed of rank `rank`'s independent scene (weak scaling: every rank its own problem)."""
+    return int(base_seed) + 1_000_003 * int(rank)
+
+
+def assign_units(sizes, world: int) -> list[list[int]]:
+    """Deterministic longest-processing-time assignment of units (e.g. partitions, weighted by their
+    Gaussian counts) to `world` ranks: units in decreasing size, each to the least-loaded rank (ties to
+    the lower rank).  Every rank computes the same assignment from the same sizes without communicating."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    sizes = np.asarray(sizes, dtype=np.int64)
+    order = sorted(range(len(sizes)), key=lambda i: (-int(sizes[i]), i))
+    load = [0] * world
+    out: list[list[int]] = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        out[r].append(i)
+        load[r] += int(sizes[i])
+    for r in range(world):
+        out[r].sort()
+    return out
+
+
+def reduce_max(values, device=None) -> list[float]:
+    """Element-wise max over ranks of a few host scalars (the timing of a measurement); identity when
+    torch.distributed is not initialised."""
+    import torch.distributed as dist
+    vals = [float(v) for v in values]
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return vals
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_throughput(units_per_rank, t_max_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed divided by the slowest rank's time."""
+    return float(sum(units_per_rank)) / (float(t_max_ms) * 1e-3)
+
+
+def gather_owned(params: torch.Tensor, keep: torch.Tensor, dst: int = 0):
+    """Merge exchange: every rank contributes the columns of its parameter planes `params` [planes, n, 4]
+    whose `keep` flag is set (its owned Gaussians); rank `dst` receives all of them concatenated in rank
+    order ([planes, total, 4]), the other ranks None.  Sizes travel first (all_gather), then the padded
+    blocks (gather), so ranks may own different numbers of Gaussians."""
+    import torch.distributed as dist
+    mine = params[:, keep.to(torch.bool)].contiguous()
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return mine
+    world, rank = dist.get_world_size(), dist.get_rank()
+    n = torch.tensor([mine.shape[1]], dtype=torch.int64, device=params.device)
+    counts = [torch.zeros_like(n) for _ in range(world)]
+    dist.all_gather(counts, n)
+    counts = [int(c.item()) for c in counts]
+    cap = max(max(counts), 1)
+    pad = torch.zeros((params.shape[0], cap, params.shape[2]), dtype=params.dtype, device=params.device)
+    pad[:, : mine.shape[1]] = mine
+    if rank == dst:
+        bufs = [torch.empty_like(pad) for _ in range(world)]
+        dist.gather(pad, gather_list=bufs, dst=dst)
+        return torch.cat([b[:, :c] for b, c in zip(bufs, counts)], dim=1)
+    dist.gather(pad, dst=dst)
+    return None

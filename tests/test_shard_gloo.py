@@ -1,0 +1,106 @@
+"""The multi-GPU host path on the CPU: two gloo ranks (no GPU).
+
+Covers what runs across processes: every rank derives the same unit assignment without communicating,
+the measurement's max-over-ranks timing and whole-job throughput, independent per-rank seeds, and the
+merge exchange (owned splats of every rank gathered in rank order to the renderer)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+from paper_2509_12138_gb300 import shard
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, outdir):
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        # 1. the same assignment on every rank, computed locally
+        sizes = [500_000, 1_500_000, 2_500_000, 3_500_000, 4_000_000, 4_500_000, 5_500_000, 6_000_000]
+        asg = shard.assign_units(sizes, world)
+        flat = torch.tensor([u for r in asg for u in r] + [len(r) for r in asg], dtype=torch.int64)
+        got = [torch.zeros_like(flat) for _ in range(world)]
+        dist.all_gather(got, flat)
+        same = all(torch.equal(g, flat) for g in got)
+        # 2. timing: each rank's own time; the reduction gives the slowest on every rank
+        t_local = 10.0 + 5.0 * rank
+        t_max, e_max = shard.reduce_max([t_local, 100.0 - rank])
+        # 3. merge exchange: rank r owns the Gaussians of its slab; keep flags select them
+        n = 5 + 3 * rank
+        params = torch.arange(2 * n * 4, dtype=torch.float32).reshape(2, n, 4) + 1000.0 * rank
+        keep = torch.tensor([(i % 2 == 0) or rank == 1 for i in range(n)])
+        merged = shard.gather_owned(params, keep, dst=0)
+        seed = shard.rank_seed(7, rank)
+        np.savez(os.path.join(outdir, f"r{rank}.npz"), same=same, t_max=t_max, e_max=e_max,
+                 merged=(merged.numpy() if merged is not None else np.zeros(0)), has=merged is not None, seed=seed,
+                 mine=np.asarray(asg[rank]))
+    finally:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+@pytest.fixture(scope="module")
+def two_ranks(tmp_path_factory):
+    out = tmp_path_factory.mktemp("gloo")
+    mp.start_processes(_worker, args=(2, _free_port(), str(out)), nprocs=2, join=True, start_method="spawn")
+    return [np.load(out / f"r{r}.npz") for r in range(2)]
+
+
+def test_assignment_identical_on_all_ranks_and_covers_each_unit_once(two_ranks):
+    assert all(bool(r["same"]) for r in two_ranks)
+    units = sorted(int(u) for r in two_ranks for u in r["mine"])
+    assert units == list(range(8))
+
+
+def test_assignment_balances_by_size():
+    sizes = [500_000, 1_500_000, 2_500_000, 3_500_000, 4_000_000, 4_500_000, 5_500_000, 6_000_000]
+    for world in (1, 2, 4, 8):
+        asg = shard.assign_units(sizes, world)
+        loads = [sum(sizes[u] for u in r) for r in asg]
+        assert sorted(u for r in asg for u in r) == list(range(8))
+        # LPT bound: the heaviest rank exceeds the mean by at most the largest unit
+        assert max(loads) <= sum(sizes) / world + max(sizes)
+    assert shard.assign_units(sizes, 8) == [[7], [6], [5], [4], [3], [2], [1], [0]]
+    with pytest.raises(ValueError):
+        shard.assign_units(sizes, 0)
+
+
+def test_timing_is_the_max_over_ranks(two_ranks):
+    for r in two_ranks:
+        assert float(r["t_max"]) == 15.0 and float(r["e_max"]) == 100.0
+    # whole-job throughput: both ranks' units over the slowest rank's time
+    assert shard.job_throughput([50, 50], 15.0) == pytest.approx(100 / 0.015)
+
+
+def test_ranks_get_independent_seeds(two_ranks):
+    assert int(two_ranks[0]["seed"]) != int(two_ranks[1]["seed"])
+    assert shard.rank_seed(7, 0) == 7
+
+
+def test_merge_gathers_owned_splats_in_rank_order(two_ranks):
+    assert bool(two_ranks[0]["has"]) and not bool(two_ranks[1]["has"])
+    expect = []
+    for rank in range(2):
+        n = 5 + 3 * rank
+        p = np.arange(2 * n * 4, dtype=np.float32).reshape(2, n, 4) + 1000.0 * rank
+        keep = np.array([(i % 2 == 0) or rank == 1 for i in range(n)])
+        expect.append(p[:, keep])
+    np.testing.assert_array_equal(two_ranks[0]["merged"], np.concatenate(expect, axis=1))
+
+
+def test_single_process_paths_need_no_process_group():
+    p = torch.ones((3, 4, 4))
+    keep = torch.tensor([True, False, True, True])
+    assert shard.gather_owned(p, keep).shape == (3, 3, 4)
+    assert shard.reduce_max([1.0, 2.0]) == [1.0, 2.0]
