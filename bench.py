@@ -201,15 +201,21 @@ def cpu_baseline(scene, frac: int):
 
 # ---------------------------------------------------------------- our arm
 def kernel_launch_count(frame, lam):
+    """Kernels libgs launches for one training step (a1-a6) of this frame; matches the ncu launch list
+    of the timed steps (profiles/launches_iso10M-1080p.md: 38 at 1080p)."""
     tile_bits = max(1, math.ceil(math.log2(frame.n_tiles)))
     unit_bits = math.ceil(math.log2(frame.units.n)) if frame.units.n > 1 else 0
-    passes = (32 + tile_bits + unit_bits + 7) // 8
-    pre = 1
-    sort = 4 + 3 * passes + 1
-    fwd = 1
-    loss = 1 + (2 if lam > 0 else 1) + 1
+    key_bits = 32 + tile_bits + unit_bits
+    passes = min(-(-key_bits // 9), -(-key_bits // 8))  # 9-bit digits when they save a pass
+    pre = 1                                   # k_preprocess
+    sort = 3 + 1 + 3 * passes + 1             # tiles scan, k_duplicate, (hist, scan, scatter) per pass, k_ranges
+    sched = frame.use_masks
+    if sched:
+        sort += 2 + 1 + 3 + 1                 # tile order, chunk counts, their scan, chunk jobs
+    fwd = 3 if sched else 1                   # chunk partials, combine, stop chunks
+    loss = 1 + (2 if lam > 0 else 1) + 1      # mask count, SSIM stats + gradient (or L1), final
     bwd = 1
-    adam = 2
+    adam = 2                                  # fused projection backward + Adam, step counter
     return pre + sort + fwd + loss + bwd + adam
 
 
