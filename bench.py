@@ -561,22 +561,46 @@ def run_merge(args, wl):
     need = max(fr.fit_capacity(params, camd[v * 96:(v + 1) * 96], owned) for v in range(wl["views"]))
     fr.set_capacity(int(need * 1.1) + 4096)
     V = wl["views"]
-    for k in range(args.warmup):
-        fr.forward(params, camd[(k % V) * 96:(k % V + 1) * 96], (1.0, 1.0, 1.0), owned)
+    # forward mode: whole-list walks (opaque renders stop early) or chunk-parallel compositing, whichever
+    # renders the warm-up views faster
+    mode_ms = {}
+    for whole in (True, False):
+        fr.walk_whole_lists = whole
+        fr.forward(params, camd[0:96], (1.0, 1.0, 1.0), owned)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for k in range(args.warmup):
+            fr.forward(params, camd[(k % V) * 96:(k % V + 1) * 96], (1.0, 1.0, 1.0), owned)
+        t1.record()
+        torch.cuda.synchronize()
+        mode_ms["whole_lists" if whole else "parallel_chunks"] = round(t0.elapsed_time(t1) / max(args.warmup, 1), 3)
+    fr.walk_whole_lists = mode_ms["whole_lists"] <= mode_ms["parallel_chunks"]
     torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for k in range(args.steps):
         v = (args.warmup + k) % V
-        fr.forward(params, camd[v * 96:(v + 1) * 96], (1.0, 1.0, 1.0), owned)
+        cam = camd[v * 96:(v + 1) * 96]
+        ev[k][0].record()
+        fr.preprocess(params, cam, owned)
+        ev[k][1].record()
+        fr.sort()
+        ev[k][2].record()
+        fr.render((1.0, 1.0, 1.0))
+        ev[k][3].record()
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / args.steps
+    stage = {name: round(float(np.mean([e[i].elapsed_time(e[i + 1]) for e in ev])), 3)
+             for i, name in enumerate(["preprocess", "bin_sort", "render_fwd"])}
     st = fr.read_status()
     kept = int((fr.radius > 0).sum())
     line = {"metric": "merged render (ghost filter + projection + sort + blend), 100M Gaussians SH3, 3840x2160",
             "value": round(wl["W"] * wl["H"] / (ms * 1e-3) / 1e6, 2), "unit": "Mpix/s", "ms_per_frame": round(ms, 3),
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+            "stage_ms": stage, "forward_mode": {"chosen": "whole_lists" if fr.walk_whole_lists else "parallel_chunks",
+                                                "warmup_ms_per_frame": mode_ms},
             "data": "synthetic", "config": {"workload": args.workload, "gaussians_with_ghosts": N,
                                             "partitions": 8, "ghost": 0.05, "visible_after_filter_last_view": kept,
                                             "instances_last_view": fr.instances()},

@@ -117,7 +117,11 @@ typedef struct gs_grad2d {
  *                                 blended entry of each chunk and a stop flag
  * chunk        entries per chunk (a multiple of 32); max_jobs >= U n_tiles +
  *              max_instances / chunk + 1, max_checkpoints >= max_instances /
- *              chunk + 1 (gs_schedule_sizes). */
+ *              chunk + 1 (gs_schedule_sizes).
+ * walk_whole_lists  0: the forward composites the chunks of a list in
+ *              parallel and combines them (training views, whose pixels rarely
+ *              stop early); 1: one warp per (list, pixel block) walks the whole
+ *              list and stops at its last pixel's stop (opaque renders). */
 typedef struct gs_schedule {
   uint32_t* tile_order;
   uint16_t* block_masks;
@@ -128,6 +132,7 @@ typedef struct gs_schedule {
   int64_t max_jobs;
   int64_t max_checkpoints;
   int32_t chunk;
+  int32_t walk_whole_lists;
 } gs_schedule;
 
 /* Unit table (host arrays, copied by value into the launch). */
@@ -335,13 +340,16 @@ int gs_step_advance(int32_t* d_step, gs_stream_t stream);
  * camera (device, 1 entry), one image [3][H][W].  Equivalent to
  * gs_preprocess (one unit over all N, with `owned`) + gs_bin_sort +
  * gs_render_fwd; proj must hold N records and the workspace
- * gs_bin_sort_workspace_size(N, max_instances) bytes. */
+ * gs_bin_sort_workspace_size(N, max_instances) bytes.  sched: NULL, or a
+ * schedule sized for one unit of width x height and max_instances (see
+ * gs_schedule), which the sort fills and the forward uses (block masks,
+ * heaviest-first order). */
 int gs_merge_render(const float* params, int64_t n_gauss, int sh_degree, const gs_owned* owned,
                     const gs_camera* cam, int width, int height, const float* bg,
                     const gs_proj* proj, int64_t max_instances, void* workspace,
                     size_t workspace_bytes, uint32_t* sorted_vals, uint32_t* ranges,
                     uint32_t* d_num_instances, float* img, float* final_T, uint32_t* n_contrib,
-                    int* d_status, gs_stream_t stream);
+                    const gs_schedule* sched, int* d_status, gs_stream_t stream);
 
 /* ---- a9: learned initialiser --------------------------------------------
  * Not in the paper: its Sec. II initialises the Gaussians from the extracted

@@ -37,7 +37,7 @@ class GsGrad2d(C.Structure):
 class GsSchedule(C.Structure):
     _fields_ = [("tile_order", C.c_void_p), ("block_masks", C.c_void_p), ("job_base", C.c_void_p),
                 ("jobs", C.c_void_p), ("checkpoints", C.c_void_p), ("chunk_last", C.c_void_p), ("max_jobs", C.c_int64),
-                ("max_checkpoints", C.c_int64), ("chunk", C.c_int32)]
+                ("max_checkpoints", C.c_int64), ("chunk", C.c_int32), ("walk_whole_lists", C.c_int32)]
 
 
 class GsUnits(C.Structure):
@@ -89,7 +89,7 @@ SIGNATURES = {
     "gs_mlp_train_step": (I32, [VP, VP, VP, VP, VP, I64, VP, VP, VP, VP, F32, VP, VP, VP]),
     "gs_init_gaussians": (I32, [VP, VP, VP, VP, I32, I64, VP, F32, VP, I64, VP]),
     "gs_merge_render": (I32, [VP, I64, I32, C.POINTER(GsOwned), VP, I32, I32, c_f32p, C.POINTER(GsProj), I64, VP, SZ,
-                              VP, VP, VP, VP, VP, VP, VP, VP]),
+                              VP, VP, VP, VP, VP, VP, C.POINTER(GsSchedule), VP, VP]),
 }
 
 OPTIONAL = set()

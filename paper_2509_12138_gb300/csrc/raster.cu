@@ -635,6 +635,52 @@ __global__ void __launch_bounds__(32) k_render_fwd_stop(const uint2* __restrict_
   nc[pix] = (uint32_t)last;
 }
 
+// Forward walking whole lists: one warp per (list, pixel block) in tile order
+// composites its list chunk after chunk and stores (T, C) of each pixel in
+// front of every interior chunk boundary (the backward's checkpoints); after
+// an early exit the remaining checkpoints hold the final state.  No work
+// follows a block's last stop, which suits renders whose pixels mostly stop
+// near the front of their lists (opaque, trained scenes).
+template <int BW>
+__global__ void __launch_bounds__(32) k_render_fwd_seq(const uint2* __restrict__ ranges,
+                                                             const uint32_t* __restrict__ order,
+                                                             const uint32_t* __restrict__ job_base, int K,
+                                                             float4* __restrict__ ckpt,
+                                                             const uint32_t* __restrict__ vals,
+                                                             const uint16_t* __restrict__ masks,
+                                                             const float2* __restrict__ xy,
+                                                             const float4* __restrict__ conic_op,
+                                                             const float4* __restrict__ rgb, int W, int H, int TX,
+                                                             int n_tiles, float bg0, float bg1, float bg2,
+                                                             float* __restrict__ img, float* __restrict__ final_T,
+                                                             uint32_t* __restrict__ n_contrib) {
+  __shared__ Rec s_rec[32];
+  int o = (int)(blockIdx.x >> 3), w = (int)(blockIdx.x & 7u);
+  PixelOf<BW> P(order, o, w, n_tiles, TX, W, H);
+  uint2 rg = ranges[(int64_t)P.u * n_tiles + P.tile];
+  int L = (int)(rg.y - rg.x);
+  int nch = (int)(job_base[o + 1] - job_base[o]);
+  int64_t cp0 = (int64_t)job_base[o] - o;
+  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+  int last = 0;
+  bool done = !P.inside;
+  for (int c = 0; c < max(nch, 1); ++c) {
+    if (c > 0 && P.inside) ckpt[(cp0 + c - 1) * TILE_PIX + P.pix_local] = make_float4(T, c0, c1, c2);
+    walk_fwd(vals, masks, xy, conic_op, rgb, rg.x, c * K, min(c * K + K, L), P.wbits, (float)P.px, (float)P.py,
+             s_rec, T, c0, c1, c2, last, done);
+  }
+  if (P.inside) {
+    int64_t plane = (int64_t)W * H;
+    int64_t pix = (int64_t)P.py * W + P.px;
+    float* im = img + (int64_t)P.u * 3 * plane;
+    im[pix] = c0 + T * bg0;
+    im[plane + pix] = c1 + T * bg1;
+    im[2 * plane + pix] = c2 + T * bg2;
+    final_T[(int64_t)P.u * plane + pix] = T;
+    n_contrib[(int64_t)P.u * plane + pix] = (uint32_t)last;
+  }
+}
+
 // Contributing lanes up to which the scheduled backward skips the warp
 // reduction of a record's nine gradient values and lets each lane issue its
 // own vector atomics.  L2 absorbs these well: at 1M and 10M Gaussians per
@@ -907,7 +953,12 @@ int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const u
   int TX = (width + TILE - 1) / TILE, TY = (height + TILE - 1) / TILE;
   dim3 grid(TX * TY * n_units);
 #define GS_FWD(BW)                                                                                                  \
-  if (sched) {                                                                                                      \
+  if (sched && sched->walk_whole_lists) {                                                                          \
+    k_render_fwd_seq<BW><<<dim3(grid.x * 8), 32, 0, s>>>(                                                           \
+        (const uint2*)ranges, sched->tile_order, sched->job_base, sched->chunk, (float4*)sched->checkpoints,        \
+        sorted_vals, sched->block_masks, (const float2*)proj->xy, (const float4*)proj->conic_op,                    \
+        (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib);        \
+  } else if (sched) {                                                                                               \
     dim3 gj((unsigned)(sched->max_jobs * 8));                                                                       \
     k_render_fwd_m<BW><<<gj, 32, 0, s>>>(                                                                           \
         (const uint2*)ranges, sched->tile_order, sched->job_base, sched->jobs, sched->chunk, (int)grid.x,            \

@@ -636,15 +636,15 @@ GS_API int gs_merge_render(const float* params, int64_t n_gauss, int sh_degree, 
                            const gs_camera* cam, int width, int height, const float* bg, const gs_proj* proj,
                            int64_t max_instances, void* workspace, size_t workspace_bytes, uint32_t* sorted_vals,
                            uint32_t* ranges, uint32_t* d_num_instances, float* img, float* final_T,
-                           uint32_t* n_contrib, int* d_status, gs_stream_t stream) {
+                           uint32_t* n_contrib, const gs_schedule* sched, int* d_status, gs_stream_t stream) {
   if (!owned || owned->n_parts < 1) return GS_ERR_INVALID;
   int64_t begin = 0, count = n_gauss;
   gs_units one = {1, &begin, &count};
   int r = gs_preprocess(params, n_gauss, sh_degree, &one, cam, width, height, owned, proj, d_status, stream);
   if (r != GS_OK) return r;
   r = gs_bin_sort_impl(proj, &one, width, height, max_instances, workspace, workspace_bytes, sorted_vals, ranges,
-                       d_num_instances, nullptr, d_status, (cudaStream_t)stream);
+                       d_num_instances, sched, d_status, (cudaStream_t)stream);
   if (r != GS_OK) return r;
-  return gs_render_fwd_impl(proj, sorted_vals, ranges, 1, width, height, bg, img, final_T, n_contrib, 0, nullptr,
+  return gs_render_fwd_impl(proj, sorted_vals, ranges, 1, width, height, bg, img, final_T, n_contrib, 0, sched,
                             (cudaStream_t)stream);
 }

@@ -145,6 +145,9 @@ class Frame:
         self.variant = int(variant)
         self.chunk = int(chunk)
         self.use_masks = True  # per-instance block masks from the sort drive the blend kernels' culling
+        # forward: chunks of a list composited in parallel and combined (False), or one walk per list
+        # that stops at its pixels' last stop (True: renders of opaque, trained scenes)
+        self.walk_whole_lists = False
         self.device = torch.device(device)
         self.N = int(n_gauss)
         self.units = units
@@ -183,7 +186,10 @@ class Frame:
             self.grads = torch.zeros((self.planes, max(self.N, 1), 4), **f32)
 
     def _sched(self):
-        return C.byref(self.sched) if self.use_masks else None
+        if not self.use_masks:
+            return None
+        self.sched.walk_whole_lists = 1 if self.walk_whole_lists else 0
+        return C.byref(self.sched)
 
     def set_capacity(self, max_instances: int):
         self.cap = int(max_instances)
@@ -280,7 +286,8 @@ class Frame:
                                      self.H, bgc, C.byref(self.proj), self.cap, _ptr(self.sort_ws),
                                      self.sort_ws.numel(), _ptr(self.sorted_vals), _ptr(self.ranges),
                                      _ptr(self.num_instances), _ptr(self.img), _ptr(self.final_T),
-                                     _ptr(self.n_contrib), _ptr(self.status), _stream()), "gs_merge_render")
+                                     _ptr(self.n_contrib), self._sched(), _ptr(self.status), _stream()),
+              "gs_merge_render")
         return self.img
 
     def read_status(self, clear=True) -> int:

@@ -20,8 +20,11 @@ def _subset(g, idx):
     return {k: np.asarray(v)[idx] for k, v in g.items()}
 
 
-def test_merge_render_parity():
-    """Ghost-filtered merged render equals the oracle's render of the Gaussians the oracle's filter keeps."""
+@pytest.mark.parametrize("use_masks,chunk,whole", [(False, 1024, False), (True, 1024, False), (True, 32, False),
+                                                   (True, 32, True)])
+def test_merge_render_parity(use_masks, chunk, whole):
+    """Ghost-filtered merged render equals the oracle's render of the Gaussians the oracle's filter keeps,
+    with and without the blend schedule."""
     n, deg, W, H = 3000, 1, 160, 120
     g = synth.random_gaussians(n, deg, 5, center=(0.5, 0.5, 0.5), extent=0.5, log_scale_range=(-4.0, -2.5))
     part = slab_partition(g["means"], 4, 0.1)
@@ -32,7 +35,9 @@ def test_merge_render_parity():
     N = len(order)
     cams = scenes.front_camera(W, H, eye=(0.5, -2.0, 1.5), target=(0.5, 0.5, 0.5))
     owned = gs.Owned(part.offsets, part.boxes, part.closed_hi)
-    fr = gs.Frame(N, gs.Units.single(N), W, H, deg, with_backward=False, with_loss=False)
+    fr = gs.Frame(N, gs.Units.single(N), W, H, deg, with_backward=False, with_loss=False, chunk=chunk)
+    fr.use_masks = use_masks
+    fr.walk_whole_lists = whole
     params = gs.pack_params(gp, deg)
     camd = gs.pack_cameras(cams)
     fr.fit_capacity(params, camd, owned)
@@ -234,16 +239,19 @@ def test_fused_projection_backward_adam_matches_separate(n_views):
     assert torch.allclose(pa, pb, rtol=1e-5, atol=1e-5)
 
 
-@pytest.mark.parametrize("chunk,opaque,n", [(32, False, 3000), (96, False, 3000), (1024, False, 3000),
-                                            (32, True, 3000), (96, True, 3000), (32, True, 60000)])
-def test_schedule_does_not_change_results(chunk, opaque, n):
+@pytest.mark.parametrize("chunk,opaque,n,whole", [(32, False, 3000, False), (96, False, 3000, False),
+                                                  (1024, False, 3000, False), (32, True, 3000, False),
+                                                  (96, True, 3000, False), (32, True, 60000, False),
+                                                  (32, True, 3000, True), (1024, False, 3000, True)])
+def test_schedule_does_not_change_results(chunk, opaque, n, whole):
     """The blend schedule (heaviest-first order, per-instance block masks, lists composited in parallel
     chunks and combined, stop chunks walked again, backward replayed in chunks from the combined
     checkpoints) only skips and reorders work.  Combining per-chunk (T, C) products changes the rounding
     order only: images agree to float rounding, n_contrib exactly, gradients up to atomic order.  Small
     chunks put many chunks on every list; the opaque scenes make most pixels stop after the first chunk,
     so the stop-chunk walk and the checkpoints after a stop are exercised; the dense scene has lists of
-    more than 128 chunks, whose stop chunks the combine pass walks itself."""
+    more than 128 chunks, whose stop chunks the combine pass walks itself.  With whole-list walks the
+    per-pixel arithmetic is that of the unscheduled kernel, so images are bit-identical."""
     deg, W, H = 1, 150, 110
     g, cams = scenes.random_scene(n, deg, 31, W, H)
     if opaque:
@@ -256,6 +264,7 @@ def test_schedule_does_not_change_results(chunk, opaque, n):
     for use_sched in (False, True):
         fr = gs.Frame(n, gs.Units.single(n), W, H, deg, chunk=chunk)
         fr.use_masks = use_sched
+        fr.walk_whole_lists = whole
         fr.fit_capacity(params, camd)
         fr.forward(params, camd, BG)
         fr.loss(torch.from_numpy(gt).cuda()[None], torch.from_numpy(mask).cuda()[None], 0.2)
@@ -276,6 +285,8 @@ def test_schedule_does_not_change_results(chunk, opaque, n):
         assert float(stopped.float().mean()) > 0.2  # the early stop is exercised
         assert float((a[1][stopped] > chunk).float().mean()) > 0.3  # ... often after the first chunk
     assert torch.equal(a[1], b[1])
+    if whole:
+        assert torch.equal(a[0], b[0]) and torch.equal(a[4], b[4])
     assert torch.allclose(a[0], b[0], rtol=0, atol=1e-5)
     assert torch.allclose(a[4], b[4], rtol=1e-4, atol=1e-7)
     sc = float(a[2].abs().max())
