@@ -202,12 +202,12 @@ def cpu_baseline(scene, frac: int):
 # ---------------------------------------------------------------- our arm
 def kernel_launch_count(frame, lam):
     """Kernels libgs launches for one training step (a1-a6) of this frame; matches the ncu launch list
-    of the timed steps (profiles/launches_iso10M-1080p.md: 38 at 1080p)."""
+    of the timed steps (profiles/launches_iso10M-1080p.md)."""
     tile_bits = max(1, math.ceil(math.log2(frame.n_tiles)))
     unit_bits = math.ceil(math.log2(frame.units.n)) if frame.units.n > 1 else 0
     key_bits = 32 + tile_bits + unit_bits
-    passes = min(-(-key_bits // 9), -(-key_bits // 8))  # 9-bit digits when they save a pass
     pre = 1                                   # k_preprocess
+    passes = min(-(-key_bits // 9), -(-key_bits // 8))  # 9-bit digits when they save a pass
     sort = 3 + 1 + 3 * passes + 1             # tiles scan, k_duplicate, (hist, scan, scatter) per pass, k_ranges
     sched = frame.use_masks
     if sched:
@@ -300,7 +300,20 @@ def run_ours(args, wl, rank, world):
         pairs.append(frame.blend_pairs())
     pairs_per_step = {key: float(np.mean([p[key] for p in pairs])) for key in pairs[0]}
 
-    # render-only (a1-a3) for Mpix/s
+    # render-only (a1-a3) for Mpix/s, in the faster forward mode on a few views (whole-list walks stop early
+    # on opaque views; chunk-parallel compositing wins where pixels rarely stop)
+    mode_ms = {}
+    for whole in (False, True):
+        frame.walk_whole_lists = whole
+        frame.forward(params, scene.cam(0), bg)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for k in range(4):
+            frame.forward(params, scene.cam(k % V), bg)
+        t1.record()
+        torch.cuda.synchronize()
+        mode_ms["whole_lists" if whole else "parallel_chunks"] = round(t0.elapsed_time(t1) / 4, 3)
+    frame.walk_whole_lists = mode_ms["whole_lists"] < mode_ms["parallel_chunks"]
     torch.cuda.synchronize()
     r0 = torch.cuda.Event(enable_timing=True)
     r1 = torch.cuda.Event(enable_timing=True)
@@ -310,6 +323,8 @@ def run_ours(args, wl, rank, world):
     r1.record()
     torch.cuda.synchronize()
     ms_render = r0.elapsed_time(r1) / args.steps
+    render_mode = {"chosen": "whole_lists" if frame.walk_whole_lists else "parallel_chunks", "ms_per_frame": mode_ms}
+    frame.walk_whole_lists = False  # the training step below uses the chunk-parallel forward
     clk = clocks.stop()
 
     # end to end through the public API with host buffers: each step copies its GT view and mask from
@@ -340,7 +355,8 @@ def run_ours(args, wl, rank, world):
     e_sec = time.perf_counter() - e0
     barrier()
     return dict(scene=scene, frame=frame, ms_total=ms_total, stage_ms=stage_ms, stages=stages, ms_render=ms_render,
-                clocks=clk, e2e_sec=e_sec, instances=instances, tile_len=tile_len, pairs=pairs_per_step, h2d=(3 * H * W * 4 + H * W), d2h=4,
+                clocks=clk, e2e_sec=e_sec, instances=instances, tile_len=tile_len, pairs=pairs_per_step,
+                render_mode=render_mode, h2d=(3 * H * W * 4 + H * W), d2h=4,
                 launches=kernel_launch_count(frame, LAMBDA_SSIM) * args.steps, N=N, W=W, H=H)
 
 
@@ -445,7 +461,7 @@ def main():
         "metric": METRIC, "value": round(value, 3), "unit": "iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
-        "render_mpix_s": round(mpix, 1), "render_ms": round(res["ms_render"], 4),
+        "render_mpix_s": round(mpix, 1), "render_ms": round(res["ms_render"], 4), "render_mode": res["render_mode"],
         "stage_ms": {k: round(float(v), 4) for k, v in zip(res["stages"], res["stage_ms"])},
         "instances_per_view": res["instances"], "tile_list_len": res["tile_len"],
         "e2e": {"value": round(shard.job_throughput([args.steps] * world, e2e_sec * 1e3), 3), "unit": "iters/s",
