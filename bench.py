@@ -327,27 +327,45 @@ def run_ours(args, wl, rank, world):
     frame.walk_whole_lists = False  # the training step below uses the chunk-parallel forward
     clk = clocks.stop()
 
-    # end to end through the public API with host buffers: each step copies its GT view and mask from
-    # pinned host memory, runs the step and reads the loss back
+    # end to end through the public API with host buffers: each step's GT view and mask are copied from
+    # pinned host memory (on a copy stream, one step ahead into a double buffer, so the copy of step k+1
+    # overlaps step k's kernels), the step runs and its loss is read back
     gt_host = torch.empty((V, 3, H, W), dtype=torch.float32).pin_memory()
     mask_host = torch.empty((V, H, W), dtype=torch.uint8).pin_memory()
     gt_host.copy_(scene.gt)
     mask_host.copy_(scene.mask)
-    gt_dev = torch.empty((1, 3, H, W), dtype=torch.float32, device=dev)
-    mask_dev = torch.empty((1, H, W), dtype=torch.uint8, device=dev)
+    gt_dev = [torch.empty((1, 3, H, W), dtype=torch.float32, device=dev) for _ in range(2)]
+    mask_dev = [torch.empty((1, H, W), dtype=torch.uint8, device=dev) for _ in range(2)]
     loss_host = torch.empty(args.steps, dtype=torch.float32).pin_memory()
+    copy_stream = torch.cuda.Stream(device=dev)
+    ready = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
+    main = torch.cuda.current_stream()
+
+    def fetch(k):
+        b, v = k % 2, (args.warmup + k) % V  # the same views as the device-timed loop
+        with torch.cuda.stream(copy_stream):
+            if k >= 2:
+                copy_stream.wait_event(consumed[b])  # step k-2's loss has read buffer b
+            gt_dev[b][0].copy_(gt_host[v], non_blocking=True)
+            mask_dev[b][0].copy_(mask_host[v], non_blocking=True)
+            ready[b].record(copy_stream)
+
     torch.cuda.synchronize()
     barrier()
     e0 = time.perf_counter()
+    fetch(0)
     for k in range(args.steps):
-        v = (args.warmup + k) % V  # the same views as the device-timed loop
-        gt_dev[0].copy_(gt_host[v], non_blocking=True)
-        mask_dev[0].copy_(mask_host[v], non_blocking=True)
+        if k + 1 < args.steps:
+            fetch(k + 1)
+        b, v = k % 2, (args.warmup + k) % V
         cam = scene.cam(v)
         frame.preprocess(params, cam)
         frame.sort()
         frame.render(bg)
-        frame.loss(gt_dev, mask_dev, LAMBDA_SSIM)
+        main.wait_event(ready[b])
+        frame.loss(gt_dev[b], mask_dev[b], LAMBDA_SSIM)
+        consumed[b].record(main)
         frame.blend_backward(bg)
         opt.fused_step(frame, cam)
         loss_host[k:k + 1].copy_(frame.loss_val, non_blocking=True)
