@@ -96,11 +96,19 @@ typedef struct gs_proj {
   uint32_t* tiles;  /* [P]     number of 16x16 tiles the splat touches     */
 } gs_proj;
 
-/* Screen-space gradients (accumulated by gs_render_bwd). */
+/* Screen-space gradients (accumulated by gs_render_bwd / gs_blend_bwd).
+ * fixed: NULL (float atomics: sums depend on the order in which warps add,
+ * within float rounding), or [P][9] int64 scratch (deterministic mode): the
+ * nine values per record (dx, dy, dA, dB, dC, d opacity, dr, dg, db)
+ * accumulate as fixed point value x 2^40 (|value| clamped to 2^22, NaN adds
+ * 0), whose integer sums do not depend on order, and are converted into
+ * dxy / dconic_op / drgb at the end of the call: gradients are bitwise
+ * reproducible. */
 typedef struct gs_grad2d {
   float* dxy;       /* [P][2] */
   float* dconic_op; /* [P][4] (dA, dB, dC, d opacity) */
   float* drgb;      /* [P][4] */
+  unsigned long long* fixed; /* [P][9] or NULL */
 } gs_grad2d;
 
 /* Blend schedule (all device buffers; see gs_bin_sort and the blend calls):

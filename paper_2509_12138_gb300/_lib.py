@@ -31,7 +31,7 @@ class GsProj(C.Structure):
 
 
 class GsGrad2d(C.Structure):
-    _fields_ = [("dxy", C.c_void_p), ("dconic_op", C.c_void_p), ("drgb", C.c_void_p)]
+    _fields_ = [("dxy", C.c_void_p), ("dconic_op", C.c_void_p), ("drgb", C.c_void_p), ("fixed", C.c_void_p)]
 
 
 class GsSchedule(C.Structure):

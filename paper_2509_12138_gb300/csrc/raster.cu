@@ -33,6 +33,41 @@ __device__ __forceinline__ void atomic_add4(float* p, float a, float b, float c,
 #endif
 }
 
+// Deterministic mode: gradients accumulate as int64 fixed point (value x 2^40,
+// rounded to nearest).  Integer addition is associative, so the sums do not
+// depend on the order in which warps add their contributions.  |value| is
+// clamped to 2^22 (|value| 2^40 stays below 2^62); NaN adds 0.
+constexpr float FIX_SCALE = 1099511627776.0f;  // 2^40
+constexpr float FIX_LIMIT = 4194304.0f;        // 2^22
+__device__ __forceinline__ unsigned long long to_fixed(float v) {
+  float c = (v == v) ? fminf(fmaxf(v, -FIX_LIMIT), FIX_LIMIT) : 0.f;
+  return (unsigned long long)__float2ll_rn(c * FIX_SCALE);
+}
+
+// One lane's nine gradient values of record pr (dx, dy | dA, dB, dC, dopacity | dr, dg, db).
+__device__ __forceinline__ void add_lane(float* dxy, float* dco, float* drgb, unsigned long long* fixed, int64_t pr,
+                                         const float* v) {
+  if (fixed) {
+    #pragma unroll
+    for (int q = 0; q < 9; ++q) atomicAdd(fixed + 9 * pr + q, to_fixed(v[q]));
+  } else {
+    atomic_add2(dxy + 2 * pr, v[0], v[1]);
+    atomic_add4(dco + 4 * pr, v[2], v[3], v[4], v[5]);
+    atomic_add4(drgb + 4 * pr, v[6], v[7], v[8], 0.f);
+  }
+}
+
+// Value q (0..8, order as above) of record pr.
+__device__ __forceinline__ void add_one(float* dxy, float* dco, float* drgb, unsigned long long* fixed, int64_t pr,
+                                        int q, float x) {
+  if (fixed) {
+    atomicAdd(fixed + 9 * pr + q, to_fixed(x));
+    return;
+  }
+  float* dst = q < 2 ? dxy + 2 * pr + q : (q < 6 ? dco + 4 * pr + (q - 2) : drgb + 4 * pr + (q - 6));
+  atomicAdd(dst, x);
+}
+
 __device__ __forceinline__ bool box_misses(float4 b, float x0, float x1, float y0, float y1) {
   return b.y < x0 || b.x > x1 || b.w < y0 || b.z > y1;
 }
@@ -186,7 +221,8 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict
                                                          const float* __restrict__ final_T,
                                                          const uint32_t* __restrict__ n_contrib,
                                                          const float* __restrict__ dimg, float* __restrict__ dxy,
-                                                         float* __restrict__ dco, float* __restrict__ drgb) {
+                                                         float* __restrict__ dco, float* __restrict__ drgb,
+                                                           unsigned long long* __restrict__ fixed) {
   const unsigned FULL = 0xffffffffu;
   __shared__ Rec s_rec[TILE_PIX / 32][32];
   int u, tile;
@@ -278,22 +314,17 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict
       if (cm) {
         int64_t pr = (int64_t)__float_as_uint(rb.w);
         if ((cm & (cm - 1)) == 0) {
-          // a single contributing lane: no reduction, three vector atomics
-          if (contrib) {
-            atomic_add2(dxy + 2 * pr, v[0], v[1]);
-            atomic_add4(dco + 4 * pr, v[2], v[3], v[4], v[5]);
-            atomic_add4(drgb + 4 * pr, v[6], v[7], v[8], 0.f);
-          }
+          // a single contributing lane: no reduction
+          if (contrib) add_lane(dxy, dco, drgb, fixed, pr, v);
         } else {
           float tot = reduce8(v, lane);
           float e8 = v[8];
           #pragma unroll
           for (int o = 16; o > 0; o >>= 1) e8 += __shfl_xor_sync(FULL, e8, o);
           if ((lane & 3) == 0) {
-            float* dst = q < 2 ? dxy + 2 * pr + q : (q < 6 ? dco + 4 * pr + (q - 2) : drgb + 4 * pr + (q - 6));
-            atomicAdd(dst, tot);
+            add_one(dxy, dco, drgb, fixed, pr, q, tot);
           } else if (lane == 1) {
-            atomicAdd(drgb + 4 * pr + 2, e8);
+            add_one(dxy, dco, drgb, fixed, pr, 8, e8);
           }
         }
       }
@@ -710,7 +741,8 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
                                                            const float* __restrict__ final_T,
                                                            const uint32_t* __restrict__ n_contrib,
                                                            const float* __restrict__ dimg, float* __restrict__ dxy,
-                                                           float* __restrict__ dco, float* __restrict__ drgb) {
+                                                           float* __restrict__ dco, float* __restrict__ drgb,
+                                                           unsigned long long* __restrict__ fixed) {
   const unsigned FULL = 0xffffffffu;
   __shared__ Rec s_rec[32];
   uint32_t jid = blockIdx.x >> 3;
@@ -835,21 +867,16 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
         if (__popc(cm) <= DIRECT_LANES) {
           // few contributing lanes (small splats): each issues its own three vector
           // atomics, which costs fewer instructions and atomic operations than a reduction
-          if (contrib) {
-            atomic_add2(dxy + 2 * pr, v[0], v[1]);
-            atomic_add4(dco + 4 * pr, v[2], v[3], v[4], v[5]);
-            atomic_add4(drgb + 4 * pr, v[6], v[7], v[8], 0.f);
-          }
+          if (contrib) add_lane(dxy, dco, drgb, fixed, pr, v);
         } else {
           float tot = reduce8(v, lane);
           float e8 = v[8];
           #pragma unroll
           for (int oo = 16; oo > 0; oo >>= 1) e8 += __shfl_xor_sync(FULL, e8, oo);
           if ((lane & 3) == 0) {
-            float* dst = q < 2 ? dxy + 2 * pr + q : (q < 6 ? dco + 4 * pr + (q - 2) : drgb + 4 * pr + (q - 6));
-            atomicAdd(dst, tot);
+            add_one(dxy, dco, drgb, fixed, pr, q, tot);
           } else if (lane == 1) {
-            atomicAdd(drgb + 4 * pr + 2, e8);
+            add_one(dxy, dco, drgb, fixed, pr, 8, e8);
           }
         }
       }
@@ -941,6 +968,19 @@ __global__ void __launch_bounds__(TILE_PIX) k_blend_pairs(const uint2* __restric
   }
 }
 
+// Deterministic mode: the int64 fixed-point sums back to the float screen-space gradients.
+__global__ void k_fixed_to_grad2d(const unsigned long long* __restrict__ fixed, int64_t P, float* __restrict__ dxy,
+                                  float* __restrict__ dco, float* __restrict__ drgb) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float g[9];
+  #pragma unroll
+  for (int q = 0; q < 9; ++q) g[q] = __ll2float_rn((long long)fixed[9 * p + q]) * (1.0f / FIX_SCALE);
+  reinterpret_cast<float2*>(dxy)[p] = make_float2(g[0], g[1]);
+  reinterpret_cast<float4*>(dco)[p] = make_float4(g[2], g[3], g[4], g[5]);
+  reinterpret_cast<float4*>(drgb)[p] = make_float4(g[6], g[7], g[8], 0.f);
+}
+
 }  // namespace
 
 int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
@@ -998,10 +1038,15 @@ int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const ui
       !n_contrib || !dL_dimg || !g2d || !g2d->dxy || !g2d->dconic_op || !g2d->drgb || n_units < 1 || (sched && !img) ||
       n_units > GS_MAX_UNITS || width <= 0 || height <= 0 || n_proj < 0 || variant < 0 || variant > 2)
     return GS_ERR_INVALID;
-  if (cudaMemsetAsync(g2d->dxy, 0, sizeof(float) * 2 * (size_t)n_proj, s) != cudaSuccess ||
-      cudaMemsetAsync(g2d->dconic_op, 0, sizeof(float) * 4 * (size_t)n_proj, s) != cudaSuccess ||
-      cudaMemsetAsync(g2d->drgb, 0, sizeof(float) * 4 * (size_t)n_proj, s) != cudaSuccess)
+  unsigned long long* fixed = g2d->fixed;
+  if (fixed) {
+    if (cudaMemsetAsync(fixed, 0, sizeof(unsigned long long) * 9 * (size_t)n_proj, s) != cudaSuccess)
+      return GS_ERR_CUDA;
+  } else if (cudaMemsetAsync(g2d->dxy, 0, sizeof(float) * 2 * (size_t)n_proj, s) != cudaSuccess ||
+             cudaMemsetAsync(g2d->dconic_op, 0, sizeof(float) * 4 * (size_t)n_proj, s) != cudaSuccess ||
+             cudaMemsetAsync(g2d->drgb, 0, sizeof(float) * 4 * (size_t)n_proj, s) != cudaSuccess) {
     return GS_ERR_CUDA;
+  }
   int TX = (width + TILE - 1) / TILE, TY = (height + TILE - 1) / TILE;
   dim3 grid(TX * TY * n_units);
 #define GS_BWD(BW)                                                                                                   \
@@ -1011,14 +1056,17 @@ int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const ui
         (const float4*)sched->checkpoints, sorted_vals, sched->block_masks, (const float2*)proj->xy,                 \
         (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX, TX * TY, TX * TY * n_units,     \
         bg[0], bg[1], bg[2],                                                                                         \
-        img, final_T, n_contrib, dL_dimg, g2d->dxy, g2d->dconic_op, g2d->drgb);                                      \
+        img, final_T, n_contrib, dL_dimg, g2d->dxy, g2d->dconic_op, g2d->drgb, fixed);                               \
   else                                                                                                               \
     k_render_bwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, nullptr, sorted_vals, (const float2*)proj->xy, \
                                                (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height,  \
                                                TX, TX * TY, bg[0], bg[1], bg[2], final_T, n_contrib, dL_dimg, g2d->dxy, \
-                                               g2d->dconic_op, g2d->drgb)
+                                               g2d->dconic_op, g2d->drgb, fixed)
   if (variant == 0) { GS_BWD(8); } else if (variant == 1) { GS_BWD(16); } else { GS_BWD(4); }
 #undef GS_BWD
+  if (fixed && n_proj > 0)
+    k_fixed_to_grad2d<<<(unsigned)((n_proj + 255) / 256), 256, 0, s>>>(fixed, n_proj, g2d->dxy, g2d->dconic_op,
+                                                                       g2d->drgb);
   return gs_check_launch();
 }
 

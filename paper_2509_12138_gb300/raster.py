@@ -140,7 +140,7 @@ class Frame:
 
     def __init__(self, n_gauss: int, units: Units, width: int, height: int, sh_degree: int, device="cuda",
                  max_instances: int | None = None, with_backward: bool = True, with_loss: bool = True,
-                 variant: int = 0, chunk: int = CHUNK):
+                 variant: int = 0, chunk: int = CHUNK, deterministic: bool = False):
         self.L = _lib.load()
         self.variant = int(variant)
         self.chunk = int(chunk)
@@ -182,7 +182,10 @@ class Frame:
             self.dxy = torch.zeros((max(P, 1), 2), **f32)
             self.dco = torch.zeros((max(P, 1), 4), **f32)
             self.drgb = torch.zeros((max(P, 1), 4), **f32)
-            self.g2d = GsGrad2d(self.dxy.data_ptr(), self.dco.data_ptr(), self.drgb.data_ptr())
+            # deterministic: screen-space gradients accumulate as int64 fixed point (bitwise reproducible)
+            self.fixed = torch.zeros((max(P, 1), 9), dtype=torch.int64, device=self.device) if deterministic else None
+            self.g2d = GsGrad2d(self.dxy.data_ptr(), self.dco.data_ptr(), self.drgb.data_ptr(),
+                                self.fixed.data_ptr() if deterministic else None)
             self.grads = torch.zeros((self.planes, max(self.N, 1), 4), **f32)
 
     def _sched(self):
@@ -394,6 +397,15 @@ class Adam:
                                          self.eps, _ptr(self.step_dev), _ptr(frame.grads) if keep_grads else None,
                                          _stream()), "gs_project_bwd_adam")
         check(self.L.gs_step_advance(_ptr(self.step_dev), _stream()), "gs_step_advance")
+
+    def state_dict(self) -> dict:
+        """Optimiser state for a checkpoint: moments and the device step counter (copies)."""
+        return {"m": self.m.clone(), "v": self.v.clone(), "step": self.step_dev.clone()}
+
+    def load_state_dict(self, st: dict):
+        self.m.copy_(st["m"])
+        self.v.copy_(st["v"])
+        self.step_dev.copy_(st["step"])
 
     def step(self, grads: torch.Tensor, zero_grad: bool = False):
         npl, n = self.params.shape[0], self.params.shape[1]

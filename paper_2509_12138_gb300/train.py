@@ -47,7 +47,7 @@ class PlainTrainer:
     def __init__(self, params: torch.Tensor, sh_degree: int, cams_dev: torch.Tensor, gt: torch.Tensor,
                  mask: torch.Tensor, train_views, lrs: LearningRates | None = None, extent: float = 1.0,
                  lr_steps: int = 7000, lam: float = 0.2, bg=(1.0, 1.0, 1.0), variant: int = 0, seed: int = 0,
-                 capacity_slack: float = 1.5):
+                 capacity_slack: float = 1.5, deterministic: bool = False):
         self.params = params
         self.deg = sh_degree
         self.cams = cams_dev
@@ -56,7 +56,8 @@ class PlainTrainer:
         self.lam, self.bg = lam, tuple(bg)
         N = params.shape[1]
         H, W = gt.shape[-2], gt.shape[-1]
-        self.frame = Frame(N, Units.single(N), W, H, sh_degree, device=params.device, variant=variant)
+        self.frame = Frame(N, Units.single(N), W, H, sh_degree, device=params.device, variant=variant,
+                           deterministic=deterministic)
         self.opt = Adam(params, sh_degree, lrs, extent, lr_steps)
         self.rng = np.random.default_rng(seed)
         self.t = 0
@@ -66,6 +67,23 @@ class PlainTrainer:
 
     def cam(self, v):
         return self.cams[v * CAM_BYTES:(v + 1) * CAM_BYTES]
+
+    def state_dict(self) -> dict:
+        """Checkpoint: parameters, optimiser state, step count and the view-order generator (copies).
+        In deterministic mode a run resumed from it continues bit for bit like the uninterrupted run."""
+        st = {"params": self.params.clone(), "opt": self.opt.state_dict(), "t": self.t,
+              "rng": self.rng.bit_generator.state}
+        if hasattr(self, "order"):
+            st["order"] = np.array(self.order)
+        return st
+
+    def load_state_dict(self, st: dict):
+        self.params.copy_(st["params"])
+        self.opt.load_state_dict(st["opt"])
+        self.t = int(st["t"])
+        self.rng.bit_generator.state = st["rng"]
+        if "order" in st:
+            self.order = np.array(st["order"])
 
     def next_view(self):
         if self.t % len(self.views) == 0:
@@ -111,7 +129,7 @@ class BatchedTrainer:
     def __init__(self, params: torch.Tensor, sh_degree: int, part_offsets, cams_dev: torch.Tensor, gt: torch.Tensor,
                  mask: torch.Tensor, train_views, views_per_step: int = 1, lrs: LearningRates | None = None,
                  extent: float = 1.0, lr_steps: int = 7000, lam: float = 0.2, bg=(1.0, 1.0, 1.0), variant: int = 0,
-                 use_graph: bool = True, capacity_slack: float = 1.5):
+                 use_graph: bool = True, capacity_slack: float = 1.5, deterministic: bool = False):
         self.params = params
         self.deg = sh_degree
         self.off = np.asarray(part_offsets, np.int64)
@@ -127,7 +145,7 @@ class BatchedTrainer:
         dev = params.device
         self.units = Units.partitions(self.off, self.vps)
         U = self.units.n
-        self.frame = Frame(N, self.units, W, H, sh_degree, device=dev, variant=variant)
+        self.frame = Frame(N, self.units, W, H, sh_degree, device=dev, variant=variant, deterministic=deterministic)
         self.opt = Adam(params, sh_degree, lrs, extent, lr_steps)
         self.cams_step = torch.zeros(U * CAM_BYTES, dtype=torch.uint8, device=dev)
         self.gt_step = torch.zeros((U, 3, H, W), dtype=torch.float32, device=dev)
@@ -190,6 +208,16 @@ class BatchedTrainer:
         else:
             self._chain()
         self.t += 1
+
+    def state_dict(self) -> dict:
+        """Checkpoint: parameters, optimiser state and step count (copies); views follow from the step."""
+        return {"params": self.params.clone(), "opt": self.opt.state_dict(), "t": self.t}
+
+    def load_state_dict(self, st: dict):
+        """Restore a checkpoint in place (the captured graph reads the same buffers, so it stays valid)."""
+        self.params.copy_(st["params"])
+        self.opt.load_state_dict(st["opt"])
+        self.t = int(st["t"])
 
     def check(self):
         st = self.frame.read_status()
