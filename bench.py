@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="iso10M-1080p", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="accumulate screen-space gradients in fixed point (bitwise reproducible steps)")
     ap.add_argument("--cpu-window", type=int, default=8, help="CPU sample: 1/(w*w) of the view's pixels")
     ap.add_argument("--experiment", default=None, choices=["learned-init"],
                     help="instead of the throughput line: the plain vs batched + learned-init comparison")
@@ -231,7 +233,8 @@ def run_ours(args, wl, rank, world):
                                       seed=shard.rank_seed(0, rank), device=dev)
     N, W, H = scene.n, scene.width, scene.height
     params = gs.pack_params(scene.init, 3, dev)
-    frame = gs.Frame(N, gs.Units.single(N), W, H, 3, device=dev, max_instances=6 * N)
+    frame = gs.Frame(N, gs.Units.single(N), W, H, 3, device=dev, max_instances=6 * N,
+                     deterministic=args.deterministic)
     opt = gs.Adam(params, 3, extent=1.0, lr_steps=7000)
     bg = scene.bg
     V = len(scene.cams)
@@ -448,6 +451,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     config = {"workload": args.workload, "gaussians": wl["n"], "width": wl["W"], "height": wl["H"],
               "views": wl["views"], "sh_degree": 3, "loss": f"masked L1 + {LAMBDA_SSIM} D-SSIM",
+              "gradient_accumulation": "int64 fixed point" if args.deterministic else "float atomics",
               "l2": "inputs larger than L2 (params+Adam state 9.6 GB at 10M)"}
     if args.impl == "reference":
         return run_reference(args, wl, rank, world, config)

@@ -864,7 +864,8 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
       unsigned cm = __ballot_sync(FULL, contrib);
       if (cm) {
         int64_t pr = (int64_t)__float_as_uint(rb.w);
-        if (__popc(cm) <= DIRECT_LANES) {
+        // fixed point: nine scalar int64 atomics per lane, so reduce unless one lane contributes
+        if (__popc(cm) <= (fixed ? 1 : DIRECT_LANES)) {
           // few contributing lanes (small splats): each issues its own three vector
           // atomics, which costs fewer instructions and atomic operations than a reduction
           if (contrib) add_lane(dxy, dco, drgb, fixed, pr, v);
