@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--deterministic", action="store_true",
                     help="accumulate screen-space gradients in fixed point (bitwise reproducible steps)")
     ap.add_argument("--cpu-window", type=int, default=8, help="CPU sample: 1/(w*w) of the view's pixels")
-    ap.add_argument("--experiment", default=None, choices=["learned-init"],
+    ap.add_argument("--experiment", default=None, choices=["learned-init", "ghost-ablation"],
                     help="instead of the throughput line: the plain vs batched + learned-init comparison")
     ap.add_argument("--exp-gaussians", type=int, default=1_000_000)
     ap.add_argument("--exp-steps", type=int, default=3000)
@@ -457,6 +457,8 @@ def main():
         return run_reference(args, wl, rank, world, config)
     if args.experiment == "learned-init":
         return run_learned_init_experiment(args)
+    if args.experiment == "ghost-ablation":
+        return run_ghost_ablation(args)
     if args.workload.startswith("batched"):
         return run_batched(args, wl)
     if args.workload.startswith("merge"):
@@ -541,6 +543,23 @@ def run_learned_init_experiment(args):
                         "learned": [h_learn.steps, [round(x, 3) for x in h_learn.seconds],
                                     [round(x, 3) for x in h_learn.psnr]]}}
     print(json.dumps(line))
+    return 0
+
+
+def run_ghost_ablation(args):
+    """Ghost cells and background masks on / off: PSNR of the merged render on held-out views, over all
+    covered pixels and over the seam band around the slab boundaries (one JSON line)."""
+    import torch
+    from paper_2509_12138_gb300 import experiment as X
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    slabs, W, H, V = [args.exp_gaussians // 4] * 4, 960, 540, 32
+    res = X.ghost_ablation(slabs, 8, V, W, H, args.exp_steps, n_parts=4, ghost=0.05, sh_degree=1, delta=0.01)
+    print(json.dumps({"experiment": "ghost cells x masks", "gaussians": sum(slabs), "partitions": 4, "ghost": 0.05,
+                      "width": W, "height": H, "views": V, "steps": args.exp_steps,
+                      "seam_band": "pixels whose surface lies within 0.01 (x) of an interior slab boundary",
+                      "results": res}))
     return 0
 
 

@@ -126,3 +126,67 @@ def run_learned_batched(scene, weights, steps: int, eval_every: int, views_per_s
         if stop_at is not None and h.psnr[-1] >= stop_at:
             break
     return h, params
+
+
+def seam_band(scene, delta: float, device="cuda"):
+    """Per view, the pixels whose visible surface lies within `delta` (in x) of an interior slab boundary:
+    the ground-truth surfels rendered with their x coordinate as colour (opaque, so a covered pixel shows
+    the x of its front surface), compared with the partition edges.  Returns bool [V, H, W]."""
+    from .workload import gt_surfels, render_gt
+    pts = scene.pts
+    nrm = scene.nrm
+    xcol = np.repeat(pts[:, :1], 3, axis=1).astype(np.float32)
+    ximg, cover = render_gt(gt_surfels(pts, nrm, xcol, scene.spacing), scene.cams, 0, (-1.0, -1.0, -1.0), device,
+                            max_instances=max(8 * len(pts), 1 << 20))
+    edges = torch.tensor(np.asarray(scene.part.edges[1:-1], np.float32), device=device)
+    d = (ximg[:, 0, :, :, None] - edges).abs().amin(-1)
+    return (d < delta) & cover.bool()
+
+
+def ghost_ablation(slab_counts, n_modes: int, n_views: int, W: int, H: int, steps: int, n_parts: int = 4,
+                   ghost: float = 0.05, sh_degree: int = 1, delta: float = 0.01, device="cuda"):
+    """Ghost cells and masks on and off (Sec. II): each configuration trains every partition on its own
+    GT (graph-captured batched trainer, one view per partition per step), merges with the ghost filter and
+    is scored on held-out views against the whole scene's GT: PSNR over the covered pixels and over the
+    seam band (pixels whose surface lies within `delta` of a slab boundary)."""
+    from .raster import Frame, Owned, Units
+    from .workload import partitioned_scene
+    out = {}
+    band = None
+    for use_ghost in (True, False):
+        ps = partitioned_scene(slab_counts, n_modes, n_views, W, H, n_parts=n_parts,
+                               ghost=ghost if use_ghost else 0.0, sh_degree=sh_degree, device=device)
+        if band is None:
+            band = seam_band(ps, delta, device)
+        train_v, test_v = split_views(n_views)
+        for use_mask in (True, False):
+            masks = ps.mask if use_mask else torch.ones_like(ps.mask)
+            params = pack_params(ps.init, sh_degree, device)
+            tr = BatchedTrainer(params, sh_degree, ps.offsets, ps.cams_dev, ps.gt, masks, train_v, views_per_step=1,
+                                lr_steps=steps)
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                tr.step()
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            tr.check()
+            owned = Owned(ps.part.offsets, ps.part.boxes, ps.part.closed_hi)
+            N = params.shape[1]
+            fr = Frame(N, Units.single(N), W, H, sh_degree, device=device, with_backward=False, with_loss=False)
+            fr.walk_whole_lists = True
+            all_p, band_p = [], []
+            for v in test_v:
+                cam = ps.cams_dev[v * 96:(v + 1) * 96]
+                fr.fit_capacity(params, cam, owned)
+                img = fr.merge_render(params, cam, ps.bg, owned)[0]
+                all_p.append(psnr(img, ps.gt_full[v], ps.mask_full[v]))
+                band_p.append(psnr(img, ps.gt_full[v], band[v]))
+            key = f"ghost={'on' if use_ghost else 'off'},mask={'on' if use_mask else 'off'}"
+            out[key] = {"psnr_covered": round(float(np.nanmean(all_p)), 3),
+                        "psnr_seam_band": round(float(np.nanmean(band_p)), 3),
+                        "train_seconds": round(secs, 3),
+                        "gaussians_with_ghosts": int(N)}
+            del tr, fr, params
+            torch.cuda.empty_cache()
+    out["seam_band_fraction_of_covered"] = round(float(band.float().sum() / ps.mask_full.float().sum()), 4)
+    return out

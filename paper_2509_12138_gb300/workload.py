@@ -130,6 +130,7 @@ class PartitionedScene:
     pts: np.ndarray
     spacing: float
     bg: tuple = (1.0, 1.0, 1.0)
+    nrm: np.ndarray | None = None  # surface normals of pts
 
     @property
     def offsets(self):
@@ -162,7 +163,7 @@ def partitioned_scene(slab_counts, n_modes: int, n_views: int, width: int, heigh
     init = plain_init(pts[order], colors[order], math.log(spacing), sh_degree)
     return PartitionedScene(part=part, sh_degree=sh_degree, width=W, height=H, cams=cams,
                             cams_dev=pack_cameras(cams, device), gt=gt, mask=mask, gt_full=gt_full,
-                            mask_full=mask_full, init=init, pts=pts, spacing=spacing)
+                            mask_full=mask_full, init=init, pts=pts, spacing=spacing, nrm=nrm)
 
 
 def interface_gaussians_device(n: int, n_modes: int, seed: int, sh_degree: int = 3, device="cuda",
