@@ -575,12 +575,13 @@ def run_batched(args, wl):
     train_v, test_v = T.split_views(wl["views"], 8)
     init = gs.pack_params(ps.init, 3)
 
-    def make(variant, vps):
+    def make(variant, vps, chunk=1024):
         return T.BatchedTrainer(init.clone(), 3, ps.offsets, ps.cams_dev, ps.gt, ps.mask, train_v,
-                                views_per_step=vps, variant=variant, lr_steps=7000)
+                                views_per_step=vps, variant=variant, lr_steps=7000, chunk=chunk)
 
-    best, table = tune.autotune(make, f"batched28M-{wl['W']}x{wl['H']}", candidates=[(0, 1), (1, 1), (0, 2)],
-                                steps=3, warmup=2)
+    best, table = tune.autotune(make, f"batched28M-{wl['W']}x{wl['H']}",
+                                candidates=[(0, 1, 1024), (0, 1, 512), (1, 1, 1024), (0, 2, 1024)],
+                                steps=3, warmup=2, use_cache=False)
     tr = make(*best)
     sec = tune.time_trainer(tr, steps=args.steps, warmup=args.warmup)
     st = tr.check()

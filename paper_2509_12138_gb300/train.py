@@ -18,7 +18,7 @@ import time
 import numpy as np
 import torch
 
-from .raster import Adam, Frame, LearningRates, Owned, Units, pack_cameras
+from .raster import CHUNK, Adam, Frame, LearningRates, Owned, Units, pack_cameras
 
 CAM_BYTES = 96
 
@@ -47,7 +47,7 @@ class PlainTrainer:
     def __init__(self, params: torch.Tensor, sh_degree: int, cams_dev: torch.Tensor, gt: torch.Tensor,
                  mask: torch.Tensor, train_views, lrs: LearningRates | None = None, extent: float = 1.0,
                  lr_steps: int = 7000, lam: float = 0.2, bg=(1.0, 1.0, 1.0), variant: int = 0, seed: int = 0,
-                 capacity_slack: float = 1.5, deterministic: bool = False):
+                 capacity_slack: float = 1.5, deterministic: bool = False, chunk: int = CHUNK):
         self.params = params
         self.deg = sh_degree
         self.cams = cams_dev
@@ -57,7 +57,7 @@ class PlainTrainer:
         N = params.shape[1]
         H, W = gt.shape[-2], gt.shape[-1]
         self.frame = Frame(N, Units.single(N), W, H, sh_degree, device=params.device, variant=variant,
-                           deterministic=deterministic)
+                           deterministic=deterministic, chunk=chunk)
         self.opt = Adam(params, sh_degree, lrs, extent, lr_steps)
         self.rng = np.random.default_rng(seed)
         self.t = 0
@@ -129,7 +129,8 @@ class BatchedTrainer:
     def __init__(self, params: torch.Tensor, sh_degree: int, part_offsets, cams_dev: torch.Tensor, gt: torch.Tensor,
                  mask: torch.Tensor, train_views, views_per_step: int = 1, lrs: LearningRates | None = None,
                  extent: float = 1.0, lr_steps: int = 7000, lam: float = 0.2, bg=(1.0, 1.0, 1.0), variant: int = 0,
-                 use_graph: bool = True, capacity_slack: float = 1.5, deterministic: bool = False):
+                 use_graph: bool = True, capacity_slack: float = 1.5, deterministic: bool = False,
+                 chunk: int = CHUNK):
         self.params = params
         self.deg = sh_degree
         self.off = np.asarray(part_offsets, np.int64)
@@ -145,7 +146,8 @@ class BatchedTrainer:
         dev = params.device
         self.units = Units.partitions(self.off, self.vps)
         U = self.units.n
-        self.frame = Frame(N, self.units, W, H, sh_degree, device=dev, variant=variant, deterministic=deterministic)
+        self.frame = Frame(N, self.units, W, H, sh_degree, device=dev, variant=variant, deterministic=deterministic,
+                           chunk=chunk)
         self.opt = Adam(params, sh_degree, lrs, extent, lr_steps)
         self.cams_step = torch.zeros(U * CAM_BYTES, dtype=torch.uint8, device=dev)
         self.gt_step = torch.zeros((U, 3, H, W), dtype=torch.float32, device=dev)

@@ -1,6 +1,8 @@
 """Autotuner for the batched training step.
 
-Candidates are (blend variant, views per step).  Each candidate builds its
+Candidates are tuples of trainer settings: (blend variant, views per step)
+and optionally the chunk length of the blend schedule (list entries per
+chunk job: long lists favour longer chunks).  Each candidate builds its
 trainer, captures its CUDA graph, and is timed over a few replays with CUDA
 events; throughput is (partition, view) units per second.  The winner is
 cached per GPU and workload in ``_build/tune_cache.json``.
@@ -50,26 +52,25 @@ def time_trainer(tr, steps: int = 6, warmup: int = 2) -> float:
 
 
 def autotune(make_trainer, key: str, candidates=None, steps: int = 6, warmup: int = 2, use_cache: bool = True):
-    """make_trainer(variant, views_per_step) -> trainer with ``.step()`` and ``.units``.
+    """make_trainer(*candidate) -> trainer with ``.step()`` and ``.units``; a candidate is
+    (variant, views_per_step) or (variant, views_per_step, chunk).
 
-    Returns (best (variant, views_per_step), table of {candidate: units/s}).  The trainers are
-    rebuilt from the same initial state by ``make_trainer``; state changes made while timing are
-    the caller's to discard."""
+    Returns (best candidate tuple, table of {candidate: units/s}).  The trainers are rebuilt from the
+    same initial state by ``make_trainer``; state changes made while timing are the caller's to discard."""
     dev = torch.cuda.get_device_name()
     full = f"{dev}|{key}"
     cache = _load_cache() if use_cache else {}
     if full in cache:
         c = cache[full]
-        return (c["variant"], c["views_per_step"]), c["table"]
+        return tuple(c["best"]), c["table"]
     table = {}
-    for (variant, vps) in (candidates or DEFAULT_CANDIDATES):
-        tr = make_trainer(variant, vps)
+    for cand in (candidates or DEFAULT_CANDIDATES):
+        tr = make_trainer(*cand)
         sec = time_trainer(tr, steps, warmup)
-        table[f"{variant},{vps}"] = tr.units.n / sec
+        table[",".join(str(x) for x in cand)] = tr.units.n / sec
         del tr
         torch.cuda.empty_cache()
-    best = max(table, key=table.get)
-    variant, vps = (int(x) for x in best.split(","))
-    cache[full] = {"variant": variant, "views_per_step": vps, "table": table}
+    best = tuple(int(x) for x in max(table, key=table.get).split(","))
+    cache[full] = {"best": list(best), "table": table}
     _save_cache(cache)
-    return (variant, vps), table
+    return best, table

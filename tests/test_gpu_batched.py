@@ -151,12 +151,13 @@ def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
     deg = 1
     gtd, mkd, camd = torch.from_numpy(gt).cuda(), torch.from_numpy(mask).cuda(), gs.pack_cameras(cams)
 
-    def make(variant, vps):
+    def make(variant, vps, chunk=1024):
         return T.BatchedTrainer(gs.pack_params(init, deg), deg, part.offsets, camd, gtd, mkd, list(range(6)),
-                                views_per_step=vps, variant=variant)
+                                views_per_step=vps, variant=variant, chunk=chunk)
 
-    best, table = tune.autotune(make, "test", candidates=[(0, 1), (1, 1), (2, 2)], steps=2, warmup=1)
-    assert best in [(0, 1), (1, 1), (2, 2)] and len(table) == 3 and all(v > 0 for v in table.values())
+    cands = [(0, 1, 1024), (1, 1, 1024), (2, 2, 1024), (0, 1, 64)]
+    best, table = tune.autotune(make, "test", candidates=cands, steps=2, warmup=1)
+    assert best in cands and len(table) == 4 and all(v > 0 for v in table.values())
     best2, _ = tune.autotune(make, "test", candidates=[(0, 1)])  # from the cache
     assert best2 == best
 
