@@ -359,6 +359,63 @@ int gs_merge_render(const float* params, int64_t n_gauss, int sh_degree, const g
                     uint32_t* d_num_instances, float* img, float* final_T, uint32_t* n_contrib,
                     const gs_schedule* sched, int* d_status, gs_stream_t stream);
 
+/* ---- adaptive density control (3D-GS densification) ----------------------
+ * The optimisation each partition is trained with (Sec. II, "Parallel
+ * Training") is standard 3D Gaussian Splatting, which clones, splits and
+ * prunes Gaussians as it trains.  Reading of its rules:
+ *   statistics per training view, for every record with radius > 0 of
+ *   Gaussian i: grad_accum[i] += |(dL/du W/2, dL/dv H/2)| (u, v: its pixel
+ *   position; dxy of gs_grad2d), denom[i] += 1, max_radius[i] = max(., radius);
+ *   plan at step t: g = grad_accum / denom (0 if denom = 0), smax = largest
+ *   scale, o = opacity; prune if o < min_opacity or (t > reset_interval and
+ *   (max_radius > max_screen or smax > 0.1 extent)); otherwise, if
+ *   g >= grad_threshold: split if smax > percent_dense extent, else clone;
+ *   apply: kept sources (not pruned, not split) in index order, then copies of
+ *   the cloned sources, then two children per split source (mean + R(q)(s * z),
+ *   log scales - log 1.6, all else copied); Adam moments copied for kept
+ *   sources, zero for new Gaussians;
+ *   opacity reset: logit opacity = min(logit opacity, logit(max_opacity)) and
+ *   the opacity's Adam moments = 0.
+ * grad_accum, denom, max_radius: device float [n_gauss] (caller zeroes them
+ * after each plan). */
+typedef struct gs_densify_cfg {
+  float grad_threshold;  /* 2e-4 in 3D-GS */
+  float percent_dense;   /* 0.01 */
+  float min_opacity;     /* 0.005 */
+  float max_screen;      /* 20 px */
+  float extent;          /* scene extent (> 0) */
+  int32_t step;          /* current optimisation step */
+  int32_t reset_interval;/* opacity reset period (3000); screen / world size pruning only after it */
+} gs_densify_cfg;
+
+/* Accumulates one step's statistics (proj and g2d of that step's units). */
+int gs_densify_stats(const gs_proj* proj, const gs_grad2d* g2d, const gs_units* units, int width,
+                     int height, float* grad_accum, float* denom, float* max_radius,
+                     gs_stream_t stream);
+
+/* Plan: each Gaussian's action and the exclusive prefixes of the kept /
+ * cloned / split counts (in the workspace, gs_densify_workspace_size(n));
+ * d_counts (device uint32[3]) receives (kept, cloned, split).  The output of
+ * gs_densify_apply holds kept + cloned + 2 split Gaussians. */
+size_t gs_densify_workspace_size(int64_t n_gauss);
+int gs_densify_plan(const float* params, int64_t n_gauss, const float* grad_accum,
+                    const float* denom, const float* max_radius, const gs_densify_cfg* cfg,
+                    void* workspace, size_t workspace_bytes, uint32_t* d_counts,
+                    gs_stream_t stream);
+
+/* Apply the plan in `workspace` (same n_gauss): params / m / v planes
+ * [planes][n_gauss][4] in, out_* planes [planes][n_out][4] out; z: device
+ * float [n_gauss][2][3] standard normal draws (used for split sources).
+ * Positions at or past n_out are not written and set GS_ERR_CAPACITY. */
+int gs_densify_apply(const float* params, const float* m, const float* v, int64_t n_gauss,
+                     int sh_degree, const float* z, const void* workspace, size_t workspace_bytes,
+                     float* out_params, float* out_m, float* out_v, int64_t n_out, int* d_status,
+                     gs_stream_t stream);
+
+/* Opacity reset of 3D-GS (see above); max_opacity in (0, 1), 0.01 in 3D-GS. */
+int gs_opacity_reset(float* params, float* m, float* v, int64_t n_gauss, float max_opacity,
+                     gs_stream_t stream);
+
 /* ---- a9: learned initialiser --------------------------------------------
  * Not in the paper: its Sec. II initialises the Gaussians from the extracted
  * isosurface points.  The plain form used there sets each Gaussian's scale

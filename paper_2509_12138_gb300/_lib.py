@@ -48,6 +48,11 @@ class GsOwned(C.Structure):
     _fields_ = [("n_parts", C.c_int32), ("part_offsets", c_i64p), ("boxes", c_f32p), ("closed_hi", c_i32p)]
 
 
+class GsDensifyCfg(C.Structure):
+    _fields_ = [("grad_threshold", C.c_float), ("percent_dense", C.c_float), ("min_opacity", C.c_float),
+                ("max_screen", C.c_float), ("extent", C.c_float), ("step", C.c_int32), ("reset_interval", C.c_int32)]
+
+
 assert C.sizeof(GsCamera) == 96
 
 VP = C.c_void_p
@@ -90,6 +95,12 @@ SIGNATURES = {
     "gs_init_gaussians": (I32, [VP, VP, VP, VP, I32, I64, VP, F32, VP, I64, VP]),
     "gs_merge_render": (I32, [VP, I64, I32, C.POINTER(GsOwned), VP, I32, I32, c_f32p, C.POINTER(GsProj), I64, VP, SZ,
                               VP, VP, VP, VP, VP, VP, C.POINTER(GsSchedule), VP, VP]),
+    "gs_densify_stats": (I32, [C.POINTER(GsProj), C.POINTER(GsGrad2d), C.POINTER(GsUnits), I32, I32, VP, VP, VP,
+                               VP]),
+    "gs_densify_workspace_size": (SZ, [I64]),
+    "gs_densify_plan": (I32, [VP, I64, VP, VP, VP, C.POINTER(GsDensifyCfg), VP, SZ, VP, VP]),
+    "gs_densify_apply": (I32, [VP, VP, VP, I64, I32, VP, VP, SZ, VP, VP, VP, I64, VP, VP]),
+    "gs_opacity_reset": (I32, [VP, VP, VP, I64, F32, VP]),
 }
 
 OPTIONAL = set()

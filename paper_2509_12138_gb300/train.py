@@ -47,10 +47,13 @@ class PlainTrainer:
     def __init__(self, params: torch.Tensor, sh_degree: int, cams_dev: torch.Tensor, gt: torch.Tensor,
                  mask: torch.Tensor, train_views, lrs: LearningRates | None = None, extent: float = 1.0,
                  lr_steps: int = 7000, lam: float = 0.2, bg=(1.0, 1.0, 1.0), variant: int = 0, seed: int = 0,
-                 capacity_slack: float = 1.5, deterministic: bool = False, chunk: int = CHUNK):
+                 capacity_slack: float = 1.5, deterministic: bool = False, chunk: int = CHUNK,
+                 densify=None):
         self.params = params
         self.deg = sh_degree
         self.cams = cams_dev
+        self._frame_args = dict(variant=variant, deterministic=deterministic, chunk=chunk)
+        self.capacity_slack = capacity_slack
         self.gt, self.mask = gt, mask
         self.views = list(train_views)
         self.lam, self.bg = lam, tuple(bg)
@@ -62,8 +65,30 @@ class PlainTrainer:
         self.rng = np.random.default_rng(seed)
         self.t = 0
         self.keep_grads = False  # also write the parameter gradient (for inspection)
-        need = max(self.frame.fit_capacity(params, self.cam(v)) for v in self.views[:: max(1, len(self.views) // 8)])
-        self.frame.set_capacity(int(need * capacity_slack) + 4096)
+        self._fit()
+        # adaptive density control (3D-GS): a DensifyConfig turns it on
+        self.densifier = None
+        if densify is not None:
+            from .densify import Densifier
+            self.densifier = Densifier(N, densify, params.device, seed)
+        self.steps_done = 0
+
+    def _fit(self):
+        need = max(self.frame.fit_capacity(self.params, self.cam(v))
+                   for v in self.views[:: max(1, len(self.views) // 8)])
+        self.frame.set_capacity(int(need * self.capacity_slack) + 4096)
+
+    def _densify(self, step: int):
+        """Clone / split / prune into new planes; the frame is rebuilt for the new count."""
+        d = self.densifier
+        counts = d.plan(self.params, step)
+        p, m, v = d.apply(self.params, self.opt.m, self.opt.v, self.deg, counts)
+        self.params, self.opt.params, self.opt.m, self.opt.v = p, p, m, v
+        N = p.shape[1]
+        H, W = self.gt.shape[-2], self.gt.shape[-1]
+        self.frame = Frame(N, Units.single(N), W, H, self.deg, device=p.device, **self._frame_args)
+        self._fit()
+        return counts
 
     def cam(self, v):
         return self.cams[v * CAM_BYTES:(v + 1) * CAM_BYTES]
@@ -72,18 +97,39 @@ class PlainTrainer:
         """Checkpoint: parameters, optimiser state, step count and the view-order generator (copies).
         In deterministic mode a run resumed from it continues bit for bit like the uninterrupted run."""
         st = {"params": self.params.clone(), "opt": self.opt.state_dict(), "t": self.t,
-              "rng": self.rng.bit_generator.state}
+              "rng": self.rng.bit_generator.state, "steps_done": self.steps_done}
         if hasattr(self, "order"):
             st["order"] = np.array(self.order)
+        d = self.densifier
+        if d is not None:
+            st["densify"] = {"grad_accum": d.grad_accum.clone(), "denom": d.denom.clone(),
+                             "max_radius": d.max_radius.clone(), "gen": d.gen.get_state()}
         return st
 
     def load_state_dict(self, st: dict):
-        self.params.copy_(st["params"])
+        if st["params"].shape != self.params.shape:  # densification changed the count: new planes, new frame
+            p = st["params"].clone()
+            self.params, self.opt.params = p, p
+            self.opt.m, self.opt.v = torch.zeros_like(p), torch.zeros_like(p)
+            N = p.shape[1]
+            H, W = self.gt.shape[-2], self.gt.shape[-1]
+            self.frame = Frame(N, Units.single(N), W, H, self.deg, device=p.device, **self._frame_args)
+            self._fit()
+        else:
+            self.params.copy_(st["params"])
         self.opt.load_state_dict(st["opt"])
         self.t = int(st["t"])
+        self.steps_done = int(st.get("steps_done", 0))
         self.rng.bit_generator.state = st["rng"]
         if "order" in st:
             self.order = np.array(st["order"])
+        if "densify" in st and self.densifier is not None:
+            d, s = self.densifier, st["densify"]
+            d._alloc(self.params.shape[1])
+            d.grad_accum.copy_(s["grad_accum"])
+            d.denom.copy_(s["denom"])
+            d.max_radius.copy_(s["max_radius"])
+            d.gen.set_state(s["gen"])
 
     def next_view(self):
         if self.t % len(self.views) == 0:
@@ -101,6 +147,14 @@ class PlainTrainer:
         fr.loss(self.gt[v:v + 1], self.mask[v:v + 1], self.lam)
         fr.blend_backward(self.bg)
         self.opt.fused_step(fr, cam, self.keep_grads)
+        self.steps_done += 1
+        d = self.densifier
+        if d is not None:
+            d.accumulate(fr)
+            if d.due(self.steps_done):
+                self._densify(self.steps_done)
+            if d.reset_due(self.steps_done):
+                d.reset_opacity(self.params, self.opt.m, self.opt.v)
 
     def check(self):
         st = self.frame.read_status()
