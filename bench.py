@@ -264,6 +264,7 @@ def run_ours(args, wl, rank, world):
     if st != 0:
         raise RuntimeError(f"device status {st} after warm-up")
     instances = frame.instances()
+    visible = float((frame.radius[: frame.P] > 0).float().mean())  # Gaussians with a projection in this view
     lens = (frame.ranges[:, 1] - frame.ranges[:, 0]).float()
     nz = lens[lens > 0]
     tile_len = {"nonempty_tiles": int(nz.numel()), "mean": round(float(nz.mean()), 1) if nz.numel() else 0,
@@ -377,7 +378,7 @@ def run_ours(args, wl, rank, world):
     barrier()
     return dict(scene=scene, frame=frame, ms_total=ms_total, stage_ms=stage_ms, stages=stages, ms_render=ms_render,
                 clocks=clk, e2e_sec=e_sec, instances=instances, tile_len=tile_len, pairs=pairs_per_step,
-                render_mode=render_mode, h2d=(3 * H * W * 4 + H * W), d2h=4,
+                render_mode=render_mode, visible=visible, h2d=(3 * H * W * 4 + H * W), d2h=4,
                 launches=kernel_launch_count(frame, LAMBDA_SSIM) * args.steps, N=N, W=W, H=H)
 
 
@@ -488,6 +489,7 @@ def main():
         "render_mpix_s": round(mpix, 1), "render_ms": round(res["ms_render"], 4), "render_mode": res["render_mode"],
         "stage_ms": {k: round(float(v), 4) for k, v in zip(res["stages"], res["stage_ms"])},
         "instances_per_view": res["instances"], "tile_list_len": res["tile_len"],
+        "visible_fraction": round(res["visible"], 4),
         "e2e": {"value": round(shard.job_throughput([args.steps] * world, e2e_sec * 1e3), 3), "unit": "iters/s",
                 "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
         "gpu_launches": res["launches"], "clocks": res["clocks"],
