@@ -71,7 +71,7 @@ def _declare(L):
     L.orc_project.argtypes = [C.c_int, C.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _I, _D, _I, _I, _I, _D]
     L.orc_bin.argtypes = [C.c_int, _D, _I, _D, C.c_int, C.c_int, C.c_longlong, _I, _I, _I, _I]
     L.orc_bin.restype = C.c_longlong
-    L.orc_render.argtypes = [C.c_int, C.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _I, _D, _I]
+    L.orc_render.argtypes = [C.c_int, C.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _I, _D, _I, _D, _D]
     L.orc_render_bruteforce.argtypes = [C.c_int, C.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _I]
     L.orc_loss.argtypes = [_D, _D, _U8, C.c_int, C.c_int, C.c_double, _D]
     L.orc_loss.restype = C.c_double
@@ -208,9 +208,14 @@ def render(g, cam, bg):
     nc = np.zeros((H, W), np.int32)
     margin = np.zeros((H, W))
     ties = np.zeros(TX * TY, np.int32)
+    stop_margin = np.zeros((H, W))
+    t_err = np.zeros((H, W))
     lib().orc_render(n, deg, _p(m), _p(ls), _p(q), _p(lo), _p(sh), _p(cam), _p(bg), _p(img), _p(T), _p(nc),
-                     _p(margin), _p(ties))
-    return dict(img=img, final_T=T, n_contrib=nc, margin=margin, tie_tiles=ties)
+                     _p(margin), _p(ties), _p(stop_margin), _p(t_err))
+    # stop_margin / t_err: the early-stop decision's own relative distance to T_MIN and a bound on the
+    # relative float32 error of T at that point (see blend_pixel)
+    return dict(img=img, final_T=T, n_contrib=nc, margin=margin, tie_tiles=ties, stop_margin=stop_margin,
+                t_err=t_err)
 
 
 def render_bruteforce(g, cam, bg):

@@ -355,6 +355,11 @@ struct PixelOut {
   S T;
   int n_contrib;
   double margin;
+  // diagnostics of the early-stop decision: its smallest relative distance to T_MIN over the
+  // entries tested, and a bound on the relative error a float32 evaluation accumulates in T
+  // over the blended entries (1e-6 per factor, times 1 / (1 - alpha) for near-opaque ones)
+  double stop_margin;
+  double t_err;
 };
 
 template <class S>
@@ -366,6 +371,7 @@ PixelOut<S> blend_pixel(int px, int py, const int* list, int len, const Proj<S>*
   S T = S(1.0);
   int last = 0;
   double margin = std::numeric_limits<double>::infinity();
+  double stop_margin = std::numeric_limits<double>::infinity(), t_err = 0.0;
   for (int k = 0; k < len; ++k) {
     const Proj<S>& g = P[list[k]];
     S dx = g.x - (double)px, dy = g.y - (double)py;
@@ -384,7 +390,9 @@ PixelOut<S> blend_pixel(int px, int py, const int* list, int len, const Proj<S>*
     if (val(alpha) < ALPHA_MIN) continue;
     S testT = T * (1.0 - alpha);
     margin = std::min(margin, std::fabs(val(testT) - T_MIN) / T_MIN);
+    stop_margin = std::min(stop_margin, std::fabs(val(testT) - T_MIN) / T_MIN);
     if (val(testT) < T_MIN) break;
+    t_err += 1e-6 / (1.0 - val(alpha));
     for (int ch = 0; ch < 3; ++ch) o.col[ch] = o.col[ch] + g.col[ch] * alpha * T;
     if (blended) blended->push_back(k);
     if (Ts) Ts->push_back(T);
@@ -395,12 +403,15 @@ PixelOut<S> blend_pixel(int px, int py, const int* list, int len, const Proj<S>*
   o.T = T;
   o.n_contrib = last;
   o.margin = margin;
+  o.stop_margin = stop_margin;
+  o.t_err = t_err;
   return o;
 }
 
 template <class S>
 void render_image(const Lists& L, const Proj<S>* P, int W, int H, const double bg[3], S* img,
-                  S* finalT, int* ncontrib, double* margin) {
+                  S* finalT, int* ncontrib, double* margin, double* stop_margin = nullptr,
+                  double* t_err = nullptr) {
   int TX = (W + TILE - 1) / TILE;
 #pragma omp parallel for schedule(dynamic, 4)
   for (int py = 0; py < H; ++py)
@@ -413,6 +424,8 @@ void render_image(const Lists& L, const Proj<S>* P, int W, int H, const double b
       if (finalT) finalT[p] = o.T;
       if (ncontrib) ncontrib[p] = o.n_contrib;
       if (margin) margin[p] = o.margin;
+      if (stop_margin) stop_margin[p] = o.stop_margin;
+      if (t_err) t_err[p] = o.t_err;
     }
 }
 
@@ -681,7 +694,8 @@ long long orc_bin(int n, const double* xy, const int* radius, const double* dept
 // distance of any blend decision to its threshold), tie_tiles[ntiles].
 void orc_render(int n, int deg, const double* means, const double* ls, const double* quats,
                 const double* logit, const double* sh, const double* camv, const double* bg,
-                double* img, double* finalT, int* ncontrib, double* margin, int* tie_tiles) {
+                double* img, double* finalT, int* ncontrib, double* margin, int* tie_tiles,
+                double* stop_margin, double* t_err) {
   Cam cam = load_cam(camv);
   Params p{n, deg, means, ls, quats, logit, sh};
   std::vector<Proj<double>> P;
@@ -693,7 +707,7 @@ void orc_render(int n, int deg, const double* means, const double* ls, const dou
   int TX = (cam.W + TILE - 1) / TILE, TY = (cam.H + TILE - 1) / TILE;
   if (tie_tiles) std::memset(tie_tiles, 0, sizeof(int) * TX * TY);
   bin_and_sort(n, x.data(), y.data(), r.data(), d.data(), cam.W, cam.H, L, tie_tiles);
-  render_image<double>(L, P.data(), cam.W, cam.H, bg, img, finalT, ncontrib, margin);
+  render_image<double>(L, P.data(), cam.W, cam.H, bg, img, finalT, ncontrib, margin, stop_margin, t_err);
 }
 
 // Brute-force render used as a pin of the tile path: each pixel independently
