@@ -119,10 +119,13 @@ typedef struct gs_grad2d {
  * job_base     [U * n_tiles + 1]  exclusive prefix (in tile_order) of the number
  *                                 of chunks of each list; job_base[U n_tiles] = jobs
  * jobs         [2 * max_jobs]     (order position, chunk) of every chunk job
- * checkpoints  [max_checkpoints][256][4]  per pixel (T, r, g, b) of the forward
- *                                 at every interior chunk boundary
- * chunk_last   [max_checkpoints][256]     forward scratch: per pixel the last
- *                                 blended entry of each chunk and a stop flag
+ * checkpoints  [max_checkpoints][256][4]  per pixel, at every interior chunk
+ *                                 boundary: T there and the colour composited
+ *                                 behind it per unit T (r, g, b), written by
+ *                                 the forward for the chunked backward
+ * chunk_last   [max_checkpoints][256]     forward scratch (per pixel and
+ *                                 chunk: last blended entry and stop flag, then
+ *                                 the T in front of the chunk)
  * chunk        entries per chunk (a multiple of 32); max_jobs >= U n_tiles +
  *              max_instances / chunk + 1, max_checkpoints >= max_instances /
  *              chunk + 1 (gs_schedule_sizes).

@@ -354,11 +354,19 @@ __device__ __forceinline__ uint32_t warp_block_bits(int w) {
 // T_MIN stops (done).  A warp reads 2 bytes (mask) and 4 bytes (record id)
 // per entry, two rounds ahead, and gathers the records of its hits one round
 // ahead; the blend itself is that of k_render_fwd.
+// With LOCAL, it also accumulates this walk's own partial (transmittance tl and
+// colour cl from tl = 1, cl = 0: the walk's contribution per unit incoming T),
+// which the checkpoints' colour-behind terms are composed from.
+struct LocalAcc {
+  float t, c0, c1, c2;
+};
+
+template <bool LOCAL = false>
 __device__ __forceinline__ void walk_fwd(const uint32_t* __restrict__ vals, const uint16_t* __restrict__ masks,
                                          const float2* __restrict__ xy, const float4* __restrict__ conic_op,
                                          const float4* __restrict__ rgb, uint32_t off, int beg, int end,
                                          uint32_t wbits, float fx, float fy, Rec* my, float& T, float& c0,
-                                         float& c1, float& c2, int& last, bool& done) {
+                                         float& c1, float& c2, int& last, bool& done, LocalAcc* loc = nullptr) {
   const unsigned FULL = 0xffffffffu;
   int lane = threadIdx.x & 31;
   bool h1 = false;
@@ -406,6 +414,11 @@ __device__ __forceinline__ void walk_fwd(const uint32_t* __restrict__ vals, cons
       c0 += rc.x * wgt; c1 += rc.y * wgt; c2 += rc.z * wgt;
       T = tT;
       last = base + j + 1;
+      if (LOCAL) {
+        float lw = alpha * loc->t;
+        loc->c0 += rc.x * lw; loc->c1 += rc.y * lw; loc->c2 += rc.z * lw;
+        loc->t *= 1.f - alpha;
+      }
     }
     __syncwarp();
   }
@@ -523,7 +536,7 @@ __global__ void __launch_bounds__(32) k_render_fwd_combine(const uint2* __restri
                                                                  const uint32_t* __restrict__ order,
                                                                  const uint32_t* __restrict__ job_base, int K,
                                                                  float4* __restrict__ ckpt,
-                                                                 const uint32_t* __restrict__ chunk_last,
+                                                                 uint32_t* __restrict__ chunk_last,
                                                                  const uint32_t* __restrict__ vals,
                                                                  const uint16_t* __restrict__ masks,
                                                                  const float2* __restrict__ xy,
@@ -565,14 +578,15 @@ __global__ void __launch_bounds__(32) k_render_fwd_combine(const uint2* __restri
     done = (lw & STOP_BIT) != 0u;  // a stop in chunk 0 is exact
   }
   int64_t cp0 = (int64_t)job_base[o] - o;
+  int stop_at = done ? 0 : nch;  // the chunk in which the pixel stopped (nch: it does not)
   for (int c = 1; c < nch; ++c) {
     int64_t slot = (cp0 + c - 1) * TILE_PIX + P.pix_local;
     bool need = false;
     if (P.inside && cstar < 0) {
-      float4 pt = ckpt[slot];
       uint32_t lw = chunk_last[slot];
-      ckpt[slot] = make_float4(T, c0, c1, c2);  // the state in front of chunk c (final once done)
+      chunk_last[slot] = __float_as_uint(T);  // T in front of chunk c (final once done)
       if (!done) {
+        float4 pt = ckpt[slot];
         float Tn = T * pt.x;
         if ((lw & STOP_BIT) == 0u && !(Tn < T_MIN)) {
           c0 += T * pt.y; c1 += T * pt.z; c2 += T * pt.w;
@@ -588,17 +602,42 @@ __global__ void __launch_bounds__(32) k_render_fwd_combine(const uint2* __restri
     }
     if (serial && __any_sync(FULL, need)) {
       bool dd = !need;  // lanes that do not walk take no part
-      walk_fwd(vals, masks, xy, conic_op, rgb, rg.x, c * K, min(c * K + K, L), P.wbits, (float)P.px, (float)P.py,
-               s_rec, T, c0, c1, c2, last, dd);
-      if (need) done = dd;
+      LocalAcc la = {1.f, 0.f, 0.f, 0.f};
+      walk_fwd<true>(vals, masks, xy, conic_op, rgb, rg.x, c * K, min(c * K + K, L), P.wbits, (float)P.px,
+                     (float)P.py, s_rec, T, c0, c1, c2, last, dd, &la);
+      if (need) {
+        ckpt[slot] = make_float4(la.t, la.c0, la.c1, la.c2);  // the chunk's partial, up to the stop
+        done = dd;
+        if (done) stop_at = c;
+      }
     }
   }
   if (!P.inside) return;
   if (cstar >= 1) {
+    // boundaries in front of the stop chunk: S_b = A_b + B_b S_c* (pass 3 knows S_c*)
+    float A0 = 0.f, A1 = 0.f, A2 = 0.f, B = 1.f;
+    for (int b = cstar - 1; b >= 1; --b) {
+      int64_t slot = (cp0 + b - 1) * TILE_PIX + P.pix_local;
+      float4 pt = ckpt[slot];
+      A0 = pt.y + pt.x * A0; A1 = pt.z + pt.x * A1; A2 = pt.w + pt.x * A2;
+      B = pt.x * B;
+      ckpt[slot] = make_float4(B, A0, A1, A2);
+    }
     im[pix] = c0; im[plane + pix] = c1; im[2 * plane + pix] = c2;
     fT[pix] = T;
     nc[pix] = (uint32_t)last | ((uint32_t)cstar << CSTAR_SHIFT) | REWALK_BIT;
   } else {
+    // checkpoint b: (T in front of chunk b, colour behind boundary b per unit T there), the chunks
+    // from b to the stop composited back to front over the background
+    float S0 = bg0, S1 = bg1, S2 = bg2;
+    for (int b = nch - 1; b >= 1; --b) {
+      int64_t slot = (cp0 + b - 1) * TILE_PIX + P.pix_local;
+      if (b <= stop_at) {
+        float4 pt = ckpt[slot];
+        S0 = pt.y + pt.x * S0; S1 = pt.z + pt.x * S1; S2 = pt.w + pt.x * S2;
+      }
+      ckpt[slot] = make_float4(__uint_as_float(chunk_last[slot]), S0, S1, S2);
+    }
     im[pix] = c0 + T * bg0;
     im[plane + pix] = c1 + T * bg1;
     im[2 * plane + pix] = c2 + T * bg2;
@@ -616,6 +655,7 @@ __global__ void __launch_bounds__(32) k_render_fwd_stop(const uint2* __restrict_
                                                               const uint32_t* __restrict__ job_base,
                                                               const uint32_t* __restrict__ jobs, int K, int NT,
                                                               float4* __restrict__ ckpt,
+                                                              uint32_t* __restrict__ chunk_last,
                                                               const uint32_t* __restrict__ vals,
                                                               const uint16_t* __restrict__ masks,
                                                               const float2* __restrict__ xy,
@@ -654,11 +694,41 @@ __global__ void __launch_bounds__(32) k_render_fwd_stop(const uint2* __restrict_
   }
   if (!__any_sync(0xffffffffu, mine)) return;
   bool done = !mine;
-  walk_fwd(vals, masks, xy, conic_op, rgb, rg.x, ch * K, min(ch * K + K, L), P.wbits, (float)P.px, (float)P.py,
-           s_rec, T, c0, c1, c2, last, done);
-  if (!mine) return;
   int64_t cp0 = (int64_t)job_base[o] - o;
-  for (int b = ch + 1; b < nch; ++b) ckpt[(cp0 + b - 1) * TILE_PIX + P.pix_local] = make_float4(T, c0, c1, c2);
+  // walk chunk c* (and, should the pixel not stop there after all, the chunks after it), keeping each
+  // walked chunk's partial and the T in front of it; chunks behind the stop get the identity partial
+  int c = ch;
+  for (; c < nch; ++c) {
+    LocalAcc la = {1.f, 0.f, 0.f, 0.f};
+    float Tin = T;
+    walk_fwd<true>(vals, masks, xy, conic_op, rgb, rg.x, c * K, min(c * K + K, L), P.wbits, (float)P.px,
+                   (float)P.py, s_rec, T, c0, c1, c2, last, done, &la);
+    if (mine) {
+      int64_t slot = (cp0 + c - 1) * TILE_PIX + P.pix_local;
+      ckpt[slot] = make_float4(la.t, la.c0, la.c1, la.c2);
+      chunk_last[slot] = __float_as_uint(Tin);
+    }
+    if (__all_sync(0xffffffffu, done)) break;
+  }
+  if (!mine) return;
+  // checkpoints: (T in front of boundary b, colour behind it per unit T), composited back to front
+  float S0 = bg0, S1 = bg1, S2 = bg2;
+  for (int b = nch - 1; b >= ch; --b) {
+    int64_t slot = (cp0 + b - 1) * TILE_PIX + P.pix_local;
+    if (b <= c) {
+      float4 pt = ckpt[slot];
+      S0 = pt.y + pt.x * S0; S1 = pt.z + pt.x * S1; S2 = pt.w + pt.x * S2;
+      ckpt[slot] = make_float4(__uint_as_float(chunk_last[slot]), S0, S1, S2);
+    } else {
+      ckpt[slot] = make_float4(T, bg0, bg1, bg2);  // behind the stop: final state, background behind
+    }
+  }
+  for (int b = 1; b < ch; ++b) {  // in front of c*: S_b = A_b + B_b S_c* as left by pass 2
+    int64_t slot = (cp0 + b - 1) * TILE_PIX + P.pix_local;
+    float4 ab = ckpt[slot];
+    ckpt[slot] = make_float4(__uint_as_float(chunk_last[slot]), ab.y + ab.x * S0, ab.z + ab.x * S1,
+                             ab.w + ab.x * S2);
+  }
   im[pix] = c0 + T * bg0;
   im[plane + pix] = c1 + T * bg1;
   im[2 * plane + pix] = c2 + T * bg2;
@@ -677,6 +747,7 @@ __global__ void __launch_bounds__(32) k_render_fwd_seq(const uint2* __restrict__
                                                              const uint32_t* __restrict__ order,
                                                              const uint32_t* __restrict__ job_base, int K,
                                                              float4* __restrict__ ckpt,
+                                                             uint32_t* __restrict__ chunk_last,
                                                              const uint32_t* __restrict__ vals,
                                                              const uint16_t* __restrict__ masks,
                                                              const float2* __restrict__ xy,
@@ -696,11 +767,25 @@ __global__ void __launch_bounds__(32) k_render_fwd_seq(const uint2* __restrict__
   int last = 0;
   bool done = !P.inside;
   for (int c = 0; c < max(nch, 1); ++c) {
-    if (c > 0 && P.inside) ckpt[(cp0 + c - 1) * TILE_PIX + P.pix_local] = make_float4(T, c0, c1, c2);
-    walk_fwd(vals, masks, xy, conic_op, rgb, rg.x, c * K, min(c * K + K, L), P.wbits, (float)P.px, (float)P.py,
-             s_rec, T, c0, c1, c2, last, done);
+    LocalAcc la = {1.f, 0.f, 0.f, 0.f};
+    float Tin = T;
+    walk_fwd<true>(vals, masks, xy, conic_op, rgb, rg.x, c * K, min(c * K + K, L), P.wbits, (float)P.px,
+                   (float)P.py, s_rec, T, c0, c1, c2, last, done, &la);
+    if (c > 0 && P.inside) {  // the chunk's partial and the T in front of it
+      int64_t slot = (cp0 + c - 1) * TILE_PIX + P.pix_local;
+      ckpt[slot] = make_float4(la.t, la.c0, la.c1, la.c2);
+      chunk_last[slot] = __float_as_uint(Tin);
+    }
   }
   if (P.inside) {
+    // checkpoints: (T in front of boundary b, colour behind it per unit T), composited back to front
+    float S0 = bg0, S1 = bg1, S2 = bg2;
+    for (int b = nch - 1; b >= 1; --b) {
+      int64_t slot = (cp0 + b - 1) * TILE_PIX + P.pix_local;
+      float4 pt = ckpt[slot];
+      S0 = pt.y + pt.x * S0; S1 = pt.z + pt.x * S1; S2 = pt.w + pt.x * S2;
+      ckpt[slot] = make_float4(__uint_as_float(chunk_last[slot]), S0, S1, S2);
+    }
     int64_t plane = (int64_t)W * H;
     int64_t pix = (int64_t)P.py * W + P.px;
     float* im = img + (int64_t)P.u * 3 * plane;
@@ -770,14 +855,11 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
     const float* d = dimg + (int64_t)u * 3 * plane;
     g0 = d[pix]; g1 = d[plane + pix]; g2 = d[2 * plane + pix];
     if (ch + 1 < nch && last > cbeg) {
+      // the forward's checkpoint at the chunk's end: T there and the colour behind it per unit T
       int pix_local = (py - ty * TILE) * TILE + (px - tx * TILE);
       float4 cp = ckpt[((int64_t)job_base[o] - o + ch) * TILE_PIX + pix_local];
-      const float* im = img + (int64_t)u * 3 * plane;
       T = cp.x;
-      float iT = 1.f / T;
-      S0 = (im[pix] - cp.y) * iT;
-      S1 = (im[plane + pix] - cp.z) * iT;
-      S2 = (im[2 * plane + pix] - cp.w) * iT;
+      S0 = cp.y; S1 = cp.z; S2 = cp.w;
     } else {
       T = final_T[(int64_t)u * plane + pix];
     }
@@ -997,7 +1079,7 @@ int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const u
   if (sched && sched->walk_whole_lists) {                                                                          \
     k_render_fwd_seq<BW><<<dim3(grid.x * 8), 32, 0, s>>>(                                                           \
         (const uint2*)ranges, sched->tile_order, sched->job_base, sched->chunk, (float4*)sched->checkpoints,        \
-        sorted_vals, sched->block_masks, (const float2*)proj->xy, (const float4*)proj->conic_op,                    \
+        sched->chunk_last, sorted_vals, sched->block_masks, (const float2*)proj->xy, (const float4*)proj->conic_op,                    \
         (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib);        \
   } else if (sched) {                                                                                               \
     dim3 gj((unsigned)(sched->max_jobs * 8));                                                                       \
@@ -1012,7 +1094,7 @@ int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const u
         (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib);        \
     k_render_fwd_stop<BW><<<gj, 32, 0, s>>>(                                                                        \
         (const uint2*)ranges, sched->tile_order, sched->job_base, sched->jobs, sched->chunk, (int)grid.x,            \
-        (float4*)sched->checkpoints, sorted_vals, sched->block_masks, (const float2*)proj->xy,                       \
+        (float4*)sched->checkpoints, sched->chunk_last, sorted_vals, sched->block_masks, (const float2*)proj->xy,    \
         (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2],  \
         img, final_T, n_contrib);                                                                                   \
   } else                                                                                                            \

@@ -178,13 +178,12 @@ def test_window_parity(full, k):
     assert use.sum() > 100, (inside.sum(), use.sum())
     gpu = {"dxy": full["dxy"][sel][use], "dconic": full["dco"][sel][use][:, :3],
            "dopacity": full["dco"][sel][use][:, 3], "drgb": full["drgb"][sel][use][:, :3]}
-    # The chunked reverse replay starts each chunk from the forward's checkpoint: T, and the colour behind the
-    # chunk as (img - C) / T.  Where a pixel is nearly saturated at a chunk boundary (T ~ 1e-4) that difference
-    # of float32 values loses ~3 digits, so a few Gaussians in front of such boundaries see errors up to ~1e-2
-    # of the group's scale (float32 epsilon / T ~ 1e-3 relative on the colour behind, times the colour
-    # range); 99.9% of the values stay within the small tests' 1e-3 of the group's scale.
+    # The chunked reverse replay starts each chunk from the forward's checkpoint (T and the colour behind the
+    # boundary, composited back to front from the chunks' partials); float32 T recovered by division along
+    # chunks of up to 1024 entries keeps 99.9% of the values within the small tests' 1e-3 of the group's scale
+    # and all within 2e-3.
     for key in gpu:
         ref = d[key][use]
         sc = np.abs(ref).max()
         err = np.abs(gpu[key] - ref) / sc
-        assert sc > 0 and np.quantile(err, 0.999) <= GRAD_TOL and err.max() <= 20 * GRAD_TOL, (key, err.max())
+        assert sc > 0 and np.quantile(err, 0.999) <= GRAD_TOL and err.max() <= 2 * GRAD_TOL, (key, err.max())
