@@ -34,6 +34,9 @@ WORKLOADS = {
     # smaller workloads for quick checks
     "iso1M-1080p": dict(n=1_000_000, modes=8, views=64, W=1920, H=1080),
     "iso200k-540p": dict(n=200_000, modes=8, views=16, W=960, H=540),
+    # the 10M scene at the square resolutions the paper trains on (1024^2 and 2048^2)
+    "iso10M-1024sq": dict(n=10_000_000, modes=16, views=128, W=1024, H=1024),
+    "iso10M-2048sq": dict(n=10_000_000, modes=16, views=64, W=2048, H=2048),
     # small device footprint (about 2.5 GB) for Nsight Compute captures of single kernels
     "iso2M-1080p-prof": dict(n=2_000_000, modes=16, views=4, W=1920, H=1080),
     # batched form: 8 x-slabs with 5% ghosts, uneven populations (28M), 16 masked views each, one
@@ -390,8 +393,24 @@ FWD_SLOTS_PER_PAIR = 15
 BWD_SLOTS_PER_PAIR = 50
 
 
-def rooflines(res):
-    """Achieved vs peak for every stage; returns (dominant stage's roofline, all)."""
+# DRAM bytes (read + write) per unit of each stage, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum, one pass, every launch of three timed steps) of the 10M-Gaussian 1080p training step
+# with the kernels as they are now; the unit is the one the stage's algorithmic work counts.  Reported only
+# for that workload, scaled by the units of the bench's own timed views.
+TRAFFIC_WORKLOAD = "iso10M-1080p"
+TRAFFIC_PER_UNIT = {
+    "preprocess": ("gaussian", 290.15),
+    "bin_sort": ("instance", 204.93),
+    "render_fwd": ("fwd_pair", 1.3294),
+    "loss": ("pixel", 20.12),
+    "blend_bwd": None,  # kernel changed since the capture
+    "project_bwd_adam": ("gaussian", 1477.54),
+}
+
+
+def rooflines(res, workload=None, issue=None):
+    """Achieved vs peak for every stage; returns (dominant stage's roofline, all).  issue: measured FP32 / MUFU
+    lane-operation rates of this device (peak.issue_rates), the denominator of the issue-bound stages."""
     peaks = {}
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -399,9 +418,17 @@ def rooflines(res):
     hbm = peaks.get("hbm_gbs")
     src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    mhz = peaks.get("sm_max_mhz", 2070.0)
     sms = 152
-    slots = 128 * sms * mhz * 1e6 / 1e12  # FP32 lane issue slots per second (T/s)
+    if issue:
+        slots = issue["fp32_tops"]
+        slots_src = (f"measured: gs_peak_issue FP32 FMA chains on all {issue['sms']} SMs in this run "
+                     f"({issue['fp32_tops']:.2f} T lane-ops/s; MUFU ex2 {issue['mufu_tops']:.2f} T/s); "
+                     "FLOP-equivalent = one FP32 issue slot")
+    else:
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        slots = 128 * sms * mhz * 1e6 / 1e12  # FP32 lane issue slots per second (T/s)
+        slots_src = (f"derived: 152 SMs x 128 FP32 lanes x {mhz:.0f} MHz (one issue slot per lane per clock; "
+                     "FLOP-equivalent = one FP32 issue slot)")
     N, I, pairs = res["N"], res["instances"], res["pairs"]
     tiles = ((res["W"] + 15) // 16) * ((res["H"] + 15) // 16)
     key_bits = 32 + max(1, (tiles - 1).bit_length())
@@ -415,6 +442,8 @@ def rooflines(res):
         "render_fwd": ("alu", pairs["fwd_pairs"] * FWD_SLOTS_PER_PAIR),
         "blend_bwd": ("alu", pairs["bwd_pairs"] * BWD_SLOTS_PER_PAIR),
     }
+    units = {"gaussian": N, "instance": I, "fwd_pair": pairs["fwd_pairs"], "bwd_pair": pairs["bwd_pairs"],
+             "pixel": res["W"] * res["H"]}
     kernel = {"preprocess": "k_preprocess", "bin_sort": "sort chain", "project_bwd_adam": "k_project_bwd_adam1",
               "loss": "loss kernels", "render_fwd": "k_render_fwd_m + k_render_fwd_combine + k_render_fwd_stop",
               "blend_bwd": "k_render_bwd_m"}
@@ -423,22 +452,28 @@ def rooflines(res):
         if name not in work:
             continue
         bound, amount = work[name]
+        traffic = None
+        if workload == TRAFFIC_WORKLOAD and TRAFFIC_PER_UNIT[name]:
+            u, per = TRAFFIC_PER_UNIT[name]
+            traffic = round(per * units[u])
         if bound == "hbm":
             ach = amount / (ms * 1e-3) / 1e9
             out[name] = {"kernel": kernel[name], "bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
-                         "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
+                         "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": traffic,
                          "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
         else:
             ach = amount / (ms * 1e-3) / 1e12
             fwd = name == "render_fwd"
-            units = pairs["fwd_pairs"] if fwd else pairs["bwd_pairs"]
+            n_pairs = pairs["fwd_pairs"] if fwd else pairs["bwd_pairs"]
             out[name] = {"kernel": kernel[name], "bound": "alu", "achieved": round(ach, 3),
                          "peak": round(slots, 2), "unit": "TFLOP/s",
-                         "frac": round(ach / slots, 4), "traffic": None,
-                         "peak_source": f"derived: 152 SMs x 128 FP32 lanes x {mhz:.0f} MHz (one issue slot "
-                                        f"per lane per clock; FLOP-equivalent = one FP32 issue slot)",
-                         "work": f"{units:.3e} (pixel, list entry) pairs x "
+                         "frac": round(ach / slots, 4), "traffic": traffic, "peak_source": slots_src,
+                         "work": f"{n_pairs:.3e} (pixel, list entry) pairs x "
                                  f"{FWD_SLOTS_PER_PAIR if fwd else BWD_SLOTS_PER_PAIR} FP32 issue slots"}
+        if traffic is not None:
+            out[name]["traffic_source"] = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum at {TRAFFIC_WORKLOAD}: "
+                                           f"{TRAFFIC_PER_UNIT[name][1]} B per {TRAFFIC_PER_UNIT[name][0]} x "
+                                           f"{units[TRAFFIC_PER_UNIT[name][0]]:.4g} {TRAFFIC_PER_UNIT[name][0]}s")
         out[name]["share"] = round(float(ms / res["stage_ms"].sum()), 4)
     dom = max(out, key=lambda k: out[k]["share"])
     return out[dom], out
@@ -474,6 +509,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import __graft_entry__
     __graft_entry__.build()
+    from paper_2509_12138_gb300 import peak
+    issue = peak.issue_rates()  # the issue-bound stages' denominator, measured before the timed region
     res = run_ours(args, wl, rank, world)
     ms_step = res["ms_total"] / args.steps
     t_max = res["ms_total"]
@@ -494,7 +531,7 @@ def main():
                 "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
         "gpu_launches": res["launches"], "clocks": res["clocks"],
     }
-    line["roofline"], line["stage_rooflines"] = rooflines(res)
+    line["roofline"], line["stage_rooflines"] = rooflines(res, args.workload, issue)
     line["blend_pairs_per_view"] = {k: round(v) for k, v in res["pairs"].items()}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(res["scene"], args.cpu_window)

@@ -471,6 +471,23 @@ int gs_init_gaussians(const float* points, const float* normals, const int32_t* 
                       const float* knn_dist, int knn_k, int64_t n, const float* weights,
                       float logit_default, float* params, int64_t n_gauss, gs_stream_t stream);
 
+/* ---- issue-rate microbenchmark (the blend kernels' roofline denominator) -
+ * The blend stages are bound by instruction issue, not by HBM or the tensor
+ * cores, so their peak is the rate at which the SMs retire FP32 and MUFU
+ * lane-operations, measured by this kernel on the device it runs on.
+ * Every thread runs GS_PEAK_CHAINS independent chains of `iters` steps:
+ * mode 0: x = fma(x, a, b) (one FP32 lane-operation per step); mode 1:
+ * x = ex2.approx(x) - b (one MUFU ex2 and one FP32 add per step).  Chain j
+ * starts at x = -j/8; out[t] = the sum of thread t's chains (device float
+ * [gs_peak_threads(n_sms)], caller-owned).  Lane-operations per launch =
+ * gs_peak_threads(n_sms) x GS_PEAK_CHAINS x iters; the caller times the
+ * launch with events on `stream`.  Bad mode, sizes or a NULL out return
+ * GS_ERR_INVALID. */
+#define GS_PEAK_CHAINS 8
+int gs_peak_threads(int n_sms);
+int gs_peak_issue(int mode, int n_sms, int iters, float a, float b, float* out,
+                  gs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,8 @@ SIGNATURES = {
                             C.POINTER(GsSchedule), VP]),
     "gs_blend_pairs": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, VP, VP, VP]),
     "gs_loss_workspace_size": (SZ, [I32, I32, I32]),
+    "gs_peak_threads": (I32, [I32]),
+    "gs_peak_issue": (I32, [I32, I32, I32, F32, F32, VP, VP]),
     "gs_loss": (I32, [VP, VP, VP, I32, I32, I32, F32, VP, SZ, VP, VP, VP]),
     "gs_render_bwd": (I32, [VP, I64, I32, C.POINTER(GsUnits), VP, C.POINTER(GsProj), VP, VP, I32, I32, c_f32p, VP,
                             VP, VP, VP, C.POINTER(GsGrad2d), VP, I32, C.POINTER(GsSchedule), VP]),

@@ -804,13 +804,45 @@ __global__ void __launch_bounds__(32) k_render_fwd_seq(const uint2* __restrict__
 // 16 keeps the same-address atomics of a record bounded for large splats.
 constexpr int DIRECT_LANES = 16;
 
+// Position and conic terms of one (pixel, record) pair's gradient from the
+// pixel offset (dx, dy), dp = o G dL/dalpha and the conic (A, B, C):
+// v = (dx, dy | dA, dB, dC) in the order add_lane expects.
+__device__ __forceinline__ void pos_conic_terms(float dx, float dy, float dp, float A, float B, float Cc, float* v) {
+  v[2] = -0.5f * dx * dx * dp;
+  v[3] = -dx * dy * dp;
+  v[4] = -0.5f * dy * dy * dp;
+  v[0] = -(A * dx + B * dy) * dp;
+  v[1] = -(Cc * dy + B * dx) * dp;
+}
+
+// Ring of deferred (pixel, record) pairs of the scheduled backward, per warp.
+constexpr int QCAP = 64;
+
+// Lanes 0..count-1 finish entries head .. head + count - 1 of the ring: the
+// position and conic terms, then the record's three vector atomics.
+__device__ __forceinline__ void bwd_queue_flush(const float4* s_q, int head, int count, int lane, float* dxy,
+                                                float* dco, float* drgb) {
+  if (lane < count) {
+    int e = (head + lane) & (QCAP - 1);
+    float4 a = s_q[e], b = s_q[QCAP + e], c = s_q[2 * QCAP + e];
+    float v[5];
+    pos_conic_terms(a.x, a.y, a.z, b.x, b.y, b.z, v);
+    int64_t pr = (int64_t)__float_as_uint(b.w);
+    atomic_add2(dxy + 2 * pr, v[0], v[1]);
+    atomic_add4(dco + 4 * pr, v[2], v[3], v[4], a.w);
+    atomic_add4(drgb + 4 * pr, c.x, c.y, c.z, 0.f);
+  }
+}
+
 // Backward over chunk jobs: job (list, chunk c, pixel block) replays entries
 // [c K, min((c + 1) K, L)) of the list back to front.  It starts from the
-// forward's checkpoint at the chunk's end (T and the colour C accumulated in
-// front of it; the colour behind is (img - C) / T), or from final_T and the
-// background for the last chunk.  Headers two rounds ahead, hit records one
-// round ahead, as in the forward.
-template <int BW>
+// forward's checkpoint at the chunk's end (T in front of it and the colour
+// behind it per unit T), or from final_T and the background for the last
+// chunk.  Headers two rounds ahead, hit records one round ahead, as in the
+// forward.  QUEUE (float accumulation) defers the gradient terms of sparse
+// hits to a per-warp ring; the deterministic mode (fixed != NULL) runs
+// without it.
+template <int BW, bool QUEUE>
 __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ ranges,
                                                            const uint32_t* __restrict__ order,
                                                            const uint32_t* __restrict__ job_base,
@@ -885,6 +917,12 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
     int k2 = n - 64 + lane;
     if (n - 32 > cbeg && k2 >= cbeg) { mk2 = masks[rg.x + k2]; pk2 = vals[rg.x + k2]; }
   }
+  // QUEUE: pairs of hits with at most DIRECT_LANES contributing lanes go to a ring of
+  // (dx, dy, dp, dopacity | A, B, C, id | dr, dg, db) entries; every 32 entries all
+  // lanes finish one pair each (conic and position terms, vector atomics).  The
+  // per-pixel state (T, colour behind) is still updated at the hit in list order.
+  __shared__ float4 s_q[QUEUE ? 3 * QCAP : 1];
+  int qh = 0, qt = 0;  // ring head and tail (warp-uniform)
   for (int top = n; top > cbeg; top -= 32) {
     int base = top - 32;
     bool hit = h1;
@@ -907,18 +945,15 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
       int j = 31 - __clz(mask);
       mask &= ~(1u << j);
       int pos = base + j;
-      float v[9];
-      #pragma unroll
-      for (int e = 0; e < 9; ++e) v[e] = 0.f;
       bool contrib = false;
+      float dx = 0.f, dy = 0.f, dp = 0.f, v5 = 0.f, v6 = 0.f, v7 = 0.f, v8 = 0.f;
       float4 ra = my[j].a, rb = my[j].b;
       if (pos < last) {
-        float dx = ra.x - fx_of(px), dy = ra.y - fy_of(py);
-        float A = ra.z, B = ra.w, Cc = rb.x, op = rb.y;
-        float power = splat_power(A, B, Cc, dx, dy);
+        dx = ra.x - fx_of(px); dy = ra.y - fy_of(py);
+        float power = splat_power(ra.z, ra.w, rb.x, dx, dy);
         if (power <= 0.f && power >= rb.z) {
           float G = __expf(power);
-          float araw = op * G;
+          float araw = rb.y * G;
           bool clamped = araw > ALPHA_MAX;
           float alpha = clamped ? ALPHA_MAX : araw;
           if (alpha >= ALPHA_MIN) {
@@ -926,46 +961,61 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
             float4 rc = my[j].c;
             T = __fdividef(T, 1.f - alpha);
             float wgt = alpha * T;
-            v[6] = wgt * g0; v[7] = wgt * g1; v[8] = wgt * g2;
+            v6 = wgt * g0; v7 = wgt * g1; v8 = wgt * g2;
             float dalpha = T * ((rc.x - S0) * g0 + (rc.y - S1) * g1 + (rc.z - S2) * g2);
             S0 = alpha * rc.x + (1.f - alpha) * S0;
             S1 = alpha * rc.y + (1.f - alpha) * S1;
             S2 = alpha * rc.z + (1.f - alpha) * S2;
-            if (!clamped) {
-              v[5] = G * dalpha;
-              float dp = araw * dalpha;
-              v[2] = -0.5f * dx * dx * dp;
-              v[3] = -dx * dy * dp;
-              v[4] = -0.5f * dy * dy * dp;
-              v[0] = -(A * dx + B * dy) * dp;
-              v[1] = -(Cc * dy + B * dx) * dp;
+            if (!clamped) {  // a clamped alpha passes no gradient to opacity, conic or position
+              v5 = G * dalpha;
+              dp = araw * dalpha;
             }
           }
         }
       }
       unsigned cm = __ballot_sync(FULL, contrib);
-      if (cm) {
-        int64_t pr = (int64_t)__float_as_uint(rb.w);
-        // fixed point: nine scalar int64 atomics per lane, so reduce unless one lane contributes
-        if (__popc(cm) <= (fixed ? 1 : DIRECT_LANES)) {
-          // few contributing lanes (small splats): each issues its own three vector
-          // atomics, which costs fewer instructions and atomic operations than a reduction
-          if (contrib) add_lane(dxy, dco, drgb, fixed, pr, v);
-        } else {
-          float tot = reduce8(v, lane);
-          float e8 = v[8];
-          #pragma unroll
-          for (int oo = 16; oo > 0; oo >>= 1) e8 += __shfl_xor_sync(FULL, e8, oo);
-          if ((lane & 3) == 0) {
-            add_one(dxy, dco, drgb, fixed, pr, q, tot);
-          } else if (lane == 1) {
-            add_one(dxy, dco, drgb, fixed, pr, 8, e8);
-          }
+      if (!cm) continue;
+      int nc = __popc(cm);
+      if (QUEUE && nc <= DIRECT_LANES) {
+        if (contrib) {
+          int e = (qt + __popc(cm & ((1u << lane) - 1u))) & (QCAP - 1);
+          s_q[e] = make_float4(dx, dy, dp, v5);
+          s_q[QCAP + e] = make_float4(ra.z, ra.w, rb.x, rb.w);
+          s_q[2 * QCAP + e] = make_float4(v6, v7, v8, 0.f);
+        }
+        qt += nc;
+        if (qt - qh >= 32) {
+          __syncwarp();
+          bwd_queue_flush(s_q, qh, 32, lane, dxy, dco, drgb);
+          qh += 32;
+          __syncwarp();
+        }
+        continue;
+      }
+      int64_t pr = (int64_t)__float_as_uint(rb.w);
+      float v[9];
+      pos_conic_terms(dx, dy, dp, ra.z, ra.w, rb.x, v);
+      v[5] = v5; v[6] = v6; v[7] = v7; v[8] = v8;
+      // fixed point: nine scalar int64 atomics per lane, so reduce unless one lane contributes
+      if (nc <= (fixed ? 1 : DIRECT_LANES)) {
+        // few contributing lanes (small splats): each issues its own three vector
+        // atomics, which costs fewer instructions and atomic operations than a reduction
+        if (contrib) add_lane(dxy, dco, drgb, fixed, pr, v);
+      } else {
+        float tot = reduce8(v, lane);
+        float e8 = v[8];
+        #pragma unroll
+        for (int oo = 16; oo > 0; oo >>= 1) e8 += __shfl_xor_sync(FULL, e8, oo);
+        if ((lane & 3) == 0) {
+          add_one(dxy, dco, drgb, fixed, pr, q, tot);
+        } else if (lane == 1) {
+          add_one(dxy, dco, drgb, fixed, pr, 8, e8);
         }
       }
     }
     __syncwarp();
   }
+  if (QUEUE && qt > qh) bwd_queue_flush(s_q, qh, qt - qh, lane, dxy, dco, drgb);
 }
 
 // Tile order: heaviest lists first (counting sort of (unit, tile) by the
@@ -1134,7 +1184,8 @@ int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const ui
   dim3 grid(TX * TY * n_units);
 #define GS_BWD(BW)                                                                                                   \
   if (sched)                                                                                                         \
-    k_render_bwd_m<BW><<<dim3((unsigned)(sched->max_jobs * 8)), 32, 0, s>>>(                                        \
+    (fixed ? k_render_bwd_m<BW, false> : k_render_bwd_m<BW, true>)<<<dim3((unsigned)(sched->max_jobs * 8)), 32, 0, \
+                                                                     s>>>(                                           \
         (const uint2*)ranges, sched->tile_order, sched->job_base, sched->jobs, sched->chunk,                         \
         (const float4*)sched->checkpoints, sorted_vals, sched->block_masks, (const float2*)proj->xy,                 \
         (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX, TX * TY, TX * TY * n_units,     \
