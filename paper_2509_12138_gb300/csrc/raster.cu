@@ -442,9 +442,8 @@ __device__ __forceinline__ void walk_fwd(const uint32_t* __restrict__ vals, cons
 // Per pixel the blended entries and the stop decision are those of the
 // sequential walk; the combine changes only the rounding order of T and C.
 constexpr uint32_t STOP_BIT = 0x80000000u;  // chunk partial: the pixel stopped inside the chunk
-constexpr uint32_t REWALK_BIT = 0x80000000u;  // n_contrib between passes 2 and 3: stop chunk pending
-constexpr int CSTAR_SHIFT = 24;              // ... with the stop chunk in bits 24..30
-constexpr int MAX_CSTAR = 127;               // lists of more chunks are finished serially in pass 2
+constexpr uint32_t REWALK_BIT = 0x80000000u;  // n_contrib between passes 2 and 3: stop chunk pending,
+                                             // the stop chunk c* in the bits below it
 
 // The warp's pixel of (list o, block w) and its geometry.
 template <int BW>
@@ -525,118 +524,126 @@ __global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ r
 // background.  For lists of several chunks, the state in front of chunk c is
 // (T, C); the chunk's partial is applied when it shows no stop and
 // T T_c >= T_MIN (then no entry of the chunk can stop the pixel), and
-// otherwise chunk c is the pixel's stop chunk c*.  The state in front of each
-// boundary up to c* is written over its partial (the backward's checkpoint).
-// Pixels that never stop are final here; pixels with c* >= 1 leave their
-// state in front of c* in img / final_T and (last | c* | REWALK_BIT) in
-// n_contrib for pass 3.  Lists of more than MAX_CSTAR + 1 chunks (or of
-// 2^24 entries or more) walk their stop chunks here, one after another.
+// otherwise chunk c is the pixel's stop chunk c*.  T in front of each
+// boundary up to c* goes to chunk_last (the backward's checkpoints take it
+// from there).  Pixels that never stop are final here; pixels with c* >= 1
+// leave their state in front of c* in img / final_T, (c* | REWALK_BIT) in
+// n_contrib and their last contributing position in chunk_last at c*'s slot
+// for pass 3.  The per-chunk loads are issued CB chunks at a time: for lists
+// of hundreds of chunks the walk is otherwise one load latency per chunk.
+constexpr int CB = 4;
+
 template <int BW>
 __global__ void __launch_bounds__(32) k_render_fwd_combine(const uint2* __restrict__ ranges,
                                                                  const uint32_t* __restrict__ order,
                                                                  const uint32_t* __restrict__ job_base, int K,
                                                                  float4* __restrict__ ckpt,
-                                                                 uint32_t* __restrict__ chunk_last,
-                                                                 const uint32_t* __restrict__ vals,
-                                                                 const uint16_t* __restrict__ masks,
-                                                                 const float2* __restrict__ xy,
-                                                                 const float4* __restrict__ conic_op,
-                                                                 const float4* __restrict__ rgb, int W, int H,
+                                                                 uint32_t* __restrict__ chunk_last, int W, int H,
                                                                  int TX, int n_tiles, float bg0, float bg1, float bg2,
                                                                  float* __restrict__ img, float* __restrict__ final_T,
                                                                  uint32_t* __restrict__ n_contrib) {
-  const unsigned FULL = 0xffffffffu;
-  __shared__ Rec s_rec[32];
   int o = (int)(blockIdx.x >> 3), w = (int)(blockIdx.x & 7u);
   int nch = (int)(job_base[o + 1] - job_base[o]);
   if (nch == 1) return;
   PixelOf<BW> P(order, o, w, n_tiles, TX, W, H);
+  if (!P.inside) return;
   int64_t plane = (int64_t)W * H;
   int64_t pix = (int64_t)P.py * W + P.px;
   float* im = img + (int64_t)P.u * 3 * plane;
   float* fT = final_T + (int64_t)P.u * plane;
   uint32_t* nc = n_contrib + (int64_t)P.u * plane;
   if (nch == 0) {
-    if (P.inside) {
-      im[pix] = bg0; im[plane + pix] = bg1; im[2 * plane + pix] = bg2;
-      fT[pix] = 1.f;
-      nc[pix] = 0u;
-    }
+    im[pix] = bg0; im[plane + pix] = bg1; im[2 * plane + pix] = bg2;
+    fT[pix] = 1.f;
+    nc[pix] = 0u;
     return;
   }
-  uint2 rg = ranges[(int64_t)P.u * n_tiles + P.tile];
-  int L = (int)(rg.y - rg.x);
-  bool serial = nch > MAX_CSTAR + 1 || L >= (1 << CSTAR_SHIFT);
-  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-  int last = 0, cstar = -1;
-  bool done = !P.inside;
-  if (P.inside) {
-    c0 = im[pix]; c1 = im[plane + pix]; c2 = im[2 * plane + pix];
-    T = fT[pix];
-    uint32_t lw = nc[pix];
-    last = (int)(lw & ~STOP_BIT);
-    done = (lw & STOP_BIT) != 0u;  // a stop in chunk 0 is exact
-  }
+  float c0 = im[pix], c1 = im[plane + pix], c2 = im[2 * plane + pix];
+  float T = fT[pix];
+  uint32_t lw0 = nc[pix];
+  int last = (int)(lw0 & ~STOP_BIT);
+  bool done = (lw0 & STOP_BIT) != 0u;  // a stop in chunk 0 is exact
+  int cstar = -1;
   int64_t cp0 = (int64_t)job_base[o] - o;
-  int stop_at = done ? 0 : nch;  // the chunk in which the pixel stopped (nch: it does not)
-  for (int c = 1; c < nch; ++c) {
-    int64_t slot = (cp0 + c - 1) * TILE_PIX + P.pix_local;
-    bool need = false;
-    if (P.inside && cstar < 0) {
-      uint32_t lw = chunk_last[slot];
-      chunk_last[slot] = __float_as_uint(T);  // T in front of chunk c (final once done)
-      if (!done) {
-        float4 pt = ckpt[slot];
-        float Tn = T * pt.x;
-        if ((lw & STOP_BIT) == 0u && !(Tn < T_MIN)) {
-          c0 += T * pt.y; c1 += T * pt.z; c2 += T * pt.w;
-          T = Tn;
-          uint32_t lc = lw & ~STOP_BIT;
-          if (lc) last = (int)lc;
-        } else if (serial) {
-          need = true;
-        } else {
-          cstar = c;  // pass 3 walks chunk c for this pixel and writes the rest
-        }
+  float4* cpp = ckpt + cp0 * TILE_PIX + P.pix_local;       // slot of boundary b: cpp[(b - 1) * TILE_PIX]
+  uint32_t* clp = chunk_last + cp0 * TILE_PIX + P.pix_local;
+  for (int cb = 1; cb < nch && cstar < 0; cb += CB) {
+    uint32_t lwv[CB];
+    float4 ptv[CB];
+    #pragma unroll
+    for (int q = 0; q < CB; ++q) {
+      int c = cb + q;
+      if (c < nch) {
+        lwv[q] = clp[(int64_t)(c - 1) * TILE_PIX];
+        if (!done) ptv[q] = cpp[(int64_t)(c - 1) * TILE_PIX];
       }
     }
-    if (serial && __any_sync(FULL, need)) {
-      bool dd = !need;  // lanes that do not walk take no part
-      LocalAcc la = {1.f, 0.f, 0.f, 0.f};
-      walk_fwd<true>(vals, masks, xy, conic_op, rgb, rg.x, c * K, min(c * K + K, L), P.wbits, (float)P.px,
-                     (float)P.py, s_rec, T, c0, c1, c2, last, dd, &la);
-      if (need) {
-        ckpt[slot] = make_float4(la.t, la.c0, la.c1, la.c2);  // the chunk's partial, up to the stop
-        done = dd;
-        if (done) stop_at = c;
+    #pragma unroll
+    for (int q = 0; q < CB; ++q) {
+      int c = cb + q;
+      if (c >= nch || cstar >= 0) break;
+      clp[(int64_t)(c - 1) * TILE_PIX] = __float_as_uint(T);  // T in front of chunk c (final once done)
+      if (done) continue;
+      float4 pt = ptv[q];
+      float Tn = T * pt.x;
+      if ((lwv[q] & STOP_BIT) == 0u && !(Tn < T_MIN)) {
+        c0 += T * pt.y; c1 += T * pt.z; c2 += T * pt.w;
+        T = Tn;
+        uint32_t lc = lwv[q] & ~STOP_BIT;
+        if (lc) last = (int)lc;
+      } else {
+        cstar = c;  // pass 3 walks chunk c for this pixel and writes the rest
       }
     }
   }
-  if (!P.inside) return;
   if (cstar >= 1) {
     // boundaries in front of the stop chunk: S_b = A_b + B_b S_c* (pass 3 knows S_c*)
     float A0 = 0.f, A1 = 0.f, A2 = 0.f, B = 1.f;
-    for (int b = cstar - 1; b >= 1; --b) {
-      int64_t slot = (cp0 + b - 1) * TILE_PIX + P.pix_local;
-      float4 pt = ckpt[slot];
-      A0 = pt.y + pt.x * A0; A1 = pt.z + pt.x * A1; A2 = pt.w + pt.x * A2;
-      B = pt.x * B;
-      ckpt[slot] = make_float4(B, A0, A1, A2);
+    for (int bb = cstar - 1; bb >= 1; bb -= CB) {
+      float4 ptv[CB];
+      #pragma unroll
+      for (int q = 0; q < CB; ++q)
+        if (bb - q >= 1) ptv[q] = cpp[(int64_t)(bb - q - 1) * TILE_PIX];
+      #pragma unroll
+      for (int q = 0; q < CB; ++q) {
+        if (bb - q < 1) break;
+        float4 pt = ptv[q];
+        A0 = pt.y + pt.x * A0; A1 = pt.z + pt.x * A1; A2 = pt.w + pt.x * A2;
+        B = pt.x * B;
+        cpp[(int64_t)(bb - q - 1) * TILE_PIX] = make_float4(B, A0, A1, A2);
+      }
     }
     im[pix] = c0; im[plane + pix] = c1; im[2 * plane + pix] = c2;
     fT[pix] = T;
-    nc[pix] = (uint32_t)last | ((uint32_t)cstar << CSTAR_SHIFT) | REWALK_BIT;
+    clp[(int64_t)(cstar - 1) * TILE_PIX] = (uint32_t)last;  // pass 3 reads it and puts T back
+    nc[pix] = (uint32_t)cstar | REWALK_BIT;
   } else {
     // checkpoint b: (T in front of chunk b, colour behind boundary b per unit T there), the chunks
-    // from b to the stop composited back to front over the background
+    // from b to the stop composited back to front over the background (a pixel that stopped in
+    // chunk 0 has the background behind every boundary)
+    int stop_at = done ? 0 : nch;
     float S0 = bg0, S1 = bg1, S2 = bg2;
-    for (int b = nch - 1; b >= 1; --b) {
-      int64_t slot = (cp0 + b - 1) * TILE_PIX + P.pix_local;
-      if (b <= stop_at) {
-        float4 pt = ckpt[slot];
-        S0 = pt.y + pt.x * S0; S1 = pt.z + pt.x * S1; S2 = pt.w + pt.x * S2;
+    for (int bb = nch - 1; bb >= 1; bb -= CB) {
+      float4 ptv[CB];
+      uint32_t tv[CB];
+      #pragma unroll
+      for (int q = 0; q < CB; ++q) {
+        int b = bb - q;
+        if (b >= 1) {
+          if (b <= stop_at) ptv[q] = cpp[(int64_t)(b - 1) * TILE_PIX];
+          tv[q] = clp[(int64_t)(b - 1) * TILE_PIX];
+        }
       }
-      ckpt[slot] = make_float4(__uint_as_float(chunk_last[slot]), S0, S1, S2);
+      #pragma unroll
+      for (int q = 0; q < CB; ++q) {
+        int b = bb - q;
+        if (b < 1) break;
+        if (b <= stop_at) {
+          float4 pt = ptv[q];
+          S0 = pt.y + pt.x * S0; S1 = pt.z + pt.x * S1; S2 = pt.w + pt.x * S2;
+        }
+        cpp[(int64_t)(b - 1) * TILE_PIX] = make_float4(__uint_as_float(tv[q]), S0, S1, S2);
+      }
     }
     im[pix] = c0 + T * bg0;
     im[plane + pix] = c1 + T * bg1;
@@ -674,7 +681,6 @@ __global__ void __launch_bounds__(32) k_render_fwd_stop(const uint2* __restrict_
   PixelOf<BW> P(order, o, w, n_tiles, TX, W, H);
   uint2 rg = ranges[(int64_t)P.u * n_tiles + P.tile];
   int L = (int)(rg.y - rg.x);
-  if (nch > MAX_CSTAR + 1 || L >= (1 << CSTAR_SHIFT)) return;  // finished in pass 2
   int64_t plane = (int64_t)W * H;
   int64_t pix = (int64_t)P.py * W + P.px;
   float* im = img + (int64_t)P.u * 3 * plane;
@@ -683,18 +689,18 @@ __global__ void __launch_bounds__(32) k_render_fwd_stop(const uint2* __restrict_
   bool mine = false;
   float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
   int last = 0;
+  int64_t cp0 = (int64_t)job_base[o] - o;
   if (P.inside) {
     uint32_t lw = nc[pix];
-    mine = (lw & REWALK_BIT) != 0u && (int)((lw >> CSTAR_SHIFT) & 127u) == ch;
+    mine = (lw & REWALK_BIT) != 0u && (int)(lw & ~REWALK_BIT) == ch;
     if (mine) {
-      last = (int)(lw & ((1u << CSTAR_SHIFT) - 1u));
+      last = (int)chunk_last[(cp0 + ch - 1) * TILE_PIX + P.pix_local];  // left there by pass 2
       c0 = im[pix]; c1 = im[plane + pix]; c2 = im[2 * plane + pix];
       T = fT[pix];
     }
   }
   if (!__any_sync(0xffffffffu, mine)) return;
   bool done = !mine;
-  int64_t cp0 = (int64_t)job_base[o] - o;
   // walk chunk c* (and, should the pixel not stop there after all, the chunks after it), keeping each
   // walked chunk's partial and the T in front of it; chunks behind the stop get the identity partial
   int c = ch;
@@ -712,22 +718,38 @@ __global__ void __launch_bounds__(32) k_render_fwd_stop(const uint2* __restrict_
   }
   if (!mine) return;
   // checkpoints: (T in front of boundary b, colour behind it per unit T), composited back to front
+  float4* cpp = ckpt + cp0 * TILE_PIX + P.pix_local;  // slot of boundary b: cpp[(b - 1) * TILE_PIX]
+  const uint32_t* clp = chunk_last + cp0 * TILE_PIX + P.pix_local;
+  for (int b = nch - 1; b > c; --b)
+    cpp[(int64_t)(b - 1) * TILE_PIX] = make_float4(T, bg0, bg1, bg2);  // behind the stop: final state
   float S0 = bg0, S1 = bg1, S2 = bg2;
-  for (int b = nch - 1; b >= ch; --b) {
-    int64_t slot = (cp0 + b - 1) * TILE_PIX + P.pix_local;
-    if (b <= c) {
-      float4 pt = ckpt[slot];
+  for (int bb = min(c, nch - 1); bb >= ch; bb -= CB) {  // walked chunks, back to front
+    float4 ptv[CB];
+    uint32_t tv[CB];
+    #pragma unroll
+    for (int q = 0; q < CB; ++q)
+      if (bb - q >= ch) { ptv[q] = cpp[(int64_t)(bb - q - 1) * TILE_PIX]; tv[q] = clp[(int64_t)(bb - q - 1) * TILE_PIX]; }
+    #pragma unroll
+    for (int q = 0; q < CB; ++q) {
+      if (bb - q < ch) break;
+      float4 pt = ptv[q];
       S0 = pt.y + pt.x * S0; S1 = pt.z + pt.x * S1; S2 = pt.w + pt.x * S2;
-      ckpt[slot] = make_float4(__uint_as_float(chunk_last[slot]), S0, S1, S2);
-    } else {
-      ckpt[slot] = make_float4(T, bg0, bg1, bg2);  // behind the stop: final state, background behind
+      cpp[(int64_t)(bb - q - 1) * TILE_PIX] = make_float4(__uint_as_float(tv[q]), S0, S1, S2);
     }
   }
-  for (int b = 1; b < ch; ++b) {  // in front of c*: S_b = A_b + B_b S_c* as left by pass 2
-    int64_t slot = (cp0 + b - 1) * TILE_PIX + P.pix_local;
-    float4 ab = ckpt[slot];
-    ckpt[slot] = make_float4(__uint_as_float(chunk_last[slot]), ab.y + ab.x * S0, ab.z + ab.x * S1,
-                             ab.w + ab.x * S2);
+  for (int bb = 1; bb < ch; bb += CB) {  // in front of c*: S_b = A_b + B_b S_c* as left by pass 2
+    float4 abv[CB];
+    uint32_t tv[CB];
+    #pragma unroll
+    for (int q = 0; q < CB; ++q)
+      if (bb + q < ch) { abv[q] = cpp[(int64_t)(bb + q - 1) * TILE_PIX]; tv[q] = clp[(int64_t)(bb + q - 1) * TILE_PIX]; }
+    #pragma unroll
+    for (int q = 0; q < CB; ++q) {
+      if (bb + q >= ch) break;
+      float4 ab = abv[q];
+      cpp[(int64_t)(bb + q - 1) * TILE_PIX] = make_float4(__uint_as_float(tv[q]), ab.y + ab.x * S0,
+                                                          ab.z + ab.x * S1, ab.w + ab.x * S2);
+    }
   }
   im[pix] = c0 + T * bg0;
   im[plane + pix] = c1 + T * bg1;
@@ -779,12 +801,22 @@ __global__ void __launch_bounds__(32) k_render_fwd_seq(const uint2* __restrict__
   }
   if (P.inside) {
     // checkpoints: (T in front of boundary b, colour behind it per unit T), composited back to front
+    float4* cpp = ckpt + cp0 * TILE_PIX + P.pix_local;  // slot of boundary b: cpp[(b - 1) * TILE_PIX]
+    const uint32_t* clp = chunk_last + cp0 * TILE_PIX + P.pix_local;
     float S0 = bg0, S1 = bg1, S2 = bg2;
-    for (int b = nch - 1; b >= 1; --b) {
-      int64_t slot = (cp0 + b - 1) * TILE_PIX + P.pix_local;
-      float4 pt = ckpt[slot];
-      S0 = pt.y + pt.x * S0; S1 = pt.z + pt.x * S1; S2 = pt.w + pt.x * S2;
-      ckpt[slot] = make_float4(__uint_as_float(chunk_last[slot]), S0, S1, S2);
+    for (int bb = nch - 1; bb >= 1; bb -= CB) {
+      float4 ptv[CB];
+      uint32_t tv[CB];
+      #pragma unroll
+      for (int q = 0; q < CB; ++q)
+        if (bb - q >= 1) { ptv[q] = cpp[(int64_t)(bb - q - 1) * TILE_PIX]; tv[q] = clp[(int64_t)(bb - q - 1) * TILE_PIX]; }
+      #pragma unroll
+      for (int q = 0; q < CB; ++q) {
+        if (bb - q < 1) break;
+        float4 pt = ptv[q];
+        S0 = pt.y + pt.x * S0; S1 = pt.z + pt.x * S1; S2 = pt.w + pt.x * S2;
+        cpp[(int64_t)(bb - q - 1) * TILE_PIX] = make_float4(__uint_as_float(tv[q]), S0, S1, S2);
+      }
     }
     int64_t plane = (int64_t)W * H;
     int64_t pix = (int64_t)P.py * W + P.px;
@@ -1140,8 +1172,7 @@ int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const u
         img, final_T, n_contrib);                                                                                   \
     k_render_fwd_combine<BW><<<dim3(grid.x * 8), 32, 0, s>>>(                                                       \
         (const uint2*)ranges, sched->tile_order, sched->job_base, sched->chunk, (float4*)sched->checkpoints,        \
-        sched->chunk_last, sorted_vals, sched->block_masks, (const float2*)proj->xy, (const float4*)proj->conic_op, \
-        (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib);        \
+        sched->chunk_last, width, height, TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib);              \
     k_render_fwd_stop<BW><<<gj, 32, 0, s>>>(                                                                        \
         (const uint2*)ranges, sched->tile_order, sched->job_base, sched->jobs, sched->chunk, (int)grid.x,            \
         (float4*)sched->checkpoints, sched->chunk_last, sorted_vals, sched->block_masks, (const float2*)proj->xy,    \

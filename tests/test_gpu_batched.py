@@ -251,8 +251,8 @@ def test_schedule_does_not_change_results(chunk, opaque, n, whole):
     order only: images agree to float rounding, n_contrib exactly, gradients up to atomic order.  Small
     chunks put many chunks on every list; the opaque scenes make most pixels stop after the first chunk,
     so the stop-chunk walk and the checkpoints after a stop are exercised; the dense scene has lists of
-    more than 128 chunks, whose stop chunks the combine pass walks itself.  With whole-list walks the
-    per-pixel arithmetic is that of the unscheduled kernel, so images are bit-identical."""
+    more than 128 chunks.  With whole-list walks the per-pixel arithmetic is that of the unscheduled
+    kernel, so images are bit-identical."""
     deg, W, H = 1, 150, 110
     g, cams = scenes.random_scene(n, deg, 31, W, H)
     if opaque:
@@ -279,7 +279,7 @@ def test_schedule_does_not_change_results(chunk, opaque, n, whole):
             if chunk == 32:
                 assert lens.max() > 4 * chunk  # several chunks per list
             if n > 10000:
-                assert lens.max() > 128 * chunk  # the combine pass's serial path
+                assert lens.max() > 128 * chunk
     a, b = res
     if opaque:
         stopped = a[4] < 1e-3
@@ -293,3 +293,36 @@ def test_schedule_does_not_change_results(chunk, opaque, n, whole):
     sc = float(a[2].abs().max())
     assert torch.allclose(a[2], b[2], rtol=1e-3, atol=1e-5 * sc)
     assert torch.allclose(a[3], b[3], rtol=1e-3, atol=1e-5 * float(a[3].abs().max()))
+
+
+@pytest.mark.parametrize("whole", [False, True])
+def test_stops_hundreds_of_chunks_deep(whole):
+    """Pixels that stop after thousands of list entries (hundreds of 32-entry chunks, stop chunks far
+    beyond 127): the chunk-parallel forward finds each pixel's stop chunk and walks it again, and the
+    backward replays from the checkpoints; results as without the schedule (tests/scenes.deep_stop_scene)."""
+    deg, W, H, chunk = 1, 32, 32, 32
+    g, cams = scenes.deep_stop_scene(5, W, H)
+    n = g["means"].shape[0]
+    params = gs.pack_params(g, deg)
+    camd = gs.pack_cameras(cams)
+    gt, mask = scenes.random_gt(W, H, 6)
+    res = []
+    for use_sched in (False, True):
+        fr = gs.Frame(n, gs.Units.single(n), W, H, deg, chunk=chunk)
+        fr.use_masks = use_sched
+        fr.walk_whole_lists = whole
+        fr.fit_capacity(params, camd)
+        fr.forward(params, camd, BG)
+        fr.loss(torch.from_numpy(gt).cuda()[None], torch.from_numpy(mask).cuda()[None], 0.2)
+        fr.backward(params, camd, BG)
+        torch.cuda.synchronize()
+        assert fr.read_status() == 0
+        res.append((fr.img.clone(), fr.n_contrib.clone(), fr.grads.clone(), fr.final_T.clone()))
+    a, b = res
+    deep = (a[3] < 1.2e-4) & (a[1] > 128 * chunk)
+    assert int(deep.sum()) > 100  # stop chunks beyond 127
+    assert torch.equal(a[1], b[1])
+    assert torch.allclose(a[0], b[0], rtol=0, atol=1e-5)
+    assert torch.allclose(a[3], b[3], rtol=1e-4, atol=1e-7)
+    sc = float(a[2].abs().max())
+    assert torch.allclose(a[2], b[2], rtol=1e-3, atol=1e-5 * sc)
