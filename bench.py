@@ -307,19 +307,21 @@ def run_ours(args, wl, rank, world):
         pairs.append(frame.blend_pairs())
     pairs_per_step = {key: float(np.mean([p[key] for p in pairs])) for key in pairs[0]}
 
-    # render-only (a1-a3) for Mpix/s, in the faster forward mode on a few views (whole-list walks stop early
-    # on opaque views; chunk-parallel compositing wins where pixels rarely stop)
+    # render-only (a1-a3) for Mpix/s, in the faster forward mode over 8 views spread around the orbit (whole-list
+    # walks stop early on opaque views; chunk-parallel compositing wins where pixels rarely stop and on the
+    # long lists of edge-on views)
     mode_ms = {}
+    probe = [(k * V) // 8 for k in range(8)]
     for whole in (False, True):
         frame.walk_whole_lists = whole
         frame.forward(params, scene.cam(0), bg)
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0.record()
-        for k in range(4):
-            frame.forward(params, scene.cam(k % V), bg)
+        for v in probe:
+            frame.forward(params, scene.cam(v), bg)
         t1.record()
         torch.cuda.synchronize()
-        mode_ms["whole_lists" if whole else "parallel_chunks"] = round(t0.elapsed_time(t1) / 4, 3)
+        mode_ms["whole_lists" if whole else "parallel_chunks"] = round(t0.elapsed_time(t1) / len(probe), 3)
     frame.walk_whole_lists = mode_ms["whole_lists"] < mode_ms["parallel_chunks"]
     torch.cuda.synchronize()
     r0 = torch.cuda.Event(enable_timing=True)
@@ -399,12 +401,12 @@ BWD_SLOTS_PER_PAIR = 50
 # for that workload, scaled by the units of the bench's own timed views.
 TRAFFIC_WORKLOAD = "iso10M-1080p"
 TRAFFIC_PER_UNIT = {
-    "preprocess": ("gaussian", 290.15),
-    "bin_sort": ("instance", 204.93),
-    "render_fwd": ("fwd_pair", 1.3294),
-    "loss": ("pixel", 20.12),
-    "blend_bwd": None,  # kernel changed since the capture
-    "project_bwd_adam": ("gaussian", 1477.54),
+    "preprocess": ("gaussian", 290.10),
+    "bin_sort": ("instance", 204.92),
+    "render_fwd": ("fwd_pair", 1.3177),
+    "loss": ("pixel", 20.03),
+    "blend_bwd": ("bwd_pair", 3.7585),
+    "project_bwd_adam": ("gaussian", 1477.61),
 }
 
 

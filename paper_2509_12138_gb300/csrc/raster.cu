@@ -699,7 +699,11 @@ __global__ void __launch_bounds__(32) k_render_fwd_stop(const uint2* __restrict_
       T = fT[pix];
     }
   }
-  if (!__any_sync(0xffffffffu, mine)) return;
+  // only the 4x4 pixel blocks of this warp's walking pixels: records whose block mask misses them
+  // cannot reach those pixels
+  uint32_t my_block = mine ? 1u << (4 * ((P.py - P.ty * TILE) >> 2) + ((P.px - P.tx * TILE) >> 2)) : 0u;
+  uint32_t wbits = __reduce_or_sync(0xffffffffu, my_block);
+  if (!wbits) return;
   bool done = !mine;
   // walk chunk c* (and, should the pixel not stop there after all, the chunks after it), keeping each
   // walked chunk's partial and the T in front of it; chunks behind the stop get the identity partial
@@ -707,7 +711,7 @@ __global__ void __launch_bounds__(32) k_render_fwd_stop(const uint2* __restrict_
   for (; c < nch; ++c) {
     LocalAcc la = {1.f, 0.f, 0.f, 0.f};
     float Tin = T;
-    walk_fwd<true>(vals, masks, xy, conic_op, rgb, rg.x, c * K, min(c * K + K, L), P.wbits, (float)P.px,
+    walk_fwd<true>(vals, masks, xy, conic_op, rgb, rg.x, c * K, min(c * K + K, L), wbits, (float)P.px,
                    (float)P.py, s_rec, T, c0, c1, c2, last, done, &la);
     if (mine) {
       int64_t slot = (cp0 + c - 1) * TILE_PIX + P.pix_local;
