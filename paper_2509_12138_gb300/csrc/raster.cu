@@ -398,17 +398,18 @@ __device__ __forceinline__ void walk_fwd(const uint32_t* __restrict__ vals, cons
       my[lane].c = c;
     }
     __syncwarp();
-    while (mask) {
-      int j = __ffs(mask) - 1;
-      mask &= mask - 1;
-      if (done) continue;
+    // hits two at a time: both alphas are evaluated independently (more independent instructions
+    // in flight per warp), then composited in list order
+    auto hit_alpha = [&](int j) -> float {  // 0 when the record cannot blend at this pixel
       float4 ra = my[j].a, rb = my[j].b;
       float power = splat_power(ra.z, ra.w, rb.x, ra.x - fx, ra.y - fy);
-      if (power > 0.f || power < rb.z) continue;
-      float alpha = fminf(ALPHA_MAX, rb.y * __expf(power));
-      if (alpha < ALPHA_MIN) continue;
+      if (power > 0.f || power < rb.z) return 0.f;
+      return fminf(ALPHA_MAX, rb.y * __expf(power));
+    };
+    auto composite = [&](int j, float alpha) {
+      if (done || alpha < ALPHA_MIN) return;
       float tT = T * (1.f - alpha);
-      if (tT < T_MIN) { done = true; continue; }
+      if (tT < T_MIN) { done = true; return; }
       float4 rc = my[j].c;
       float wgt = alpha * T;
       c0 += rc.x * wgt; c1 += rc.y * wgt; c2 += rc.z * wgt;
@@ -419,6 +420,17 @@ __device__ __forceinline__ void walk_fwd(const uint32_t* __restrict__ vals, cons
         loc->c0 += rc.x * lw; loc->c1 += rc.y * lw; loc->c2 += rc.z * lw;
         loc->t *= 1.f - alpha;
       }
+    };
+    while (mask) {
+      int j1 = __ffs(mask) - 1;
+      mask &= mask - 1;
+      bool two = mask != 0u;
+      int j2 = two ? __ffs(mask) - 1 : j1;
+      if (two) mask &= mask - 1;
+      float a1 = hit_alpha(j1);
+      float a2 = two ? hit_alpha(j2) : 0.f;
+      composite(j1, a1);
+      if (two) composite(j2, a2);
     }
     __syncwarp();
   }
