@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--deterministic", action="store_true",
                     help="accumulate screen-space gradients in fixed point (bitwise reproducible steps)")
+    ap.add_argument("--random-order", action="store_true",
+                    help="keep the sampler's random point order instead of the extraction's Z-order")
     ap.add_argument("--cpu-window", type=int, default=8, help="CPU sample: 1/(w*w) of the view's pixels")
     ap.add_argument("--experiment", default=None, choices=["learned-init", "ghost-ablation"],
                     help="instead of the throughput line: the plain vs batched + learned-init comparison")
@@ -233,7 +235,7 @@ def run_ours(args, wl, rank, world):
     from paper_2509_12138_gb300 import shard
     # weak scaling: every rank trains its own independent scene (no collective on the data path)
     scene = workload.isosurface_scene(wl["n"], wl["modes"], wl["views"], wl["W"], wl["H"], sh_degree=3,
-                                      seed=shard.rank_seed(0, rank), device=dev)
+                                      seed=shard.rank_seed(0, rank), device=dev, spatial=not args.random_order)
     N, W, H = scene.n, scene.width, scene.height
     params = gs.pack_params(scene.init, 3, dev)
     frame = gs.Frame(N, gs.Units.single(N), W, H, 3, device=dev, max_instances=6 * N,
@@ -397,20 +399,20 @@ BWD_SLOTS_PER_PAIR = 50
 
 # DRAM bytes (read + write) per unit of each stage, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum, one pass, every launch of three timed steps) of the 10M-Gaussian 1080p training step
-# with the kernels as they are now; the unit is the one the stage's algorithmic work counts.  Reported only
-# for that workload, scaled by the units of the bench's own timed views.
+# with the kernels as they are now and the points in Z-order; the unit is the one the stage's algorithmic
+# work counts.  Reported only for that workload and order, scaled by the units of the bench's own timed views.
 TRAFFIC_WORKLOAD = "iso10M-1080p"
 TRAFFIC_PER_UNIT = {
-    "preprocess": ("gaussian", 290.10),
-    "bin_sort": ("instance", 204.92),
-    "render_fwd": ("fwd_pair", 1.3177),
-    "loss": ("pixel", 20.03),
-    "blend_bwd": ("bwd_pair", 3.7585),
-    "project_bwd_adam": ("gaussian", 1477.61),
+    "preprocess": ("gaussian", 290.09),
+    "bin_sort": ("instance", 204.85),
+    "render_fwd": ("fwd_pair", 0.2471),
+    "loss": ("pixel", 20.02),
+    "blend_bwd": ("bwd_pair", 0.6271),
+    "project_bwd_adam": ("gaussian", 1477.58),
 }
 
 
-def rooflines(res, workload=None, issue=None):
+def rooflines(res, workload=None, issue=None, random_order=False):
     """Achieved vs peak for every stage; returns (dominant stage's roofline, all).  issue: measured FP32 / MUFU
     lane-operation rates of this device (peak.issue_rates), the denominator of the issue-bound stages."""
     peaks = {}
@@ -455,7 +457,7 @@ def rooflines(res, workload=None, issue=None):
             continue
         bound, amount = work[name]
         traffic = None
-        if workload == TRAFFIC_WORKLOAD and TRAFFIC_PER_UNIT[name]:
+        if workload == TRAFFIC_WORKLOAD and not random_order and TRAFFIC_PER_UNIT[name]:
             u, per = TRAFFIC_PER_UNIT[name]
             traffic = round(per * units[u])
         if bound == "hbm":
@@ -490,7 +492,8 @@ def main():
     config = {"workload": args.workload, "gaussians": wl["n"], "width": wl["W"], "height": wl["H"],
               "views": wl["views"], "sh_degree": 3, "loss": f"masked L1 + {LAMBDA_SSIM} D-SSIM",
               "gradient_accumulation": "int64 fixed point" if args.deterministic else "float atomics",
-              "l2": "inputs larger than L2 (params+Adam state 9.6 GB at 10M)"}
+              "l2": "inputs larger than L2 (params+Adam state 9.6 GB at 10M)",
+              "point_order": "random" if args.random_order else "z-order"}
     if args.impl == "reference":
         return run_reference(args, wl, rank, world, config)
     if args.experiment == "learned-init":
@@ -533,7 +536,7 @@ def main():
                 "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
         "gpu_launches": res["launches"], "clocks": res["clocks"],
     }
-    line["roofline"], line["stage_rooflines"] = rooflines(res, args.workload, issue)
+    line["roofline"], line["stage_rooflines"] = rooflines(res, args.workload, issue, args.random_order)
     line["blend_pairs_per_view"] = {k: round(v) for k, v in res["pairs"].items()}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(res["scene"], args.cpu_window)

@@ -101,8 +101,14 @@ def render_gt(gauss: dict, cams: synth.Cameras, sh_degree: int, bg, device="cuda
 
 
 def isosurface_scene(n: int, n_modes: int, n_views: int, width: int, height: int, sh_degree: int = 3,
-                     seed: int = 0, radius: float = 1.5, device="cuda", init_log_scale=None) -> Scene:
+                     seed: int = 0, radius: float = 1.5, device="cuda", init_log_scale=None,
+                     spatial: bool = True) -> Scene:
+    """spatial: store the points in Z-order (synth.spatial_order), the cell-by-cell order in which an
+    isosurface extraction emits them; False keeps the sampler's random order."""
     pts, nrm, _ = synth.interface_points(n, n_modes, seed)
+    if spatial:
+        o = synth.spatial_order(pts)
+        pts, nrm = pts[o], nrm[o]
     colors = synth.lambert_colors(pts, nrm)
     spacing = spacing_estimate(nrm, n)
     cams = synth.orbital_cameras(n_views, radius, center=(0.5, 0.5, 0.5), width=width, height=height)
@@ -144,6 +150,8 @@ def partitioned_scene(slab_counts, n_modes: int, n_views: int, width: int, heigh
     constant x-density (slab_counts points per slab)."""
     from .partition import slab_partition
     pts, nrm, _ = synth.slab_density_points(n_modes=n_modes, slab_counts=slab_counts, seed=seed)
+    o = synth.spatial_order(pts)  # Z-order, as an isosurface extraction emits the points
+    pts, nrm = pts[o], nrm[o]
     n = pts.shape[0]
     colors = synth.lambert_colors(pts, nrm)
     spacing = spacing_estimate(nrm, n)
@@ -166,6 +174,16 @@ def partitioned_scene(slab_counts, n_modes: int, n_views: int, width: int, heigh
                             mask_full=mask_full, init=init, pts=pts, spacing=spacing, nrm=nrm)
 
 
+def _spread2(v: torch.Tensor) -> torch.Tensor:
+    """x in [0, 1) quantised to 16 bits, its bits moved to the even positions 0, 2, ..., 30 (int64)."""
+    q = (v.double() * 65535.0).round().long().clamp_(0, 65535)
+    q = (q | (q << 8)) & 0x00FF00FF
+    q = (q | (q << 4)) & 0x0F0F0F0F
+    q = (q | (q << 2)) & 0x33333333
+    q = (q | (q << 1)) & 0x55555555
+    return q
+
+
 def interface_gaussians_device(n: int, n_modes: int, seed: int, sh_degree: int = 3, device="cuda",
                                chunk: int = 1 << 24):
     """Plain-initialised Gaussians on the perturbed interface generated directly on the device (for
@@ -185,11 +203,19 @@ def interface_gaussians_device(n: int, n_modes: int, seed: int, sh_degree: int =
     npl = param_planes(sh_degree)
     params = torch.zeros((npl, n, 4), dtype=torch.float32, device=device)
     xs = torch.empty(n, dtype=torch.float32, device=device)
+    ys = torch.empty(n, dtype=torch.float32, device=device)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        xs[a:b] = torch.rand(b - a, generator=gen, device=device)
+        ys[a:b] = torch.rand(b - a, generator=gen, device=device)
+    # Z-order over (x, y) (the interface is a height field): the cell-by-cell order of an extraction
+    o = torch.argsort(_spread2(xs) | (_spread2(ys) << 1), stable=True)
+    xs, ys = xs[o], ys[o]
+    del o
     area = 0.0
     for a in range(0, n, chunk):
         b = min(n, a + chunk)
-        x = torch.rand(b - a, generator=gen, device=device)
-        y = torch.rand(b - a, generator=gen, device=device)
+        x, y = xs[a:b], ys[a:b]
         arg = 2.0 * math.pi * (x[:, None] * kx + y[:, None] * ky) + phase
         h = 0.1 * (torch.sin(arg) * amp).sum(1)
         dh = 0.1 * torch.cos(arg) * amp * 2.0 * math.pi
@@ -204,7 +230,6 @@ def interface_gaussians_device(n: int, n_modes: int, seed: int, sh_degree: int =
         col = torch.stack([0.2 + 0.75 * zn, 0.4 + 0.2 * zn, 0.9 - 0.7 * zn], 1) * shade[:, None]
         dc = (col.clamp(0, 1) - 0.5) / Y00
         params[3, a:b, 0:3] = dc
-        xs[a:b] = x
     spacing = (0.5 + 0.75 + 0.9375) / 3.0 / math.sqrt(n / (area / n))
     params[1, :, 0:3] = math.log(spacing)
     params[1, :, 3] = math.log(0.5 / 0.5)  # opacity 0.5 for a visible render-only scene

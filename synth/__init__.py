@@ -206,6 +206,28 @@ def slab_density_points(n_modes: int, slab_counts, seed: int = 0):
     return interface_points(int(slab_counts.sum()), n_modes, seed, x_density=slab_counts)
 
 
+def _spread3(v):
+    """Bits 0..9 of v moved to bits 0, 3, 6, ..., 27 (uint64)."""
+    v = v & np.uint64(0x3FF)
+    v = (v | (v << np.uint64(16))) & np.uint64(0x030000FF)
+    v = (v | (v << np.uint64(8))) & np.uint64(0x0300F00F)
+    v = (v | (v << np.uint64(4))) & np.uint64(0x030C30C3)
+    v = (v | (v << np.uint64(2))) & np.uint64(0x09249249)
+    return v
+
+
+def spatial_order(points):
+    """Permutation that puts points in Z-order (Morton order of a 1024^3 grid over their bounding
+    box), the cell-by-cell coherence of the points an isosurface extraction emits.  Stable."""
+    p = np.asarray(points, dtype=np.float64)
+    if p.shape[0] == 0:
+        return np.zeros(0, dtype=np.int64)
+    lo, hi = p.min(axis=0), p.max(axis=0)
+    q = ((p - lo) / np.maximum(hi - lo, 1e-30) * 1023.0).round().astype(np.uint64)
+    code = _spread3(q[:, 0]) | (_spread3(q[:, 1]) << np.uint64(1)) | (_spread3(q[:, 2]) << np.uint64(2))
+    return np.argsort(code, kind="stable")
+
+
 def lambert_colors(points, normals):
     """Albedo ramp over normalised height, shaded by a fixed directional light.
 

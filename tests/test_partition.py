@@ -48,3 +48,20 @@ def test_uneven_slab_populations():
     pts, _, _ = synth.slab_density_points(8, counts, seed=3)
     part = slab_partition(pts, 8, 0.0)
     assert np.array_equal(part.sizes(), counts)
+
+
+def test_spatial_order_is_the_z_order():
+    """synth.spatial_order sorts points by their Morton code on a 1024^3 grid over the bounding box
+    (checked against a bit-by-bit interleave), stably, and is a permutation."""
+    rng = np.random.default_rng(7)
+    p = rng.random((3000, 3))
+    p[:20] = p[20:40]  # equal points keep their order
+    o = synth.spatial_order(p)
+    assert np.array_equal(np.sort(o), np.arange(len(p)))
+    lo, hi = p.min(0), p.max(0)
+    q = np.round((p - lo) / (hi - lo) * 1023).astype(np.int64)
+    code = np.zeros(len(p), np.int64)
+    for b in range(10):
+        for a in range(3):
+            code |= ((q[:, a] >> b) & 1) << (3 * b + a)
+    assert np.array_equal(o, np.argsort(code, kind="stable"))
