@@ -118,7 +118,9 @@ typedef struct gs_grad2d {
  *                                 box of it) reaches 4x4 pixel block (bx, by)
  * job_base     [U * n_tiles + 1]  exclusive prefix (in tile_order) of the number
  *                                 of chunks of each list; job_base[U n_tiles] = jobs
- * jobs         [2 * max_jobs]     (order position, chunk) of every chunk job
+ * jobs         [2 * max_jobs]     (order position, chunk) of every chunk job; the
+ *                                 last entry, which no job reaches, is the blend
+ *                                 kernels' work counter (reset by each call)
  * checkpoints  [max_checkpoints][256][4]  per pixel, at every interior chunk
  *                                 boundary: T there and the colour composited
  *                                 behind it per unit T (r, g, b), written by

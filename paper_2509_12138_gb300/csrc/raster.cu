@@ -499,36 +499,49 @@ __global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ r
                                                            const float4* __restrict__ rgb, int W, int H, int TX,
                                                            int n_tiles, float bg0, float bg1, float bg2,
                                                            float* __restrict__ img, float* __restrict__ final_T,
-                                                           uint32_t* __restrict__ n_contrib) {
+                                                           uint32_t* __restrict__ n_contrib,
+    uint32_t* __restrict__ ticket) {
   __shared__ Rec s_rec[32];
-  uint32_t jid = blockIdx.x >> 3;
-  if (jid >= job_base[NT]) return;
-  int w = (int)(blockIdx.x & 7u);
-  int o = (int)jobs[2 * (int64_t)jid], ch = (int)jobs[2 * (int64_t)jid + 1];
-  PixelOf<BW> P(order, o, w, n_tiles, TX, W, H);
-  int nch = (int)(job_base[o + 1] - job_base[o]);
-  uint2 rg = ranges[(int64_t)P.u * n_tiles + P.tile];
-  int L = (int)(rg.y - rg.x);
-  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-  int last = 0;
-  bool done = !P.inside;
-  walk_fwd(vals, masks, xy, conic_op, rgb, rg.x, ch * K, min(ch * K + K, L), P.wbits, (float)P.px, (float)P.py,
-           s_rec, T, c0, c1, c2, last, done);
-  if (!P.inside) return;
-  int64_t plane = (int64_t)W * H;
-  int64_t pix = (int64_t)P.py * W + P.px;
-  float* im = img + (int64_t)P.u * 3 * plane;
-  if (nch == 1 || ch == 0) {
-    bool fin = nch == 1;
-    im[pix] = fin ? c0 + T * bg0 : c0;
-    im[plane + pix] = fin ? c1 + T * bg1 : c1;
-    im[2 * plane + pix] = fin ? c2 + T * bg2 : c2;
-    final_T[(int64_t)P.u * plane + pix] = T;
-    n_contrib[(int64_t)P.u * plane + pix] = (uint32_t)last | (!fin && done ? STOP_BIT : 0u);
-  } else {
-    int64_t slot = ((int64_t)job_base[o] - o + ch - 1) * TILE_PIX + P.pix_local;
-    ckpt[slot] = make_float4(T, c0, c1, c2);
-    chunk_last[slot] = (uint32_t)last | (done ? STOP_BIT : 0u);
+  // the resident warps take the (chunk job, pixel block) units from a ticket counter (zeroed before
+  // the launch), the next ticket fetched while a unit runs: no block of a grid sized for the capacity
+  // sits idle, and units of very different cost still spread as they finish
+  const uint32_t total = job_base[NT] * 8u;
+  auto job = [&](uint32_t vb) {
+    uint32_t jid = vb >> 3;
+    int w = (int)(vb & 7u);
+    int o = (int)jobs[2 * (int64_t)jid], ch = (int)jobs[2 * (int64_t)jid + 1];
+    PixelOf<BW> P(order, o, w, n_tiles, TX, W, H);
+    int nch = (int)(job_base[o + 1] - job_base[o]);
+    uint2 rg = ranges[(int64_t)P.u * n_tiles + P.tile];
+    int L = (int)(rg.y - rg.x);
+    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+    int last = 0;
+    bool done = !P.inside;
+    walk_fwd(vals, masks, xy, conic_op, rgb, rg.x, ch * K, min(ch * K + K, L), P.wbits, (float)P.px, (float)P.py,
+             s_rec, T, c0, c1, c2, last, done);
+    if (!P.inside) return;
+    int64_t plane = (int64_t)W * H;
+    int64_t pix = (int64_t)P.py * W + P.px;
+    float* im = img + (int64_t)P.u * 3 * plane;
+    if (nch == 1 || ch == 0) {
+      bool fin = nch == 1;
+      im[pix] = fin ? c0 + T * bg0 : c0;
+      im[plane + pix] = fin ? c1 + T * bg1 : c1;
+      im[2 * plane + pix] = fin ? c2 + T * bg2 : c2;
+      final_T[(int64_t)P.u * plane + pix] = T;
+      n_contrib[(int64_t)P.u * plane + pix] = (uint32_t)last | (!fin && done ? STOP_BIT : 0u);
+    } else {
+      int64_t slot = ((int64_t)job_base[o] - o + ch - 1) * TILE_PIX + P.pix_local;
+      ckpt[slot] = make_float4(T, c0, c1, c2);
+      chunk_last[slot] = (uint32_t)last | (done ? STOP_BIT : 0u);
+    }
+  };
+  const bool lead = (threadIdx.x & 31) == 0;
+  uint32_t vb = __shfl_sync(0xffffffffu, lead ? atomicAdd(ticket, 1u) : 0u, 0);
+  while (vb < total) {
+    uint32_t nxt = lead ? atomicAdd(ticket, 1u) : 0u;
+    job(vb);
+    vb = __shfl_sync(0xffffffffu, nxt, 0);
   }
 }
 
@@ -907,163 +920,176 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
                                                            const uint32_t* __restrict__ n_contrib,
                                                            const float* __restrict__ dimg, float* __restrict__ dxy,
                                                            float* __restrict__ dco, float* __restrict__ drgb,
-                                                           unsigned long long* __restrict__ fixed) {
+                                                           unsigned long long* __restrict__ fixed,
+    uint32_t* __restrict__ ticket) {
   const unsigned FULL = 0xffffffffu;
   __shared__ Rec s_rec[32];
-  uint32_t jid = blockIdx.x >> 3;
-  if (jid >= job_base[NT]) return;
-  int w = (int)(blockIdx.x & 7u);
-  int o = (int)jobs[2 * (int64_t)jid], ch = (int)jobs[2 * (int64_t)jid + 1];
-  uint32_t f = order[o];
-  int u = (int)(f / (uint32_t)n_tiles), tile = (int)(f % (uint32_t)n_tiles);
-  int nch = (int)(job_base[o + 1] - job_base[o]);
-  int tx = tile % TX, ty = tile / TX;
-  constexpr int BH = 32 / BW, NWX = TILE / BW;
-  int lane = threadIdx.x & 31;
-  int px = tx * TILE + (w % NWX) * BW + (lane % BW), py = ty * TILE + (w / NWX) * BH + (lane / BW);
-  uint32_t wbits = warp_block_bits<BW>(w);
-  bool inside = px < W && py < H;
-  uint2 rg = ranges[(int64_t)u * n_tiles + tile];
-  int L = (int)(rg.y - rg.x);
-  int cbeg = ch * K, cend = min(cbeg + K, L);
-  int64_t plane = (int64_t)W * H;
-  int64_t pix = (int64_t)py * W + px;
-  float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, S0 = bg0, S1 = bg1, S2 = bg2;
-  int last = 0;
-  if (inside) {
-    last = (int)n_contrib[(int64_t)u * plane + pix];
-    const float* d = dimg + (int64_t)u * 3 * plane;
-    g0 = d[pix]; g1 = d[plane + pix]; g2 = d[2 * plane + pix];
-    if (ch + 1 < nch && last > cbeg) {
-      // the forward's checkpoint at the chunk's end: T there and the colour behind it per unit T
-      int pix_local = (py - ty * TILE) * TILE + (px - tx * TILE);
-      float4 cp = ckpt[((int64_t)job_base[o] - o + ch) * TILE_PIX + pix_local];
-      T = cp.x;
-      S0 = cp.y; S1 = cp.z; S2 = cp.w;
-    } else {
-      T = final_T[(int64_t)u * plane + pix];
-    }
-  }
-  // entries this warp replays: [cbeg, min(cend, max over its pixels of last))
-  int n = min(__reduce_max_sync(FULL, last), cend);
-  Rec* my = &s_rec[0];
-  int q = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-  bool h1 = false;
-  uint32_t p1 = 0;
-  float2 m1 = make_float2(0.f, 0.f);
-  float4 co1 = make_float4(0.f, 0.f, 0.f, 0.f), cc1 = co1;
-  uint32_t mk2 = 0, pk2 = 0;
-  {
-    int k = n - 32 + lane;
-    if (n > cbeg && k >= cbeg) {
-      uint32_t mk = masks[rg.x + k];
-      if (mk & wbits) {
-        p1 = vals[rg.x + k];
-        h1 = true; m1 = xy[p1]; co1 = conic_op[p1]; cc1 = rgb[p1];
+  // the resident warps take the (chunk job, pixel block) units from a ticket counter (zeroed before
+  // the launch), the next ticket fetched while a unit runs: no block of a grid sized for the capacity
+  // sits idle, and units of very different cost still spread as they finish
+  const uint32_t total = job_base[NT] * 8u;
+  auto job = [&](uint32_t vb) {
+    uint32_t jid = vb >> 3;
+    int w = (int)(vb & 7u);
+    int o = (int)jobs[2 * (int64_t)jid], ch = (int)jobs[2 * (int64_t)jid + 1];
+    uint32_t f = order[o];
+    int u = (int)(f / (uint32_t)n_tiles), tile = (int)(f % (uint32_t)n_tiles);
+    int nch = (int)(job_base[o + 1] - job_base[o]);
+    int tx = tile % TX, ty = tile / TX;
+    constexpr int BH = 32 / BW, NWX = TILE / BW;
+    int lane = threadIdx.x & 31;
+    int px = tx * TILE + (w % NWX) * BW + (lane % BW), py = ty * TILE + (w / NWX) * BH + (lane / BW);
+    uint32_t wbits = warp_block_bits<BW>(w);
+    bool inside = px < W && py < H;
+    uint2 rg = ranges[(int64_t)u * n_tiles + tile];
+    int L = (int)(rg.y - rg.x);
+    int cbeg = ch * K, cend = min(cbeg + K, L);
+    int64_t plane = (int64_t)W * H;
+    int64_t pix = (int64_t)py * W + px;
+    float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, S0 = bg0, S1 = bg1, S2 = bg2;
+    int last = 0;
+    if (inside) {
+      last = (int)n_contrib[(int64_t)u * plane + pix];
+      const float* d = dimg + (int64_t)u * 3 * plane;
+      g0 = d[pix]; g1 = d[plane + pix]; g2 = d[2 * plane + pix];
+      if (ch + 1 < nch && last > cbeg) {
+        // the forward's checkpoint at the chunk's end: T there and the colour behind it per unit T
+        int pix_local = (py - ty * TILE) * TILE + (px - tx * TILE);
+        float4 cp = ckpt[((int64_t)job_base[o] - o + ch) * TILE_PIX + pix_local];
+        T = cp.x;
+        S0 = cp.y; S1 = cp.z; S2 = cp.w;
+      } else {
+        T = final_T[(int64_t)u * plane + pix];
       }
     }
-    int k2 = n - 64 + lane;
-    if (n - 32 > cbeg && k2 >= cbeg) { mk2 = masks[rg.x + k2]; pk2 = vals[rg.x + k2]; }
-  }
-  // QUEUE: pairs of hits with at most DIRECT_LANES contributing lanes go to a ring of
-  // (dx, dy, dp, dopacity | A, B, C, id | dr, dg, db) entries; every 32 entries all
-  // lanes finish one pair each (conic and position terms, vector atomics).  The
-  // per-pixel state (T, colour behind) is still updated at the hit in list order.
-  __shared__ float4 s_q[QUEUE ? 3 * QCAP : 1];
-  int qh = 0, qt = 0;  // ring head and tail (warp-uniform)
-  for (int top = n; top > cbeg; top -= 32) {
-    int base = top - 32;
-    bool hit = h1;
-    uint32_t p = p1;
-    float2 m = m1;
-    float4 co = co1, c = cc1;
-    h1 = (mk2 & wbits) != 0;
-    if (h1) { p1 = pk2; m1 = xy[pk2]; co1 = conic_op[pk2]; cc1 = rgb[pk2]; }
-    int k2 = top - 96 + lane;
-    mk2 = 0;
-    if (top - 64 > cbeg && k2 >= cbeg) { mk2 = masks[rg.x + k2]; pk2 = vals[rg.x + k2]; }
-    unsigned mask = __ballot_sync(FULL, hit);
-    if (hit) {
-      my[lane].a = make_float4(m.x, m.y, co.x, co.y);
-      my[lane].b = make_float4(co.z, co.w, c.w, __uint_as_float(p));
-      my[lane].c = c;
+    // entries this warp replays: [cbeg, min(cend, max over its pixels of last))
+    int n = min(__reduce_max_sync(FULL, last), cend);
+    Rec* my = &s_rec[0];
+    int q = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    bool h1 = false;
+    uint32_t p1 = 0;
+    float2 m1 = make_float2(0.f, 0.f);
+    float4 co1 = make_float4(0.f, 0.f, 0.f, 0.f), cc1 = co1;
+    uint32_t mk2 = 0, pk2 = 0;
+    {
+      int k = n - 32 + lane;
+      if (n > cbeg && k >= cbeg) {
+        uint32_t mk = masks[rg.x + k];
+        if (mk & wbits) {
+          p1 = vals[rg.x + k];
+          h1 = true; m1 = xy[p1]; co1 = conic_op[p1]; cc1 = rgb[p1];
+        }
+      }
+      int k2 = n - 64 + lane;
+      if (n - 32 > cbeg && k2 >= cbeg) { mk2 = masks[rg.x + k2]; pk2 = vals[rg.x + k2]; }
     }
-    __syncwarp();
-    while (mask) {
-      int j = 31 - __clz(mask);
-      mask &= ~(1u << j);
-      int pos = base + j;
-      bool contrib = false;
-      float dx = 0.f, dy = 0.f, dp = 0.f, v5 = 0.f, v6 = 0.f, v7 = 0.f, v8 = 0.f;
-      float4 ra = my[j].a, rb = my[j].b;
-      if (pos < last) {
-        dx = ra.x - fx_of(px); dy = ra.y - fy_of(py);
-        float power = splat_power(ra.z, ra.w, rb.x, dx, dy);
-        if (power <= 0.f && power >= rb.z) {
-          float G = __expf(power);
-          float araw = rb.y * G;
-          bool clamped = araw > ALPHA_MAX;
-          float alpha = clamped ? ALPHA_MAX : araw;
-          if (alpha >= ALPHA_MIN) {
-            contrib = true;
-            float4 rc = my[j].c;
-            T = __fdividef(T, 1.f - alpha);
-            float wgt = alpha * T;
-            v6 = wgt * g0; v7 = wgt * g1; v8 = wgt * g2;
-            float dalpha = T * ((rc.x - S0) * g0 + (rc.y - S1) * g1 + (rc.z - S2) * g2);
-            S0 = alpha * rc.x + (1.f - alpha) * S0;
-            S1 = alpha * rc.y + (1.f - alpha) * S1;
-            S2 = alpha * rc.z + (1.f - alpha) * S2;
-            if (!clamped) {  // a clamped alpha passes no gradient to opacity, conic or position
-              v5 = G * dalpha;
-              dp = araw * dalpha;
+    // QUEUE: pairs of hits with at most DIRECT_LANES contributing lanes go to a ring of
+    // (dx, dy, dp, dopacity | A, B, C, id | dr, dg, db) entries; every 32 entries all
+    // lanes finish one pair each (conic and position terms, vector atomics).  The
+    // per-pixel state (T, colour behind) is still updated at the hit in list order.
+    __shared__ float4 s_q[QUEUE ? 3 * QCAP : 1];
+    int qh = 0, qt = 0;  // ring head and tail (warp-uniform)
+    for (int top = n; top > cbeg; top -= 32) {
+      int base = top - 32;
+      bool hit = h1;
+      uint32_t p = p1;
+      float2 m = m1;
+      float4 co = co1, c = cc1;
+      h1 = (mk2 & wbits) != 0;
+      if (h1) { p1 = pk2; m1 = xy[pk2]; co1 = conic_op[pk2]; cc1 = rgb[pk2]; }
+      int k2 = top - 96 + lane;
+      mk2 = 0;
+      if (top - 64 > cbeg && k2 >= cbeg) { mk2 = masks[rg.x + k2]; pk2 = vals[rg.x + k2]; }
+      unsigned mask = __ballot_sync(FULL, hit);
+      if (hit) {
+        my[lane].a = make_float4(m.x, m.y, co.x, co.y);
+        my[lane].b = make_float4(co.z, co.w, c.w, __uint_as_float(p));
+        my[lane].c = c;
+      }
+      __syncwarp();
+      while (mask) {
+        int j = 31 - __clz(mask);
+        mask &= ~(1u << j);
+        int pos = base + j;
+        bool contrib = false;
+        float dx = 0.f, dy = 0.f, dp = 0.f, v5 = 0.f, v6 = 0.f, v7 = 0.f, v8 = 0.f;
+        float4 ra = my[j].a, rb = my[j].b;
+        if (pos < last) {
+          dx = ra.x - fx_of(px); dy = ra.y - fy_of(py);
+          float power = splat_power(ra.z, ra.w, rb.x, dx, dy);
+          if (power <= 0.f && power >= rb.z) {
+            float G = __expf(power);
+            float araw = rb.y * G;
+            bool clamped = araw > ALPHA_MAX;
+            float alpha = clamped ? ALPHA_MAX : araw;
+            if (alpha >= ALPHA_MIN) {
+              contrib = true;
+              float4 rc = my[j].c;
+              T = __fdividef(T, 1.f - alpha);
+              float wgt = alpha * T;
+              v6 = wgt * g0; v7 = wgt * g1; v8 = wgt * g2;
+              float dalpha = T * ((rc.x - S0) * g0 + (rc.y - S1) * g1 + (rc.z - S2) * g2);
+              S0 = alpha * rc.x + (1.f - alpha) * S0;
+              S1 = alpha * rc.y + (1.f - alpha) * S1;
+              S2 = alpha * rc.z + (1.f - alpha) * S2;
+              if (!clamped) {  // a clamped alpha passes no gradient to opacity, conic or position
+                v5 = G * dalpha;
+                dp = araw * dalpha;
+              }
             }
           }
         }
-      }
-      unsigned cm = __ballot_sync(FULL, contrib);
-      if (!cm) continue;
-      int nc = __popc(cm);
-      if (QUEUE && nc <= DIRECT_LANES) {
-        if (contrib) {
-          int e = (qt + __popc(cm & ((1u << lane) - 1u))) & (QCAP - 1);
-          s_q[e] = make_float4(dx, dy, dp, v5);
-          s_q[QCAP + e] = make_float4(ra.z, ra.w, rb.x, rb.w);
-          s_q[2 * QCAP + e] = make_float4(v6, v7, v8, 0.f);
+        unsigned cm = __ballot_sync(FULL, contrib);
+        if (!cm) continue;
+        int nc = __popc(cm);
+        if (QUEUE && nc <= DIRECT_LANES) {
+          if (contrib) {
+            int e = (qt + __popc(cm & ((1u << lane) - 1u))) & (QCAP - 1);
+            s_q[e] = make_float4(dx, dy, dp, v5);
+            s_q[QCAP + e] = make_float4(ra.z, ra.w, rb.x, rb.w);
+            s_q[2 * QCAP + e] = make_float4(v6, v7, v8, 0.f);
+          }
+          qt += nc;
+          if (qt - qh >= 32) {
+            __syncwarp();
+            bwd_queue_flush(s_q, qh, 32, lane, dxy, dco, drgb);
+            qh += 32;
+            __syncwarp();
+          }
+          continue;
         }
-        qt += nc;
-        if (qt - qh >= 32) {
-          __syncwarp();
-          bwd_queue_flush(s_q, qh, 32, lane, dxy, dco, drgb);
-          qh += 32;
-          __syncwarp();
-        }
-        continue;
-      }
-      int64_t pr = (int64_t)__float_as_uint(rb.w);
-      float v[9];
-      pos_conic_terms(dx, dy, dp, ra.z, ra.w, rb.x, v);
-      v[5] = v5; v[6] = v6; v[7] = v7; v[8] = v8;
-      // fixed point: nine scalar int64 atomics per lane, so reduce unless one lane contributes
-      if (nc <= (fixed ? 1 : DIRECT_LANES)) {
-        // few contributing lanes (small splats): each issues its own three vector
-        // atomics, which costs fewer instructions and atomic operations than a reduction
-        if (contrib) add_lane(dxy, dco, drgb, fixed, pr, v);
-      } else {
-        float tot = reduce8(v, lane);
-        float e8 = v[8];
-        #pragma unroll
-        for (int oo = 16; oo > 0; oo >>= 1) e8 += __shfl_xor_sync(FULL, e8, oo);
-        if ((lane & 3) == 0) {
-          add_one(dxy, dco, drgb, fixed, pr, q, tot);
-        } else if (lane == 1) {
-          add_one(dxy, dco, drgb, fixed, pr, 8, e8);
+        int64_t pr = (int64_t)__float_as_uint(rb.w);
+        float v[9];
+        pos_conic_terms(dx, dy, dp, ra.z, ra.w, rb.x, v);
+        v[5] = v5; v[6] = v6; v[7] = v7; v[8] = v8;
+        // fixed point: nine scalar int64 atomics per lane, so reduce unless one lane contributes
+        if (nc <= (fixed ? 1 : DIRECT_LANES)) {
+          // few contributing lanes (small splats): each issues its own three vector
+          // atomics, which costs fewer instructions and atomic operations than a reduction
+          if (contrib) add_lane(dxy, dco, drgb, fixed, pr, v);
+        } else {
+          float tot = reduce8(v, lane);
+          float e8 = v[8];
+          #pragma unroll
+          for (int oo = 16; oo > 0; oo >>= 1) e8 += __shfl_xor_sync(FULL, e8, oo);
+          if ((lane & 3) == 0) {
+            add_one(dxy, dco, drgb, fixed, pr, q, tot);
+          } else if (lane == 1) {
+            add_one(dxy, dco, drgb, fixed, pr, 8, e8);
+          }
         }
       }
+      __syncwarp();
     }
-    __syncwarp();
+    if (QUEUE && qt > qh) bwd_queue_flush(s_q, qh, qt - qh, lane, dxy, dco, drgb);
+  };
+  const bool lead = (threadIdx.x & 31) == 0;
+  uint32_t vb = __shfl_sync(0xffffffffu, lead ? atomicAdd(ticket, 1u) : 0u, 0);
+  while (vb < total) {
+    uint32_t nxt = lead ? atomicAdd(ticket, 1u) : 0u;
+    job(vb);
+    vb = __shfl_sync(0xffffffffu, nxt, 0);
   }
-  if (QUEUE && qt > qh) bwd_queue_flush(s_q, qh, qt - qh, lane, dxy, dco, drgb);
 }
 
 // Tile order: heaviest lists first (counting sort of (unit, tile) by the
@@ -1162,6 +1188,25 @@ __global__ void k_fixed_to_grad2d(const unsigned long long* __restrict__ fixed, 
   reinterpret_cast<float4*>(drgb)[p] = make_float4(g[6], g[7], g[8], 0.f);
 }
 
+// Grid of a one-warp kernel whose blocks take units of work from a ticket counter: as many blocks as
+// stay resident on the device, at most one per unit.
+template <typename K>
+unsigned resident_grid(K kernel, int64_t units) {
+  int dev = 0, sms = 0, per = 0;
+  if (units < 1) return 1u;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 32, 0) != cudaSuccess || sms < 1 || per < 1)
+    return (unsigned)units;
+  int64_t g = (int64_t)sms * per;
+  return (unsigned)(g < units ? g : units);
+}
+
+// The ticket word of the scheduled blend kernels: the jobs array's last entry, which no job uses
+// (a list of L entries has ceil(L / K) < L / K + 1 jobs, so there are fewer than max_jobs - 1).
+inline uint32_t* sched_ticket(const gs_schedule* sched) {
+  return sched->jobs + 2 * (sched->max_jobs - 1);
+}
+
 }  // namespace
 
 int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
@@ -1180,16 +1225,16 @@ int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const u
         sched->chunk_last, sorted_vals, sched->block_masks, (const float2*)proj->xy, (const float4*)proj->conic_op,                    \
         (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib);        \
   } else if (sched) {                                                                                               \
-    dim3 gj((unsigned)(sched->max_jobs * 8));                                                                       \
-    k_render_fwd_m<BW><<<gj, 32, 0, s>>>(                                                                           \
+    if (cudaMemsetAsync(sched_ticket(sched), 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;          \
+    k_render_fwd_m<BW><<<dim3(resident_grid(k_render_fwd_m<BW>, sched->max_jobs * 8)), 32, 0, s>>>(                 \
         (const uint2*)ranges, sched->tile_order, sched->job_base, sched->jobs, sched->chunk, (int)grid.x,            \
         (float4*)sched->checkpoints, sched->chunk_last, sorted_vals, sched->block_masks, (const float2*)proj->xy,   \
         (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2],  \
-        img, final_T, n_contrib);                                                                                   \
+        img, final_T, n_contrib, sched_ticket(sched));                                                              \
     k_render_fwd_combine<BW><<<dim3(grid.x * 8), 32, 0, s>>>(                                                       \
         (const uint2*)ranges, sched->tile_order, sched->job_base, sched->chunk, (float4*)sched->checkpoints,        \
         sched->chunk_last, width, height, TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib);              \
-    k_render_fwd_stop<BW><<<gj, 32, 0, s>>>(                                                                        \
+    k_render_fwd_stop<BW><<<dim3((unsigned)(sched->max_jobs * 8)), 32, 0, s>>>(                                     \
         (const uint2*)ranges, sched->tile_order, sched->job_base, sched->jobs, sched->chunk, (int)grid.x,            \
         (float4*)sched->checkpoints, sched->chunk_last, sorted_vals, sched->block_masks, (const float2*)proj->xy,    \
         (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2],  \
@@ -1231,13 +1276,16 @@ int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const ui
   dim3 grid(TX * TY * n_units);
 #define GS_BWD(BW)                                                                                                   \
   if (sched)                                                                                                         \
-    (fixed ? k_render_bwd_m<BW, false> : k_render_bwd_m<BW, true>)<<<dim3((unsigned)(sched->max_jobs * 8)), 32, 0, \
-                                                                     s>>>(                                           \
-        (const uint2*)ranges, sched->tile_order, sched->job_base, sched->jobs, sched->chunk,                         \
-        (const float4*)sched->checkpoints, sorted_vals, sched->block_masks, (const float2*)proj->xy,                 \
-        (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX, TX * TY, TX * TY * n_units,     \
-        bg[0], bg[1], bg[2],                                                                                         \
-        img, final_T, n_contrib, dL_dimg, g2d->dxy, g2d->dconic_op, g2d->drgb, fixed);                               \
+    {                                                                                                              \
+      if (cudaMemsetAsync(sched_ticket(sched), 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;        \
+      auto kb = fixed ? k_render_bwd_m<BW, false> : k_render_bwd_m<BW, true>;                                      \
+      kb<<<dim3(resident_grid(kb, sched->max_jobs * 8)), 32, 0, s>>>(                                               \
+          (const uint2*)ranges, sched->tile_order, sched->job_base, sched->jobs, sched->chunk,                       \
+          (const float4*)sched->checkpoints, sorted_vals, sched->block_masks, (const float2*)proj->xy,               \
+          (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX, TX * TY, TX * TY * n_units,   \
+          bg[0], bg[1], bg[2],                                                                                       \
+          img, final_T, n_contrib, dL_dimg, g2d->dxy, g2d->dconic_op, g2d->drgb, fixed, sched_ticket(sched));        \
+    }                                                                                                              \
   else                                                                                                               \
     k_render_bwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, nullptr, sorted_vals, (const float2*)proj->xy, \
                                                (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height,  \

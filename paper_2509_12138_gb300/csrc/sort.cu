@@ -218,29 +218,32 @@ __global__ void __launch_bounds__(RS_T) k_radix_hist(const uint64_t* __restrict_
   constexpr int BINS = 1 << BITS;
   __shared__ uint32_t s_h[RS_T / 32][BINS];
   int64_t I = *d_count;
-  int64_t base = (int64_t)blockIdx.x * RS_TILE;
-  if (base >= I) return;
   const uint64_t* keys = cur[pass] ? k1 : k0;
   int w = threadIdx.x >> 5;
-  for (int k = threadIdx.x; k < (RS_T / 32) * BINS; k += RS_T) (&s_h[0][0])[k] = 0u;
-  // every load of the block's keys in flight at once, then the counting
-  uint32_t dg[RS_ITEMS];
-  #pragma unroll
-  for (int j = 0; j < RS_ITEMS; ++j) {
-    int64_t k = base + (int64_t)j * RS_T + threadIdx.x;
-    dg[j] = k < I ? ((uint32_t)(keys[k] >> shift) & (BINS - 1u)) : 0xffffffffu;
-  }
-  __syncthreads();
-  #pragma unroll
-  for (int j = 0; j < RS_ITEMS; ++j)
-    if (dg[j] != 0xffffffffu) atomicAdd(&s_h[w][dg[j]], 1u);
-  __syncthreads();
-  for (int d = threadIdx.x; d < BINS; d += RS_T) {
-    uint32_t s = 0;
+  // the grid holds as many blocks as stay resident; they take the 4096-key tiles in turn
+  for (int64_t t = blockIdx.x; t * RS_TILE < I; t += gridDim.x) {
+    int64_t base = t * RS_TILE;
+    for (int k = threadIdx.x; k < (RS_T / 32) * BINS; k += RS_T) (&s_h[0][0])[k] = 0u;
+    // every load of the tile's keys in flight at once, then the counting
+    uint32_t dg[RS_ITEMS];
     #pragma unroll
-    for (int q = 0; q < RS_T / 32; ++q) s += s_h[q][d];
-    hist[(int64_t)d * stride + blockIdx.x] = s;
-    if (s) atomicAdd(&totals[pass * RS_BINS_MAX + d], s);
+    for (int j = 0; j < RS_ITEMS; ++j) {
+      int64_t k = base + (int64_t)j * RS_T + threadIdx.x;
+      dg[j] = k < I ? ((uint32_t)(keys[k] >> shift) & (BINS - 1u)) : 0xffffffffu;
+    }
+    __syncthreads();
+    #pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j)
+      if (dg[j] != 0xffffffffu) atomicAdd(&s_h[w][dg[j]], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < BINS; d += RS_T) {
+      uint32_t c = 0;
+      #pragma unroll
+      for (int q = 0; q < RS_T / 32; ++q) c += s_h[q][d];
+      hist[(int64_t)d * stride + t] = c;
+      if (c) atomicAdd(&totals[pass * RS_BINS_MAX + d], c);
+    }
+    __syncthreads();
   }
 }
 
@@ -306,8 +309,6 @@ __global__ void __launch_bounds__(RS_T, 2) k_radix_scatter(uint64_t* __restrict_
   uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);
   uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(uint64_t) * RS_TILE);
   int64_t I = *d_count;
-  int64_t base = (int64_t)blockIdx.x * RS_TILE;
-  if (base >= I) return;
   int c = cur[pass];
   if (cur[pass + 1] == c) return;  // skipped pass
   const uint64_t* kin = c ? k1 : k0;
@@ -315,100 +316,105 @@ __global__ void __launch_bounds__(RS_T, 2) k_radix_scatter(uint64_t* __restrict_
   uint64_t* kout = c ? k0 : k1;
   uint32_t* vout = c ? v0 : v1;
   int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  #pragma unroll
-  for (int e = 0; e < DPT; ++e) {
-    int dd = tid + e * RS_T;
-    s_off[dd] = hist[(int64_t)dd * stride + blockIdx.x];
-    #pragma unroll
-    for (int q = 0; q < NW; ++q) s_wc[q][dd] = 0u;
-  }
-  uint32_t lt = (1u << lane) - 1u;
-  uint64_t key[RS_ITEMS];
-  uint32_t val[RS_ITEMS];
-  uint32_t rnk[RS_ITEMS / 2];  // ranks within the digit among this warp's keys, two 16-bit ranks a word
-  int64_t wk = base + (int64_t)w * WKEYS + lane;  // this lane's key of round 0
-  int64_t rem64 = I - wk;
-  int rem = rem64 > RS_TILE ? RS_TILE : (int)rem64;  // round j holds a key iff 32 j < rem
-  const uint64_t* kp = kin + wk;
-  const uint32_t* vp = vin + wk;
-  #pragma unroll
-  for (int j = 0; j < RS_ITEMS; ++j) {
-    bool valid = j * 32 < rem;
-    key[j] = valid ? kp[j * 32] : 0ull;
-    val[j] = valid ? vp[j * 32] : 0u;
-  }
-  __syncthreads();
-  #pragma unroll
-  for (int j = 0; j < RS_ITEMS; ++j) {
-    bool valid = j * 32 < rem;
-    uint32_t d = valid ? ((uint32_t)(key[j] >> shift) & (BINS - 1u)) : (uint32_t)BINS;
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
-    uint32_t before = valid ? s_wc[w][d] : 0u;
-    uint32_t r = before + __popc(peers & lt);  // < WKEYS: fits 16 bits
-    if (j & 1) rnk[j >> 1] |= r << 16; else rnk[j >> 1] = r;
-    __syncwarp();
-    if (valid && (peers & lt) == 0u) s_wc[w][d] = before + __popc(peers);  // lowest lane of the group
-    __syncwarp();
-  }
-  __syncthreads();
-  // per digit: exclusive scan of the warp counts (warp order = key order); thread tid
-  // owns digits tid * DPT .. tid * DPT + DPT - 1, then a block scan gives digit starts
-  {
-    uint32_t cnts[DPT];
-    uint32_t cnt = 0;
+  // the grid holds as many blocks as stay resident; they take the 4096-key tiles in turn
+  for (int64_t t = blockIdx.x; t * RS_TILE < I; t += gridDim.x) {
+    int64_t base = t * RS_TILE;
     #pragma unroll
     for (int e = 0; e < DPT; ++e) {
-      int dd = tid * DPT + e;
-      uint32_t acc = 0;
+      int dd = tid + e * RS_T;
+      s_off[dd] = hist[(int64_t)dd * stride + t];
       #pragma unroll
-      for (int q = 0; q < NW; ++q) {
-        uint32_t cq = s_wc[q][dd];
-        s_wc[q][dd] = acc;
-        acc += cq;
-      }
-      cnts[e] = acc;
-      cnt += acc;
+      for (int q = 0; q < NW; ++q) s_wc[q][dd] = 0u;
     }
-    uint32_t inc = cnt;
+    uint32_t lt = (1u << lane) - 1u;
+    uint64_t key[RS_ITEMS];
+    uint32_t val[RS_ITEMS];
+    uint32_t rnk[RS_ITEMS / 2];  // ranks within the digit among this warp's keys, two 16-bit ranks a word
+    int64_t wk = base + (int64_t)w * WKEYS + lane;  // this lane's key of round 0
+    int64_t rem64 = I - wk;
+    int rem = rem64 > RS_TILE ? RS_TILE : (int)rem64;  // round j holds a key iff 32 j < rem
+    const uint64_t* kp = kin + wk;
+    const uint32_t* vp = vin + wk;
     #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t nb = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += nb;
+    for (int j = 0; j < RS_ITEMS; ++j) {
+      bool valid = j * 32 < rem;
+      key[j] = valid ? kp[j * 32] : 0ull;
+      val[j] = valid ? vp[j * 32] : 0u;
     }
-    if (lane == 31) s_warp[w] = inc;
     __syncthreads();
-    if (w == 0) {
-      uint32_t x = lane < NW ? s_warp[lane] : 0u, xi = x;
+    #pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j) {
+      bool valid = j * 32 < rem;
+      uint32_t d = valid ? ((uint32_t)(key[j] >> shift) & (BINS - 1u)) : (uint32_t)BINS;
+      uint32_t peers = __match_any_sync(0xffffffffu, d);
+      uint32_t before = valid ? s_wc[w][d] : 0u;
+      uint32_t r = before + __popc(peers & lt);  // < WKEYS: fits 16 bits
+      if (j & 1) rnk[j >> 1] |= r << 16; else rnk[j >> 1] = r;
+      __syncwarp();
+      if (valid && (peers & lt) == 0u) s_wc[w][d] = before + __popc(peers);  // lowest lane of the group
+      __syncwarp();
+    }
+    __syncthreads();
+    // per digit: exclusive scan of the warp counts (warp order = key order); thread tid
+    // owns digits tid * DPT .. tid * DPT + DPT - 1, then a block scan gives digit starts
+    {
+      uint32_t cnts[DPT];
+      uint32_t cnt = 0;
+      #pragma unroll
+      for (int e = 0; e < DPT; ++e) {
+        int dd = tid * DPT + e;
+        uint32_t acc = 0;
+        #pragma unroll
+        for (int q = 0; q < NW; ++q) {
+          uint32_t cq = s_wc[q][dd];
+          s_wc[q][dd] = acc;
+          acc += cq;
+        }
+        cnts[e] = acc;
+        cnt += acc;
+      }
+      uint32_t inc = cnt;
       #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        uint32_t nb = __shfl_up_sync(0xffffffffu, xi, o);
-        if (lane >= o) xi += nb;
+        uint32_t nb = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += nb;
       }
-      if (lane < NW) s_warp[lane] = xi - x;
+      if (lane == 31) s_warp[w] = inc;
+      __syncthreads();
+      if (w == 0) {
+        uint32_t x = lane < NW ? s_warp[lane] : 0u, xi = x;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          uint32_t nb = __shfl_up_sync(0xffffffffu, xi, o);
+          if (lane >= o) xi += nb;
+        }
+        if (lane < NW) s_warp[lane] = xi - x;
+      }
+      __syncthreads();
+      uint32_t st = inc - cnt + s_warp[w];
+      #pragma unroll
+      for (int e = 0; e < DPT; ++e) { s_lstart[tid * DPT + e] = st; st += cnts[e]; }
     }
     __syncthreads();
-    uint32_t st = inc - cnt + s_warp[w];
     #pragma unroll
-    for (int e = 0; e < DPT; ++e) { s_lstart[tid * DPT + e] = st; st += cnts[e]; }
-  }
-  __syncthreads();
-  #pragma unroll
-  for (int j = 0; j < RS_ITEMS; ++j) {
-    if (j * 32 >= rem) continue;
-    uint32_t d = (uint32_t)(key[j] >> shift) & (BINS - 1u);
-    uint32_t r = (j & 1) ? (rnk[j >> 1] >> 16) : (rnk[j >> 1] & 0xffffu);
-    uint32_t pos = s_lstart[d] + s_wc[w][d] + r;
-    s_keys[pos] = key[j];
-    s_vals[pos] = val[j];
-  }
-  __syncthreads();
-  int n_here = (int)min((int64_t)RS_TILE, I - base);
-  for (int i = tid; i < n_here; i += RS_T) {
-    uint64_t kk = s_keys[i];
-    uint32_t d = (uint32_t)(kk >> shift) & (BINS - 1u);
-    uint32_t gp = s_off[d] + (uint32_t)i - s_lstart[d];
-    kout[gp] = kk;
-    vout[gp] = s_vals[i];
+    for (int j = 0; j < RS_ITEMS; ++j) {
+      if (j * 32 >= rem) continue;
+      uint32_t d = (uint32_t)(key[j] >> shift) & (BINS - 1u);
+      uint32_t r = (j & 1) ? (rnk[j >> 1] >> 16) : (rnk[j >> 1] & 0xffffu);
+      uint32_t pos = s_lstart[d] + s_wc[w][d] + r;
+      s_keys[pos] = key[j];
+      s_vals[pos] = val[j];
+    }
+    __syncthreads();
+    int n_here = (int)min((int64_t)RS_TILE, I - base);
+    for (int i = tid; i < n_here; i += RS_T) {
+      uint64_t kk = s_keys[i];
+      uint32_t d = (uint32_t)(kk >> shift) & (BINS - 1u);
+      uint32_t gp = s_off[d] + (uint32_t)i - s_lstart[d];
+      kout[gp] = kk;
+      vout[gp] = s_vals[i];
+    }
+    __syncthreads();  // the tile's shared-memory staging is read out before the next tile reuses it
   }
 }
 
@@ -421,29 +427,29 @@ __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ k0,
                                                 const float4* __restrict__ conic_op, uint16_t* __restrict__ masks,
                                                 int key_masks) {
   int64_t I = *d_count;
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= I) return;
   int c = cur[final_pass];
   const uint64_t* keys = c ? k1 : k0;
   const uint32_t* vals = c ? v1 : v0;
   // unit | tile bits (key bits 32..47 when the block masks ride in bits 48..63)
   uint32_t utm = key_masks ? 0xffffu : 0xffffffffu;
-  uint64_t kk = keys[k];
-  uint32_t ut = (uint32_t)(kk >> 32) & utm;
-  uint32_t p = vals[k];
-  out_vals[k] = p;
-  uint32_t mask = (1u << tile_bits) - 1u;
-  uint32_t tile = ut & mask;
-  int64_t flat = (int64_t)(ut >> tile_bits) * n_tiles + tile;
-  if (k == 0 || ((uint32_t)(keys[k - 1] >> 32) & utm) != ut) ranges[2 * flat] = (uint32_t)k;
-  if (k == I - 1 || ((uint32_t)(keys[k + 1] >> 32) & utm) != ut) ranges[2 * flat + 1] = (uint32_t)(k + 1);
-  if (masks && key_masks) {
-    masks[k] = (uint16_t)(kk >> 48);
-  } else if (masks) {
-    // which 4x4 pixel blocks of its tile the record's alpha >= 1/255 box reaches
-    float pm;
-    float4 b = alpha_box(xy[p], conic_op[p], pm);
-    masks[k] = (uint16_t)block_mask(b, (int)(tile % (uint32_t)TX), (int)(tile / (uint32_t)TX));
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < I; k += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t kk = keys[k];
+    uint32_t ut = (uint32_t)(kk >> 32) & utm;
+    uint32_t p = vals[k];
+    out_vals[k] = p;
+    uint32_t mask = (1u << tile_bits) - 1u;
+    uint32_t tile = ut & mask;
+    int64_t flat = (int64_t)(ut >> tile_bits) * n_tiles + tile;
+    if (k == 0 || ((uint32_t)(keys[k - 1] >> 32) & utm) != ut) ranges[2 * flat] = (uint32_t)k;
+    if (k == I - 1 || ((uint32_t)(keys[k + 1] >> 32) & utm) != ut) ranges[2 * flat + 1] = (uint32_t)(k + 1);
+    if (masks && key_masks) {
+      masks[k] = (uint16_t)(kk >> 48);
+    } else if (masks) {
+      // which 4x4 pixel blocks of its tile the record's alpha >= 1/255 box reaches
+      float pm;
+      float4 b = alpha_box(xy[p], conic_op[p], pm);
+      masks[k] = (uint16_t)block_mask(b, (int)(tile % (uint32_t)TX), (int)(tile / (uint32_t)TX));
+    }
   }
 }
 
@@ -466,6 +472,20 @@ __global__ void k_chunk_jobs(const uint32_t* __restrict__ job_base, int NT, int6
     jobs[2 * (int64_t)j] = (uint32_t)o;
     jobs[2 * (int64_t)j + 1] = j - b;
   }
+}
+
+// As many blocks of `threads` as stay resident on the device, at most `units`: the grid of a kernel
+// whose blocks take equal units of work in turn (a grid sized for the capacity would mostly hold
+// blocks that find nothing to do).
+template <typename K>
+unsigned resident_blocks(K kernel, int threads, size_t dyn_smem, int64_t units) {
+  int dev = 0, sms = 0, per = 0;
+  if (units < 1) return 1u;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, dyn_smem) != cudaSuccess || sms < 1 || per < 1)
+    return (unsigned)units;
+  int64_t g = (int64_t)sms * per;
+  return (unsigned)(g < units ? g : units);
 }
 
 int bits_for(int64_t n) {
@@ -527,7 +547,6 @@ int gs_schedule_check(const gs_schedule* sched, int n_units, int n_tiles, int64_
 int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int height, int64_t max_instances,
                      void* workspace, size_t workspace_bytes, uint32_t* sorted_vals, uint32_t* ranges,
                      uint32_t* d_num_instances, const gs_schedule* sched, int* d_status, cudaStream_t s) {
-  uint32_t* tile_order = sched ? sched->tile_order : nullptr;
   uint16_t* block_masks = sched ? sched->block_masks : nullptr;
   UnitTable U;
   int64_t P = 0;
@@ -587,22 +606,25 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
         cudaFuncSetAttribute(k_radix_scatter<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, SCATTER_DYN_SMEM) !=
             cudaSuccess)
       return GS_ERR_CUDA;
-    unsigned nrb = (unsigned)stride;
+    unsigned gh = digit == 9 ? resident_blocks(k_radix_hist<9>, RS_T, 0, stride)
+                             : resident_blocks(k_radix_hist<8>, RS_T, 0, stride);
+    unsigned gs = digit == 9 ? resident_blocks(k_radix_scatter<9>, RS_T, SCATTER_DYN_SMEM, stride)
+                             : resident_blocks(k_radix_scatter<8>, RS_T, SCATTER_DYN_SMEM, stride);
     for (int pass = 0; pass < passes; ++pass) {
       int shift = digit * pass;
       if (digit == 9) {
-        k_radix_hist<9><<<nrb, RS_T, 0, s>>>(k0, k1, cur, pass, d_num_instances, shift, hist, stride, totals);
+        k_radix_hist<9><<<gh, RS_T, 0, s>>>(k0, k1, cur, pass, d_num_instances, shift, hist, stride, totals);
         k_radix_scan<<<512, 1024, 0, s>>>(hist, stride, totals, pass, 512, d_num_instances, cur);
-        k_radix_scatter<9><<<nrb, RS_T, SCATTER_DYN_SMEM, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift,
-                                                                hist, stride);
+        k_radix_scatter<9><<<gs, RS_T, SCATTER_DYN_SMEM, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift,
+                                                               hist, stride);
       } else {
-        k_radix_hist<8><<<nrb, RS_T, 0, s>>>(k0, k1, cur, pass, d_num_instances, shift, hist, stride, totals);
+        k_radix_hist<8><<<gh, RS_T, 0, s>>>(k0, k1, cur, pass, d_num_instances, shift, hist, stride, totals);
         k_radix_scan<<<256, 1024, 0, s>>>(hist, stride, totals, pass, 256, d_num_instances, cur);
-        k_radix_scatter<8><<<nrb, RS_T, SCATTER_DYN_SMEM, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift,
-                                                                hist, stride);
+        k_radix_scatter<8><<<gs, RS_T, SCATTER_DYN_SMEM, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift,
+                                                               hist, stride);
       }
     }
-    k_ranges<<<(unsigned)((max_instances + 255) / 256), 256, 0, s>>>(
+    k_ranges<<<resident_blocks(k_ranges, 256, 0, (max_instances + 255) / 256), 256, 0, s>>>(
         k0, k1, v0, v1, cur, passes, d_num_instances, tile_bits, n_tiles, TX, ranges, sorted_vals,
         (const float2*)proj->xy, (const float4*)proj->conic_op, block_masks, key_masks);
   }
