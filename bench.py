@@ -403,11 +403,11 @@ BWD_SLOTS_PER_PAIR = 50
 # work counts.  Reported only for that workload and order, scaled by the units of the bench's own timed views.
 TRAFFIC_WORKLOAD = "iso10M-1080p"
 TRAFFIC_PER_UNIT = {
-    "preprocess": ("gaussian", 290.09),
-    "bin_sort": ("instance", 204.85),
-    "render_fwd": ("fwd_pair", 0.2471),
+    "preprocess": ("gaussian", 290.10),
+    "bin_sort": ("instance", 204.90),
+    "render_fwd": ("fwd_pair", 0.2758),
     "loss": ("pixel", 20.02),
-    "blend_bwd": ("bwd_pair", 0.6271),
+    "blend_bwd": ("bwd_pair", 0.8939),
     "project_bwd_adam": ("gaussian", 1477.58),
 }
 
