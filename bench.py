@@ -208,8 +208,8 @@ def cpu_baseline(scene, frac: int):
 
 # ---------------------------------------------------------------- our arm
 def kernel_launch_count(frame, lam):
-    """Kernels libgs launches for one training step (a1-a6) of this frame; matches the ncu launch list
-    of the timed steps (profiles/launches_iso10M-1080p.md)."""
+    """Kernels libgs launches for one training step (a1-a6) of this frame (the kernel launches ncu lists
+    for the timed steps; the two 4-byte memsets of the blend kernels' ticket counter are not kernels)."""
     tile_bits = max(1, math.ceil(math.log2(frame.n_tiles)))
     unit_bits = math.ceil(math.log2(frame.units.n)) if frame.units.n > 1 else 0
     key_bits = 32 + tile_bits + unit_bits
