@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--deterministic", action="store_true",
                     help="accumulate screen-space gradients in fixed point (bitwise reproducible steps)")
+    ap.add_argument("--chunk", type=int, default=1024, help="list entries per chunk job of the blend schedule")
     ap.add_argument("--random-order", action="store_true",
                     help="keep the sampler's random point order instead of the extraction's Z-order")
     ap.add_argument("--cpu-window", type=int, default=8, help="CPU sample: 1/(w*w) of the view's pixels")
@@ -239,7 +240,7 @@ def run_ours(args, wl, rank, world):
     N, W, H = scene.n, scene.width, scene.height
     params = gs.pack_params(scene.init, 3, dev)
     frame = gs.Frame(N, gs.Units.single(N), W, H, 3, device=dev, max_instances=6 * N,
-                     deterministic=args.deterministic)
+                     deterministic=args.deterministic, chunk=args.chunk)
     opt = gs.Adam(params, 3, extent=1.0, lr_steps=7000)
     bg = scene.bg
     V = len(scene.cams)
@@ -493,7 +494,7 @@ def main():
               "views": wl["views"], "sh_degree": 3, "loss": f"masked L1 + {LAMBDA_SSIM} D-SSIM",
               "gradient_accumulation": "int64 fixed point" if args.deterministic else "float atomics",
               "l2": "inputs larger than L2 (params+Adam state 9.6 GB at 10M)",
-              "point_order": "random" if args.random_order else "z-order"}
+              "point_order": "random" if args.random_order else "z-order", "chunk": args.chunk}
     if args.impl == "reference":
         return run_reference(args, wl, rank, world, config)
     if args.experiment == "learned-init":
