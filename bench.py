@@ -276,15 +276,23 @@ def run_ours(args, wl, rank, world):
     tile_len = {"nonempty_tiles": int(nz.numel()), "mean": round(float(nz.mean()), 1) if nz.numel() else 0,
                 "p99": float(torch.quantile(nz, 0.99)) if nz.numel() else 0, "max": int(lens.max())}
 
-    def barrier():
+    watch = None
+    if world > 1:
+        import torch.distributed as dist
+        # host heartbeat between phases: a peer that failed is named before the next phase's kernels launch
+        watch = shard.PeerWatch(dist.distributed_c10d._get_default_store(), rank, world, timeout_s=120.0)
+
+    def barrier(phase=None):
         if world > 1:
-            import torch.distributed as dist
+            if phase is not None:
+                watch.beat(phase)
+                watch.check(phase)
             dist.barrier()
 
     clocks = ClockSampler(device_uuid(dev))
     clocks.start()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(args.steps)]
-    barrier()
+    barrier(1)  # every rank finished its warm-up
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -511,8 +519,9 @@ def main():
         return 1
     torch.cuda.set_device(local)
     if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        from paper_2509_12138_gb300 import shard as _shard
+        # a rank that dies ends the others' next collective after 5 minutes at most instead of a hang
+        _shard.init_group("nccl", timeout_s=300.0, device_id=torch.device("cuda", local))
     import __graft_entry__
     __graft_entry__.build()
     from paper_2509_12138_gb300 import peak

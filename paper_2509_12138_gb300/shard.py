@@ -11,6 +11,9 @@ uses (NCCL on GPUs, gloo on the CPU in the tests).
 """
 from __future__ import annotations
 
+import time
+from datetime import timedelta
+
 import numpy as np
 import torch
 
@@ -79,3 +82,44 @@ def gather_owned(params: torch.Tensor, keep: torch.Tensor, dst: int = 0):
         return torch.cat([b[:, :c] for b, c in zip(bufs, counts)], dim=1)
     dist.gather(pad, dst=dst)
     return None
+
+
+def init_group(backend: str, timeout_s: float = 300.0, **kwargs):
+    """torch.distributed process group whose collectives give up after `timeout_s` seconds: a rank that
+    died or never joins ends the others' next collective with an error instead of a hang."""
+    import torch.distributed as dist
+    dist.init_process_group(backend, timeout=timedelta(seconds=timeout_s), **kwargs)
+
+
+class PeerFailure(RuntimeError):
+    """A peer rank did not report a step within the heartbeat timeout."""
+
+
+class PeerWatch:
+    """Host-side heartbeat between steps through a key-value store (the process group's store, or any
+    torch.distributed Store): after step s every rank sets ``beat/<rank>`` to s; before launching step
+    s + 1 a rank waits up to `timeout_s` for every peer to have reported step s and raises PeerFailure
+    naming the ranks that did not.  Nothing here touches a GPU, so a failed peer is noticed before any
+    kernel of the next step is in flight."""
+
+    def __init__(self, store, rank: int, world: int, timeout_s: float = 5.0, poll_s: float = 0.01):
+        self.store, self.rank, self.world = store, int(rank), int(world)
+        self.timeout_s, self.poll_s = float(timeout_s), float(poll_s)
+
+    def beat(self, step: int):
+        self.store.set(f"beat/{self.rank}", str(int(step)))
+
+    def _step_of(self, r: int) -> int:
+        if not self.store.check([f"beat/{r}"]):
+            return -1
+        return int(self.store.get(f"beat/{r}"))
+
+    def check(self, step: int):
+        deadline = time.monotonic() + self.timeout_s
+        while True:
+            late = [r for r in range(self.world) if r != self.rank and self._step_of(r) < step]
+            if not late:
+                return
+            if time.monotonic() >= deadline:
+                raise PeerFailure(f"ranks {late} did not report step {step} within {self.timeout_s} s")
+            time.sleep(self.poll_s)

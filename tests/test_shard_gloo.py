@@ -5,6 +5,7 @@ the measurement's max-over-ranks timing and whole-job throughput, independent pe
 merge exchange (owned splats of every rank gathered in rank order to the renderer)."""
 import os
 import socket
+import time
 
 import numpy as np
 import pytest
@@ -104,3 +105,52 @@ def test_single_process_paths_need_no_process_group():
     keep = torch.tensor([True, False, True, True])
     assert shard.gather_owned(p, keep).shape == (3, 3, 4)
     assert shard.reduce_max([1.0, 2.0]) == [1.0, 2.0]
+
+
+def _failing_worker(rank, world, port, outdir):
+    """Rank 1 leaves after step 1 (its host loop ends without reporting step 2, as after an exception that
+    its own handler swallowed); rank 0 must learn of it from the heartbeat before its next step, and a
+    collective with the departed rank must end in an error rather than hang."""
+    shard.init_group("gloo", timeout_s=3.0, init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    store = dist.distributed_c10d._get_default_store()
+    watch = shard.PeerWatch(store, rank, world, timeout_s=2.0)
+    for step in (1, 2):
+        if rank == 1 and step == 2:
+            os._exit(0)  # the failure, injected on the host: this rank is gone
+        watch.beat(step)
+        if rank == 0:
+            t0 = time.monotonic()
+            try:
+                watch.check(step)
+                res = "ok"
+            except shard.PeerFailure as e:
+                res = f"failure: {e}"
+            dt = time.monotonic() - t0
+            if step == 2:
+                t1 = time.monotonic()
+                try:
+                    shard.reduce_max([1.0])
+                    coll = "returned"
+                except Exception as e:  # the peer is gone: gloo reports it, or the group times out
+                    coll = f"error: {type(e).__name__}"
+                np.savez(os.path.join(outdir, "fail.npz"), res=res, dt=dt, coll=coll, dt_coll=time.monotonic() - t1)
+                os._exit(0)
+            assert res == "ok", res
+
+
+def test_failed_rank_is_detected_on_the_host_and_collectives_do_not_hang(tmp_path):
+    ctx = mp.start_processes(_failing_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=False,
+                             start_method="spawn")
+    t0 = time.monotonic()
+    while True:
+        if ctx.join(timeout=1):
+            break
+        if all(not p.is_alive() for p in ctx.processes) or time.monotonic() - t0 > 60:
+            break
+    for p in ctx.processes:
+        if p.is_alive():
+            p.kill()
+    r = np.load(tmp_path / "fail.npz")
+    assert str(r["res"]).startswith("failure: ranks [1] did not report step 2")
+    assert 1.5 < float(r["dt"]) < 10.0
+    assert str(r["coll"]).startswith("error") and float(r["dt_coll"]) < 30.0
