@@ -734,7 +734,10 @@ def run_reference(args, wl, rank, world, config):
         print(json.dumps({"impl": "reference", "unavailable": "the scene's GT is rendered on the GPU; no CUDA device"}))
         return 0
     scene = workload.isosurface_scene(wl["n"], wl["modes"], wl["views"], wl["W"], wl["H"], sh_degree=3, seed=0)
-    cs = CpuSample(scene, args.cpu_window)
+    # each step is a bounded sample (~4 s of host work at the default size); long runs take a smaller one so
+    # that the whole run stays within a few minutes (the estimate of a full iteration scales with it)
+    many = args.steps + args.warmup > 20
+    cs = CpuSample(scene, max(args.cpu_window, 12) if many else args.cpu_window, gfrac=250 if many else 100)
     for _ in range(args.warmup):
         cs.step()
     times = [cs.step() for _ in range(args.steps)]
