@@ -1,6 +1,7 @@
 """Pins of the oracle's loss and gradients.
 
-* loss: SSIM(x, x) = 1; closed form on constant images; masked L1 by hand;
+* loss: SSIM(x, x) = 1; closed form on constant images; masked L1 by hand; the masked D-SSIM
+  loss against SSIM statistics filtered by scipy (window, padding and constants of R13);
 * loss gradient: against the dual-number directional derivative and FD;
 * parameter gradient (reverse replay + projection Jacobian): against the
   exact dual-number directional derivative of the whole pipeline, along
@@ -158,3 +159,29 @@ def test_alpha_clamp_gradient_is_zero():
     r = oracle.loss_and_grads(g, cam, np.ones(3), gt, mask, 0.0)
     assert r["g2d"]["dopacity"][0] == 0.0 and np.all(r["g2d"]["dconic"][0] == 0.0)
     assert np.abs(r["g2d"]["drgb"][0]).max() > 0
+
+
+def test_masked_ssim_loss_matches_library_filtered_statistics():
+    """The loss at lambda = 0.2 against SSIM statistics from scipy's Gaussian filter (sigma 1.5, radius 5,
+    zero padding: the 11x11 window of R13), masked means over mask pixels and channels."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(5)
+    H, W = 29, 41
+    x = rng.uniform(0, 1, (3, H, W))
+    y = np.clip(0.7 * x + rng.normal(0, 0.1, (3, H, W)), 0, 1)
+    mask = (rng.uniform(0, 1, (H, W)) > 0.25).astype(np.uint8)
+
+    def g(a):
+        return ndimage.gaussian_filter(a, 1.5, mode="constant", cval=0.0, truncate=5.0 / 1.5)
+
+    C1, C2 = 0.01 ** 2, 0.03 ** 2
+    ssim = []
+    for c in range(3):
+        mx, my = g(x[c]), g(y[c])
+        sxx, syy, sxy = g(x[c] * x[c]) - mx * mx, g(y[c] * y[c]) - my * my, g(x[c] * y[c]) - mx * my
+        ssim.append(((2 * mx * my + C1) * (2 * sxy + C2)) / ((mx * mx + my * my + C1) * (sxx + syy + C2)))
+    m = mask.astype(bool)
+    ssim_mean = np.mean([s[m] for s in ssim])
+    l1 = np.abs(x - y)[:, m].mean()
+    expected = 0.8 * l1 + 0.2 * (1.0 - ssim_mean)
+    assert oracle.loss(x, y, mask, 0.2, grad=False) == pytest.approx(expected, rel=1e-10)
