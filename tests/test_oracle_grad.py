@@ -1,7 +1,7 @@
 """Pins of the oracle's loss and gradients.
 
 * loss: SSIM(x, x) = 1; closed form on constant images; masked L1 by hand; the masked D-SSIM
-  loss against SSIM statistics filtered by scipy (window, padding and constants of R13);
+  loss against SSIM statistics filtered by scipy (11x11 Gaussian window, zero padding, C1, C2);
 * loss gradient: against the dual-number directional derivative and FD;
 * parameter gradient (reverse replay + projection Jacobian): against the
   exact dual-number directional derivative of the whole pipeline, along
@@ -163,7 +163,7 @@ def test_alpha_clamp_gradient_is_zero():
 
 def test_masked_ssim_loss_matches_library_filtered_statistics():
     """The loss at lambda = 0.2 against SSIM statistics from scipy's Gaussian filter (sigma 1.5, radius 5,
-    zero padding: the 11x11 window of R13), masked means over mask pixels and channels."""
+    zero padding: the 11x11 window), C1 = 0.01^2, C2 = 0.03^2, masked means over mask pixels and channels."""
     ndimage = pytest.importorskip("scipy.ndimage")
     rng = np.random.default_rng(5)
     H, W = 29, 41
