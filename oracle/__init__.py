@@ -10,9 +10,9 @@ module only converts numpy arrays.  Each wrapper names the definition it
 follows; the pins that check them are in ``tests/test_oracle_*.py``.
 
 Parity status: every function here is pinned by a closed form, brute force,
-a library routine, finite differences or dual numbers, except the choice of
-Adam learning rates and the loss weighting (readings, not derivable from the
-paper; the optimiser itself is pinned).
+a library routine, finite differences or dual numbers.  Parity unpinned: the
+values of the Adam learning rates and the loss weighting (readings, not
+derivable from the paper; the optimiser and the loss themselves are pinned).
 """
 from __future__ import annotations
 
