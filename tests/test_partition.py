@@ -65,3 +65,20 @@ def test_spatial_order_is_the_z_order():
         for a in range(3):
             code |= ((q[:, a] >> b) & 1) << (3 * b + a)
     assert np.array_equal(o, np.argsort(code, kind="stable"))
+
+
+def test_device_z_order_bits():
+    """The 100M render scene's (x, y) Z-order key: 16-bit quantised coordinates with their bits
+    interleaved (x on even, y on odd positions), checked bit by bit."""
+    import torch
+    from paper_2509_12138_gb300.workload import _spread2
+    v = torch.rand(500, generator=torch.Generator().manual_seed(3))
+    q = (v.double() * 65535.0).round().long()
+    got = _spread2(v)
+    for i in range(len(v)):
+        want = 0
+        for b in range(16):
+            want |= ((int(q[i]) >> b) & 1) << (2 * b)
+        assert int(got[i]) == want
+    key = _spread2(v[:250]) | (_spread2(v[250:]) << 1)
+    assert int(key.max()) < 1 << 32
