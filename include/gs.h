@@ -87,7 +87,12 @@ typedef struct gs_camera {
 
 /* Per (unit, Gaussian) projected records, indexed by projected index. */
 typedef struct gs_proj {
-  float* xy;        /* [P][2]  pixel-space mean                            */
+  float* xy;        /* [P][4]  pixel-space mean as float pairs (x, y, x_lo,
+                     y_lo): u = x + x_lo, v = y + y_lo with |lo| at most half
+                     an ulp of the high part; both parts together carry the
+                     position to ~2^-44 relative (float32 alone would carry
+                     ~6e-5 px at u ~ 10^3, which moves alpha near the 1/255
+                     edge of sub-pixel splats)                             */
   float* conic_op;  /* [P][4]  (A, B, C, opacity), conic = inverse 2D cov  */
   float* rgb;       /* [P][4]  (r, g, b, f) after SH, +0.5 and clamp at 0;
                      f: power below which alpha < 1/255 for certain      */
@@ -231,8 +236,10 @@ int gs_schedule_sizes(int n_units, int width, int height, int64_t max_instances,
  * sorted_vals must hold GS_STATIC_SORT_MAX_INSTANCES entries.  All calls share
  * the array and it keeps the last call's contents (each call clears what must
  * start at zero): calls whose work overlaps on the GPU race.  The first call
- * on a device looks up the array's address with that device current; make it
- * before any stream capture. */
+ * on a device looks up the array's address with that device current, and a
+ * call from a new context of the device (after cudaDeviceReset) looks it up
+ * again; make those calls before any stream capture.  It builds no blend
+ * schedule: the blend calls that read its lists take sched = NULL. */
 #define GS_STATIC_SORT_MAX_RECORDS 131072
 #define GS_STATIC_SORT_MAX_INSTANCES 524288
 #define GS_STATIC_SORT_SCRATCH_BYTES 13631488
@@ -241,7 +248,8 @@ int gs_bin_sort_static(const gs_proj* proj, const gs_units* units, int width, in
                        int* d_status, gs_stream_t stream);
 
 /* ---- a3: front-to-back blend per 16x16 tile -------------------------------
- * For pixel (px, py) over its tile's list in order: d = xy - (px, py),
+ * For pixel (px, py) over its tile's list in order: d = xy - (px, py)
+ * (evaluated as ((x - o) + x_lo) - (px - o) with o the tile's corner),
  * power = -(A dx^2 + C dy^2)/2 - B dx dy, skipped if > 0;
  * alpha = min(0.99, opacity e^power), skipped if < 1/255; if T (1 - alpha) <
  * 1e-4 the entry is not blended and the pixel stops; else C += alpha T rgb,
@@ -328,23 +336,101 @@ int gs_project_bwd(const float* params, int64_t n_gauss, int sh_degree, const gs
  * Learning rates per plane component: lr = lr_init * (lr_final / lr_init)^
  * (min(t, lr_steps) / lr_steps) (log-linear; constant when init == final);
  * lr_init, lr_final: host float[n_planes][4].  If zero_grad, g is set to 0.
- * d_step: device int32, read only (advance it with gs_step_advance). */
+ * d_step: device int32, read only (advance it with gs_step_advance).
+ * A float4 of gradients holding a non-finite value sets GS_ERR_NONFINITE in
+ * d_status (may be NULL) and its four parameters and moments keep their
+ * values. */
 int gs_adam_step(float* params, float* grads, float* m, float* v, int64_t n_gauss, int n_planes,
                  const float* lr_init, const float* lr_final, int32_t lr_steps, float beta1,
-                 float beta2, float eps, const int32_t* d_step, int zero_grad, gs_stream_t stream);
+                 float beta2, float eps, const int32_t* d_step, int zero_grad, int* d_status,
+                 gs_stream_t stream);
 
 /* Projection backward fused with the Adam step (same arithmetic as
  * gs_project_bwd followed by gs_adam_step with zero_grad = 0): each
  * Gaussian's parameter gradient is formed in registers and applied at once.
- * grads may be NULL; otherwise it also receives the gradient. */
+ * grads may be NULL; otherwise it also receives the gradient.  A Gaussian
+ * whose screen-space or parameter gradient holds a non-finite value sets
+ * GS_ERR_NONFINITE in d_status (may be NULL) and keeps its parameters and
+ * moments. */
 int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
                         const gs_camera* cams, const gs_proj* proj, const gs_grad2d* g2d, float* m,
                         float* v, const float* lr_init, const float* lr_final, int32_t lr_steps,
                         float beta1, float beta2, float eps, const int32_t* d_step, float* grads,
-                        gs_stream_t stream);
+                        int* d_status, gs_stream_t stream);
 
 /* *d_step += 1 on the device (keeps CUDA-graph replays advancing). */
 int gs_step_advance(int32_t* d_step, gs_stream_t stream);
+
+/* ---- a7: one batched training step of all (partition, view) units -------
+ * The paper trains every data partition independently on its own views
+ * (Sec. II, "Data Partitioning", "Parallel Training"); here the partitions
+ * and views_per_step views of each are the units of one call.  Unit
+ * u = (partition k = u / views_per_step, slot j = u % views_per_step) trains
+ * partition k's Gaussians (units->gauss_begin / gauss_count) on view
+ *     v = train_views[(t * views_per_step + j + k) mod n_train],  t = *d_step,
+ * i.e. consecutive steps walk the training views and partitions are
+ * staggered by one view.  The call enqueues, on `stream` and without any host
+ * work that depends on t: gs_gather_views (camera, ground truth and mask of
+ * each unit into the step buffers), gs_preprocess, gs_bin_sort,
+ * gs_render_fwd, gs_loss, gs_blend_bwd, gs_project_bwd_adam (Adam step t + 1)
+ * and gs_step_advance.  A CUDA graph that captures one call therefore
+ * replays every later step.  All pointers are caller-owned; "host" marks host
+ * arrays, every other pointer is device memory.  Device errors (capacity,
+ * non-finite values) go to d_status as in the individual calls. */
+typedef struct gs_train_batch_desc {
+  float* params;                 /* [n_planes][n_gauss][4], updated in place */
+  float* adam_m;                 /* Adam moments, same layout */
+  float* adam_v;
+  int64_t n_gauss;
+  int32_t sh_degree;
+  int32_t views_per_step;
+  const gs_units* units;         /* host unit table, n_parts * views_per_step units */
+  const gs_camera* cam_pool;     /* [n_views] cameras of the training set */
+  const float* gt_pool;          /* [n_parts][n_views][3][H][W] each partition's ground truth */
+  const uint8_t* mask_pool;      /* [n_parts][n_views][H][W] its background masks */
+  const int32_t* train_views;    /* [n_train] view ids used for training */
+  int32_t n_views;
+  int32_t n_train;
+  int32_t width;
+  int32_t height;
+  float lambda_ssim;             /* loss weight of 1 - SSIM (gs_loss) */
+  float bg[3];                   /* background colour */
+  const float* lr_init;          /* host [n_planes][4] (gs_adam_step) */
+  const float* lr_final;         /* host [n_planes][4] or NULL */
+  int32_t lr_steps;
+  float beta1;
+  float beta2;
+  float eps;
+  int32_t* d_step;               /* [1] step counter t, advanced by one per call */
+  gs_camera* cams_step;          /* [U] step buffers written by the gather */
+  float* gt_step;                /* [U][3][H][W] */
+  uint8_t* mask_step;            /* [U][H][W] */
+  const gs_proj* proj;           /* host struct of [P] record buffers, P = sum of gauss_count */
+  int64_t max_instances;         /* capacity of sorted_vals and of the sort workspace */
+  void* sort_ws;                 /* gs_bin_sort_workspace_size(P, max_instances) bytes */
+  size_t sort_ws_bytes;
+  uint32_t* sorted_vals;         /* [max_instances] */
+  uint32_t* ranges;              /* [U * n_tiles][2] */
+  uint32_t* d_num_instances;     /* [1] */
+  const gs_schedule* sched;      /* host struct of the blend schedule buffers, or NULL */
+  float* img;                    /* [U][3][H][W] */
+  float* final_T;                /* [U][H][W] */
+  uint32_t* n_contrib;           /* [U][H][W] */
+  void* loss_ws;                 /* gs_loss_workspace_size(U, W, H) bytes */
+  size_t loss_ws_bytes;
+  float* d_loss;                 /* [1] mean loss over the units */
+  float* dL_dimg;                /* [U][3][H][W] */
+  const gs_grad2d* g2d;          /* host struct of [P] screen-space gradient buffers */
+  float* grads;                  /* parameter gradient (planes layout) or NULL */
+  int32_t variant;               /* blend execution shape (gs_render_fwd) */
+} gs_train_batch_desc;
+
+int gs_train_batch(const gs_train_batch_desc* desc, int* d_status, gs_stream_t stream);
+
+/* The gather step alone: the views of step *d_step (same rule) into
+ * cams_step, gt_step and mask_step (16-byte copies when pointers and sizes
+ * allow).  Lets a caller inspect or size a step without training it. */
+int gs_gather_views(const gs_train_batch_desc* desc, const int32_t* d_step, gs_stream_t stream);
 
 /* ---- a8: merged render of all partitions (Sec. II, "Global Reconstruction")
  * The splats of all partitions, concatenated in partition order, are rendered

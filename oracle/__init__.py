@@ -68,7 +68,7 @@ def _declare(L):
     L.orc_set_threads.argtypes = [C.c_int]
     L.orc_sh_basis.argtypes = [C.c_int, C.c_int, _D, _D]
     L.orc_quat_to_rot.argtypes = [C.c_int, _D, _D]
-    L.orc_project.argtypes = [C.c_int, C.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _I, _D, _I, _I, _I, _D]
+    L.orc_project.argtypes = [C.c_int, C.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _I, _D, _I, _I, _I, _D, _I]
     L.orc_bin.argtypes = [C.c_int, _D, _I, _D, C.c_int, C.c_int, C.c_longlong, _I, _I, _I, _I]
     L.orc_bin.restype = C.c_longlong
     L.orc_render.argtypes = [C.c_int, C.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _I, _D, _I, _D, _D]
@@ -176,10 +176,14 @@ def project(g, cam):
     cam = _d(cam)
     out = dict(xy=np.zeros((n, 2)), conic=np.zeros((n, 3)), opacity=np.zeros(n), rgb=np.zeros((n, 3)),
                clamp=np.zeros(n, np.int32), depth=np.zeros(n), radius=np.zeros(n, np.int32),
-               rect=np.zeros((n, 4), np.int32), tiles=np.zeros(n, np.int32), cov2d=np.zeros((n, 3)))
+               rect=np.zeros((n, 4), np.int32), tiles=np.zeros(n, np.int32), cov2d=np.zeros((n, 3)),
+               unstable=np.zeros(n, np.int32))
     lib().orc_project(n, deg, _p(m), _p(ls), _p(q), _p(lo), _p(sh), _p(cam), _p(out["xy"]), _p(out["conic"]),
                       _p(out["opacity"]), _p(out["rgb"]), _p(out["clamp"]), _p(out["depth"]),
-                      _p(out["radius"]), _p(out["rect"]), _p(out["tiles"]), _p(out["cov2d"]))
+                      _p(out["radius"]), _p(out["rect"]), _p(out["tiles"]), _p(out["cov2d"]), _p(out["unstable"]))
+    # depth: the float32 rounding of the FP64 camera-space z (the sort key); unstable: bits 1 (near
+    # cull), 2 (radius), 4 (tile rectangle) of the decisions a float32 evaluation may take the other
+    # way, by the error model stated in gs_oracle.cpp
     return out
 
 

@@ -187,14 +187,24 @@ void quat_to_rot(const S q[4], S R[9]) {
 }
 
 // ---------------------------------------------------------------- projection
-// float32 sort key of a mean: camera-space z by a fixed chain of fused
-// multiply-adds on the (float32) inputs.
-static inline double depth_key(const double* R, const double* t, double x, double y, double z) {
-  float k = std::fma((float)R[8], (float)z, (float)t[2]);
-  k = std::fma((float)R[7], (float)y, k);
-  k = std::fma((float)R[6], (float)x, k);
-  return (double)k;
-}
+// The list order is decided on the depth key: the camera-space z of the mean
+// rounded to float32 (the key is stored as a float32 bit pattern).  Here z is
+// evaluated in FP64 from the (float32-representable) inputs, whose products are
+// exact in FP64, and rounded once.
+static inline double depth_key(double z) { return (double)(float)z; }
+
+// Float32 error model of the discrete decisions (diagnostics only: the FP64
+// decisions are the oracle's results).  A decision is "unstable" when it
+// changes as the continuous quantity it is taken on moves by a bound on the
+// error a float32 evaluation of the same formula can make, u = 2^-24:
+//   z (near cull):  8 u (|r20 x| + |r21 y| + |r22 z| + |t2|)  (four terms, a few roundings each);
+//   pixel u, v:     computed as float pairs (hi + lo, ~2^-44 relative): 2^-40 [ f (s_t / z + |t_x| s_z / z^2)
+//                   + |u| ] with s_t, s_z the sums of the terms' magnitudes of t_x and z;
+//   3 sqrt(lambda): relative 4 u (33 + mid / sqrt(max(0.1, disc))): a, b, c carry absolute errors
+//                   up to ~30 u lambda_max (sums of products of a PSD form, which cancel for thin
+//                   splats seen edge-on), and disc = mid^2 - det loses ~4 u mid^2 to its own roundings;
+//                   half of lambda's relative error reaches the square root; the factor 4 is slack.
+enum { UNSTABLE_CULL = 1, UNSTABLE_RADIUS = 2, UNSTABLE_RECT = 4 };
 
 template <class S>
 struct Proj {
@@ -204,6 +214,7 @@ struct Proj {
   S col[3];      // RGB after the +0.5 offset and the clamp at 0
   S depth;       // float32 sort key (camera-space z), see depth_key
   int radius;    // 0 = culled
+  int unstable;  // UNSTABLE_* bits: decisions a float32 evaluation may take the other way
   int rect[4];
   int tiles;
   int clamp;     // bit c set if channel c was clamped to 0
@@ -218,15 +229,19 @@ template <class S>
 Proj<S> project_one(const S mu[3], const S ls[3], const S q[4], S logit, const S* sh, int deg,
                     const Cam& cam) {
   Proj<S> P;
-  P.radius = 0; P.tiles = 0; P.clamp = 0;
+  P.radius = 0; P.tiles = 0; P.clamp = 0; P.unstable = 0;
   P.rect[0] = P.rect[1] = P.rect[2] = P.rect[3] = 0;
   const double* R = cam.R;
   S t[3];
   for (int i = 0; i < 3; ++i) t[i] = R[3 * i] * mu[0] + R[3 * i + 1] * mu[1] + R[3 * i + 2] * mu[2] + cam.t[i];
-  // The list order is a discrete decision taken on the float32 camera-space z,
-  // evaluated as fma(r20, x, fma(r21, y, fma(r22, z, t2))) on the float32 inputs;
-  // the blend itself uses the FP64 quantities.
-  P.depth = S(depth_key(R, cam.t, val(mu[0]), val(mu[1]), val(mu[2])));
+  P.depth = S(depth_key(val(t[2])));
+  const double U32 = std::ldexp(1.0, -24);
+  double tsum[3];
+  for (int i = 0; i < 3; ++i)
+    tsum[i] = std::fabs(R[3 * i] * val(mu[0])) + std::fabs(R[3 * i + 1] * val(mu[1])) +
+              std::fabs(R[3 * i + 2] * val(mu[2])) + std::fabs(cam.t[i]);
+  double ez = 8.0 * U32 * tsum[2];
+  if (std::fabs(val(t[2]) - cam.znear) <= ez) P.unstable |= UNSTABLE_CULL;
   if (val(t[2]) <= cam.znear) return P;
 
   // Sigma3D = (Rq S)(Rq S)^T
@@ -280,6 +295,28 @@ Proj<S> project_one(const S mu[3], const S ls[3], const S q[4], S logit, const S
   int TX = (cam.W + TILE - 1) / TILE, TY = (cam.H + TILE - 1) / TILE;
   tile_rect(val(P.x), val(P.y), radius, TX, TY, P.rect);
   int tiles = (P.rect[2] - P.rect[0]) * (P.rect[3] - P.rect[1]);
+  {
+    // stability of the radius and of the rectangle (see the error model above)
+    double tz = val(t[2]);
+    double eps_r = 4.0 * U32 * (33.0 + mid / std::sqrt(std::max(LAMBDA_FLOOR, mid * mid - val(det))));
+    double r3 = 3.0 * std::sqrt(lam);
+    int rlo = (int)std::ceil(r3 * (1.0 - eps_r)), rhi = (int)std::ceil(r3 * (1.0 + eps_r));
+    if (rlo != radius || rhi != radius) P.unstable |= UNSTABLE_RADIUS;
+    double f[2] = {cam.fx, cam.fy}, pix[2] = {val(P.x), val(P.y)};
+    double e[2];
+    for (int k = 0; k < 2; ++k) {
+      e[k] = std::ldexp(1.0, -40) * (std::fabs(f[k]) * (tsum[k] / tz + std::fabs(val(t[k])) * tsum[2] / (tz * tz)) +
+                                     std::fabs(pix[k]));
+    }
+    for (int sx = -1; sx <= 1; sx += 2)
+      for (int sy = -1; sy <= 1; sy += 2)
+        for (int rr = rlo; rr <= rhi; ++rr) {
+          int q[4];
+          tile_rect(pix[0] + sx * e[0], pix[1] + sy * e[1], rr, TX, TY, q);
+          if (q[0] != P.rect[0] || q[1] != P.rect[1] || q[2] != P.rect[2] || q[3] != P.rect[3])
+            P.unstable |= UNSTABLE_RECT;
+        }
+  }
   if (radius == 0 || tiles == 0) return P;
   P.radius = radius;
   P.tiles = tiles;
@@ -644,11 +681,12 @@ void orc_quat_to_rot(int n, const double* q, double* R) {
 
 // Per-Gaussian projection for one camera.  Outputs are per Gaussian:
 // xy[2], conic[3] (A, B, C), opacity, rgb[3], clamp bits, depth, radius,
-// rect[4], tiles touched, cov2d[3] (a, b, c before inversion).
+// rect[4], tiles touched, cov2d[3] (a, b, c before inversion), unstable (UNSTABLE_*
+// bits of the float32 error model).
 void orc_project(int n, int deg, const double* means, const double* ls, const double* quats,
                  const double* logit, const double* sh, const double* camv, double* xy, double* conic,
                  double* opacity, double* rgb, int* clampbits, double* depth, int* radius, int* rect,
-                 int* tiles, double* cov2d) {
+                 int* tiles, double* cov2d, int* unstable) {
   Cam cam = load_cam(camv);
   Params p{n, deg, means, ls, quats, logit, sh};
   std::vector<Proj<double>> P;
@@ -665,6 +703,7 @@ void orc_project(int n, int deg, const double* means, const double* ls, const do
     radius[i] = g.radius;
     for (int k = 0; k < 4; ++k) rect[4 * i + k] = vis ? g.rect[k] : 0;
     tiles[i] = g.tiles;
+    if (unstable) unstable[i] = g.unstable;
     if (cov2d) {
       bool has = val(g.depth) > cam.znear;
       cov2d[3 * i] = has ? g.a : 0; cov2d[3 * i + 1] = has ? g.b : 0; cov2d[3 * i + 2] = has ? g.c : 0;

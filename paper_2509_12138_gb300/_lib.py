@@ -53,6 +53,23 @@ class GsDensifyCfg(C.Structure):
                 ("max_screen", C.c_float), ("extent", C.c_float), ("step", C.c_int32), ("reset_interval", C.c_int32)]
 
 
+class GsTrainBatchDesc(C.Structure):
+    """gs_train_batch_desc (include/gs.h), field for field."""
+    _fields_ = [("params", C.c_void_p), ("adam_m", C.c_void_p), ("adam_v", C.c_void_p), ("n_gauss", C.c_int64),
+                ("sh_degree", C.c_int32), ("views_per_step", C.c_int32), ("units", C.POINTER(GsUnits)),
+                ("cam_pool", C.c_void_p), ("gt_pool", C.c_void_p), ("mask_pool", C.c_void_p),
+                ("train_views", C.c_void_p), ("n_views", C.c_int32), ("n_train", C.c_int32), ("width", C.c_int32),
+                ("height", C.c_int32), ("lambda_ssim", C.c_float), ("bg", C.c_float * 3), ("lr_init", c_f32p),
+                ("lr_final", c_f32p), ("lr_steps", C.c_int32), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("d_step", C.c_void_p), ("cams_step", C.c_void_p), ("gt_step", C.c_void_p),
+                ("mask_step", C.c_void_p), ("proj", C.POINTER(GsProj)), ("max_instances", C.c_int64),
+                ("sort_ws", C.c_void_p), ("sort_ws_bytes", C.c_size_t), ("sorted_vals", C.c_void_p),
+                ("ranges", C.c_void_p), ("d_num_instances", C.c_void_p), ("sched", C.POINTER(GsSchedule)),
+                ("img", C.c_void_p), ("final_T", C.c_void_p), ("n_contrib", C.c_void_p), ("loss_ws", C.c_void_p),
+                ("loss_ws_bytes", C.c_size_t), ("d_loss", C.c_void_p), ("dL_dimg", C.c_void_p),
+                ("g2d", C.POINTER(GsGrad2d)), ("grads", C.c_void_p), ("variant", C.c_int32)]
+
+
 assert C.sizeof(GsCamera) == 96
 
 VP = C.c_void_p
@@ -84,10 +101,10 @@ SIGNATURES = {
     "gs_blend_bwd": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, c_f32p, VP, VP, VP, VP, C.POINTER(GsGrad2d),
                            I64, I32, C.POINTER(GsSchedule), VP]),
     "gs_project_bwd": (I32, [VP, I64, I32, C.POINTER(GsUnits), VP, C.POINTER(GsProj), C.POINTER(GsGrad2d), VP, VP]),
-    "gs_adam_step": (I32, [VP, VP, VP, VP, I64, I32, c_f32p, c_f32p, I32, F32, F32, F32, VP, I32, VP]),
+    "gs_adam_step": (I32, [VP, VP, VP, VP, I64, I32, c_f32p, c_f32p, I32, F32, F32, F32, VP, I32, VP, VP]),
     "gs_step_advance": (I32, [VP, VP]),
     "gs_project_bwd_adam": (I32, [VP, I64, I32, C.POINTER(GsUnits), VP, C.POINTER(GsProj), C.POINTER(GsGrad2d), VP,
-                                  VP, c_f32p, c_f32p, I32, F32, F32, F32, VP, VP, VP]),
+                                  VP, c_f32p, c_f32p, I32, F32, F32, F32, VP, VP, VP, VP]),
     "gs_knn_workspace_size": (SZ, [I64, c_i32p]),
     "gs_knn": (I32, [VP, I64, I32, c_f32p, F32, c_i32p, VP, SZ, VP, VP, VP]),
     "gs_mlp_param_count": (I32, []),
@@ -103,6 +120,8 @@ SIGNATURES = {
     "gs_densify_plan": (I32, [VP, I64, VP, VP, VP, C.POINTER(GsDensifyCfg), VP, SZ, VP, VP]),
     "gs_densify_apply": (I32, [VP, VP, VP, I64, I32, VP, VP, SZ, VP, VP, VP, I64, VP, VP]),
     "gs_opacity_reset": (I32, [VP, VP, VP, I64, F32, VP]),
+    "gs_train_batch": (I32, [C.POINTER(GsTrainBatchDesc), VP, VP]),
+    "gs_gather_views": (I32, [C.POINTER(GsTrainBatchDesc), VP, VP]),
 }
 
 OPTIONAL = set()

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include "gs.h"
+#include <nvtx3/nvToolsExt.h>
 
 #define GS_API extern "C" __attribute__((visibility("default")))
 
@@ -54,16 +55,46 @@ __device__ __forceinline__ int part_of(const OwnedTable& O, int64_t i) {
 __device__ __forceinline__ int floordiv16(int a) { return a >> 4; }  // arithmetic shift = floor
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
-// Tile rectangle [x0, x1) x [y0, y1) of a splat at (u, v) with radius r.
+// ---- float pairs (unevaluated sums hi + lo): error-free transformations
+// Knuth's TwoSum: s + e = a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// Dekker's TwoProduct with a fused multiply-add: p + e = a b exactly.
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// floor of the pair u = hi + lo (|lo| <= half an ulp of hi): one below
+// floor(hi) when hi is an integer and lo is negative.
+__device__ __forceinline__ int floor_pair(float hi, float lo) {
+  float f = floorf(hi);
+  return (int)f - ((f == hi && lo < 0.f) ? 1 : 0);
+}
+
+// Tile rectangle [x0, x1) x [y0, y1) of a splat at m = (u, v) with radius r,
+// the pixel position given as float pairs (m.x + m.z, m.y + m.w).
 // floor((u - r)/16) = floor((floor(u) - r)/16) for integer r, so the integer
-// form is exact and matches any exact evaluation of the float formula.
-__device__ __forceinline__ void tile_rect(float u, float v, int r, int TX, int TY, int& x0, int& y0,
-                                          int& x1, int& y1) {
-  int fu = (int)floorf(u), fv = (int)floorf(v);
+// form is exact and matches any exact evaluation of the formula.
+__device__ __forceinline__ void tile_rect(float4 m, int r, int TX, int TY, int& x0, int& y0, int& x1, int& y1) {
+  int fu = floor_pair(m.x, m.z), fv = floor_pair(m.y, m.w);
   x0 = clampi(floordiv16(fu - r), 0, TX);
   y0 = clampi(floordiv16(fv - r), 0, TY);
   x1 = clampi(floordiv16(fu + r + TILE - 1), 0, TX);
   y1 = clampi(floordiv16(fv + r + TILE - 1), 0, TY);
+}
+
+// Offset of a record's pixel position from the origin o (an integer pixel
+// coordinate) along one axis: (hi - o) + lo.  The blend kernels evaluate every
+// (pixel, record) pair as this offset minus the pixel's own offset from the
+// same origin (the tile's corner), so the power is computed from a small,
+// accurate difference rather than from coordinates of ~10^3 pixels, and all
+// kernels (forward, backward, any pixel-block shape) get bit-identical values.
+__device__ __forceinline__ float rel_pos(float hi, float lo, float o) {
+  return __fadd_rn(__fsub_rn(hi, o), lo);
 }
 
 // power = -(A dx^2 + C dy^2)/2 - B dx dy, written with explicit fmas so that
@@ -130,6 +161,16 @@ __host__ __device__ __forceinline__ int param_planes(int deg) {
 }
 
 }  // namespace gs
+
+// NVTX range around a host entry point (header-only NVTX3: a no-op unless a
+// profiler is attached), so that every gs_* call shows on a timeline.
+struct GsRange {
+  explicit GsRange(const char* name) { nvtxRangePushA(name); }
+  ~GsRange() { nvtxRangePop(); }
+  GsRange(const GsRange&) = delete;
+  GsRange& operator=(const GsRange&) = delete;
+};
+#define GS_RANGE(name) GsRange gs_range_guard_(name)
 
 // host-side helpers
 int gs_fill_units(const gs_units* u, gs::UnitTable& t, int64_t* total);

@@ -155,6 +155,7 @@ GS_API size_t gs_densify_workspace_size(int64_t n_gauss) {
 
 GS_API int gs_densify_stats(const gs_proj* proj, const gs_grad2d* g2d, const gs_units* units, int width, int height,
                             float* grad_accum, float* denom, float* max_radius, gs_stream_t stream) {
+  GS_RANGE("gs_densify_stats");
   UnitTable U;
   int64_t P = 0;
   if (!proj || !proj->radius || !g2d || !g2d->dxy || !grad_accum || !denom || !max_radius || width <= 0 ||
@@ -169,6 +170,7 @@ GS_API int gs_densify_stats(const gs_proj* proj, const gs_grad2d* g2d, const gs_
 GS_API int gs_densify_plan(const float* params, int64_t n_gauss, const float* grad_accum, const float* denom,
                            const float* max_radius, const gs_densify_cfg* cfg, void* workspace,
                            size_t workspace_bytes, uint32_t* d_counts, gs_stream_t stream) {
+  GS_RANGE("gs_densify_plan");
   if (!params || n_gauss < 1 || !grad_accum || !denom || !max_radius || !cfg || !workspace || !d_counts ||
       ((uintptr_t)workspace & 255u) || !(cfg->extent > 0.f))
     return GS_ERR_INVALID;
@@ -196,6 +198,7 @@ GS_API int gs_densify_plan(const float* params, int64_t n_gauss, const float* gr
 GS_API int gs_densify_apply(const float* params, const float* m, const float* v, int64_t n_gauss, int sh_degree,
                             const float* z, const void* workspace, size_t workspace_bytes, float* out_params,
                             float* out_m, float* out_v, int64_t n_out, int* d_status, gs_stream_t stream) {
+  GS_RANGE("gs_densify_apply");
   int npl = param_planes(sh_degree);
   if (!params || !m || !v || n_gauss < 1 || npl < 0 || !z || !workspace || !out_params || !out_m || !out_v ||
       n_out < 0 || ((uintptr_t)workspace & 255u))
@@ -212,6 +215,7 @@ GS_API int gs_densify_apply(const float* params, const float* m, const float* v,
 
 GS_API int gs_opacity_reset(float* params, float* m, float* v, int64_t n_gauss, float max_opacity,
                             gs_stream_t stream) {
+  GS_RANGE("gs_opacity_reset");
   if (!params || !m || !v || n_gauss < 0 || !(max_opacity > 0.f && max_opacity < 1.f)) return GS_ERR_INVALID;
   if (n_gauss == 0) return GS_OK;
   k_opacity_reset<<<(unsigned)((n_gauss + 255) / 256), 256, 0, (cudaStream_t)stream>>>(

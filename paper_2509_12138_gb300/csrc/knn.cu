@@ -158,6 +158,7 @@ GS_API size_t gs_knn_workspace_size(int64_t n, const int32_t* grid_dims) {
 GS_API int gs_knn(const float* points, int64_t n, int k, const float* grid_lo, float cell_size,
                   const int32_t* grid_dims, void* workspace, size_t workspace_bytes, int32_t* idx, float* dist,
                   gs_stream_t stream) {
+  GS_RANGE("gs_knn");
   if (!points || !idx || !dist || !grid_lo || !grid_dims || !workspace || n < 0 || !(cell_size > 0.f) ||
       !(k == 3 || k == 8 || k == 16))
     return GS_ERR_INVALID;

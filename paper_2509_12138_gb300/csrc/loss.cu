@@ -266,6 +266,7 @@ GS_API size_t gs_loss_workspace_size(int n_units, int width, int height) {
 GS_API int gs_loss(const float* img, const float* gt, const uint8_t* mask, int n_units, int width, int height,
                    float lambda_ssim, void* workspace, size_t workspace_bytes, float* d_loss, float* dL_dimg,
                    gs_stream_t stream) {
+  GS_RANGE("gs_loss");
   if (!img || !gt || !mask || !d_loss || !dL_dimg || !workspace || n_units < 1 || width <= 0 || height <= 0 ||
       !(lambda_ssim >= 0.f && lambda_ssim <= 1.f))
     return GS_ERR_INVALID;
@@ -305,6 +306,7 @@ GS_API int gs_blend_bwd(const gs_proj* proj, const uint32_t* sorted_vals, const 
                         int width, int height, const float* bg, const float* img, const float* final_T,
                         const uint32_t* n_contrib, const float* dL_dimg, const gs_grad2d* g2d, int64_t n_proj,
                         int variant, const gs_schedule* sched, gs_stream_t stream) {
+  GS_RANGE("gs_blend_bwd");
   return gs_blend_bwd_impl(proj, sorted_vals, ranges, n_units, width, height, bg, final_T, n_contrib, dL_dimg,
                            g2d, n_proj, variant, sched, img, (cudaStream_t)stream);
 }
@@ -315,6 +317,7 @@ GS_API int gs_render_bwd(const float* params, int64_t n_gauss, int sh_degree, co
                          const float* final_T, const uint32_t* n_contrib, const float* dL_dimg,
                          const gs_grad2d* g2d, float* grads, int variant, const gs_schedule* sched,
                          gs_stream_t stream) {
+  GS_RANGE("gs_render_bwd");
   UnitTable U;
   int64_t P = 0;
   if (gs_fill_units(units, U, &P) != GS_OK) return GS_ERR_INVALID;

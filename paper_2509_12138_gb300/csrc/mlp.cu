@@ -473,6 +473,7 @@ GS_API int gs_mlp_param_count(void) { return NPARAM; }
 
 GS_API int gs_mlp_features(const float* points, const float* normals, const int32_t* knn_idx, const float* knn_dist,
                            int64_t n, uint16_t* features, gs_stream_t stream) {
+  GS_RANGE("gs_mlp_features");
   if (!knn_args_ok(points, normals, knn_idx, knn_dist, n) || !features) return GS_ERR_INVALID;
   if (n == 0) return GS_OK;
   if (set_smem(k_features_out, Smem::FWD_END) != GS_OK) return GS_ERR_CUDA;
@@ -483,6 +484,7 @@ GS_API int gs_mlp_features(const float* points, const float* normals, const int3
 
 GS_API int gs_mlp_forward(const float* points, const float* normals, const int32_t* knn_idx, const float* knn_dist,
                           int64_t n, const float* weights, float* out, gs_stream_t stream) {
+  GS_RANGE("gs_mlp_forward");
   if (!knn_args_ok(points, normals, knn_idx, knn_dist, n) || !weights || !out) return GS_ERR_INVALID;
   if (n == 0) return GS_OK;
   if (set_smem(k_mlp_forward, Smem::FWD_END) != GS_OK) return GS_ERR_CUDA;
@@ -494,6 +496,7 @@ GS_API int gs_mlp_forward(const float* points, const float* normals, const int32
 GS_API int gs_mlp_train_step(const float* points, const float* normals, const int32_t* knn_idx,
                              const float* knn_dist, const float* targets, int64_t n, float* weights, float* grad,
                              float* m, float* v, float lr, const int32_t* d_step, float* d_loss, gs_stream_t stream) {
+  GS_RANGE("gs_mlp_train_step");
   if (!knn_args_ok(points, normals, knn_idx, knn_dist, n) || !targets || !weights || !grad || !m || !v ||
       !d_step || !d_loss || n < 1 || !(lr > 0.f))
     return GS_ERR_INVALID;
@@ -508,12 +511,14 @@ GS_API int gs_mlp_train_step(const float* points, const float* normals, const in
   int r = gs_check_launch();
   if (r != GS_OK) return r;
   float lr4[4] = {lr, lr, lr, lr};
-  return gs_adam_step(weights, grad, m, v, NPARAM / 4, 1, lr4, lr4, 0, 0.9f, 0.999f, 1e-8f, d_step, 0, stream);
+  return gs_adam_step(weights, grad, m, v, NPARAM / 4, 1, lr4, lr4, 0, 0.9f, 0.999f, 1e-8f, d_step, 0, nullptr,
+                      stream);
 }
 
 GS_API int gs_init_gaussians(const float* points, const float* normals, const int32_t* knn_idx,
                              const float* knn_dist, int knn_k, int64_t n, const float* weights, float logit_default,
                              float* params, int64_t n_gauss, gs_stream_t stream) {
+  GS_RANGE("gs_init_gaussians");
   if (!points || !knn_dist || !params || n < 0 || n > n_gauss || knn_k < 3) return GS_ERR_INVALID;
   if (weights && (!normals || !knn_idx || knn_k != KNN)) return GS_ERR_INVALID;
   if (n == 0) return GS_OK;

@@ -53,6 +53,7 @@ GS_API int gs_peak_threads(int n_sms) {
 
 GS_API int gs_peak_issue(int mode, int n_sms, int iters, float a, float b, float* out,
                          gs_stream_t stream) {
+  GS_RANGE("gs_peak_issue");
   if (!out || n_sms <= 0 || iters <= 0 || (mode != 0 && mode != 1)) return GS_ERR_INVALID;
   const dim3 grid(n_sms * PEAK_BLOCKS_PER_SM);
   cudaStream_t s = (cudaStream_t)stream;

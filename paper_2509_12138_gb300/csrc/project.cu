@@ -131,10 +131,52 @@ struct Geo {
   float xzc, yzc;
 };
 
-// Camera-space z by a fixed fma chain: it is the depth sort key, so its
-// rounding is part of the definition of the list order.
+// One row of the view transform, r0 x + r1 y + r2 z + t, as a float pair
+// (h, l) with h the value rounded once to float32.  Each product is split
+// exactly by TwoProduct, the products are summed with TwoSum, which returns
+// every addition's rounding error, and the collected error terms are added at
+// the end; h + l then equals the exact value up to about 2^-44 of the terms'
+// magnitude, so h is the correctly rounded value unless the exact one lies
+// that close to a rounding boundary.  The explicitly rounded intrinsics keep
+// the compiler from contracting the steps.
+__device__ __forceinline__ void view_row(const float* r, float4 m, float& h, float& l) {
+  float p0, e0, p1, e1, p2, e2;
+  two_prod(r[0], m.x, p0, e0);
+  two_prod(r[1], m.y, p1, e1);
+  two_prod(r[2], m.z, p2, e2);
+  float lo = __fadd_rn(__fadd_rn(e0, e1), e2);
+  float s, e;
+  two_sum(r[3], p0, s, e);
+  lo = __fadd_rn(lo, e);
+  two_sum(s, p1, s, e);
+  lo = __fadd_rn(lo, e);
+  two_sum(s, p2, s, e);
+  lo = __fadd_rn(lo, e);
+  two_sum(s, lo, h, l);
+}
+
+// Camera-space z rounded to float32: the depth sort key (row 2 of viewmat).
 __device__ __forceinline__ float cam_z(const float* V, float4 m) {
-  return __fmaf_rn(V[8], m.x, __fmaf_rn(V[9], m.y, __fmaf_rn(V[10], m.z, V[11])));
+  float h, l;
+  view_row(V + 8, m, h, l);
+  return h;
+}
+
+// Pixel coordinate f t / z + c of camera-space (t, z), both float pairs, as a
+// float pair (h, l): the quotient's remainder t_h - q_h z_h is exact by one
+// fused multiply-add, the product f q by TwoProduct, the sum with c by TwoSum.
+__device__ __forceinline__ void pixel_pair(float th, float tl, float zh, float zl, float f, float c, float& h,
+                                           float& l) {
+  float qh = __fdiv_rn(th, zh);
+  float r = __fmaf_rn(-qh, zh, th);
+  r = __fadd_rn(r, __fsub_rn(tl, __fmul_rn(qh, zl)));
+  float ql = __fdiv_rn(r, zh);
+  float ph, pe;
+  two_prod(f, qh, ph, pe);
+  pe = __fmaf_rn(f, ql, pe);
+  float sh, se;
+  two_sum(ph, c, sh, se);
+  two_sum(sh, __fadd_rn(se, pe), h, l);
 }
 
 __device__ __forceinline__ void quat_rot(float4 q, float* R, float* qn_out) {
@@ -214,7 +256,7 @@ template <int DEG>
 __global__ void __launch_bounds__(256) k_preprocess(const float4* __restrict__ params, int64_t N,
                                                     UnitTable U, OwnedTable O,
                                                     const gs_camera* __restrict__ cams, int W, int H,
-                                                    float2* __restrict__ xy, float4* __restrict__ conic_op,
+                                                    float4* __restrict__ xy, float4* __restrict__ conic_op,
                                                     float4* __restrict__ rgb, float* __restrict__ depth,
                                                     int* __restrict__ radius, uint32_t* __restrict__ tiles,
                                                     int* status) {
@@ -230,7 +272,8 @@ __global__ void __launch_bounds__(256) k_preprocess(const float4* __restrict__ p
   int r_out = 0;
   uint32_t tiles_out = 0;
   const float* V = cam.viewmat;
-  float tz = cam_z(V, mean);
+  float tz, tzl;
+  view_row(V + 8, mean, tz, tzl);  // tz: the correctly rounded camera-space z (the sort key)
   depth[p] = tz;
   if (tz > cam.znear && owned_keep(O, i, mean)) {
     Geo g;
@@ -240,10 +283,16 @@ __global__ void __launch_bounds__(256) k_preprocess(const float4* __restrict__ p
       float mid = 0.5f * (g.a + g.c);
       float lam = mid + sqrtf(fmaxf(LAMBDA_FLOOR, mid * mid - g.det));
       int r = (int)ceilf(3.0f * sqrtf(lam));
-      float px = cam.fx * g.t[0] / tz + cam.cx;
-      float py = cam.fy * g.t[1] / tz + cam.cy;
+      // pixel position as float pairs (x + x_lo, y + y_lo), from the view rows in pairs
+      float t0h, t0l, t1h, t1l;
+      view_row(V, mean, t0h, t0l);
+      view_row(V + 4, mean, t1h, t1l);
+      float4 pxy;
+      pixel_pair(t0h, t0l, tz, tzl, cam.fx, cam.cx, pxy.x, pxy.z);
+      pixel_pair(t1h, t1l, tz, tzl, cam.fy, cam.cy, pxy.y, pxy.w);
+      float px = pxy.x, py = pxy.y;
       int x0, y0, x1, y1;
-      tile_rect(px, py, r, TX, TY, x0, y0, x1, y1);
+      tile_rect(pxy, r, TX, TY, x0, y0, x1, y1);
       uint32_t nt = (uint32_t)((x1 - x0) * (y1 - y0));
       if (r > 0 && nt > 0) {
         // colour
@@ -263,12 +312,13 @@ __global__ void __launch_bounds__(256) k_preprocess(const float4* __restrict__ p
           col[ch] = fmaxf(acc, 0.f);
         }
         float op = 1.0f / (1.0f + expf(-sop.w));
-        xy[p] = make_float2(px, py);
+        xy[p] = pxy;
         conic_op[p] = make_float4(g.c * idet, -g.b * idet, g.a * idet, op);
         rgb[p] = make_float4(col[0], col[1], col[2], power_floor(op));
         r_out = r;
         tiles_out = nt;
-        if (!(isfinite(px) && isfinite(py) && isfinite(col[0] + col[1] + col[2]))) {
+        if (!(isfinite(px) && isfinite(py) && isfinite(col[0] + col[1] + col[2]) &&
+              isfinite(g.c * idet + g.b * idet + g.a * idet) && isfinite(op))) {
           set_status(status, GS_ERR_NONFINITE);
           r_out = 0;
           tiles_out = 0;
@@ -470,10 +520,15 @@ struct AdamLR {
   float4 fin[16];
 };
 
+__device__ __forceinline__ bool finite4(float4 a) {
+  return isfinite(a.x) && isfinite(a.y) && isfinite(a.z) && isfinite(a.w);
+}
+
 __global__ void __launch_bounds__(256) k_adam(float4* __restrict__ p, float4* __restrict__ g,
                                               float4* __restrict__ m, float4* __restrict__ v, int64_t N,
                                               int n_planes, AdamLR lr, int lr_steps, float b1, float b2,
-                                              float eps, const int32_t* __restrict__ d_step, int zero) {
+                                              float eps, const int32_t* __restrict__ d_step, int zero,
+                                              int* __restrict__ status) {
   __shared__ float4 s_lr[16];
   int t = *d_step + 1;
   if (threadIdx.x < n_planes) {
@@ -491,6 +546,11 @@ __global__ void __launch_bounds__(256) k_adam(float4* __restrict__ p, float4* __
     int plane = (int)(k / N);
     float4 L = s_lr[plane];
     float4 P = p[k], G = g[k], Mv = m[k], Vv = v[k];
+    if (zero) g[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!finite4(G)) {  // a non-finite gradient: reported, and these four values keep their state
+      set_status(status, GS_ERR_NONFINITE);
+      continue;
+    }
     float* pp = &P.x; float* gg = &G.x; float* mm = &Mv.x; float* vv = &Vv.x; const float* ll = &L.x;
     #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -499,7 +559,6 @@ __global__ void __launch_bounds__(256) k_adam(float4* __restrict__ p, float4* __
       pp[c] -= ll[c] * (mm[c] * ibc1) / (sqrtf(vv[c] * ibc2) + eps);
     }
     p[k] = P; m[k] = Mv; v[k] = Vv;
-    if (zero) g[k] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
@@ -527,7 +586,7 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam(float4* __restrict__ p
                                                           const float4* __restrict__ grgb, float4* __restrict__ m,
                                                           float4* __restrict__ v, AdamLR lr, int lr_steps, float b1,
                                                           float b2, float eps, const int32_t* __restrict__ d_step,
-                                                          float4* __restrict__ grads) {
+                                                          float4* __restrict__ grads, int* __restrict__ status) {
   constexpr int NP = ShCount<DEG>::NP;
   constexpr int NPL = 3 + NP;
   __shared__ float4 s_lr[16];
@@ -555,13 +614,18 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam(float4* __restrict__ p
   project_grads<DEG>(i, mean, sop, quat, c, U, cams, radius, gxy, gco, grgb, dmean, dls, dq, dlogit, dsh);
   float4 G[3] = {make_float4(dmean[0], dmean[1], dmean[2], 0.f), make_float4(dls[0], dls[1], dls[2], dlogit),
                  make_float4(dq[0], dq[1], dq[2], dq[3])};
+  // a non-finite gradient is reported and leaves this Gaussian's parameters and moments as they are
+  bool ok = finite4(G[0]) && finite4(G[1]) && finite4(G[2]);
+  #pragma unroll
+  for (int k = 0; k < 4 * NP; ++k) ok = ok && isfinite(dsh[k]);
+  if (!ok) set_status(status, GS_ERR_NONFINITE);
   float4 Pv[3] = {mean, sop, quat};
   #pragma unroll
   for (int k = 0; k < 3; ++k) {
     int64_t o = k * N + i;
     float4 M = m[o], V = v[o];
     adam4(Pv[k], G[k], M, V, s_lr[k], b1, b2, ibc1, ibc2, eps);
-    params[o] = Pv[k]; m[o] = M; v[o] = V;
+    if (ok) { params[o] = Pv[k]; m[o] = M; v[o] = V; }
     if (grads) grads[o] = G[k];
   }
   #pragma unroll
@@ -571,7 +635,7 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam(float4* __restrict__ p
     float4 Gk = make_float4(dsh[4 * k], dsh[4 * k + 1], dsh[4 * k + 2], dsh[4 * k + 3]);
     float4 M = m[o], V = v[o];
     adam4(P, Gk, M, V, s_lr[3 + k], b1, b2, ibc1, ibc2, eps);
-    params[o] = P; m[o] = M; v[o] = V;
+    if (ok) { params[o] = P; m[o] = M; v[o] = V; }
     if (grads) grads[o] = Gk;
   }
 }
@@ -609,7 +673,7 @@ __global__ void __launch_bounds__(PBA_T) k_project_bwd_adam1(float4* __restrict_
                                                            const float4* __restrict__ grgb, float4* __restrict__ m,
                                                            float4* __restrict__ v, AdamLR lr, int lr_steps, float b1,
                                                            float b2, float eps, const int32_t* __restrict__ d_step,
-                                                           float4* __restrict__ grads) {
+                                                           float4* __restrict__ grads, int* __restrict__ status) {
   constexpr int NC = ShCount<DEG>::NC;
   constexpr int NP = ShCount<DEG>::NP;
   constexpr int NPL = 3 + NP;
@@ -656,11 +720,13 @@ __global__ void __launch_bounds__(PBA_T) k_project_bwd_adam1(float4* __restrict_
   float4 mean = sP[tl], sop = sP[PBA_T + tl], quat = sP[2 * PBA_T + tl];
   float dmean[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, dlogit = 0.f;
   float Y[16], gc[3] = {0.f, 0.f, 0.f}, il = 0.f, dir[3] = {0.f, 0.f, 0.f};
+  bool ok = true;  // false: a non-finite gradient, reported; this Gaussian's state is then left as it is
   if (vis) {
     const gs_camera& cam = cams[uu];
     float2 g_xy = gxy[pidx];
     float4 g_co = gco[pidx];
     float4 g_rgb = grgb[pidx];
+    ok = isfinite(g_xy.x) && isfinite(g_xy.y) && finite4(g_co) && finite4(g_rgb);
     // pass A: colour before the clamp
     float vx = mean.x - cam.campos[0], vy = mean.y - cam.campos[1], vz = mean.z - cam.campos[2];
     il = 1.0f / sqrtf(vx * vx + vy * vy + vz * vz);
@@ -768,6 +834,12 @@ __global__ void __launch_bounds__(PBA_T) k_project_bwd_adam1(float4* __restrict_
     dq[1] = (gx - dot * x) * inv;
     dq[2] = (gy - dot * y) * inv;
     dq[3] = (gz - dot * z) * inv;
+    // with finite screen-space gradients and parameters, every gradient below is finite
+    ok = ok && finite4(make_float4(dmean[0], dmean[1], dmean[2], dlogit)) &&
+         finite4(make_float4(dls[0], dls[1], dls[2], 0.f)) && finite4(make_float4(dq[0], dq[1], dq[2], dq[3]));
+    #pragma unroll
+    for (int k = 0; k < NP; ++k) ok = ok && finite4(sP[(3 + k) * PBA_T + tl]);
+    if (!ok) set_status(status, GS_ERR_NONFINITE);
   } else {
     #pragma unroll
     for (int k = 0; k < 16; ++k) Y[k] = 0.f;
@@ -796,7 +868,7 @@ __global__ void __launch_bounds__(PBA_T) k_project_bwd_adam1(float4* __restrict_
     float4 Gk = make_float4(G[0], G[1], G[2], G[3]);
     float4 Mv = slot[tl], Vv = slot[PBA_T + tl];
     adam4(P, Gk, Mv, Vv, s_lr[3 + k], b1, b2, ibc1, ibc2, eps);
-    params[o] = P; m[o] = Mv; v[o] = Vv;
+    if (ok) { params[o] = P; m[o] = Mv; v[o] = Vv; }
     if (grads) grads[o] = Gk;
     mv_copy(k + PBA_R);  // the slot's values are consumed: refill it PBA_R steps ahead
   }
@@ -818,7 +890,7 @@ __global__ void __launch_bounds__(PBA_T) k_project_bwd_adam1(float4* __restrict_
     const float4* slot = sR + ((NP + k) % PBA_R) * 2 * PBA_T;
     float4 Mv = slot[tl], Vv = slot[PBA_T + tl];
     adam4(Pv[k], Gp[k], Mv, Vv, s_lr[k], b1, b2, ibc1, ibc2, eps);
-    params[o] = Pv[k]; m[o] = Mv; v[o] = Vv;
+    if (ok) { params[o] = Pv[k]; m[o] = Mv; v[o] = Vv; }
     if (grads) grads[o] = Gp[k];
     mv_copy(NP + k + PBA_R);
   }
@@ -878,6 +950,7 @@ static bool units_in_range(const UnitTable& t, int64_t n_gauss) {
 GS_API int gs_param_planes(int sh_degree) { return param_planes(sh_degree); }
 
 GS_API int gs_status_read(int* d_status, int clear, gs_stream_t stream) {
+  GS_RANGE("gs_status_read");
   if (!d_status) return GS_ERR_INVALID;
   int h = 0;
   if (cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess)
@@ -890,6 +963,7 @@ GS_API int gs_status_read(int* d_status, int clear, gs_stream_t stream) {
 GS_API int gs_preprocess(const float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
                          const gs_camera* cams, int width, int height, const gs_owned* owned,
                          const gs_proj* proj, int* d_status, gs_stream_t stream) {
+  GS_RANGE("gs_preprocess");
   UnitTable U;
   OwnedTable O;
   int64_t P = 0;
@@ -906,7 +980,7 @@ GS_API int gs_preprocess(const float* params, int64_t n_gauss, int sh_degree, co
   cudaStream_t s = (cudaStream_t)stream;
   const float4* p4 = (const float4*)params;
 #define GS_PRE(D)                                                                                   \
-  k_preprocess<D><<<grid, block, 0, s>>>(p4, n_gauss, U, O, cams, width, height, (float2*)proj->xy, \
+  k_preprocess<D><<<grid, block, 0, s>>>(p4, n_gauss, U, O, cams, width, height, (float4*)proj->xy, \
                                          (float4*)proj->conic_op, (float4*)proj->rgb, proj->depth,   \
                                          proj->radius, proj->tiles, d_status)
   switch (sh_degree) {
@@ -922,6 +996,7 @@ GS_API int gs_preprocess(const float* params, int64_t n_gauss, int sh_degree, co
 GS_API int gs_project_bwd(const float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
                           const gs_camera* cams, const gs_proj* proj, const gs_grad2d* g2d, float* grads,
                           gs_stream_t stream) {
+  GS_RANGE("gs_project_bwd");
   UnitTable U;
   int64_t P = 0;
   if (((!params || !grads) && n_gauss > 0) || !cams || !proj || !g2d || n_gauss < 0 ||
@@ -948,7 +1023,8 @@ GS_API int gs_project_bwd(const float* params, int64_t n_gauss, int sh_degree, c
 
 GS_API int gs_adam_step(float* params, float* grads, float* m, float* v, int64_t n_gauss, int n_planes,
                         const float* lr_init, const float* lr_final, int32_t lr_steps, float beta1, float beta2,
-                        float eps, const int32_t* d_step, int zero_grad, gs_stream_t stream) {
+                        float eps, const int32_t* d_step, int zero_grad, int* d_status, gs_stream_t stream) {
+  GS_RANGE("gs_adam_step");
   if (!params || !grads || !m || !v || !lr_init || !d_step || n_gauss < 0 || n_planes < 1 || n_planes > 16)
     return GS_ERR_INVALID;
   if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps >= 0.f)) return GS_ERR_INVALID;
@@ -968,11 +1044,13 @@ GS_API int gs_adam_step(float* params, float* grads, float* m, float* v, int64_t
   int64_t cap = (int64_t)sms * 8;
   unsigned grid = (unsigned)(want < cap ? want : cap);
   k_adam<<<grid, 256, 0, (cudaStream_t)stream>>>((float4*)params, (float4*)grads, (float4*)m, (float4*)v, n_gauss,
-                                                 n_planes, lr, lr_steps, beta1, beta2, eps, d_step, zero_grad);
+                                                 n_planes, lr, lr_steps, beta1, beta2, eps, d_step, zero_grad,
+                                                 d_status);
   return gs_check_launch();
 }
 
 GS_API int gs_step_advance(int32_t* d_step, gs_stream_t stream) {
+  GS_RANGE("gs_step_advance");
   if (!d_step) return GS_ERR_INVALID;
   k_step_advance<<<1, 1, 0, (cudaStream_t)stream>>>(d_step);
   return gs_check_launch();
@@ -981,7 +1059,9 @@ GS_API int gs_step_advance(int32_t* d_step, gs_stream_t stream) {
 GS_API int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
                                const gs_camera* cams, const gs_proj* proj, const gs_grad2d* g2d, float* m, float* v,
                                const float* lr_init, const float* lr_final, int32_t lr_steps, float beta1,
-                               float beta2, float eps, const int32_t* d_step, float* grads, gs_stream_t stream) {
+                               float beta2, float eps, const int32_t* d_step, float* grads, int* d_status,
+                               gs_stream_t stream) {
+  GS_RANGE("gs_project_bwd_adam");
   UnitTable U;
   int64_t P = 0;
   int npl = param_planes(sh_degree);
@@ -1016,7 +1096,7 @@ GS_API int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, co
   k_project_bwd_adam1<D><<<grid1, PBA_T, smem1, s>>>((float4*)params, n_gauss, U, cams, proj->radius,            \
                                                 (const float2*)g2d->dxy, (const float4*)g2d->dconic_op,          \
                                                 (const float4*)g2d->drgb, (float4*)m, (float4*)v, lr, lr_steps,   \
-                                                beta1, beta2, eps, d_step, (float4*)grads)
+                                                beta1, beta2, eps, d_step, (float4*)grads, d_status)
     switch (sh_degree) {
       case 0: GS_PBA1(0); break;
       case 1: GS_PBA1(1); break;
@@ -1030,7 +1110,7 @@ GS_API int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, co
   k_project_bwd_adam<D><<<grid, block, 0, s>>>((float4*)params, n_gauss, U, cams, proj->radius,                 \
                                                (const float2*)g2d->dxy, (const float4*)g2d->dconic_op,          \
                                                (const float4*)g2d->drgb, (float4*)m, (float4*)v, lr, lr_steps,   \
-                                               beta1, beta2, eps, d_step, (float4*)grads)
+                                               beta1, beta2, eps, d_step, (float4*)grads, d_status)
   switch (sh_degree) {
     case 0: GS_PBA(0); break;
     case 1: GS_PBA(1); break;

@@ -96,7 +96,7 @@ template <int BW>
 __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict__ ranges,
                                                          const uint32_t* __restrict__ order,
                                                          const uint32_t* __restrict__ vals,
-                                                         const float2* __restrict__ xy,
+                                                         const float4* __restrict__ xy,
                                                          const float4* __restrict__ conic_op,
                                                          const float4* __restrict__ rgb, int W, int H, int TX,
                                                          int n_tiles, float bg0, float bg1, float bg2,
@@ -118,15 +118,17 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict
   float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
   int last = 0;
   bool done = !inside;
-  float fx = (float)px, fy = (float)py;
+  // pixel offsets from the tile's corner, the origin of the staged record positions (rel_pos)
+  float tox = (float)(tx * TILE), toy = (float)(ty * TILE);
+  float fx = (float)(px - tx * TILE), fy = (float)(py - ty * TILE);
   Rec* my = &s_rec[w][0];
   uint32_t p_n = 0;
-  float2 m_n = make_float2(0.f, 0.f);
+  float4 m_n = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 co_n = make_float4(0.f, 0.f, 0.f, 0.f), c_n = co_n;
   if (lane < n) { p_n = vals[rg.x + lane]; m_n = xy[p_n]; co_n = conic_op[p_n]; c_n = rgb[p_n]; }
   for (int base = 0; base < n; base += 32) {
     if (__all_sync(FULL, done)) break;
-    float2 m = m_n;
+    float4 m = m_n;
     float4 co = co_n, c = c_n;
     bool valid = base + lane < n;
     int kn = base + 32 + lane;
@@ -134,12 +136,12 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict
     float pmin = 0.f;
     bool hit = false;
     if (valid) {
-      float4 b = alpha_box(m, co, pmin);
+      float4 b = alpha_box(make_float2(m.x, m.y), co, pmin);
       hit = !box_misses(b, wx0, wx1, wy0, wy1);
     }
     unsigned mask = __ballot_sync(FULL, hit);
     if (hit) {
-      my[lane].a = make_float4(m.x, m.y, co.x, co.y);
+      my[lane].a = make_float4(rel_pos(m.x, m.z, tox), rel_pos(m.y, m.w, toy), co.x, co.y);
       my[lane].b = make_float4(co.z, co.w, pmin, 0.f);
       my[lane].c = c;
     }
@@ -174,9 +176,6 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_fwd(const uint2* __restrict
     n_contrib[(int64_t)u * plane + pix] = (uint32_t)last;
   }
 }
-
-__device__ __forceinline__ float fx_of(int px) { return (float)px; }
-__device__ __forceinline__ float fy_of(int py) { return (float)py; }
 
 // Sum of 8 values over the warp in 9 shuffles: each butterfly level halves the
 // set of values a lane carries; afterwards lane l holds the total of value
@@ -214,7 +213,7 @@ template <int BW>
 __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict__ ranges,
                                                          const uint32_t* __restrict__ order,
                                                          const uint32_t* __restrict__ vals,
-                                                         const float2* __restrict__ xy,
+                                                         const float4* __restrict__ xy,
                                                          const float4* __restrict__ conic_op,
                                                          const float4* __restrict__ rgb, int W, int H, int TX,
                                                          int n_tiles, float bg0, float bg1, float bg2,
@@ -247,7 +246,8 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict
   }
   int n = min(__reduce_max_sync(FULL, last), (int)(rg.y - rg.x));
   float S0 = bg0, S1 = bg1, S2 = bg2;  // colour behind the current entry
-  float fx = (float)px, fy = (float)py;
+  float tox = (float)(tx * TILE), toy = (float)(ty * TILE);
+  float fx = (float)(px - tx * TILE), fy = (float)(py - ty * TILE);
   Rec* my = &s_rec[w][0];
   // lanes (l & 3) == 0 hold butterfly value q(l); value 8 (d blue) is held by all lanes
   int q = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
@@ -257,13 +257,13 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict
     bool hit = false;
     if (k >= 0) {
       uint32_t p = vals[rg.x + k];
-      float2 m = xy[p];
+      float4 m = xy[p];
       float4 co = conic_op[p];
       float pm;
-      float4 b = alpha_box(m, co, pm);
+      float4 b = alpha_box(make_float2(m.x, m.y), co, pm);
       hit = !box_misses(b, wx0, wx1, wy0, wy1);
       if (hit) {
-        my[lane].a = make_float4(m.x, m.y, co.x, co.y);
+        my[lane].a = make_float4(rel_pos(m.x, m.z, tox), rel_pos(m.y, m.w, toy), co.x, co.y);
         my[lane].b = make_float4(co.z, co.w, pm, __uint_as_float(p));
         my[lane].c = rgb[p];
       }
@@ -363,14 +363,14 @@ struct LocalAcc {
 
 template <bool LOCAL = false>
 __device__ __forceinline__ void walk_fwd(const uint32_t* __restrict__ vals, const uint16_t* __restrict__ masks,
-                                         const float2* __restrict__ xy, const float4* __restrict__ conic_op,
+                                         const float4* __restrict__ xy, const float4* __restrict__ conic_op,
                                          const float4* __restrict__ rgb, uint32_t off, int beg, int end,
-                                         uint32_t wbits, float fx, float fy, Rec* my, float& T, float& c0,
+                                         uint32_t wbits, float tox, float toy, float fx, float fy, Rec* my, float& T, float& c0,
                                          float& c1, float& c2, int& last, bool& done, LocalAcc* loc = nullptr) {
   const unsigned FULL = 0xffffffffu;
   int lane = threadIdx.x & 31;
   bool h1 = false;
-  float2 m1 = make_float2(0.f, 0.f);
+  float4 m1 = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 co1 = make_float4(0.f, 0.f, 0.f, 0.f), cc1 = co1;
   uint32_t mk2 = 0, pk2 = 0;
   if (beg + lane < end) {
@@ -384,7 +384,7 @@ __device__ __forceinline__ void walk_fwd(const uint32_t* __restrict__ vals, cons
   for (int base = beg; base < end; base += 32) {
     if (__all_sync(FULL, done)) break;
     bool hit = h1;
-    float2 m = m1;
+    float4 m = m1;
     float4 co = co1, c = cc1;
     h1 = (mk2 & wbits) != 0;
     if (h1) { m1 = xy[pk2]; co1 = conic_op[pk2]; cc1 = rgb[pk2]; }
@@ -393,7 +393,7 @@ __device__ __forceinline__ void walk_fwd(const uint32_t* __restrict__ vals, cons
     if (k2 < end) { mk2 = masks[off + k2]; pk2 = vals[off + k2]; }
     unsigned mask = __ballot_sync(FULL, hit);
     if (hit) {
-      my[lane].a = make_float4(m.x, m.y, co.x, co.y);
+      my[lane].a = make_float4(rel_pos(m.x, m.z, tox), rel_pos(m.y, m.w, toy), co.x, co.y);
       my[lane].b = make_float4(co.z, co.w, c.w, 0.f);
       my[lane].c = c;
     }
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ r
                                                            uint32_t* __restrict__ chunk_last,
                                                            const uint32_t* __restrict__ vals,
                                                            const uint16_t* __restrict__ masks,
-                                                           const float2* __restrict__ xy,
+                                                           const float4* __restrict__ xy,
                                                            const float4* __restrict__ conic_op,
                                                            const float4* __restrict__ rgb, int W, int H, int TX,
                                                            int n_tiles, float bg0, float bg1, float bg2,
@@ -517,8 +517,9 @@ __global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ r
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
     int last = 0;
     bool done = !P.inside;
-    walk_fwd(vals, masks, xy, conic_op, rgb, rg.x, ch * K, min(ch * K + K, L), P.wbits, (float)P.px, (float)P.py,
-             s_rec, T, c0, c1, c2, last, done);
+    walk_fwd(vals, masks, xy, conic_op, rgb, rg.x, ch * K, min(ch * K + K, L), P.wbits, (float)(P.tx * TILE),
+             (float)(P.ty * TILE), (float)(P.px - P.tx * TILE), (float)(P.py - P.ty * TILE), s_rec, T, c0, c1, c2,
+             last, done);
     if (!P.inside) return;
     int64_t plane = (int64_t)W * H;
     int64_t pix = (int64_t)P.py * W + P.px;
@@ -690,7 +691,7 @@ __global__ void __launch_bounds__(32) k_render_fwd_stop(const uint2* __restrict_
                                                               uint32_t* __restrict__ chunk_last,
                                                               const uint32_t* __restrict__ vals,
                                                               const uint16_t* __restrict__ masks,
-                                                              const float2* __restrict__ xy,
+                                                              const float4* __restrict__ xy,
                                                               const float4* __restrict__ conic_op,
                                                               const float4* __restrict__ rgb, int W, int H, int TX,
                                                               int n_tiles, float bg0, float bg1, float bg2,
@@ -736,8 +737,9 @@ __global__ void __launch_bounds__(32) k_render_fwd_stop(const uint2* __restrict_
   for (; c < nch; ++c) {
     LocalAcc la = {1.f, 0.f, 0.f, 0.f};
     float Tin = T;
-    walk_fwd<true>(vals, masks, xy, conic_op, rgb, rg.x, c * K, min(c * K + K, L), wbits, (float)P.px,
-                   (float)P.py, s_rec, T, c0, c1, c2, last, done, &la);
+    walk_fwd<true>(vals, masks, xy, conic_op, rgb, rg.x, c * K, min(c * K + K, L), wbits, (float)(P.tx * TILE),
+                   (float)(P.ty * TILE), (float)(P.px - P.tx * TILE), (float)(P.py - P.ty * TILE), s_rec, T, c0, c1,
+                   c2, last, done, &la);
     if (mine) {
       int64_t slot = (cp0 + c - 1) * TILE_PIX + P.pix_local;
       ckpt[slot] = make_float4(la.t, la.c0, la.c1, la.c2);
@@ -801,7 +803,7 @@ __global__ void __launch_bounds__(32) k_render_fwd_seq(const uint2* __restrict__
                                                              uint32_t* __restrict__ chunk_last,
                                                              const uint32_t* __restrict__ vals,
                                                              const uint16_t* __restrict__ masks,
-                                                             const float2* __restrict__ xy,
+                                                             const float4* __restrict__ xy,
                                                              const float4* __restrict__ conic_op,
                                                              const float4* __restrict__ rgb, int W, int H, int TX,
                                                              int n_tiles, float bg0, float bg1, float bg2,
@@ -820,8 +822,9 @@ __global__ void __launch_bounds__(32) k_render_fwd_seq(const uint2* __restrict__
   for (int c = 0; c < max(nch, 1); ++c) {
     LocalAcc la = {1.f, 0.f, 0.f, 0.f};
     float Tin = T;
-    walk_fwd<true>(vals, masks, xy, conic_op, rgb, rg.x, c * K, min(c * K + K, L), P.wbits, (float)P.px,
-                   (float)P.py, s_rec, T, c0, c1, c2, last, done, &la);
+    walk_fwd<true>(vals, masks, xy, conic_op, rgb, rg.x, c * K, min(c * K + K, L), P.wbits, (float)(P.tx * TILE),
+                   (float)(P.ty * TILE), (float)(P.px - P.tx * TILE), (float)(P.py - P.ty * TILE), s_rec, T, c0, c1,
+                   c2, last, done, &la);
     if (c > 0 && P.inside) {  // the chunk's partial and the T in front of it
       int64_t slot = (cp0 + c - 1) * TILE_PIX + P.pix_local;
       ckpt[slot] = make_float4(la.t, la.c0, la.c1, la.c2);
@@ -904,14 +907,14 @@ __device__ __forceinline__ void bwd_queue_flush(const float4* s_q, int head, int
 // hits to a per-warp ring; the deterministic mode (fixed != NULL) runs
 // without it.
 template <int BW, bool QUEUE>
-__global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(32, 32) k_render_bwd_m(const uint2* __restrict__ ranges,
                                                            const uint32_t* __restrict__ order,
                                                            const uint32_t* __restrict__ job_base,
                                                            const uint32_t* __restrict__ jobs, int K,
                                                            const float4* __restrict__ ckpt,
                                                            const uint32_t* __restrict__ vals,
                                                            const uint16_t* __restrict__ masks,
-                                                           const float2* __restrict__ xy,
+                                                           const float4* __restrict__ xy,
                                                            const float4* __restrict__ conic_op,
                                                            const float4* __restrict__ rgb, int W, int H, int TX,
                                                            int n_tiles, int NT, float bg0, float bg1, float bg2,
@@ -941,6 +944,8 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
     int px = tx * TILE + (w % NWX) * BW + (lane % BW), py = ty * TILE + (w / NWX) * BH + (lane / BW);
     uint32_t wbits = warp_block_bits<BW>(w);
     bool inside = px < W && py < H;
+    float tox = (float)(tx * TILE), toy = (float)(ty * TILE);  // origin of the staged record positions
+    float lx = (float)(px - tx * TILE), ly = (float)(py - ty * TILE);
     uint2 rg = ranges[(int64_t)u * n_tiles + tile];
     int L = (int)(rg.y - rg.x);
     int cbeg = ch * K, cend = min(cbeg + K, L);
@@ -968,7 +973,7 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
     int q = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
     bool h1 = false;
     uint32_t p1 = 0;
-    float2 m1 = make_float2(0.f, 0.f);
+    float4 m1 = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 co1 = make_float4(0.f, 0.f, 0.f, 0.f), cc1 = co1;
     uint32_t mk2 = 0, pk2 = 0;
     {
@@ -993,7 +998,7 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
       int base = top - 32;
       bool hit = h1;
       uint32_t p = p1;
-      float2 m = m1;
+      float4 m = m1;
       float4 co = co1, c = cc1;
       h1 = (mk2 & wbits) != 0;
       if (h1) { p1 = pk2; m1 = xy[pk2]; co1 = conic_op[pk2]; cc1 = rgb[pk2]; }
@@ -1002,7 +1007,7 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
       if (top - 64 > cbeg && k2 >= cbeg) { mk2 = masks[rg.x + k2]; pk2 = vals[rg.x + k2]; }
       unsigned mask = __ballot_sync(FULL, hit);
       if (hit) {
-        my[lane].a = make_float4(m.x, m.y, co.x, co.y);
+        my[lane].a = make_float4(rel_pos(m.x, m.z, tox), rel_pos(m.y, m.w, toy), co.x, co.y);
         my[lane].b = make_float4(co.z, co.w, c.w, __uint_as_float(p));
         my[lane].c = c;
       }
@@ -1015,7 +1020,7 @@ __global__ void __launch_bounds__(32) k_render_bwd_m(const uint2* __restrict__ r
         float dx = 0.f, dy = 0.f, dp = 0.f, v5 = 0.f, v6 = 0.f, v7 = 0.f, v8 = 0.f;
         float4 ra = my[j].a, rb = my[j].b;
         if (pos < last) {
-          dx = ra.x - fx_of(px); dy = ra.y - fy_of(py);
+          dx = ra.x - lx; dy = ra.y - ly;
           float power = splat_power(ra.z, ra.w, rb.x, dx, dy);
           if (power <= 0.f && power >= rb.z) {
             float G = __expf(power);
@@ -1132,7 +1137,7 @@ __global__ void k_order_scatter(const uint2* __restrict__ ranges, int n, const u
 // entries the reverse replay walks per pixel (the backward's unit).
 __global__ void __launch_bounds__(TILE_PIX) k_blend_pairs(const uint2* __restrict__ ranges,
                                                           const uint32_t* __restrict__ vals,
-                                                          const float2* __restrict__ xy,
+                                                          const float4* __restrict__ xy,
                                                           const float4* __restrict__ conic_op, int W, int H, int TX,
                                                           int n_tiles, const uint32_t* __restrict__ n_contrib,
                                                           unsigned long long* __restrict__ counts) {
@@ -1149,9 +1154,11 @@ __global__ void __launch_bounds__(TILE_PIX) k_blend_pairs(const uint2* __restric
     int j = 0;
     for (; j < L; ++j) {
       uint32_t p = vals[rg.x + j];
-      float2 m = xy[p];
+      float4 m = xy[p];
       float4 co = conic_op[p];
-      float power = splat_power(co.x, co.y, co.z, m.x - (float)px, m.y - (float)py);
+      float dx = rel_pos(m.x, m.z, (float)(tx * TILE)) - (float)(px - tx * TILE);
+      float dy = rel_pos(m.y, m.w, (float)(ty * TILE)) - (float)(py - ty * TILE);
+      float power = splat_power(co.x, co.y, co.z, dx, dy);
       if (power > 0.f) continue;
       float alpha = fminf(ALPHA_MAX, co.w * __expf(power));
       if (alpha < ALPHA_MIN) continue;
@@ -1222,13 +1229,13 @@ int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const u
   if (sched && sched->walk_whole_lists) {                                                                          \
     k_render_fwd_seq<BW><<<dim3(grid.x * 8), 32, 0, s>>>(                                                           \
         (const uint2*)ranges, sched->tile_order, sched->job_base, sched->chunk, (float4*)sched->checkpoints,        \
-        sched->chunk_last, sorted_vals, sched->block_masks, (const float2*)proj->xy, (const float4*)proj->conic_op,                    \
+        sched->chunk_last, sorted_vals, sched->block_masks, (const float4*)proj->xy, (const float4*)proj->conic_op,                    \
         (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib);        \
   } else if (sched) {                                                                                               \
     if (cudaMemsetAsync(sched_ticket(sched), 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;          \
     k_render_fwd_m<BW><<<dim3(resident_grid(k_render_fwd_m<BW>, sched->max_jobs * 8)), 32, 0, s>>>(                 \
         (const uint2*)ranges, sched->tile_order, sched->job_base, sched->jobs, sched->chunk, (int)grid.x,            \
-        (float4*)sched->checkpoints, sched->chunk_last, sorted_vals, sched->block_masks, (const float2*)proj->xy,   \
+        (float4*)sched->checkpoints, sched->chunk_last, sorted_vals, sched->block_masks, (const float4*)proj->xy,   \
         (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2],  \
         img, final_T, n_contrib, sched_ticket(sched));                                                              \
     k_render_fwd_combine<BW><<<dim3(grid.x * 8), 32, 0, s>>>(                                                       \
@@ -1236,11 +1243,11 @@ int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const u
         sched->chunk_last, width, height, TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib);              \
     k_render_fwd_stop<BW><<<dim3((unsigned)(sched->max_jobs * 8)), 32, 0, s>>>(                                     \
         (const uint2*)ranges, sched->tile_order, sched->job_base, sched->jobs, sched->chunk, (int)grid.x,            \
-        (float4*)sched->checkpoints, sched->chunk_last, sorted_vals, sched->block_masks, (const float2*)proj->xy,    \
+        (float4*)sched->checkpoints, sched->chunk_last, sorted_vals, sched->block_masks, (const float4*)proj->xy,    \
         (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2],  \
         img, final_T, n_contrib);                                                                                   \
   } else                                                                                                            \
-    k_render_fwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, nullptr, sorted_vals, (const float2*)proj->xy, \
+    k_render_fwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, nullptr, sorted_vals, (const float4*)proj->xy, \
                                                (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, \
                                                TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib)
   if (variant == 0) { GS_FWD(8); } else if (variant == 1) { GS_FWD(16); } else { GS_FWD(4); }
@@ -1251,6 +1258,7 @@ int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const u
 GS_API int gs_render_fwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
                          int width, int height, const float* bg, float* img, float* final_T, uint32_t* n_contrib,
                          int variant, const gs_schedule* sched, gs_stream_t stream) {
+  GS_RANGE("gs_render_fwd");
   return gs_render_fwd_impl(proj, sorted_vals, ranges, n_units, width, height, bg, img, final_T, n_contrib, variant,
                             sched, (cudaStream_t)stream);
 }
@@ -1281,13 +1289,13 @@ int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const ui
       auto kb = fixed ? k_render_bwd_m<BW, false> : k_render_bwd_m<BW, true>;                                      \
       kb<<<dim3(resident_grid(kb, sched->max_jobs * 8)), 32, 0, s>>>(                                               \
           (const uint2*)ranges, sched->tile_order, sched->job_base, sched->jobs, sched->chunk,                       \
-          (const float4*)sched->checkpoints, sorted_vals, sched->block_masks, (const float2*)proj->xy,               \
+          (const float4*)sched->checkpoints, sorted_vals, sched->block_masks, (const float4*)proj->xy,               \
           (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX, TX * TY, TX * TY * n_units,   \
           bg[0], bg[1], bg[2],                                                                                       \
           img, final_T, n_contrib, dL_dimg, g2d->dxy, g2d->dconic_op, g2d->drgb, fixed, sched_ticket(sched));        \
     }                                                                                                              \
   else                                                                                                               \
-    k_render_bwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, nullptr, sorted_vals, (const float2*)proj->xy, \
+    k_render_bwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, nullptr, sorted_vals, (const float4*)proj->xy, \
                                                (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height,  \
                                                TX, TX * TY, bg[0], bg[1], bg[2], final_T, n_contrib, dL_dimg, g2d->dxy, \
                                                g2d->dconic_op, g2d->drgb, fixed)
@@ -1302,13 +1310,14 @@ int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const ui
 GS_API int gs_blend_pairs(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
                           int width, int height, const uint32_t* n_contrib, unsigned long long* d_count,
                           gs_stream_t stream) {
+  GS_RANGE("gs_blend_pairs");
   if (!proj || !proj->xy || !proj->conic_op || !sorted_vals || !ranges || !n_contrib || !d_count || n_units < 1 ||
       n_units > GS_MAX_UNITS || width <= 0 || height <= 0)
     return GS_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(d_count, 0, 3 * sizeof(unsigned long long), s) != cudaSuccess) return GS_ERR_CUDA;
   int TX = (width + TILE - 1) / TILE, TY = (height + TILE - 1) / TILE;
-  k_blend_pairs<<<dim3(TX * TY, n_units), TILE_PIX, 0, s>>>((const uint2*)ranges, sorted_vals, (const float2*)proj->xy,
+  k_blend_pairs<<<dim3(TX * TY, n_units), TILE_PIX, 0, s>>>((const uint2*)ranges, sorted_vals, (const float4*)proj->xy,
                                                             (const float4*)proj->conic_op, width, height, TX, TX * TY,
                                                             n_contrib, d_count);
   return gs_check_launch();

@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_down(const uint32_t* __restrict
 // With key_masks set, the 16-bit block mask of each (record, tile) instance
 // rides in key bits 48..63, above every bit the radix passes sort on, so the
 // sort carries it to the instance's sorted position at no extra traffic.
-__global__ void __launch_bounds__(256) k_duplicate(UnitTable U, const float2* __restrict__ xy,
+__global__ void __launch_bounds__(256) k_duplicate(UnitTable U, const float4* __restrict__ xy,
                                                    const float4* __restrict__ conic_op,
                                                    const float* __restrict__ depth,
                                                    const int* __restrict__ radius,
@@ -185,15 +185,15 @@ __global__ void __launch_bounds__(256) k_duplicate(UnitTable U, const float2* __
   if (nt == 0) return;
   int u = unit_of(U, p);
   int TX = (W + TILE - 1) / TILE, TY = (H + TILE - 1) / TILE;
-  float2 m = xy[p];
+  float4 m = xy[p];
   int x0, y0, x1, y1;
-  tile_rect(m.x, m.y, radius[p], TX, TY, x0, y0, x1, y1);
+  tile_rect(m, radius[p], TX, TY, x0, y0, x1, y1);
   uint64_t dbits = (uint64_t)__float_as_uint(depth[p]);
   uint64_t hi = (uint64_t)u << (tile_bits + 32);
   float4 box = make_float4(1.f, -1.f, 1.f, -1.f);
   if (key_masks) {
     float pm;
-    box = alpha_box(m, conic_op[p], pm);
+    box = alpha_box(make_float2(m.x, m.y), conic_op[p], pm);
   }
   int64_t o = offsets[p];
   for (int ty = y0; ty < y1; ++ty)
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ k0,
                                                 const int32_t* __restrict__ cur, int final_pass,
                                                 const uint32_t* __restrict__ d_count, int tile_bits,
                                                 int n_tiles, int TX, uint32_t* __restrict__ ranges,
-                                                uint32_t* __restrict__ out_vals, const float2* __restrict__ xy,
+                                                uint32_t* __restrict__ out_vals, const float4* __restrict__ xy,
                                                 const float4* __restrict__ conic_op, uint16_t* __restrict__ masks,
                                                 int key_masks) {
   int64_t I = *d_count;
@@ -447,7 +447,8 @@ __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ k0,
     } else if (masks) {
       // which 4x4 pixel blocks of its tile the record's alpha >= 1/255 box reaches
       float pm;
-      float4 b = alpha_box(xy[p], conic_op[p], pm);
+      float4 m = xy[p];
+      float4 b = alpha_box(make_float2(m.x, m.y), conic_op[p], pm);
       masks[k] = (uint16_t)block_mask(b, (int)(tile % (uint32_t)TX), (int)(tile / (uint32_t)TX));
     }
   }
@@ -597,7 +598,7 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
                                                d_num_instances, d_status);
   // block masks ride in the keys when unit | tile | depth leave bits 48..63 free
   int key_masks = (block_masks && key_bits <= 48) ? 1 : 0;
-  k_duplicate<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(U, (const float2*)proj->xy, (const float4*)proj->conic_op,
+  k_duplicate<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(U, (const float4*)proj->xy, (const float4*)proj->conic_op,
                                                           proj->depth, proj->radius, proj->tiles, offsets, width,
                                                           height, tile_bits, max_instances, key_masks, k0, v0);
   if (max_instances > 0) {
@@ -626,7 +627,7 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
     }
     k_ranges<<<resident_blocks(k_ranges, 256, 0, (max_instances + 255) / 256), 256, 0, s>>>(
         k0, k1, v0, v1, cur, passes, d_num_instances, tile_bits, n_tiles, TX, ranges, sorted_vals,
-        (const float2*)proj->xy, (const float4*)proj->conic_op, block_masks, key_masks);
+        (const float4*)proj->xy, (const float4*)proj->conic_op, block_masks, key_masks);
   }
   if (sched) return gs_schedule_jobs(ranges, n_tiles * U.n, ws + L.order, ws + L.jscan, sched, s);
   return gs_check_launch();
@@ -635,6 +636,7 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
 GS_API int gs_bin_sort(const gs_proj* proj, const gs_units* units, int width, int height, int64_t max_instances,
                        void* workspace, size_t workspace_bytes, uint32_t* sorted_vals, uint32_t* ranges,
                        uint32_t* d_num_instances, const gs_schedule* sched, int* d_status, gs_stream_t stream) {
+  GS_RANGE("gs_bin_sort");
   return gs_bin_sort_impl(proj, units, width, height, max_instances, workspace, workspace_bytes, sorted_vals,
                           ranges, d_num_instances, sched, d_status, (cudaStream_t)stream);
 }
@@ -659,6 +661,7 @@ GS_API int gs_merge_render(const float* params, int64_t n_gauss, int sh_degree, 
                            int64_t max_instances, void* workspace, size_t workspace_bytes, uint32_t* sorted_vals,
                            uint32_t* ranges, uint32_t* d_num_instances, float* img, float* final_T,
                            uint32_t* n_contrib, const gs_schedule* sched, int* d_status, gs_stream_t stream) {
+  GS_RANGE("gs_merge_render");
   if (!owned || owned->n_parts < 1) return GS_ERR_INVALID;
   int64_t begin = 0, count = n_gauss;
   gs_units one = {1, &begin, &count};

@@ -160,7 +160,8 @@ class Frame:
         self.n_tiles = self.TX * self.TY
         U = units.n
         f32 = dict(dtype=torch.float32, device=self.device)
-        self.xy = torch.zeros((max(P, 1), 2), **f32)
+        # pixel-space means as float pairs (x, y, x_lo, y_lo); xy64() gives x + x_lo, y + y_lo
+        self.xy = torch.zeros((max(P, 1), 4), **f32)
         self.conic_op = torch.zeros((max(P, 1), 4), **f32)
         self.rgb = torch.zeros((max(P, 1), 4), **f32)
         self.depth = torch.zeros(max(P, 1), **f32)
@@ -305,6 +306,11 @@ class Frame:
         c = cnt.tolist()
         return {"blended": int(c[0]), "fwd_pairs": int(c[1]), "bwd_pairs": int(c[2])}
 
+    def xy64(self) -> np.ndarray:
+        """Pixel-space means [P, 2] as float64: the exact sums of the float pairs (synchronises)."""
+        a = self.xy.cpu().numpy().astype(np.float64)
+        return a[:, :2] + a[:, 2:]
+
     def instances(self) -> int:
         return int(self.num_instances.item())
 
@@ -379,6 +385,8 @@ class Adam:
         self.m = torch.zeros_like(params)
         self.v = torch.zeros_like(params)
         self.step_dev = torch.zeros(1, dtype=torch.int32, device=params.device)
+        # device status word of step(): GS_ERR_NONFINITE when a gradient value was not finite
+        self.status = torch.zeros(1, dtype=torch.int32, device=params.device)
         init, fin = (lrs or LearningRates()).tables(sh_degree, extent)
         self.lr_init = np.ascontiguousarray(init.reshape(-1))
         self.lr_final = np.ascontiguousarray(fin.reshape(-1))
@@ -395,7 +403,7 @@ class Adam:
                                          _ptr(self.v), self.lr_init.ctypes.data_as(_lib.c_f32p),
                                          self.lr_final.ctypes.data_as(_lib.c_f32p), self.lr_steps, self.b1, self.b2,
                                          self.eps, _ptr(self.step_dev), _ptr(frame.grads) if keep_grads else None,
-                                         _stream()), "gs_project_bwd_adam")
+                                         _ptr(frame.status), _stream()), "gs_project_bwd_adam")
         check(self.L.gs_step_advance(_ptr(self.step_dev), _stream()), "gs_step_advance")
 
     def state_dict(self) -> dict:
@@ -412,5 +420,5 @@ class Adam:
         check(self.L.gs_adam_step(_ptr(self.params), _ptr(grads), _ptr(self.m), _ptr(self.v), n, npl,
                                   self.lr_init.ctypes.data_as(_lib.c_f32p), self.lr_final.ctypes.data_as(_lib.c_f32p),
                                   self.lr_steps, self.b1, self.b2, self.eps, _ptr(self.step_dev), int(zero_grad),
-                                  _stream()), "gs_adam_step")
+                                  _ptr(self.status), _stream()), "gs_adam_step")
         check(self.L.gs_step_advance(_ptr(self.step_dev), _stream()), "gs_step_advance")

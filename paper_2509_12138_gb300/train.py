@@ -4,11 +4,10 @@
   (projection, sort, blend, loss, backward, Adam launched one by one).
 * ``BatchedTrainer`` -- the batched form (paper Sec. II trains partitions
   independently; here all partitions and a batch of views per partition are
-  one set of units): every kernel of a step covers all (partition, view)
-  units, and the whole step is captured once in a CUDA graph and replayed.
-
-Each step draws its views from the training set; the per-step GT images,
-masks and cameras are copied into static buffers that the graph reads.
+  one set of units): one gs_train_batch call runs a step of every
+  (partition, view) unit, choosing the views on the device from the step
+  counter, so the call is captured once in a CUDA graph and every later step
+  is a replay with no host work.
 """
 from __future__ import annotations
 
@@ -18,7 +17,11 @@ import time
 import numpy as np
 import torch
 
-from .raster import CHUNK, Adam, Frame, LearningRates, Owned, Units, pack_cameras
+import ctypes as C
+
+from . import _lib
+from ._lib import GsTrainBatchDesc, check
+from .raster import CHUNK, Adam, Frame, LearningRates, Owned, Units, _ptr, _stream, pack_cameras
 
 CAM_BYTES = 96
 
@@ -190,14 +193,15 @@ class BatchedTrainer:
         self.off = np.asarray(part_offsets, np.int64)
         self.n_parts = len(self.off) - 1
         self.vps = int(views_per_step)
-        self.cams = cams_dev
-        self.gt, self.mask = gt, mask
+        self.cams = cams_dev.contiguous()
+        self.gt, self.mask = gt.contiguous(), mask.contiguous()
         self.views = list(train_views)
         self.lam, self.bg = lam, tuple(bg)
         self.use_graph = use_graph
         N = params.shape[1]
         H, W = gt.shape[-2], gt.shape[-1]
         dev = params.device
+        self.L = _lib.load()
         self.units = Units.partitions(self.off, self.vps)
         U = self.units.n
         self.frame = Frame(N, self.units, W, H, sh_degree, device=dev, variant=variant, deterministic=deterministic,
@@ -206,9 +210,12 @@ class BatchedTrainer:
         self.cams_step = torch.zeros(U * CAM_BYTES, dtype=torch.uint8, device=dev)
         self.gt_step = torch.zeros((U, 3, H, W), dtype=torch.float32, device=dev)
         self.mask_step = torch.zeros((U, H, W), dtype=torch.uint8, device=dev)
+        self.train_views = torch.tensor(self.views, dtype=torch.int32, device=dev)
+        self._t_probe = torch.zeros(1, dtype=torch.int32, device=dev)
         self.t = 0
         self.graph = None
         self.keep_grads = False  # also write the parameter gradient (for inspection)
+        self.desc = None
         # instance capacity: the largest need over a sweep of the training views
         need = 0
         for t0 in range(0, len(self.views), max(1, len(self.views) // 4)):
@@ -217,32 +224,61 @@ class BatchedTrainer:
         self.frame.set_capacity(int(need * capacity_slack) + 4096)
 
     def view_of(self, t: int, k: int, j: int) -> int:
-        """View of unit (partition k, slot j) at step t (staggered across partitions)."""
+        """View of unit (partition k, slot j) at step t (staggered across partitions); gs_train_batch applies
+        the same rule on the device."""
         return self.views[(t * self.vps + j + k) % len(self.views)]
 
+    def _build_desc(self):
+        """The gs_train_batch descriptor: pointers to this trainer's, its frame's and its optimiser's buffers
+        (rebuilt when the frame's capacity changes)."""
+        fr, opt = self.frame, self.opt
+        H, W = fr.H, fr.W
+        d = GsTrainBatchDesc()
+        d.params, d.adam_m, d.adam_v = self.params.data_ptr(), opt.m.data_ptr(), opt.v.data_ptr()
+        d.n_gauss, d.sh_degree, d.views_per_step = self.params.shape[1], self.deg, self.vps
+        d.units = C.pointer(self.units.struct)
+        d.cam_pool, d.gt_pool, d.mask_pool = self.cams.data_ptr(), self.gt.data_ptr(), self.mask.data_ptr()
+        d.train_views, d.n_views, d.n_train = self.train_views.data_ptr(), self.gt.shape[1], len(self.views)
+        d.width, d.height, d.lambda_ssim = W, H, float(self.lam)
+        d.bg = (C.c_float * 3)(*[float(x) for x in self.bg])
+        d.lr_init = opt.lr_init.ctypes.data_as(_lib.c_f32p)
+        d.lr_final = opt.lr_final.ctypes.data_as(_lib.c_f32p)
+        d.lr_steps, d.beta1, d.beta2, d.eps = opt.lr_steps, opt.b1, opt.b2, opt.eps
+        d.d_step = opt.step_dev.data_ptr()
+        d.cams_step, d.gt_step, d.mask_step = (self.cams_step.data_ptr(), self.gt_step.data_ptr(),
+                                               self.mask_step.data_ptr())
+        d.proj = C.pointer(fr.proj)
+        d.max_instances, d.sort_ws, d.sort_ws_bytes = fr.cap, fr.sort_ws.data_ptr(), fr.sort_ws.numel()
+        d.sorted_vals, d.ranges, d.d_num_instances = (fr.sorted_vals.data_ptr(), fr.ranges.data_ptr(),
+                                                      fr.num_instances.data_ptr())
+        if fr.use_masks:
+            fr.sched.walk_whole_lists = 1 if fr.walk_whole_lists else 0
+            d.sched = C.pointer(fr.sched)
+        d.img, d.final_T, d.n_contrib = fr.img.data_ptr(), fr.final_T.data_ptr(), fr.n_contrib.data_ptr()
+        d.loss_ws, d.loss_ws_bytes = fr.loss_ws.data_ptr(), fr.loss_ws.numel()
+        d.d_loss, d.dL_dimg = fr.loss_val.data_ptr(), fr.dimg.data_ptr()
+        d.g2d = C.pointer(fr.g2d)
+        d.grads = fr.grads.data_ptr() if self.keep_grads else None
+        d.variant = fr.variant
+        self.desc = d
+        self._desc_key = (fr.cap, self.keep_grads, fr.use_masks, fr.walk_whole_lists)
+
     def _load(self, t: int):
-        u = 0
-        for k in range(self.n_parts):
-            for j in range(self.vps):
-                v = self.view_of(t, k, j)
-                self.cams_step[u * CAM_BYTES:(u + 1) * CAM_BYTES].copy_(self.cams[v * CAM_BYTES:(v + 1) * CAM_BYTES])
-                self.gt_step[u].copy_(self.gt[k, v])
-                self.mask_step[u].copy_(self.mask[k, v])
-                u += 1
+        """The step buffers of step t (gs_gather_views on the device), for inspection and capacity sizing."""
+        if self.desc is None:
+            self._build_desc()
+        self._t_probe.fill_(int(t))
+        check(self.L.gs_gather_views(C.byref(self.desc), _ptr(self._t_probe), _stream()), "gs_gather_views")
 
     def _chain(self):
         fr = self.frame
-        fr.preprocess(self.params, self.cams_step)
-        fr.sort()
-        fr.render(self.bg)
-        fr.loss(self.gt_step, self.mask_step, self.lam)
-        fr.blend_backward(self.bg)
-        self.opt.fused_step(fr, self.cams_step, self.keep_grads)
+        if self.desc is None or self._desc_key != (fr.cap, self.keep_grads, fr.use_masks, fr.walk_whole_lists):
+            self._build_desc()
+        check(self.L.gs_train_batch(C.byref(self.desc), _ptr(fr.status), _stream()), "gs_train_batch")
 
     def capture(self):
         """Run step t eagerly (on a side stream, so lazy initialisation happens outside the capture), then
-        record the whole training step (all units) as a CUDA graph for the following steps."""
-        self._load(self.t)
+        record the whole training step (one gs_train_batch call) as a CUDA graph for the following steps."""
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
@@ -255,10 +291,10 @@ class BatchedTrainer:
         self.graph = g
 
     def step(self):
+        """One training step of every unit; its views follow from the device step counter."""
         if self.use_graph and self.graph is None:
             self.capture()
             return
-        self._load(self.t)
         if self.use_graph:
             self.graph.replay()
         else:

@@ -16,10 +16,18 @@ def gauss64(g):
 
 
 def rects(xy, radius, W, H):
-    """Tile rectangles from (x, y, radius) with floor((u - r)/16), floor((u + r + 15)/16), clamped."""
+    """Tile rectangles with floor((u - r)/16), floor((u + r + 15)/16), clamped.  ``xy`` is [n, 2] exact
+    float64 positions, or the kernels' [n, 4] float pairs (x, y, x_lo, y_lo), whose floor is taken exactly."""
     TX, TY = (W + TILE - 1) // TILE, (H + TILE - 1) // TILE
-    fu = np.floor(xy[:, 0]).astype(np.int64)
-    fv = np.floor(xy[:, 1]).astype(np.int64)
+    xy = np.asarray(xy)
+    if xy.shape[1] == 4:
+        hi, lo = xy[:, :2].astype(np.float64), xy[:, 2:].astype(np.float64)
+        f = np.floor(hi)
+        fl = (f - ((f == hi) & (lo < 0))).astype(np.int64)
+        fu, fv = fl[:, 0], fl[:, 1]
+    else:
+        fu = np.floor(xy[:, 0]).astype(np.int64)
+        fv = np.floor(xy[:, 1]).astype(np.int64)
     r = radius.astype(np.int64)
     x0 = np.clip((fu - r) // TILE, 0, TX)
     y0 = np.clip((fv - r) // TILE, 0, TY)
@@ -28,6 +36,17 @@ def rects(xy, radius, W, H):
     out = np.stack([x0, y0, x1, y1], 1)
     out[r <= 0] = 0
     return out
+
+
+def discrete_mismatch(o_proj, g_xy4, g_radius, g_tiles, W, H):
+    """Gaussians whose visibility, radius, tile rectangle or tile count differ between the kernels and the
+    oracle.  Returns (mismatch mask, True where every mismatch is a decision the oracle flags as a float32
+    near-tie)."""
+    r_gpu = rects(g_xy4, g_radius, W, H)
+    vis_o, vis_g = o_proj["radius"] > 0, g_radius > 0
+    mism = (vis_o != vis_g) | (g_radius != o_proj["radius"]) | np.any(r_gpu != o_proj["rect"], axis=1) \
+        | (g_tiles != o_proj["tiles"])
+    return mism, bool(np.all(o_proj["unstable"][mism] != 0))
 
 
 def run_gpu(g, cams, deg, bg, gt=None, mask=None, lam=0.2, backward=True, units=None, max_instances=None):
@@ -59,7 +78,8 @@ def run_gpu(g, cams, deg, bg, gt=None, mask=None, lam=0.2, backward=True, units=
     out["img"] = fr.img.cpu().numpy()
     out["final_T"] = fr.final_T.cpu().numpy()
     out["n_contrib"] = fr.n_contrib.cpu().numpy()
-    out["xy"] = fr.xy.cpu().numpy()
+    out["xy4"] = fr.xy.cpu().numpy()
+    out["xy"] = fr.xy64()
     out["conic_op"] = fr.conic_op.cpu().numpy()
     out["rgb"] = fr.rgb.cpu().numpy()
     out["depth"] = fr.depth.cpu().numpy()
@@ -69,18 +89,19 @@ def run_gpu(g, cams, deg, bg, gt=None, mask=None, lam=0.2, backward=True, units=
     return out
 
 
-def exclusion_mask(o_proj, g_xy, g_radius, tie_tiles, margin, W, H, margin_tol=1e-5):
-    """Pixels excluded from image comparison: near-threshold pixels (oracle margin), and tiles touched by
-    a Gaussian whose radius or rectangle differs between FP32 and FP64.  (The list order itself is decided
-    on the float32 depth key on both sides, and equal keys fall back to the index, so it needs no exclusion.)"""
+def exclusion_mask(o_proj, g_xy4, g_radius, g_tiles, margin, W, H, margin_tol=1e-5):
+    """Pixels excluded from image comparison, and their causes: pixels where some blend decision of the
+    oracle sits within ``margin_tol`` (relative) of its threshold, and the tiles touched by a Gaussian whose
+    visibility, radius or rectangle differs between the kernels and the oracle (each such Gaussian must be
+    a decision the oracle flags as a float32 near-tie).  Returns (pixels, n differing Gaussians, all flagged)."""
     TX, TY = (W + TILE - 1) // TILE, (H + TILE - 1) // TILE
     bad_tile = np.zeros((TY, TX), bool)
-    r_gpu = rects(g_xy.astype(np.float64), g_radius, W, H)
+    mism, flagged = discrete_mismatch(o_proj, g_xy4, g_radius, g_tiles, W, H)
+    r_gpu = rects(g_xy4, g_radius, W, H)
     r_orc = o_proj["rect"].astype(np.int64)
-    diff = np.nonzero((g_radius != o_proj["radius"]) | np.any(r_gpu != r_orc, axis=1))[0]
-    for i in diff:
+    for i in np.nonzero(mism)[0]:
         for r in (r_gpu[i], r_orc[i]):
             bad_tile[r[1]:r[3], r[0]:r[2]] = True
     pix = np.kron(bad_tile, np.ones((TILE, TILE), bool))[:H, :W]
     pix |= margin < margin_tol
-    return pix, len(diff)
+    return pix, int(mism.sum()), flagged

@@ -57,3 +57,31 @@ def test_device_code_is_sm_103a():
     if out.returncode != 0:
         pytest.skip("cuobjdump unavailable")
     assert "sm_103a" in out.stdout
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding passes by pointer has the header's size and field offsets (a C program
+    compiled with gcc against include/gs.h prints them)."""
+    import shutil
+    from paper_2509_12138_gb300 import _lib
+    if not shutil.which("gcc"):
+        pytest.skip("gcc unavailable")
+    structs = {"gs_camera": _lib.GsCamera, "gs_proj": _lib.GsProj, "gs_grad2d": _lib.GsGrad2d,
+               "gs_schedule": _lib.GsSchedule, "gs_units": _lib.GsUnits, "gs_owned": _lib.GsOwned,
+               "gs_densify_cfg": _lib.GsDensifyCfg, "gs_train_batch_desc": _lib.GsTrainBatchDesc}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gs.h"', 'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.split("\n") if l)
+    for cname, py in structs.items():
+        assert int(got[cname]) == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)

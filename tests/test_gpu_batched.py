@@ -56,8 +56,8 @@ def test_merge_render_parity(use_masks, chunk, whole):
     o = oracle.render(gauss64(sub), cam, BG)
     op = oracle.project(gauss64(sub), cam)
     xy = fr.xy.cpu().numpy()[keep]
-    excl, _ = exclusion_mask(op, xy, rad[keep], o["tie_tiles"], o["margin"], W, H)
-    assert excl.mean() < 0.01
+    excl, _, flagged = exclusion_mask(op, xy, rad[keep], fr.tiles.cpu().numpy()[keep], o["margin"], W, H)
+    assert flagged and excl.mean() < 0.01
     err = np.abs(fr.img.cpu().numpy()[0] - o["img"]).max(axis=0)
     assert err[~excl].max() <= 1e-4
 
@@ -111,6 +111,52 @@ def test_batched_partition_units_parity():
     assert float(fr.loss_val.item()) == pytest.approx(ref_loss, rel=1e-4)
     scale = np.abs(ref_grad).max()
     assert np.abs(grads - ref_grad).max() <= 1e-3 * scale
+
+
+def test_train_batch_abi_matches_oracle_per_unit():
+    """gs_train_batch called through the C ABI: the views it gathers on the device for step t, the loss and
+    the parameter gradient of one batched step over 3 partitions x 2 views equal the oracle summed per unit,
+    and the device step counter advances; a second call gathers the views of step t + 1."""
+    import ctypes as C
+    from paper_2509_12138_gb300 import _lib
+    init, part, cams, gt, mask = _partitioned(seed=3)
+    deg = 1
+    params = gs.pack_params(init, deg)
+    tr = T.BatchedTrainer(params, deg, part.offsets, gs.pack_cameras(cams), torch.from_numpy(gt).cuda(),
+                          torch.from_numpy(mask).cuda(), list(range(1, 6)), views_per_step=2, use_graph=False)
+    tr.keep_grads = True
+    tr._build_desc()
+    L = _lib.load()
+    p0 = gs.unpack_params(params, deg)
+    for t in range(2):
+        rc = L.gs_train_batch(C.byref(tr.desc), C.c_void_p(tr.frame.status.data_ptr()),
+                              C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == 0
+        torch.cuda.synchronize()
+        assert tr.frame.read_status() == 0
+        assert int(tr.opt.step_dev.item()) == t + 1
+        U = tr.units.n
+        grads = gs.unpack_grads(tr.frame.grads, deg)
+        ref_loss, ref_grad = 0.0, np.zeros_like(grads)
+        for k in range(part.n):
+            s_, e_ = part.offsets[k], part.offsets[k + 1]
+            sub = gauss64(_subset(p0, np.arange(s_, e_)))
+            for j in range(2):
+                v = tr.view_of(t, k, j)
+                u = k * 2 + j
+                # the gathered camera, ground truth and mask are those of view v of partition k
+                assert torch.equal(tr.gt_step[u].cpu(), torch.from_numpy(gt[k, v]))
+                assert torch.equal(tr.mask_step[u].cpu(), torch.from_numpy(mask[k, v]))
+                assert torch.equal(tr.cams_step[u * 96:(u + 1) * 96], tr.cams[v * 96:(v + 1) * 96])
+                if t == 0:  # the oracle from the (synthetic) initial parameters
+                    r = oracle.loss_and_grads(sub, oracle.camera_block(cams, v), BG, gt[k, v].astype(np.float64),
+                                              mask[k, v], 0.2)
+                    ref_loss += r["loss"] / U
+                    ref_grad[s_:e_] += r["grads"] / U
+        if t == 0:
+            assert float(tr.frame.loss_val.item()) == pytest.approx(ref_loss, rel=1e-4)
+            scale = np.abs(ref_grad).max()
+            assert np.abs(grads - ref_grad).max() <= 1e-3 * scale
 
 
 def test_graph_replay_matches_eager():

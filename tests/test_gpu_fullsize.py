@@ -1,105 +1,102 @@
 """Parity at the benchmark's full size, in the launch configuration the benchmark times.
 
-10M Gaussians (SH3, 16-mode interface), 1920x1080, the benchmark's Frame (instance capacity 6N, blend
-schedule with 1024-entry chunks, chunk-parallel forward) after a few training steps.  The oracle cannot
-render the whole view, so it renders tile-aligned 64x64 windows (same intrinsics, principal point shifted by
-the window's origin) from the Gaussians that reach them: among them the window holding the view's longest
-tile list.  Compared there: the tile lists (bit-exact, oracle binning fed the GPU's float32 projections),
-pixel values, final T and n_contrib (outside near-threshold pixels), and the screen-space gradients of every
-Gaussian whose tile rectangle lies inside the window (all of its pixels are in the window)."""
+10M Gaussians (SH3) on the 16-mode interface, 1920x1080, the benchmark's Frame (instance capacity 6N,
+blend schedule with 1024-entry chunks, chunk-parallel forward).  Inputs are synthetic and seeded: the plain
+initialisation perturbed the way training moves it (anisotropic scales, random rotations, opacities, view-
+dependent colour), and a seeded upstream image gradient for the backward.  The oracle cannot render the
+whole view, so it renders tile-aligned 64x64 windows (same intrinsics, principal point shifted by the
+window's origin) from the Gaussians its own FP64 projection puts there; the heaviest window is found from
+the oracle's tile counts.  Compared there, end to end (FP64 oracle from the parameters vs the kernels):
+the tile lists, pixel values, final T and n_contrib, and the screen-space gradients of every Gaussian whose
+tile rectangle lies inside the window.  Exclusions (decisions within 1e-5 of a threshold, early stops within
+four times the oracle's float32 error bound of T, tiles touched by a Gaussian whose float32 decisions
+differ, each such decision flagged by the oracle) are counted and bounded; every compared gradient is
+within 1e-3 of its group's scale."""
+import math
+
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import paper_2509_12138_gb300 as gs
+import synth
 from paper_2509_12138_gb300 import workload
-from tests.gpu_util import exclusion_mask, gauss64, rects
+from tests.gpu_util import gauss64, rects
 
 pytestmark = pytest.mark.gpu
 N, W, H, WIN = 10_000_000, 1920, 1080, 64
 IMG_TOL, GRAD_TOL = 1e-4, 1e-3
-# Walks of tens of thousands of entries over thin splats: float32 conics of ill-conditioned 2D covariances
-# carry up to ~3e-4 relative error (an alpha 1.4e-4 from 1/255 was seen decided the other way), so decisions
-# within 3e-4 of a threshold are not compared (1e-5 in the small tests), and neither are early stops within
-# four times the float32 error bound of T (oracle t_err).
-MARGIN_TOL = 3e-4
+MARGIN_TOL = 1e-5
+TW = WIN // 16
+
+
+def perturbed_interface(n, seed=0):
+    """The benchmark's 10M plain initialisation, perturbed by seeded draws: log-scales + N(0, 0.25),
+    uniformly random rotations, opacities sigmoid(U(-2.5, 2.5)), SH rest N(0, 0.05)."""
+    pts, nrm, _ = synth.interface_points(n, 16, seed)
+    o = synth.spatial_order(pts)
+    pts, nrm = pts[o], nrm[o]
+    col = synth.lambert_colors(pts, nrm)
+    g = workload.plain_init(pts, col, math.log(workload.spacing_estimate(nrm, n)), 3)
+    s = synth.streams(seed + 100, ["ls", "q", "op", "sh"])
+    g["log_scales"] = (g["log_scales"] + s["ls"].normal(0.0, 0.25, (n, 3))).astype(np.float32)
+    q = s["q"].normal(0.0, 1.0, (n, 4))
+    g["quats"] = (q / np.linalg.norm(q, axis=1, keepdims=True)).astype(np.float32)
+    g["logit_opacity"] = s["op"].uniform(-2.5, 2.5, n).astype(np.float32)
+    g["sh"][:, 1:, :] = s["sh"].normal(0.0, 0.05, (n, 15, 3)).astype(np.float32)
+    return g
 
 
 @pytest.fixture(scope="module")
 def full():
-    scene = workload.isosurface_scene(N, 16, 8, W, H, sh_degree=3, seed=0)
-    params = gs.pack_params(scene.init, 3)
-    frame = gs.Frame(N, gs.Units.single(N), W, H, 3, max_instances=6 * N)
-    opt = gs.Adam(params, 3, extent=1.0, lr_steps=7000)
-    bg = scene.bg
-    for v in range(3):  # a few optimiser steps, as the benchmark's warm-up
-        cam = scene.cam(v)
-        frame.preprocess(params, cam)
-        frame.sort()
-        frame.render(bg)
-        frame.loss(scene.gt[v:v + 1], scene.mask[v:v + 1], 0.2)
-        frame.blend_backward(bg)
-        opt.fused_step(frame, cam)
+    g = perturbed_interface(N)
+    cams = synth.orbital_cameras(8, 1.5, center=(0.5, 0.5, 0.5), width=W, height=H)
     v = 5
-    cam = scene.cam(v)
-    frame.preprocess(params, cam)
+    camd = gs.pack_cameras(cams)[v * 96:(v + 1) * 96]
+    dimg = synth.streams(7, ["dimg"])["dimg"].uniform(-1.0, 1.0, (1, 3, H, W)).astype(np.float32)
+    params = gs.pack_params(g, 3)
+    frame = gs.Frame(N, gs.Units.single(N), W, H, 3, max_instances=6 * N)
+    bg = (1.0, 1.0, 1.0)
+    frame.preprocess(params, camd)
     frame.sort()
     frame.render(bg)
-    frame.loss(scene.gt[v:v + 1], scene.mask[v:v + 1], 0.2)
-    frame.blend_backward(bg)
+    frame.blend_backward(bg, torch.from_numpy(dimg).cuda())
     torch.cuda.synchronize()
     assert frame.read_status() == 0
     vals, ranges = frame.sorted_lists()
     out = dict(img=frame.img[0].cpu().numpy(), final_T=frame.final_T[0].cpu().numpy(),
-               n_contrib=frame.n_contrib[0].cpu().numpy(), dimg=frame.dimg[0].cpu().numpy(),
-               xy=frame.xy.cpu().numpy(), radius=frame.radius.cpu().numpy(), depth=frame.depth.cpu().numpy(),
+               n_contrib=frame.n_contrib[0].cpu().numpy(), dimg=dimg[0], xy4=frame.xy.cpu().numpy(),
+               radius=frame.radius.cpu().numpy(), tiles=frame.tiles.cpu().numpy(),
                dxy=frame.dxy.cpu().numpy(), dco=frame.dco.cpu().numpy(), drgb=frame.drgb.cpu().numpy(),
-               vals=vals, ranges=ranges, g=gauss64(gs.unpack_params(params, 3)),
-               cam=oracle.camera_block(scene.cams, v), bg=np.asarray(bg, np.float64))
-    del frame, opt, params, scene
+               vals=vals, ranges=ranges, g=gauss64(g), cam=oracle.camera_block(cams, v),
+               bg=np.asarray(bg, np.float64))
+    del frame, params
     torch.cuda.empty_cache()
+    # the oracle's own projection of the whole view: tile counts pick the windows
+    o = oracle.project(out["g"], out["cam"])
+    out["o_rect"], out["o_unstable"] = o["rect"], o["unstable"]
+    TX, TY = (W + 15) // 16, (H + 15) // 16
+    cnt = np.zeros((TY + 1, TX + 1), np.int64)
+    r = o["rect"][o["radius"] > 0]
+    np.add.at(cnt, (r[:, 1], r[:, 0]), 1)
+    np.add.at(cnt, (r[:, 3], r[:, 0]), -1)
+    np.add.at(cnt, (r[:, 1], r[:, 2]), -1)
+    np.add.at(cnt, (r[:, 3], r[:, 2]), 1)
+    out["tile_counts"] = cnt.cumsum(0).cumsum(1)[:TY, :TX].reshape(-1)
     return out
 
 
 def _windows(full):
     TX = (W + 15) // 16
-    L = full["ranges"][:, 1] - full["ranges"][:, 0]
-    heavy = int(np.argmax(L))
+    L = full["tile_counts"]
     rng = np.random.default_rng(0)
-    covered = np.nonzero(L > 0)[0]
-    picks = [heavy] + [int(t) for t in rng.choice(covered, 2, replace=False)]
+    picks = [int(np.argmax(L))] + [int(t) for t in rng.choice(np.nonzero(L > 0)[0], 2, replace=False)]
     out = []
     for t in picks:
         tx, ty = t % TX, t // TX
-        x0 = min(max(tx - 1, 0), (W - WIN) // 16) * 16
-        y0 = min(max(ty - 1, 0), (H - WIN) // 16) * 16
-        out.append((x0, y0))
+        out.append((min(max(tx - 1, 0), (W - WIN) // 16) * 16, min(max(ty - 1, 0), (H - WIN) // 16) * 16))
     return out, int(L.max())
-
-
-def _exclusion(op, xy_w, rad_gpu, margin):
-    """Pixels not compared: near-threshold pixels (oracle margin), and, for each Gaussian whose float32 tile
-    rectangle differs from the FP64 one, the pixels of the tiles in which only one side lists it where its
-    alpha could reach 1/255 (half of it, for slack).  Lists with tens of thousands of entries always hold some
-    such Gaussian, so excluding whole tiles would exclude most of a heavy window."""
-    bad = margin < MARGIN_TOL
-    r_gpu = rects(xy_w.astype(np.float64), rad_gpu, WIN, WIN)
-    r_orc = op["rect"].astype(np.int64)
-    yy, xx = np.mgrid[0:WIN, 0:WIN].astype(np.float64)
-    for i in np.nonzero(np.any(r_gpu != r_orc, axis=1))[0]:
-        only = np.zeros((WIN // 16, WIN // 16), bool)
-        for r, s in ((r_gpu[i], 1), (r_orc[i], -1)):
-            m = np.zeros_like(only)
-            m[r[1]:r[3], r[0]:r[2]] = True
-            only ^= m
-        if not only.any():
-            continue
-        a, b, c = op["conic"][i]
-        dx, dy = op["xy"][i][0] - xx, op["xy"][i][1] - yy
-        alpha = op["opacity"][i] * np.exp(-0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy)
-        bad |= np.kron(only, np.ones((16, 16), bool)) & (alpha >= 0.5 / 255.0)
-    return bad
 
 
 def _window_cam(cam, x0, y0):
@@ -110,6 +107,12 @@ def _window_cam(cam, x0, y0):
     return c
 
 
+def _overlap(r, x0, y0, grow=0):
+    tx0, ty0 = x0 // 16, y0 // 16
+    return ((r[:, 0] - grow < tx0 + TW) & (r[:, 2] + grow > tx0) & (r[:, 1] - grow < ty0 + TW)
+            & (r[:, 3] + grow > ty0))
+
+
 @pytest.mark.parametrize("k", [0, 1, 2])
 def test_window_parity(full, k):
     wins, longest = _windows(full)
@@ -117,73 +120,98 @@ def test_window_parity(full, k):
     x0, y0 = wins[k]
     cw = _window_cam(full["cam"], x0, y0)
     g = full["g"]
-    # Gaussians that reach the window by the oracle's FP64 projection or by the GPU's float32 one
-    TW = WIN // 16
-    r_full = rects(full["xy"].astype(np.float64), full["radius"], W, H)
-    gpu_reach = ((full["radius"] > 0) & (r_full[:, 0] < x0 // 16 + TW) & (r_full[:, 2] > x0 // 16)
-                 & (r_full[:, 1] < y0 // 16 + TW) & (r_full[:, 3] > y0 // 16))
-    sel = np.nonzero(gpu_reach | (oracle.project(g, cw)["tiles"] > 0))[0]
+    # Gaussians the oracle's projection puts in the window, and flagged ones next to it
+    sel = np.nonzero(_overlap(full["o_rect"], x0, y0) | ((full["o_unstable"] != 0) & _overlap(full["o_rect"], x0, y0, 1)))[0]
     sub = {key: val[sel] for key, val in g.items()}
-    # lists: the oracle's binning of the GPU's own float32 projections equals the GPU's lists for the window
-    xy_w = full["xy"][sel].astype(np.float64) - np.array([x0, y0], np.float64)
-    L = oracle.bin_sort(xy_w, full["radius"][sel], full["depth"][sel].astype(np.float64), WIN, WIN)
+    op = oracle.project(sub, cw)
+    o = oracle.render(sub, cw, full["bg"])
     TX = (W + 15) // 16
+    # lists, end to end: the GPU's window tiles equal the oracle's lists from its own projection, except tiles
+    # holding a Gaussian whose float32 decisions differ (each one flagged)
+    a4 = full["xy4"][sel].astype(np.float64)
+    xy_w = a4[:, :2] + a4[:, 2:] - np.array([x0, y0], np.float64)  # exact: float pairs and integer shifts
+    rad_g = full["radius"][sel]
+    r_g, r_o = rects(xy_w, rad_g, WIN, WIN), op["rect"]
+    mism = ((op["radius"] > 0) != (rad_g > 0)) | (op["radius"] != rad_g) | np.any(r_g != r_o, axis=1)
+    assert np.all(op["unstable"][mism] != 0), sel[np.nonzero(mism & (op["unstable"] == 0))[0][:5]]
+    L = oracle.bin_sort(op["xy"], op["radius"], op["depth"], WIN, WIN)
+    in_sel = np.zeros(N, bool)
+    in_sel[sel] = True
+    bad_tiles = np.zeros((TW, TW), bool)
     for wy in range(TW):
         for wx in range(TW):
             t = (y0 // 16 + wy) * TX + (x0 // 16 + wx)
             a, b = full["ranges"][t]
             oa, ob = L["ranges"][wy * TW + wx]
-            assert np.array_equal(full["vals"][a:b], sel[L["idx"][oa:ob]])
-    # image, final T, n_contrib
-    o = oracle.render(sub, cw, full["bg"])
-    op = oracle.project(sub, cw)
+            gl, ol = full["vals"][a:b], sel[L["idx"][oa:ob]]
+            if len(gl) == len(ol) and np.array_equal(gl, ol):
+                continue
+            assert np.all(in_sel[gl]), "a GPU list holds a Gaussian the oracle does not place near the window"
+            diff = np.setxor1d(gl, ol)
+            if len(diff):
+                assert np.all(op["unstable"][np.searchsorted(sel, diff)] != 0), \
+                    f"tile ({wx},{wy}) differs without a flagged Gaussian"
+            else:
+                # the same entries in another order: only depth keys within one float32 ulp may swap
+                kg = op["depth"][np.searchsorted(sel, gl)].astype(np.float32)
+                ko = op["depth"][np.searchsorted(sel, ol)].astype(np.float32)
+                at = gl != ol
+                assert np.all(np.abs(kg[at] - ko[at]) <= np.spacing(np.maximum(kg[at], ko[at]))), \
+                    f"tile ({wx},{wy}) reordered beyond a near-tie of the depth keys"
+            bad_tiles[wy, wx] = True
+    # pixels: outside near-threshold decisions, float32-limited early stops and tiles of flagged Gaussians
     stop = o["stop_margin"] < 4.0 * o["t_err"]
-    excl = _exclusion(op, xy_w, full["radius"][sel], o["margin"]) | stop
-    assert excl.mean() < 0.15, excl.mean()
-    # float32 compositing over thousands of entries: |dT| <= t_err T and |dC| <= t_err (oracle's bound on
-    # the relative float32 error of T), so a pixel may differ by 2 t_err on top of the small tests' 1e-4
+    excl = (o["margin"] < MARGIN_TOL) | stop | np.kron(bad_tiles, np.ones((16, 16), bool))
+    for i in np.nonzero(mism)[0]:
+        for r in (r_g[i], r_o[i]):
+            excl[16 * r[1]:16 * r[3], 16 * r[0]:16 * r[2]] = True
     img = full["img"][:, y0:y0 + WIN, x0:x0 + WIN]
-    tol = IMG_TOL + 2.0 * o["t_err"]
-    assert np.all((np.abs(img - o["img"]).max(axis=0) <= tol)[~excl])
+    # float32 compositing over thousands of entries: |dT| <= t_err T and |dC| <= t_err (the oracle's bound on
+    # the relative float32 error of T), so a pixel may differ by 2 t_err on top of the small tests' 1e-4
+    err_img = np.abs(img - o["img"]).max(axis=0)
     dT = np.abs(full["final_T"][y0:y0 + WIN, x0:x0 + WIN] - o["final_T"])
-    over = (dT > IMG_TOL + o["t_err"] * o["final_T"]) & ~excl
-    if over.any():
-        y, x = np.argwhere(over)[0]
-        pytest.fail(f"final_T at ({y},{x}): gpu {full['final_T'][y0 + y, x0 + x]} oracle {o['final_T'][y, x]} "
-                    f"t_err {o['t_err'][y, x]} margin {o['margin'][y, x]} stop_margin {o['stop_margin'][y, x]} "
-                    f"n_contrib gpu {full['n_contrib'][y0 + y, x0 + x]} oracle {o['n_contrib'][y, x]} "
-                    f"pixels over {int(over.sum())}")
-    # n_contrib is a position in the tile's list: compare it in the tiles whose lists agree entry for entry
-    # (no Gaussian with a different float32 / FP64 rectangle), outside near-threshold pixels
-    tile_excl, _ = exclusion_mask(op, xy_w.astype(np.float32), full["radius"][sel], o["tie_tiles"], o["margin"],
-                                  WIN, WIN, margin_tol=MARGIN_TOL)
-    tile_excl |= stop
-    assert tile_excl.mean() < 0.5
-    assert np.array_equal(full["n_contrib"][y0:y0 + WIN, x0:x0 + WIN][~tile_excl], o["n_contrib"][~tile_excl])
+    nc_ok = full["n_contrib"][y0:y0 + WIN, x0:x0 + WIN] == o["n_contrib"]
+    print(f"window {k} ({x0},{y0}): {len(sel)} Gaussians, longest list {longest}; excluded pixels: "
+          f"{int((o['margin'] < MARGIN_TOL).sum())} near a threshold, {int(stop.sum())} float32-limited stops, "
+          f"{int(bad_tiles.sum())} tiles with flagged list differences ({int(mism.sum())} flagged Gaussians differ); "
+          f"max image error {err_img[~excl].max():.2e}")
+    assert excl.mean() < 0.05, excl.mean()
+    assert np.all((err_img <= IMG_TOL + 2.0 * o["t_err"])[~excl])
+    assert np.all((dT <= IMG_TOL + o["t_err"] * o["final_T"])[~excl])
+    assert np.all(nc_ok[~excl])
     # screen-space gradients of the Gaussians whose whole rectangle lies in the window
     d = oracle.render_backward(sub, cw, full["bg"], full["dimg"][:, y0:y0 + WIN, x0:x0 + WIN].astype(np.float64))
-    r = rects(full["xy"][sel].astype(np.float64), full["radius"][sel], W, H)
+    r = rects(full["xy4"][sel], full["radius"][sel], W, H)
     inside = ((r[:, 0] >= x0 // 16) & (r[:, 2] <= x0 // 16 + TW) & (r[:, 1] >= y0 // 16) & (r[:, 3] <= y0 // 16 + TW)
-              & (full["radius"][sel] > 0))
-    # ... whose footprint (alpha >= 1/255, with slack) holds no excluded pixel: only those pixels add to
-    # a Gaussian's gradient
+              & (full["radius"][sel] > 0) & (op["radius"] > 0))
+    # ... whose footprint (alpha >= 1/255, with slack) holds no pixel with a decision near its threshold or
+    # a flagged list difference.  Pixels whose early stop sits within float32 error stay in: the entry a
+    # flipped stop adds or drops has weight alpha T < 1e-4, and the colour behind it reaches an earlier
+    # entry's gradient scaled by that weight, so it moves no gradient by more than ~1e-4 of its scale.
+    excl_g = excl & ~(stop & ~((o["margin"] < MARGIN_TOL) | np.kron(bad_tiles, np.ones((16, 16), bool))))
+    for i in np.nonzero(mism)[0]:
+        for r in (r_g[i], r_o[i]):
+            excl_g[16 * r[1]:16 * r[3], 16 * r[0]:16 * r[2]] = True
     touches_excl = np.zeros(len(sel), bool)
     yy, xx = np.mgrid[0:WIN, 0:WIN].astype(np.float64)
     for i in np.nonzero(inside)[0]:
         a, b, c = op["conic"][i]
         dx, dy = op["xy"][i][0] - xx, op["xy"][i][1] - yy
         foot = op["opacity"][i] * np.exp(-0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy) >= 0.5 / 255.0
-        touches_excl[i] = (foot & excl).any()
+        touches_excl[i] = (foot & excl_g).any()
     use = inside & ~touches_excl
-    assert use.sum() > 100, (inside.sum(), use.sum())
+    print(f"  gradients: {int(inside.sum())} Gaussians inside, {int((inside & touches_excl).sum())} excluded "
+          f"(footprint holds one of {int(excl_g.sum())} pixels with a near-threshold decision), {int(use.sum())} "
+          f"compared")
+    assert use.sum() > 0.9 * inside.sum(), (inside.sum(), use.sum())
     gpu = {"dxy": full["dxy"][sel][use], "dconic": full["dco"][sel][use][:, :3],
            "dopacity": full["dco"][sel][use][:, 3], "drgb": full["drgb"][sel][use][:, :3]}
-    # The chunked reverse replay starts each chunk from the forward's checkpoint (T and the colour behind the
-    # boundary, composited back to front from the chunks' partials); float32 T recovered by division along
-    # chunks of up to 1024 entries keeps 99.9% of the values within the small tests' 1e-3 of the group's scale
-    # and all within 2e-3.
     for key in gpu:
         ref = d[key][use]
         sc = np.abs(ref).max()
         err = np.abs(gpu[key] - ref) / sc
-        assert sc > 0 and np.quantile(err, 0.999) <= GRAD_TOL and err.max() <= 2 * GRAD_TOL, (key, err.max())
+        big = np.abs(ref) >= 1e-2 * sc  # per-element relative error of the values above 1% of the scale
+        rel = (np.abs(gpu[key] - ref)[big] / np.abs(ref)[big]).max()
+        print(f"  {key}: max error {err.max():.2e} of the group scale; per-element relative error above 1% of "
+              f"the scale {rel:.2e}")
+        assert sc > 0 and err.max() <= GRAD_TOL, (key, err.max())

@@ -1,12 +1,15 @@
 """CUDA path vs the FP64 oracle, element by element (needs a GPU).
 
 Bars (from the method's statement of parity):
-* tile counts and sorted per-tile lists: bit-exact (the oracle's binning and
-  sort fed the CUDA path's own float32 means, radii and depths);
+* visibility, radius, tile rectangle and tile count of every Gaussian: equal,
+  except decisions the oracle flags as float32 near-ties (its stated error
+  model), whose count must stay at or below 1e-5 of the instances;
+* sorted per-tile lists: equal to the oracle's own lists (its FP64 projection,
+  depth key = float32 rounding of the FP64 camera-space z), except tiles that
+  hold such a flagged Gaussian, counted the same way;
 * images: max abs error <= 1e-4 per colour channel, excluding pixels whose
   FP64 decisions sit within 1e-5 (relative) of a threshold and tiles touched by
-  a splat whose float32 rectangle differs from the FP64 one (both counted,
-  must stay below 1% of the image);
+  a flagged Gaussian whose decisions differ (counted, < 1% of the image);
 * gradients: per parameter group, max |g_gpu - g_orc| <= 1e-3 * max |g_orc|.
 """
 import math
@@ -18,7 +21,7 @@ import torch
 import oracle
 import synth
 from tests import scenes
-from tests.gpu_util import exclusion_mask, gauss64, rects, run_gpu
+from tests.gpu_util import discrete_mismatch, exclusion_mask, gauss64, rects, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -32,44 +35,66 @@ def _case(n, deg, seed, W, H, extent=0.9, ls=(-3.5, -2.0)):
     return g, cams
 
 
-@pytest.mark.parametrize("n,deg,W,H,seed", [(3000, 3, 200, 150, 0), (2000, 0, 128, 128, 1), (1500, 1, 97, 61, 2),
-                                            (2500, 2, 256, 144, 3)])
+PREPROCESS_CASES = [(3000, 3, 200, 150, 0), (2000, 0, 128, 128, 1), (1500, 1, 97, 61, 2), (2500, 2, 256, 144, 3)]
+
+
+@pytest.mark.parametrize("n,deg,W,H,seed", PREPROCESS_CASES)
 def test_preprocess_parity(n, deg, W, H, seed):
     g, cams = _case(n, deg, seed, W, H)
     out = run_gpu(g, cams, deg, BG)
     cam = oracle.camera_block(cams, 0)
     o = oracle.project(gauss64(g), cam)
-    vis_o = o["radius"] > 0
-    vis_g = out["radius"] > 0
-    # visibility differs only through a radius/rect near-tie at the image border
-    assert (vis_o != vis_g).sum() <= max(1, n // 1000)
-    both = vis_o & vis_g
-    assert np.allclose(out["xy"][both], o["xy"][both], rtol=1e-5, atol=2e-4)
-    assert np.allclose(out["depth"][both], o["depth"][both], rtol=1e-6)
+    # discrete decisions: every difference is a near-tie the oracle flags, and they are rare
+    mism, flagged = discrete_mismatch(o, out["xy4"], out["radius"], out["tiles"], W, H)
+    n_inst = int(o["tiles"].sum())
+    print(f"preprocess n={n}: {int(mism.sum())} differing decisions (all flagged: {flagged}), "
+          f"{int((o['unstable'] != 0).sum())} flagged Gaussians, {n_inst} instances")
+    assert flagged, np.nonzero(mism)[0][:10]
+    assert mism.sum() <= 1e-5 * n_inst
+    # the sort key: the correctly rounded float32 camera-space z on both sides
+    assert np.array_equal(out["depth"], o["depth"].astype(np.float32))
+    both = (o["radius"] > 0) & (out["radius"] > 0)
+    # pixel position: float pairs, ~2^-44 relative
+    assert np.allclose(out["xy"][both], o["xy"][both], rtol=1e-11, atol=1e-9)
     A = o["conic"][both]
     sc = np.abs(A).max(axis=1, keepdims=True)
     assert np.all(np.abs(out["conic_op"][both, :3] - A) <= 2e-4 * sc)
     assert np.allclose(out["conic_op"][both, 3], o["opacity"][both], rtol=1e-5, atol=1e-6)
     assert np.allclose(out["rgb"][both, :3], o["rgb"][both], atol=2e-5)
-    same_r = out["radius"] == o["radius"]
-    assert same_r[both].mean() > 0.995
-    ok = both & same_r
-    r_gpu = rects(out["xy"].astype(np.float64), out["radius"], W, H)
-    same_rect = np.all(r_gpu == o["rect"], axis=1)
-    assert same_rect[ok].mean() > 0.995
-    assert np.array_equal(out["tiles"][ok & same_rect], o["tiles"][ok & same_rect])
+
+
+def _lists_vs_oracle(out, o, W, H):
+    """Tiles whose GPU list differs from the oracle's own list; each must hold a Gaussian with a flagged
+    decision that differs between the two sides.  Returns (differing tiles, instances in them)."""
+    L = oracle.bin_sort(o["xy"], o["radius"], o["depth"], W, H)
+    mism, flagged = discrete_mismatch(o, out["xy4"], out["radius"], out["tiles"], W, H)
+    assert flagged
+    bad = set(np.nonzero(mism)[0].tolist())
+    n_bad, inst_bad = 0, 0
+    for t in range(L["ranges"].shape[0]):
+        a, b = out["ranges"][t]
+        oa, ob = L["ranges"][t]
+        gl, ol = out["vals"][a:b], L["idx"][oa:ob]
+        if len(gl) == len(ol) and np.array_equal(gl, ol):
+            continue
+        assert bad & (set(gl.tolist()) ^ set(ol.tolist())), f"tile {t} differs without a flagged Gaussian"
+        n_bad += 1
+        inst_bad += max(len(gl), len(ol))
+    return n_bad, inst_bad, len(L["idx"])
 
 
 @pytest.mark.parametrize("n,deg,W,H,seed", [(3000, 3, 200, 150, 4), (5000, 0, 333, 97, 5)])
 def test_sort_lists_bit_exact(n, deg, W, H, seed):
-    """Oracle binning+sort fed the GPU's own float32 xy / radius / depth equals the GPU lists exactly."""
+    """The GPU's sorted tile lists equal the oracle's lists from its own FP64 projection (depth key: the
+    float32 rounding of the FP64 camera-space z; equal keys by Gaussian index), tile by tile."""
     g, cams = _case(n, deg, seed, W, H)
     out = run_gpu(g, cams, deg, BG)
-    L = oracle.bin_sort(out["xy"].astype(np.float64), out["radius"], out["depth"].astype(np.float64), W, H)
     assert out["status"] == 0
-    assert len(out["vals"]) == int(out["tiles"].sum()) == len(L["idx"])
-    assert np.array_equal(out["vals"], L["idx"])
-    assert np.array_equal(out["ranges"], L["ranges"])
+    assert len(out["vals"]) == int(out["tiles"].sum())
+    o = oracle.project(gauss64(g), oracle.camera_block(cams, 0))
+    n_bad, inst_bad, I = _lists_vs_oracle(out, o, W, H)
+    print(f"lists: {n_bad} tiles ({inst_bad} instances) differ at flagged near-ties, of {I} instances")
+    assert inst_bad <= 1e-5 * I
 
 
 @pytest.mark.parametrize("n,deg,W,H,seed", [(3000, 3, 200, 150, 6), (800, 0, 64, 64, 7), (4000, 1, 161, 93, 8)])
@@ -80,8 +105,9 @@ def test_render_parity(n, deg, W, H, seed):
     cam = oracle.camera_block(cams, 0)
     o = oracle.render(gauss64(g), cam, bg)
     op = oracle.project(gauss64(g), cam)
-    excl, ndiff = exclusion_mask(op, out["xy"], out["radius"], o["tie_tiles"], o["margin"], W, H)
-    assert excl.mean() < 0.01, (excl.mean(), ndiff)
+    excl, ndiff, flagged = exclusion_mask(op, out["xy4"], out["radius"], out["tiles"], o["margin"], W, H)
+    print(f"render n={n}: {excl.sum()} of {excl.size} pixels excluded ({ndiff} flagged Gaussians differ)")
+    assert flagged and excl.mean() < 0.01, (excl.mean(), ndiff)
     err = np.abs(out["img"][0] - o["img"]).max(axis=0)
     assert err[~excl].max() <= IMG_TOL, err[~excl].max()
     assert np.abs(out["final_T"][0] - o["final_T"])[~excl].max() <= IMG_TOL
@@ -178,8 +204,8 @@ def test_multi_unit_batch_parity():
         o = oracle.render(gauss64(g), cam, BG)
         op = oracle.project(gauss64(g), cam)
         P = slice(k * n, (k + 1) * n)
-        excl, _ = exclusion_mask(op, out["xy"][P], out["radius"][P], o["tie_tiles"], o["margin"], 120, 88)
-        assert excl.mean() < 0.01
+        excl, _, flagged = exclusion_mask(op, out["xy4"][P], out["radius"][P], out["tiles"][P], o["margin"], 120, 88)
+        assert flagged and excl.mean() < 0.01
         assert np.abs(out["img"][k] - o["img"]).max(axis=0)[~excl].max() <= IMG_TOL
         r = oracle.loss_and_grads(gauss64(g), cam, BG, gts[k].astype(np.float64), masks[k], 0.2)
         loss_sum += r["loss"]
@@ -288,3 +314,58 @@ def test_blend_work_counters():
     assert 0 < c["blended"] <= c["bwd_pairs"] <= c["fwd_pairs"]
     lens = (fr.ranges[:, 1] - fr.ranges[:, 0]).cpu().numpy()
     assert c["fwd_pairs"] <= int(lens.sum()) * 256
+
+
+def test_fused_projection_backward_adam_vs_oracle():
+    """The fused projection backward + Adam kernel the benchmark runs, against the oracle's FP64 parameter
+    gradient (reverse replay, dual-number projection Jacobian) followed by the oracle's Adam step.  The
+    moments start from seeded values in the range training reaches (so the update depends smoothly on the
+    gradient) at step t = 11 of a log-linear learning-rate schedule."""
+    import paper_2509_12138_gb300 as gsp
+    n, deg, W, H, seed = 1200, 3, 120, 90, 15
+    g, cams = _case(n, deg, seed, W, H, ls=(-3.0, -1.8))
+    gt, mask = scenes.random_gt(W, H, seed + 50)
+    cam = oracle.camera_block(cams, 0)
+    r = oracle.loss_and_grads(gauss64(g), cam, BG, gt.astype(np.float64), mask, 0.2)
+    go = r["grads"]
+    groups = [slice(0, 3), slice(3, 6), slice(6, 10), slice(10, 11), slice(11, 14), slice(14, go.shape[1])]
+    sc = np.zeros(go.shape[1])
+    for sl in groups:
+        sc[sl] = np.abs(go[:, sl]).max()
+    rng = np.random.default_rng(seed)
+    m0 = rng.normal(0.0, 1.0, go.shape) * sc
+    v0 = rng.uniform(0.5, 2.0, go.shape) * sc * sc
+    fr = gsp.Frame(n, gsp.Units.single(n), W, H, deg)
+    params = gsp.pack_params(g, deg)
+    camd = gsp.pack_cameras(cams)
+    fr.fit_capacity(params, camd)
+    fr.forward(params, camd, BG)
+    fr.loss(torch.from_numpy(gt).cuda()[None], torch.from_numpy(mask).cuda()[None], 0.2)
+    fr.blend_backward(BG)
+    opt = gsp.Adam(params, deg, extent=1.0, lr_steps=100)
+    opt.m.copy_(gsp.pack_params(oracle.unflatten_params(m0, deg), deg))
+    opt.v.copy_(gsp.pack_params(oracle.unflatten_params(v0, deg), deg))
+    opt.step_dev.fill_(10)
+    opt.fused_step(fr, camd, keep_grads=True)
+    torch.cuda.synchronize()
+    assert fr.read_status() == 0
+    # the gradient the fused kernel formed
+    _group_check(gsp.unpack_grads(fr.grads, deg), go, deg)
+    # Adam at t = 11 with the per-element learning rates of the schedule
+    t, steps = 11, 100
+    li, lf = opt.lr_init.astype(np.float64), opt.lr_final.astype(np.float64)
+    lr = np.where(li == lf, li, li * (lf / np.where(li > 0, li, 1.0)) ** (min(t, steps) / steps))
+    npl = params.shape[0]
+    lr_el = gsp.unpack_grads(torch.from_numpy(np.repeat(lr.reshape(npl, 1, 4), n, axis=1).astype(np.float32)), deg)
+    p0 = oracle.flatten_params(gsp.unpack_params(gsp.pack_params(g, deg), deg))
+    p_ref, m_ref, v_ref = oracle.adam(p0, go, m0, v0, lr_el.astype(np.float64), 0.9, 0.999, 1e-15, t)
+    p_gpu = oracle.flatten_params(gsp.unpack_params(params, deg))
+    m_gpu = gsp.unpack_grads(opt.m, deg)
+    v_gpu = gsp.unpack_grads(opt.v, deg)
+    # a gradient error of 1e-3 of the group scale moves m by 1e-4 of it, v by ~1e-3 of its own size, and the
+    # update by ~2e-4 of the learning rate; on top of float32 rounding of each stored value
+    ulp = lambda x: np.spacing(np.abs(x).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(m_gpu - m_ref) <= 1e-4 * sc + 4 * ulp(m_ref))
+    assert np.all(np.abs(v_gpu - v_ref) <= 3e-3 * np.abs(v_ref) + 4 * ulp(v_ref))
+    assert np.all(np.abs(p_gpu - p_ref) <= 1e-3 * lr_el + 4 * ulp(p_ref))
+    assert int(opt.step_dev.item()) == 11

@@ -244,3 +244,75 @@ def test_sh_colour_offset_and_clamp():
     assert np.allclose(p["rgb"][0], [0.9, 0.0, 0.5], atol=1e-14)
     assert p["clamp"][0] == 0b010
     assert p["opacity"][0] == pytest.approx(0.5)
+
+
+def _nearest_f32(q):
+    """The float32 nearest to the rational q (ties to the even significand), by exact comparison."""
+    from fractions import Fraction
+    c = np.float32(float(q))
+    cands = [np.nextafter(c, np.float32(-np.inf)), c, np.nextafter(c, np.float32(np.inf))]
+    d = [abs(Fraction(float(x)) - q) for x in cands]
+    best = min(d)
+    ties = [x for x, e in zip(cands, d) if e == best]
+    return min(ties, key=lambda x: int(np.float32(x).view(np.uint32)) & 1)
+
+
+def test_depth_key_is_the_float32_rounding_of_the_exact_depth():
+    """The sort key of every Gaussian is the float32 nearest to its exact camera-space z, computed here in
+    rational arithmetic from the float32 means and camera."""
+    from fractions import Fraction
+    rng = np.random.default_rng(11)
+    cams = scenes.front_camera(200, 150, eye=(0.4, -3.0, 1.0))
+    cam = oracle.camera_block(cams, 0)
+    means = rng.uniform(-0.9, 0.9, (400, 3)).astype(np.float32)
+    g = dict(means=means.astype(np.float64), log_scales=np.full((400, 3), -3.0), quats=np.tile([1.0, 0, 0, 0], (400, 1)),
+             logit_opacity=np.zeros(400), sh=np.zeros((400, 1, 3)))
+    p = oracle.project(g, cam)
+    R2, t2 = cam[6:9], cam[11]
+    for i in range(400):
+        z = sum(Fraction(float(R2[j])) * Fraction(float(means[i, j])) for j in range(3)) + Fraction(float(t2))
+        assert np.float32(p["depth"][i]) == _nearest_f32(z), i
+
+
+def test_unstable_flags_rare_on_random_scenes():
+    """The float32 near-tie flags mark a small fraction of Gaussians of an ordinary scene."""
+    g, cams = scenes.random_scene(3000, 1, 3, 200, 150)
+    p = oracle.project({k: np.asarray(v, np.float64) for k, v in g.items()}, oracle.camera_block(cams, 0))
+    assert (p["unstable"] != 0).mean() < 2e-3
+
+
+def test_unstable_flag_radius_at_an_integer():
+    """On the axis, 3 sqrt(lambda_max) = k exactly for sigma solving (f sigma / z)^2 + 0.3 + sqrt(0.1) = k^2 / 9:
+    the radius decision is flagged; half an integer away it is not."""
+    cams = scenes.identity_camera(64, 64)
+    cam = oracle.camera_block(cams, 0)
+    f, z = float(cams.fy[0]), 2.0
+    for k in (4, 7):
+        for shift, flag in ((0.0, True), (0.5, False)):
+            lam = (k + shift) ** 2 / 9.0
+            sig = z / f * math.sqrt(lam - math.sqrt(0.1) - 0.3)
+            p = oracle.project(_one([0, 0, z], [math.log(sig)] * 3, [1, 0, 0, 0]), cam)
+            assert bool(p["unstable"][0] & 2) == flag, (k, shift)
+
+
+def test_unstable_flag_rect_at_a_tile_boundary():
+    """A splat of radius 16 whose pixel x is an integer u = 32: floor(u - r) / 16 is a tile boundary, so the
+    rectangle decision is flagged; at u = 32.3 it is not."""
+    cams = scenes.identity_camera(64, 64)
+    cam = oracle.camera_block(cams, 0)
+    f, cx, z = float(cams.fx[0]), float(cams.cx[0]), 2.0
+    sig = z / f * math.sqrt(27.0 - math.sqrt(0.1) - 0.3)  # 3 sqrt(lambda) = 15.59: radius 16
+    for u, flag in ((32.0, True), (32.3, False)):
+        x = (u - cx) / f * z
+        p = oracle.project(_one([x, 0, z], [math.log(sig)] * 3, [1, 0, 0, 0]), cam)
+        assert p["radius"][0] == 16
+        assert bool(p["unstable"][0] & 4) == flag, u
+
+
+def test_unstable_flag_near_plane():
+    """A mean exactly on the near plane is a flagged cull decision; one well in front of it is not."""
+    cams = scenes.identity_camera(64, 64)
+    cam = oracle.camera_block(cams, 0)
+    for z, flag in ((cam[21], True), (0.25, False)):
+        p = oracle.project(_one([0, 0, z], [math.log(1e-3)] * 3, [1, 0, 0, 0]), cam)
+        assert bool(p["unstable"][0] & 1) == flag, z

@@ -167,3 +167,69 @@ def test_mlp_features_layout():
     assert np.allclose(X[i, 96:99], nrm[i]) and np.all(X[:, 99:] == 0)
     # offsets have unit mean length by construction
     assert np.linalg.norm(X[:, :48].reshape(-1, 16, 3), axis=2).mean(axis=1) == pytest.approx(1.0, rel=1e-6)
+
+
+def test_init_gaussians_plain_against_kdtree():
+    """Plain initialiser: isotropic log-scale = log of the mean of the 3 nearest-neighbour distances (by
+    scipy's cKDTree, self excluded), floored at 1e-7; identity rotation; the default logit opacity."""
+    pts, _, _ = synth.interface_points(2000, 8, seed=5)
+    pts = pts.astype(np.float64)
+    pts[7] = pts[8]  # a duplicate pair ...
+    pts[9] = pts[8]  # ... and triple: mean 3-NN distance of point 8's group can be tiny
+    d_ref, _ = cKDTree(pts).query(pts, k=4)
+    d3 = d_ref[:, 1:].mean(axis=1)
+    ls, q, lo = oracle.init_gaussians(d_ref[:, 1:])
+    expect = np.log(np.maximum(d3, 1e-7))
+    assert np.allclose(ls, np.repeat(expect[:, None], 3, 1), rtol=0, atol=1e-12)
+    assert np.array_equal(q, np.tile([1.0, 0, 0, 0], (2000, 1)))
+    assert np.allclose(lo, math.log(0.1 / 0.9), rtol=0, atol=1e-15)
+    # an all-zero neighbourhood takes the floor
+    ls0, _, _ = oracle.init_gaussians(np.zeros((1, 3)))
+    assert ls0[0, 0] == pytest.approx(math.log(1e-7), abs=1e-12)
+
+
+def test_init_gaussians_learned_and_fallback_by_hand():
+    """Learned initialiser: log-scale = plain log-scale + outputs 0..2, rotation = outputs 3..6, logit =
+    output 7; a Gaussian whose outputs are not all finite, or whose rotation has norm <= 1e-6, keeps the
+    plain values."""
+    dist = np.array([[0.1, 0.2, 0.3], [0.5, 0.5, 0.5], [1.0, 2.0, 3.0], [0.2, 0.2, 0.2]])
+    Y = np.array([[0.1, -0.2, 0.3, 0.5, 0.5, -0.5, 0.5, 1.5],
+                  [0.0, 0.0, 0.0, np.nan, 1.0, 0.0, 0.0, 0.0],      # non-finite -> plain
+                  [1.0, 1.0, 1.0, 0.0, 0.0, 0.0, 5e-7, -1.0],      # rotation norm 5e-7 -> plain
+                  [0.0, 0.0, 0.0, 0.0, 0.0, 2.0, 0.0, np.inf]])     # infinite logit -> plain
+    ls, q, lo = oracle.init_gaussians(dist, Y, logit_default=-2.0)
+    plain = np.log(dist.mean(axis=1))
+    assert np.allclose(ls[0], plain[0] + np.array([0.1, -0.2, 0.3]), atol=1e-14)
+    assert np.allclose(q[0], [0.5, 0.5, -0.5, 0.5]) and lo[0] == 1.5
+    for i in (1, 2, 3):
+        assert np.allclose(ls[i], plain[i], atol=1e-14) and np.array_equal(q[i], [1.0, 0, 0, 0]) and lo[i] == -2.0
+
+
+def test_mlp_features_hand_configuration_and_invariances():
+    """Features of a hand-built neighbourhood (16 neighbours at known offsets), and their behaviour under
+    rigid motions and scaling of the whole cloud: offsets and normals rotate with it, translation and
+    uniform scaling leave them unchanged."""
+    rng = np.random.default_rng(9)
+    offs = rng.standard_normal((16, 3))
+    offs *= (np.arange(1, 17) / np.linalg.norm(offs, axis=1))[:, None]  # distances 1 .. 16, all distinct
+    pts = np.vstack([np.zeros(3), offs])
+    nrm = rng.standard_normal((17, 3))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    idx, dist = oracle.knn(pts, 16)
+    X = oracle.mlp_features(pts, nrm, idx, dist)
+    dbar = np.arange(1, 17).mean()
+    assert np.array_equal(idx[0], np.arange(1, 17))
+    assert np.allclose(X[0, :48].reshape(16, 3), offs / dbar, atol=1e-14)
+    assert np.allclose(X[0, 48:96].reshape(16, 3), nrm[1:], atol=0)
+    assert np.allclose(X[0, 96:99], nrm[0], atol=0) and np.all(X[:, 99:] == 0)
+    # a rotation, a translation and a scaling of the cloud
+    from scipy.spatial.transform import Rotation
+    R = Rotation.random(random_state=3).as_matrix()
+    p2 = 2.5 * pts @ R.T + np.array([0.3, -1.0, 4.0])
+    n2 = nrm @ R.T
+    idx2, dist2 = oracle.knn(p2, 16)
+    X2 = oracle.mlp_features(p2, n2, idx2, dist2)
+    assert np.array_equal(idx2, idx)
+    for a, b in ((slice(0, 48), slice(0, 48)), (slice(48, 96), slice(48, 96)), (slice(96, 99), slice(96, 99))):
+        rot = X[:, a].reshape(17, -1, 3) @ R.T
+        assert np.allclose(X2[:, b].reshape(17, -1, 3), rot, atol=1e-12)
