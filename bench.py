@@ -62,10 +62,12 @@ def parse():
     ap.add_argument("--deterministic", action="store_true",
                     help="accumulate screen-space gradients in fixed point (bitwise reproducible steps)")
     ap.add_argument("--chunk", type=int, default=1024, help="list entries per chunk job of the blend schedule")
+    ap.add_argument("--sparse-adam", action="store_true",
+                    help="Gaussians without gradient in a step keep their parameters and moments")
     ap.add_argument("--random-order", action="store_true",
                     help="keep the sampler's random point order instead of the extraction's Z-order")
     ap.add_argument("--cpu-window", type=int, default=8, help="CPU sample: 1/(w*w) of the view's pixels")
-    ap.add_argument("--experiment", default=None, choices=["learned-init", "ghost-ablation"],
+    ap.add_argument("--experiment", default=None, choices=["learned-init", "ghost-ablation", "cpu-oracle"],
                     help="instead of the throughput line: the plain vs batched + learned-init comparison")
     ap.add_argument("--exp-gaussians", type=int, default=1_000_000)
     ap.add_argument("--exp-steps", type=int, default=3000)
@@ -210,7 +212,7 @@ def cpu_baseline(scene, frac: int):
 # ---------------------------------------------------------------- our arm
 def kernel_launch_count(frame, lam):
     """Kernels libgs launches for one training step (a1-a6) of this frame (the kernel launches ncu lists
-    for the timed steps; the two 4-byte memsets of the blend kernels' ticket counter are not kernels)."""
+    for the timed steps; the 4-byte memsets of the ticket counters are not kernels)."""
     tile_bits = max(1, math.ceil(math.log2(frame.n_tiles)))
     unit_bits = math.ceil(math.log2(frame.units.n)) if frame.units.n > 1 else 0
     key_bits = 32 + tile_bits + unit_bits
@@ -242,6 +244,7 @@ def run_ours(args, wl, rank, world):
     frame = gs.Frame(N, gs.Units.single(N), W, H, 3, device=dev, max_instances=6 * N,
                      deterministic=args.deterministic, chunk=args.chunk)
     opt = gs.Adam(params, 3, extent=1.0, lr_steps=7000)
+    opt.sparse = bool(args.sparse_adam)
     bg = scene.bg
     V = len(scene.cams)
 
@@ -317,6 +320,19 @@ def run_ours(args, wl, rank, world):
         frame.forward(params, scene.cam((args.warmup + k) % V), bg)
         pairs.append(frame.blend_pairs())
     pairs_per_step = {key: float(np.mean([p[key] for p in pairs])) for key in pairs[0]}
+    # Gaussians whose nine screen-space gradient values are all zero in a view (those a sparse Adam would
+    # skip), over timed views, outside the timed region (no parameter update)
+    zero_frac = []
+    for k in range(min(args.steps, 8)):
+        v = (args.warmup + k) % V
+        cam = scene.cam(v)
+        frame.preprocess(params, cam)
+        frame.sort()
+        frame.render(bg)
+        frame.loss(scene.gt[v:v + 1], scene.mask[v:v + 1], LAMBDA_SSIM)
+        frame.blend_backward(bg)
+        g = frame.dxy[:N].abs().sum(1) + frame.dco[:N].abs().sum(1) + frame.drgb[:N, :3].abs().sum(1)
+        zero_frac.append(float((g == 0).float().mean()))
 
     # render-only (a1-a3) for Mpix/s, in the faster forward mode over 8 views spread around the orbit (whole-list
     # walks stop early on opaque views; chunk-parallel compositing wins where pixels rarely stop and on the
@@ -394,14 +410,17 @@ def run_ours(args, wl, rank, world):
     barrier()
     return dict(scene=scene, frame=frame, ms_total=ms_total, stage_ms=stage_ms, stages=stages, ms_render=ms_render,
                 clocks=clk, e2e_sec=e_sec, instances=instances, tile_len=tile_len, pairs=pairs_per_step,
-                render_mode=render_mode, visible=visible, h2d=(3 * H * W * 4 + H * W), d2h=4,
+                render_mode=render_mode, visible=visible, zero_grad_frac=float(np.mean(zero_frac)),
+                h2d=(3 * H * W * 4 + H * W), d2h=4,
                 launches=kernel_launch_count(frame, LAMBDA_SSIM) * args.steps, N=N, W=W, H=H)
 
 
 # Blend kernels' algorithmic work: FP32 issue slots (one per lane-operation, FMA and MUFU included) per
-# (pixel, list entry) pair of the standard per-pixel walk: the forward evaluates every entry until the pixel
-# stops (~15 slots: offset, quadratic form, exp, alpha, tests, T and colour updates), the reverse replay every
-# entry up to n_contrib (~50 slots: alpha, T recovery, colour-behind update, 9 gradient terms).
+# (pixel, list entry) pair that a walk skipping the records whose alpha box misses the pixel's 4x4 block must
+# evaluate (gs_blend_pairs counts them on the device): the forward each such entry until the pixel stops (~15
+# slots: offset, quadratic form, exp, alpha, tests, T and colour updates), the reverse replay each such entry up
+# to n_contrib (~50 slots: alpha, T recovery, colour-behind update, 9 gradient terms).  The pairs of the plain
+# per-pixel walk (every entry of the tile's list) are reported beside it as the work the block masks avoid.
 FWD_SLOTS_PER_PAIR = 15
 BWD_SLOTS_PER_PAIR = 50
 
@@ -412,11 +431,11 @@ BWD_SLOTS_PER_PAIR = 50
 # work counts.  Reported only for that workload and order, scaled by the units of the bench's own timed views.
 TRAFFIC_WORKLOAD = "iso10M-1080p"
 TRAFFIC_PER_UNIT = {
-    "preprocess": ("gaussian", 290.10),
+    "preprocess": None,
     "bin_sort": ("instance", 204.90),
-    "render_fwd": ("fwd_pair", 0.2758),
+    "render_fwd": None,
     "loss": ("pixel", 20.02),
-    "blend_bwd": ("bwd_pair", 0.8939),
+    "blend_bwd": None,
     "project_bwd_adam": ("gaussian", 1477.58),
 }
 
@@ -447,13 +466,14 @@ def rooflines(res, workload=None, issue=None, random_order=False):
     key_bits = 32 + max(1, (tiles - 1).bit_length())
     passes = min(-(-key_bits // 9), -(-key_bits // 8))  # 9-bit digits when they save a pass
     work = {
-        "preprocess": ("hbm", N * (59 * 4 + 52)),
+        # 15 parameter planes read (240 B at SH3); xy pair, conic, rgb, depth, radius, tiles written (60 B)
+        "preprocess": ("hbm", N * (15 * 16 + 60)),
         "bin_sort": ("hbm", N * 8 + I * (12 + passes * 32 + 16)),
         # params, m, v read and written; the gradient stays in registers; screen gradients read
         "project_bwd_adam": ("hbm", N * (59 * 4 * 6 + 40 + 4)),
         "loss": ("hbm", res["W"] * res["H"] * (3 * 4 * 3 + 1 + 3 * 4 * 6)),
-        "render_fwd": ("alu", pairs["fwd_pairs"] * FWD_SLOTS_PER_PAIR),
-        "blend_bwd": ("alu", pairs["bwd_pairs"] * BWD_SLOTS_PER_PAIR),
+        "render_fwd": ("alu", pairs["fwd_pairs_masked"] * FWD_SLOTS_PER_PAIR),
+        "blend_bwd": ("alu", pairs["bwd_pairs_masked"] * BWD_SLOTS_PER_PAIR),
     }
     units = {"gaussian": N, "instance": I, "fwd_pair": pairs["fwd_pairs"], "bwd_pair": pairs["bwd_pairs"],
              "pixel": res["W"] * res["H"]}
@@ -477,12 +497,15 @@ def rooflines(res, workload=None, issue=None, random_order=False):
         else:
             ach = amount / (ms * 1e-3) / 1e12
             fwd = name == "render_fwd"
-            n_pairs = pairs["fwd_pairs"] if fwd else pairs["bwd_pairs"]
+            n_pairs = pairs["fwd_pairs_masked"] if fwd else pairs["bwd_pairs_masked"]
+            n_plain = pairs["fwd_pairs"] if fwd else pairs["bwd_pairs"]
             out[name] = {"kernel": kernel[name], "bound": "alu", "achieved": round(ach, 3),
                          "peak": round(slots, 2), "unit": "TFLOP/s",
                          "frac": round(ach / slots, 4), "traffic": traffic, "peak_source": slots_src,
-                         "work": f"{n_pairs:.3e} (pixel, list entry) pairs x "
-                                 f"{FWD_SLOTS_PER_PAIR if fwd else BWD_SLOTS_PER_PAIR} FP32 issue slots"}
+                         "work": f"{n_pairs:.3e} (pixel, list entry) pairs inside the block masks x "
+                                 f"{FWD_SLOTS_PER_PAIR if fwd else BWD_SLOTS_PER_PAIR} FP32 issue slots",
+                         "work_avoided": f"{n_plain - n_pairs:.3e} pairs of the plain per-pixel walk "
+                                         f"({n_plain:.3e}) fall outside the masks"}
         if traffic is not None:
             out[name]["traffic_source"] = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum at {TRAFFIC_WORKLOAD}: "
                                            f"{TRAFFIC_PER_UNIT[name][1]} B per {TRAFFIC_PER_UNIT[name][0]} x "
@@ -502,13 +525,16 @@ def main():
               "views": wl["views"], "sh_degree": 3, "loss": f"masked L1 + {LAMBDA_SSIM} D-SSIM",
               "gradient_accumulation": "int64 fixed point" if args.deterministic else "float atomics",
               "l2": "inputs larger than L2 (params+Adam state 9.6 GB at 10M)",
-              "point_order": "random" if args.random_order else "z-order", "chunk": args.chunk}
+              "point_order": "random" if args.random_order else "z-order", "chunk": args.chunk,
+              "adam": "sparse" if args.sparse_adam else "dense"}
     if args.impl == "reference":
         return run_reference(args, wl, rank, world, config)
     if args.experiment == "learned-init":
         return run_learned_init_experiment(args)
     if args.experiment == "ghost-ablation":
         return run_ghost_ablation(args)
+    if args.experiment == "cpu-oracle":
+        return run_cpu_oracle_timing(args)
     if args.workload.startswith("batched"):
         return run_batched(args, wl)
     if args.workload.startswith("merge"):
@@ -542,6 +568,7 @@ def main():
         "stage_ms": {k: round(float(v), 4) for k, v in zip(res["stages"], res["stage_ms"])},
         "instances_per_view": res["instances"], "tile_list_len": res["tile_len"],
         "visible_fraction": round(res["visible"], 4),
+        "zero_gradient_fraction": round(res["zero_grad_frac"], 4),
         "e2e": {"value": round(shard.job_throughput([args.steps] * world, e2e_sec * 1e3), 3), "unit": "iters/s",
                 "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
         "gpu_launches": res["launches"], "clocks": res["clocks"],
@@ -617,6 +644,90 @@ def run_ghost_ablation(args):
     return 0
 
 
+def _cpu_model() -> str:
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu model")):
+                return ln.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _oracle_iteration(g64, cams, views, gt, mask, lam):
+    """One measured FP64 training iteration of the oracle: for each view its render, loss, reverse replay and
+    projection Jacobian; then one Adam step over all parameters.  Returns seconds."""
+    import oracle
+    bg = np.ones(3)
+    t0 = time.perf_counter()
+    grads = 0.0
+    for k, v in enumerate(views):
+        cam = oracle.camera_block(cams, v)
+        r = oracle.render(g64, cam, bg)
+        _, dimg = oracle.loss(r["img"], gt[k], mask[k], lam)
+        g2d = oracle.render_backward(g64, cam, bg, dimg)
+        grads = grads + oracle.project_backward(g64, cam, g2d)
+    flat = oracle.flatten_params(g64)
+    oracle.adam(flat, grads, np.zeros_like(flat), np.zeros_like(flat), 1e-3, 0.9, 0.999, 1e-15, 1)
+    return time.perf_counter() - t0
+
+
+def run_cpu_oracle_timing(args):
+    """The FP64 oracle, as it stands, timed on this machine's host cores for one full training iteration
+    (measured, not sampled): the small configuration (2,000 Gaussians on the unit sphere, SH0, all eight
+    128x128 views, masked L1) and a 1M-Gaussian interface (SH3, one 1920x1080 view, masked L1 + 0.2 D-SSIM).
+    Targets are the oracle's own renders (untimed set-up).  One JSON line."""
+    import oracle
+    import synth
+    from paper_2509_12138_gb300 import workload
+    oracle.build()
+    out = {"experiment": "cpu oracle, measured iterations", "cores": oracle.num_threads(),
+           "nproc": os.cpu_count(), "cpu": _cpu_model(), "results": []}
+    # small configuration
+    n = 2000
+    pts, _ = synth.sphere_points(n, 0)
+    _, dist = oracle.knn(pts.astype(np.float64), 3)
+    ls = np.log(np.maximum(dist.mean(axis=1), 1e-7))
+    y00 = 0.5 / math.sqrt(math.pi)
+    init = dict(means=pts.astype(np.float64), log_scales=np.repeat(ls[:, None], 3, 1),
+                quats=np.tile([1.0, 0, 0, 0], (n, 1)), logit_opacity=np.full(n, math.log(0.1 / 0.9)),
+                sh=np.zeros((n, 1, 3)))
+    pert = synth.target_perturbation(n, 0)
+    target = dict(init, means=init["means"] + pert["mean_noise"], log_scales=init["log_scales"] + pert["log_scale_noise"],
+                  logit_opacity=np.full(n, math.log(0.8 / 0.2)), sh=((pert["rgb"] - 0.5) / y00)[:, None, :])
+    cams = synth.orbital_cameras(8, 3.0, width=128, height=128)
+    gt, mask = [], []
+    for v in range(8):
+        r = oracle.render(target, oracle.camera_block(cams, v), np.ones(3))
+        gt.append(r["img"])
+        mask.append(((1.0 - r["final_T"]) >= 1.0 / 255.0).astype(np.uint8))
+    t = _oracle_iteration(init, cams, list(range(8)), gt, mask, 0.0)
+    out["results"].append({"config": "2,000 Gaussians, SH0, 8 views of 128x128, masked L1", "kind": "measured",
+                           "seconds_per_iteration": round(t, 3), "iters_per_s": round(1.0 / t, 4)})
+    # 1M-Gaussian interface, one 1080p view
+    n2, W, H = args.exp_gaussians, 1920, 1080
+    pts, nrm, _ = synth.interface_points(n2, 8, 0)
+    o = synth.spatial_order(pts)
+    pts, nrm = pts[o], nrm[o]
+    col = synth.lambert_colors(pts, nrm)
+    sp = workload.spacing_estimate(nrm, n2)
+    init2 = {k: np.asarray(v, np.float64) for k, v in workload.plain_init(pts, col, math.log(sp), 3).items()}
+    surf = {k: np.asarray(v, np.float64) for k, v in workload.gt_surfels(pts, nrm, col, sp).items()}
+    cams2 = synth.orbital_cameras(64, 1.5, center=(0.5, 0.5, 0.5), width=W, height=H)
+    r = oracle.render(surf, oracle.camera_block(cams2, 1), np.ones(3))
+    m2 = ((1.0 - r["final_T"]) >= 1.0 / 255.0).astype(np.uint8)
+    t2 = _oracle_iteration(init2, cams2, [1], [r["img"]], [m2], LAMBDA_SSIM)
+    out["results"].append({"config": f"{n2:,} Gaussians, SH3, one 1920x1080 view, masked L1 + 0.2 D-SSIM",
+                           "kind": "measured", "seconds_per_iteration": round(t2, 3),
+                           "iters_per_s": round(1.0 / t2, 5)})
+    print(json.dumps(out))
+    return 0
+
+
 def run_batched(args, wl):
     """Batched form: all 8 partitions x views-per-step units as one graph-captured step, autotuned."""
     import torch
@@ -638,10 +749,18 @@ def run_batched(args, wl):
                                 steps=3, warmup=2, use_cache=False)
     tr = make(*best)
     sec = tune.time_trainer(tr, steps=args.steps, warmup=args.warmup)
+    # host time of a step: the graph replay of the one gs_train_batch call (views chosen on the device)
+    torch.cuda.synchronize()
+    h0 = time.perf_counter()
+    for _ in range(args.steps):
+        tr.step()
+    host_us = (time.perf_counter() - h0) / args.steps * 1e6
+    torch.cuda.synchronize()
     st = tr.check()
     line = {"metric": "batched train step, 8 ghost-celled partitions (28M Gaussians) x views per step, 1080p",
             "value": round(tr.units.n / sec, 3), "unit": "(partition, view) units/s",
-            "steps_per_s": round(1.0 / sec, 3), "ms_per_step": round(sec * 1e3, 3), "n_gpus": 1,
+            "steps_per_s": round(1.0 / sec, 3), "ms_per_step": round(sec * 1e3, 3),
+            "host_us_per_step": round(host_us, 1), "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic", "config": {"workload": args.workload, "gaussians_with_ghosts": int(ps.offsets[-1]),
                                             "slab_sizes": wl["slabs"], "views_per_partition": wl["views"],

@@ -133,6 +133,10 @@ typedef struct gs_grad2d {
  * chunk_last   [max_checkpoints][256]     forward scratch (per pixel and
  *                                 chunk: last blended entry and stop flag, then
  *                                 the T in front of the chunk)
+ * stop_queue   [8 * max_jobs + 1] forward scratch: the (chunk job, pixel block)
+ *                                 units in which some pixel stops, for the
+ *                                 forward's re-walk pass; the last entry counts
+ *                                 them
  * chunk        entries per chunk (a multiple of 32); max_jobs >= U n_tiles +
  *              max_instances / chunk + 1, max_checkpoints >= max_instances /
  *              chunk + 1 (gs_schedule_sizes).
@@ -147,6 +151,7 @@ typedef struct gs_schedule {
   uint32_t* jobs;
   float* checkpoints;
   uint32_t* chunk_last;
+  uint32_t* stop_queue;
   int64_t max_jobs;
   int64_t max_checkpoints;
   int32_t chunk;
@@ -198,11 +203,10 @@ int gs_preprocess(const float* params, int64_t n_gauss, int sh_degree, const gs_
                   const gs_proj* proj, int* d_status, gs_stream_t stream);
 
 /* ---- a2: duplication + radix sort + tile ranges ---------------------------
- * Each visible record p of unit u is duplicated once per covered tile, in
- * record order and row-major tile order, with the 64-bit key
- * (u << (tile_bits + 32)) | (tile << 32) | float_bits(depth) and value p.
- * A stable LSD radix sort (8-bit digits) orders the keys, so equal keys keep
- * record order: each tile's list is ordered by (depth, record index).
+ * Each visible record p of unit u has one instance per covered tile; each
+ * (unit, tile) list holds the instances of its records ordered by
+ * (float32 depth, record index p), i.e. the order of a stable sort by depth of
+ * the records in index order.
  * ranges[u * n_tiles + tile] = [start, end) into sorted_vals.
  * sched (may be NULL): also fills the blend schedule: tile order (heaviest
  * lists first), per-instance block masks and the chunk jobs of every list
@@ -216,6 +220,22 @@ int gs_bin_sort(const gs_proj* proj, const gs_units* units, int width, int heigh
                 int64_t max_instances, void* workspace, size_t workspace_bytes,
                 uint32_t* sorted_vals, uint32_t* ranges, uint32_t* d_num_instances,
                 const gs_schedule* sched, int* d_status, gs_stream_t stream);
+
+/* The same lists, ranges, instance count and schedule as gs_bin_sort (same
+ * arguments and workspace) by the other sort design.  gs_bin_sort sorts the
+ * (unit | tile | depth) keys of all instances with one global stable LSD radix
+ * sort (5 passes of 9-bit digits over the 45 key bits of one 1080p unit).
+ * gs_bin_sort_bucketed gathers the instances per (unit, tile) list with
+ * atomics (arbitrary order inside a list), then sorts every list over its own
+ * depth range: lists of up to 4096 instances in one CTA's shared memory, longer
+ * ones cut into 4096-key jobs that run stable 9-bit passes together (as many
+ * passes as the list's depth offsets have 9-bit digits); equal depths are then
+ * ordered by record index.  Requires n_units * n_tiles <= 256 * 240 * 135
+ * (else GS_ERR_INVALID). */
+int gs_bin_sort_bucketed(const gs_proj* proj, const gs_units* units, int width, int height,
+                         int64_t max_instances, void* workspace, size_t workspace_bytes,
+                         uint32_t* sorted_vals, uint32_t* ranges, uint32_t* d_num_instances,
+                         const gs_schedule* sched, int* d_status, gs_stream_t stream);
 
 /* Buffer sizes of a gs_schedule for n_units units of width x height and the
  * given instance capacity and chunk length: *max_jobs, *max_checkpoints. */
@@ -269,15 +289,18 @@ int gs_render_fwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32
                   float* final_T, uint32_t* n_contrib, int variant, const gs_schedule* sched,
                   gs_stream_t stream);
 
-/* Diagnostic work counters of the last gs_render_fwd (device uint64 [3]):
+/* Diagnostic work counters of the last gs_render_fwd (device uint64 [5]):
  * d_count[0] = blended (pixel, record) pairs (records before n_contrib whose
  * alpha reaches 1/255); d_count[1] = (pixel, list entry) pairs a sequential
  * front-to-back walk evaluates up to and including the entry that stops the
- * pixel (the forward's algorithmic work unit); d_count[2] = sum of n_contrib
- * over pixels (the entries the reverse replay walks: the backward's unit). */
+ * pixel; d_count[2] = sum of n_contrib over pixels (the entries the reverse
+ * replay walks); d_count[3], d_count[4] = the pairs of d_count[1] and
+ * d_count[2] whose block mask (block_masks of gs_bin_sort's schedule, in
+ * sorted order; NULL gives 0) reaches the pixel's 4x4 block: the work of a
+ * walk that skips records whose alpha box misses the pixel's block. */
 int gs_blend_pairs(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges,
                    int n_units, int width, int height, const uint32_t* n_contrib,
-                   unsigned long long* d_count, gs_stream_t stream);
+                   const uint16_t* block_masks, unsigned long long* d_count, gs_stream_t stream);
 
 /* ---- a4: masked photometric loss (mask: Sec. II, "Image Rendering and
  * Masking") ---------------------------------------------------------------
@@ -351,12 +374,15 @@ int gs_adam_step(float* params, float* grads, float* m, float* v, int64_t n_gaus
  * grads may be NULL; otherwise it also receives the gradient.  A Gaussian
  * whose screen-space or parameter gradient holds a non-finite value sets
  * GS_ERR_NONFINITE in d_status (may be NULL) and keeps its parameters and
- * moments. */
+ * moments.  sparse != 0: a Gaussian whose gradient is zero in this step (no
+ * view of the call reaches it with a non-zero screen-space gradient) keeps its
+ * parameters and moments too, and costs no parameter or moment traffic (the
+ * sparse Adam of 3D-GS updates only the Gaussians a view touches). */
 int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
                         const gs_camera* cams, const gs_proj* proj, const gs_grad2d* g2d, float* m,
                         float* v, const float* lr_init, const float* lr_final, int32_t lr_steps,
                         float beta1, float beta2, float eps, const int32_t* d_step, float* grads,
-                        int* d_status, gs_stream_t stream);
+                        int sparse, int* d_status, gs_stream_t stream);
 
 /* *d_step += 1 on the device (keeps CUDA-graph replays advancing). */
 int gs_step_advance(int32_t* d_step, gs_stream_t stream);
@@ -423,6 +449,7 @@ typedef struct gs_train_batch_desc {
   const gs_grad2d* g2d;          /* host struct of [P] screen-space gradient buffers */
   float* grads;                  /* parameter gradient (planes layout) or NULL */
   int32_t variant;               /* blend execution shape (gs_render_fwd) */
+  int32_t sparse_adam;           /* gs_project_bwd_adam's sparse flag */
 } gs_train_batch_desc;
 
 int gs_train_batch(const gs_train_batch_desc* desc, int* d_status, gs_stream_t stream);

@@ -89,6 +89,8 @@ def _declare(L):
     L.orc_bf16_round.restype = C.c_double
     L.orc_mlp_features.argtypes = [C.c_int, _D, _D, _I, _D, _D]
     L.orc_mlp_forward.argtypes = [C.c_int] + [_D] * 10
+    L.orc_mlp_forward_full.argtypes = [C.c_int] + [_D] * 12
+    L.orc_bf16_round_array.argtypes = [C.c_longlong, _D, _D]
     L.orc_mlp_backward.argtypes = [C.c_int] + [_D] * 14
     L.orc_mlp_backward.restype = C.c_double
     L.orc_init_gaussians.argtypes = [C.c_int, _D, C.c_int, _D, C.c_double, _D, _D, _D]
@@ -318,8 +320,11 @@ def owned(means, part_of, boxes, closed_hi):
 
 
 def bf16_round(x):
-    f = lib().orc_bf16_round
-    return np.vectorize(lambda v: f(float(v)))(np.asarray(x, dtype=np.float64))
+    """Nearest bfloat16 value (ties to even) of every element, as float64."""
+    a = _d(x)
+    out = np.zeros_like(a)
+    lib().orc_bf16_round_array(a.size, _p(a), _p(out))
+    return out
 
 
 def mlp_features(pts, nrm, knn_idx, knn_dist):
@@ -336,8 +341,10 @@ def mlp_forward(X, w):
     n = X.shape[0]
     H1, H2, Y = np.zeros((n, 64)), np.zeros((n, 64)), np.zeros((n, 8))
     ws = [_d(w[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
-    lib().orc_mlp_forward(n, _p(X), *[_p(a) for a in ws], _p(H1), _p(H2), _p(Y))
-    return dict(H1=H1, H2=H2, Y=Y)
+    A1, A2 = np.zeros((n, 64)), np.zeros((n, 64))
+    lib().orc_mlp_forward_full(n, _p(X), *[_p(a) for a in ws], _p(H1), _p(H2), _p(Y), _p(A1), _p(A2))
+    # H1, H2: post-ReLU activations before their bf16 rounding; A1, A2: the pre-activations
+    return dict(H1=H1, H2=H2, Y=Y, A1=A1, A2=A2)
 
 
 def mlp_backward(X, w, T):

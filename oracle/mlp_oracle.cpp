@@ -39,6 +39,10 @@ extern "C" {
 
 double orc_bf16_round(double x) { return bf16(x); }
 
+void orc_bf16_round_array(long long n, const double* x, double* out) {
+  for (long long k = 0; k < n; ++k) out[k] = bf16(x[k]);
+}
+
 // Features of point i from its 16 nearest neighbours (sorted by distance):
 // [0, 48)   neighbour offsets (p_j - p_i) divided by the mean neighbour distance
 // [48, 96)  neighbour unit normals
@@ -65,10 +69,10 @@ void orc_mlp_features(int n, const double* pts, const double* nrm, const int* kn
 }
 
 // Forward pass.  H1, H2 are the post-ReLU activations before their bf16
-// rounding; Y the outputs.
-void orc_mlp_forward(int n, const double* X, const double* W1, const double* b1, const double* W2,
-                     const double* b2, const double* W3, const double* b3, double* H1, double* H2,
-                     double* Y) {
+// rounding; Y the outputs; A1, A2 (may be NULL) the pre-activations.
+void orc_mlp_forward_full(int n, const double* X, const double* W1, const double* b1, const double* W2,
+                          const double* b2, const double* W3, const double* b3, double* H1, double* H2,
+                          double* Y, double* A1, double* A2) {
   std::vector<double> w1(KIN * HID), w2(HID * HID), w3(HID * KOUT);
   for (int k = 0; k < KIN * HID; ++k) w1[k] = bf16(W1[k]);
   for (int k = 0; k < HID * HID; ++k) w2[k] = bf16(W2[k]);
@@ -80,6 +84,7 @@ void orc_mlp_forward(int n, const double* X, const double* W1, const double* b1,
       double acc = 0;
       for (int k = 0; k < KIN; ++k) acc += xb[k] * w1[k * HID + o];
       acc += b1[o];
+      if (A1) A1[(size_t)HID * i + o] = acc;
       double h = acc > 0 ? acc : 0.0;
       H1[(size_t)HID * i + o] = h;
       h1b[o] = bf16(h);
@@ -88,6 +93,7 @@ void orc_mlp_forward(int n, const double* X, const double* W1, const double* b1,
       double acc = 0;
       for (int k = 0; k < HID; ++k) acc += h1b[k] * w2[k * HID + o];
       acc += b2[o];
+      if (A2) A2[(size_t)HID * i + o] = acc;
       double h = acc > 0 ? acc : 0.0;
       H2[(size_t)HID * i + o] = h;
       h2b[o] = bf16(h);
@@ -98,6 +104,12 @@ void orc_mlp_forward(int n, const double* X, const double* W1, const double* b1,
       Y[(size_t)KOUT * i + o] = acc + b3[o];
     }
   }
+}
+
+void orc_mlp_forward(int n, const double* X, const double* W1, const double* b1, const double* W2,
+                     const double* b2, const double* W3, const double* b3, double* H1, double* H2,
+                     double* Y) {
+  orc_mlp_forward_full(n, X, W1, b1, W2, b2, W3, b3, H1, H2, Y, nullptr, nullptr);
 }
 
 // Loss L = sum (Y - T)^2 / (8 n) and its weight gradients, by the chain rule

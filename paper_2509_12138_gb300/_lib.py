@@ -36,7 +36,8 @@ class GsGrad2d(C.Structure):
 
 class GsSchedule(C.Structure):
     _fields_ = [("tile_order", C.c_void_p), ("block_masks", C.c_void_p), ("job_base", C.c_void_p),
-                ("jobs", C.c_void_p), ("checkpoints", C.c_void_p), ("chunk_last", C.c_void_p), ("max_jobs", C.c_int64),
+                ("jobs", C.c_void_p), ("checkpoints", C.c_void_p), ("chunk_last", C.c_void_p),
+                ("stop_queue", C.c_void_p), ("max_jobs", C.c_int64),
                 ("max_checkpoints", C.c_int64), ("chunk", C.c_int32), ("walk_whole_lists", C.c_int32)]
 
 
@@ -67,7 +68,8 @@ class GsTrainBatchDesc(C.Structure):
                 ("ranges", C.c_void_p), ("d_num_instances", C.c_void_p), ("sched", C.POINTER(GsSchedule)),
                 ("img", C.c_void_p), ("final_T", C.c_void_p), ("n_contrib", C.c_void_p), ("loss_ws", C.c_void_p),
                 ("loss_ws_bytes", C.c_size_t), ("d_loss", C.c_void_p), ("dL_dimg", C.c_void_p),
-                ("g2d", C.POINTER(GsGrad2d)), ("grads", C.c_void_p), ("variant", C.c_int32)]
+                ("g2d", C.POINTER(GsGrad2d)), ("grads", C.c_void_p), ("variant", C.c_int32),
+                ("sparse_adam", C.c_int32)]
 
 
 assert C.sizeof(GsCamera) == 96
@@ -89,9 +91,11 @@ SIGNATURES = {
                           C.POINTER(GsSchedule), VP, VP]),
     "gs_schedule_sizes": (I32, [I32, I32, I32, I64, I32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "gs_bin_sort_static": (I32, [C.POINTER(GsProj), C.POINTER(GsUnits), I32, I32, VP, VP, VP, VP, VP]),
+    "gs_bin_sort_bucketed": (I32, [C.POINTER(GsProj), C.POINTER(GsUnits), I32, I32, I64, VP, SZ, VP, VP, VP,
+                                 C.POINTER(GsSchedule), VP, VP]),
     "gs_render_fwd": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, c_f32p, VP, VP, VP, I32,
                             C.POINTER(GsSchedule), VP]),
-    "gs_blend_pairs": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, VP, VP, VP]),
+    "gs_blend_pairs": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, VP, VP, VP, VP]),
     "gs_loss_workspace_size": (SZ, [I32, I32, I32]),
     "gs_peak_threads": (I32, [I32]),
     "gs_peak_issue": (I32, [I32, I32, I32, F32, F32, VP, VP]),
@@ -104,7 +108,7 @@ SIGNATURES = {
     "gs_adam_step": (I32, [VP, VP, VP, VP, I64, I32, c_f32p, c_f32p, I32, F32, F32, F32, VP, I32, VP, VP]),
     "gs_step_advance": (I32, [VP, VP]),
     "gs_project_bwd_adam": (I32, [VP, I64, I32, C.POINTER(GsUnits), VP, C.POINTER(GsProj), C.POINTER(GsGrad2d), VP,
-                                  VP, c_f32p, c_f32p, I32, F32, F32, F32, VP, VP, VP, VP]),
+                                  VP, c_f32p, c_f32p, I32, F32, F32, F32, VP, VP, I32, VP, VP]),
     "gs_knn_workspace_size": (SZ, [I64, c_i32p]),
     "gs_knn": (I32, [VP, I64, I32, c_f32p, F32, c_i32p, VP, SZ, VP, VP, VP]),
     "gs_mlp_param_count": (I32, []),

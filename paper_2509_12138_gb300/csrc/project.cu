@@ -586,7 +586,8 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam(float4* __restrict__ p
                                                           const float4* __restrict__ grgb, float4* __restrict__ m,
                                                           float4* __restrict__ v, AdamLR lr, int lr_steps, float b1,
                                                           float b2, float eps, const int32_t* __restrict__ d_step,
-                                                          float4* __restrict__ grads, int* __restrict__ status) {
+                                                          float4* __restrict__ grads, int sparse,
+                                                          int* __restrict__ status) {
   constexpr int NP = ShCount<DEG>::NP;
   constexpr int NPL = 3 + NP;
   __shared__ float4 s_lr[16];
@@ -616,9 +617,13 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam(float4* __restrict__ p
                  make_float4(dq[0], dq[1], dq[2], dq[3])};
   // a non-finite gradient is reported and leaves this Gaussian's parameters and moments as they are
   bool ok = finite4(G[0]) && finite4(G[1]) && finite4(G[2]);
+  bool any = false;
   #pragma unroll
-  for (int k = 0; k < 4 * NP; ++k) ok = ok && isfinite(dsh[k]);
+  for (int k = 0; k < 4 * NP; ++k) { ok = ok && isfinite(dsh[k]); any = any || dsh[k] != 0.f; }
   if (!ok) set_status(status, GS_ERR_NONFINITE);
+  #pragma unroll
+  for (int k = 0; k < 3; ++k) any = any || G[k].x != 0.f || G[k].y != 0.f || G[k].z != 0.f || G[k].w != 0.f;
+  if (sparse && !any) ok = false;  // sparse: a Gaussian without gradient keeps its state
   float4 Pv[3] = {mean, sop, quat};
   #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -673,7 +678,8 @@ __global__ void __launch_bounds__(PBA_T) k_project_bwd_adam1(float4* __restrict_
                                                            const float4* __restrict__ grgb, float4* __restrict__ m,
                                                            float4* __restrict__ v, AdamLR lr, int lr_steps, float b1,
                                                            float b2, float eps, const int32_t* __restrict__ d_step,
-                                                           float4* __restrict__ grads, int* __restrict__ status) {
+                                                           float4* __restrict__ grads, int sparse,
+                                                           int* __restrict__ status) {
   constexpr int NC = ShCount<DEG>::NC;
   constexpr int NP = ShCount<DEG>::NP;
   constexpr int NPL = 3 + NP;
@@ -688,6 +694,32 @@ __global__ void __launch_bounds__(PBA_T) k_project_bwd_adam1(float4* __restrict_
   __syncthreads();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
+  // the unit containing i (units are disjoint here)
+  int uu = -1;
+  int64_t pidx = 0;
+  for (int u = 0; u < U.n; ++u) {
+    int64_t l = i - U.gauss_begin[u];
+    if (l >= 0 && l < U.proj_base[u + 1] - U.proj_base[u]) { uu = u; pidx = U.proj_base[u] + l; break; }
+  }
+  bool vis = uu >= 0 && __ldg(radius + pidx) > 0;
+  // sparse: a Gaussian with no screen-space gradient in this step keeps its parameters and moments (no
+  // load, no store), as a sparse Adam updates only the Gaussians a view touches
+  if (sparse) {
+    bool any = false;
+    if (vis) {
+      float2 a = gxy[pidx];
+      float4 b = gco[pidx], c = grgb[pidx];
+      any = a.x != 0.f || a.y != 0.f || b.x != 0.f || b.y != 0.f || b.z != 0.f || b.w != 0.f || c.x != 0.f ||
+            c.y != 0.f || c.z != 0.f;
+    }
+    if (!any) {
+      if (grads) {
+        #pragma unroll
+        for (int k = 0; k < NPL; ++k) grads[k * N + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      return;
+    }
+  }
   extern __shared__ float4 s_stage[];  // [NPL][PBA_T] parameters, then [PBA_R][2][PBA_T] m, v ring
   const int tl = threadIdx.x;
   float4* sP = s_stage;
@@ -708,14 +740,6 @@ __global__ void __launch_bounds__(PBA_T) k_project_bwd_adam1(float4* __restrict_
   #pragma unroll
   for (int q = 0; q < PBA_R; ++q) mv_copy(q);
   float ibc1 = 1.f / (1.f - powf(b1, (float)t)), ibc2 = 1.f / (1.f - powf(b2, (float)t));
-  // the unit containing i (units are disjoint here)
-  int uu = -1;
-  int64_t pidx = 0;
-  for (int u = 0; u < U.n; ++u) {
-    int64_t l = i - U.gauss_begin[u];
-    if (l >= 0 && l < U.proj_base[u + 1] - U.proj_base[u]) { uu = u; pidx = U.proj_base[u] + l; break; }
-  }
-  bool vis = uu >= 0 && __ldg(radius + pidx) > 0;
   cp_async_wait<PBA_R>();  // this thread's parameter planes have landed
   float4 mean = sP[tl], sop = sP[PBA_T + tl], quat = sP[2 * PBA_T + tl];
   float dmean[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, dlogit = 0.f;
@@ -1059,8 +1083,8 @@ GS_API int gs_step_advance(int32_t* d_step, gs_stream_t stream) {
 GS_API int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
                                const gs_camera* cams, const gs_proj* proj, const gs_grad2d* g2d, float* m, float* v,
                                const float* lr_init, const float* lr_final, int32_t lr_steps, float beta1,
-                               float beta2, float eps, const int32_t* d_step, float* grads, int* d_status,
-                               gs_stream_t stream) {
+                               float beta2, float eps, const int32_t* d_step, float* grads, int sparse,
+                               int* d_status, gs_stream_t stream) {
   GS_RANGE("gs_project_bwd_adam");
   UnitTable U;
   int64_t P = 0;
@@ -1096,7 +1120,7 @@ GS_API int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, co
   k_project_bwd_adam1<D><<<grid1, PBA_T, smem1, s>>>((float4*)params, n_gauss, U, cams, proj->radius,            \
                                                 (const float2*)g2d->dxy, (const float4*)g2d->dconic_op,          \
                                                 (const float4*)g2d->drgb, (float4*)m, (float4*)v, lr, lr_steps,   \
-                                                beta1, beta2, eps, d_step, (float4*)grads, d_status)
+                                                beta1, beta2, eps, d_step, (float4*)grads, sparse, d_status)
     switch (sh_degree) {
       case 0: GS_PBA1(0); break;
       case 1: GS_PBA1(1); break;
@@ -1110,7 +1134,7 @@ GS_API int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, co
   k_project_bwd_adam<D><<<grid, block, 0, s>>>((float4*)params, n_gauss, U, cams, proj->radius,                 \
                                                (const float2*)g2d->dxy, (const float4*)g2d->dconic_op,          \
                                                (const float4*)g2d->drgb, (float4*)m, (float4*)v, lr, lr_steps,   \
-                                               beta1, beta2, eps, d_step, (float4*)grads, d_status)
+                                               beta1, beta2, eps, d_step, (float4*)grads, sparse, d_status)
   switch (sh_degree) {
     case 0: GS_PBA(0); break;
     case 1: GS_PBA(1); break;

@@ -365,8 +365,9 @@ template <bool LOCAL = false>
 __device__ __forceinline__ void walk_fwd(const uint32_t* __restrict__ vals, const uint16_t* __restrict__ masks,
                                          const float4* __restrict__ xy, const float4* __restrict__ conic_op,
                                          const float4* __restrict__ rgb, uint32_t off, int beg, int end,
-                                         uint32_t wbits, float tox, float toy, float fx, float fy, Rec* my, float& T, float& c0,
-                                         float& c1, float& c2, int& last, bool& done, LocalAcc* loc = nullptr) {
+                                         uint32_t wbits, float tox, float toy, float fx, float fy, Rec* my, float& T,
+                                         float& c0, float& c1, float& c2, int& last, bool& done,
+                                         LocalAcc* loc = nullptr) {
   const unsigned FULL = 0xffffffffu;
   int lane = threadIdx.x & 31;
   bool h1 = false;
@@ -462,7 +463,7 @@ template <int BW>
 struct PixelOf {
   int u, tile, tx, ty, px, py, pix_local;
   bool inside;
-  uint32_t wbits;
+  uint32_t wbits;  // the 4x4 blocks of the warp's pixels
   __device__ __forceinline__ PixelOf(const uint32_t* __restrict__ order, int o, int w, int n_tiles, int TX, int W,
                                      int H) {
     uint32_t f = order[o];
@@ -559,37 +560,19 @@ __global__ void __launch_bounds__(32) k_render_fwd_m(const uint2* __restrict__ r
 // of hundreds of chunks the walk is otherwise one load latency per chunk.
 constexpr int CB = 4;
 
+// The combine of one pixel (pass 2), for a list of nch >= 2 chunks; cstar
+// receives the pixel's stop chunk (-1: none, or a stop inside chunk 0).
 template <int BW>
-__global__ void __launch_bounds__(32) k_render_fwd_combine(const uint2* __restrict__ ranges,
-                                                                 const uint32_t* __restrict__ order,
-                                                                 const uint32_t* __restrict__ job_base, int K,
-                                                                 float4* __restrict__ ckpt,
-                                                                 uint32_t* __restrict__ chunk_last, int W, int H,
-                                                                 int TX, int n_tiles, float bg0, float bg1, float bg2,
-                                                                 float* __restrict__ img, float* __restrict__ final_T,
-                                                                 uint32_t* __restrict__ n_contrib) {
-  int o = (int)(blockIdx.x >> 3), w = (int)(blockIdx.x & 7u);
-  int nch = (int)(job_base[o + 1] - job_base[o]);
-  if (nch == 1) return;
-  PixelOf<BW> P(order, o, w, n_tiles, TX, W, H);
-  if (!P.inside) return;
-  int64_t plane = (int64_t)W * H;
-  int64_t pix = (int64_t)P.py * W + P.px;
-  float* im = img + (int64_t)P.u * 3 * plane;
-  float* fT = final_T + (int64_t)P.u * plane;
-  uint32_t* nc = n_contrib + (int64_t)P.u * plane;
-  if (nch == 0) {
-    im[pix] = bg0; im[plane + pix] = bg1; im[2 * plane + pix] = bg2;
-    fT[pix] = 1.f;
-    nc[pix] = 0u;
-    return;
-  }
+__device__ __forceinline__ void combine_pixel(const PixelOf<BW>& P, int o, int nch, int64_t plane, int64_t pix,
+                                              float* im, float* fT, uint32_t* nc, float4* __restrict__ ckpt,
+                                              uint32_t* __restrict__ chunk_last,
+                                              const uint32_t* __restrict__ job_base, float bg0, float bg1, float bg2,
+                                              int& cstar) {
   float c0 = im[pix], c1 = im[plane + pix], c2 = im[2 * plane + pix];
   float T = fT[pix];
   uint32_t lw0 = nc[pix];
   int last = (int)(lw0 & ~STOP_BIT);
   bool done = (lw0 & STOP_BIT) != 0u;  // a stop in chunk 0 is exact
-  int cstar = -1;
   int64_t cp0 = (int64_t)job_base[o] - o;
   float4* cpp = ckpt + cp0 * TILE_PIX + P.pix_local;       // slot of boundary b: cpp[(b - 1) * TILE_PIX]
   uint32_t* clp = chunk_last + cp0 * TILE_PIX + P.pix_local;
@@ -679,14 +662,55 @@ __global__ void __launch_bounds__(32) k_render_fwd_combine(const uint2* __restri
   }
 }
 
-// Pass 3: job (list o, chunk c, block w) walks chunk c again for the pixels
-// whose stop chunk is c, from the state pass 2 left, and writes their final
-// image, final_T, n_contrib and the checkpoints after c (final state).
+template <int BW>
+__global__ void __launch_bounds__(32) k_render_fwd_combine(const uint2* __restrict__ ranges,
+                                                                 const uint32_t* __restrict__ order,
+                                                                 const uint32_t* __restrict__ job_base, int K,
+                                                                 float4* __restrict__ ckpt,
+                                                                 uint32_t* __restrict__ chunk_last, int W, int H,
+                                                                 int TX, int n_tiles, float bg0, float bg1, float bg2,
+                                                                 float* __restrict__ img, float* __restrict__ final_T,
+                                                                 uint32_t* __restrict__ n_contrib,
+                                                                 uint32_t* __restrict__ queue, uint32_t qcap) {
+  int o = (int)(blockIdx.x >> 3), w = (int)(blockIdx.x & 7u);
+  int nch = (int)(job_base[o + 1] - job_base[o]);
+  if (nch == 1) return;
+  PixelOf<BW> P(order, o, w, n_tiles, TX, W, H);
+  int64_t plane = (int64_t)W * H;
+  int64_t pix = (int64_t)P.py * W + P.px;
+  float* im = img + (int64_t)P.u * 3 * plane;
+  float* fT = final_T + (int64_t)P.u * plane;
+  uint32_t* nc = n_contrib + (int64_t)P.u * plane;
+  if (nch == 0) {  // the whole warp returns here
+    if (P.inside) {
+      im[pix] = bg0; im[plane + pix] = bg1; im[2 * plane + pix] = bg2;
+      fT[pix] = 1.f;
+      nc[pix] = 0u;
+    }
+    return;
+  }
+  int cstar = -1;
+  if (P.inside) combine_pixel(P, o, nch, plane, pix, im, fT, nc, ckpt, chunk_last, job_base, bg0, bg1, bg2, cstar);
+  // queue the units pass 3 walks: one (stop chunk, pixel block) per distinct stop chunk of the warp's pixels
+  int key = cstar >= 1 ? cstar : -1;
+  unsigned peers = __match_any_sync(0xffffffffu, key);
+  if (key >= 1 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+    uint32_t slot = atomicAdd(queue + qcap, 1u);
+    queue[slot] = ((job_base[o] + (uint32_t)key) << 3) | (uint32_t)w;
+  }
+}
+
+// Pass 3: the units pass 2 queued, (list o, chunk c, block w) with some pixel
+// of block w stopping in chunk c: walks chunk c again for those pixels from
+// the state pass 2 left, and writes their final image, final_T, n_contrib and
+// the checkpoints after c (final state).  A resident grid takes the queued
+// units from a ticket counter (zeroed before the launch), so no block is
+// launched for a chunk in which nothing stops.
 template <int BW>
 __global__ void __launch_bounds__(32) k_render_fwd_stop(const uint2* __restrict__ ranges,
                                                               const uint32_t* __restrict__ order,
                                                               const uint32_t* __restrict__ job_base,
-                                                              const uint32_t* __restrict__ jobs, int K, int NT,
+                                                              const uint32_t* __restrict__ jobs, int K,
                                                               float4* __restrict__ ckpt,
                                                               uint32_t* __restrict__ chunk_last,
                                                               const uint32_t* __restrict__ vals,
@@ -696,14 +720,17 @@ __global__ void __launch_bounds__(32) k_render_fwd_stop(const uint2* __restrict_
                                                               const float4* __restrict__ rgb, int W, int H, int TX,
                                                               int n_tiles, float bg0, float bg1, float bg2,
                                                               float* __restrict__ img, float* __restrict__ final_T,
-                                                              uint32_t* __restrict__ n_contrib) {
+                                                              uint32_t* __restrict__ n_contrib,
+                                                              const uint32_t* __restrict__ queue, uint32_t qcap,
+                                                              uint32_t* __restrict__ ticket) {
   __shared__ Rec s_rec[32];
-  uint32_t jid = blockIdx.x >> 3;
-  if (jid >= job_base[NT]) return;
+  const uint32_t total = queue[qcap];
+  auto job = [&](uint32_t ent) {
+  uint32_t jid = ent >> 3;
   int o = (int)jobs[2 * (int64_t)jid], ch = (int)jobs[2 * (int64_t)jid + 1];
   if (ch == 0) return;
   int nch = (int)(job_base[o + 1] - job_base[o]);
-  int w = (int)(blockIdx.x & 7u);
+  int w = (int)(ent & 7u);
   PixelOf<BW> P(order, o, w, n_tiles, TX, W, H);
   uint2 rg = ranges[(int64_t)P.u * n_tiles + P.tile];
   int L = (int)(rg.y - rg.x);
@@ -787,7 +814,16 @@ __global__ void __launch_bounds__(32) k_render_fwd_stop(const uint2* __restrict_
   im[2 * plane + pix] = c2 + T * bg2;
   fT[pix] = T;
   nc[pix] = (uint32_t)last;
+  };
+  const bool lead = (threadIdx.x & 31) == 0;
+  uint32_t e = __shfl_sync(0xffffffffu, lead ? atomicAdd(ticket, 1u) : 0u, 0);
+  while (e < total) {
+    uint32_t nxt = lead ? atomicAdd(ticket, 1u) : 0u;
+    job(queue[e]);
+    e = __shfl_sync(0xffffffffu, nxt, 0);
+  }
 }
+
 
 // Forward walking whole lists: one warp per (list, pixel block) in tile order
 // composites its list chunk after chunk and stores (T, C) of each pixel in
@@ -1133,18 +1169,22 @@ __global__ void k_order_scatter(const uint2* __restrict__ ranges, int n, const u
 // counts[0] = blended (pixel, record) pairs (records before n_contrib whose
 // alpha reaches 1/255); counts[1] = (pixel, list entry) pairs the sequential
 // front-to-back walk evaluates, up to and including the entry that stops the
-// pixel (the forward's algorithmic unit); counts[2] = sum of n_contrib, the
-// entries the reverse replay walks per pixel (the backward's unit).
+// pixel; counts[2] = sum of n_contrib, the entries the reverse replay walks
+// per pixel; counts[3], counts[4] = the pairs of counts[1] and counts[2]
+// whose block mask reaches the pixel's 4x4 block (0 without masks): the
+// (pixel, entry) pairs a walk that skips masked-out records must evaluate.
 __global__ void __launch_bounds__(TILE_PIX) k_blend_pairs(const uint2* __restrict__ ranges,
                                                           const uint32_t* __restrict__ vals,
                                                           const float4* __restrict__ xy,
                                                           const float4* __restrict__ conic_op, int W, int H, int TX,
                                                           int n_tiles, const uint32_t* __restrict__ n_contrib,
+                                                          const uint16_t* __restrict__ masks,
                                                           unsigned long long* __restrict__ counts) {
   int tile = blockIdx.x, u = blockIdx.y;
   int tx = tile % TX, ty = tile / TX;
   int px = tx * TILE + (threadIdx.x & 15), py = ty * TILE + (threadIdx.x >> 4);
-  unsigned long long c = 0, visited = 0, replay = 0;
+  const uint32_t blk = 1u << (4 * ((threadIdx.x >> 4) >> 2) + ((threadIdx.x & 15) >> 2));
+  unsigned long long c = 0, visited = 0, replay = 0, m_visited = 0, m_replay = 0;
   if (px < W && py < H) {
     uint2 rg = ranges[(int64_t)u * n_tiles + tile];
     int L = (int)(rg.y - rg.x);
@@ -1153,6 +1193,9 @@ __global__ void __launch_bounds__(TILE_PIX) k_blend_pairs(const uint2* __restric
     float T = 1.f;
     int j = 0;
     for (; j < L; ++j) {
+      bool in_mask = masks && (masks[rg.x + j] & blk);
+      m_visited += in_mask ? 1 : 0;
+      m_replay += (in_mask && j < last) ? 1 : 0;
       uint32_t p = vals[rg.x + j];
       float4 m = xy[p];
       float4 co = conic_op[p];
@@ -1168,17 +1211,23 @@ __global__ void __launch_bounds__(TILE_PIX) k_blend_pairs(const uint2* __restric
       T = tT;
     }
     visited = (unsigned long long)min(j + 1, L);
+    // the remaining entries up to n_contrib count for the replay (none after a stop, which ends the list)
+    for (int k = j + 1; k < min(last, L); ++k) m_replay += (masks && (masks[rg.x + k] & blk)) ? 1 : 0;
   }
   #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     c += __shfl_xor_sync(0xffffffffu, c, o);
     visited += __shfl_xor_sync(0xffffffffu, visited, o);
     replay += __shfl_xor_sync(0xffffffffu, replay, o);
+    m_visited += __shfl_xor_sync(0xffffffffu, m_visited, o);
+    m_replay += __shfl_xor_sync(0xffffffffu, m_replay, o);
   }
   if ((threadIdx.x & 31) == 0) {
     if (c) atomicAdd(&counts[0], c);
     if (visited) atomicAdd(&counts[1], visited);
     if (replay) atomicAdd(&counts[2], replay);
+    if (m_visited) atomicAdd(&counts[3], m_visited);
+    if (m_replay) atomicAdd(&counts[4], m_replay);
   }
 }
 
@@ -1225,6 +1274,8 @@ int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const u
     return GS_ERR_INVALID;
   int TX = (width + TILE - 1) / TILE, TY = (height + TILE - 1) / TILE;
   dim3 grid(TX * TY * n_units);
+  // the re-walk queue holds at most one entry per (chunk job, pixel block); its count follows it
+  const uint32_t qcap = sched ? (uint32_t)(8 * sched->max_jobs) : 0u;
 #define GS_FWD(BW)                                                                                                  \
   if (sched && sched->walk_whole_lists) {                                                                          \
     k_render_fwd_seq<BW><<<dim3(grid.x * 8), 32, 0, s>>>(                                                           \
@@ -1238,14 +1289,17 @@ int gs_render_fwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const u
         (float4*)sched->checkpoints, sched->chunk_last, sorted_vals, sched->block_masks, (const float4*)proj->xy,   \
         (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2],  \
         img, final_T, n_contrib, sched_ticket(sched));                                                              \
+    if (cudaMemsetAsync(sched->stop_queue + qcap, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;     \
     k_render_fwd_combine<BW><<<dim3(grid.x * 8), 32, 0, s>>>(                                                       \
         (const uint2*)ranges, sched->tile_order, sched->job_base, sched->chunk, (float4*)sched->checkpoints,        \
-        sched->chunk_last, width, height, TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib);              \
-    k_render_fwd_stop<BW><<<dim3((unsigned)(sched->max_jobs * 8)), 32, 0, s>>>(                                     \
-        (const uint2*)ranges, sched->tile_order, sched->job_base, sched->jobs, sched->chunk, (int)grid.x,            \
+        sched->chunk_last, width, height, TX, TX * TY, bg[0], bg[1], bg[2], img, final_T, n_contrib,               \
+        sched->stop_queue, qcap);                                                                                   \
+    if (cudaMemsetAsync(sched_ticket(sched), 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;          \
+    k_render_fwd_stop<BW><<<dim3(resident_grid(k_render_fwd_stop<BW>, (int64_t)qcap)), 32, 0, s>>>(                 \
+        (const uint2*)ranges, sched->tile_order, sched->job_base, sched->jobs, sched->chunk,                        \
         (float4*)sched->checkpoints, sched->chunk_last, sorted_vals, sched->block_masks, (const float4*)proj->xy,    \
         (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX, TX * TY, bg[0], bg[1], bg[2],  \
-        img, final_T, n_contrib);                                                                                   \
+        img, final_T, n_contrib, sched->stop_queue, qcap, sched_ticket(sched));                                     \
   } else                                                                                                            \
     k_render_fwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, nullptr, sorted_vals, (const float4*)proj->xy, \
                                                (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, \
@@ -1308,18 +1362,18 @@ int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const ui
 }
 
 GS_API int gs_blend_pairs(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
-                          int width, int height, const uint32_t* n_contrib, unsigned long long* d_count,
-                          gs_stream_t stream) {
+                          int width, int height, const uint32_t* n_contrib, const uint16_t* block_masks,
+                          unsigned long long* d_count, gs_stream_t stream) {
   GS_RANGE("gs_blend_pairs");
   if (!proj || !proj->xy || !proj->conic_op || !sorted_vals || !ranges || !n_contrib || !d_count || n_units < 1 ||
       n_units > GS_MAX_UNITS || width <= 0 || height <= 0)
     return GS_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemsetAsync(d_count, 0, 3 * sizeof(unsigned long long), s) != cudaSuccess) return GS_ERR_CUDA;
+  if (cudaMemsetAsync(d_count, 0, 5 * sizeof(unsigned long long), s) != cudaSuccess) return GS_ERR_CUDA;
   int TX = (width + TILE - 1) / TILE, TY = (height + TILE - 1) / TILE;
   k_blend_pairs<<<dim3(TX * TY, n_units), TILE_PIX, 0, s>>>((const uint2*)ranges, sorted_vals, (const float4*)proj->xy,
                                                             (const float4*)proj->conic_op, width, height, TX, TX * TY,
-                                                            n_contrib, d_count);
+                                                            n_contrib, block_masks, d_count);
   return gs_check_launch();
 }
 

@@ -20,6 +20,9 @@
 
 using namespace gs;
 
+// words of the bucketed sort's long-list scratch (sort_seg.cu), held in the value buffers
+void gs_seg_ws_words(int64_t cap, size_t* words_s, size_t* words_l);
+
 namespace {
 
 constexpr int SCAN_T = 256;
@@ -50,8 +53,11 @@ WsLayout ws_layout(int64_t P, int64_t C) {
   L.bsums = o; o += align256(sizeof(uint32_t) * (size_t)(nsb + 1));
   L.keys0 = o; o += align256(sizeof(uint64_t) * (size_t)(C > 0 ? C : 1));
   L.keys1 = o; o += align256(sizeof(uint64_t) * (size_t)(C > 0 ? C : 1));
-  L.vals0 = o; o += align256(sizeof(uint32_t) * (size_t)(C > 0 ? C : 1));
-  L.vals1 = o; o += align256(sizeof(uint32_t) * (size_t)(C > 0 ? C : 1));
+  size_t ws_s = 0, ws_l = 0;
+  gs_seg_ws_words(C, &ws_s, &ws_l);
+  const size_t cw = (size_t)(C > 0 ? C : 1);
+  L.vals0 = o; o += align256(sizeof(uint32_t) * (cw > ws_s ? cw : ws_s));
+  L.vals1 = o; o += align256(sizeof(uint32_t) * (cw > ws_l ? cw : ws_l));
   L.hist = o; o += align256(sizeof(uint32_t) * RS_BINS_MAX * (size_t)(nrb > 0 ? nrb : 1));
   L.totals = o; o += align256(sizeof(uint32_t) * RS_BINS_MAX * MAX_PASSES);
   L.cur = o; o += align256(sizeof(int32_t) * (MAX_PASSES + 1));
@@ -519,10 +525,10 @@ GS_API size_t gs_bin_sort_workspace_size(int64_t n_proj, int64_t max_instances) 
 // The sort chain, shared by gs_bin_sort and the fixed-scratch variant.
 int gs_tile_order_impl(const uint32_t* ranges, int n, uint32_t* ws, uint32_t* order, cudaStream_t s);
 
-// Tile order, then the chunk jobs in that order.
+// Tile order (unless the sort already made it), then the chunk jobs in that order.
 int gs_schedule_jobs(const uint32_t* ranges, int NT, char* order_ws, char* scan_ws, const gs_schedule* sched,
-                     cudaStream_t s) {
-  int r = gs_tile_order_impl(ranges, NT, (uint32_t*)order_ws, sched->tile_order, s);
+                     cudaStream_t s, bool order_done = false) {
+  int r = order_done ? GS_OK : gs_tile_order_impl(ranges, NT, (uint32_t*)order_ws, sched->tile_order, s);
   if (r != GS_OK) return r;
   unsigned nb = (unsigned)((NT + 255) / 256);
   k_chunk_count<<<nb, 256, 0, s>>>((const uint2*)ranges, sched->tile_order, NT, sched->chunk, sched->job_base);
@@ -535,7 +541,7 @@ int gs_schedule_jobs(const uint32_t* ranges, int NT, char* order_ws, char* scan_
 int gs_schedule_check(const gs_schedule* sched, int n_units, int n_tiles, int64_t max_instances) {
   if (!sched) return GS_OK;
   if (!sched->tile_order || !sched->block_masks || !sched->job_base || !sched->jobs || !sched->checkpoints ||
-      !sched->chunk_last ||
+      !sched->chunk_last || !sched->stop_queue ||
       sched->chunk < 32 || (sched->chunk & 31))
     return GS_ERR_INVALID;
   int64_t NT = (int64_t)n_units * n_tiles;
@@ -545,9 +551,16 @@ int gs_schedule_check(const gs_schedule* sched, int n_units, int n_tiles, int64_
   return GS_OK;
 }
 
+int gs_seg_sort(const UnitTable& U, int64_t P, const gs_proj* proj, int width, int height, int64_t cap,
+                uint64_t* keysA, uint64_t* keysB, uint32_t* wsS, uint32_t* wsL, uint32_t* bsums, uint32_t* ctr,
+                uint32_t* sorted_vals, uint32_t* ranges, uint16_t* masks, cudaStream_t s);
+
+// method 0: the global LSD radix sort of (unit | tile | depth) keys; 1: the bucketed sort (sort_seg.cu).
+// Both give the same lists, ranges and masks.
 int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int height, int64_t max_instances,
                      void* workspace, size_t workspace_bytes, uint32_t* sorted_vals, uint32_t* ranges,
-                     uint32_t* d_num_instances, const gs_schedule* sched, int* d_status, cudaStream_t s) {
+                     uint32_t* d_num_instances, const gs_schedule* sched, int* d_status, cudaStream_t s,
+                     int method) {
   uint16_t* block_masks = sched ? sched->block_masks : nullptr;
   UnitTable U;
   int64_t P = 0;
@@ -596,6 +609,14 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
   k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);
   k_scan_down<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, P, bsums, nsb, offsets, max_instances,
                                                d_num_instances, d_status);
+  if (method == 1) {
+    if ((int64_t)n_tiles * U.n > MAX_SCHED_TILES) return GS_ERR_INVALID;
+    int r = gs_seg_sort(U, P, proj, width, height, max_instances, k0, k1, v0, v1, (uint32_t*)(ws + L.jscan),
+                        (uint32_t*)cur, sorted_vals, ranges, block_masks, s);
+    if (r != GS_OK) return r;
+    if (sched) return gs_schedule_jobs(ranges, n_tiles * U.n, ws + L.order, ws + L.jscan, sched, s);
+    return gs_check_launch();
+  }
   // block masks ride in the keys when unit | tile | depth leave bits 48..63 free
   int key_masks = (block_masks && key_bits <= 48) ? 1 : 0;
   k_duplicate<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(U, (const float4*)proj->xy, (const float4*)proj->conic_op,
@@ -638,7 +659,16 @@ GS_API int gs_bin_sort(const gs_proj* proj, const gs_units* units, int width, in
                        uint32_t* d_num_instances, const gs_schedule* sched, int* d_status, gs_stream_t stream) {
   GS_RANGE("gs_bin_sort");
   return gs_bin_sort_impl(proj, units, width, height, max_instances, workspace, workspace_bytes, sorted_vals,
-                          ranges, d_num_instances, sched, d_status, (cudaStream_t)stream);
+                          ranges, d_num_instances, sched, d_status, (cudaStream_t)stream, 0);
+}
+
+GS_API int gs_bin_sort_bucketed(const gs_proj* proj, const gs_units* units, int width, int height,
+                                int64_t max_instances, void* workspace, size_t workspace_bytes,
+                                uint32_t* sorted_vals, uint32_t* ranges, uint32_t* d_num_instances,
+                                const gs_schedule* sched, int* d_status, gs_stream_t stream) {
+  GS_RANGE("gs_bin_sort_bucketed");
+  return gs_bin_sort_impl(proj, units, width, height, max_instances, workspace, workspace_bytes, sorted_vals,
+                          ranges, d_num_instances, sched, d_status, (cudaStream_t)stream, 1);
 }
 
 GS_API int gs_schedule_sizes(int n_units, int width, int height, int64_t max_instances, int chunk, int64_t* max_jobs,
@@ -668,7 +698,7 @@ GS_API int gs_merge_render(const float* params, int64_t n_gauss, int sh_degree, 
   int r = gs_preprocess(params, n_gauss, sh_degree, &one, cam, width, height, owned, proj, d_status, stream);
   if (r != GS_OK) return r;
   r = gs_bin_sort_impl(proj, &one, width, height, max_instances, workspace, workspace_bytes, sorted_vals, ranges,
-                       d_num_instances, sched, d_status, (cudaStream_t)stream);
+                       d_num_instances, sched, d_status, (cudaStream_t)stream, 0);
   if (r != GS_OK) return r;
   return gs_render_fwd_impl(proj, sorted_vals, ranges, 1, width, height, bg, img, final_T, n_contrib, 0, sched,
                             (cudaStream_t)stream);

@@ -35,7 +35,8 @@
 
 int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int height, int64_t max_instances,
                      void* workspace, size_t workspace_bytes, uint32_t* sorted_vals, uint32_t* ranges,
-                     uint32_t* d_num_instances, const gs_schedule* sched, int* d_status, cudaStream_t s);
+                     uint32_t* d_num_instances, const gs_schedule* sched, int* d_status, cudaStream_t s,
+                     int method);
 
 namespace {
 
@@ -122,5 +123,5 @@ GS_API int gs_bin_sort_static(const gs_proj* proj, const gs_units* units, int wi
   int r = scratch_ptr(&ws);
   if (r != GS_OK) return r;
   return gs_bin_sort_impl(proj, units, width, height, cap, ws, SCRATCH_BYTES, sorted_vals, ranges, d_num_instances,
-                          nullptr, d_status, (cudaStream_t)stream);
+                          nullptr, d_status, (cudaStream_t)stream, 0);
 }

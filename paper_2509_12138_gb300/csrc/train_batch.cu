@@ -112,7 +112,7 @@ GS_API int gs_train_batch(const gs_train_batch_desc* d, int* d_status, gs_stream
     return r;
   if ((r = gs_project_bwd_adam(d->params, d->n_gauss, d->sh_degree, d->units, d->cams_step, d->proj, d->g2d,
                                d->adam_m, d->adam_v, d->lr_init, d->lr_final, d->lr_steps, d->beta1, d->beta2, d->eps,
-                               d->d_step, d->grads, d_status, stream)) != GS_OK)
+                               d->d_step, d->grads, d->sparse_adam, d_status, stream)) != GS_OK)
     return r;
   return gs_step_advance(d->d_step, stream);
 }

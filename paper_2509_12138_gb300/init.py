@@ -116,8 +116,10 @@ class MLPTrainer:
         self.loss = torch.zeros(1, dtype=torch.float32, device=weights.device)
         self.lr = lr
 
-    def step(self, points, normals, knn_idx, knn_dist, targets):
-        n = points.shape[0]
+    def step(self, points, normals, knn_idx, knn_dist, targets, n: int | None = None):
+        """One Adam step on the first n points (all by default; neighbour indices may point anywhere in
+        ``points``)."""
+        n = points.shape[0] if n is None else int(n)
         check(self.L.gs_mlp_train_step(_ptr(points), _ptr(normals), _ptr(knn_idx), _ptr(knn_dist), _ptr(targets), n,
                                        _ptr(self.w), _ptr(self.grad), _ptr(self.m), _ptr(self.v), float(self.lr),
                                        _ptr(self.step_dev), _ptr(self.loss), _stream()), "gs_mlp_train_step")

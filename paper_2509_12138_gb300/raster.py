@@ -210,9 +210,10 @@ class Frame:
         self.jobs = torch.zeros(2 * mj.value, dtype=torch.int32, device=self.device)
         self.checkpoints = torch.zeros((mc.value, 256, 4), dtype=torch.float32, device=self.device)
         self.chunk_last = torch.zeros((mc.value, 256), dtype=torch.int32, device=self.device)
+        self.stop_queue = torch.zeros(8 * mj.value + 1, dtype=torch.int32, device=self.device)
         self.sched = GsSchedule(self.tile_order.data_ptr(), self.block_masks.data_ptr(), self.job_base.data_ptr(),
                                 self.jobs.data_ptr(), self.checkpoints.data_ptr(), self.chunk_last.data_ptr(),
-                                mj.value, mc.value, self.chunk)
+                                self.stop_queue.data_ptr(), mj.value, mc.value, self.chunk)
         self.num_instances = torch.zeros(1, dtype=torch.int32, device=self.device)
 
     # -- steps
@@ -222,11 +223,12 @@ class Frame:
                                    self.W, self.H, C.byref(owned.struct) if owned is not None else None,
                                    C.byref(self.proj), _ptr(self.status), _stream()), "gs_preprocess")
 
-    def sort(self):
-        check(self.L.gs_bin_sort(C.byref(self.proj), C.byref(self.units.struct), self.W, self.H, self.cap,
-                                 _ptr(self.sort_ws), self.sort_ws.numel(), _ptr(self.sorted_vals), _ptr(self.ranges),
-                                 _ptr(self.num_instances), self._sched(), _ptr(self.status), _stream()),
-              "gs_bin_sort")
+    def sort(self, bucketed: bool = False):
+        """gs_bin_sort (one global radix sort), or gs_bin_sort_bucketed (per-list sorts; same results)."""
+        fn = self.L.gs_bin_sort_bucketed if bucketed else self.L.gs_bin_sort
+        check(fn(C.byref(self.proj), C.byref(self.units.struct), self.W, self.H, self.cap, _ptr(self.sort_ws),
+                 self.sort_ws.numel(), _ptr(self.sorted_vals), _ptr(self.ranges), _ptr(self.num_instances),
+                 self._sched(), _ptr(self.status), _stream()), "gs_bin_sort")
 
     def render(self, bg):
         bgc = (C.c_float * 3)(*[float(x) for x in bg])
@@ -299,12 +301,16 @@ class Frame:
 
     def blend_pairs(self) -> dict:
         """Work counters of the last forward (diagnostic; synchronises): blended (pixel, record) pairs,
-        (pixel, entry) pairs a sequential walk evaluates until each pixel stops, and the sum of n_contrib."""
-        cnt = torch.zeros(3, dtype=torch.int64, device=self.device)
+        (pixel, entry) pairs a sequential walk evaluates until each pixel stops, the sum of n_contrib, and
+        the two pair counts restricted to entries whose block mask reaches the pixel's 4x4 block."""
+        cnt = torch.zeros(5, dtype=torch.int64, device=self.device)
+        masks = self.block_masks if self.use_masks else None
         check(self.L.gs_blend_pairs(C.byref(self.proj), _ptr(self.sorted_vals), _ptr(self.ranges), self.units.n,
-                                    self.W, self.H, _ptr(self.n_contrib), _ptr(cnt), _stream()), "gs_blend_pairs")
+                                    self.W, self.H, _ptr(self.n_contrib), _ptr(masks), _ptr(cnt), _stream()),
+              "gs_blend_pairs")
         c = cnt.tolist()
-        return {"blended": int(c[0]), "fwd_pairs": int(c[1]), "bwd_pairs": int(c[2])}
+        return {"blended": int(c[0]), "fwd_pairs": int(c[1]), "bwd_pairs": int(c[2]), "fwd_pairs_masked": int(c[3]),
+                "bwd_pairs_masked": int(c[4])}
 
     def xy64(self) -> np.ndarray:
         """Pixel-space means [P, 2] as float64: the exact sums of the float pairs (synchronises)."""
@@ -387,6 +393,8 @@ class Adam:
         self.step_dev = torch.zeros(1, dtype=torch.int32, device=params.device)
         # device status word of step(): GS_ERR_NONFINITE when a gradient value was not finite
         self.status = torch.zeros(1, dtype=torch.int32, device=params.device)
+        # fused_step: Gaussians without gradient in a step keep their state (sparse Adam)
+        self.sparse = False
         init, fin = (lrs or LearningRates()).tables(sh_degree, extent)
         self.lr_init = np.ascontiguousarray(init.reshape(-1))
         self.lr_final = np.ascontiguousarray(fin.reshape(-1))
@@ -403,7 +411,7 @@ class Adam:
                                          _ptr(self.v), self.lr_init.ctypes.data_as(_lib.c_f32p),
                                          self.lr_final.ctypes.data_as(_lib.c_f32p), self.lr_steps, self.b1, self.b2,
                                          self.eps, _ptr(self.step_dev), _ptr(frame.grads) if keep_grads else None,
-                                         _ptr(frame.status), _stream()), "gs_project_bwd_adam")
+                                         int(self.sparse), _ptr(frame.status), _stream()), "gs_project_bwd_adam")
         check(self.L.gs_step_advance(_ptr(self.step_dev), _stream()), "gs_step_advance")
 
     def state_dict(self) -> dict:

@@ -260,8 +260,9 @@ class BatchedTrainer:
         d.g2d = C.pointer(fr.g2d)
         d.grads = fr.grads.data_ptr() if self.keep_grads else None
         d.variant = fr.variant
+        d.sparse_adam = int(opt.sparse)
         self.desc = d
-        self._desc_key = (fr.cap, self.keep_grads, fr.use_masks, fr.walk_whole_lists)
+        self._desc_key = (fr.cap, self.keep_grads, fr.use_masks, fr.walk_whole_lists, opt.sparse)
 
     def _load(self, t: int):
         """The step buffers of step t (gs_gather_views on the device), for inspection and capacity sizing."""
@@ -272,7 +273,8 @@ class BatchedTrainer:
 
     def _chain(self):
         fr = self.frame
-        if self.desc is None or self._desc_key != (fr.cap, self.keep_grads, fr.use_masks, fr.walk_whole_lists):
+        if self.desc is None or self._desc_key != (fr.cap, self.keep_grads, fr.use_masks, fr.walk_whole_lists,
+                                                   self.opt.sparse):
             self._build_desc()
         check(self.L.gs_train_batch(C.byref(self.desc), _ptr(fr.status), _stream()), "gs_train_batch")
 

@@ -17,23 +17,21 @@ BG = (1.0, 1.0, 1.0)
 
 
 def test_stats_parity():
+    """The statistics of two steps, from seeded screen-space gradients and radii (a third of the records
+    culled) written into a frame's buffers, against the oracle on the same values."""
     n, deg, W, H = 3000, 1, 120, 90
-    g, cams = scenes.random_scene(n, deg, 91, W, H)
-    params = gs.pack_params(g, deg)
-    camd = gs.pack_cameras(cams)
-    gt, mask = scenes.random_gt(W, H, 92)
+    rng = np.random.default_rng(91)
+    dxy = rng.normal(0.0, 1e-4, (n, 2)).astype(np.float32)
+    rad = np.where(rng.random(n) < 1 / 3, 0, rng.integers(1, 40, n)).astype(np.int32)
     fr = gs.Frame(n, gs.Units.single(n), W, H, deg)
-    fr.fit_capacity(params, camd)
-    fr.forward(params, camd, BG)
-    fr.loss(torch.from_numpy(gt).cuda()[None], torch.from_numpy(mask).cuda()[None], 0.2)
-    fr.backward(params, camd, BG)
+    fr.dxy.copy_(torch.from_numpy(dxy))
+    fr.radius.copy_(torch.from_numpy(rad))
     d = Densifier(n)
     d.accumulate(fr)
     d.accumulate(fr)
     torch.cuda.synchronize()
-    dxy, rad = fr.dxy.cpu().numpy(), fr.radius.cpu().numpy()
-    ga, dn, mr = D.stats(np.zeros(n), np.zeros(n), np.zeros(n), dxy, rad, W, H)
-    ga, dn, mr = D.stats(ga, dn, mr, dxy, rad, W, H)
+    ga, dn, mr = D.stats(np.zeros(n), np.zeros(n), np.zeros(n), dxy.astype(np.float64), rad, W, H)
+    ga, dn, mr = D.stats(ga, dn, mr, dxy.astype(np.float64), rad, W, H)
     assert (rad > 0).sum() > 100
     np.testing.assert_allclose(d.grad_accum.cpu().numpy(), ga, rtol=1e-5, atol=1e-12)
     np.testing.assert_array_equal(d.denom.cpu().numpy(), dn)
@@ -67,7 +65,8 @@ def test_plan_and_apply_parity(step):
     d.grad_accum.copy_(torch.from_numpy(grad))
     d.denom.copy_(torch.from_numpy(denom))
     d.max_radius.copy_(torch.from_numpy(maxr))
-    z = torch.randn((n, 2, 3), device="cuda", generator=torch.Generator(device="cuda").manual_seed(step))
+    z_np = np.random.default_rng(step + 1).standard_normal((n, 2, 3)).astype(np.float32)
+    z = torch.from_numpy(z_np).cuda()
     counts = d.plan(params, step)
     po, mo, vo = d.apply(params, m, v, deg, counts, z)
     torch.cuda.synchronize()
@@ -78,7 +77,7 @@ def test_plan_and_apply_parity(step):
     gm = {k: np.asarray(x, np.float64) for k, x in un(m).items()}
     gv = {k: np.asarray(x, np.float64) for k, x in un(v).items()}
     ref, rm, rv = D.apply({k: np.asarray(x, np.float64) for k, x in g.items()}, gm, gv, act,
-                          z.double().cpu().numpy())
+                          z_np.astype(np.float64))
     out, om, ov = un(po), un(mo), un(vo)
     n_copy = counts[0] + counts[1]
     for k in ref:
@@ -97,8 +96,10 @@ def test_opacity_reset_parity():
     params = gs.pack_params(g, deg)
     m = gs.pack_params({k: v + 1.0 for k, v in g.items()}, deg)
     v = gs.pack_params({k: v + 2.0 for k, v in g.items()}, deg)
+    m_in = {k: np.asarray(x + 1.0, np.float64) for k, x in g.items()}
+    v_in = {k: np.asarray(x + 2.0, np.float64) for k, x in g.items()}
     Densifier(n).reset_opacity(params, m, v)
-    rg, rm, rv = D.opacity_reset(g, gs.unpack_params(m, deg), gs.unpack_params(v, deg))
+    rg, rm, rv = D.opacity_reset({k: np.asarray(x, np.float64) for k, x in g.items()}, m_in, v_in)
     out = gs.unpack_params(params, deg)
     np.testing.assert_allclose(out["logit_opacity"], rg["logit_opacity"], atol=1e-6)
     np.testing.assert_array_equal(gs.unpack_params(m, deg)["logit_opacity"], 0.0)

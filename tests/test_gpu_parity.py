@@ -251,7 +251,7 @@ def test_autograd_function_matches_frame_backward():
     fr = gsp.Frame(n, gsp.Units.single(n), W, H, deg)
     camd = gsp.pack_cameras(cams)
     img = gsp.rasterize(params, fr, camd, BG)
-    w = torch.randn_like(img)
+    w = torch.from_numpy(np.random.default_rng(51).standard_normal(tuple(img.shape)).astype(np.float32)).cuda()
     (img * w).sum().backward()
     fr2 = gsp.Frame(n, gsp.Units.single(n), W, H, deg)
     fr2.forward(params.detach(), camd, BG)
@@ -312,6 +312,10 @@ def test_blend_work_counters():
     nc = int(fr.n_contrib.sum().item())
     assert c["bwd_pairs"] == nc > 0
     assert 0 < c["blended"] <= c["bwd_pairs"] <= c["fwd_pairs"]
+    # a blended pair has alpha >= 1/255, so its record's alpha box (and block mask) reaches the pixel
+    assert c["blended"] <= c["bwd_pairs_masked"] <= c["bwd_pairs"]
+    assert c["bwd_pairs_masked"] <= c["fwd_pairs_masked"] <= c["fwd_pairs"]
+    assert c["fwd_pairs_masked"] < c["fwd_pairs"]
     lens = (fr.ranges[:, 1] - fr.ranges[:, 0]).cpu().numpy()
     assert c["fwd_pairs"] <= int(lens.sum()) * 256
 
@@ -369,3 +373,47 @@ def test_fused_projection_backward_adam_vs_oracle():
     assert np.all(np.abs(v_gpu - v_ref) <= 3e-3 * np.abs(v_ref) + 4 * ulp(v_ref))
     assert np.all(np.abs(p_gpu - p_ref) <= 1e-3 * lr_el + 4 * ulp(p_ref))
     assert int(opt.step_dev.item()) == 11
+
+
+def test_sparse_adam_skips_only_gaussians_without_gradient():
+    """With the sparse flag, a Gaussian whose screen-space gradient is zero in the step (here: behind the
+    image, or outside the loss mask) keeps its parameters and moments; every other Gaussian gets exactly
+    the dense update."""
+    import paper_2509_12138_gb300 as gsp
+    n, deg, W, H = 1500, 1, 96, 72
+    g, cams = _case(n, deg, 30, W, H)
+    g["means"][:200, 0] += 50.0  # far to the side of the view: culled, no gradient
+    gt, mask = scenes.random_gt(W, H, 31)
+    rng = np.random.default_rng(1)
+    res = []
+    for sparse in (False, True):
+        # fixed-point gradient accumulation: both runs see bit-identical screen-space gradients
+        fr = gsp.Frame(n, gsp.Units.single(n), W, H, deg, deterministic=True)
+        params = gsp.pack_params(g, deg)
+        camd = gsp.pack_cameras(cams)
+        fr.fit_capacity(params, camd)
+        fr.forward(params, camd, BG)
+        fr.loss(torch.from_numpy(gt).cuda()[None], torch.from_numpy(mask).cuda()[None], 0.2)
+        fr.blend_backward(BG)
+        opt = gsp.Adam(params, deg, extent=1.0, lr_steps=100)
+        r = np.random.default_rng(1)
+        opt.m.copy_(torch.from_numpy(r.normal(0, 1e-3, tuple(opt.m.shape)).astype(np.float32)))
+        opt.v.copy_(torch.from_numpy(r.uniform(1e-7, 1e-6, tuple(opt.v.shape)).astype(np.float32)))
+        opt.step_dev.fill_(4)
+        m0, v0, p0 = opt.m.clone(), opt.v.clone(), params.clone()
+        opt.sparse = sparse
+        opt.fused_step(fr, camd, keep_grads=True)
+        torch.cuda.synchronize()
+        assert fr.read_status() == 0
+        g2 = torch.cat([fr.dxy[:n].abs(), fr.dco[:n].abs(), fr.drgb[:n, :3].abs()], 1).sum(1) > 0
+        res.append(dict(p=params.clone(), m=opt.m.clone(), v=opt.v.clone(), p0=p0, m0=m0, v0=v0, touched=g2))
+    dense, sp = res
+    touched = sp["touched"]
+    assert torch.equal(touched, dense["touched"]) and 0 < int(touched.sum()) < n
+    assert int((~touched[:200]).sum()) == 200
+    for k in ("p", "m", "v"):
+        # touched Gaussians: the dense update bit for bit; untouched: unchanged state
+        assert torch.equal(sp[k][:, touched], dense[k][:, touched]), k
+        assert torch.equal(sp[k][:, ~touched], sp[k + "0"][:, ~touched]), k
+    # the dense step does move untouched Gaussians (momentum), so the two differ there
+    assert not torch.equal(dense["p"][:, ~touched], dense["p0"][:, ~touched])
