@@ -71,6 +71,10 @@ def parse():
                     help="instead of the throughput line: the plain vs batched + learned-init comparison")
     ap.add_argument("--exp-gaussians", type=int, default=1_000_000)
     ap.add_argument("--exp-steps", type=int, default=3000)
+    ap.add_argument("--exp-modes", type=int, default=8, help="learned-init: interface modes")
+    ap.add_argument("--exp-width", type=int, default=1920)
+    ap.add_argument("--exp-height", type=int, default=1080)
+    ap.add_argument("--exp-views", type=int, default=64)
     return ap.parse_args()
 
 
@@ -595,9 +599,12 @@ def run_learned_init_experiment(args):
     torch.cuda.set_device(0)
     import __graft_entry__
     __graft_entry__.build()
-    n, W, H, V, steps = args.exp_gaussians, 1920, 1080, 64, args.exp_steps
+    n, W, H, V, steps = args.exp_gaussians, args.exp_width, args.exp_height, args.exp_views, args.exp_steps
+    modes = args.exp_modes
     every = max(steps // 15, 1)
-    src = workload.isosurface_scene(n, 8, V, W, H, sh_degree=3, seed=101)
+    t_scene = time.perf_counter()
+    src = workload.isosurface_scene(n, modes, V, W, H, sh_degree=3, seed=101)
+    t_scene = time.perf_counter() - t_scene
     h_src, trained = X.run_plain(src, steps, every)
     t0 = time.perf_counter()
     w, losses = X.fit_mlp(src, trained, steps=600)
@@ -605,19 +612,25 @@ def run_learned_init_experiment(args):
     t_fit = time.perf_counter() - t0
     del src, trained
     torch.cuda.empty_cache()
-    dst = workload.isosurface_scene(n, 8, V, W, H, sh_degree=3, seed=202)
+    dst = workload.isosurface_scene(n, modes, V, W, H, sh_degree=3, seed=202)
     h_plain, _ = X.run_plain(dst, steps, every)
     target = h_plain.psnr[-1] - 0.1
     h_learn, _ = X.run_learned_batched(dst, w, steps, every, views_per_step=2, stop_at=target)
     s_hit, t_hit = h_learn.time_to(target)
-    line = {"experiment": "learned-init vs plain", "gaussians": n, "width": W, "height": H, "views": V,
+    fit = None if t_hit is None else round(t_hit + t_fit, 3)
+    fit_src = None if t_hit is None else round(t_hit + t_fit + h_src.seconds[-1], 3)
+    line = {"experiment": "learned-init vs plain", "gaussians": n, "modes": modes, "width": W, "height": H,
+            "views": V, "scene_build_seconds": round(t_scene, 1),
             "plain": {"steps": steps, "seconds": round(h_plain.seconds[-1], 3), "psnr": round(h_plain.psnr[-1], 3),
                       "psnr_at_init": round(h_plain.psnr[0], 3)},
             "batched_learned": {"views_per_step": 2, "psnr_at_init": round(h_learn.psnr[0], 3),
                                 "steps_to_plain_psnr_minus_0.1dB": s_hit,
                                 "seconds_to_plain_psnr_minus_0.1dB": None if t_hit is None else round(t_hit, 3),
+                                "seconds_with_mlp_fit": fit,
+                                "seconds_with_mlp_fit_and_source_training": fit_src,
                                 "final_psnr": round(h_learn.psnr[-1], 3)},
-            "mlp": {"fit_seconds": round(t_fit, 3), "loss_first": losses[0], "loss_last": losses[-1],
+            "mlp": {"fit_seconds": round(t_fit, 3), "source_training_seconds": round(h_src.seconds[-1], 3),
+                    "loss_first": losses[0], "loss_last": losses[-1],
                     "trained_on": "converged splats of another seed of the interface"},
             "history": {"plain": [h_plain.steps, [round(x, 3) for x in h_plain.seconds],
                                   [round(x, 3) for x in h_plain.psnr]],

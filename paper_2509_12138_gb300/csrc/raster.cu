@@ -348,6 +348,50 @@ __device__ __forceinline__ uint32_t warp_block_bits(int w) {
   return bits;
 }
 
+// Transpose of a 32 x 32 bit matrix held one row per lane: bit j of the
+// result in lane p is bit p of lane j's word (five butterfly exchanges of
+// 16-, 8-, 4-, 2- and 1-bit blocks).
+__device__ __forceinline__ uint32_t transpose32(uint32_t x) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t MS[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+  #pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int s = 16 >> k;
+    const uint32_t m = MS[k];
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, s);
+    x = (lane & s) ? (((y & ~m) >> s) | (x & ~m)) : ((x & m) | ((y & m) << s));
+  }
+  return x;
+}
+
+// Lanes of a warp's pixel block (bw x 32 / bw pixels from tile-local origin
+// (ox, oy), lane = row bw + column) whose pixel centre lies in a record's
+// alpha >= 1/255 box (alpha_box: conservative, so every pixel outside it has
+// alpha < 1/255 and would be skipped by the blend).  (rx, ry): the record's
+// tile-local position; co: conic and opacity.
+__device__ __forceinline__ uint32_t hit_lanes(float rx, float ry, float4 co, float ox, float oy, int bw) {
+  float pm;
+  const float4 b = alpha_box(make_float2(rx, ry), co, pm);
+  if (!(b.x <= b.y)) return 0u;
+  const int bh = 32 / bw;
+  const float c0 = fmaxf(ceilf(b.x - ox), 0.f), c1 = fminf(floorf(b.y - ox), (float)(bw - 1));
+  const float r0 = fmaxf(ceilf(b.z - oy), 0.f), r1 = fminf(floorf(b.w - oy), (float)(bh - 1));
+  if (!(c0 <= c1) || !(r0 <= r1)) return 0u;
+  const int lo = (int)c0, rl = (int)r0, rh = (int)r1;
+  const uint32_t cm = ((2u << ((int)c1 - lo)) - 1u) << lo;
+  uint32_t m = 0u;
+  for (int r = rl; r <= rh; ++r) m |= cm << (r * bw);
+  return m;
+}
+
+// Rounds with at least this many hits walk per-lane hit lists: each lane
+// takes, in list order, only the hits whose alpha box reaches its pixel
+// (forward walk; reverse replay).  Below them the box and the transpose cost
+// more than the hits they spare (10M Gaussians at 1080p, thresholds swept
+// over 1-24: 12 and 8 were fastest).
+constexpr int HIT_LISTS_FWD = 12;
+constexpr int HIT_LISTS_BWD = 8;
+
 // Front-to-back walk of list entries [beg, end) (indices from the list's
 // start `off`) for one warp's pixel block, compositing into (T, c, last) of
 // the lanes that are not done; a lane whose transmittance would fall below
@@ -370,6 +414,9 @@ __device__ __forceinline__ void walk_fwd(const uint32_t* __restrict__ vals, cons
                                          LocalAcc* loc = nullptr) {
   const unsigned FULL = 0xffffffffu;
   int lane = threadIdx.x & 31;
+  // the warp's pixel block: tile-local origin and width
+  const float ox = __shfl_sync(FULL, fx, 0), oy = __shfl_sync(FULL, fy, 0);
+  const int bw = __popc(__ballot_sync(FULL, fy == oy));
   bool h1 = false;
   float4 m1 = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 co1 = make_float4(0.f, 0.f, 0.f, 0.f), cc1 = co1;
@@ -393,8 +440,9 @@ __device__ __forceinline__ void walk_fwd(const uint32_t* __restrict__ vals, cons
     mk2 = 0;
     if (k2 < end) { mk2 = masks[off + k2]; pk2 = vals[off + k2]; }
     unsigned mask = __ballot_sync(FULL, hit);
+    const float rx = rel_pos(m.x, m.z, tox), ry = rel_pos(m.y, m.w, toy);
     if (hit) {
-      my[lane].a = make_float4(rel_pos(m.x, m.z, tox), rel_pos(m.y, m.w, toy), co.x, co.y);
+      my[lane].a = make_float4(rx, ry, co.x, co.y);
       my[lane].b = make_float4(co.z, co.w, c.w, 0.f);
       my[lane].c = c;
     }
@@ -422,16 +470,32 @@ __device__ __forceinline__ void walk_fwd(const uint32_t* __restrict__ vals, cons
         loc->t *= 1.f - alpha;
       }
     };
-    while (mask) {
-      int j1 = __ffs(mask) - 1;
-      mask &= mask - 1;
-      bool two = mask != 0u;
-      int j2 = two ? __ffs(mask) - 1 : j1;
-      if (two) mask &= mask - 1;
-      float a1 = hit_alpha(j1);
-      float a2 = two ? hit_alpha(j2) : 0.f;
-      composite(j1, a1);
-      if (two) composite(j2, a2);
+    if (__popc(mask) >= HIT_LISTS_FWD) {
+      // per-lane hit lists: bit j of `mine` = hit j's alpha box reaches this lane's pixel
+      uint32_t mine = transpose32(hit ? hit_lanes(rx, ry, co, ox, oy, bw) : 0u);
+      while (mine && !done) {
+        int j1 = __ffs(mine) - 1;
+        mine &= mine - 1;
+        bool two = mine != 0u;
+        int j2 = two ? __ffs(mine) - 1 : j1;
+        if (two) mine &= mine - 1;
+        float a1 = hit_alpha(j1);
+        float a2 = two ? hit_alpha(j2) : 0.f;
+        composite(j1, a1);
+        if (two) composite(j2, a2);
+      }
+    } else {
+      while (mask) {
+        int j1 = __ffs(mask) - 1;
+        mask &= mask - 1;
+        bool two = mask != 0u;
+        int j2 = two ? __ffs(mask) - 1 : j1;
+        if (two) mask &= mask - 1;
+        float a1 = hit_alpha(j1);
+        float a2 = two ? hit_alpha(j2) : 0.f;
+        composite(j1, a1);
+        if (two) composite(j2, a2);
+      }
     }
     __syncwarp();
   }
@@ -1042,12 +1106,70 @@ __global__ void __launch_bounds__(32, 32) k_render_bwd_m(const uint2* __restrict
       mk2 = 0;
       if (top - 64 > cbeg && k2 >= cbeg) { mk2 = masks[rg.x + k2]; pk2 = vals[rg.x + k2]; }
       unsigned mask = __ballot_sync(FULL, hit);
+      const float rx = rel_pos(m.x, m.z, tox), ry = rel_pos(m.y, m.w, toy);
       if (hit) {
-        my[lane].a = make_float4(rel_pos(m.x, m.z, tox), rel_pos(m.y, m.w, toy), co.x, co.y);
+        my[lane].a = make_float4(rx, ry, co.x, co.y);
         my[lane].b = make_float4(co.z, co.w, c.w, __uint_as_float(p));
         my[lane].c = c;
       }
       __syncwarp();
+      if (QUEUE && __popc(mask) >= HIT_LISTS_BWD) {
+        // per-lane hit lists, back to front: bit j of `mine` = hit j's alpha box reaches this lane's
+        // pixel and the entry lies in front of the pixel's last contribution; every pair goes to the ring
+        uint32_t mine = transpose32(hit ? hit_lanes(rx, ry, co, (float)((w % NWX) * BW), (float)((w / NWX) * BH), BW)
+                                        : 0u);
+        const int upto = last - base;
+        mine &= upto >= 32 ? 0xffffffffu : (upto > 0 ? (1u << upto) - 1u : 0u);
+        while (__any_sync(FULL, mine != 0u)) {
+          const bool act = mine != 0u;
+          const int j = act ? 31 - __clz(mine) : 0;
+          if (act) mine &= ~(1u << j);
+          bool contrib = false;
+          float dx = 0.f, dy = 0.f, dp = 0.f, v5 = 0.f, v6 = 0.f, v7 = 0.f, v8 = 0.f;
+          float4 ra = my[j].a, rb = my[j].b;
+          if (act) {
+            dx = ra.x - lx; dy = ra.y - ly;
+            float power = splat_power(ra.z, ra.w, rb.x, dx, dy);
+            if (power <= 0.f && power >= rb.z) {
+              float G = __expf(power);
+              float araw = rb.y * G;
+              bool clamped = araw > ALPHA_MAX;
+              float alpha = clamped ? ALPHA_MAX : araw;
+              if (alpha >= ALPHA_MIN) {
+                contrib = true;
+                float4 rc = my[j].c;
+                T = __fdividef(T, 1.f - alpha);
+                float wgt = alpha * T;
+                v6 = wgt * g0; v7 = wgt * g1; v8 = wgt * g2;
+                float dalpha = T * ((rc.x - S0) * g0 + (rc.y - S1) * g1 + (rc.z - S2) * g2);
+                S0 = alpha * rc.x + (1.f - alpha) * S0;
+                S1 = alpha * rc.y + (1.f - alpha) * S1;
+                S2 = alpha * rc.z + (1.f - alpha) * S2;
+                if (!clamped) {
+                  v5 = G * dalpha;
+                  dp = araw * dalpha;
+                }
+              }
+            }
+          }
+          unsigned cm = __ballot_sync(FULL, contrib);
+          if (!cm) continue;
+          if (contrib) {
+            int e = (qt + __popc(cm & ((1u << lane) - 1u))) & (QCAP - 1);
+            s_q[e] = make_float4(dx, dy, dp, v5);
+            s_q[QCAP + e] = make_float4(ra.z, ra.w, rb.x, rb.w);
+            s_q[2 * QCAP + e] = make_float4(v6, v7, v8, 0.f);
+          }
+          qt += __popc(cm);
+          if (qt - qh >= 32) {
+            __syncwarp();
+            bwd_queue_flush(s_q, qh, 32, lane, dxy, dco, drgb);
+            qh += 32;
+            __syncwarp();
+          }
+        }
+        mask = 0u;  // every hit of the round is done
+      }
       while (mask) {
         int j = 31 - __clz(mask);
         mask &= ~(1u << j);
