@@ -75,6 +75,11 @@ def parse():
     ap.add_argument("--exp-width", type=int, default=1920)
     ap.add_argument("--exp-height", type=int, default=1080)
     ap.add_argument("--exp-views", type=int, default=64)
+    ap.add_argument("--exp-views-per-step", type=int, default=2, help="learned-init: views per batched step")
+    ap.add_argument("--exp-learned-lr", type=float, default=1.0,
+                    help="learned-init: factor on the scale, opacity and rotation learning rates of the learned form")
+    ap.add_argument("--exp-learned-mean-lr", type=float, default=1.0,
+                    help="learned-init: factor on the position learning rates of the learned form")
     return ap.parse_args()
 
 
@@ -615,7 +620,14 @@ def run_learned_init_experiment(args):
     dst = workload.isosurface_scene(n, modes, V, W, H, sh_degree=3, seed=202)
     h_plain, _ = X.run_plain(dst, steps, every)
     target = h_plain.psnr[-1] - 0.1
-    h_learn, _ = X.run_learned_batched(dst, w, steps, every, views_per_step=2, stop_at=target)
+    from paper_2509_12138_gb300.raster import LearningRates
+    f = args.exp_learned_lr
+    d = LearningRates()
+    fm = args.exp_learned_mean_lr
+    lrs = LearningRates(mean_init=d.mean_init * fm, mean_final=d.mean_final * fm, scale=d.scale * f,
+                        opacity=d.opacity * f, rotation=d.rotation * f)
+    vps = args.exp_views_per_step
+    h_learn, _ = X.run_learned_batched(dst, w, steps, every, views_per_step=vps, lrs=lrs, stop_at=target)
     s_hit, t_hit = h_learn.time_to(target)
     fit = None if t_hit is None else round(t_hit + t_fit, 3)
     fit_src = None if t_hit is None else round(t_hit + t_fit + h_src.seconds[-1], 3)
@@ -623,7 +635,9 @@ def run_learned_init_experiment(args):
             "views": V, "scene_build_seconds": round(t_scene, 1),
             "plain": {"steps": steps, "seconds": round(h_plain.seconds[-1], 3), "psnr": round(h_plain.psnr[-1], 3),
                       "psnr_at_init": round(h_plain.psnr[0], 3)},
-            "batched_learned": {"views_per_step": 2, "psnr_at_init": round(h_learn.psnr[0], 3),
+            "batched_learned": {"views_per_step": vps, "lr_factor_scale_opacity_rotation": f,
+                                "lr_factor_position": fm,
+                                "psnr_at_init": round(h_learn.psnr[0], 3),
                                 "steps_to_plain_psnr_minus_0.1dB": s_hit,
                                 "seconds_to_plain_psnr_minus_0.1dB": None if t_hit is None else round(t_hit, 3),
                                 "seconds_with_mlp_fit": fit,
