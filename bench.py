@@ -435,17 +435,20 @@ BWD_SLOTS_PER_PAIR = 50
 
 
 # DRAM bytes (read + write) per unit of each stage, from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, one pass, every launch of three timed steps) of the 10M-Gaussian 1080p training step
-# with the kernels as they are now and the points in Z-order; the unit is the one the stage's algorithmic
-# work counts.  Reported only for that workload and order, scaled by the units of the bench's own timed views.
+# dram__bytes_write.sum, one pass, every launch of three timed steps) of the 2M-Gaussian 1080p training step
+# (iso2M-1080p-prof) with the kernels as they are now and the points in Z-order; the unit is the one the
+# stage's algorithmic work counts.  Given only for the stages whose data stream far exceeds L2 at that size
+# (so that their traffic grows in proportion to the units), and reported for the 10M workload in Z-order,
+# scaled by the units of the bench's own timed views.
 TRAFFIC_WORKLOAD = "iso10M-1080p"
+TRAFFIC_CAPTURED_ON = "iso2M-1080p-prof"
 TRAFFIC_PER_UNIT = {
-    "preprocess": None,
-    "bin_sort": ("instance", 204.90),
+    "preprocess": ("gaussian", 290.31),
+    "bin_sort": None,
     "render_fwd": None,
-    "loss": ("pixel", 20.02),
+    "loss": None,
     "blend_bwd": None,
-    "project_bwd_adam": ("gaussian", 1477.58),
+    "project_bwd_adam": ("gaussian", 1451.90),
 }
 
 
@@ -516,7 +519,8 @@ def rooflines(res, workload=None, issue=None, random_order=False):
                          "work_avoided": f"{n_plain - n_pairs:.3e} pairs of the plain per-pixel walk "
                                          f"({n_plain:.3e}) fall outside the masks"}
         if traffic is not None:
-            out[name]["traffic_source"] = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum at {TRAFFIC_WORKLOAD}: "
+            out[name]["traffic_source"] = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum on {TRAFFIC_CAPTURED_ON}, "
+                                           f"scaled to {TRAFFIC_WORKLOAD} by units: "
                                            f"{TRAFFIC_PER_UNIT[name][1]} B per {TRAFFIC_PER_UNIT[name][0]} x "
                                            f"{units[TRAFFIC_PER_UNIT[name][0]]:.4g} {TRAFFIC_PER_UNIT[name][0]}s")
         out[name]["share"] = round(float(ms / res["stage_ms"].sum()), 4)
