@@ -174,8 +174,15 @@ class CpuSample:
         self.frac, self.gfrac = frac, gfrac
         g64 = {k: np.asarray(v, np.float64) for k, v in scene.init.items()}
         self.cam, (x0, y0, w, h) = cpu_window_camera(scene.cams, view, frac)
-        self.gt = scene.gt[view, :, y0:y0 + h, x0:x0 + w].double().cpu().numpy()
-        self.mask = scene.mask[view, y0:y0 + h, x0:x0 + w].cpu().numpy()
+        # the window's GT image and mask, rendered by the oracle from the scene's surfels (set-up, not timed)
+        from paper_2509_12138_gb300 import workload
+        surf = workload.gt_surfels(scene.pts, scene.nrm, scene.colors, scene.spacing)
+        s64 = {k: np.asarray(v, np.float64) for k, v in surf.items()}
+        ps = oracle.project(s64, self.cam)
+        ssel = np.nonzero(ps["tiles"] > 0)[0]
+        rg = oracle.render({k: v[ssel] for k, v in s64.items()}, self.cam, np.ones(3))
+        self.gt = rg["img"]
+        self.mask = ((1.0 - rg["final_T"]) >= 1.0 / 255.0).astype(np.uint8)
         # Gaussians that reach the window (selection is set-up, not timed)
         p = oracle.project(g64, self.cam)
         sel = np.nonzero(p["tiles"] > 0)[0]
@@ -875,15 +882,11 @@ def run_reference(args, wl, rank, world, config):
     """The oracle, as it stands, timed on the host cores (rank 0 only)."""
     if rank != 0:
         return 0
-    import torch
     import oracle
     from paper_2509_12138_gb300 import workload
     oracle.build()
-    have_gpu = torch.cuda.is_available()
-    if not have_gpu:
-        print(json.dumps({"impl": "reference", "unavailable": "the scene's GT is rendered on the GPU; no CUDA device"}))
-        return 0
-    scene = workload.isosurface_scene(wl["n"], wl["modes"], wl["views"], wl["W"], wl["H"], sh_degree=3, seed=0)
+    # host-only scene: the oracle renders the GT of its own sample window (no device code runs in this arm)
+    scene = workload.isosurface_points(wl["n"], wl["modes"], wl["views"], wl["W"], wl["H"], sh_degree=3, seed=0)
     # each step is a bounded sample (~4 s of host work at the default size); long runs take a smaller one so
     # that the whole run stays within a few minutes (the estimate of a full iteration scales with it)
     many = args.steps + args.warmup > 20

@@ -100,9 +100,24 @@ def render_gt(gauss: dict, cams: synth.Cameras, sh_degree: int, bg, device="cuda
     return gt, mask
 
 
-def isosurface_scene(n: int, n_modes: int, n_views: int, width: int, height: int, sh_degree: int = 3,
-                     seed: int = 0, radius: float = 1.5, device="cuda", init_log_scale=None,
-                     spatial: bool = True) -> Scene:
+@dataclass
+class PointScene:
+    """The host side of an isosurface scene: points, cameras and the plain initialisation, no GT images
+    (for consumers that render what they need themselves, such as the oracle's timed sample)."""
+    n: int
+    sh_degree: int
+    width: int
+    height: int
+    cams: synth.Cameras
+    init: dict
+    pts: np.ndarray
+    nrm: np.ndarray
+    colors: np.ndarray
+    spacing: float
+
+
+def isosurface_points(n: int, n_modes: int, n_views: int, width: int, height: int, sh_degree: int = 3,
+                      seed: int = 0, radius: float = 1.5, init_log_scale=None, spatial: bool = True) -> PointScene:
     """spatial: store the points in Z-order (synth.spatial_order), the cell-by-cell order in which an
     isosurface extraction emits them; False keeps the sampler's random order."""
     pts, nrm, _ = synth.interface_points(n, n_modes, seed)
@@ -112,12 +127,22 @@ def isosurface_scene(n: int, n_modes: int, n_views: int, width: int, height: int
     colors = synth.lambert_colors(pts, nrm)
     spacing = spacing_estimate(nrm, n)
     cams = synth.orbital_cameras(n_views, radius, center=(0.5, 0.5, 0.5), width=width, height=height)
-    gt, mask = render_gt(gt_surfels(pts, nrm, colors, spacing), cams, 0, (1.0, 1.0, 1.0), device,
-                         max_instances=max(8 * n, 1 << 20))
     ls = math.log(spacing) if init_log_scale is None else init_log_scale
     init = plain_init(pts, colors, ls, sh_degree)
-    return Scene(n=n, sh_degree=sh_degree, width=width, height=height, cams=cams, cams_dev=pack_cameras(cams, device),
-                 gt=gt, mask=mask, init=init, pts=pts, nrm=nrm, colors=colors, spacing=spacing)
+    return PointScene(n=n, sh_degree=sh_degree, width=width, height=height, cams=cams, init=init, pts=pts, nrm=nrm,
+                      colors=colors, spacing=spacing)
+
+
+def isosurface_scene(n: int, n_modes: int, n_views: int, width: int, height: int, sh_degree: int = 3,
+                     seed: int = 0, radius: float = 1.5, device="cuda", init_log_scale=None,
+                     spatial: bool = True) -> Scene:
+    """The points of isosurface_points with every view's GT image and mask rendered on the device."""
+    ps = isosurface_points(n, n_modes, n_views, width, height, sh_degree, seed, radius, init_log_scale, spatial)
+    gt, mask = render_gt(gt_surfels(ps.pts, ps.nrm, ps.colors, ps.spacing), ps.cams, 0, (1.0, 1.0, 1.0), device,
+                         max_instances=max(8 * n, 1 << 20))
+    return Scene(n=n, sh_degree=sh_degree, width=width, height=height, cams=ps.cams,
+                 cams_dev=pack_cameras(ps.cams, device), gt=gt, mask=mask, init=ps.init, pts=ps.pts, nrm=ps.nrm,
+                 colors=ps.colors, spacing=ps.spacing)
 
 
 @dataclass
