@@ -427,7 +427,7 @@ def run_ours(args, wl, rank, world):
     return dict(scene=scene, frame=frame, ms_total=ms_total, stage_ms=stage_ms, stages=stages, ms_render=ms_render,
                 clocks=clk, e2e_sec=e_sec, instances=instances, tile_len=tile_len, pairs=pairs_per_step,
                 render_mode=render_mode, visible=visible, zero_grad_frac=float(np.mean(zero_frac)),
-                h2d=(3 * H * W * 4 + H * W), d2h=4,
+                sparse_adam=bool(args.sparse_adam), h2d=(3 * H * W * 4 + H * W), d2h=4,
                 launches=kernel_launch_count(frame, LAMBDA_SSIM) * args.steps, N=N, W=W, H=H)
 
 
@@ -489,7 +489,10 @@ def rooflines(res, workload=None, issue=None, random_order=False):
         "preprocess": ("hbm", N * (15 * 16 + 60)),
         "bin_sort": ("hbm", N * 8 + I * (12 + passes * 32 + 16)),
         # params, m, v read and written; the gradient stays in registers; screen gradients read
-        "project_bwd_adam": ("hbm", N * (59 * 4 * 6 + 40 + 4)),
+        # screen gradients and radius of every Gaussian; params, m, v read and written for the updated ones
+        # (sparse Adam: those with a non-zero gradient)
+        "project_bwd_adam": ("hbm", N * (40 + 4) + N * (1.0 - (res.get("zero_grad_frac", 0.0) if res.get("sparse_adam")
+                                                               else 0.0)) * 59 * 4 * 6),
         "loss": ("hbm", res["W"] * res["H"] * (3 * 4 * 3 + 1 + 3 * 4 * 6)),
         "render_fwd": ("alu", pairs["fwd_pairs_masked"] * FWD_SLOTS_PER_PAIR),
         "blend_bwd": ("alu", pairs["bwd_pairs_masked"] * BWD_SLOTS_PER_PAIR),
@@ -505,7 +508,9 @@ def rooflines(res, workload=None, issue=None, random_order=False):
             continue
         bound, amount = work[name]
         traffic = None
-        if workload == TRAFFIC_WORKLOAD and not random_order and TRAFFIC_PER_UNIT[name]:
+        # (the captured traffic is that of the dense update)
+        sparse_upd = name == "project_bwd_adam" and res.get("sparse_adam")
+        if workload == TRAFFIC_WORKLOAD and not random_order and TRAFFIC_PER_UNIT[name] and not sparse_upd:
             u, per = TRAFFIC_PER_UNIT[name]
             traffic = round(per * units[u])
         if bound == "hbm":
