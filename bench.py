@@ -76,6 +76,10 @@ def parse():
     ap.add_argument("--exp-height", type=int, default=1080)
     ap.add_argument("--exp-views", type=int, default=64)
     ap.add_argument("--exp-views-per-step", type=int, default=2, help="learned-init: views per batched step")
+    ap.add_argument("--exp-init-scale", type=float, default=1.0,
+                    help="ghost-ablation: factor on the plain initialisation's scale")
+    ap.add_argument("--exp-seam-delta", type=float, default=0.01,
+                    help="ghost-ablation: seam band half-width (x distance of the visible surface from a slab edge)")
     ap.add_argument("--exp-learned-lr", type=float, default=1.0,
                     help="learned-init: factor on the scale, opacity and rotation learning rates of the learned form")
     ap.add_argument("--exp-learned-mean-lr", type=float, default=1.0,
@@ -679,10 +683,13 @@ def run_ghost_ablation(args):
     import __graft_entry__
     __graft_entry__.build()
     slabs, W, H, V = [args.exp_gaussians // 4] * 4, 960, 540, 32
-    res = X.ghost_ablation(slabs, 8, V, W, H, args.exp_steps, n_parts=4, ghost=0.05, sh_degree=1, delta=0.01)
+    res = X.ghost_ablation(slabs, 8, V, W, H, args.exp_steps, n_parts=4, ghost=0.05, sh_degree=1,
+                           delta=args.exp_seam_delta, init_scale=args.exp_init_scale)
     print(json.dumps({"experiment": "ghost cells x masks", "gaussians": sum(slabs), "partitions": 4, "ghost": 0.05,
                       "width": W, "height": H, "views": V, "steps": args.exp_steps,
-                      "seam_band": "pixels whose surface lies within 0.01 (x) of an interior slab boundary",
+                      "init_scale": args.exp_init_scale,
+                      "seam_band": f"pixels whose surface lies within {args.exp_seam_delta} (x) of an interior slab "
+                                   "boundary",
                       "results": res}))
     return 0
 

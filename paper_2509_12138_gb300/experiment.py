@@ -144,7 +144,8 @@ def seam_band(scene, delta: float, device="cuda"):
 
 
 def ghost_ablation(slab_counts, n_modes: int, n_views: int, W: int, H: int, steps: int, n_parts: int = 4,
-                   ghost: float = 0.05, sh_degree: int = 1, delta: float = 0.01, device="cuda"):
+                   ghost: float = 0.05, sh_degree: int = 1, delta: float = 0.01, device="cuda",
+                   init_scale: float = 1.0):
     """Ghost cells and masks on and off (Sec. II): each configuration trains every partition on its own
     GT (graph-captured batched trainer, one view per partition per step), merges with the ghost filter and
     is scored on held-out views against the whole scene's GT: PSNR over the covered pixels and over the
@@ -155,7 +156,8 @@ def ghost_ablation(slab_counts, n_modes: int, n_views: int, W: int, H: int, step
     band = None
     for use_ghost in (True, False):
         ps = partitioned_scene(slab_counts, n_modes, n_views, W, H, n_parts=n_parts,
-                               ghost=ghost if use_ghost else 0.0, sh_degree=sh_degree, device=device)
+                               ghost=ghost if use_ghost else 0.0, sh_degree=sh_degree, device=device,
+                               init_scale=init_scale)
         if band is None:
             band = seam_band(ps, delta, device)
         train_v, test_v = split_views(n_views)

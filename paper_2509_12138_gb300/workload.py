@@ -170,9 +170,10 @@ class PartitionedScene:
 
 def partitioned_scene(slab_counts, n_modes: int, n_views: int, width: int, height: int, n_parts: int = 8,
                       ghost: float = 0.05, sh_degree: int = 3, seed: int = 0, radius: float = 1.5,
-                      device="cuda") -> PartitionedScene:
+                      device="cuda", init_scale: float = 1.0) -> PartitionedScene:
     """The interface split into x-slabs with ghost layers; uneven slab populations from a piecewise
-    constant x-density (slab_counts points per slab)."""
+    constant x-density (slab_counts points per slab).  init_scale: factor on the plain initialisation's
+    isotropic scale (the mean 3-NN spacing)."""
     from .partition import slab_partition
     pts, nrm, _ = synth.slab_density_points(n_modes=n_modes, slab_counts=slab_counts, seed=seed)
     o = synth.spatial_order(pts)  # Z-order, as an isosurface extraction emits the points
@@ -193,7 +194,7 @@ def partitioned_scene(slab_counts, n_modes: int, n_views: int, width: int, heigh
     gt_full, mask_full = render_gt(gt_surfels(pts, nrm, colors, spacing), cams, 0, (1.0, 1.0, 1.0), device,
                                    max_instances=max(8 * n, 1 << 20))
     order = part.order
-    init = plain_init(pts[order], colors[order], math.log(spacing), sh_degree)
+    init = plain_init(pts[order], colors[order], math.log(spacing * init_scale), sh_degree)
     return PartitionedScene(part=part, sh_degree=sh_degree, width=W, height=H, cams=cams,
                             cams_dev=pack_cameras(cams, device), gt=gt, mask=mask, gt_full=gt_full,
                             mask_full=mask_full, init=init, pts=pts, spacing=spacing, nrm=nrm)
