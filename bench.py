@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--exp-height", type=int, default=1080)
     ap.add_argument("--exp-views", type=int, default=64)
     ap.add_argument("--exp-views-per-step", type=int, default=2, help="learned-init: views per batched step")
+    ap.add_argument("--exp-fit-points", type=int, default=2_000_000,
+                    help="learned-init: the MLP trains on a random subset of this many source points")
     ap.add_argument("--exp-init-scale", type=float, default=1.0,
                     help="ghost-ablation: factor on the plain initialisation's scale")
     ap.add_argument("--exp-seam-delta", type=float, default=0.01,
@@ -632,7 +634,7 @@ def run_learned_init_experiment(args):
     t_scene = time.perf_counter() - t_scene
     h_src, trained = X.run_plain(src, steps, every)
     t0 = time.perf_counter()
-    w, losses = X.fit_mlp(src, trained, steps=600)
+    w, losses = X.fit_mlp(src, trained, steps=600, fit_points=args.exp_fit_points)
     torch.cuda.synchronize()
     t_fit = time.perf_counter() - t0
     del src, trained
@@ -664,6 +666,7 @@ def run_learned_init_experiment(args):
                                 "seconds_with_mlp_fit_and_source_training": fit_src,
                                 "final_psnr": round(h_learn.psnr[-1], 3)},
             "mlp": {"fit_seconds": round(t_fit, 3), "source_training_seconds": round(h_src.seconds[-1], 3),
+                    "fit_points": min(args.exp_fit_points, n),
                     "loss_first": losses[0], "loss_last": losses[-1],
                     "trained_on": "converged splats of another seed of the interface"},
             "history": {"plain": [h_plain.steps, [round(x, 3) for x in h_plain.seconds],

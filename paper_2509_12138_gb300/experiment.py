@@ -73,16 +73,31 @@ def run_plain(scene, steps: int, eval_every: int, device="cuda", lrs: LearningRa
     return h, params
 
 
-def fit_mlp(scene, trained_params, steps: int = 600, lr: float = 2e-3, seed: int = 0, device="cuda"):
-    """Train the initialiser MLP on one scene's points against its converged splats."""
+def fit_mlp(scene, trained_params, steps: int = 600, lr: float = 2e-3, seed: int = 0, device="cuda",
+            fit_points: int | None = None):
+    """Train the initialiser MLP on one scene's points against its converged splats.  fit_points: train on
+    a seeded random subset of that many points (their neighbours still come from the whole cloud); all
+    points when None or not smaller than the scene."""
     P, Nn = _points(scene, device)
     idx, dist = gi.knn(P, 16)
     targets = gi.targets_from_params(trained_params, dist)
+    n = P.shape[0]
+    n_fit = n
+    if fit_points is not None and fit_points < n:
+        # the subset first: the train step takes its own points from rows 0 .. n_fit - 1 of a permuted cloud
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        perm = torch.randperm(n, generator=g).to(P.device)
+        inv = torch.empty_like(perm)
+        inv[perm] = torch.arange(n, device=P.device)
+        P, Nn = P[perm].contiguous(), Nn[perm].contiguous()
+        idx = inv[idx[perm].long()].to(idx.dtype).contiguous()
+        dist, targets = dist[perm].contiguous(), targets[perm].contiguous()
+        n_fit = int(fit_points)
     w = gi.init_weights(seed, device)
     tr = gi.MLPTrainer(w, lr=lr)
     losses = []
     for k in range(steps):
-        l = tr.step(P, Nn, idx, dist, targets)
+        l = tr.step(P, Nn, idx, dist, targets, n_fit)
         if k % 50 == 0 or k == steps - 1:
             losses.append(float(l.item()))
     return w, losses
