@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--deterministic", action="store_true",
                     help="accumulate screen-space gradients in fixed point (bitwise reproducible steps)")
     ap.add_argument("--chunk", type=int, default=1024, help="list entries per chunk job of the blend schedule")
+    ap.add_argument("--separate-preprocess", action="store_true",
+                    help="a1 as its own launch each step instead of fused into the previous step's Adam kernel")
     ap.add_argument("--sparse-adam", action="store_true",
                     help="Gaussians without gradient in a step keep their parameters and moments")
     ap.add_argument("--random-order", action="store_true",
@@ -232,13 +234,13 @@ def cpu_baseline(scene, frac: int):
 
 
 # ---------------------------------------------------------------- our arm
-def kernel_launch_count(frame, lam):
+def kernel_launch_count(frame, lam, fused_pre=False):
     """Kernels libgs launches for one training step (a1-a6) of this frame (the kernel launches ncu lists
     for the timed steps; the 4-byte memsets of the ticket counters are not kernels)."""
     tile_bits = max(1, math.ceil(math.log2(frame.n_tiles)))
     unit_bits = math.ceil(math.log2(frame.units.n)) if frame.units.n > 1 else 0
     key_bits = 32 + tile_bits + unit_bits
-    pre = 1                                   # k_preprocess
+    pre = 0 if fused_pre else 1               # k_preprocess (fused into the previous step's Adam kernel)
     passes = min(-(-key_bits // 9), -(-key_bits // 8))  # 9-bit digits when they save a pass
     sort = 3 + 1 + 3 * passes + 1             # tiles scan, k_duplicate, (hist, scan, scatter) per pass, k_ranges
     sched = frame.use_masks
@@ -271,10 +273,15 @@ def run_ours(args, wl, rank, world):
     V = len(scene.cams)
 
     # stage boundaries for per-kernel timing (events on the launching stream)
-    def step(v, ev=None):
+    # a1 of step k + 1 runs fused into step k's projection backward + Adam (gs_project_bwd_adam_next): the
+    # updated parameters are projected while still on chip; only the first step of a loop preprocesses
+    fuse = not args.separate_preprocess
+
+    def step(v, ev=None, pre=True):
         cam = scene.cam(v)
         if ev: ev[0].record()
-        frame.preprocess(params, cam)
+        if pre or not fuse:
+            frame.preprocess(params, cam)
         if ev: ev[1].record()
         frame.sort()
         if ev: ev[2].record()
@@ -284,12 +291,12 @@ def run_ours(args, wl, rank, world):
         if ev: ev[4].record()
         frame.blend_backward(bg)
         if ev: ev[5].record()
-        opt.fused_step(frame, cam)
+        opt.fused_step(frame, cam, next_cams_dev=scene.cam((v + 1) % V) if fuse else None)
         if ev: ev[6].record()
 
     stages = ["preprocess", "bin_sort", "render_fwd", "loss", "blend_bwd", "project_bwd_adam"]
     for w in range(args.warmup):
-        step(w % V)
+        step(w % V, pre=w == 0)
     torch.cuda.synchronize()
     st = frame.read_status()
     if st != 0:
@@ -324,7 +331,7 @@ def run_ours(args, wl, rank, world):
     torch.cuda.nvtx.range_push("timed_steps")  # lets a profiler select exactly the timed launches
     t0.record()
     for k in range(args.steps):
-        step((args.warmup + k) % V, evs[k])
+        step((args.warmup + k) % V, evs[k], pre=False)
     t1.record()
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
@@ -418,14 +425,15 @@ def run_ours(args, wl, rank, world):
             fetch(k + 1)
         b, v = k % 2, (args.warmup + k) % V
         cam = scene.cam(v)
-        frame.preprocess(params, cam)
+        if k == 0 or not fuse:
+            frame.preprocess(params, cam)
         frame.sort()
         frame.render(bg)
         main.wait_event(ready[b])
         frame.loss(gt_dev[b], mask_dev[b], LAMBDA_SSIM)
         consumed[b].record(main)
         frame.blend_backward(bg)
-        opt.fused_step(frame, cam)
+        opt.fused_step(frame, cam, next_cams_dev=scene.cam((v + 1) % V) if fuse else None)
         loss_host[k:k + 1].copy_(frame.loss_val, non_blocking=True)
     torch.cuda.synchronize()
     e_sec = time.perf_counter() - e0
@@ -433,8 +441,8 @@ def run_ours(args, wl, rank, world):
     return dict(scene=scene, frame=frame, ms_total=ms_total, stage_ms=stage_ms, stages=stages, ms_render=ms_render,
                 clocks=clk, e2e_sec=e_sec, instances=instances, tile_len=tile_len, pairs=pairs_per_step,
                 render_mode=render_mode, visible=visible, zero_grad_frac=float(np.mean(zero_frac)),
-                sparse_adam=bool(args.sparse_adam), h2d=(3 * H * W * 4 + H * W), d2h=4,
-                launches=kernel_launch_count(frame, LAMBDA_SSIM) * args.steps, N=N, W=W, H=H)
+                sparse_adam=bool(args.sparse_adam), fused_pre=fuse, h2d=(3 * H * W * 4 + H * W), d2h=4,
+                launches=kernel_launch_count(frame, LAMBDA_SSIM, fuse) * args.steps, N=N, W=W, H=H)
 
 
 # Blend kernels' algorithmic work: FP32 issue slots (one per lane-operation, FMA and MUFU included) per
@@ -505,7 +513,14 @@ def rooflines(res, workload=None, issue=None, random_order=False):
     }
     units = {"gaussian": N, "instance": I, "fwd_pair": pairs["fwd_pairs"], "bwd_pair": pairs["bwd_pairs"],
              "pixel": res["W"] * res["H"]}
-    kernel = {"preprocess": "k_preprocess", "bin_sort": "sort chain", "project_bwd_adam": "k_project_bwd_adam1",
+    fused = bool(res.get("fused_pre"))
+    if fused:
+        # the next step's a1 runs inside the Adam kernel: its records (60 B per Gaussian) are written there, the
+        # parameters it reads are already on chip, and the preprocess stage is empty
+        work["project_bwd_adam"] = ("hbm", work["project_bwd_adam"][1] + N * 60)
+        work.pop("preprocess")
+    kernel = {"preprocess": "k_preprocess", "bin_sort": "sort chain",
+              "project_bwd_adam": "k_project_bwd_adam1 (+ the next step's a1)" if fused else "k_project_bwd_adam1",
               "loss": "loss kernels", "render_fwd": "k_render_fwd_m + k_render_fwd_combine + k_render_fwd_stop",
               "blend_bwd": "k_render_bwd_m"}
     out = {}
@@ -514,8 +529,8 @@ def rooflines(res, workload=None, issue=None, random_order=False):
             continue
         bound, amount = work[name]
         traffic = None
-        # (the captured traffic is that of the dense update)
-        sparse_upd = name == "project_bwd_adam" and res.get("sparse_adam")
+        # (the captured traffic is that of the dense update without the fused projection)
+        sparse_upd = name == "project_bwd_adam" and (res.get("sparse_adam") or fused)
         if workload == TRAFFIC_WORKLOAD and not random_order and TRAFFIC_PER_UNIT[name] and not sparse_upd:
             u, per = TRAFFIC_PER_UNIT[name]
             traffic = round(per * units[u])

@@ -387,6 +387,22 @@ int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, const gs_
                         float beta1, float beta2, float eps, const int32_t* d_step, float* grads,
                         int sparse, int* d_status, gs_stream_t stream);
 
+/* gs_project_bwd_adam followed, in the same kernel, by a1 of the next step:
+ * every Gaussian of a unit, as stored after its update (its old values where
+ * it kept them), is projected for next_cams[unit] (device [n_units]; width x
+ * height) and its record written over `proj` (position, conic and opacity,
+ * colour, depth, radius, tiles: exactly what gs_preprocess with no owned
+ * filter writes for those parameters and cameras).  The parameters are not
+ * read again from memory.  Requires every Gaussian in at most one unit (else
+ * GS_ERR_INVALID) and proj's record arrays.  A non-finite projection sets
+ * GS_ERR_NONFINITE and culls the record, as gs_preprocess does. */
+int gs_project_bwd_adam_next(float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
+                             const gs_camera* cams, const gs_proj* proj, const gs_grad2d* g2d, float* m,
+                             float* v, const float* lr_init, const float* lr_final, int32_t lr_steps,
+                             float beta1, float beta2, float eps, const int32_t* d_step, float* grads,
+                             int sparse, const gs_camera* next_cams, int width, int height, int* d_status,
+                             gs_stream_t stream);
+
 /* *d_step += 1 on the device (keeps CUDA-graph replays advancing). */
 int gs_step_advance(int32_t* d_step, gs_stream_t stream);
 

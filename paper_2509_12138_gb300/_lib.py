@@ -109,6 +109,9 @@ SIGNATURES = {
     "gs_step_advance": (I32, [VP, VP]),
     "gs_project_bwd_adam": (I32, [VP, I64, I32, C.POINTER(GsUnits), VP, C.POINTER(GsProj), C.POINTER(GsGrad2d), VP,
                                   VP, c_f32p, c_f32p, I32, F32, F32, F32, VP, VP, I32, VP, VP]),
+    "gs_project_bwd_adam_next": (I32, [VP, I64, I32, C.POINTER(GsUnits), VP, C.POINTER(GsProj),
+                                       C.POINTER(GsGrad2d), VP, VP, c_f32p, c_f32p, I32, F32, F32, F32, VP, VP, I32,
+                                       VP, I32, I32, VP, VP]),
     "gs_knn_workspace_size": (SZ, [I64, c_i32p]),
     "gs_knn": (I32, [VP, I64, I32, c_f32p, F32, c_i32p, VP, SZ, VP, VP, VP]),
     "gs_mlp_param_count": (I32, []),

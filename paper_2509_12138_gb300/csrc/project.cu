@@ -252,30 +252,29 @@ __device__ __forceinline__ bool owned_keep(const OwnedTable& O, int64_t i, float
   return in;
 }
 
+// One projected record (a1) of a Gaussian for one camera: depth always;
+// position pair, conic and opacity, colour and power floor when it is
+// visible; radius and tile count (0 when culled).  keep: the Gaussian passes
+// the caller's ownership filter.  The SH planes are read (only for a visible
+// record) from sh[k * sh_stride], k < NP: global memory for k_preprocess,
+// shared memory for the fused projection backward + Adam, which projects the
+// updated Gaussian for the next step's camera.  Not inlined, so that both
+// callers run one compiled body: the compiler cannot contract the covariance,
+// conic or colour arithmetic differently in the two kernels, and their
+// records are bit-identical for equal inputs.
 template <int DEG>
-__global__ void __launch_bounds__(256) k_preprocess(const float4* __restrict__ params, int64_t N,
-                                                    UnitTable U, OwnedTable O,
-                                                    const gs_camera* __restrict__ cams, int W, int H,
-                                                    float4* __restrict__ xy, float4* __restrict__ conic_op,
-                                                    float4* __restrict__ rgb, float* __restrict__ depth,
-                                                    int* __restrict__ radius, uint32_t* __restrict__ tiles,
-                                                    int* status) {
-  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p >= U.proj_base[U.n]) return;
-  int u = unit_of(U, p);
-  int64_t i = U.gauss_begin[u] + (p - U.proj_base[u]);
-  const gs_camera& cam = cams[u];
+__device__ __noinline__ void project_record(const gs_camera& cam, float4 mean, float4 sop, float4 quat, int W, int H,
+                                            bool keep, const float4* sh, int64_t sh_stride, float4* xy,
+                                            float4* conic_op, float4* rgb, float* depth, int* radius,
+                                            uint32_t* tiles, int* status) {
   int TX = (W + TILE - 1) / TILE, TY = (H + TILE - 1) / TILE;
-  float4 mean = __ldg(params + i);
-  float4 sop = __ldg(params + N + i);
-  float4 quat = __ldg(params + 2 * N + i);
   int r_out = 0;
   uint32_t tiles_out = 0;
   const float* V = cam.viewmat;
   float tz, tzl;
   view_row(V + 8, mean, tz, tzl);  // tz: the correctly rounded camera-space z (the sort key)
-  depth[p] = tz;
-  if (tz > cam.znear && owned_keep(O, i, mean)) {
+  *depth = tz;
+  if (tz > cam.znear && keep) {
     Geo g;
     geometry(cam, mean, sop, quat, g, nullptr);
     if (g.det > 0.f) {
@@ -302,7 +301,11 @@ __global__ void __launch_bounds__(256) k_preprocess(const float4* __restrict__ p
         float Y[16];
         sh_basis<DEG>(dx, dy, dz, Y);
         float c[4 * ShCount<DEG>::NP];
-        load_sh<DEG>(params, N, i, c);
+        #pragma unroll
+        for (int k = 0; k < ShCount<DEG>::NP; ++k) {
+          float4 q = sh[k * sh_stride];
+          c[4 * k] = q.x; c[4 * k + 1] = q.y; c[4 * k + 2] = q.z; c[4 * k + 3] = q.w;
+        }
         float col[3];
         #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
@@ -312,9 +315,9 @@ __global__ void __launch_bounds__(256) k_preprocess(const float4* __restrict__ p
           col[ch] = fmaxf(acc, 0.f);
         }
         float op = 1.0f / (1.0f + expf(-sop.w));
-        xy[p] = pxy;
-        conic_op[p] = make_float4(g.c * idet, -g.b * idet, g.a * idet, op);
-        rgb[p] = make_float4(col[0], col[1], col[2], power_floor(op));
+        *xy = pxy;
+        *conic_op = make_float4(g.c * idet, -g.b * idet, g.a * idet, op);
+        *rgb = make_float4(col[0], col[1], col[2], power_floor(op));
         r_out = r;
         tiles_out = nt;
         if (!(isfinite(px) && isfinite(py) && isfinite(col[0] + col[1] + col[2]) &&
@@ -326,8 +329,27 @@ __global__ void __launch_bounds__(256) k_preprocess(const float4* __restrict__ p
       }
     }
   }
-  radius[p] = r_out;
-  tiles[p] = tiles_out;
+  *radius = r_out;
+  *tiles = tiles_out;
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) k_preprocess(const float4* __restrict__ params, int64_t N,
+                                                    UnitTable U, OwnedTable O,
+                                                    const gs_camera* __restrict__ cams, int W, int H,
+                                                    float4* __restrict__ xy, float4* __restrict__ conic_op,
+                                                    float4* __restrict__ rgb, float* __restrict__ depth,
+                                                    int* __restrict__ radius, uint32_t* __restrict__ tiles,
+                                                    int* status) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= U.proj_base[U.n]) return;
+  int u = unit_of(U, p);
+  int64_t i = U.gauss_begin[u] + (p - U.proj_base[u]);
+  float4 mean = __ldg(params + i);
+  float4 sop = __ldg(params + N + i);
+  float4 quat = __ldg(params + 2 * N + i);
+  project_record<DEG>(cams[u], mean, sop, quat, W, H, owned_keep(O, i, mean), params + 3 * N + i, N, xy + p,
+                      conic_op + p, rgb + p, depth + p, radius + p, tiles + p, status);
 }
 
 // Projection backward: chain rule of k_preprocess for every parameter of
@@ -655,6 +677,19 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int NG>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NG) : "memory"); }
 
+// The next step's projection, fused into the projection backward + Adam
+// (cams NULL: none): camera per unit, image size and the record arrays.
+struct NextProj {
+  const gs_camera* cams;
+  int W, H;
+  float4* xy;
+  float4* conic_op;
+  float4* rgb;
+  float* depth;
+  int* radius;
+  uint32_t* tiles;
+};
+
 constexpr int PBA_T = 64;  // Gaussians per block of the staged kernel
 constexpr int PBA_R = 4;   // moment planes (m and v) in flight per thread
 
@@ -672,14 +707,14 @@ constexpr int PBA_R = 4;   // moment planes (m and v) in flight per thread
 template <int DEG>
 __global__ void __launch_bounds__(PBA_T) k_project_bwd_adam1(float4* __restrict__ params, int64_t N, UnitTable U,
                                                            const gs_camera* __restrict__ cams,
-                                                           const int* __restrict__ radius,
+                                                           const int* radius,  // overwritten by nx (own record)
                                                            const float2* __restrict__ gxy,
                                                            const float4* __restrict__ gco,
                                                            const float4* __restrict__ grgb, float4* __restrict__ m,
                                                            float4* __restrict__ v, AdamLR lr, int lr_steps, float b1,
                                                            float b2, float eps, const int32_t* __restrict__ d_step,
                                                            float4* __restrict__ grads, int sparse,
-                                                           int* __restrict__ status) {
+                                                           int* __restrict__ status, NextProj nx) {
   constexpr int NC = ShCount<DEG>::NC;
   constexpr int NP = ShCount<DEG>::NP;
   constexpr int NPL = 3 + NP;
@@ -717,6 +752,10 @@ __global__ void __launch_bounds__(PBA_T) k_project_bwd_adam1(float4* __restrict_
         #pragma unroll
         for (int k = 0; k < NPL; ++k) grads[k * N + i] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
+      if (nx.cams && uu >= 0)  // the next step's record of the unchanged Gaussian
+        project_record<DEG>(nx.cams[uu], __ldg(params + i), __ldg(params + N + i), __ldg(params + 2 * N + i), nx.W,
+                            nx.H, true, params + 3 * N + i, N, nx.xy + pidx, nx.conic_op + pidx, nx.rgb + pidx,
+                            nx.depth + pidx, nx.radius + pidx, nx.tiles + pidx, status);
       return;
     }
   }
@@ -892,7 +931,10 @@ __global__ void __launch_bounds__(PBA_T) k_project_bwd_adam1(float4* __restrict_
     float4 Gk = make_float4(G[0], G[1], G[2], G[3]);
     float4 Mv = slot[tl], Vv = slot[PBA_T + tl];
     adam4(P, Gk, Mv, Vv, s_lr[3 + k], b1, b2, ibc1, ibc2, eps);
-    if (ok) { params[o] = P; m[o] = Mv; v[o] = Vv; }
+    if (ok) {
+      params[o] = P; m[o] = Mv; v[o] = Vv;
+      if (nx.cams) sP[(3 + k) * PBA_T + tl] = P;  // the updated plane, for the next step's colour
+    }
     if (grads) grads[o] = Gk;
     mv_copy(k + PBA_R);  // the slot's values are consumed: refill it PBA_R steps ahead
   }
@@ -918,6 +960,11 @@ __global__ void __launch_bounds__(PBA_T) k_project_bwd_adam1(float4* __restrict_
     if (grads) grads[o] = Gp[k];
     mv_copy(NP + k + PBA_R);
   }
+  // a1 of the next step, fused: the updated Gaussian (as stored) projected for the next camera of its unit
+  if (nx.cams && uu >= 0)
+    project_record<DEG>(nx.cams[uu], ok ? Pv[0] : mean, ok ? Pv[1] : sop, ok ? Pv[2] : quat, nx.W, nx.H, true,
+                        sP + 3 * PBA_T + tl, PBA_T, nx.xy + pidx, nx.conic_op + pidx, nx.rgb + pidx,
+                        nx.depth + pidx, nx.radius + pidx, nx.tiles + pidx, status);
 }
 
 __global__ void k_step_advance(int32_t* s) { *s += 1; }
@@ -1080,12 +1127,12 @@ GS_API int gs_step_advance(int32_t* d_step, gs_stream_t stream) {
   return gs_check_launch();
 }
 
-GS_API int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
-                               const gs_camera* cams, const gs_proj* proj, const gs_grad2d* g2d, float* m, float* v,
-                               const float* lr_init, const float* lr_final, int32_t lr_steps, float beta1,
-                               float beta2, float eps, const int32_t* d_step, float* grads, int sparse,
-                               int* d_status, gs_stream_t stream) {
-  GS_RANGE("gs_project_bwd_adam");
+static int project_bwd_adam_impl(float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
+                                 const gs_camera* cams, const gs_proj* proj, const gs_grad2d* g2d, float* m,
+                                 float* v, const float* lr_init, const float* lr_final, int32_t lr_steps, float beta1,
+                                 float beta2, float eps, const int32_t* d_step, float* grads, int sparse,
+                                 int* d_status, gs_stream_t stream, const gs_camera* next_cams, int width,
+                                 int height) {
   UnitTable U;
   int64_t P = 0;
   int npl = param_planes(sh_degree);
@@ -1102,9 +1149,6 @@ GS_API int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, co
     lr.init[k] = make_float4(lr_init[4 * k], lr_init[4 * k + 1], lr_init[4 * k + 2], lr_init[4 * k + 3]);
     lr.fin[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
   }
-  if (n_gauss == 0) return GS_OK;
-  dim3 block(128), grid((unsigned)((n_gauss + 127) / 128));
-  cudaStream_t s = (cudaStream_t)stream;
   // every Gaussian in at most one unit: the streaming kernel applies
   bool disjoint = true;
   for (int a = 0; a < U.n && disjoint; ++a)
@@ -1113,6 +1157,17 @@ GS_API int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, co
       int64_t b0 = U.gauss_begin[b], b1 = b0 + (U.proj_base[b + 1] - U.proj_base[b]);
       if (a0 < b1 && b0 < a1) disjoint = false;
     }
+  NextProj nx{};
+  if (next_cams) {
+    if (!disjoint || width <= 0 || height <= 0 || !proj->xy || !proj->conic_op || !proj->rgb || !proj->depth ||
+        !proj->tiles)
+      return GS_ERR_INVALID;
+    nx = NextProj{next_cams, width, height, (float4*)proj->xy, (float4*)proj->conic_op, (float4*)proj->rgb,
+                  proj->depth, proj->radius, proj->tiles};
+  }
+  if (n_gauss == 0) return GS_OK;
+  dim3 block(128), grid((unsigned)((n_gauss + 127) / 128));
+  cudaStream_t s = (cudaStream_t)stream;
   if (disjoint) {
     dim3 grid1((unsigned)((n_gauss + PBA_T - 1) / PBA_T));
     size_t smem1 = sizeof(float4) * ((size_t)npl + 2 * PBA_R) * PBA_T;  // 23,552 B at degree 3
@@ -1120,7 +1175,7 @@ GS_API int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, co
   k_project_bwd_adam1<D><<<grid1, PBA_T, smem1, s>>>((float4*)params, n_gauss, U, cams, proj->radius,            \
                                                 (const float2*)g2d->dxy, (const float4*)g2d->dconic_op,          \
                                                 (const float4*)g2d->drgb, (float4*)m, (float4*)v, lr, lr_steps,   \
-                                                beta1, beta2, eps, d_step, (float4*)grads, sparse, d_status)
+                                                beta1, beta2, eps, d_step, (float4*)grads, sparse, d_status, nx)
     switch (sh_degree) {
       case 0: GS_PBA1(0); break;
       case 1: GS_PBA1(1); break;
@@ -1143,4 +1198,26 @@ GS_API int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, co
   }
 #undef GS_PBA
   return gs_check_launch();
+}
+
+GS_API int gs_project_bwd_adam(float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
+                               const gs_camera* cams, const gs_proj* proj, const gs_grad2d* g2d, float* m, float* v,
+                               const float* lr_init, const float* lr_final, int32_t lr_steps, float beta1,
+                               float beta2, float eps, const int32_t* d_step, float* grads, int sparse,
+                               int* d_status, gs_stream_t stream) {
+  GS_RANGE("gs_project_bwd_adam");
+  return project_bwd_adam_impl(params, n_gauss, sh_degree, units, cams, proj, g2d, m, v, lr_init, lr_final, lr_steps,
+                               beta1, beta2, eps, d_step, grads, sparse, d_status, stream, nullptr, 0, 0);
+}
+
+GS_API int gs_project_bwd_adam_next(float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
+                                    const gs_camera* cams, const gs_proj* proj, const gs_grad2d* g2d, float* m,
+                                    float* v, const float* lr_init, const float* lr_final, int32_t lr_steps,
+                                    float beta1, float beta2, float eps, const int32_t* d_step, float* grads,
+                                    int sparse, const gs_camera* next_cams, int width, int height, int* d_status,
+                                    gs_stream_t stream) {
+  GS_RANGE("gs_project_bwd_adam_next");
+  if (!next_cams) return GS_ERR_INVALID;
+  return project_bwd_adam_impl(params, n_gauss, sh_degree, units, cams, proj, g2d, m, v, lr_init, lr_final, lr_steps,
+                               beta1, beta2, eps, d_step, grads, sparse, d_status, stream, next_cams, width, height);
 }

@@ -402,16 +402,21 @@ class Adam:
         self.b1, self.b2 = betas
         self.eps = eps
 
-    def fused_step(self, frame: "Frame", cams_dev, keep_grads: bool = False):
+    def fused_step(self, frame: "Frame", cams_dev, keep_grads: bool = False, next_cams_dev=None):
         """Projection backward of ``frame``'s screen-space gradients fused with this Adam step
-        (gs_project_bwd_adam); ``frame.grads`` receives the gradient only if keep_grads."""
-        npl, n = self.params.shape[0], self.params.shape[1]
-        check(self.L.gs_project_bwd_adam(_ptr(self.params), n, frame.deg, C.byref(frame.units.struct),
-                                         _ptr(cams_dev), C.byref(frame.proj), C.byref(frame.g2d), _ptr(self.m),
-                                         _ptr(self.v), self.lr_init.ctypes.data_as(_lib.c_f32p),
-                                         self.lr_final.ctypes.data_as(_lib.c_f32p), self.lr_steps, self.b1, self.b2,
-                                         self.eps, _ptr(self.step_dev), _ptr(frame.grads) if keep_grads else None,
-                                         int(self.sparse), _ptr(frame.status), _stream()), "gs_project_bwd_adam")
+        (gs_project_bwd_adam); ``frame.grads`` receives the gradient only if keep_grads.  With next_cams_dev
+        the same kernel also projects the updated Gaussians for those cameras into ``frame``'s records
+        (gs_project_bwd_adam_next), so the next step needs no preprocess call."""
+        n = self.params.shape[1]
+        common = (_ptr(self.params), n, frame.deg, C.byref(frame.units.struct), _ptr(cams_dev), C.byref(frame.proj),
+                  C.byref(frame.g2d), _ptr(self.m), _ptr(self.v), self.lr_init.ctypes.data_as(_lib.c_f32p),
+                  self.lr_final.ctypes.data_as(_lib.c_f32p), self.lr_steps, self.b1, self.b2, self.eps,
+                  _ptr(self.step_dev), _ptr(frame.grads) if keep_grads else None, int(self.sparse))
+        if next_cams_dev is None:
+            check(self.L.gs_project_bwd_adam(*common, _ptr(frame.status), _stream()), "gs_project_bwd_adam")
+        else:
+            check(self.L.gs_project_bwd_adam_next(*common, _ptr(next_cams_dev), frame.W, frame.H, _ptr(frame.status),
+                                                  _stream()), "gs_project_bwd_adam_next")
         check(self.L.gs_step_advance(_ptr(self.step_dev), _stream()), "gs_step_advance")
 
     def state_dict(self) -> dict:

@@ -42,6 +42,20 @@ def test_rooflines_hbm_and_issue_stages():
     assert out["preprocess"]["achieved"] == pytest.approx(10_000_000 * 300 / 0.4e-3 / 1e9, rel=1e-3)
 
 
+def test_rooflines_with_the_projection_fused_into_adam():
+    ms = {"preprocess": 0.001, "bin_sort": 1.3, "render_fwd": 2.0, "loss": 0.13, "blend_bwd": 1.8,
+          "project_bwd_adam": 2.5}
+    res = _res(ms)
+    res["fused_pre"] = True
+    dom, out = bench.rooflines(res, "iso10M-1080p", None)
+    assert "preprocess" not in out and dom is out["project_bwd_adam"]
+    ach = 10_000_000 * (236 * 6 + 44 + 60) / 2.5e-3 / 1e9
+    assert out["project_bwd_adam"]["achieved"] == pytest.approx(ach, rel=1e-3)
+    assert out["project_bwd_adam"]["traffic"] is None  # not captured for the fused kernel
+    frame = types.SimpleNamespace(n_tiles=120 * 68, units=types.SimpleNamespace(n=1), use_masks=True)
+    assert bench.kernel_launch_count(frame, 0.2, True) == bench.kernel_launch_count(frame, 0.2) - 1
+
+
 def test_traffic_scales_by_units_and_only_for_the_captured_workload():
     ms = {"preprocess": 0.4, "bin_sort": 1.3, "render_fwd": 2.0, "loss": 0.13, "blend_bwd": 1.8,
           "project_bwd_adam": 2.4}

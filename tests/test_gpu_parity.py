@@ -417,3 +417,55 @@ def test_sparse_adam_skips_only_gaussians_without_gradient():
         assert torch.equal(sp[k][:, ~touched], sp[k + "0"][:, ~touched]), k
     # the dense step does move untouched Gaussians (momentum), so the two differ there
     assert not torch.equal(dense["p"][:, ~touched], dense["p0"][:, ~touched])
+
+
+@pytest.mark.parametrize("sparse", [False, True])
+def test_fused_next_projection_equals_separate_preprocess(sparse):
+    """gs_project_bwd_adam_next: the same update as gs_project_bwd_adam (parameters and moments bit for bit),
+    and over the frame's records exactly what gs_preprocess writes for the updated parameters and the next
+    camera (position pairs, conics, colours, depths, radii, tile counts)."""
+    import paper_2509_12138_gb300 as gsp
+    n, deg, W, H = 3000, 3, 160, 120
+    g = synth.random_gaussians(n, deg, 41, extent=0.8, log_scale_range=(-3.5, -2.0))
+    cams = synth.orbital_cameras(2, 3.0, width=W, height=H)
+    camd = gsp.pack_cameras(cams)
+    cam_a, cam_b = camd[0:96], camd[96:192]
+    gt, mask = scenes.random_gt(W, H, 42)
+    fr = gsp.Frame(n, gsp.Units.single(n), W, H, deg, deterministic=True)
+    params = gsp.pack_params(g, deg)
+    fr.fit_capacity(params, cam_a)
+    fr.forward(params, cam_a, BG)
+    fr.loss(torch.from_numpy(gt).cuda()[None], torch.from_numpy(mask).cuda()[None], 0.2)
+    fr.blend_backward(BG)
+    opt = gsp.Adam(params, deg, extent=1.0, lr_steps=100)
+    opt.sparse = sparse
+    r = np.random.default_rng(3)
+    m0 = torch.from_numpy(r.normal(0, 1e-3, tuple(opt.m.shape)).astype(np.float32)).cuda()
+    v0 = torch.from_numpy(r.uniform(1e-7, 1e-6, tuple(opt.v.shape)).astype(np.float32)).cuda()
+    p0 = params.clone()
+    recs = ("xy", "conic_op", "rgb", "depth", "radius", "tiles")
+    out = []
+    for fused in (False, True):
+        params.copy_(p0)
+        opt.m.copy_(m0)
+        opt.v.copy_(v0)
+        opt.step_dev.fill_(2)
+        fr.preprocess(params, cam_a)  # this step's records (the fused kernel reads their radii)
+        if fused:
+            opt.fused_step(fr, cam_a, next_cams_dev=cam_b)
+        else:
+            opt.fused_step(fr, cam_a)
+            fr.preprocess(params, cam_b)
+        torch.cuda.synchronize()
+        assert fr.read_status() == 0
+        out.append({k: getattr(fr, k)[:n].clone() for k in recs} | dict(p=params.clone(), m=opt.m.clone(),
+                                                                          v=opt.v.clone()))
+    a, b = out
+    for k in ("p", "m", "v"):
+        assert torch.equal(a[k], b[k]), k
+    vis = a["radius"] > 0
+    assert int(vis.sum()) > n // 2
+    for k in ("depth", "radius", "tiles"):
+        assert torch.equal(a[k], b[k]), k
+    for k in ("xy", "conic_op", "rgb"):  # written for visible records only
+        assert torch.equal(a[k][vis], b[k][vis]), k
