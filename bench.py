@@ -470,6 +470,8 @@ TRAFFIC_PER_UNIT = {
     "loss": None,
     "blend_bwd": None,
     "project_bwd_adam": ("gaussian", 1451.90),
+    # the same kernel with the next step's projection fused in (gs_project_bwd_adam_next)
+    "project_bwd_adam_next": ("gaussian", 1512.19),
 }
 
 
@@ -529,10 +531,11 @@ def rooflines(res, workload=None, issue=None, random_order=False):
             continue
         bound, amount = work[name]
         traffic = None
-        # (the captured traffic is that of the dense update without the fused projection)
-        sparse_upd = name == "project_bwd_adam" and (res.get("sparse_adam") or fused)
-        if workload == TRAFFIC_WORKLOAD and not random_order and TRAFFIC_PER_UNIT[name] and not sparse_upd:
-            u, per = TRAFFIC_PER_UNIT[name]
+        # (the captured traffic is that of the dense update)
+        tkey = "project_bwd_adam_next" if (fused and name == "project_bwd_adam") else name
+        sparse_upd = name == "project_bwd_adam" and res.get("sparse_adam")
+        if workload == TRAFFIC_WORKLOAD and not random_order and TRAFFIC_PER_UNIT[tkey] and not sparse_upd:
+            u, per = TRAFFIC_PER_UNIT[tkey]
             traffic = round(per * units[u])
         if bound == "hbm":
             ach = amount / (ms * 1e-3) / 1e9
@@ -554,8 +557,8 @@ def rooflines(res, workload=None, issue=None, random_order=False):
         if traffic is not None:
             out[name]["traffic_source"] = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum on {TRAFFIC_CAPTURED_ON}, "
                                            f"scaled to {TRAFFIC_WORKLOAD} by units: "
-                                           f"{TRAFFIC_PER_UNIT[name][1]} B per {TRAFFIC_PER_UNIT[name][0]} x "
-                                           f"{units[TRAFFIC_PER_UNIT[name][0]]:.4g} {TRAFFIC_PER_UNIT[name][0]}s")
+                                           f"{TRAFFIC_PER_UNIT[tkey][1]} B per {TRAFFIC_PER_UNIT[tkey][0]} x "
+                                           f"{units[TRAFFIC_PER_UNIT[tkey][0]]:.4g} {TRAFFIC_PER_UNIT[tkey][0]}s")
         out[name]["share"] = round(float(ms / res["stage_ms"].sum()), 4)
     dom = max(out, key=lambda k: out[k]["share"])
     return out[dom], out
