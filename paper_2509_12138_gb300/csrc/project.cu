@@ -738,7 +738,9 @@ __global__ void __launch_bounds__(PBA_T) k_project_bwd_adam1(float4* __restrict_
   }
   bool vis = uu >= 0 && __ldg(radius + pidx) > 0;
   // sparse: a Gaussian with no screen-space gradient in this step keeps its parameters and moments (no
-  // load, no store), as a sparse Adam updates only the Gaussians a view touches
+  // load, no store), as a sparse Adam updates only the Gaussians a view touches; with the next step's
+  // projection fused in it joins the other lanes at that projection (one call per warp)
+  bool skip = false;
   if (sparse) {
     bool any = false;
     if (vis) {
@@ -752,219 +754,228 @@ __global__ void __launch_bounds__(PBA_T) k_project_bwd_adam1(float4* __restrict_
         #pragma unroll
         for (int k = 0; k < NPL; ++k) grads[k * N + i] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      if (nx.cams && uu >= 0)  // the next step's record of the unchanged Gaussian
-        project_record<DEG>(nx.cams[uu], __ldg(params + i), __ldg(params + N + i), __ldg(params + 2 * N + i), nx.W,
-                            nx.H, true, params + 3 * N + i, N, nx.xy + pidx, nx.conic_op + pidx, nx.rgb + pidx,
-                            nx.depth + pidx, nx.radius + pidx, nx.tiles + pidx, status);
-      return;
+      if (!nx.cams) return;
+      skip = true;
     }
   }
+  // the parameters the next step's projection takes: as stored after the update, or unchanged
+  float4 pm, ps, pq;
+  const float4* shp;
+  int64_t shs;
   extern __shared__ float4 s_stage[];  // [NPL][PBA_T] parameters, then [PBA_R][2][PBA_T] m, v ring
-  const int tl = threadIdx.x;
-  float4* sP = s_stage;
-  float4* sR = s_stage + NPL * PBA_T;
-  // update sequence q = 0 .. NPL - 1 takes plane (q + 3) % NPL: the SH planes, then 0, 1, 2
-  auto mv_copy = [&](int q) {
-    if (q < NPL) {
-      int k = (q + 3) % NPL;
-      float4* slot = sR + (q % PBA_R) * 2 * PBA_T;
-      cp_async16(slot + tl, m + k * N + i);
-      cp_async16(slot + PBA_T + tl, v + k * N + i);
+  if (!skip) {
+    const int tl = threadIdx.x;
+    float4* sP = s_stage;
+    float4* sR = s_stage + NPL * PBA_T;
+    // update sequence q = 0 .. NPL - 1 takes plane (q + 3) % NPL: the SH planes, then 0, 1, 2
+    auto mv_copy = [&](int q) {
+      if (q < NPL) {
+        int k = (q + 3) % NPL;
+        float4* slot = sR + (q % PBA_R) * 2 * PBA_T;
+        cp_async16(slot + tl, m + k * N + i);
+        cp_async16(slot + PBA_T + tl, v + k * N + i);
+      }
+      cp_async_commit();  // one group per sequence step (empty past the end) keeps the counting uniform
+    };
+    #pragma unroll
+    for (int k = 0; k < NPL; ++k) cp_async16(sP + k * PBA_T + tl, params + k * N + i);
+    cp_async_commit();
+    #pragma unroll
+    for (int q = 0; q < PBA_R; ++q) mv_copy(q);
+    float ibc1 = 1.f / (1.f - powf(b1, (float)t)), ibc2 = 1.f / (1.f - powf(b2, (float)t));
+    cp_async_wait<PBA_R>();  // this thread's parameter planes have landed
+    float4 mean = sP[tl], sop = sP[PBA_T + tl], quat = sP[2 * PBA_T + tl];
+    float dmean[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, dlogit = 0.f;
+    float Y[16], gc[3] = {0.f, 0.f, 0.f}, il = 0.f, dir[3] = {0.f, 0.f, 0.f};
+    bool ok = true;  // false: a non-finite gradient, reported; this Gaussian's state is then left as it is
+    if (vis) {
+      const gs_camera& cam = cams[uu];
+      float2 g_xy = gxy[pidx];
+      float4 g_co = gco[pidx];
+      float4 g_rgb = grgb[pidx];
+      ok = isfinite(g_xy.x) && isfinite(g_xy.y) && finite4(g_co) && finite4(g_rgb);
+      // pass A: colour before the clamp
+      float vx = mean.x - cam.campos[0], vy = mean.y - cam.campos[1], vz = mean.z - cam.campos[2];
+      il = 1.0f / sqrtf(vx * vx + vy * vy + vz * vz);
+      dir[0] = vx * il; dir[1] = vy * il; dir[2] = vz * il;
+      sh_basis<DEG>(dir[0], dir[1], dir[2], Y);
+      float col[3] = {0.5f, 0.5f, 0.5f};
+      #pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        float4 q = sP[(3 + k) * PBA_T + tl];
+        const float* qq = &q.x;
+        #pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          int f = 4 * k + e;
+          if (f < 3 * NC) col[f % 3] += Y[f / 3] * qq[e];
+        }
+      }
+      gc[0] = col[0] < 0.f ? 0.f : g_rgb.x;
+      gc[1] = col[1] < 0.f ? 0.f : g_rgb.y;
+      gc[2] = col[2] < 0.f ? 0.f : g_rgb.z;
+      // everything but the SH direction term (as in project_grads)
+      float qn[5];
+      Geo g;
+      geometry(cam, mean, sop, quat, g, qn);
+      float itz = 1.0f / g.t[2];
+      float dt[3] = {0.f, 0.f, 0.f};
+      {
+        float op = 1.0f / (1.0f + expf(-sop.w));
+        dlogit = g_co.w * op * (1.f - op);
+      }
+      dt[0] += g_xy.x * cam.fx * itz;
+      dt[1] += g_xy.y * cam.fy * itz;
+      dt[2] += -(g_xy.x * cam.fx * g.t[0] + g_xy.y * cam.fy * g.t[1]) * itz * itz;
+      float a = g.a, b = g.b, cc = g.c, det = g.det;
+      float id2 = 1.0f / (det * det);
+      float gA = g_co.x, gB = g_co.y, gC = g_co.z;
+      float da = (-cc * cc * gA + b * cc * gB - b * b * gC) * id2;
+      float db = (2.f * b * cc * gA - (det + 2.f * b * b) * gB + 2.f * a * b * gC) * id2;
+      float dc = (-b * b * gA + a * b * gB - a * a * gC) * id2;
+      const float* T = g.T2;
+      float hb = 0.5f * db;
+      float GT0[3], GT1[3];
+      #pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        GT0[j] = da * T[j] + hb * T[3 + j];
+        GT1[j] = hb * T[j] + dc * T[3 + j];
+      }
+      float dSig[9];
+      #pragma unroll
+      for (int i2 = 0; i2 < 3; ++i2)
+        #pragma unroll
+        for (int j = 0; j < 3; ++j) dSig[3 * i2 + j] = T[i2] * GT0[j] + T[3 + i2] * GT1[j];
+      const float* S6 = g.Sig;
+      float Sg[9] = {S6[0], S6[1], S6[2], S6[1], S6[3], S6[4], S6[2], S6[4], S6[5]};
+      float dT2[6];
+      #pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        dT2[j] = 2.f * (GT0[0] * Sg[j] + GT0[1] * Sg[3 + j] + GT0[2] * Sg[6 + j]);
+        dT2[3 + j] = 2.f * (GT1[0] * Sg[j] + GT1[1] * Sg[3 + j] + GT1[2] * Sg[6 + j]);
+      }
+      const float* V = cam.viewmat;
+      float dJ00 = dT2[0] * V[0] + dT2[1] * V[1] + dT2[2] * V[2];
+      float dJ02 = dT2[0] * V[8] + dT2[1] * V[9] + dT2[2] * V[10];
+      float dJ11 = dT2[3] * V[4] + dT2[4] * V[5] + dT2[5] * V[6];
+      float dJ12 = dT2[3] * V[8] + dT2[4] * V[9] + dT2[5] * V[10];
+      dt[2] += -(dJ00 * cam.fx + dJ11 * cam.fy) * itz * itz;
+      if (g.clx) {
+        dt[2] += dJ02 * cam.fx * g.xzc * itz * itz;
+      } else {
+        dt[0] += -dJ02 * cam.fx * itz * itz;
+        dt[2] += 2.f * dJ02 * cam.fx * g.t[0] * itz * itz * itz;
+      }
+      if (g.cly) {
+        dt[2] += dJ12 * cam.fy * g.yzc * itz * itz;
+      } else {
+        dt[1] += -dJ12 * cam.fy * itz * itz;
+        dt[2] += 2.f * dJ12 * cam.fy * g.t[1] * itz * itz * itz;
+      }
+      #pragma unroll
+      for (int k = 0; k < 3; ++k) dmean[k] += V[k] * dt[0] + V[4 + k] * dt[1] + V[8 + k] * dt[2];
+      float M[9];
+      #pragma unroll
+      for (int i2 = 0; i2 < 3; ++i2)
+        #pragma unroll
+        for (int j = 0; j < 3; ++j) M[3 * i2 + j] = g.Rq[3 * i2 + j] * g.s[j];
+      float dR[9];
+      #pragma unroll
+      for (int i2 = 0; i2 < 3; ++i2)
+        #pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          float dM = 2.f * (dSig[3 * i2] * M[j] + dSig[3 * i2 + 1] * M[3 + j] + dSig[3 * i2 + 2] * M[6 + j]);
+          dls[j] += dM * g.Rq[3 * i2 + j] * g.s[j];
+          dR[3 * i2 + j] = dM * g.s[j];
+        }
+      float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+      float gw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+      float gx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] +
+                        w * dR[7] - 2.f * x * dR[8]);
+      float gy = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] +
+                        z * dR[7] - 2.f * y * dR[8]);
+      float gz = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
+                        x * dR[6] + y * dR[7]);
+      float dot = gw * w + gx * x + gy * y + gz * z;
+      float inv = qn[4];
+      dq[0] = (gw - dot * w) * inv;
+      dq[1] = (gx - dot * x) * inv;
+      dq[2] = (gy - dot * y) * inv;
+      dq[3] = (gz - dot * z) * inv;
+      // with finite screen-space gradients and parameters, every gradient below is finite
+      ok = ok && finite4(make_float4(dmean[0], dmean[1], dmean[2], dlogit)) &&
+           finite4(make_float4(dls[0], dls[1], dls[2], 0.f)) && finite4(make_float4(dq[0], dq[1], dq[2], dq[3]));
+      #pragma unroll
+      for (int k = 0; k < NP; ++k) ok = ok && finite4(sP[(3 + k) * PBA_T + tl]);
+      if (!ok) set_status(status, GS_ERR_NONFINITE);
+    } else {
+      #pragma unroll
+      for (int k = 0; k < 16; ++k) Y[k] = 0.f;
     }
-    cp_async_commit();  // one group per sequence step (empty past the end) keeps the counting uniform
-  };
-  #pragma unroll
-  for (int k = 0; k < NPL; ++k) cp_async16(sP + k * PBA_T + tl, params + k * N + i);
-  cp_async_commit();
-  #pragma unroll
-  for (int q = 0; q < PBA_R; ++q) mv_copy(q);
-  float ibc1 = 1.f / (1.f - powf(b1, (float)t)), ibc2 = 1.f / (1.f - powf(b2, (float)t));
-  cp_async_wait<PBA_R>();  // this thread's parameter planes have landed
-  float4 mean = sP[tl], sop = sP[PBA_T + tl], quat = sP[2 * PBA_T + tl];
-  float dmean[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, dlogit = 0.f;
-  float Y[16], gc[3] = {0.f, 0.f, 0.f}, il = 0.f, dir[3] = {0.f, 0.f, 0.f};
-  bool ok = true;  // false: a non-finite gradient, reported; this Gaussian's state is then left as it is
-  if (vis) {
-    const gs_camera& cam = cams[uu];
-    float2 g_xy = gxy[pidx];
-    float4 g_co = gco[pidx];
-    float4 g_rgb = grgb[pidx];
-    ok = isfinite(g_xy.x) && isfinite(g_xy.y) && finite4(g_co) && finite4(g_rgb);
-    // pass A: colour before the clamp
-    float vx = mean.x - cam.campos[0], vy = mean.y - cam.campos[1], vz = mean.z - cam.campos[2];
-    il = 1.0f / sqrtf(vx * vx + vy * vy + vz * vz);
-    dir[0] = vx * il; dir[1] = vy * il; dir[2] = vz * il;
-    sh_basis<DEG>(dir[0], dir[1], dir[2], Y);
-    float col[3] = {0.5f, 0.5f, 0.5f};
+    // pass B: per SH plane, its gradient, the direction term and the Adam update
+    float wsum[16];
+    #pragma unroll
+    for (int k = 0; k < 16; ++k) wsum[k] = 0.f;
     #pragma unroll
     for (int k = 0; k < NP; ++k) {
-      float4 q = sP[(3 + k) * PBA_T + tl];
-      const float* qq = &q.x;
+      int64_t o = (3 + k) * N + i;
+      float4 P = sP[(3 + k) * PBA_T + tl];
+      cp_async_wait<PBA_R - 1>();  // the moments of sequence step k
+      const float4* slot = sR + (k % PBA_R) * 2 * PBA_T;
+      float* pp = &P.x;
+      float G[4];
       #pragma unroll
       for (int e = 0; e < 4; ++e) {
         int f = 4 * k + e;
-        if (f < 3 * NC) col[f % 3] += Y[f / 3] * qq[e];
+        G[e] = 0.f;
+        if (f < 3 * NC) {
+          G[e] = Y[f / 3] * gc[f % 3];
+          wsum[f / 3] += pp[e] * gc[f % 3];
+        }
       }
-    }
-    gc[0] = col[0] < 0.f ? 0.f : g_rgb.x;
-    gc[1] = col[1] < 0.f ? 0.f : g_rgb.y;
-    gc[2] = col[2] < 0.f ? 0.f : g_rgb.z;
-    // everything but the SH direction term (as in project_grads)
-    float qn[5];
-    Geo g;
-    geometry(cam, mean, sop, quat, g, qn);
-    float itz = 1.0f / g.t[2];
-    float dt[3] = {0.f, 0.f, 0.f};
-    {
-      float op = 1.0f / (1.0f + expf(-sop.w));
-      dlogit = g_co.w * op * (1.f - op);
-    }
-    dt[0] += g_xy.x * cam.fx * itz;
-    dt[1] += g_xy.y * cam.fy * itz;
-    dt[2] += -(g_xy.x * cam.fx * g.t[0] + g_xy.y * cam.fy * g.t[1]) * itz * itz;
-    float a = g.a, b = g.b, cc = g.c, det = g.det;
-    float id2 = 1.0f / (det * det);
-    float gA = g_co.x, gB = g_co.y, gC = g_co.z;
-    float da = (-cc * cc * gA + b * cc * gB - b * b * gC) * id2;
-    float db = (2.f * b * cc * gA - (det + 2.f * b * b) * gB + 2.f * a * b * gC) * id2;
-    float dc = (-b * b * gA + a * b * gB - a * a * gC) * id2;
-    const float* T = g.T2;
-    float hb = 0.5f * db;
-    float GT0[3], GT1[3];
-    #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      GT0[j] = da * T[j] + hb * T[3 + j];
-      GT1[j] = hb * T[j] + dc * T[3 + j];
-    }
-    float dSig[9];
-    #pragma unroll
-    for (int i2 = 0; i2 < 3; ++i2)
-      #pragma unroll
-      for (int j = 0; j < 3; ++j) dSig[3 * i2 + j] = T[i2] * GT0[j] + T[3 + i2] * GT1[j];
-    const float* S6 = g.Sig;
-    float Sg[9] = {S6[0], S6[1], S6[2], S6[1], S6[3], S6[4], S6[2], S6[4], S6[5]};
-    float dT2[6];
-    #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      dT2[j] = 2.f * (GT0[0] * Sg[j] + GT0[1] * Sg[3 + j] + GT0[2] * Sg[6 + j]);
-      dT2[3 + j] = 2.f * (GT1[0] * Sg[j] + GT1[1] * Sg[3 + j] + GT1[2] * Sg[6 + j]);
-    }
-    const float* V = cam.viewmat;
-    float dJ00 = dT2[0] * V[0] + dT2[1] * V[1] + dT2[2] * V[2];
-    float dJ02 = dT2[0] * V[8] + dT2[1] * V[9] + dT2[2] * V[10];
-    float dJ11 = dT2[3] * V[4] + dT2[4] * V[5] + dT2[5] * V[6];
-    float dJ12 = dT2[3] * V[8] + dT2[4] * V[9] + dT2[5] * V[10];
-    dt[2] += -(dJ00 * cam.fx + dJ11 * cam.fy) * itz * itz;
-    if (g.clx) {
-      dt[2] += dJ02 * cam.fx * g.xzc * itz * itz;
-    } else {
-      dt[0] += -dJ02 * cam.fx * itz * itz;
-      dt[2] += 2.f * dJ02 * cam.fx * g.t[0] * itz * itz * itz;
-    }
-    if (g.cly) {
-      dt[2] += dJ12 * cam.fy * g.yzc * itz * itz;
-    } else {
-      dt[1] += -dJ12 * cam.fy * itz * itz;
-      dt[2] += 2.f * dJ12 * cam.fy * g.t[1] * itz * itz * itz;
-    }
-    #pragma unroll
-    for (int k = 0; k < 3; ++k) dmean[k] += V[k] * dt[0] + V[4 + k] * dt[1] + V[8 + k] * dt[2];
-    float M[9];
-    #pragma unroll
-    for (int i2 = 0; i2 < 3; ++i2)
-      #pragma unroll
-      for (int j = 0; j < 3; ++j) M[3 * i2 + j] = g.Rq[3 * i2 + j] * g.s[j];
-    float dR[9];
-    #pragma unroll
-    for (int i2 = 0; i2 < 3; ++i2)
-      #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        float dM = 2.f * (dSig[3 * i2] * M[j] + dSig[3 * i2 + 1] * M[3 + j] + dSig[3 * i2 + 2] * M[6 + j]);
-        dls[j] += dM * g.Rq[3 * i2 + j] * g.s[j];
-        dR[3 * i2 + j] = dM * g.s[j];
+      float4 Gk = make_float4(G[0], G[1], G[2], G[3]);
+      float4 Mv = slot[tl], Vv = slot[PBA_T + tl];
+      adam4(P, Gk, Mv, Vv, s_lr[3 + k], b1, b2, ibc1, ibc2, eps);
+      if (ok) {
+        params[o] = P; m[o] = Mv; v[o] = Vv;
+        if (nx.cams) sP[(3 + k) * PBA_T + tl] = P;  // the updated plane, for the next step's colour
       }
-    float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
-    float gw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
-    float gx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] +
-                      w * dR[7] - 2.f * x * dR[8]);
-    float gy = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] +
-                      z * dR[7] - 2.f * y * dR[8]);
-    float gz = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
-                      x * dR[6] + y * dR[7]);
-    float dot = gw * w + gx * x + gy * y + gz * z;
-    float inv = qn[4];
-    dq[0] = (gw - dot * w) * inv;
-    dq[1] = (gx - dot * x) * inv;
-    dq[2] = (gy - dot * y) * inv;
-    dq[3] = (gz - dot * z) * inv;
-    // with finite screen-space gradients and parameters, every gradient below is finite
-    ok = ok && finite4(make_float4(dmean[0], dmean[1], dmean[2], dlogit)) &&
-         finite4(make_float4(dls[0], dls[1], dls[2], 0.f)) && finite4(make_float4(dq[0], dq[1], dq[2], dq[3]));
+      if (grads) grads[o] = Gk;
+      mv_copy(k + PBA_R);  // the slot's values are consumed: refill it PBA_R steps ahead
+    }
+    if (vis && DEG > 0) {
+      float sx, sy, sz;
+      sh_grad<DEG>(dir[0], dir[1], dir[2], wsum, sx, sy, sz);
+      float d = sx * dir[0] + sy * dir[1] + sz * dir[2];
+      dmean[0] += (sx - d * dir[0]) * il;
+      dmean[1] += (sy - d * dir[1]) * il;
+      dmean[2] += (sz - d * dir[2]) * il;
+    }
+    float4 Gp[3] = {make_float4(dmean[0], dmean[1], dmean[2], 0.f), make_float4(dls[0], dls[1], dls[2], dlogit),
+                    make_float4(dq[0], dq[1], dq[2], dq[3])};
+    float4 Pv[3] = {mean, sop, quat};
     #pragma unroll
-    for (int k = 0; k < NP; ++k) ok = ok && finite4(sP[(3 + k) * PBA_T + tl]);
-    if (!ok) set_status(status, GS_ERR_NONFINITE);
+    for (int k = 0; k < 3; ++k) {
+      int64_t o = k * N + i;
+      cp_async_wait<PBA_R - 1>();  // the moments of sequence step NP + k
+      const float4* slot = sR + ((NP + k) % PBA_R) * 2 * PBA_T;
+      float4 Mv = slot[tl], Vv = slot[PBA_T + tl];
+      adam4(Pv[k], Gp[k], Mv, Vv, s_lr[k], b1, b2, ibc1, ibc2, eps);
+      if (ok) { params[o] = Pv[k]; m[o] = Mv; v[o] = Vv; }
+      if (grads) grads[o] = Gp[k];
+      mv_copy(NP + k + PBA_R);
+    }
+    pm = ok ? Pv[0] : mean; ps = ok ? Pv[1] : sop; pq = ok ? Pv[2] : quat;
+    shp = sP + 3 * PBA_T + tl;
+    shs = PBA_T;
   } else {
-    #pragma unroll
-    for (int k = 0; k < 16; ++k) Y[k] = 0.f;
+    pm = __ldg(params + i); ps = __ldg(params + N + i); pq = __ldg(params + 2 * N + i);
+    shp = params + 3 * N + i;
+    shs = N;
   }
-  // pass B: per SH plane, its gradient, the direction term and the Adam update
-  float wsum[16];
-  #pragma unroll
-  for (int k = 0; k < 16; ++k) wsum[k] = 0.f;
-  #pragma unroll
-  for (int k = 0; k < NP; ++k) {
-    int64_t o = (3 + k) * N + i;
-    float4 P = sP[(3 + k) * PBA_T + tl];
-    cp_async_wait<PBA_R - 1>();  // the moments of sequence step k
-    const float4* slot = sR + (k % PBA_R) * 2 * PBA_T;
-    float* pp = &P.x;
-    float G[4];
-    #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      int f = 4 * k + e;
-      G[e] = 0.f;
-      if (f < 3 * NC) {
-        G[e] = Y[f / 3] * gc[f % 3];
-        wsum[f / 3] += pp[e] * gc[f % 3];
-      }
-    }
-    float4 Gk = make_float4(G[0], G[1], G[2], G[3]);
-    float4 Mv = slot[tl], Vv = slot[PBA_T + tl];
-    adam4(P, Gk, Mv, Vv, s_lr[3 + k], b1, b2, ibc1, ibc2, eps);
-    if (ok) {
-      params[o] = P; m[o] = Mv; v[o] = Vv;
-      if (nx.cams) sP[(3 + k) * PBA_T + tl] = P;  // the updated plane, for the next step's colour
-    }
-    if (grads) grads[o] = Gk;
-    mv_copy(k + PBA_R);  // the slot's values are consumed: refill it PBA_R steps ahead
-  }
-  if (vis && DEG > 0) {
-    float sx, sy, sz;
-    sh_grad<DEG>(dir[0], dir[1], dir[2], wsum, sx, sy, sz);
-    float d = sx * dir[0] + sy * dir[1] + sz * dir[2];
-    dmean[0] += (sx - d * dir[0]) * il;
-    dmean[1] += (sy - d * dir[1]) * il;
-    dmean[2] += (sz - d * dir[2]) * il;
-  }
-  float4 Gp[3] = {make_float4(dmean[0], dmean[1], dmean[2], 0.f), make_float4(dls[0], dls[1], dls[2], dlogit),
-                  make_float4(dq[0], dq[1], dq[2], dq[3])};
-  float4 Pv[3] = {mean, sop, quat};
-  #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    int64_t o = k * N + i;
-    cp_async_wait<PBA_R - 1>();  // the moments of sequence step NP + k
-    const float4* slot = sR + ((NP + k) % PBA_R) * 2 * PBA_T;
-    float4 Mv = slot[tl], Vv = slot[PBA_T + tl];
-    adam4(Pv[k], Gp[k], Mv, Vv, s_lr[k], b1, b2, ibc1, ibc2, eps);
-    if (ok) { params[o] = Pv[k]; m[o] = Mv; v[o] = Vv; }
-    if (grads) grads[o] = Gp[k];
-    mv_copy(NP + k + PBA_R);
-  }
-  // a1 of the next step, fused: the updated Gaussian (as stored) projected for the next camera of its unit
+  // a1 of the next step, fused: the Gaussian as stored projected for the next camera of its unit
   if (nx.cams && uu >= 0)
-    project_record<DEG>(nx.cams[uu], ok ? Pv[0] : mean, ok ? Pv[1] : sop, ok ? Pv[2] : quat, nx.W, nx.H, true,
-                        sP + 3 * PBA_T + tl, PBA_T, nx.xy + pidx, nx.conic_op + pidx, nx.rgb + pidx,
-                        nx.depth + pidx, nx.radius + pidx, nx.tiles + pidx, status);
+    project_record<DEG>(nx.cams[uu], pm, ps, pq, nx.W, nx.H, true, shp, shs, nx.xy + pidx, nx.conic_op + pidx,
+                        nx.rgb + pidx, nx.depth + pidx, nx.radius + pidx, nx.tiles + pidx, status);
 }
 
 __global__ void k_step_advance(int32_t* s) { *s += 1; }
