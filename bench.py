@@ -3,7 +3,9 @@
 
 One step = one optimiser step on one 1920x1080 view: projection, binning +
 radix sort, forward blend, masked L1 + SSIM loss, backward (blend replay +
-projection), Adam.  Metric: train iters/s at 10M Gaussians, 1080p (plus render
+projection), Adam; the projection of each step runs inside the previous step's
+Adam kernel (gs_project_bwd_adam_next; --separate-preprocess: its own launch).
+Metric: train iters/s at 10M Gaussians, 1080p (plus render
 Mpix/s).  Inputs are synthetic (see paper_2509_12138_gb300/workload.py) and
 resident in HBM; params + Adam state (9.6 GB) and per-view GT are far larger
 than L2, so no explicit flush is needed between steps.
