@@ -215,3 +215,48 @@ def test_window_parity(full, k):
         print(f"  {key}: max error {err.max():.2e} of the group scale; per-element relative error above 1% of "
               f"the scale {rel:.2e}")
         assert sc > 0 and err.max() <= GRAD_TOL, (key, err.max())
+
+
+def test_fused_next_projection_full_size():
+    """The benchmark's step at full size: the next view's records written by the fused projection backward +
+    Adam kernel are bit-identical to gs_preprocess of the updated parameters, and the update itself equals
+    the unfused kernel's bit for bit (10M Gaussians, 1080p, the benchmark's Frame)."""
+    g = perturbed_interface(N, seed=3)
+    cams = synth.orbital_cameras(8, 1.5, center=(0.5, 0.5, 0.5), width=W, height=H)
+    camd = gs.pack_cameras(cams)
+    cam_a, cam_b = camd[2 * 96:3 * 96], camd[3 * 96:4 * 96]
+    dimg = torch.from_numpy(synth.streams(8, ["dimg"])["dimg"].uniform(-1.0, 1.0, (1, 3, H, W))
+                            .astype(np.float32)).cuda()
+    params = gs.pack_params(g, 3)
+    frame = gs.Frame(N, gs.Units.single(N), W, H, 3, max_instances=6 * N)
+    bg = (1.0, 1.0, 1.0)
+    frame.preprocess(params, cam_a)
+    frame.sort()
+    frame.render(bg)
+    frame.blend_backward(bg, dimg)
+    opt = gs.Adam(params, 3, extent=1.0, lr_steps=7000)
+    p0 = params.clone()
+    recs = ("xy", "conic_op", "rgb", "depth", "radius", "tiles")
+    out = []
+    for fused in (False, True):
+        params.copy_(p0)
+        opt.m.zero_()
+        opt.v.zero_()
+        opt.step_dev.zero_()
+        frame.preprocess(params, cam_a)
+        if fused:
+            opt.fused_step(frame, cam_a, next_cams_dev=cam_b)
+        else:
+            opt.fused_step(frame, cam_a)
+            frame.preprocess(params, cam_b)
+        torch.cuda.synchronize()
+        assert frame.read_status() == 0
+        vis = frame.radius[:N] > 0
+        out.append(dict(vis=vis.clone(), p=params.clone(), m=opt.m.clone(),
+                        **{k: getattr(frame, k)[:N].clone() for k in recs}))
+    a, b = out
+    for k in ("p", "m", "depth", "radius", "tiles"):
+        assert torch.equal(a[k], b[k]), k
+    for k in ("xy", "conic_op", "rgb"):
+        assert torch.equal(a[k][a["vis"]], b[k][b["vis"]]), k
+    assert int(a["vis"].sum()) > N // 2
