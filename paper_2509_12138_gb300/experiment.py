@@ -73,6 +73,19 @@ def run_plain(scene, steps: int, eval_every: int, device="cuda", lrs: LearningRa
     return h, params
 
 
+def subset_first(P, Nn, idx, dist, targets, seed: int):
+    """The cloud in a seeded random order, its neighbour indices renumbered to match: any first n rows are
+    then a random subset whose neighbours (anywhere in the cloud) are the same points as before.  The MLP
+    train step takes its own points from rows 0 .. n - 1."""
+    n = P.shape[0]
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    perm = torch.randperm(n, generator=g).to(P.device)
+    inv = torch.empty_like(perm)
+    inv[perm] = torch.arange(n, device=P.device)
+    return (P[perm].contiguous(), Nn[perm].contiguous(), inv[idx[perm].long()].to(idx.dtype).contiguous(),
+            dist[perm].contiguous(), targets[perm].contiguous())
+
+
 def fit_mlp(scene, trained_params, steps: int = 600, lr: float = 2e-3, seed: int = 0, device="cuda",
             fit_points: int | None = None):
     """Train the initialiser MLP on one scene's points against its converged splats.  fit_points: train on
@@ -84,14 +97,7 @@ def fit_mlp(scene, trained_params, steps: int = 600, lr: float = 2e-3, seed: int
     n = P.shape[0]
     n_fit = n
     if fit_points is not None and fit_points < n:
-        # the subset first: the train step takes its own points from rows 0 .. n_fit - 1 of a permuted cloud
-        g = torch.Generator(device="cpu").manual_seed(seed)
-        perm = torch.randperm(n, generator=g).to(P.device)
-        inv = torch.empty_like(perm)
-        inv[perm] = torch.arange(n, device=P.device)
-        P, Nn = P[perm].contiguous(), Nn[perm].contiguous()
-        idx = inv[idx[perm].long()].to(idx.dtype).contiguous()
-        dist, targets = dist[perm].contiguous(), targets[perm].contiguous()
+        P, Nn, idx, dist, targets = subset_first(P, Nn, idx, dist, targets, seed)
         n_fit = int(fit_points)
     w = gi.init_weights(seed, device)
     tr = gi.MLPTrainer(w, lr=lr)
