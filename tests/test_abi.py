@@ -50,6 +50,33 @@ def test_binding_loads_and_host_checks_without_gpu():
     assert L.gs_loss_workspace_size(0, 8, 8) == 0
 
 
+def test_fused_next_projection_refuses_overlapping_units_without_gpu():
+    """gs_project_bwd_adam_next writes one record per Gaussian, so a Gaussian in two units is refused
+    (GS_ERR_INVALID) by the host check, before any device pointer is used; disjoint units pass the same
+    check and reach the zero-Gaussian early return."""
+    import numpy as np
+    from paper_2509_12138_gb300 import _lib
+    L = _lib.load()
+    fake = 1 << 20  # never dereferenced: the call returns before any launch
+    proj = _lib.GsProj(fake, fake, fake, fake, fake, fake)
+    g2d = _lib.GsGrad2d(fake, fake, fake, 0)
+    lr = np.zeros(16 * 4, np.float32)
+
+    def call(begin, count, n_gauss, W=64):
+        b, c = np.array(begin, np.int64), np.array(count, np.int64)
+        units = _lib.GsUnits(len(b), b.ctypes.data_as(_lib.c_i64p), c.ctypes.data_as(_lib.c_i64p))
+        lp = lr.ctypes.data_as(_lib.c_f32p)
+        return L.gs_project_bwd_adam_next(fake, n_gauss, 0, C.byref(units), fake, C.byref(proj), C.byref(g2d),
+                                          fake, fake, lp, lp, 10, 0.9, 0.999, 1e-15, fake, None, 0, fake, W, 48,
+                                          None, None)
+
+    assert call([0, 2000], [2500, 2000], 4000) == 1   # [2000, 2500) in both units
+    assert call([0, 0], [10, 10], 10) == 1           # the same view twice
+    assert call([0, 2500], [2500, 1500], 4000, W=0) == 1  # empty image
+    assert call([0, 2500], [2500, 1500], 0) == 1     # units past the Gaussians
+    assert call([0], [0], 0) == 0                    # nothing to do: no launch
+
+
 def test_device_code_is_sm_103a():
     from paper_2509_12138_gb300 import build
     path = build.build()

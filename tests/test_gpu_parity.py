@@ -469,3 +469,52 @@ def test_fused_next_projection_equals_separate_preprocess(sparse):
         assert torch.equal(a[k], b[k]), k
     for k in ("xy", "conic_op", "rgb"):  # written for visible records only
         assert torch.equal(a[k][vis], b[k][vis]), k
+
+
+
+def test_fused_next_projection_two_units():
+    """Two disjoint units (two partitions, each with its own camera now and its own next camera): the update
+    and every record equal gs_project_bwd_adam followed by gs_preprocess of the updated parameters for that
+    unit's next camera."""
+    import paper_2509_12138_gb300 as gsp
+    n, deg, W, H = 4000, 1, 128, 96
+    g = synth.random_gaussians(n, deg, 51, extent=0.8, log_scale_range=(-3.5, -2.0))
+    camd = gsp.pack_cameras(synth.orbital_cameras(4, 3.0, width=W, height=H))
+    now, nxt = torch.cat([camd[0:96], camd[96:192]]), torch.cat([camd[192:288], camd[288:384]])
+    units = gsp.Units(np.array([0, 2500], np.int64), np.array([2500, 1500], np.int64))
+    gts = [scenes.random_gt(W, H, 52 + u) for u in range(2)]
+    gt = torch.from_numpy(np.stack([t[0] for t in gts])).cuda()
+    mask = torch.from_numpy(np.stack([t[1] for t in gts])).cuda()
+    fr = gsp.Frame(n, units, W, H, deg, deterministic=True)
+    params = gsp.pack_params(g, deg)
+    fr.fit_capacity(params, now)
+    fr.forward(params, now, BG)
+    fr.loss(gt, mask, 0.2)
+    fr.blend_backward(BG)
+    opt = gsp.Adam(params, deg, extent=1.0, lr_steps=100)
+    p0 = params.clone()
+    recs = ("xy", "conic_op", "rgb", "depth", "radius", "tiles")
+    out = []
+    for fused in (False, True):
+        params.copy_(p0)
+        opt.m.zero_()
+        opt.v.zero_()
+        opt.step_dev.zero_()
+        fr.preprocess(params, now)
+        if fused:
+            opt.fused_step(fr, now, next_cams_dev=nxt)
+        else:
+            opt.fused_step(fr, now)
+            fr.preprocess(params, nxt)
+        torch.cuda.synchronize()
+        assert fr.read_status() == 0
+        out.append({k: getattr(fr, k)[:n].clone() for k in recs} | dict(p=params.clone(), m=opt.m.clone()))
+    a, b = out
+    assert torch.equal(a["p"], b["p"]) and torch.equal(a["m"], b["m"])
+    assert not torch.equal(a["p"], p0)
+    vis = a["radius"] > 0
+    assert int(vis[:2500].sum()) > 1000 and int(vis[2500:].sum()) > 600
+    for k in ("depth", "radius", "tiles"):
+        assert torch.equal(a[k], b[k]), k
+    for k in ("xy", "conic_op", "rgb"):
+        assert torch.equal(a[k][vis], b[k][vis]), k
