@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--chunk", type=int, default=1024, help="list entries per chunk job of the blend schedule")
     ap.add_argument("--separate-preprocess", action="store_true",
                     help="a1 as its own launch each step instead of fused into the previous step's Adam kernel")
+    ap.add_argument("--sort", default="depth_first", choices=["depth_first", "global"],
+                    help="a2 design: records sorted by depth, then instances binned (gs_bin_sort), or one radix "
+                         "sort of all instance keys (gs_bin_sort_global)")
     ap.add_argument("--sparse-adam", action="store_true",
                     help="Gaussians without gradient in a step keep their parameters and moments")
     ap.add_argument("--random-order", action="store_true",
@@ -239,12 +242,17 @@ def cpu_baseline(scene, frac: int):
 def kernel_launch_count(frame, lam, fused_pre=False):
     """Kernels libgs launches for one training step (a1-a6) of this frame (the kernel launches ncu lists
     for the timed steps; the 4-byte memsets of the ticket counters are not kernels)."""
-    tile_bits = max(1, math.ceil(math.log2(frame.n_tiles)))
-    unit_bits = math.ceil(math.log2(frame.units.n)) if frame.units.n > 1 else 0
+    tile_bits = (frame.n_tiles - 1).bit_length()
+    unit_bits = (frame.units.n - 1).bit_length()
     key_bits = 32 + tile_bits + unit_bits
     pre = 0 if fused_pre else 1               # k_preprocess (fused into the previous step's Adam kernel)
-    passes = min(-(-key_bits // 9), -(-key_bits // 8))  # 9-bit digits when they save a pass
-    sort = 3 + 1 + 3 * passes + 1             # tiles scan, k_duplicate, (hist, scan, scatter) per pass, k_ranges
+    if getattr(frame, "sort_design", "depth_first") == "depth_first" and tile_bits + unit_bits <= 16:
+        # visibility scan + compaction (3), 4 depth passes of (hist, scan, scatter), instance counts, their
+        # block sums' scan and the emission (3), ceil(unit|tile bits / 8) instance passes, k_ranges32
+        sort = 3 + 3 * 4 + 3 + 3 * (-(-(tile_bits + unit_bits) // 8)) + 1
+    else:
+        passes = min(-(-key_bits // 9), -(-key_bits // 8))  # 9-bit digits when they save a pass
+        sort = 3 + 1 + 3 * passes + 1         # tiles scan, k_duplicate, (hist, scan, scatter) per pass, k_ranges
     sched = frame.use_masks
     if sched:
         sort += 2 + 1 + 3 + 1                 # tile order, chunk counts, their scan, chunk jobs
@@ -269,6 +277,7 @@ def run_ours(args, wl, rank, world):
     params = gs.pack_params(scene.init, 3, dev)
     frame = gs.Frame(N, gs.Units.single(N), W, H, 3, device=dev, max_instances=6 * N,
                      deterministic=args.deterministic, chunk=args.chunk)
+    frame.sort_design = args.sort
     opt = gs.Adam(params, 3, extent=1.0, lr_steps=7000)
     opt.sparse = bool(args.sparse_adam)
     bg = scene.bg
@@ -443,6 +452,7 @@ def run_ours(args, wl, rank, world):
     return dict(scene=scene, frame=frame, ms_total=ms_total, stage_ms=stage_ms, stages=stages, ms_render=ms_render,
                 clocks=clk, e2e_sec=e_sec, instances=instances, tile_len=tile_len, pairs=pairs_per_step,
                 render_mode=render_mode, visible=visible, zero_grad_frac=float(np.mean(zero_frac)),
+                sort_design=args.sort,
                 sparse_adam=bool(args.sparse_adam), fused_pre=fuse, h2d=(3 * H * W * 4 + H * W), d2h=4,
                 launches=kernel_launch_count(frame, LAMBDA_SSIM, fuse) * args.steps, N=N, W=W, H=H)
 
@@ -502,10 +512,20 @@ def rooflines(res, workload=None, issue=None, random_order=False):
     tiles = ((res["W"] + 15) // 16) * ((res["H"] + 15) // 16)
     key_bits = 32 + max(1, (tiles - 1).bit_length())
     passes = min(-(-key_bits // 9), -(-key_bits // 8))  # 9-bit digits when they save a pass
+    if res.get("sort_design", "global") == "depth_first" and key_bits - 32 <= 16:
+        Vv = N * res["visible"]
+        tp = -(-(key_bits - 32) // 8)
+        # per record: tile counts read twice (8 B); per visible record: depth read and (depth, id) written
+        # (12 B), 4 depth passes of 4 B histogram read + 8 B read + 8 B written, count gather (8 B), emission
+        # reads (id, xy, conic, radius: 40 B); per instance: (key, id) written (8 B), tp passes of 20 B,
+        # ranges / ids / masks (14 B)
+        sort_bytes = N * 8 + Vv * (12 + 4 * 20 + 8 + 40) + I * (8 + tp * 20 + 14)
+    else:
+        sort_bytes = N * 8 + I * (12 + passes * 32 + 16)
     work = {
         # 15 parameter planes read (240 B at SH3); xy pair, conic, rgb, depth, radius, tiles written (60 B)
         "preprocess": ("hbm", N * (15 * 16 + 60)),
-        "bin_sort": ("hbm", N * 8 + I * (12 + passes * 32 + 16)),
+        "bin_sort": ("hbm", sort_bytes),
         # params, m, v read and written; the gradient stays in registers; screen gradients read
         # screen gradients and radius of every Gaussian; params, m, v read and written for the updated ones
         # (sparse Adam: those with a non-zero gradient)
@@ -577,7 +597,7 @@ def main():
               "gradient_accumulation": "int64 fixed point" if args.deterministic else "float atomics",
               "l2": "inputs larger than L2 (params+Adam state 9.6 GB at 10M)",
               "point_order": "random" if args.random_order else "z-order", "chunk": args.chunk,
-              "adam": "sparse" if args.sparse_adam else "dense"}
+              "adam": "sparse" if args.sparse_adam else "dense", "sort": args.sort}
     if args.impl == "reference":
         return run_reference(args, wl, rank, world, config)
     if args.experiment == "learned-init":

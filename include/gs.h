@@ -221,10 +221,22 @@ int gs_bin_sort(const gs_proj* proj, const gs_units* units, int width, int heigh
                 uint32_t* sorted_vals, uint32_t* ranges, uint32_t* d_num_instances,
                 const gs_schedule* sched, int* d_status, gs_stream_t stream);
 
-/* The same lists, ranges, instance count and schedule as gs_bin_sort (same
- * arguments and workspace) by the other sort design.  gs_bin_sort sorts the
+/* How gs_bin_sort orders the lists: it compacts the visible records (tiles >
+ * 0) in index order, sorts them by their float32 depth bits with stable LSD
+ * radix passes (four 8-bit digits; a digit that every key shares is skipped
+ * on the device), emits each record's instances in that order as 32-bit keys
+ * (block mask << 16 | unit << tile_bits | tile) and sorts those stably on the
+ * unit | tile bits (one or two 8-bit passes): stability leaves every list in
+ * (depth, record index) order.  It needs unit | tile ids of at most 16 bits
+ * (one 4K unit: 15 bits; eight 1080p units: 16); for more it runs
+ * gs_bin_sort_global.  On capacity overflow the nearest instances are kept.
+ *
+ * gs_bin_sort_global and gs_bin_sort_bucketed: the same lists, ranges,
+ * instance count and schedule as gs_bin_sort (same arguments and workspace)
+ * by the other two sort designs.  gs_bin_sort_global sorts the
  * (unit | tile | depth) keys of all instances with one global stable LSD radix
- * sort (5 passes of 9-bit digits over the 45 key bits of one 1080p unit).
+ * sort (5 passes of 9-bit digits over the 45 key bits of one 1080p unit); on
+ * capacity overflow it keeps the first instances in record order.
  * gs_bin_sort_bucketed gathers the instances per (unit, tile) list with
  * atomics (arbitrary order inside a list), then sorts every list over its own
  * depth range: lists of up to 4096 instances in one CTA's shared memory, longer
@@ -235,6 +247,10 @@ int gs_bin_sort(const gs_proj* proj, const gs_units* units, int width, int heigh
  * equal depths is put in record-index order by one thread (heapsort): fast for
  * the short runs of real scenes, slow (seconds) for runs of ~10^6 instances at
  * one depth in one tile. */
+int gs_bin_sort_global(const gs_proj* proj, const gs_units* units, int width, int height,
+                       int64_t max_instances, void* workspace, size_t workspace_bytes,
+                       uint32_t* sorted_vals, uint32_t* ranges, uint32_t* d_num_instances,
+                       const gs_schedule* sched, int* d_status, gs_stream_t stream);
 int gs_bin_sort_bucketed(const gs_proj* proj, const gs_units* units, int width, int height,
                          int64_t max_instances, void* workspace, size_t workspace_bytes,
                          uint32_t* sorted_vals, uint32_t* ranges, uint32_t* d_num_instances,

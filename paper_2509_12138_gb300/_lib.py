@@ -93,6 +93,8 @@ SIGNATURES = {
     "gs_bin_sort_static": (I32, [C.POINTER(GsProj), C.POINTER(GsUnits), I32, I32, VP, VP, VP, VP, VP]),
     "gs_bin_sort_bucketed": (I32, [C.POINTER(GsProj), C.POINTER(GsUnits), I32, I32, I64, VP, SZ, VP, VP, VP,
                                  C.POINTER(GsSchedule), VP, VP]),
+    "gs_bin_sort_global": (I32, [C.POINTER(GsProj), C.POINTER(GsUnits), I32, I32, I64, VP, SZ, VP, VP, VP,
+                                 C.POINTER(GsSchedule), VP, VP]),
     "gs_render_fwd": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, c_f32p, VP, VP, VP, I32,
                             C.POINTER(GsSchedule), VP]),
     "gs_blend_pairs": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, VP, VP, VP, VP]),

@@ -38,7 +38,7 @@ constexpr int SCATTER_DYN_SMEM = RS_TILE * (int)(sizeof(uint64_t) + sizeof(uint3
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsLayout {
-  size_t offsets, bsums, keys0, keys1, vals0, vals1, hist, totals, cur, order, jscan, total;
+  size_t offsets, bsums, keys0, keys1, vals0, vals1, hist, totals, cur, misc, order, jscan, total;
 };
 
 // per-(unit, tile) scan scratch is sized for the largest tile grid (4K, 256 units)
@@ -48,11 +48,13 @@ WsLayout ws_layout(int64_t P, int64_t C) {
   WsLayout L;
   size_t o = 0;
   int64_t nsb = (P + SCAN_BLOCK - 1) / SCAN_BLOCK;
-  int64_t nrb = (C + RS_TILE - 1) / RS_TILE;
+  // the depth-first design sorts up to P records before it bins up to C instances
+  const int64_t K = C > P ? C : P;
+  int64_t nrb = (K + RS_TILE - 1) / RS_TILE;
   L.offsets = o; o += align256(sizeof(uint32_t) * (size_t)(P > 0 ? P : 1));
   L.bsums = o; o += align256(sizeof(uint32_t) * (size_t)(nsb + 1));
-  L.keys0 = o; o += align256(sizeof(uint64_t) * (size_t)(C > 0 ? C : 1));
-  L.keys1 = o; o += align256(sizeof(uint64_t) * (size_t)(C > 0 ? C : 1));
+  L.keys0 = o; o += align256(sizeof(uint64_t) * (size_t)(K > 0 ? K : 1));
+  L.keys1 = o; o += align256(sizeof(uint64_t) * (size_t)(K > 0 ? K : 1));
   size_t ws_s = 0, ws_l = 0;
   gs_seg_ws_words(C, &ws_s, &ws_l);
   const size_t cw = (size_t)(C > 0 ? C : 1);
@@ -60,7 +62,8 @@ WsLayout ws_layout(int64_t P, int64_t C) {
   L.vals1 = o; o += align256(sizeof(uint32_t) * (cw > ws_l ? cw : ws_l));
   L.hist = o; o += align256(sizeof(uint32_t) * RS_BINS_MAX * (size_t)(nrb > 0 ? nrb : 1));
   L.totals = o; o += align256(sizeof(uint32_t) * RS_BINS_MAX * MAX_PASSES);
-  L.cur = o; o += align256(sizeof(int32_t) * (MAX_PASSES + 1));
+  L.cur = o; o += align256(sizeof(int32_t) * 2 * (MAX_PASSES + 1));
+  L.misc = o; o += align256(sizeof(uint32_t) * 4);
   L.order = o; o += align256(sizeof(uint32_t) * 66);
   L.jscan = o; o += align256(sizeof(uint32_t) * (size_t)((MAX_SCHED_TILES + SCAN_BLOCK - 1) / SCAN_BLOCK + 1));
   L.total = o;
@@ -214,9 +217,8 @@ __global__ void __launch_bounds__(256) k_duplicate(UnitTable U, const float4* __
 }
 
 // ---- radix pass kernels
-template <int BITS>
-__global__ void __launch_bounds__(RS_T) k_radix_hist(const uint64_t* __restrict__ k0,
-                                                     const uint64_t* __restrict__ k1,
+template <int BITS, typename KT>
+__global__ void __launch_bounds__(RS_T) k_radix_hist(const KT* __restrict__ k0, const KT* __restrict__ k1,
                                                      const int32_t* __restrict__ cur, int pass,
                                                      const uint32_t* __restrict__ d_count, int shift,
                                                      uint32_t* __restrict__ hist, int64_t stride,
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(RS_T) k_radix_hist(const uint64_t* __restrict_
   constexpr int BINS = 1 << BITS;
   __shared__ uint32_t s_h[RS_T / 32][BINS];
   int64_t I = *d_count;
-  const uint64_t* keys = cur[pass] ? k1 : k0;
+  const KT* keys = cur[pass] ? k1 : k0;
   int w = threadIdx.x >> 5;
   // the grid holds as many blocks as stay resident; they take the 4096-key tiles in turn
   for (int64_t t = blockIdx.x; t * RS_TILE < I; t += gridDim.x) {
@@ -297,8 +299,8 @@ __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ hist
 // counts are scanned across warps.  Keys are then placed in a block-local
 // digit-sorted buffer in shared memory and written out so that each digit's
 // run goes to consecutive global positions (coalesced stores).
-template <int BITS>
-__global__ void __launch_bounds__(RS_T, 2) k_radix_scatter(uint64_t* __restrict__ k0, uint64_t* __restrict__ k1,
+template <int BITS, typename KT>
+__global__ void __launch_bounds__(RS_T, sizeof(KT) == 4 ? 3 : 2) k_radix_scatter(KT* __restrict__ k0, KT* __restrict__ k1,
                                                         uint32_t* __restrict__ v0, uint32_t* __restrict__ v1,
                                                         const int32_t* __restrict__ cur, int pass,
                                                         const uint32_t* __restrict__ d_count, int shift,
@@ -312,14 +314,14 @@ __global__ void __launch_bounds__(RS_T, 2) k_radix_scatter(uint64_t* __restrict_
   __shared__ uint32_t s_wc[NW][BINS];   // per-warp digit counts, then each warp's offset within the digit
   __shared__ uint32_t s_warp[33];
   extern __shared__ __align__(16) unsigned char s_dyn[];  // RS_TILE keys, then RS_TILE values
-  uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);
-  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(uint64_t) * RS_TILE);
+  KT* s_keys = reinterpret_cast<KT*>(s_dyn);
+  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(KT) * RS_TILE);
   int64_t I = *d_count;
   int c = cur[pass];
   if (cur[pass + 1] == c) return;  // skipped pass
-  const uint64_t* kin = c ? k1 : k0;
+  const KT* kin = c ? k1 : k0;
   const uint32_t* vin = c ? v1 : v0;
-  uint64_t* kout = c ? k0 : k1;
+  KT* kout = c ? k0 : k1;
   uint32_t* vout = c ? v0 : v1;
   int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   // the grid holds as many blocks as stay resident; they take the 4096-key tiles in turn
@@ -333,18 +335,18 @@ __global__ void __launch_bounds__(RS_T, 2) k_radix_scatter(uint64_t* __restrict_
       for (int q = 0; q < NW; ++q) s_wc[q][dd] = 0u;
     }
     uint32_t lt = (1u << lane) - 1u;
-    uint64_t key[RS_ITEMS];
+    KT key[RS_ITEMS];
     uint32_t val[RS_ITEMS];
     uint32_t rnk[RS_ITEMS / 2];  // ranks within the digit among this warp's keys, two 16-bit ranks a word
     int64_t wk = base + (int64_t)w * WKEYS + lane;  // this lane's key of round 0
     int64_t rem64 = I - wk;
     int rem = rem64 > RS_TILE ? RS_TILE : (int)rem64;  // round j holds a key iff 32 j < rem
-    const uint64_t* kp = kin + wk;
+    const KT* kp = kin + wk;
     const uint32_t* vp = vin + wk;
     #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
       bool valid = j * 32 < rem;
-      key[j] = valid ? kp[j * 32] : 0ull;
+      key[j] = valid ? kp[j * 32] : (KT)0;
       val[j] = valid ? vp[j * 32] : 0u;
     }
     __syncthreads();
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(RS_T, 2) k_radix_scatter(uint64_t* __restrict_
     __syncthreads();
     int n_here = (int)min((int64_t)RS_TILE, I - base);
     for (int i = tid; i < n_here; i += RS_T) {
-      uint64_t kk = s_keys[i];
+      KT kk = s_keys[i];
       uint32_t d = (uint32_t)(kk >> shift) & (BINS - 1u);
       uint32_t gp = s_off[d] + (uint32_t)i - s_lstart[d];
       kout[gp] = kk;
@@ -457,6 +459,206 @@ __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ k0,
       float4 b = alpha_box(make_float2(m.x, m.y), conic_op[p], pm);
       masks[k] = (uint16_t)block_mask(b, (int)(tile % (uint32_t)TX), (int)(tile / (uint32_t)TX));
     }
+  }
+}
+
+// ---- depth-first design: sort the visible records by depth once, then bin their instances by
+// (unit, tile) with a stable sort on 32-bit keys (block mask << 16 | unit | tile).  Stability makes
+// each list come out in (depth, record index) order, the order of the global key sort.
+
+// visible records (tiles > 0) per 2048-record scan block
+__global__ void __launch_bounds__(SCAN_T) k_vis_reduce(const uint32_t* __restrict__ tiles, int64_t P,
+                                                       uint32_t* __restrict__ bsums) {
+  __shared__ uint32_t s_warp[33];
+  int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK;
+  uint32_t s = 0;
+  #pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j) {
+    int64_t k = base + (int64_t)j * SCAN_T + threadIdx.x;
+    if (k < P && tiles[k] > 0u) ++s;
+  }
+  uint32_t tot;
+  block_excl_scan(s, s_warp, &tot);
+  if (threadIdx.x == 0) bsums[blockIdx.x] = tot;
+}
+
+// compaction in record order: (depth bits, record index) of every visible record; *d_vis = their number.
+// Round j of a block covers its records [256 j, 256 j + 256) (coalesced loads); a record's slot is the
+// block's base, the visible records of earlier (round, warp) pairs and those of lower lanes.
+__global__ void __launch_bounds__(SCAN_T) k_vis_compact(const uint32_t* __restrict__ tiles,
+                                                        const float* __restrict__ depth, int64_t P,
+                                                        const uint32_t* __restrict__ bsums, int64_t nb,
+                                                        uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                        uint32_t* __restrict__ d_vis) {
+  constexpr int NW = SCAN_T / 32;
+  static_assert(SCAN_ITEMS * NW == 64, "one warp scans the (round, warp) counts two per lane");
+  __shared__ uint32_t s_cnt[SCAN_ITEMS * NW];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK;
+  uint32_t bal[SCAN_ITEMS];
+  #pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j) {
+    int64_t k = base + (int64_t)j * SCAN_T + threadIdx.x;
+    bal[j] = __ballot_sync(0xffffffffu, k < P && tiles[k] > 0u);
+    if (lane == 0) s_cnt[j * NW + w] = __popc(bal[j]);
+  }
+  __syncthreads();
+  if (w == 0) {  // exclusive scan of the 64 (round, warp) counts, two per lane
+    uint32_t a = s_cnt[2 * lane], b = s_cnt[2 * lane + 1];
+    uint32_t inc = warp_incl_scan(a + b);
+    s_cnt[2 * lane] = inc - a - b;
+    s_cnt[2 * lane + 1] = inc - b;
+  }
+  __syncthreads();
+  uint32_t c0 = bsums[blockIdx.x];
+  uint32_t lt = (1u << lane) - 1u;
+  #pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j)
+    if (bal[j] >> lane & 1u) {
+      int64_t k = base + (int64_t)j * SCAN_T + threadIdx.x;
+      uint32_t c = c0 + s_cnt[j * NW + w] + __popc(bal[j] & lt);
+      keys[c] = __float_as_uint(depth[k]);
+      vals[c] = (uint32_t)k;
+    }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *d_vis = bsums[nb];
+}
+
+// instance count of every 2048 records in depth order (scan blocks), for the scan of the offsets
+__global__ void __launch_bounds__(SCAN_T) k_dup_reduce(const uint32_t* __restrict__ vA,
+                                                       const uint32_t* __restrict__ vB,
+                                                       const int32_t* __restrict__ cur, int final_pass,
+                                                       const uint32_t* __restrict__ d_vis,
+                                                       const uint32_t* __restrict__ tiles,
+                                                       uint32_t* __restrict__ bsums) {
+  __shared__ uint32_t s_warp[33];
+  const uint32_t* v = cur[final_pass] ? vB : vA;
+  int64_t V = *d_vis;
+  int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK;
+  uint32_t s = 0;
+  #pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j) {
+    int64_t i = base + (int64_t)j * SCAN_T + threadIdx.x;
+    if (i < V) s += tiles[v[i]];
+  }
+  uint32_t tot;
+  block_excl_scan(s, s_warp, &tot);
+  if (threadIdx.x == 0) bsums[blockIdx.x] = tot;
+}
+
+// one 32-bit key per (record, covered tile), records taken in depth order.  Block b takes sorted records
+// [2048 b, 2048 b + 2048), thread t the 8 consecutive ones from 2048 b + 8 t; their instances are numbered
+// from the block's scanned base in record order.  The block stages its instances in shared memory in
+// windows of EMIT_WIN and writes each window out with coalesced stores (a thread only visits the
+// instances of its records that fall in the window, so a window costs O(its instances + 8) per thread).
+// Block 0 also writes the instance count (clamped to the capacity, GS_ERR_CAPACITY beyond it).
+constexpr int EMIT_WIN = 4096;
+__global__ void __launch_bounds__(SCAN_T) k_dup_emit(UnitTable U, const float4* __restrict__ xy,
+                                                     const float4* __restrict__ conic_op,
+                                                     const int* __restrict__ radius, const uint32_t* __restrict__ vA,
+                                                     const uint32_t* __restrict__ vB, const int32_t* __restrict__ cur,
+                                                     int final_pass, const uint32_t* __restrict__ d_vis,
+                                                     const uint32_t* __restrict__ bsums, int64_t nb, int W, int H,
+                                                     int tile_bits, int64_t cap, int key_masks,
+                                                     uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                     uint32_t* __restrict__ d_count, int* __restrict__ status) {
+  __shared__ uint32_t s_warp[33];
+  __shared__ uint32_t s_p[SCAN_BLOCK];
+  __shared__ uint32_t s_key[EMIT_WIN];
+  __shared__ uint32_t s_val[EMIT_WIN];
+  const uint32_t* v = cur[final_pass] ? vB : vA;
+  int64_t V = *d_vis;
+  int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK;
+  #pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j) {
+    int64_t i = base + (int64_t)j * SCAN_T + threadIdx.x;
+    s_p[j * SCAN_T + threadIdx.x] = i < V ? v[i] : 0xffffffffu;
+  }
+  __syncthreads();
+  int TX = (W + TILE - 1) / TILE, TY = (H + TILE - 1) / TILE;
+  int rx0[SCAN_ITEMS], ry0[SCAN_ITEMS], rw[SCAN_ITEMS], rh[SCAN_ITEMS];
+  float4 box[SCAN_ITEMS];
+  uint32_t n = 0;
+  #pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j) {
+    uint32_t p = s_p[threadIdx.x * SCAN_ITEMS + j];
+    rx0[j] = ry0[j] = rw[j] = rh[j] = 0;
+    box[j] = make_float4(1.f, -1.f, 1.f, -1.f);
+    if (p != 0xffffffffu) {
+      float4 m = xy[p];
+      int x0, y0, x1, y1;
+      tile_rect(m, radius[p], TX, TY, x0, y0, x1, y1);
+      rx0[j] = x0; ry0[j] = y0; rw[j] = x1 - x0; rh[j] = y1 - y0;
+      n += (uint32_t)((x1 - x0) * (y1 - y0));
+      if (key_masks) {
+        float pm;
+        box[j] = alpha_box(make_float2(m.x, m.y), conic_op[p], pm);
+      }
+    }
+  }
+  uint32_t tot;
+  uint32_t lo = block_excl_scan(n, s_warp, &tot);  // this thread's first instance within the block
+  int64_t ob = (int64_t)bsums[blockIdx.x];           // the block's first instance
+  for (uint32_t win = 0; win < tot; win += EMIT_WIN) {
+    uint32_t a = lo;
+    #pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+      uint32_t c = (uint32_t)(rw[j] * rh[j]);
+      uint32_t k0 = a > win ? a : win;
+      uint32_t k1 = a + c < win + EMIT_WIN ? a + c : win + EMIT_WIN;
+      if (k0 < k1) {
+        uint32_t p = s_p[threadIdx.x * SCAN_ITEMS + j];
+        uint32_t hi = (uint32_t)unit_of(U, p) << tile_bits;
+        uint32_t t = k0 - a;
+        int ty = ry0[j] + (int)(t / (uint32_t)rw[j]), tx = rx0[j] + (int)(t % (uint32_t)rw[j]);
+        for (uint32_t k = k0; k < k1; ++k) {
+          uint32_t mk = key_masks ? block_mask(box[j], tx, ty) << 16 : 0u;
+          s_key[k - win] = mk | hi | (uint32_t)(ty * TX + tx);
+          s_val[k - win] = p;
+          if (++tx == rx0[j] + rw[j]) { tx = rx0[j]; ++ty; }
+        }
+      }
+      a += c;
+    }
+    __syncthreads();
+    uint32_t wn = tot - win < (uint32_t)EMIT_WIN ? tot - win : (uint32_t)EMIT_WIN;
+    for (uint32_t i = threadIdx.x; i < wn; i += SCAN_T) {
+      int64_t g = ob + win + i;
+      if (g < cap) {
+        keys[g] = s_key[i];
+        vals[g] = s_val[i];
+      }
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    uint32_t total = bsums[nb];
+    if ((int64_t)total > cap) {
+      set_status(status, GS_ERR_CAPACITY);
+      total = (uint32_t)cap;
+    }
+    *d_count = total;
+  }
+}
+
+// list ranges, record ids and block masks from the sorted 32-bit instance keys
+__global__ void __launch_bounds__(256) k_ranges32(const uint32_t* __restrict__ kA, const uint32_t* __restrict__ kB,
+                                                  const uint32_t* __restrict__ vA, const uint32_t* __restrict__ vB,
+                                                  const int32_t* __restrict__ cur, int final_pass,
+                                                  const uint32_t* __restrict__ d_count, int tile_bits, int n_tiles,
+                                                  uint32_t* __restrict__ ranges, uint32_t* __restrict__ out_vals,
+                                                  uint16_t* __restrict__ masks) {
+  int64_t I = *d_count;
+  int c = cur[final_pass];
+  const uint32_t* keys = c ? kB : kA;
+  const uint32_t* vals = c ? vB : vA;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < I; k += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t kk = keys[k];
+    uint32_t ut = kk & 0xffffu;
+    out_vals[k] = vals[k];
+    int64_t flat = (int64_t)(ut >> tile_bits) * n_tiles + (ut & ((1u << tile_bits) - 1u));
+    if (k == 0 || (keys[k - 1] & 0xffffu) != ut) ranges[2 * flat] = (uint32_t)k;
+    if (k == I - 1 || (keys[k + 1] & 0xffffu) != ut) ranges[2 * flat + 1] = (uint32_t)(k + 1);
+    if (masks) masks[k] = (uint16_t)(kk >> 16);
   }
 }
 
@@ -555,8 +757,69 @@ int gs_seg_sort(const UnitTable& U, int64_t P, const gs_proj* proj, int width, i
                 uint64_t* keysA, uint64_t* keysB, uint32_t* wsS, uint32_t* wsL, uint32_t* bsums, uint32_t* ctr,
                 uint32_t* sorted_vals, uint32_t* ranges, uint16_t* masks, cudaStream_t s);
 
-// method 0: the global LSD radix sort of (unit | tile | depth) keys; 1: the bucketed sort (sort_seg.cu).
-// Both give the same lists, ranges and masks.
+// The depth-first design (method 2): compact the visible records in record order, sort them by their
+// 32-bit depth keys (stable 8-bit passes; a pass whose digit all keys share is skipped), scan their
+// instance counts in that order, emit one 32-bit (mask | unit | tile) key per instance, sort those
+// stably on the unit | tile bits (ut_bits <= 16: one or two 8-bit passes) and read off the lists.
+// Buffers: the record pairs ping-pong between keys0 (keys at word 0, ids at word P) and keys1; the
+// instance pairs between (vals0, vals1) and (keys0, keys1) reinterpreted as 32-bit words.
+static int depth_first_sort(const UnitTable& U, int64_t P, const gs_proj* proj, int width, int height, int64_t cap,
+                     int tile_bits, int ut_bits, int64_t nsb, int64_t stride, uint32_t* bsums,
+                     uint64_t* k0, uint64_t* k1, uint32_t* v0, uint32_t* v1, uint32_t* hist, uint32_t* totals,
+                     int32_t* cur, uint32_t* d_vis, uint32_t* sorted_vals, uint32_t* ranges,
+                     uint32_t* d_num_instances, uint16_t* block_masks, int* d_status, cudaStream_t s) {
+  constexpr size_t DYN32 = RS_TILE * (sizeof(uint32_t) + sizeof(uint32_t));
+  int n_tiles = ((width + TILE - 1) / TILE) * ((height + TILE - 1) / TILE);
+  uint32_t* dkA = (uint32_t*)k0;
+  uint32_t* dvA = dkA + P;
+  uint32_t* dkB = (uint32_t*)k1;
+  uint32_t* dvB = dkB + P;
+  if (cudaFuncSetAttribute(k_radix_scatter<8, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DYN32) !=
+      cudaSuccess)
+    return GS_ERR_CUDA;
+  unsigned gh = resident_blocks(k_radix_hist<8, uint32_t>, RS_T, 0, stride);
+  unsigned gsc = resident_blocks(k_radix_scatter<8, uint32_t>, RS_T, DYN32, stride);
+  k_vis_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, P, bsums);
+  k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);
+  k_vis_compact<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, proj->depth, P, bsums, nsb, dkA, dvA, d_vis);
+  constexpr int DEPTH_PASSES = 4;
+  for (int pass = 0; pass < DEPTH_PASSES; ++pass) {
+    k_radix_hist<8, uint32_t><<<gh, RS_T, 0, s>>>(dkA, dkB, cur, pass, d_vis, 8 * pass, hist, stride, totals);
+    k_radix_scan<<<256, 1024, 0, s>>>(hist, stride, totals, pass, 256, d_vis, cur);
+    k_radix_scatter<8, uint32_t><<<gsc, RS_T, DYN32, s>>>(dkA, dkB, dvA, dvB, cur, pass, d_vis, 8 * pass, hist,
+                                                          stride);
+  }
+  k_dup_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(dvA, dvB, cur, DEPTH_PASSES, d_vis, proj->tiles, bsums);
+  k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);
+  int key_masks = block_masks ? 1 : 0;
+  uint32_t* ikA = v0;
+  uint32_t* ivA = v1;
+  uint32_t* ikB = (uint32_t*)k0;
+  uint32_t* ivB = (uint32_t*)k1;
+  k_dup_emit<<<(unsigned)nsb, SCAN_T, 0, s>>>(U, (const float4*)proj->xy, (const float4*)proj->conic_op,
+                                              proj->radius, dvA, dvB, cur, DEPTH_PASSES, d_vis, bsums, nsb, width,
+                                              height, tile_bits, cap, key_masks, ikA, ivA, d_num_instances,
+                                              d_status);
+  if (cap == 0) return gs_check_launch();
+  // the instance passes keep their own buffer parity and digit totals
+  int32_t* cur_t = cur + MAX_PASSES + 1;
+  uint32_t* totals_t = totals + DEPTH_PASSES * RS_BINS_MAX;
+  int tpasses = (ut_bits + 7) / 8;
+  for (int pass = 0; pass < tpasses; ++pass) {
+    k_radix_hist<8, uint32_t><<<gh, RS_T, 0, s>>>(ikA, ikB, cur_t, pass, d_num_instances, 8 * pass, hist, stride,
+                                                  totals_t);
+    k_radix_scan<<<256, 1024, 0, s>>>(hist, stride, totals_t, pass, 256, d_num_instances, cur_t);
+    k_radix_scatter<8, uint32_t><<<gsc, RS_T, DYN32, s>>>(ikA, ikB, ivA, ivB, cur_t, pass, d_num_instances, 8 * pass,
+                                                          hist, stride);
+  }
+  k_ranges32<<<resident_blocks(k_ranges32, 256, 0, (cap + 255) / 256), 256, 0, s>>>(
+      ikA, ikB, ivA, ivB, cur_t, tpasses, d_num_instances, tile_bits, n_tiles, ranges, sorted_vals, block_masks);
+  return gs_check_launch();
+}
+
+// method 0: the global LSD radix sort of (unit | tile | depth) keys; 1: the bucketed sort (sort_seg.cu);
+// 2: the depth-first design (falls back to 0 when unit | tile needs more than 16 bits).  All give the
+// same lists, ranges and masks.
 int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int height, int64_t max_instances,
                      void* workspace, size_t workspace_bytes, uint32_t* sorted_vals, uint32_t* ranges,
                      uint32_t* d_num_instances, const gs_schedule* sched, int* d_status, cudaStream_t s,
@@ -579,6 +842,7 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
   int unit_bits = bits_for(U.n);
   if (tile_bits + unit_bits > 32) return GS_ERR_INVALID;
   int key_bits = 32 + tile_bits + unit_bits;
+  if (method == 2 && tile_bits + unit_bits > 16) method = 0;  // unit | tile beside the mask in 32 bits
   // 9-bit digits when they save a pass (45-bit keys at 1080p: 5 passes instead of 6)
   int digit = ((key_bits + 8) / 9 < (key_bits + 7) / 8) ? 9 : 8;
   int passes = (key_bits + digit - 1) / digit;
@@ -592,12 +856,12 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
   uint32_t* hist = (uint32_t*)(ws + L.hist);
   uint32_t* totals = (uint32_t*)(ws + L.totals);
   int32_t* cur = (int32_t*)(ws + L.cur);
-  int64_t stride = (max_instances + RS_TILE - 1) / RS_TILE;
+  int64_t stride = ((max_instances > P ? max_instances : P) + RS_TILE - 1) / RS_TILE;
   if (stride < 1) stride = 1;
 
   if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)n_tiles * U.n, s) != cudaSuccess ||
       cudaMemsetAsync(totals, 0, sizeof(uint32_t) * RS_BINS_MAX * MAX_PASSES, s) != cudaSuccess ||
-      cudaMemsetAsync(cur, 0, sizeof(int32_t) * (MAX_PASSES + 1), s) != cudaSuccess ||
+      cudaMemsetAsync(cur, 0, sizeof(int32_t) * 2 * (MAX_PASSES + 1), s) != cudaSuccess ||
       cudaMemsetAsync(d_num_instances, 0, sizeof(uint32_t), s) != cudaSuccess)
     return GS_ERR_CUDA;
   if (P == 0) {
@@ -605,6 +869,14 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
     return gs_check_launch();
   }
   int64_t nsb = (P + SCAN_BLOCK - 1) / SCAN_BLOCK;
+  if (method == 2) {
+    int r = depth_first_sort(U, P, proj, width, height, max_instances, tile_bits, tile_bits + unit_bits, nsb, stride,
+                             bsums, k0, k1, v0, v1, hist, totals, cur, (uint32_t*)(ws + L.misc),
+                             sorted_vals, ranges, d_num_instances, block_masks, d_status, s);
+    if (r != GS_OK) return r;
+    if (sched) return gs_schedule_jobs(ranges, n_tiles * U.n, ws + L.order, ws + L.jscan, sched, s);
+    return gs_check_launch();
+  }
   k_scan_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, P, bsums);
   k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);
   k_scan_down<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, P, bsums, nsb, offsets, max_instances,
@@ -623,26 +895,26 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
                                                           proj->depth, proj->radius, proj->tiles, offsets, width,
                                                           height, tile_bits, max_instances, key_masks, k0, v0);
   if (max_instances > 0) {
-    if (cudaFuncSetAttribute(k_radix_scatter<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SCATTER_DYN_SMEM) !=
+    if (cudaFuncSetAttribute(k_radix_scatter<8, uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, SCATTER_DYN_SMEM) !=
             cudaSuccess ||
-        cudaFuncSetAttribute(k_radix_scatter<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, SCATTER_DYN_SMEM) !=
+        cudaFuncSetAttribute(k_radix_scatter<9, uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, SCATTER_DYN_SMEM) !=
             cudaSuccess)
       return GS_ERR_CUDA;
-    unsigned gh = digit == 9 ? resident_blocks(k_radix_hist<9>, RS_T, 0, stride)
-                             : resident_blocks(k_radix_hist<8>, RS_T, 0, stride);
-    unsigned gs = digit == 9 ? resident_blocks(k_radix_scatter<9>, RS_T, SCATTER_DYN_SMEM, stride)
-                             : resident_blocks(k_radix_scatter<8>, RS_T, SCATTER_DYN_SMEM, stride);
+    unsigned gh = digit == 9 ? resident_blocks(k_radix_hist<9, uint64_t>, RS_T, 0, stride)
+                             : resident_blocks(k_radix_hist<8, uint64_t>, RS_T, 0, stride);
+    unsigned gs = digit == 9 ? resident_blocks(k_radix_scatter<9, uint64_t>, RS_T, SCATTER_DYN_SMEM, stride)
+                             : resident_blocks(k_radix_scatter<8, uint64_t>, RS_T, SCATTER_DYN_SMEM, stride);
     for (int pass = 0; pass < passes; ++pass) {
       int shift = digit * pass;
       if (digit == 9) {
-        k_radix_hist<9><<<gh, RS_T, 0, s>>>(k0, k1, cur, pass, d_num_instances, shift, hist, stride, totals);
+        k_radix_hist<9, uint64_t><<<gh, RS_T, 0, s>>>(k0, k1, cur, pass, d_num_instances, shift, hist, stride, totals);
         k_radix_scan<<<512, 1024, 0, s>>>(hist, stride, totals, pass, 512, d_num_instances, cur);
-        k_radix_scatter<9><<<gs, RS_T, SCATTER_DYN_SMEM, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift,
+        k_radix_scatter<9, uint64_t><<<gs, RS_T, SCATTER_DYN_SMEM, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift,
                                                                hist, stride);
       } else {
-        k_radix_hist<8><<<gh, RS_T, 0, s>>>(k0, k1, cur, pass, d_num_instances, shift, hist, stride, totals);
+        k_radix_hist<8, uint64_t><<<gh, RS_T, 0, s>>>(k0, k1, cur, pass, d_num_instances, shift, hist, stride, totals);
         k_radix_scan<<<256, 1024, 0, s>>>(hist, stride, totals, pass, 256, d_num_instances, cur);
-        k_radix_scatter<8><<<gs, RS_T, SCATTER_DYN_SMEM, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift,
+        k_radix_scatter<8, uint64_t><<<gs, RS_T, SCATTER_DYN_SMEM, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift,
                                                                hist, stride);
       }
     }
@@ -658,6 +930,15 @@ GS_API int gs_bin_sort(const gs_proj* proj, const gs_units* units, int width, in
                        void* workspace, size_t workspace_bytes, uint32_t* sorted_vals, uint32_t* ranges,
                        uint32_t* d_num_instances, const gs_schedule* sched, int* d_status, gs_stream_t stream) {
   GS_RANGE("gs_bin_sort");
+  return gs_bin_sort_impl(proj, units, width, height, max_instances, workspace, workspace_bytes, sorted_vals,
+                          ranges, d_num_instances, sched, d_status, (cudaStream_t)stream, 2);
+}
+
+GS_API int gs_bin_sort_global(const gs_proj* proj, const gs_units* units, int width, int height,
+                              int64_t max_instances, void* workspace, size_t workspace_bytes, uint32_t* sorted_vals,
+                              uint32_t* ranges, uint32_t* d_num_instances, const gs_schedule* sched, int* d_status,
+                              gs_stream_t stream) {
+  GS_RANGE("gs_bin_sort_global");
   return gs_bin_sort_impl(proj, units, width, height, max_instances, workspace, workspace_bytes, sorted_vals,
                           ranges, d_num_instances, sched, d_status, (cudaStream_t)stream, 0);
 }
@@ -698,7 +979,7 @@ GS_API int gs_merge_render(const float* params, int64_t n_gauss, int sh_degree, 
   int r = gs_preprocess(params, n_gauss, sh_degree, &one, cam, width, height, owned, proj, d_status, stream);
   if (r != GS_OK) return r;
   r = gs_bin_sort_impl(proj, &one, width, height, max_instances, workspace, workspace_bytes, sorted_vals, ranges,
-                       d_num_instances, sched, d_status, (cudaStream_t)stream, 0);
+                       d_num_instances, sched, d_status, (cudaStream_t)stream, 2);
   if (r != GS_OK) return r;
   return gs_render_fwd_impl(proj, sorted_vals, ranges, 1, width, height, bg, img, final_T, n_contrib, 0, sched,
                             (cudaStream_t)stream);

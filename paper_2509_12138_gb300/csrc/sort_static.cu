@@ -123,5 +123,5 @@ GS_API int gs_bin_sort_static(const gs_proj* proj, const gs_units* units, int wi
   int r = scratch_ptr(&ws);
   if (r != GS_OK) return r;
   return gs_bin_sort_impl(proj, units, width, height, cap, ws, SCRATCH_BYTES, sorted_vals, ranges, d_num_instances,
-                          nullptr, d_status, (cudaStream_t)stream, 0);
+                          nullptr, d_status, (cudaStream_t)stream, 2);
 }

@@ -223,9 +223,15 @@ class Frame:
                                    self.W, self.H, C.byref(owned.struct) if owned is not None else None,
                                    C.byref(self.proj), _ptr(self.status), _stream()), "gs_preprocess")
 
-    def sort(self, bucketed: bool = False):
-        """gs_bin_sort (one global radix sort), or gs_bin_sort_bucketed (per-list sorts; same results)."""
-        fn = self.L.gs_bin_sort_bucketed if bucketed else self.L.gs_bin_sort
+    sort_design = "depth_first"
+
+    def sort(self, design: str = None):
+        """gs_bin_sort (records sorted by depth, then their instances binned), gs_bin_sort_global (one radix
+        sort of all instance keys) or gs_bin_sort_bucketed (per-list sorts); all three give the same lists.
+        design: "depth_first", "global" or "bucketed" (default: the frame's sort_design)."""
+        design = design or self.sort_design
+        fn = {"depth_first": self.L.gs_bin_sort, "global": self.L.gs_bin_sort_global,
+              "bucketed": self.L.gs_bin_sort_bucketed}[design]
         check(fn(C.byref(self.proj), C.byref(self.units.struct), self.W, self.H, self.cap, _ptr(self.sort_ws),
                  self.sort_ws.numel(), _ptr(self.sorted_vals), _ptr(self.ranges), _ptr(self.num_instances),
                  self._sched(), _ptr(self.status), _stream()), "gs_bin_sort")

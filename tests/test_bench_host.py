@@ -77,11 +77,19 @@ def test_traffic_scales_by_units_and_only_for_the_captured_workload():
 
 
 def test_launch_count_of_one_step():
-    frame = types.SimpleNamespace(n_tiles=120 * 68, units=types.SimpleNamespace(n=1), use_masks=True)
+    frame = types.SimpleNamespace(n_tiles=120 * 68, units=types.SimpleNamespace(n=1), use_masks=True,
+                                  sort_design="global")
     # preprocess 1; sort 3 + 1 + 3 x 5 passes + 1; schedule 7; forward 3; loss 4; backward 1; Adam 2
     assert bench.kernel_launch_count(frame, 0.2) == 38
     frame.use_masks = False
     assert bench.kernel_launch_count(frame, 0.0) == 1 + 20 + 1 + 3 + 1 + 2
+    # depth-first sort: visibility scan + compaction 3, depth passes 12, instance counts + their scan +
+    # emission 3, two instance passes over the 13 tile bits 6, ranges 1
+    frame.sort_design, frame.use_masks = "depth_first", True
+    assert bench.kernel_launch_count(frame, 0.2) == 1 + 25 + 7 + 3 + 4 + 1 + 2
+    # unit | tile ids over 16 bits: the global sort's chain
+    frame.units.n = 16
+    assert bench.kernel_launch_count(frame, 0.2) == 1 + (3 + 1 + 3 * 6 + 1) + 7 + 3 + 4 + 1 + 2
 
 
 def test_clock_parsing():
