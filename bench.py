@@ -473,17 +473,19 @@ BWD_SLOTS_PER_PAIR = 50
 # stage's algorithmic work counts.  Given only for the stages whose data stream far exceeds L2 at that size
 # (so that their traffic grows in proportion to the units), and reported for the 10M workload in Z-order,
 # scaled by the units of the bench's own timed views.
+# The depth-first sort's working set (the 10M records' depth pairs, 80 MB) stays in L2 at 2M, so its figure
+# comes from a one-pass capture of the sort kernels alone (-k) on the 10M workload itself.
 TRAFFIC_WORKLOAD = "iso10M-1080p"
 TRAFFIC_CAPTURED_ON = "iso2M-1080p-prof"
 TRAFFIC_PER_UNIT = {
-    "preprocess": ("gaussian", 290.31),
-    "bin_sort": None,
+    "preprocess": ("gaussian", 290.31, TRAFFIC_CAPTURED_ON),
+    "bin_sort": ("instance", 117.57, TRAFFIC_WORKLOAD),
     "render_fwd": None,
     "loss": None,
     "blend_bwd": None,
-    "project_bwd_adam": ("gaussian", 1451.90),
+    "project_bwd_adam": ("gaussian", 1451.90, TRAFFIC_CAPTURED_ON),
     # the same kernel with the next step's projection fused in (gs_project_bwd_adam_next)
-    "project_bwd_adam_next": ("gaussian", 1512.19),
+    "project_bwd_adam_next": ("gaussian", 1512.19, TRAFFIC_CAPTURED_ON),
 }
 
 
@@ -556,8 +558,11 @@ def rooflines(res, workload=None, issue=None, random_order=False):
         # (the captured traffic is that of the dense update)
         tkey = "project_bwd_adam_next" if (fused and name == "project_bwd_adam") else name
         sparse_upd = name == "project_bwd_adam" and res.get("sparse_adam")
-        if workload == TRAFFIC_WORKLOAD and not random_order and TRAFFIC_PER_UNIT[tkey] and not sparse_upd:
-            u, per = TRAFFIC_PER_UNIT[tkey]
+        # (the sort's figure is that of the depth-first design)
+        other_sort = name == "bin_sort" and res.get("sort_design", "global") != "depth_first"
+        if (workload == TRAFFIC_WORKLOAD and not random_order and TRAFFIC_PER_UNIT[tkey] and not sparse_upd
+                and not other_sort):
+            u, per, _ = TRAFFIC_PER_UNIT[tkey]
             traffic = round(per * units[u])
         if bound == "hbm":
             ach = amount / (ms * 1e-3) / 1e9
@@ -577,8 +582,10 @@ def rooflines(res, workload=None, issue=None, random_order=False):
                          "work_avoided": f"{n_plain - n_pairs:.3e} pairs of the plain per-pixel walk "
                                          f"({n_plain:.3e}) fall outside the masks"}
         if traffic is not None:
-            out[name]["traffic_source"] = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum on {TRAFFIC_CAPTURED_ON}, "
-                                           f"scaled to {TRAFFIC_WORKLOAD} by units: "
+            on = TRAFFIC_PER_UNIT[tkey][2]
+            out[name]["traffic_source"] = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum on {on}, "
+                                           + (f"scaled to {TRAFFIC_WORKLOAD} by units: " if on != TRAFFIC_WORKLOAD
+                                              else "per unit times the units of the timed views: ") +
                                            f"{TRAFFIC_PER_UNIT[tkey][1]} B per {TRAFFIC_PER_UNIT[tkey][0]} x "
                                            f"{units[TRAFFIC_PER_UNIT[tkey][0]]:.4g} {TRAFFIC_PER_UNIT[tkey][0]}s")
         out[name]["share"] = round(float(ms / res["stage_ms"].sum()), 4)

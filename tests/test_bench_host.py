@@ -9,9 +9,10 @@ import pytest
 import bench
 
 
-def _res(stage_ms):
+def _res(stage_ms, sort_design="depth_first"):
     stages = list(stage_ms)
-    return dict(N=10_000_000, instances=17_000_000, W=1920, H=1080, stages=stages,
+    return dict(N=10_000_000, instances=17_000_000, W=1920, H=1080, stages=stages, sort_design=sort_design,
+                visible=1.0,
                 stage_ms=np.array([stage_ms[k] for k in stages]),
                 pairs={"blended": 6e7, "fwd_pairs": 4e9, "bwd_pairs": 2.5e9, "fwd_pairs_masked": 6e8,
                        "bwd_pairs_masked": 4e8})
@@ -66,10 +67,13 @@ def test_traffic_scales_by_units_and_only_for_the_captured_workload():
         if entry is None:  # kernels changed since their counters were taken: no traffic figure
             assert out[name]["traffic"] is None
             continue
-        unit, per = entry
+        unit, per, _ = entry
         n = {"gaussian": 10_000_000, "instance": 17_000_000, "pixel": 1920 * 1080, "fwd_pair": 4e9,
              "bwd_pair": 2.5e9}[unit]
         assert out[name]["traffic"] == round(per * n)
+    # the sort's figure was taken on the depth-first design only
+    _, glob = bench.rooflines(_res(ms, "global"), "iso10M-1080p", None)
+    assert glob["bin_sort"]["traffic"] is None and glob["preprocess"]["traffic"] is not None
     _, other = bench.rooflines(_res(ms), "iso1M-1080p", None)
     assert all(v["traffic"] is None for v in other.values())
     _, rnd = bench.rooflines(_res(ms), "iso10M-1080p", None, random_order=True)
