@@ -77,7 +77,11 @@ def _declare(L):
     L.orc_loss.restype = C.c_double
     L.orc_loss_dir.argtypes = [_D, _D, _D, _U8, C.c_int, C.c_int, C.c_double]
     L.orc_loss_dir.restype = C.c_double
-    L.orc_render_backward.argtypes = [C.c_int, C.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D]
+    L.orc_render_backward.argtypes = [C.c_int, C.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D]
+    L.orc_bg_penalty.argtypes = [_D, _U8, C.c_int, C.c_int, C.c_double, _D]
+    L.orc_bg_penalty.restype = C.c_double
+    L.orc_penalty_params_dir.argtypes = [C.c_int, C.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _U8, C.c_double, _D]
+    L.orc_penalty_params_dir.restype = C.c_double
     L.orc_project_backward.argtypes = [C.c_int, C.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D]
     L.orc_loss_params_dir.argtypes = [C.c_int, C.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _U8,
                                       C.c_double, _D]
@@ -252,13 +256,39 @@ def loss_dir(img, direction, gt, mask, lam: float) -> float:
     return lib().orc_loss_dir(_p(img), _p(direction), _p(gt), _p(mask), W, H, float(lam))
 
 
-def render_backward(g, cam, bg, dimg):
+def render_backward(g, cam, bg, dimg, dT=None):
+    """Screen-space gradients from dL/dimage and, optionally, dL/dT_final ([H, W]) of a loss term on the
+    pixels' final transmittance (the background-opacity penalty)."""
     n, deg, m, ls, q, lo, sh = _gauss(g)
     cam, bg, dimg = _d(cam), _d(bg), _d(dimg)
+    dT = None if dT is None else _d(dT)
     out = dict(dxy=np.zeros((n, 2)), dconic=np.zeros((n, 3)), dopacity=np.zeros(n), drgb=np.zeros((n, 3)))
     lib().orc_render_backward(n, deg, _p(m), _p(ls), _p(q), _p(lo), _p(sh), _p(cam), _p(bg), _p(dimg),
+                              _p(dT) if dT is not None else None,
                               _p(out["dxy"]), _p(out["dconic"]), _p(out["dopacity"]), _p(out["drgb"]))
     return out
+
+
+def bg_penalty(final_T, mask, lam: float):
+    """Background-opacity penalty of one view: lam x mean of (1 - T_final) over the pixels outside the mask
+    (0 if there are none), and its gradient dpenalty/dT_final [H, W]."""
+    final_T = _d(final_T)
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    H, W = mask.shape
+    dT = np.zeros((H, W))
+    val = lib().orc_bg_penalty(_p(final_T), _p(mask), W, H, float(lam), _p(dT))
+    return val, dT
+
+
+def penalty_params_dir(g, tangent, cam, bg, mask, lam: float):
+    """(penalty, exact directional derivative along ``tangent`` [n, n_params]) by dual numbers."""
+    n, deg, m, ls, q, lo, sh = _gauss(g)
+    tangent, cam, bg = _d(tangent), _d(cam), _d(bg)
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    dp = np.zeros(1)
+    v = lib().orc_penalty_params_dir(n, deg, _p(m), _p(ls), _p(q), _p(lo), _p(sh), _p(tangent), _p(cam), _p(bg),
+                                     _p(mask), float(lam), _p(dp))
+    return v, float(dp[0])
 
 
 def project_backward(g, cam, g2d):

@@ -796,10 +796,12 @@ double orc_loss_dir(const double* img, const double* dir, const double* gt, cons
 
 // Screen-space gradients of the loss for one view, by reverse replay of the
 // blend: per visible Gaussian dL/d(x, y), dL/d(A, B, C), dL/d opacity and
-// dL/d rgb.  dimg is dL/dimage [3][H][W].
+// dL/d rgb.  dimg is dL/dimage [3][H][W]; dT (may be NULL) is dL/dT_final
+// [H][W], the gradient of a loss term on the pixels' final transmittance.
 void orc_render_backward(int n, int deg, const double* means, const double* ls, const double* quats,
                          const double* logit, const double* sh, const double* camv, const double* bg,
-                         const double* dimg, double* dxy, double* dconic, double* dop, double* drgb) {
+                         const double* dimg, const double* dT, double* dxy, double* dconic, double* dop,
+                         double* drgb) {
   Cam cam = load_cam(camv);
   Params p{n, deg, means, ls, quats, logit, sh};
   std::vector<Proj<double>> P;
@@ -824,9 +826,11 @@ void orc_render_backward(int n, int deg, const double* means, const double* ls, 
       std::vector<int> blended;
       std::vector<double> Ts;
       PixelOut<double> o = blend_pixel(px, py, list, len, P.data(), bg, &blended, &Ts);
-      (void)o;
       size_t q = (size_t)py * W + px;
       double g[3] = {dimg[q], dimg[np + q], dimg[2 * np + q]};
+      // T_final is the product of (1 - alpha_k) over the blended entries, so its derivative with
+      // respect to one entry's alpha_i is -T_final / (1 - alpha_i)
+      double gT = dT ? dT[q] : 0.0;
       // colour of everything behind entry k, seen through entry k's own gap
       double behind[3] = {bg[0], bg[1], bg[2]};
       for (int b = (int)blended.size() - 1; b >= 0; --b) {
@@ -845,6 +849,7 @@ void orc_render_backward(int n, int deg, const double* means, const double* ls, 
           dalpha += Ti * (G.col[ch] - behind[ch]) * g[ch];
           behind[ch] = alpha * G.col[ch] + (1.0 - alpha) * behind[ch];
         }
+        dalpha += gT * (-o.T / (1.0 - alpha));
         if (clamped) continue;
         dop[j] += e * dalpha;
         double dpow = araw * dalpha;
@@ -920,6 +925,55 @@ double orc_loss_params_dir(int n, int deg, const double* means, const double* ls
   Dual l = loss_value<Dual>(img.data(), gt, mask, cam.W, cam.H, lam);
   if (dloss) *dloss = l.d;
   return l.v;
+}
+
+// Background-opacity penalty of one view (a variant of the mask of Sec. II,
+// "Image Rendering and Masking"): lam times the mean of the rendered opacity
+// 1 - T_final over the pixels outside the mask (0 when there are none).
+// dT (may be NULL) receives dpenalty/dT_final [H][W].
+double orc_bg_penalty(const double* finalT, const unsigned char* mask, int W, int H, double lam, double* dT) {
+  size_t np = (size_t)W * H;
+  size_t nb = 0;
+  double acc = 0.0;
+  for (size_t q = 0; q < np; ++q)
+    if (!mask[q]) { acc += 1.0 - finalT[q]; ++nb; }
+  if (dT)
+    for (size_t q = 0; q < np; ++q) dT[q] = (!mask[q] && nb) ? -lam / (double)nb : 0.0;
+  return nb ? lam * acc / (double)nb : 0.0;
+}
+
+// The penalty of one view and its exact directional derivative along a
+// parameter tangent (dual numbers through projection and blending, as
+// orc_loss_params_dir).  Returns the penalty; *dpen receives the derivative.
+double orc_penalty_params_dir(int n, int deg, const double* means, const double* ls, const double* quats,
+                              const double* logit, const double* sh, const double* tangent, const double* camv,
+                              const double* bg, const unsigned char* mask, double lam, double* dpen) {
+  Cam cam = load_cam(camv);
+  Params p{n, deg, means, ls, quats, logit, sh};
+  int np = n_params(deg);
+  std::vector<Proj<Dual>> P(n);
+  for (int i = 0; i < n; ++i) {
+    std::vector<double> v(np);
+    gather_params(p, i, v.data());
+    std::vector<Dual> dv(np);
+    for (int k = 0; k < np; ++k) dv[k] = Dual(v[k], tangent[(size_t)np * i + k]);
+    P[i] = project_vec<Dual>(dv.data(), deg, cam);
+  }
+  std::vector<double> x(n), y(n), d(n);
+  std::vector<int> r(n);
+  for (int i = 0; i < n; ++i) { x[i] = P[i].x.v; y[i] = P[i].y.v; r[i] = P[i].radius; d[i] = P[i].depth.v; }
+  Lists L;
+  bin_and_sort(n, x.data(), y.data(), r.data(), d.data(), cam.W, cam.H, L, nullptr);
+  size_t npx = (size_t)cam.W * cam.H;
+  std::vector<Dual> img(3 * npx), T(npx);
+  render_image<Dual>(L, P.data(), cam.W, cam.H, bg, img.data(), T.data(), nullptr, nullptr);
+  Dual acc(0.0, 0.0);
+  size_t nb = 0;
+  for (size_t q = 0; q < npx; ++q)
+    if (!mask[q]) { acc = acc + (Dual(1.0, 0.0) - T[q]); ++nb; }
+  if (!nb) { if (dpen) *dpen = 0.0; return 0.0; }
+  if (dpen) *dpen = lam * acc.d / (double)nb;
+  return lam * acc.v / (double)nb;
 }
 
 // Textbook Adam with bias correction, one step t >= 1, per-element learning rate.
