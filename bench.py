@@ -87,6 +87,9 @@ def parse():
                     help="learned-init: the MLP trains on a random subset of this many source points")
     ap.add_argument("--exp-init-scale", type=float, default=1.0,
                     help="ghost-ablation: factor on the plain initialisation's scale")
+    ap.add_argument("--exp-lambda-bg", type=float, default=0.1,
+                    help="ghost-ablation: weight of the background-opacity penalty of the 'mask=on+bg' variant "
+                         "(0: leave the variant out)")
     ap.add_argument("--exp-seam-delta", type=float, default=0.01,
                     help="ghost-ablation: seam band half-width (x distance of the visible surface from a slab edge)")
     ap.add_argument("--exp-learned-lr", type=float, default=1.0,
@@ -734,10 +737,10 @@ def run_ghost_ablation(args):
     __graft_entry__.build()
     slabs, W, H, V = [args.exp_gaussians // 4] * 4, 960, 540, 32
     res = X.ghost_ablation(slabs, 8, V, W, H, args.exp_steps, n_parts=4, ghost=0.05, sh_degree=1,
-                           delta=args.exp_seam_delta, init_scale=args.exp_init_scale)
+                           delta=args.exp_seam_delta, init_scale=args.exp_init_scale, lambda_bg=args.exp_lambda_bg)
     print(json.dumps({"experiment": "ghost cells x masks", "gaussians": sum(slabs), "partitions": 4, "ghost": 0.05,
                       "width": W, "height": H, "views": V, "steps": args.exp_steps,
-                      "init_scale": args.exp_init_scale,
+                      "init_scale": args.exp_init_scale, "lambda_bg": args.exp_lambda_bg,
                       "seam_band": f"pixels whose surface lies within {args.exp_seam_delta} (x) of an interior slab "
                                    "boundary",
                       "results": res}))

@@ -335,6 +335,20 @@ int gs_loss(const float* img, const float* gt, const uint8_t* mask, int n_units,
             int height, float lambda_ssim, void* workspace, size_t workspace_bytes, float* d_loss,
             float* dL_dimg, gs_stream_t stream);
 
+/* Background-opacity penalty, a variant of the masked loss (the paper's mask
+ * removes the pixels a partition does not own, Sec. II "Image Rendering and
+ * Masking"; this term also asks those pixels to stay transparent).  Per unit
+ * with n_bg > 0 pixels outside the mask: P = lambda_bg sum_{p not in M}
+ * (1 - final_T[p]) / n_bg (0 when n_bg = 0); the mean over units is ADDED to
+ * *d_loss (call it after gs_loss).  dL_dT: [U][H][W] float, overwritten with
+ * dP/dT_final (-lambda_bg / (U n_bg) outside the mask, 0 inside), the input of
+ * the same name of gs_render_bwd / gs_blend_bwd.  lambda_bg >= 0, finite.
+ * Workspace: gs_bg_penalty_workspace_size(n_units) bytes, 256-byte aligned. */
+size_t gs_bg_penalty_workspace_size(int n_units);
+int gs_bg_penalty(const float* final_T, const uint8_t* mask, int n_units, int width, int height,
+                  float lambda_bg, void* workspace, size_t workspace_bytes, float* d_loss, float* dL_dT,
+                  gs_stream_t stream);
+
 /* ---- a5: backward ---------------------------------------------------------
  * Blend backward: per pixel, the tile list is replayed back to front from
  * n_contrib, recovering T_i = T_{i+1} / (1 - alpha_i) from final_T (no
@@ -345,25 +359,29 @@ int gs_loss(const float* img, const float* gt, const uint8_t* mask, int n_units,
  * reduced across each warp with shuffles, then across the tile in shared
  * memory, then added to `g2d` with one set of global atomics per (tile,
  * Gaussian).  g2d is zeroed by this call.
+ * dL_dT: NULL, or dL/dT_final [U][H][W] of a loss term on the final
+ * transmittance (gs_bg_penalty): since T_final = prod_k (1 - alpha_k) over
+ * the blended entries, every blended entry i of the pixel adds
+ * -dL_dT T_final / (1 - alpha_i) to dL/dalpha_i.
  * Projection backward: chain rule of a1 onto all parameters, summed over the
  * units containing each Gaussian; grads (planes layout) are overwritten.
  * variant, sched: as for gs_render_fwd.  With a schedule, each list is
  * replayed in chunks of sched->chunk entries by independent warps: a chunk
- * starts from the forward's checkpoint at its end (transmittance T and the
- * colour C accumulated in front of it; the colour behind is (img - C) / T).
- * img: the forward's image (read only with a schedule). */
+ * starts from the forward's checkpoint at its end (the transmittance there
+ * and the colour composited behind it per unit transmittance).
+ * img: the forward's image (required with a schedule). */
 int gs_render_bwd(const float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
                   const gs_camera* cams, const gs_proj* proj, const uint32_t* sorted_vals,
                   const uint32_t* ranges, int width, int height, const float* bg, const float* img,
                   const float* final_T, const uint32_t* n_contrib, const float* dL_dimg,
-                  const gs_grad2d* g2d, float* grads, int variant, const gs_schedule* sched,
-                  gs_stream_t stream);
+                  const float* dL_dT, const gs_grad2d* g2d, float* grads, int variant,
+                  const gs_schedule* sched, gs_stream_t stream);
 
 /* Blend backward only: g2d ([n_proj] records) is zeroed, then accumulated. */
 int gs_blend_bwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges,
                  int n_units, int width, int height, const float* bg, const float* img,
                  const float* final_T, const uint32_t* n_contrib, const float* dL_dimg,
-                 const gs_grad2d* g2d,
+                 const float* dL_dT, const gs_grad2d* g2d,
                  int64_t n_proj, int variant, const gs_schedule* sched, gs_stream_t stream);
 
 /* Projection backward only (grads overwritten). */
@@ -485,6 +503,10 @@ typedef struct gs_train_batch_desc {
   float* grads;                  /* parameter gradient (planes layout) or NULL */
   int32_t variant;               /* blend execution shape (gs_render_fwd) */
   int32_t sparse_adam;           /* gs_project_bwd_adam's sparse flag */
+  float lambda_bg;               /* > 0: add gs_bg_penalty with this weight (then the next three are needed) */
+  void* bg_ws;                   /* gs_bg_penalty_workspace_size(U) bytes */
+  size_t bg_ws_bytes;
+  float* dL_dT;                  /* [U][H][W] */
 } gs_train_batch_desc;
 
 int gs_train_batch(const gs_train_batch_desc* desc, int* d_status, gs_stream_t stream);

@@ -69,7 +69,9 @@ class GsTrainBatchDesc(C.Structure):
                 ("img", C.c_void_p), ("final_T", C.c_void_p), ("n_contrib", C.c_void_p), ("loss_ws", C.c_void_p),
                 ("loss_ws_bytes", C.c_size_t), ("d_loss", C.c_void_p), ("dL_dimg", C.c_void_p),
                 ("g2d", C.POINTER(GsGrad2d)), ("grads", C.c_void_p), ("variant", C.c_int32),
-                ("sparse_adam", C.c_int32)]
+                ("sparse_adam", C.c_int32),
+                ("lambda_bg", C.c_float), ("bg_ws", C.c_void_p), ("bg_ws_bytes", C.c_size_t),
+                ("dL_dT", C.c_void_p)]
 
 
 assert C.sizeof(GsCamera) == 96
@@ -103,9 +105,11 @@ SIGNATURES = {
     "gs_peak_issue": (I32, [I32, I32, I32, F32, F32, VP, VP]),
     "gs_loss": (I32, [VP, VP, VP, I32, I32, I32, F32, VP, SZ, VP, VP, VP]),
     "gs_render_bwd": (I32, [VP, I64, I32, C.POINTER(GsUnits), VP, C.POINTER(GsProj), VP, VP, I32, I32, c_f32p, VP,
-                            VP, VP, VP, C.POINTER(GsGrad2d), VP, I32, C.POINTER(GsSchedule), VP]),
-    "gs_blend_bwd": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, c_f32p, VP, VP, VP, VP, C.POINTER(GsGrad2d),
+                            VP, VP, VP, VP, C.POINTER(GsGrad2d), VP, I32, C.POINTER(GsSchedule), VP]),
+    "gs_blend_bwd": (I32, [C.POINTER(GsProj), VP, VP, I32, I32, I32, c_f32p, VP, VP, VP, VP, VP, C.POINTER(GsGrad2d),
                            I64, I32, C.POINTER(GsSchedule), VP]),
+    "gs_bg_penalty_workspace_size": (SZ, [I32]),
+    "gs_bg_penalty": (I32, [VP, VP, I32, I32, I32, F32, VP, SZ, VP, VP, VP]),
     "gs_project_bwd": (I32, [VP, I64, I32, C.POINTER(GsUnits), VP, C.POINTER(GsProj), C.POINTER(GsGrad2d), VP, VP]),
     "gs_adam_step": (I32, [VP, VP, VP, VP, I64, I32, c_f32p, c_f32p, I32, F32, F32, F32, VP, I32, VP, VP]),
     "gs_step_advance": (I32, [VP, VP]),

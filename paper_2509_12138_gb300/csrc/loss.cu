@@ -256,7 +256,76 @@ __global__ void k_loss_final(const uint32_t* msum, const double* l1sum, const do
   *out = (float)(acc / U);
 }
 
+// Background-opacity penalty (variant of the mask): per unit, the number of pixels outside the mask
+// and the sum of their rendered opacity 1 - T_final (one atomic per warp).
+__global__ void __launch_bounds__(256) k_bg_sum(const float* __restrict__ final_T, const uint8_t* __restrict__ mask,
+                                                int64_t plane, unsigned long long* __restrict__ cnt,
+                                                double* __restrict__ sum) {
+  int u = blockIdx.y;
+  const float* T = final_T + (int64_t)u * plane;
+  const uint8_t* m = mask + (int64_t)u * plane;
+  unsigned c = 0;
+  double a = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < plane; k += (int64_t)gridDim.x * blockDim.x)
+    if (m[k] == 0) { ++c; a += (double)(1.f - T[k]); }
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_down_sync(0xffffffffu, c, o);
+    a += __shfl_down_sync(0xffffffffu, a, o);
+  }
+  if ((threadIdx.x & 31) == 0 && c) {
+    atomicAdd(&cnt[u], (unsigned long long)c);
+    atomicAdd(&sum[u], a);
+  }
+}
+
+// dpenalty/dT_final: -lambda / (U n_bg) at the unit's background pixels, 0 at mask pixels
+__global__ void __launch_bounds__(256) k_bg_grad(const uint8_t* __restrict__ mask, int64_t plane,
+                                                 const unsigned long long* __restrict__ cnt, float lam, float invU,
+                                                 float* __restrict__ dLdT) {
+  int u = blockIdx.y;
+  unsigned long long n = cnt[u];
+  float g = n ? -lam * invU / (float)n : 0.f;
+  const uint8_t* m = mask + (int64_t)u * plane;
+  float* d = dLdT + (int64_t)u * plane;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < plane; k += (int64_t)gridDim.x * blockDim.x)
+    d[k] = m[k] == 0 ? g : 0.f;
+}
+
+__global__ void k_bg_final(const unsigned long long* cnt, const double* sum, int U, float lam, float* out) {
+  double acc = 0.0;
+  for (int u = 0; u < U; ++u)
+    if (cnt[u]) acc += sum[u] / (double)cnt[u];
+  *out += (float)(lam * acc / U);
+}
+
 }  // namespace
+
+GS_API size_t gs_bg_penalty_workspace_size(int n_units) {
+  if (n_units < 1) return 0;
+  return a256(sizeof(unsigned long long) * (size_t)n_units) + a256(sizeof(double) * (size_t)n_units);
+}
+
+GS_API int gs_bg_penalty(const float* final_T, const uint8_t* mask, int n_units, int width, int height,
+                         float lambda_bg, void* workspace, size_t workspace_bytes, float* d_loss, float* dL_dT,
+                         gs_stream_t stream) {
+  GS_RANGE("gs_bg_penalty");
+  if (!final_T || !mask || !d_loss || !dL_dT || !workspace || n_units < 1 || n_units > GS_MAX_UNITS || width <= 0 ||
+      height <= 0 || !(lambda_bg >= 0.f) || !isfinite(lambda_bg))
+    return GS_ERR_INVALID;
+  size_t need = gs_bg_penalty_workspace_size(n_units);
+  if (workspace_bytes < need || ((uintptr_t)workspace & 255u)) return GS_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* cnt = (unsigned long long*)workspace;
+  double* sum = (double*)((char*)workspace + a256(sizeof(unsigned long long) * (size_t)n_units));
+  if (cudaMemsetAsync(workspace, 0, need, s) != cudaSuccess) return GS_ERR_CUDA;
+  int64_t plane = (int64_t)width * height;
+  int gx = (int)((plane + 255) / 256);
+  if (gx > 1024) gx = 1024;
+  k_bg_sum<<<dim3(gx, n_units), 256, 0, s>>>(final_T, mask, plane, cnt, sum);
+  k_bg_grad<<<dim3(gx, n_units), 256, 0, s>>>(mask, plane, cnt, lambda_bg, 1.f / n_units, dL_dT);
+  k_bg_final<<<1, 1, 0, s>>>(cnt, sum, n_units, lambda_bg, d_loss);
+  return gs_check_launch();
+}
 
 GS_API size_t gs_loss_workspace_size(int n_units, int width, int height) {
   if (n_units < 1 || width <= 0 || height <= 0) return 0;
@@ -299,30 +368,30 @@ GS_API int gs_loss(const float* img, const float* gt, const uint8_t* mask, int n
 // ---- backward entry points (blend + projection)
 int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
                       int width, int height, const float* bg, const float* final_T, const uint32_t* n_contrib,
-                      const float* dL_dimg, const gs_grad2d* g2d, int64_t n_proj, int variant,
+                      const float* dL_dimg, const float* dL_dT, const gs_grad2d* g2d, int64_t n_proj, int variant,
                       const gs_schedule* sched, const float* img, cudaStream_t s);
 
 GS_API int gs_blend_bwd(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
                         int width, int height, const float* bg, const float* img, const float* final_T,
-                        const uint32_t* n_contrib, const float* dL_dimg, const gs_grad2d* g2d, int64_t n_proj,
-                        int variant, const gs_schedule* sched, gs_stream_t stream) {
+                        const uint32_t* n_contrib, const float* dL_dimg, const float* dL_dT, const gs_grad2d* g2d,
+                        int64_t n_proj, int variant, const gs_schedule* sched, gs_stream_t stream) {
   GS_RANGE("gs_blend_bwd");
   return gs_blend_bwd_impl(proj, sorted_vals, ranges, n_units, width, height, bg, final_T, n_contrib, dL_dimg,
-                           g2d, n_proj, variant, sched, img, (cudaStream_t)stream);
+                           dL_dT, g2d, n_proj, variant, sched, img, (cudaStream_t)stream);
 }
 
 GS_API int gs_render_bwd(const float* params, int64_t n_gauss, int sh_degree, const gs_units* units,
                          const gs_camera* cams, const gs_proj* proj, const uint32_t* sorted_vals,
                          const uint32_t* ranges, int width, int height, const float* bg, const float* img,
                          const float* final_T, const uint32_t* n_contrib, const float* dL_dimg,
-                         const gs_grad2d* g2d, float* grads, int variant, const gs_schedule* sched,
-                         gs_stream_t stream) {
+                         const float* dL_dT, const gs_grad2d* g2d, float* grads, int variant,
+                         const gs_schedule* sched, gs_stream_t stream) {
   GS_RANGE("gs_render_bwd");
   UnitTable U;
   int64_t P = 0;
   if (gs_fill_units(units, U, &P) != GS_OK) return GS_ERR_INVALID;
-  int r = gs_blend_bwd_impl(proj, sorted_vals, ranges, U.n, width, height, bg, final_T, n_contrib, dL_dimg, g2d, P,
-                            variant, sched, img, (cudaStream_t)stream);
+  int r = gs_blend_bwd_impl(proj, sorted_vals, ranges, U.n, width, height, bg, final_T, n_contrib, dL_dimg, dL_dT,
+                            g2d, P, variant, sched, img, (cudaStream_t)stream);
   if (r != GS_OK) return r;
   return gs_project_bwd(params, n_gauss, sh_degree, units, cams, proj, g2d, grads, stream);
 }

@@ -219,7 +219,8 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict
                                                          int n_tiles, float bg0, float bg1, float bg2,
                                                          const float* __restrict__ final_T,
                                                          const uint32_t* __restrict__ n_contrib,
-                                                         const float* __restrict__ dimg, float* __restrict__ dxy,
+                                                         const float* __restrict__ dimg,
+                                                         const float* __restrict__ dLdT, float* __restrict__ dxy,
                                                          float* __restrict__ dco, float* __restrict__ drgb,
                                                            unsigned long long* __restrict__ fixed) {
   const unsigned FULL = 0xffffffffu;
@@ -237,12 +238,14 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict
   int64_t plane = (int64_t)W * H;
   int64_t pix = (int64_t)py * W + px;
   float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+  float qT = 0.f;  // dL/dT_final x T_final: a blended entry adds -qT / (1 - alpha) to dL/dalpha
   int last = 0;
   if (inside) {
     T = final_T[(int64_t)u * plane + pix];
     last = (int)n_contrib[(int64_t)u * plane + pix];
     const float* d = dimg + (int64_t)u * 3 * plane;
     g0 = d[pix]; g1 = d[plane + pix]; g2 = d[2 * plane + pix];
+    if (dLdT) qT = dLdT[(int64_t)u * plane + pix] * T;
   }
   int n = min(__reduce_max_sync(FULL, last), (int)(rg.y - rg.x));
   float S0 = bg0, S1 = bg1, S2 = bg2;  // colour behind the current entry
@@ -295,6 +298,7 @@ __global__ void __launch_bounds__(TILE_PIX) k_render_bwd(const uint2* __restrict
             float wgt = alpha * T;
             v[6] = wgt * g0; v[7] = wgt * g1; v[8] = wgt * g2;
             float dalpha = T * ((rc.x - S0) * g0 + (rc.y - S1) * g1 + (rc.z - S2) * g2);
+            if (qT != 0.f) dalpha -= __fdividef(qT, 1.f - alpha);
             S0 = alpha * rc.x + (1.f - alpha) * S0;
             S1 = alpha * rc.y + (1.f - alpha) * S1;
             S2 = alpha * rc.z + (1.f - alpha) * S2;
@@ -1024,7 +1028,8 @@ __global__ void __launch_bounds__(32, 32) k_render_bwd_m(const uint2* __restrict
                                                            const float* __restrict__ img,
                                                            const float* __restrict__ final_T,
                                                            const uint32_t* __restrict__ n_contrib,
-                                                           const float* __restrict__ dimg, float* __restrict__ dxy,
+                                                           const float* __restrict__ dimg,
+                                                           const float* __restrict__ dLdT, float* __restrict__ dxy,
                                                            float* __restrict__ dco, float* __restrict__ drgb,
                                                            unsigned long long* __restrict__ fixed,
     uint32_t* __restrict__ ticket) {
@@ -1055,11 +1060,13 @@ __global__ void __launch_bounds__(32, 32) k_render_bwd_m(const uint2* __restrict
     int64_t plane = (int64_t)W * H;
     int64_t pix = (int64_t)py * W + px;
     float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, S0 = bg0, S1 = bg1, S2 = bg2;
+    float qT = 0.f;  // dL/dT_final x T_final: a blended entry adds -qT / (1 - alpha) to dL/dalpha
     int last = 0;
     if (inside) {
       last = (int)n_contrib[(int64_t)u * plane + pix];
       const float* d = dimg + (int64_t)u * 3 * plane;
       g0 = d[pix]; g1 = d[plane + pix]; g2 = d[2 * plane + pix];
+      if (dLdT) qT = dLdT[(int64_t)u * plane + pix] * final_T[(int64_t)u * plane + pix];
       if (ch + 1 < nch && last > cbeg) {
         // the forward's checkpoint at the chunk's end: T there and the colour behind it per unit T
         int pix_local = (py - ty * TILE) * TILE + (px - tx * TILE);
@@ -1145,6 +1152,7 @@ __global__ void __launch_bounds__(32, 32) k_render_bwd_m(const uint2* __restrict
                 float wgt = alpha * T;
                 v6 = wgt * g0; v7 = wgt * g1; v8 = wgt * g2;
                 float dalpha = T * ((rc.x - S0) * g0 + (rc.y - S1) * g1 + (rc.z - S2) * g2);
+                if (qT != 0.f) dalpha -= __fdividef(qT, 1.f - alpha);
                 S0 = alpha * rc.x + (1.f - alpha) * S0;
                 S1 = alpha * rc.y + (1.f - alpha) * S1;
                 S2 = alpha * rc.z + (1.f - alpha) * S2;
@@ -1195,6 +1203,7 @@ __global__ void __launch_bounds__(32, 32) k_render_bwd_m(const uint2* __restrict
               float wgt = alpha * T;
               v6 = wgt * g0; v7 = wgt * g1; v8 = wgt * g2;
               float dalpha = T * ((rc.x - S0) * g0 + (rc.y - S1) * g1 + (rc.z - S2) * g2);
+              if (qT != 0.f) dalpha -= __fdividef(qT, 1.f - alpha);
               S0 = alpha * rc.x + (1.f - alpha) * S0;
               S1 = alpha * rc.y + (1.f - alpha) * S1;
               S2 = alpha * rc.z + (1.f - alpha) * S2;
@@ -1444,7 +1453,7 @@ GS_API int gs_render_fwd(const gs_proj* proj, const uint32_t* sorted_vals, const
 
 int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const uint32_t* ranges, int n_units,
                       int width, int height, const float* bg, const float* final_T, const uint32_t* n_contrib,
-                      const float* dL_dimg, const gs_grad2d* g2d, int64_t n_proj, int variant,
+                      const float* dL_dimg, const float* dL_dT, const gs_grad2d* g2d, int64_t n_proj, int variant,
                       const gs_schedule* sched, const float* img, cudaStream_t s) {
   if (!proj || !proj->xy || !proj->conic_op || !proj->rgb || !sorted_vals || !ranges || !bg || !final_T ||
       !n_contrib || !dL_dimg || !g2d || !g2d->dxy || !g2d->dconic_op || !g2d->drgb || n_units < 1 || (sched && !img) ||
@@ -1471,13 +1480,14 @@ int gs_blend_bwd_impl(const gs_proj* proj, const uint32_t* sorted_vals, const ui
           (const float4*)sched->checkpoints, sorted_vals, sched->block_masks, (const float4*)proj->xy,               \
           (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height, TX, TX * TY, TX * TY * n_units,   \
           bg[0], bg[1], bg[2],                                                                                       \
-          img, final_T, n_contrib, dL_dimg, g2d->dxy, g2d->dconic_op, g2d->drgb, fixed, sched_ticket(sched));        \
+          img, final_T, n_contrib, dL_dimg, dL_dT, g2d->dxy, g2d->dconic_op, g2d->drgb, fixed,                       \
+          sched_ticket(sched));                                                                                      \
     }                                                                                                              \
   else                                                                                                               \
     k_render_bwd<BW><<<grid, TILE_PIX, 0, s>>>((const uint2*)ranges, nullptr, sorted_vals, (const float4*)proj->xy, \
                                                (const float4*)proj->conic_op, (const float4*)proj->rgb, width, height,  \
-                                               TX, TX * TY, bg[0], bg[1], bg[2], final_T, n_contrib, dL_dimg, g2d->dxy, \
-                                               g2d->dconic_op, g2d->drgb, fixed)
+                                               TX, TX * TY, bg[0], bg[1], bg[2], final_T, n_contrib, dL_dimg, dL_dT,    \
+                                               g2d->dxy, g2d->dconic_op, g2d->drgb, fixed)
   if (variant == 0) { GS_BWD(8); } else if (variant == 1) { GS_BWD(16); } else { GS_BWD(4); }
 #undef GS_BWD
   if (fixed && n_proj > 0)

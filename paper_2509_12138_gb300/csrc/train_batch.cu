@@ -105,10 +105,15 @@ GS_API int gs_train_batch(const gs_train_batch_desc* d, int* d_status, gs_stream
   if ((r = gs_loss(d->img, d->gt_step, d->mask_step, U, d->width, d->height, d->lambda_ssim, d->loss_ws,
                    d->loss_ws_bytes, d->d_loss, d->dL_dimg, stream)) != GS_OK)
     return r;
+  const bool pen = d->lambda_bg > 0.f;
+  if (pen && (r = gs_bg_penalty(d->final_T, d->mask_step, U, d->width, d->height, d->lambda_bg, d->bg_ws,
+                                d->bg_ws_bytes, d->d_loss, d->dL_dT, stream)) != GS_OK)
+    return r;
   int64_t P = 0;
   for (int u = 0; u < U; ++u) P += d->units->gauss_count[u];
   if ((r = gs_blend_bwd(d->proj, d->sorted_vals, d->ranges, U, d->width, d->height, d->bg, d->img, d->final_T,
-                        d->n_contrib, d->dL_dimg, d->g2d, P, d->variant, d->sched, stream)) != GS_OK)
+                        d->n_contrib, d->dL_dimg, pen ? d->dL_dT : nullptr, d->g2d, P, d->variant, d->sched,
+                        stream)) != GS_OK)
     return r;
   if ((r = gs_project_bwd_adam(d->params, d->n_gauss, d->sh_degree, d->units, d->cams_step, d->proj, d->g2d,
                                d->adam_m, d->adam_v, d->lr_init, d->lr_final, d->lr_steps, d->beta1, d->beta2, d->eps,

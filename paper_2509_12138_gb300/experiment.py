@@ -166,11 +166,13 @@ def seam_band(scene, delta: float, device="cuda"):
 
 def ghost_ablation(slab_counts, n_modes: int, n_views: int, W: int, H: int, steps: int, n_parts: int = 4,
                    ghost: float = 0.05, sh_degree: int = 1, delta: float = 0.01, device="cuda",
-                   init_scale: float = 1.0):
+                   init_scale: float = 1.0, lambda_bg: float = 0.0):
     """Ghost cells and masks on and off (Sec. II): each configuration trains every partition on its own
     GT (graph-captured batched trainer, one view per partition per step), merges with the ghost filter and
     is scored on held-out views against the whole scene's GT: PSNR over the covered pixels and over the
-    seam band (pixels whose surface lies within `delta` of a slab boundary)."""
+    seam band (pixels whose surface lies within `delta` of a slab boundary).  lambda_bg > 0 adds the mask
+    variant "mask=on+bg": the masked loss plus the background-opacity penalty of that weight (the mean
+    rendered opacity over the pixels outside the mask, gs_bg_penalty)."""
     from .raster import Frame, Owned, Units
     from .workload import partitioned_scene
     out = {}
@@ -182,11 +184,12 @@ def ghost_ablation(slab_counts, n_modes: int, n_views: int, W: int, H: int, step
         if band is None:
             band = seam_band(ps, delta, device)
         train_v, test_v = split_views(n_views)
-        for use_mask in (True, False):
+        modes = [("on", True, 0.0), ("off", False, 0.0)] + ([("on+bg", True, lambda_bg)] if lambda_bg > 0 else [])
+        for mode, use_mask, lam_bg in modes:
             masks = ps.mask if use_mask else torch.ones_like(ps.mask)
             params = pack_params(ps.init, sh_degree, device)
             tr = BatchedTrainer(params, sh_degree, ps.offsets, ps.cams_dev, ps.gt, masks, train_v, views_per_step=1,
-                                lr_steps=steps)
+                                lr_steps=steps, lambda_bg=lam_bg)
             t0 = time.perf_counter()
             for _ in range(steps):
                 tr.step()
@@ -204,7 +207,7 @@ def ghost_ablation(slab_counts, n_modes: int, n_views: int, W: int, H: int, step
                 img = fr.merge_render(params, cam, ps.bg, owned)[0]
                 all_p.append(psnr(img, ps.gt_full[v], ps.mask_full[v]))
                 band_p.append(psnr(img, ps.gt_full[v], band[v]))
-            key = f"ghost={'on' if use_ghost else 'off'},mask={'on' if use_mask else 'off'}"
+            key = f"ghost={'on' if use_ghost else 'off'},mask={mode}"
             out[key] = {"psnr_covered": round(float(np.nanmean(all_p)), 3),
                         "psnr_seam_band": round(float(np.nanmean(band_p)), 3),
                         "train_seconds": round(secs, 3),

@@ -179,6 +179,7 @@ class Frame:
             self.loss_ws = _alloc_ws(self.L.gs_loss_workspace_size(U, self.W, self.H), self.device)
             self.loss_val = torch.zeros(1, **f32)
             self.dimg = torch.zeros((U, 3, self.H, self.W), **f32)
+        self.dL_dT = None  # dpenalty/dT_final of the background-opacity penalty (made by bg_penalty)
         if with_backward:
             self.dxy = torch.zeros((max(P, 1), 2), **f32)
             self.dco = torch.zeros((max(P, 1), 4), **f32)
@@ -266,12 +267,24 @@ class Frame:
                              _stream()), "gs_loss")
         return self.loss_val
 
-    def blend_backward(self, bg, dimg: torch.Tensor | None = None):
+    def bg_penalty(self, mask: torch.Tensor, lam: float) -> torch.Tensor:
+        """Background-opacity penalty (gs_bg_penalty): adds lam x the mean rendered opacity outside the mask
+        to the loss value and returns dpenalty/dT_final, the dT input of the backward calls."""
+        if self.dL_dT is None:
+            self.dL_dT = torch.zeros((self.units.n, self.H, self.W), dtype=torch.float32, device=self.device)
+            self.bg_ws = _alloc_ws(self.L.gs_bg_penalty_workspace_size(self.units.n), self.device)
+        check(self.L.gs_bg_penalty(_ptr(self.final_T), _ptr(mask), self.units.n, self.W, self.H, float(lam),
+                                   _ptr(self.bg_ws), self.bg_ws.numel(), _ptr(self.loss_val), _ptr(self.dL_dT),
+                                   _stream()), "gs_bg_penalty")
+        return self.dL_dT
+
+    def blend_backward(self, bg, dimg: torch.Tensor | None = None, dT: torch.Tensor | None = None):
         bgc = (C.c_float * 3)(*[float(x) for x in bg])
         d = self.dimg if dimg is None else dimg
         check(self.L.gs_blend_bwd(C.byref(self.proj), _ptr(self.sorted_vals), _ptr(self.ranges), self.units.n,
                                   self.W, self.H, bgc, _ptr(self.img), _ptr(self.final_T), _ptr(self.n_contrib),
-                                  _ptr(d), C.byref(self.g2d), self.P, self.variant, self._sched(), _stream()),
+                                  _ptr(d), _ptr(dT), C.byref(self.g2d), self.P, self.variant, self._sched(),
+                                  _stream()),
               "gs_blend_bwd")
 
     def project_backward(self, params, cams_dev):
@@ -280,13 +293,14 @@ class Frame:
               "gs_project_bwd")
         return self.grads
 
-    def backward(self, params, cams_dev, bg, dimg: torch.Tensor | None = None):
+    def backward(self, params, cams_dev, bg, dimg: torch.Tensor | None = None, dT: torch.Tensor | None = None):
         bgc = (C.c_float * 3)(*[float(x) for x in bg])
         d = self.dimg if dimg is None else dimg
         check(self.L.gs_render_bwd(_ptr(params), self.N, self.deg, C.byref(self.units.struct), _ptr(cams_dev),
                                    C.byref(self.proj), _ptr(self.sorted_vals), _ptr(self.ranges), self.W, self.H,
                                    bgc, _ptr(self.img), _ptr(self.final_T), _ptr(self.n_contrib), _ptr(d),
-                                   C.byref(self.g2d), _ptr(self.grads), self.variant, self._sched(), _stream()),
+                                   _ptr(dT), C.byref(self.g2d), _ptr(self.grads), self.variant, self._sched(),
+                                   _stream()),
               "gs_render_bwd")
         return self.grads
 

@@ -19,9 +19,9 @@ import torch
 
 import ctypes as C
 
-from . import _lib
+from . import _lib, checkpoint
 from ._lib import GsTrainBatchDesc, check
-from .raster import CHUNK, Adam, Frame, LearningRates, Owned, Units, _ptr, _stream, pack_cameras
+from .raster import CHUNK, Adam, Frame, LearningRates, Owned, Units, _alloc_ws, _ptr, _stream, pack_cameras
 
 CAM_BYTES = 96
 
@@ -109,6 +109,14 @@ class PlainTrainer:
                              "max_radius": d.max_radius.clone(), "gen": d.gen.get_state()}
         return st
 
+    def save(self, path: str):
+        """Write the checkpoint (state_dict) to a file in the on-disk format of checkpoint.py."""
+        checkpoint.save(path, self.state_dict(), self.params.shape[1], self.deg, int(self.opt.step_dev.item()))
+
+    def load(self, path: str):
+        """Resume from a file written by save()."""
+        self.load_state_dict(checkpoint.load(path, self.params.device)[0])
+
     def load_state_dict(self, st: dict):
         if st["params"].shape != self.params.shape:  # densification changed the count: new planes, new frame
             p = st["params"].clone()
@@ -187,8 +195,10 @@ class BatchedTrainer:
                  mask: torch.Tensor, train_views, views_per_step: int = 1, lrs: LearningRates | None = None,
                  extent: float = 1.0, lr_steps: int = 7000, lam: float = 0.2, bg=(1.0, 1.0, 1.0), variant: int = 0,
                  use_graph: bool = True, capacity_slack: float = 1.5, deterministic: bool = False,
-                 chunk: int = CHUNK):
+                 chunk: int = CHUNK, lambda_bg: float = 0.0):
+        """lambda_bg > 0 adds the background-opacity penalty (gs_bg_penalty) to every unit's loss."""
         self.params = params
+        self.lambda_bg = float(lambda_bg)
         self.deg = sh_degree
         self.off = np.asarray(part_offsets, np.int64)
         self.n_parts = len(self.off) - 1
@@ -261,6 +271,12 @@ class BatchedTrainer:
         d.grads = fr.grads.data_ptr() if self.keep_grads else None
         d.variant = fr.variant
         d.sparse_adam = int(opt.sparse)
+        if self.lambda_bg > 0.0:
+            if fr.dL_dT is None:
+                fr.dL_dT = torch.zeros((self.units.n, H, W), dtype=torch.float32, device=self.params.device)
+                fr.bg_ws = _alloc_ws(self.L.gs_bg_penalty_workspace_size(self.units.n), self.params.device)
+            d.lambda_bg, d.bg_ws, d.bg_ws_bytes = self.lambda_bg, fr.bg_ws.data_ptr(), fr.bg_ws.numel()
+            d.dL_dT = fr.dL_dT.data_ptr()
         self.desc = d
         self._desc_key = (fr.cap, self.keep_grads, fr.use_masks, fr.walk_whole_lists, opt.sparse)
 
@@ -306,6 +322,14 @@ class BatchedTrainer:
     def state_dict(self) -> dict:
         """Checkpoint: parameters, optimiser state and step count (copies); views follow from the step."""
         return {"params": self.params.clone(), "opt": self.opt.state_dict(), "t": self.t}
+
+    def save(self, path: str):
+        """Write the checkpoint (state_dict) to a file in the on-disk format of checkpoint.py."""
+        checkpoint.save(path, self.state_dict(), self.params.shape[1], self.deg, int(self.opt.step_dev.item()))
+
+    def load(self, path: str):
+        """Resume from a file written by save()."""
+        self.load_state_dict(checkpoint.load(path, self.params.device)[0])
 
     def load_state_dict(self, st: dict):
         """Restore a checkpoint in place (the captured graph reads the same buffers, so it stays valid)."""

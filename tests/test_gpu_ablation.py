@@ -3,7 +3,8 @@
 Two x-slab partitions of the interface, 8 views at 192x108, 200 batched steps per configuration: every
 configuration trains, merges with the ghost filter and scores the held-out views; ghost layers add
 Gaussians that the merge then drops; the seam band is a non-empty part of the covered pixels; the merged
-render of every configuration reaches more than 20 dB against the whole scene's GT."""
+render of every configuration (including the masked loss with the background-opacity penalty) reaches more
+than 20 dB against the whole scene's GT."""
 import math
 
 import pytest
@@ -14,8 +15,10 @@ pytestmark = pytest.mark.gpu
 
 
 def test_ghost_mask_ablation_small():
-    res = X.ghost_ablation([10_000, 10_000], 4, 8, 192, 108, 200, n_parts=2, ghost=0.05, sh_degree=0, delta=0.01)
-    keys = ["ghost=on,mask=on", "ghost=on,mask=off", "ghost=off,mask=on", "ghost=off,mask=off"]
+    res = X.ghost_ablation([10_000, 10_000], 4, 8, 192, 108, 200, n_parts=2, ghost=0.05, sh_degree=0, delta=0.01,
+                           lambda_bg=0.1)
+    keys = ["ghost=on,mask=on", "ghost=on,mask=off", "ghost=off,mask=on", "ghost=off,mask=off",
+            "ghost=on,mask=on+bg", "ghost=off,mask=on+bg"]
     for k in keys:
         r = res[k]
         assert math.isfinite(r["psnr_covered"]) and r["psnr_covered"] > 20.0, (k, r)

@@ -372,3 +372,44 @@ def test_stops_hundreds_of_chunks_deep(whole):
     assert torch.allclose(a[3], b[3], rtol=1e-4, atol=1e-7)
     sc = float(a[2].abs().max())
     assert torch.allclose(a[2], b[2], rtol=1e-3, atol=1e-5 * sc)
+
+
+def test_train_batch_with_bg_penalty_matches_oracle_per_unit():
+    """gs_train_batch with the background-opacity penalty (lambda_bg > 0): the loss and the parameter gradient
+    of the first step equal the oracle's masked loss plus penalty, per unit, averaged over the 3 x 2 units."""
+    import ctypes as C
+    from paper_2509_12138_gb300 import _lib
+    init, part, cams, gt, mask = _partitioned(seed=5)
+    deg, lam_bg = 1, 0.3
+    params = gs.pack_params(init, deg)
+    tr = T.BatchedTrainer(params, deg, part.offsets, gs.pack_cameras(cams), torch.from_numpy(gt).cuda(),
+                          torch.from_numpy(mask).cuda(), list(range(1, 6)), views_per_step=2, use_graph=False,
+                          lambda_bg=lam_bg)
+    tr.keep_grads = True
+    tr._build_desc()
+    L = _lib.load()
+    p0 = gs.unpack_params(params, deg)
+    rc = L.gs_train_batch(C.byref(tr.desc), C.c_void_p(tr.frame.status.data_ptr()),
+                          C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert tr.frame.read_status() == 0
+    U = tr.units.n
+    grads = gs.unpack_grads(tr.frame.grads, deg)
+    ref_loss, ref_grad, pen = 0.0, np.zeros_like(grads), 0.0
+    for k in range(part.n):
+        s_, e_ = part.offsets[k], part.offsets[k + 1]
+        sub = gauss64(_subset(p0, np.arange(s_, e_)))
+        for j in range(2):
+            v = tr.view_of(0, k, j)
+            cam = oracle.camera_block(cams, v)
+            r = oracle.render(sub, cam, BG)
+            lv, dimg = oracle.loss(r["img"], gt[k, v].astype(np.float64), mask[k, v], 0.2)
+            pv, dT = oracle.bg_penalty(r["final_T"], mask[k, v], lam_bg)
+            g2d = oracle.render_backward(sub, cam, BG, dimg, dT)
+            ref_loss += (lv + pv) / U
+            pen += pv / U
+            ref_grad[s_:e_] += oracle.project_backward(sub, cam, g2d) / U
+    assert pen > 1e-3 * ref_loss
+    assert float(tr.frame.loss_val.item()) == pytest.approx(ref_loss, rel=1e-4)
+    assert np.abs(grads - ref_grad).max() <= 1e-3 * np.abs(ref_grad).max()

@@ -65,7 +65,10 @@ def _small_scene():
     return workload.isosurface_scene(30000, 4, 8, 128, 96, sh_degree=1, seed=5)
 
 
-def test_checkpoint_resume_is_bitwise_identical():
+@pytest.mark.parametrize("on_disk", [False, True])
+def test_checkpoint_resume_is_bitwise_identical(on_disk, tmp_path):
+    """A run resumed from a checkpoint (in memory, or through the on-disk file format) continues bit for bit
+    like the uninterrupted run."""
     scene = _small_scene()
     train_v, _ = split_views(len(scene.cams))
 
@@ -80,9 +83,14 @@ def test_checkpoint_resume_is_bitwise_identical():
     b = trainer()
     for _ in range(3):
         b.step()
-    ck = b.state_dict()
     c = trainer()  # a fresh process would start here from the checkpoint
-    c.load_state_dict(ck)
+    if on_disk:
+        path = str(tmp_path / "resume.ckpt")
+        b.save(path)
+        del b
+        c.load(path)
+    else:
+        c.load_state_dict(b.state_dict())
     for _ in range(3):
         c.step()
     torch.cuda.synchronize()

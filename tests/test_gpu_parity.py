@@ -518,3 +518,44 @@ def test_fused_next_projection_two_units():
         assert torch.equal(a[k], b[k]), k
     for k in ("xy", "conic_op", "rgb"):
         assert torch.equal(a[k][vis], b[k][vis]), k
+
+
+@pytest.mark.parametrize("sched,det", [(True, False), (False, False), (True, True)])
+def test_bg_penalty_parity(sched, det):
+    """Masked loss plus the background-opacity penalty (gs_bg_penalty): the loss value, dL/dT_final and every
+    parameter gradient through the reverse replay (scheduled or plain kernels, float or fixed-point
+    accumulation) against the oracle's penalty and its reverse replay with dL/dT_final."""
+    import paper_2509_12138_gb300 as gsp
+    n, deg, W, H, seed, lam, lam_bg = 1500, 2, 120, 90, 41, 0.2, 0.5
+    g, cams = _case(n, deg, seed, W, H, ls=(-3.0, -1.8))
+    gt, mask = scenes.random_gt(W, H, seed + 50)
+    fr = gsp.Frame(n, gsp.Units.single(n), W, H, deg, deterministic=det)
+    fr.use_masks = sched
+    params = gsp.pack_params(g, deg)
+    camd = gsp.pack_cameras(cams)
+    fr.fit_capacity(params, camd)
+    fr.forward(params, camd, BG)
+    fr.loss(torch.from_numpy(gt).cuda(), torch.from_numpy(mask).cuda(), lam)
+    dT = fr.bg_penalty(torch.from_numpy(mask).cuda(), lam_bg)
+    fr.backward(params, camd, BG, dT=dT)
+    torch.cuda.synchronize()
+    assert fr.read_status() == 0
+    cam = oracle.camera_block(cams, 0)
+    g64 = gauss64(g)
+    r = oracle.render(g64, cam, BG)
+    lval, dimg = oracle.loss(r["img"], gt.astype(np.float64), mask, lam)
+    pval, dTo = oracle.bg_penalty(r["final_T"], mask, lam_bg)
+    assert pval > 0.0
+    assert float(fr.loss_val.item()) == pytest.approx(lval + pval, rel=1e-4)
+    assert np.allclose(dT.cpu().numpy()[0], dTo, rtol=1e-6, atol=0.0)
+    g2o = oracle.render_backward(g64, cam, BG, dimg, dTo)
+    go = oracle.project_backward(g64, cam, g2o)
+    vis = fr.radius.cpu().numpy() > 0
+    dco = fr.dco.cpu().numpy()
+    for a, b in [(fr.dxy.cpu().numpy(), g2o["dxy"]), (dco[:, :3], g2o["dconic"]), (dco[:, 3], g2o["dopacity"])]:
+        assert np.abs(a[vis] - b[vis]).max() <= GRAD_TOL * np.abs(b).max()
+    _group_check(gsp.unpack_grads(fr.grads, deg), go, deg)
+    # the penalty's share of the opacity gradient is material (the check above is not the loss alone)
+    g2l = oracle.render_backward(g64, cam, BG, dimg)
+    diff = np.abs(g2o["dopacity"] - g2l["dopacity"]).max()
+    assert diff > 0.05 * np.abs(g2o["dopacity"]).max()
