@@ -691,7 +691,7 @@ struct NextProj {
 };
 
 constexpr int PBA_T = 64;  // Gaussians per block of the staged kernel
-constexpr int PBA_R = 4;   // moment planes (m and v) in flight per thread
+constexpr int PBA_R = 6;   // moment planes (m and v) in flight per thread (7 or more: 210 registers)
 
 // Projection backward fused with Adam for Gaussians that belong to exactly
 // one unit (one view of one partition).  On entry every thread starts async

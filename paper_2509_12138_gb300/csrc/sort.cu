@@ -466,28 +466,39 @@ __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ k0,
 // (unit, tile) with a stable sort on 32-bit keys (block mask << 16 | unit | tile).  Stability makes
 // each list come out in (depth, record index) order, the order of the global key sort.
 
-// visible records (tiles > 0) per 2048-record scan block
-__global__ void __launch_bounds__(SCAN_T) k_vis_reduce(const uint32_t* __restrict__ tiles, int64_t P,
-                                                       uint32_t* __restrict__ bsums) {
+// visible records (tiles > 0) per 2048-record scan block, and the smallest depth key among them
+// (*dmin: float32 depth bits, which order as unsigned integers for positive depths; set to all ones
+// before the launch)
+__global__ void __launch_bounds__(SCAN_T) k_vis_reduce(const uint32_t* __restrict__ tiles,
+                                                       const float* __restrict__ depth, int64_t P,
+                                                       uint32_t* __restrict__ bsums, uint32_t* __restrict__ dmin) {
   __shared__ uint32_t s_warp[33];
   int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK;
-  uint32_t s = 0;
+  uint32_t s = 0, mn = 0xffffffffu;
   #pragma unroll
   for (int j = 0; j < SCAN_ITEMS; ++j) {
     int64_t k = base + (int64_t)j * SCAN_T + threadIdx.x;
-    if (k < P && tiles[k] > 0u) ++s;
+    if (k < P && tiles[k] > 0u) {
+      ++s;
+      mn = min(mn, __float_as_uint(depth[k]));
+    }
   }
+  mn = __reduce_min_sync(0xffffffffu, mn);
+  if ((threadIdx.x & 31) == 0 && mn != 0xffffffffu) atomicMin(dmin, mn);
   uint32_t tot;
   block_excl_scan(s, s_warp, &tot);
   if (threadIdx.x == 0) bsums[blockIdx.x] = tot;
 }
 
-// compaction in record order: (depth bits, record index) of every visible record; *d_vis = their number.
+// compaction in record order: (depth bits - *dmin, record index) of every visible record; *d_vis = their
+// number.  Keys relative to the nearest visible depth keep the order and leave the top bits zero: the
+// depths of one view span far fewer than 2^32 float32 steps.
 // Round j of a block covers its records [256 j, 256 j + 256) (coalesced loads); a record's slot is the
 // block's base, the visible records of earlier (round, warp) pairs and those of lower lanes.
 __global__ void __launch_bounds__(SCAN_T) k_vis_compact(const uint32_t* __restrict__ tiles,
                                                         const float* __restrict__ depth, int64_t P,
                                                         const uint32_t* __restrict__ bsums, int64_t nb,
+                                                        const uint32_t* __restrict__ dmin,
                                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                         uint32_t* __restrict__ d_vis) {
   constexpr int NW = SCAN_T / 32;
@@ -511,13 +522,14 @@ __global__ void __launch_bounds__(SCAN_T) k_vis_compact(const uint32_t* __restri
   }
   __syncthreads();
   uint32_t c0 = bsums[blockIdx.x];
+  const uint32_t d0 = *dmin;
   uint32_t lt = (1u << lane) - 1u;
   #pragma unroll
   for (int j = 0; j < SCAN_ITEMS; ++j)
     if (bal[j] >> lane & 1u) {
       int64_t k = base + (int64_t)j * SCAN_T + threadIdx.x;
       uint32_t c = c0 + s_cnt[j * NW + w] + __popc(bal[j] & lt);
-      keys[c] = __float_as_uint(depth[k]);
+      keys[c] = __float_as_uint(depth[k]) - d0;
       vals[c] = (uint32_t)k;
     }
   if (blockIdx.x == 0 && threadIdx.x == 0) *d_vis = bsums[nb];
@@ -552,7 +564,7 @@ __global__ void __launch_bounds__(SCAN_T) k_dup_reduce(const uint32_t* __restric
 // instances of its records that fall in the window, so a window costs O(its instances + 8) per thread).
 // Block 0 also writes the instance count (clamped to the capacity, GS_ERR_CAPACITY beyond it).
 constexpr int EMIT_WIN = 4096;
-__global__ void __launch_bounds__(SCAN_T) k_dup_emit(UnitTable U, const float4* __restrict__ xy,
+__global__ void __launch_bounds__(SCAN_T, 3) k_dup_emit(UnitTable U, const float4* __restrict__ xy,
                                                      const float4* __restrict__ conic_op,
                                                      const int* __restrict__ radius, const uint32_t* __restrict__ vA,
                                                      const uint32_t* __restrict__ vB, const int32_t* __restrict__ cur,
@@ -758,7 +770,10 @@ int gs_seg_sort(const UnitTable& U, int64_t P, const gs_proj* proj, int width, i
                 uint32_t* sorted_vals, uint32_t* ranges, uint16_t* masks, cudaStream_t s);
 
 // The depth-first design (method 2): compact the visible records in record order, sort them by their
-// 32-bit depth keys (stable 8-bit passes; a pass whose digit all keys share is skipped), scan their
+// 32-bit depth keys taken relative to the nearest visible depth (three stable 9-bit passes over bits
+// 0-26, then a pass over bits 27-31 that the device skips when every key is below 2^27, as it is when the
+// view's depths stay within a factor of ~2^16 of each other; any pass whose digit all keys share is
+// skipped), scan their
 // instance counts in that order, emit one 32-bit (mask | unit | tile) key per instance, sort those
 // stably on the unit | tile bits (ut_bits <= 16: one or two 8-bit passes) and read off the lists.
 // Buffers: the record pairs ping-pong between keys0 (keys at word 0, ids at word P) and keys1; the
@@ -775,19 +790,31 @@ static int depth_first_sort(const UnitTable& U, int64_t P, const gs_proj* proj, 
   uint32_t* dkB = (uint32_t*)k1;
   uint32_t* dvB = dkB + P;
   if (cudaFuncSetAttribute(k_radix_scatter<8, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DYN32) !=
-      cudaSuccess)
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_radix_scatter<9, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DYN32) !=
+          cudaSuccess)
     return GS_ERR_CUDA;
   unsigned gh = resident_blocks(k_radix_hist<8, uint32_t>, RS_T, 0, stride);
   unsigned gsc = resident_blocks(k_radix_scatter<8, uint32_t>, RS_T, DYN32, stride);
-  k_vis_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, P, bsums);
+  unsigned gh9 = resident_blocks(k_radix_hist<9, uint32_t>, RS_T, 0, stride);
+  unsigned gsc9 = resident_blocks(k_radix_scatter<9, uint32_t>, RS_T, DYN32, stride);
+  uint32_t* d_min = d_vis + 1;
+  if (cudaMemsetAsync(d_min, 0xff, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
+  k_vis_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, proj->depth, P, bsums, d_min);
   k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);
-  k_vis_compact<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, proj->depth, P, bsums, nsb, dkA, dvA, d_vis);
+  k_vis_compact<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, proj->depth, P, bsums, nsb, d_min, dkA, dvA, d_vis);
   constexpr int DEPTH_PASSES = 4;
-  for (int pass = 0; pass < DEPTH_PASSES; ++pass) {
-    k_radix_hist<8, uint32_t><<<gh, RS_T, 0, s>>>(dkA, dkB, cur, pass, d_vis, 8 * pass, hist, stride, totals);
+  for (int pass = 0; pass < DEPTH_PASSES - 1; ++pass) {
+    k_radix_hist<9, uint32_t><<<gh9, RS_T, 0, s>>>(dkA, dkB, cur, pass, d_vis, 9 * pass, hist, stride, totals);
+    k_radix_scan<<<512, 1024, 0, s>>>(hist, stride, totals, pass, 512, d_vis, cur);
+    k_radix_scatter<9, uint32_t><<<gsc9, RS_T, DYN32, s>>>(dkA, dkB, dvA, dvB, cur, pass, d_vis, 9 * pass, hist,
+                                                           stride);
+  }
+  {  // bits 27-31 (the 8-bit digit's upper bits are zero)
+    const int pass = DEPTH_PASSES - 1;
+    k_radix_hist<8, uint32_t><<<gh, RS_T, 0, s>>>(dkA, dkB, cur, pass, d_vis, 27, hist, stride, totals);
     k_radix_scan<<<256, 1024, 0, s>>>(hist, stride, totals, pass, 256, d_vis, cur);
-    k_radix_scatter<8, uint32_t><<<gsc, RS_T, DYN32, s>>>(dkA, dkB, dvA, dvB, cur, pass, d_vis, 8 * pass, hist,
-                                                          stride);
+    k_radix_scatter<8, uint32_t><<<gsc, RS_T, DYN32, s>>>(dkA, dkB, dvA, dvB, cur, pass, d_vis, 27, hist, stride);
   }
   k_dup_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(dvA, dvB, cur, DEPTH_PASSES, d_vis, proj->tiles, bsums);
   k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);

@@ -170,3 +170,31 @@ def test_sort_unit_tile_bits(W, H, views):
     cams = synth.orbital_cameras(views, 3.0, width=W, height=H)
     a, b, c = _all(g, cams, 0)
     _same(a, b, c)
+
+
+@pytest.mark.parametrize("z_far", [40.0, 1e6])
+def test_depth_first_sort_depth_range(z_far):
+    """Depths log-uniform from 0.25 to z_far: the depth-first design sorts keys relative to the nearest depth
+    in three 9-bit passes (bits 0-26) and a pass over bits 27-31, which the device skips unless some key
+    reaches 2^27 (z_far = 1e6: depths spanning ~2^22 float32 exponent steps, so the pass runs).  Lists equal
+    the other designs' either way."""
+    rng = np.random.default_rng(int(z_far) % 97)
+    W = H = 128
+    cams = scenes.identity_camera(W, H)
+    f, cx = float(cams.fx[0]), float(cams.cx[0])
+    n = 6000
+    z = np.exp(rng.uniform(np.log(0.25), np.log(z_far), n))
+    u, v = rng.uniform(0, W - 1, n), rng.uniform(0, H - 1, n)
+    means = np.stack([(u - cx) / f * z, (v - cx) / f * z, z], 1)
+    g = dict(means=means.astype(np.float32),
+             log_scales=np.log(rng.uniform(1.0, 12.0, n) * z / f)[:, None].repeat(3, 1).astype(np.float32),
+             quats=np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)),
+             logit_opacity=np.zeros(n, np.float32), sh=np.zeros((n, 1, 3), np.float32))
+    a, b, c = _all(g, cams, 0)
+    _same(a, b, c)
+    fr = gs.Frame(n, gs.Units.single(n), W, H, 0, with_backward=False, with_loss=False)
+    fr.preprocess(gs.pack_params(g, 0), gs.pack_cameras(cams))
+    torch.cuda.synchronize()
+    d = fr.depth.cpu().numpy()[fr.radius.cpu().numpy() > 0].view(np.uint32).astype(np.int64)
+    span = int(d.max() - d.min())
+    assert (span >= 1 << 27) == (z_far > 1e5), span
