@@ -524,8 +524,9 @@ def rooflines(res, workload=None, issue=None, random_order=False):
         # (4 B), depth read and (relative depth, id) written (12 B), 3 depth passes of 4 B histogram read +
         # 8 B read + 8 B written, the histogram of the top bits (4 B; its pass is skipped when the view's
         # relative depths stay below 2^27), count gather (8 B), emission reads (id, xy, conic, radius: 40 B);
-        # per instance: (key, id) written (8 B), tp passes of 20 B, ranges / ids / masks (14 B)
-        sort_bytes = N * 8 + Vv * (4 + 12 + 3 * 20 + 4 + 8 + 40) + I * (8 + tp * 20 + 14)
+        # per instance: (key, id) written (8 B), tp passes of 20 B (the last writes the record ids to the
+        # output), the block mask written by the last pass (2 B), the key read for the ranges (4 B)
+        sort_bytes = N * 8 + Vv * (4 + 12 + 3 * 20 + 4 + 8 + 40) + I * (8 + tp * 20 + 2 + 4)
     else:
         sort_bytes = N * 8 + I * (12 + passes * 32 + 16)
     work = {

@@ -299,12 +299,15 @@ __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ hist
 // counts are scanned across warps.  Keys are then placed in a block-local
 // digit-sorted buffer in shared memory and written out so that each digit's
 // run goes to consecutive global positions (coalesced stores).
-template <int BITS, typename KT>
+template <int BITS, typename KT, bool FINAL = false>
 __global__ void __launch_bounds__(RS_T, sizeof(KT) == 4 ? 3 : 2) k_radix_scatter(KT* __restrict__ k0, KT* __restrict__ k1,
                                                         uint32_t* __restrict__ v0, uint32_t* __restrict__ v1,
                                                         const int32_t* __restrict__ cur, int pass,
                                                         const uint32_t* __restrict__ d_count, int shift,
-                                                        const uint32_t* __restrict__ hist, int64_t stride) {
+                                                        const uint32_t* __restrict__ hist, int64_t stride,
+                                                        uint32_t* __restrict__ vfinal, uint16_t* __restrict__ mfinal) {
+  // FINAL: the values go to vfinal instead of the other value buffer (the last pass of a sort writes the
+  // caller's output directly), and bits 16-31 of each key (the block mask) to mfinal unless it is NULL
   constexpr int BINS = 1 << BITS;
   constexpr int NW = RS_T / 32;
   constexpr int DPT = BINS / RS_T;      // digits per thread in the per-digit steps
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(RS_T, sizeof(KT) == 4 ? 3 : 2) k_radix_scatter
   const KT* kin = c ? k1 : k0;
   const uint32_t* vin = c ? v1 : v0;
   KT* kout = c ? k0 : k1;
-  uint32_t* vout = c ? v0 : v1;
+  uint32_t* vout = FINAL ? vfinal : (c ? v0 : v1);
   int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   // the grid holds as many blocks as stay resident; they take the 4096-key tiles in turn
   for (int64_t t = blockIdx.x; t * RS_TILE < I; t += gridDim.x) {
@@ -421,6 +424,7 @@ __global__ void __launch_bounds__(RS_T, sizeof(KT) == 4 ? 3 : 2) k_radix_scatter
       uint32_t gp = s_off[d] + (uint32_t)i - s_lstart[d];
       kout[gp] = kk;
       vout[gp] = s_vals[i];
+      if (FINAL && mfinal) mfinal[gp] = (uint16_t)((uint64_t)kk >> 16);
     }
     __syncthreads();  // the tile's shared-memory staging is read out before the next tile reuses it
   }
@@ -473,6 +477,8 @@ __global__ void __launch_bounds__(SCAN_T) k_vis_reduce(const uint32_t* __restric
                                                        const float* __restrict__ depth, int64_t P,
                                                        uint32_t* __restrict__ bsums, uint32_t* __restrict__ dmin) {
   __shared__ uint32_t s_warp[33];
+  __shared__ uint32_t s_min;
+  if (threadIdx.x == 0) s_min = 0xffffffffu;
   int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK;
   uint32_t s = 0, mn = 0xffffffffu;
   #pragma unroll
@@ -484,10 +490,15 @@ __global__ void __launch_bounds__(SCAN_T) k_vis_reduce(const uint32_t* __restric
     }
   }
   mn = __reduce_min_sync(0xffffffffu, mn);
-  if ((threadIdx.x & 31) == 0 && mn != 0xffffffffu) atomicMin(dmin, mn);
+  __syncthreads();  // s_min initialised
+  if ((threadIdx.x & 31) == 0) atomicMin(&s_min, mn);
   uint32_t tot;
-  block_excl_scan(s, s_warp, &tot);
-  if (threadIdx.x == 0) bsums[blockIdx.x] = tot;
+  block_excl_scan(s, s_warp, &tot);  // (its barriers also order the shared minimum)
+  // one global atomic per block: per-warp atomics on the one address cost ~30 us at 10M records
+  if (threadIdx.x == 0) {
+    bsums[blockIdx.x] = tot;
+    if (s_min != 0xffffffffu) atomicMin(dmin, s_min);
+  }
 }
 
 // compaction in record order: (depth bits - *dmin, record index) of every visible record; *d_vis = their
@@ -652,7 +663,8 @@ __global__ void __launch_bounds__(SCAN_T, 3) k_dup_emit(UnitTable U, const float
   }
 }
 
-// list ranges, record ids and block masks from the sorted 32-bit instance keys
+// list ranges from the sorted 32-bit instance keys, and the record ids and block masks when the last
+// instance pass was skipped (otherwise that pass wrote them)
 __global__ void __launch_bounds__(256) k_ranges32(const uint32_t* __restrict__ kA, const uint32_t* __restrict__ kB,
                                                   const uint32_t* __restrict__ vA, const uint32_t* __restrict__ vB,
                                                   const int32_t* __restrict__ cur, int final_pass,
@@ -661,16 +673,19 @@ __global__ void __launch_bounds__(256) k_ranges32(const uint32_t* __restrict__ k
                                                   uint16_t* __restrict__ masks) {
   int64_t I = *d_count;
   int c = cur[final_pass];
+  const bool copy = final_pass < 1 || cur[final_pass - 1] == c;  // the last pass was skipped
   const uint32_t* keys = c ? kB : kA;
   const uint32_t* vals = c ? vB : vA;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < I; k += (int64_t)gridDim.x * blockDim.x) {
     uint32_t kk = keys[k];
     uint32_t ut = kk & 0xffffu;
-    out_vals[k] = vals[k];
     int64_t flat = (int64_t)(ut >> tile_bits) * n_tiles + (ut & ((1u << tile_bits) - 1u));
     if (k == 0 || (keys[k - 1] & 0xffffu) != ut) ranges[2 * flat] = (uint32_t)k;
     if (k == I - 1 || (keys[k + 1] & 0xffffu) != ut) ranges[2 * flat + 1] = (uint32_t)(k + 1);
-    if (masks) masks[k] = (uint16_t)(kk >> 16);
+    if (copy) {
+      out_vals[k] = vals[k];
+      if (masks) masks[k] = (uint16_t)(kk >> 16);
+    }
   }
 }
 
@@ -792,12 +807,15 @@ static int depth_first_sort(const UnitTable& U, int64_t P, const gs_proj* proj, 
   if (cudaFuncSetAttribute(k_radix_scatter<8, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DYN32) !=
           cudaSuccess ||
       cudaFuncSetAttribute(k_radix_scatter<9, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DYN32) !=
-          cudaSuccess)
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_radix_scatter<8, uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)DYN32) != cudaSuccess)
     return GS_ERR_CUDA;
   unsigned gh = resident_blocks(k_radix_hist<8, uint32_t>, RS_T, 0, stride);
   unsigned gsc = resident_blocks(k_radix_scatter<8, uint32_t>, RS_T, DYN32, stride);
   unsigned gh9 = resident_blocks(k_radix_hist<9, uint32_t>, RS_T, 0, stride);
   unsigned gsc9 = resident_blocks(k_radix_scatter<9, uint32_t>, RS_T, DYN32, stride);
+  unsigned gscf = resident_blocks(k_radix_scatter<8, uint32_t, true>, RS_T, DYN32, stride);
   uint32_t* d_min = d_vis + 1;
   if (cudaMemsetAsync(d_min, 0xff, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
   k_vis_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, proj->depth, P, bsums, d_min);
@@ -808,13 +826,14 @@ static int depth_first_sort(const UnitTable& U, int64_t P, const gs_proj* proj, 
     k_radix_hist<9, uint32_t><<<gh9, RS_T, 0, s>>>(dkA, dkB, cur, pass, d_vis, 9 * pass, hist, stride, totals);
     k_radix_scan<<<512, 1024, 0, s>>>(hist, stride, totals, pass, 512, d_vis, cur);
     k_radix_scatter<9, uint32_t><<<gsc9, RS_T, DYN32, s>>>(dkA, dkB, dvA, dvB, cur, pass, d_vis, 9 * pass, hist,
-                                                           stride);
+                                                           stride, nullptr, nullptr);
   }
   {  // bits 27-31 (the 8-bit digit's upper bits are zero)
     const int pass = DEPTH_PASSES - 1;
     k_radix_hist<8, uint32_t><<<gh, RS_T, 0, s>>>(dkA, dkB, cur, pass, d_vis, 27, hist, stride, totals);
     k_radix_scan<<<256, 1024, 0, s>>>(hist, stride, totals, pass, 256, d_vis, cur);
-    k_radix_scatter<8, uint32_t><<<gsc, RS_T, DYN32, s>>>(dkA, dkB, dvA, dvB, cur, pass, d_vis, 27, hist, stride);
+    k_radix_scatter<8, uint32_t><<<gsc, RS_T, DYN32, s>>>(dkA, dkB, dvA, dvB, cur, pass, d_vis, 27, hist, stride,
+                                                          nullptr, nullptr);
   }
   k_dup_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(dvA, dvB, cur, DEPTH_PASSES, d_vis, proj->tiles, bsums);
   k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);
@@ -836,8 +855,14 @@ static int depth_first_sort(const UnitTable& U, int64_t P, const gs_proj* proj, 
     k_radix_hist<8, uint32_t><<<gh, RS_T, 0, s>>>(ikA, ikB, cur_t, pass, d_num_instances, 8 * pass, hist, stride,
                                                   totals_t);
     k_radix_scan<<<256, 1024, 0, s>>>(hist, stride, totals_t, pass, 256, d_num_instances, cur_t);
-    k_radix_scatter<8, uint32_t><<<gsc, RS_T, DYN32, s>>>(ikA, ikB, ivA, ivB, cur_t, pass, d_num_instances, 8 * pass,
-                                                          hist, stride);
+    // the last pass writes the record ids and block masks to the outputs (k_ranges32 copies them only
+    // when the device skips that pass)
+    if (pass == tpasses - 1)
+      k_radix_scatter<8, uint32_t, true><<<gscf, RS_T, DYN32, s>>>(ikA, ikB, ivA, ivB, cur_t, pass, d_num_instances,
+                                                                   8 * pass, hist, stride, sorted_vals, block_masks);
+    else
+      k_radix_scatter<8, uint32_t><<<gsc, RS_T, DYN32, s>>>(ikA, ikB, ivA, ivB, cur_t, pass, d_num_instances, 8 * pass,
+                                                            hist, stride, nullptr, nullptr);
   }
   k_ranges32<<<resident_blocks(k_ranges32, 256, 0, (cap + 255) / 256), 256, 0, s>>>(
       ikA, ikB, ivA, ivB, cur_t, tpasses, d_num_instances, tile_bits, n_tiles, ranges, sorted_vals, block_masks);
@@ -937,12 +962,12 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
         k_radix_hist<9, uint64_t><<<gh, RS_T, 0, s>>>(k0, k1, cur, pass, d_num_instances, shift, hist, stride, totals);
         k_radix_scan<<<512, 1024, 0, s>>>(hist, stride, totals, pass, 512, d_num_instances, cur);
         k_radix_scatter<9, uint64_t><<<gs, RS_T, SCATTER_DYN_SMEM, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift,
-                                                               hist, stride);
+                                                               hist, stride, nullptr, nullptr);
       } else {
         k_radix_hist<8, uint64_t><<<gh, RS_T, 0, s>>>(k0, k1, cur, pass, d_num_instances, shift, hist, stride, totals);
         k_radix_scan<<<256, 1024, 0, s>>>(hist, stride, totals, pass, 256, d_num_instances, cur);
         k_radix_scatter<8, uint64_t><<<gs, RS_T, SCATTER_DYN_SMEM, s>>>(k0, k1, v0, v1, cur, pass, d_num_instances, shift,
-                                                               hist, stride);
+                                                               hist, stride, nullptr, nullptr);
       }
     }
     k_ranges<<<resident_blocks(k_ranges, 256, 0, (max_instances + 255) / 256), 256, 0, s>>>(
