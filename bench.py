@@ -522,8 +522,8 @@ def rooflines(res, workload=None, issue=None, random_order=False):
         tp = -(-(key_bits - 32) // 8)
         # per record: tile counts read twice (8 B); per visible record: depth read for the nearest depth
         # (4 B), depth read and (relative depth, id) written (12 B), 3 depth passes of 4 B histogram read +
-        # 8 B read + 8 B written, the histogram of the top bits (4 B; its pass is skipped when the view's
-        # relative depths stay below 2^27), count gather (8 B), emission reads (id, xy, conic, radius: 40 B);
+        # 8 B read + 8 B written, the histogram of the top byte (4 B; its pass is skipped when the view's
+        # relative depths stay below 2^24), count gather (8 B), emission reads (id, xy, conic, radius: 40 B);
         # per instance: (key, id) written (8 B), tp passes of 20 B (the last writes the record ids to the
         # output), the block mask written by the last pass (2 B), the key read for the ranges (4 B)
         sort_bytes = N * 8 + Vv * (4 + 12 + 3 * 20 + 4 + 8 + 40) + I * (8 + tp * 20 + 2 + 4)

@@ -223,10 +223,9 @@ int gs_bin_sort(const gs_proj* proj, const gs_units* units, int width, int heigh
 
 /* How gs_bin_sort orders the lists: it compacts the visible records (tiles >
  * 0) in index order, sorts them by their float32 depth bits taken relative to
- * the nearest visible depth with stable LSD radix passes (three 9-bit digits,
- * then bits 27-31; a digit that every key shares is skipped on the device, so
- * the last pass runs only when the view's depths span more than a factor of
- * ~2^16), emits each record's instances in that order as 32-bit keys
+ * the nearest visible depth with stable LSD radix passes (four 8-bit digits;
+ * a digit that every key shares is skipped on the device, so the top pass runs
+ * only when the view's depths span more than a factor of ~4), emits each record's instances in that order as 32-bit keys
  * (block mask << 16 | unit << tile_bits | tile) and sorts those stably on the
  * unit | tile bits (one or two 8-bit passes): stability leaves every list in
  * (depth, record index) order.  It needs unit | tile ids of at most 16 bits

@@ -484,9 +484,14 @@ __global__ void __launch_bounds__(SCAN_T) k_vis_reduce(const uint32_t* __restric
   #pragma unroll
   for (int j = 0; j < SCAN_ITEMS; ++j) {
     int64_t k = base + (int64_t)j * SCAN_T + threadIdx.x;
-    if (k < P && tiles[k] > 0u) {
-      ++s;
-      mn = min(mn, __float_as_uint(depth[k]));
+    if (k < P) {
+      // both loads issued before either is tested (a depth load behind the visibility test doubled the
+      // kernel's time)
+      uint32_t tk = tiles[k], dk = __float_as_uint(depth[k]);
+      if (tk > 0u) {
+        ++s;
+        mn = min(mn, dk);
+      }
     }
   }
   mn = __reduce_min_sync(0xffffffffu, mn);
@@ -785,10 +790,9 @@ int gs_seg_sort(const UnitTable& U, int64_t P, const gs_proj* proj, int width, i
                 uint32_t* sorted_vals, uint32_t* ranges, uint16_t* masks, cudaStream_t s);
 
 // The depth-first design (method 2): compact the visible records in record order, sort them by their
-// 32-bit depth keys taken relative to the nearest visible depth (three stable 9-bit passes over bits
-// 0-26, then a pass over bits 27-31 that the device skips when every key is below 2^27, as it is when the
-// view's depths stay within a factor of ~2^16 of each other; any pass whose digit all keys share is
-// skipped), scan their
+// 32-bit depth keys taken relative to the nearest visible depth (stable 8-bit passes; a pass whose digit
+// all keys share is skipped on the device: the top one whenever the view's depths stay within a factor
+// of ~4 of each other, so that every relative key is below 2^24), scan their
 // instance counts in that order, emit one 32-bit (mask | unit | tile) key per instance, sort those
 // stably on the unit | tile bits (ut_bits <= 16: one or two 8-bit passes) and read off the lists.
 // Buffers: the record pairs ping-pong between keys0 (keys at word 0, ids at word P) and keys1; the
@@ -806,34 +810,25 @@ static int depth_first_sort(const UnitTable& U, int64_t P, const gs_proj* proj, 
   uint32_t* dvB = dkB + P;
   if (cudaFuncSetAttribute(k_radix_scatter<8, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DYN32) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(k_radix_scatter<9, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DYN32) !=
-          cudaSuccess ||
       cudaFuncSetAttribute(k_radix_scatter<8, uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)DYN32) != cudaSuccess)
     return GS_ERR_CUDA;
   unsigned gh = resident_blocks(k_radix_hist<8, uint32_t>, RS_T, 0, stride);
   unsigned gsc = resident_blocks(k_radix_scatter<8, uint32_t>, RS_T, DYN32, stride);
-  unsigned gh9 = resident_blocks(k_radix_hist<9, uint32_t>, RS_T, 0, stride);
-  unsigned gsc9 = resident_blocks(k_radix_scatter<9, uint32_t>, RS_T, DYN32, stride);
   unsigned gscf = resident_blocks(k_radix_scatter<8, uint32_t, true>, RS_T, DYN32, stride);
   uint32_t* d_min = d_vis + 1;
   if (cudaMemsetAsync(d_min, 0xff, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
   k_vis_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, proj->depth, P, bsums, d_min);
   k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);
   k_vis_compact<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, proj->depth, P, bsums, nsb, d_min, dkA, dvA, d_vis);
+  // (three 9-bit passes and a skipped top pass measured slower: a 9-bit scatter pass took 76 us against
+  // 48 us for an 8-bit one at 10M records)
   constexpr int DEPTH_PASSES = 4;
-  for (int pass = 0; pass < DEPTH_PASSES - 1; ++pass) {
-    k_radix_hist<9, uint32_t><<<gh9, RS_T, 0, s>>>(dkA, dkB, cur, pass, d_vis, 9 * pass, hist, stride, totals);
-    k_radix_scan<<<512, 1024, 0, s>>>(hist, stride, totals, pass, 512, d_vis, cur);
-    k_radix_scatter<9, uint32_t><<<gsc9, RS_T, DYN32, s>>>(dkA, dkB, dvA, dvB, cur, pass, d_vis, 9 * pass, hist,
-                                                           stride, nullptr, nullptr);
-  }
-  {  // bits 27-31 (the 8-bit digit's upper bits are zero)
-    const int pass = DEPTH_PASSES - 1;
-    k_radix_hist<8, uint32_t><<<gh, RS_T, 0, s>>>(dkA, dkB, cur, pass, d_vis, 27, hist, stride, totals);
+  for (int pass = 0; pass < DEPTH_PASSES; ++pass) {
+    k_radix_hist<8, uint32_t><<<gh, RS_T, 0, s>>>(dkA, dkB, cur, pass, d_vis, 8 * pass, hist, stride, totals);
     k_radix_scan<<<256, 1024, 0, s>>>(hist, stride, totals, pass, 256, d_vis, cur);
-    k_radix_scatter<8, uint32_t><<<gsc, RS_T, DYN32, s>>>(dkA, dkB, dvA, dvB, cur, pass, d_vis, 27, hist, stride,
-                                                          nullptr, nullptr);
+    k_radix_scatter<8, uint32_t><<<gsc, RS_T, DYN32, s>>>(dkA, dkB, dvA, dvB, cur, pass, d_vis, 8 * pass, hist,
+                                                          stride, nullptr, nullptr);
   }
   k_dup_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(dvA, dvB, cur, DEPTH_PASSES, d_vis, proj->tiles, bsums);
   k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);

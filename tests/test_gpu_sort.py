@@ -172,18 +172,18 @@ def test_sort_unit_tile_bits(W, H, views):
     _same(a, b, c)
 
 
-@pytest.mark.parametrize("z_far", [40.0, 1e6])
+@pytest.mark.parametrize("z_far", [1.9, 1e6])
 def test_depth_first_sort_depth_range(z_far):
-    """Depths log-uniform from 0.25 to z_far: the depth-first design sorts keys relative to the nearest depth
-    in three 9-bit passes (bits 0-26) and a pass over bits 27-31, which the device skips unless some key
-    reaches 2^27 (z_far = 1e6: depths spanning ~2^22 float32 exponent steps, so the pass runs).  Lists equal
-    the other designs' either way."""
+    """Depths log-uniform from 0.5 to z_far: the depth-first design sorts depth keys relative to the nearest
+    depth in four 8-bit passes, the top one skipped on the device when every relative key is below 2^24
+    (z_far = 1.9: depths within a factor of 4) and run otherwise (z_far = 1e6).  Lists equal the other
+    designs' either way."""
     rng = np.random.default_rng(int(z_far) % 97)
     W = H = 128
     cams = scenes.identity_camera(W, H)
     f, cx = float(cams.fx[0]), float(cams.cx[0])
     n = 6000
-    z = np.exp(rng.uniform(np.log(0.25), np.log(z_far), n))
+    z = np.exp(rng.uniform(np.log(0.5), np.log(z_far), n))
     u, v = rng.uniform(0, W - 1, n), rng.uniform(0, H - 1, n)
     means = np.stack([(u - cx) / f * z, (v - cx) / f * z, z], 1)
     g = dict(means=means.astype(np.float32),
@@ -197,4 +197,4 @@ def test_depth_first_sort_depth_range(z_far):
     torch.cuda.synchronize()
     d = fr.depth.cpu().numpy()[fr.radius.cpu().numpy() > 0].view(np.uint32).astype(np.int64)
     span = int(d.max() - d.min())
-    assert (span >= 1 << 27) == (z_far > 1e5), span
+    assert (span >= 1 << 24) == (z_far > 2.0), span
