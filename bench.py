@@ -834,41 +834,83 @@ def run_cpu_oracle_timing(args):
 
 
 def run_batched(args, wl):
-    """Batched form: all 8 partitions x views-per-step units as one graph-captured step, autotuned."""
+    """Batched form: the partitions x views-per-step units as one graph-captured step, autotuned.  Under
+    torchrun each rank takes the partitions of the longest-first assignment (shard.assign_units, computed on
+    every rank alike) and trains them as its own batched step: no collective on the data path; a barrier
+    around the timed steps and the max of the per-rank times, value = the units of all ranks over it."""
     import torch
     import paper_2509_12138_gb300 as gs
-    from paper_2509_12138_gb300 import train as T, tune, workload
-    torch.cuda.set_device(0)
+    from paper_2509_12138_gb300 import shard, train as T, tune, workload
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        shard.init_group("nccl", timeout_s=300.0, device_id=torch.device("cuda", local))
     import __graft_entry__
     __graft_entry__.build()
     ps = workload.partitioned_scene(wl["slabs"], wl["modes"], wl["views"], wl["W"], wl["H"], n_parts=8, ghost=0.05)
     train_v, test_v = T.split_views(wl["views"], 8)
-    init = gs.pack_params(ps.init, 3)
+    mine = shard.assign_units(np.diff(ps.offsets), world)[rank]
+    idx, off = shard.partition_subset(ps.offsets, mine)
+    if world > 1:  # this rank's partitions only
+        init = gs.pack_params({k: np.asarray(v)[idx] for k, v in ps.init.items()}, 3)
+        gt, mask = ps.gt[mine].contiguous(), ps.mask[mine].contiguous()
+    else:
+        init, gt, mask = gs.pack_params(ps.init, 3), ps.gt, ps.mask
 
     def make(variant, vps, chunk=1024):
-        return T.BatchedTrainer(init.clone(), 3, ps.offsets, ps.cams_dev, ps.gt, ps.mask, train_v,
+        return T.BatchedTrainer(init.clone(), 3, off, ps.cams_dev, gt, mask, train_v,
                                 views_per_step=vps, variant=variant, lr_steps=7000, chunk=chunk)
 
-    best, table = tune.autotune(make, f"batched28M-{wl['W']}x{wl['H']}",
+    best, table = tune.autotune(make, f"batched28M-{wl['W']}x{wl['H']}-{len(mine)}parts",
                                 candidates=[(0, 1, 1024), (0, 1, 512), (1, 1, 1024), (0, 2, 1024)],
                                 steps=3, warmup=2, use_cache=False)
     tr = make(*best)
-    sec = tune.time_trainer(tr, steps=args.steps, warmup=args.warmup)
-    # host time of a step: the graph replay of the one gs_train_batch call (views chosen on the device)
+    for _ in range(args.warmup):
+        tr.step()
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        tr.step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_max = shard.reduce_max([ms], device="cuda")[0]
+    units = tr.units.n * args.steps
+    if dist is not None:
+        u = torch.tensor([units], dtype=torch.int64, device="cuda")
+        dist.all_reduce(u)
+        units = int(u.item())
+    sec = t_max / 1e3 / args.steps
+    # host time of a step: the graph replay of the one gs_train_batch call (views chosen on the device)
     h0 = time.perf_counter()
     for _ in range(args.steps):
         tr.step()
     host_us = (time.perf_counter() - h0) / args.steps * 1e6
     torch.cuda.synchronize()
     st = tr.check()
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
     line = {"metric": "batched train step, 8 ghost-celled partitions (28M Gaussians) x views per step, 1080p",
-            "value": round(tr.units.n / sec, 3), "unit": "(partition, view) units/s",
+            "value": round(units / (t_max / 1e3), 3), "unit": "(partition, view) units/s",
             "steps_per_s": round(1.0 / sec, 3), "ms_per_step": round(sec * 1e3, 3),
-            "host_us_per_step": round(host_us, 1), "n_gpus": 1,
+            "host_us_per_step": round(host_us, 1), "n_gpus": world, "scaling": "strong",
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic", "config": {"workload": args.workload, "gaussians_with_ghosts": int(ps.offsets[-1]),
                                             "slab_sizes": wl["slabs"], "views_per_partition": wl["views"],
+                                            "partitions_of_rank0": mine,
                                             "graph": True, "autotune": {"best": best, "units_per_s": table}},
             "status": st}
     print(json.dumps(line))

@@ -116,13 +116,20 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const uint32_t* __restri
   if (threadIdx.x == 0) bsums[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_bsums(uint32_t* bsums, int64_t nb) {
+// bmins (may be NULL): per-block minima reduced on the way into *dmin
+__global__ void __launch_bounds__(1024) k_scan_bsums(uint32_t* bsums, int64_t nb, const uint32_t* bmins,
+                                                     uint32_t* dmin) {
   __shared__ uint32_t s_warp[33];
   __shared__ uint32_t s_carry;
-  if (threadIdx.x == 0) s_carry = 0;
+  __shared__ uint32_t s_min;
+  if (threadIdx.x == 0) { s_carry = 0; s_min = 0xffffffffu; }
   __syncthreads();
   for (int64_t base = 0; base < nb; base += blockDim.x) {
     int64_t k = base + threadIdx.x;
+    if (bmins) {
+      uint32_t mn = __reduce_min_sync(0xffffffffu, k < nb ? bmins[k] : 0xffffffffu);
+      if ((threadIdx.x & 31) == 0) atomicMin(&s_min, mn);
+    }
     uint32_t v = k < nb ? bsums[k] : 0u;
     uint32_t tot;
     uint32_t ex = block_excl_scan(v, s_warp, &tot);
@@ -132,7 +139,10 @@ __global__ void __launch_bounds__(1024) k_scan_bsums(uint32_t* bsums, int64_t nb
     if (threadIdx.x == 0) s_carry = carry + tot;
     __syncthreads();
   }
-  if (threadIdx.x == 0) bsums[nb] = s_carry;
+  if (threadIdx.x == 0) {
+    bsums[nb] = s_carry;
+    if (bmins) *dmin = s_min;
+  }
 }
 
 __global__ void __launch_bounds__(SCAN_T) k_scan_down(const uint32_t* __restrict__ in, int64_t P,
@@ -471,11 +481,12 @@ __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ k0,
 // each list come out in (depth, record index) order, the order of the global key sort.
 
 // visible records (tiles > 0) per 2048-record scan block, and the smallest depth key among them
-// (*dmin: float32 depth bits, which order as unsigned integers for positive depths; set to all ones
-// before the launch)
+// (bmins: float32 depth bits, which order as unsigned integers for positive depths; all ones for a block
+// without visible records).  k_scan_bsums reduces the block minima: one global atomic per block on a
+// single address took ~30 us at 10M records.
 __global__ void __launch_bounds__(SCAN_T) k_vis_reduce(const uint32_t* __restrict__ tiles,
                                                        const float* __restrict__ depth, int64_t P,
-                                                       uint32_t* __restrict__ bsums, uint32_t* __restrict__ dmin) {
+                                                       uint32_t* __restrict__ bsums, uint32_t* __restrict__ bmins) {
   __shared__ uint32_t s_warp[33];
   __shared__ uint32_t s_min;
   if (threadIdx.x == 0) s_min = 0xffffffffu;
@@ -499,10 +510,9 @@ __global__ void __launch_bounds__(SCAN_T) k_vis_reduce(const uint32_t* __restric
   if ((threadIdx.x & 31) == 0) atomicMin(&s_min, mn);
   uint32_t tot;
   block_excl_scan(s, s_warp, &tot);  // (its barriers also order the shared minimum)
-  // one global atomic per block: per-warp atomics on the one address cost ~30 us at 10M records
   if (threadIdx.x == 0) {
     bsums[blockIdx.x] = tot;
-    if (s_min != 0xffffffffu) atomicMin(dmin, s_min);
+    bmins[blockIdx.x] = s_min;
   }
 }
 
@@ -746,7 +756,7 @@ int gs_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, void* ws, uint32_t
   int64_t nsb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
   uint32_t* bsums = (uint32_t*)ws;
   k_scan_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(in, n, bsums);
-  k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);
+  k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb, nullptr, nullptr);
   k_scan_down<<<(unsigned)nsb, SCAN_T, 0, s>>>(in, n, bsums, nsb, out, INT64_MAX, d_total, nullptr);
   return gs_check_launch();
 }
@@ -800,7 +810,7 @@ int gs_seg_sort(const UnitTable& U, int64_t P, const gs_proj* proj, int width, i
 static int depth_first_sort(const UnitTable& U, int64_t P, const gs_proj* proj, int width, int height, int64_t cap,
                      int tile_bits, int ut_bits, int64_t nsb, int64_t stride, uint32_t* bsums,
                      uint64_t* k0, uint64_t* k1, uint32_t* v0, uint32_t* v1, uint32_t* hist, uint32_t* totals,
-                     int32_t* cur, uint32_t* d_vis, uint32_t* sorted_vals, uint32_t* ranges,
+                     int32_t* cur, uint32_t* d_vis, uint32_t* bmin_ws, uint32_t* sorted_vals, uint32_t* ranges,
                      uint32_t* d_num_instances, uint16_t* block_masks, int* d_status, cudaStream_t s) {
   constexpr size_t DYN32 = RS_TILE * (sizeof(uint32_t) + sizeof(uint32_t));
   int n_tiles = ((width + TILE - 1) / TILE) * ((height + TILE - 1) / TILE);
@@ -817,9 +827,9 @@ static int depth_first_sort(const UnitTable& U, int64_t P, const gs_proj* proj, 
   unsigned gsc = resident_blocks(k_radix_scatter<8, uint32_t>, RS_T, DYN32, stride);
   unsigned gscf = resident_blocks(k_radix_scatter<8, uint32_t, true>, RS_T, DYN32, stride);
   uint32_t* d_min = d_vis + 1;
-  if (cudaMemsetAsync(d_min, 0xff, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
-  k_vis_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, proj->depth, P, bsums, d_min);
-  k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);
+  uint32_t* bmins = bmin_ws;  // nsb entries
+  k_vis_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, proj->depth, P, bsums, bmins);
+  k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb, bmins, d_min);
   k_vis_compact<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, proj->depth, P, bsums, nsb, d_min, dkA, dvA, d_vis);
   // (three 9-bit passes and a skipped top pass measured slower: a 9-bit scatter pass took 76 us against
   // 48 us for an 8-bit one at 10M records)
@@ -831,7 +841,7 @@ static int depth_first_sort(const UnitTable& U, int64_t P, const gs_proj* proj, 
                                                           stride, nullptr, nullptr);
   }
   k_dup_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(dvA, dvB, cur, DEPTH_PASSES, d_vis, proj->tiles, bsums);
-  k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);
+  k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb, nullptr, nullptr);
   int key_masks = block_masks ? 1 : 0;
   uint32_t* ikA = v0;
   uint32_t* ivA = v1;
@@ -918,14 +928,14 @@ int gs_bin_sort_impl(const gs_proj* proj, const gs_units* units, int width, int 
   int64_t nsb = (P + SCAN_BLOCK - 1) / SCAN_BLOCK;
   if (method == 2) {
     int r = depth_first_sort(U, P, proj, width, height, max_instances, tile_bits, tile_bits + unit_bits, nsb, stride,
-                             bsums, k0, k1, v0, v1, hist, totals, cur, (uint32_t*)(ws + L.misc),
+                             bsums, k0, k1, v0, v1, hist, totals, cur, (uint32_t*)(ws + L.misc), offsets,
                              sorted_vals, ranges, d_num_instances, block_masks, d_status, s);
     if (r != GS_OK) return r;
     if (sched) return gs_schedule_jobs(ranges, n_tiles * U.n, ws + L.order, ws + L.jscan, sched, s);
     return gs_check_launch();
   }
   k_scan_reduce<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, P, bsums);
-  k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb);
+  k_scan_bsums<<<1, 1024, 0, s>>>(bsums, nsb, nullptr, nullptr);
   k_scan_down<<<(unsigned)nsb, SCAN_T, 0, s>>>(proj->tiles, P, bsums, nsb, offsets, max_instances,
                                                d_num_instances, d_status);
   if (method == 1) {

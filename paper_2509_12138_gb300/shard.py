@@ -42,6 +42,20 @@ def assign_units(sizes, world: int) -> list[list[int]]:
     return out
 
 
+def partition_subset(offsets, parts) -> tuple[np.ndarray, np.ndarray]:
+    """The Gaussians of partitions `parts` of a partition-major layout (partition k holds
+    [offsets[k], offsets[k + 1])): their indices in partition order and the offsets of the sub-layout
+    (the rank's own partition-major parameter planes)."""
+    offsets = np.asarray(offsets, dtype=np.int64)
+    parts = [int(k) for k in parts]
+    if any(k < 0 or k >= len(offsets) - 1 for k in parts) or len(set(parts)) != len(parts):
+        raise ValueError(f"partitions {parts} not a subset of 0..{len(offsets) - 2}")
+    idx = [np.arange(offsets[k], offsets[k + 1], dtype=np.int64) for k in parts]
+    sizes = [len(a) for a in idx]
+    sub = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return (np.concatenate(idx) if idx else np.zeros(0, np.int64)), sub
+
+
 def reduce_max(values, device=None) -> list[float]:
     """Element-wise max over ranks of a few host scalars (the timing of a measurement); identity when
     torch.distributed is not initialised."""

@@ -100,6 +100,27 @@ def test_merge_gathers_owned_splats_in_rank_order(two_ranks):
     np.testing.assert_array_equal(two_ranks[0]["merged"], np.concatenate(expect, axis=1))
 
 
+def test_partition_subset_covers_each_gaussian_once():
+    """The ranks' partition subsets of a partition-major layout: each Gaussian in exactly one rank's
+    subset, in partition order, with sub-layout offsets of the partitions' sizes."""
+    offsets = np.array([0, 7, 7, 20, 26, 41, 50, 61, 80])
+    sizes = np.diff(offsets)
+    seen = []
+    for world in (1, 2, 3, 8):
+        seen = []
+        for parts in shard.assign_units(sizes, world):
+            idx, sub = shard.partition_subset(offsets, parts)
+            assert np.array_equal(np.diff(sub), sizes[parts])
+            for j, k in enumerate(parts):
+                assert np.array_equal(idx[sub[j]:sub[j + 1]], np.arange(offsets[k], offsets[k + 1]))
+            seen.extend(idx.tolist())
+        assert sorted(seen) == list(range(80))
+    with pytest.raises(ValueError):
+        shard.partition_subset(offsets, [8])
+    with pytest.raises(ValueError):
+        shard.partition_subset(offsets, [1, 1])
+
+
 def test_single_process_paths_need_no_process_group():
     p = torch.ones((3, 4, 4))
     keep = torch.tensor([True, False, True, True])
