@@ -482,7 +482,7 @@ TRAFFIC_WORKLOAD = "iso10M-1080p"
 TRAFFIC_CAPTURED_ON = "iso2M-1080p-prof"
 TRAFFIC_PER_UNIT = {
     "preprocess": ("gaussian", 290.31, TRAFFIC_CAPTURED_ON),
-    "bin_sort": ("instance", 117.57, TRAFFIC_WORKLOAD),
+    "bin_sort": ("instance", 114.20, TRAFFIC_WORKLOAD),
     "render_fwd": None,
     "loss": None,
     "blend_bwd": None,
