@@ -855,9 +855,11 @@ def run_batched(args, wl):
     train_v, test_v = T.split_views(wl["views"], 8)
     mine = shard.assign_units(np.diff(ps.offsets), world)[rank]
     idx, off = shard.partition_subset(ps.offsets, mine)
-    if world > 1:  # this rank's partitions only
+    if world > 1 and mine:  # this rank's partitions only
         init = gs.pack_params({k: np.asarray(v)[idx] for k, v in ps.init.items()}, 3)
         gt, mask = ps.gt[mine].contiguous(), ps.mask[mine].contiguous()
+    elif world > 1:
+        init = gt = mask = None
     else:
         init, gt, mask = gs.pack_params(ps.init, 3), ps.gt, ps.mask
 
@@ -865,19 +867,22 @@ def run_batched(args, wl):
         return T.BatchedTrainer(init.clone(), 3, off, ps.cams_dev, gt, mask, train_v,
                                 views_per_step=vps, variant=variant, lr_steps=7000, chunk=chunk)
 
-    best, table = tune.autotune(make, f"batched28M-{wl['W']}x{wl['H']}-{len(mine)}parts",
-                                candidates=[(0, 1, 1024), (0, 1, 512), (1, 1, 1024), (0, 2, 1024)],
-                                steps=3, warmup=2, use_cache=False)
-    tr = make(*best)
-    for _ in range(args.warmup):
-        tr.step()
+    # a rank without partitions (more ranks than partitions) joins the barriers and reductions with no work
+    tr, best, table = None, None, {}
+    if mine:
+        best, table = tune.autotune(make, f"batched28M-{wl['W']}x{wl['H']}-{len(mine)}parts",
+                                    candidates=[(0, 1, 1024), (0, 1, 512), (1, 1, 1024), (0, 2, 1024)],
+                                    steps=3, warmup=2, use_cache=False)
+        tr = make(*best)
+        for _ in range(args.warmup):
+            tr.step()
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    for _ in range(args.steps):
+    for _ in range(args.steps if tr is not None else 0):
         tr.step()
     b.record()
     torch.cuda.synchronize()
@@ -886,7 +891,7 @@ def run_batched(args, wl):
         dist.barrier()
     torch.cuda.synchronize()
     t_max = shard.reduce_max([ms], device="cuda")[0]
-    units = tr.units.n * args.steps
+    units = tr.units.n * args.steps if tr is not None else 0
     if dist is not None:
         u = torch.tensor([units], dtype=torch.int64, device="cuda")
         dist.all_reduce(u)
@@ -894,11 +899,11 @@ def run_batched(args, wl):
     sec = t_max / 1e3 / args.steps
     # host time of a step: the graph replay of the one gs_train_batch call (views chosen on the device)
     h0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(args.steps if tr is not None else 0):
         tr.step()
     host_us = (time.perf_counter() - h0) / args.steps * 1e6
     torch.cuda.synchronize()
-    st = tr.check()
+    st = tr.check() if tr is not None else 0
     if dist is not None:
         dist.destroy_process_group()
     if rank != 0:
