@@ -1,8 +1,11 @@
-// a2: tile-instance duplication, stable LSD radix sort of 64-bit
-// (unit | tile | depth) keys, and per-tile list ranges.
+// a2: the per-tile lists in (depth, record index) order and their ranges.
+// gs_bin_sort (depth-first design): the visible records sorted by depth once,
+// their tile instances emitted in that order as 32-bit (mask | unit | tile)
+// keys and sorted stably on the unit | tile bits.  gs_bin_sort_global: one
+// stable LSD radix sort of 64-bit (unit | tile | depth) instance keys.
 //
-// Sort design (one pass per 8-bit digit, three kernels per pass, all sized
-// from the instance capacity so the chain is CUDA-graph capturable):
+// Radix passes (one pass per 8- or 9-bit digit, three kernels per pass, all
+// sized from the capacity so the chain is CUDA-graph capturable):
 //   hist    : each 4096-key block builds a 256-bin digit histogram (per-warp
 //             shared-memory bins) and adds it to the pass totals;
 //   scan    : one CTA per digit scans that digit's per-block counts in block
@@ -517,8 +520,8 @@ __global__ void __launch_bounds__(SCAN_T) k_vis_reduce(const uint32_t* __restric
 }
 
 // compaction in record order: (depth bits - *dmin, record index) of every visible record; *d_vis = their
-// number.  Keys relative to the nearest visible depth keep the order and leave the top bits zero: the
-// depths of one view span far fewer than 2^32 float32 steps.
+// number.  Keys relative to the nearest visible depth keep the order and leave the top byte zero when the
+// view's depths stay within a factor of ~4 (then the device skips the top radix pass).
 // Round j of a block covers its records [256 j, 256 j + 256) (coalesced loads); a record's slot is the
 // block's base, the visible records of earlier (round, warp) pairs and those of lower lanes.
 __global__ void __launch_bounds__(SCAN_T) k_vis_compact(const uint32_t* __restrict__ tiles,
