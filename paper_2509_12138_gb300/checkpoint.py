@@ -68,15 +68,20 @@ def save(path: str, state: dict, n_gauss: int, sh_degree: int, step: int) -> Non
     head = _HEAD.pack(MAGIC, VERSION, len(js), int(n_gauss), int(sh_degree), int(step))
     body_start = _pad(len(head) + len(js))
     tmp = f"{path}.tmp"
-    with open(tmp, "wb") as f:
-        f.write(head)
-        f.write(js)
-        f.write(b"\0" * (body_start - len(head) - len(js)))
-        for (name, kind, a), e in zip(arrays, table):
-            b = a.astype(a.dtype.newbyteorder("<"), copy=False).tobytes()
-            f.write(b)
-            f.write(b"\0" * (_pad(len(b)) - len(b)))
-    os.replace(tmp, path)
+    try:
+        with open(tmp, "wb") as f:
+            f.write(head)
+            f.write(js)
+            f.write(b"\0" * (body_start - len(head) - len(js)))
+            for _, _, a in arrays:
+                b = a.astype(a.dtype.newbyteorder("<"), copy=False).tobytes()
+                f.write(b)
+                f.write(b"\0" * (_pad(len(b)) - len(b)))
+        os.replace(tmp, path)
+    except BaseException:
+        if os.path.exists(tmp):
+            os.remove(tmp)
+        raise
 
 
 def read_header(path: str) -> dict:
